@@ -1,0 +1,708 @@
+/*
+ * fluoro_oracle.c -- CPU oracle for the fluorescent participating-media light tracer.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline /
+ * reference leg may load this library. It shares no code, header, table or constant generator
+ * with the CUDA path; both sides implement the same published definitions independently.
+ *
+ * Plain, scalar, fp64, one path at a time (OpenMP only splits the path-id range).
+ * Paper: Abdellah et al., "A Physically Plausible Model for Rendering Highly Scattering
+ * Fluorescent Participating Media" (arXiv 1706.03024).
+ *
+ * What it computes (an unbiased Monte Carlo estimate of the steady, per-wavelength fluorescent
+ * RTE of Sec. 4.2, Eq. 9 and Eq. 11, by light (photon) tracing, Sec. 3):
+ *   - a photon of unit power leaves a source at one spectral line (p(x_n), p(lambda_x) of Eq. 12);
+ *   - free flight by delta tracking against a per-wavelength majorant (transmittance, Eq. 6);
+ *   - at a real collision the particle type is chosen in proportion to its coefficient
+ *     (Sec. 4.1: scatterer, or dye d with share eps_d * a_d(lambda) * c_d);
+ *   - scattering and fluorescent re-emission are isotropic (Sec. 2.1);
+ *   - a dye absorption re-emits with probability QY (Sec. 4.1) at a wavelength drawn from the
+ *     normalised emission spectrum, independent of the exciting wavelength (Eq. 10, Sec. 2.1);
+ *   - photons escaping the medium are tallied per face; every scattering, emission, wall and
+ *     Lambertian-light vertex is connected to the sensor with the three-point form (Eq. 3-6):
+ *     vertex intensity x transmittance x sensor importance.
+ * The transmittance of a connection is the exact line integral of the piecewise-constant
+ * extinction (Eq. 6), not an estimate.
+ *
+ * Pinned by tests/test_oracle_pins.py against closed forms (Beer-Lambert, uncollided
+ * transmission, Chandrasekhar H-function reflectance, thin-dye emission spectrum, slab
+ * fluorescence yield with analytic solid angles, single-scattering film), conservation identities
+ * and brute-force statistics. Adjoint reference: see or_adjoint below.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAX_DYES 4
+#define OR_MAX_EMITTERS 32
+#define OR_MAX_BINS 128
+#define OR_NCOUNTERS 16
+#define OR_PI 3.14159265358979323846
+
+/* counters (same meaning as the GPU library's, defined independently) */
+enum {
+    OC_PATHS = 0, OC_EVENTS, OC_NULLS, OC_ESCAPES, OC_ABSORBED_DEAD, OC_RR_KILLS, OC_CAP_HITS,
+    OC_STEP_BUDGET, OC_CONNECTIONS, OC_VF_REJECTED, OC_WALL_BOUNCES, OC_EMISSIONS, OC_SCATTERS,
+    OC_DYE_ABSORPTIONS, OC_STEPS, OC_MAJORANT_VIOLATIONS
+};
+
+typedef struct {
+    int kind;           /* 0 collimated, 1 Lambertian (cosine-weighted about dir, axis-aligned) */
+    double origin[3];   /* emitting parallelogram origin + a*eu + b*ev, a, b uniform in [0,1) */
+    double eu[3], ev[3];
+    double dir[3];      /* propagation direction (collimated) or surface normal (Lambertian) */
+    double lambda_nm;   /* spectral line */
+    double power;       /* relative power; lines are chosen in proportion (p(lambda_x), Eq. 12) */
+} or_emitter;
+
+typedef struct {
+    int kind;           /* 0 none, 1 orthographic, 2 pinhole */
+    int width, height;
+    double origin[3];   /* ortho: film corner; pinhole: eye */
+    double U[3], V[3];  /* ortho: full film edges; pinhole: right / up unit vectors */
+    double view[3];     /* ortho: direction from the scene to the camera; pinhole: forward axis */
+    double fov_y_deg;   /* pinhole vertical field of view */
+} or_sensor;
+
+typedef struct {
+    /* spectrum */
+    int n_bins;
+    double lambda0, dlambda;
+    /* dyes */
+    int n_dyes;
+    const float *abs_shape;   /* [n_dyes][n_bins] peak-normalised absorption spectrum a_d */
+    const float *emit_spec;   /* [n_dyes][n_bins] emission spectrum f_m (any scale)        */
+    const float *eps;         /* [n_dyes] napierian cm^-1 per unit concentration at peak    */
+    const float *qy;          /* [n_dyes] quantum yield                                      */
+    /* medium */
+    double lo[3], hi[3];
+    int dims[3];              /* grid resolution; all zero => homogeneous                    */
+    const float *conc;        /* [n_dyes][nz][ny][nx] or NULL                                */
+    const float *conc_uniform;/* [n_dyes] used when conc == NULL                             */
+    const uint8_t *solvent;   /* [nz][ny][nx] 0/1 or NULL (solvent everywhere)               */
+    double sigma_s, sigma_a0; /* solvent scattering and flat background absorption, cm^-1   */
+    int wall_mask;            /* bit f: face f is a Lambertian wall                          */
+    double wall_albedo;
+    /* sources */
+    int n_emitters;
+    const or_emitter *emitters;
+    /* sensor */
+    or_sensor sensor;
+} or_scene;
+
+typedef struct {
+    uint64_t n_paths;
+    uint64_t path_offset;
+    uint32_t seed;
+    uint32_t medium_id;
+    int n_rr;                 /* Russian roulette once n_events >= n_rr                      */
+    int max_inelastic;        /* <0 unlimited; k >= 0: the (k+1)-th dye absorption kills     */
+    int analog;               /* 0 weighted QY / albedo, 1 analog coins                      */
+    int n_threads;
+    int64_t max_events;       /* a real collision with n_events == max_events ends the path */
+    int64_t max_steps;        /* tracking-step budget per path                               */
+} or_params;
+
+typedef struct {
+    double *face;             /* [2][6][n_bins]   escaped weight: [fluoresced][face][bin]    */
+    double *absorbed;         /* [n_dyes+1][n_bins] weight absorbed (last row: background)   */
+    double *emitted;          /* [n_dyes][n_bins] weight re-emitted                          */
+    double *film;             /* [H][W][n_bins] or NULL                                      */
+    uint64_t *counters;       /* [OR_NCOUNTERS]                                              */
+    uint32_t *path_events;    /* [n_paths] real events per path, or NULL                     */
+} or_result;
+
+/* ---------------------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+ * SC'11): ten rounds of two 32x32->64 multiplies on a 4-word counter, the key bumped by the
+ * Weyl constants between rounds. */
+static void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* 24-bit uniform in [0,1): exact in fp32 and fp64 */
+static double u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+#define STEP_SPAWN 0xFFFFFFFFu
+
+typedef struct { double u[4]; } block4;
+
+static block4 rng_block(uint32_t seed, uint32_t medium, uint64_t path, uint32_t step, uint32_t slot)
+{
+    uint32_t ctr[4] = { (uint32_t)path, step, slot, (uint32_t)(path >> 32) };
+    uint32_t key[2] = { seed, medium };
+    uint32_t o[4];
+    philox4x32_10(ctr, key, o);
+    block4 b;
+    for (int i = 0; i < 4; ++i) b.u[i] = u24(o[i]);
+    return b;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Spectral tables built from the scene (Eq. 10 and Sec. 4.1). */
+typedef struct {
+    int B, D;
+    double sig_a[OR_MAX_DYES][OR_MAX_BINS];  /* eps_d * a_d(lambda_i), per unit concentration */
+    double cdf[OR_MAX_DYES][OR_MAX_BINS];    /* emission CDF, fp64                           */
+    float cdf32[OR_MAX_DYES][OR_MAX_BINS];   /* the same CDF rounded to fp32 (decision)      */
+    double qy[OR_MAX_DYES];
+    double cmax[OR_MAX_DYES];                /* max concentration over the grid              */
+    double smax;                             /* max solvent indicator                        */
+    double majorant[OR_MAX_BINS];            /* sigma_bar(lambda)                            */
+    int homogeneous;
+    int em_bin[OR_MAX_EMITTERS];
+    float em_cdf32[OR_MAX_EMITTERS];
+    double A_pix, tan_half, aspect;
+} tables;
+
+/* Emission pmf p_i = f_m(lambda_i) / sum_j f_m(lambda_j) (Eq. 10 with the bin as delta-lambda);
+ * CDF_i = (sum_{j<=i} f_j) / (sum_j f_j), summed left to right in fp64, last entry forced to 1. */
+static void build_cdf(const float *f, int B, double *cdf, float *cdf32)
+{
+    double tot = 0.0;
+    for (int i = 0; i < B; ++i) tot += (double)f[i];
+    double run = 0.0;
+    for (int i = 0; i < B; ++i) {
+        run += (double)f[i];
+        cdf[i] = run / tot;
+        cdf32[i] = (float)cdf[i];
+    }
+    cdf[B - 1] = 1.0;
+    cdf32[B - 1] = 1.0f;
+}
+
+/* Nearest bin centre, ties to the lower bin. */
+static int snap_bin(double lambda_nm, double l0, double dl, int B)
+{
+    double b = (lambda_nm - l0) / dl;
+    int k = (int)ceil(b - 0.5);
+    if (k < 0) k = 0;
+    if (k > B - 1) k = B - 1;
+    return k;
+}
+
+static int nvox(const or_scene *s) { return s->dims[0] * s->dims[1] * s->dims[2]; }
+
+static void build_tables(const or_scene *s, tables *t)
+{
+    memset(t, 0, sizeof(*t));
+    t->B = s->n_bins;
+    t->D = s->n_dyes;
+    t->homogeneous = (s->conc == NULL && s->solvent == NULL);
+    for (int d = 0; d < s->n_dyes; ++d) {
+        for (int i = 0; i < s->n_bins; ++i)
+            t->sig_a[d][i] = (double)s->eps[d] * (double)s->abs_shape[d * s->n_bins + i];
+        build_cdf(s->emit_spec + (size_t)d * s->n_bins, s->n_bins, t->cdf[d], t->cdf32[d]);
+        t->qy[d] = (double)s->qy[d];
+        if (s->conc) {
+            double m = 0.0;
+            const float *g = s->conc + (size_t)d * nvox(s);
+            for (int v = 0; v < nvox(s); ++v) if ((double)g[v] > m) m = (double)g[v];
+            t->cmax[d] = m;
+        } else {
+            t->cmax[d] = (double)s->conc_uniform[d];
+        }
+    }
+    t->smax = 1.0;
+    if (s->solvent) {
+        t->smax = 0.0;
+        for (int v = 0; v < nvox(s); ++v) if (s->solvent[v]) { t->smax = 1.0; break; }
+    }
+    for (int i = 0; i < s->n_bins; ++i) {
+        double m = t->smax * (s->sigma_s + s->sigma_a0);
+        for (int d = 0; d < s->n_dyes; ++d) m += t->sig_a[d][i] * t->cmax[d];
+        t->majorant[i] = m;
+    }
+    double ptot = 0.0;
+    for (int k = 0; k < s->n_emitters; ++k) ptot += s->emitters[k].power;
+    double run = 0.0;
+    for (int k = 0; k < s->n_emitters; ++k) {
+        run += s->emitters[k].power;
+        t->em_cdf32[k] = (float)(run / ptot);
+        t->em_bin[k] = snap_bin(s->emitters[k].lambda_nm, s->lambda0, s->dlambda, s->n_bins);
+    }
+    if (s->n_emitters > 0) t->em_cdf32[s->n_emitters - 1] = 1.0f;
+    const or_sensor *c = &s->sensor;
+    if (c->kind == 1) {
+        double lu = sqrt(c->U[0] * c->U[0] + c->U[1] * c->U[1] + c->U[2] * c->U[2]);
+        double lv = sqrt(c->V[0] * c->V[0] + c->V[1] * c->V[1] + c->V[2] * c->V[2]);
+        t->A_pix = lu * lv / ((double)c->width * (double)c->height);
+    } else if (c->kind == 2) {
+        t->tan_half = tan(0.5 * c->fov_y_deg * OR_PI / 180.0);
+        t->aspect = (double)c->width / (double)c->height;
+        t->A_pix = (2.0 * t->tan_half * t->aspect) * (2.0 * t->tan_half) /
+                   ((double)c->width * (double)c->height);
+    }
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Medium: nearest-voxel (piecewise-constant) fields over a grid that spans the AABB. */
+static int voxel_index(const or_scene *s, const double x[3])
+{
+    int idx[3];
+    for (int k = 0; k < 3; ++k) {
+        double f = (x[k] - s->lo[k]) / (s->hi[k] - s->lo[k]) * (double)s->dims[k];
+        int i = (int)floor(f);
+        if (i < 0) i = 0;
+        if (i > s->dims[k] - 1) i = s->dims[k] - 1;
+        idx[k] = i;
+    }
+    return (idx[2] * s->dims[1] + idx[1]) * s->dims[0] + idx[0];
+}
+
+/* Coefficients at a point: solvent part and each dye's absorption (Sec. 4.1):
+ * sigma_t = s(x) (sigma_s + sigma_a0) + sum_d eps_d a_d(lambda) c_d(x). */
+typedef struct { double scat, dye[OR_MAX_DYES], bg, total; } coeffs;
+
+static coeffs coeffs_at(const or_scene *s, const tables *t, const double x[3], int bin)
+{
+    coeffs c;
+    double sv = 1.0;
+    int v = -1;
+    if (!t->homogeneous) v = voxel_index(s, x);
+    if (s->solvent) sv = s->solvent[v] ? 1.0 : 0.0;
+    c.scat = sv * s->sigma_s;
+    c.bg = sv * s->sigma_a0;
+    c.total = c.scat + c.bg;
+    for (int d = 0; d < s->n_dyes; ++d) {
+        double conc = s->conc ? (double)s->conc[(size_t)d * nvox(s) + v] : (double)s->conc_uniform[d];
+        c.dye[d] = t->sig_a[d][bin] * conc;
+        c.total += c.dye[d];
+    }
+    return c;
+}
+
+/* Distance to leave the AABB along (x, w), and the face: faces (-x,+x,-y,+y,-z,+z) = 0..5;
+ * ties go to the lowest face index. */
+static double exit_distance(const or_scene *s, const double x[3], const double w[3], int *face)
+{
+    double best = INFINITY;
+    int bf = -1;
+    for (int k = 0; k < 3; ++k) {
+        double tk;
+        int f;
+        if (w[k] > 0.0)      { tk = (s->hi[k] - x[k]) / w[k]; f = 2 * k + 1; }
+        else if (w[k] < 0.0) { tk = (s->lo[k] - x[k]) / w[k]; f = 2 * k; }
+        else continue;
+        if (tk < 0.0) tk = 0.0;
+        if (tk < best) { best = tk; bf = f; }
+    }
+    *face = bf;
+    return best;
+}
+
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* Exact optical depth int_0^L sigma_t(x0 + t w) dt of the piecewise-constant field (Eq. 6):
+ * the segment is cut at every voxel-plane crossing and sigma_t is evaluated at each piece's
+ * midpoint. */
+static double optical_depth(const or_scene *s, const tables *t, const double x0[3],
+                            const double w[3], double L, int bin)
+{
+    if (L <= 0.0) return 0.0;
+    if (t->homogeneous) {
+        coeffs c = coeffs_at(s, t, x0, bin);
+        return c.total * L;
+    }
+    int cap = 2 + s->dims[0] + s->dims[1] + s->dims[2] + 8;
+    double *cuts = (double *)malloc(sizeof(double) * (size_t)cap);
+    int n = 0;
+    cuts[n++] = 0.0;
+    cuts[n++] = L;
+    for (int k = 0; k < 3; ++k) {
+        if (w[k] == 0.0) continue;
+        double h = (s->hi[k] - s->lo[k]) / (double)s->dims[k];
+        for (int j = 1; j < s->dims[k]; ++j) {
+            double tk = (s->lo[k] + j * h - x0[k]) / w[k];
+            if (tk > 0.0 && tk < L) cuts[n++] = tk;
+        }
+    }
+    qsort(cuts, (size_t)n, sizeof(double), cmp_double);
+    double tau = 0.0;
+    for (int i = 0; i + 1 < n; ++i) {
+        double a = cuts[i], b = cuts[i + 1];
+        if (b <= a) continue;
+        double m = 0.5 * (a + b);
+        double xm[3] = { x0[0] + m * w[0], x0[1] + m * w[1], x0[2] + m * w[2] };
+        coeffs c = coeffs_at(s, t, xm, bin);
+        tau += c.total * (b - a);
+    }
+    free(cuts);
+    return tau;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Directions. */
+static void iso_dir(double u1, double u2, double w[3])
+{
+    double z = 1.0 - 2.0 * u1;
+    double phi = 2.0 * OR_PI * u2;
+    double r = sqrt(fmax(0.0, 1.0 - z * z));
+    w[0] = r * cos(phi);
+    w[1] = r * sin(phi);
+    w[2] = z;
+}
+
+/* Cosine-weighted direction about the axis-aligned normal sign*e_k; tangents e_{k+1}, e_{k+2}. */
+static void cosine_dir(double u1, double u2, int k, double sign, double w[3])
+{
+    double r = sqrt(u1);
+    double phi = 2.0 * OR_PI * u2;
+    double zl = sqrt(fmax(0.0, 1.0 - u1));
+    w[k] = sign * zl;
+    w[(k + 1) % 3] = r * cos(phi);
+    w[(k + 2) % 3] = r * sin(phi);
+}
+
+static void normal_axis(const double n[3], int *k, double *sign)
+{
+    int best = 0;
+    for (int i = 1; i < 3; ++i) if (fabs(n[i]) > fabs(n[best])) best = i;
+    *k = best;
+    *sign = n[best] > 0.0 ? 1.0 : -1.0;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Sensor connection (Eq. 3-6): contribution = vertex intensity toward the sensor
+ * x transmittance x sensor importance.
+ *   vertex intensity per unit photon weight: 1/(4 pi) for isotropic medium vertices (Sec. 2.1),
+ *   cos(theta_o)/pi for Lambertian wall and light vertices.
+ *   ortho importance: 1/A_pix (film = radiance averaged over the pixel's area);
+ *   pinhole importance x geometry: 1/(A_pix r^2 cos^3 theta), A_pix the pixel area on the
+ *   image plane at unit distance (film = radiance averaged over image-plane area).
+ * The connecting segment must leave the box through an open (non-wall) face. */
+typedef struct { int lambertian; int axis; double sign; } vtx_kind;
+
+static void connect_sensor(const or_scene *s, const tables *t, const double x[3], int bin,
+                           double w, vtx_kind vk, double *film, uint64_t *cnt)
+{
+    const or_sensor *c = &s->sensor;
+    if (c->kind == 0 || film == NULL) return;
+    double dir[3], geom, r2 = 0.0;
+    int px, py;
+    if (c->kind == 1) {
+        for (int k = 0; k < 3; ++k) dir[k] = c->view[k];
+        double d[3] = { x[0] - c->origin[0], x[1] - c->origin[1], x[2] - c->origin[2] };
+        double uu = c->U[0] * c->U[0] + c->U[1] * c->U[1] + c->U[2] * c->U[2];
+        double vv = c->V[0] * c->V[0] + c->V[1] * c->V[1] + c->V[2] * c->V[2];
+        double su = (d[0] * c->U[0] + d[1] * c->U[1] + d[2] * c->U[2]) / uu;
+        double sv = (d[0] * c->V[0] + d[1] * c->V[1] + d[2] * c->V[2]) / vv;
+        if (!(su >= 0.0 && su < 1.0 && sv >= 0.0 && sv < 1.0)) return;
+        px = (int)floor(su * c->width);
+        py = (int)floor(sv * c->height);
+        if (px >= c->width || py >= c->height) return;
+        geom = 1.0 / t->A_pix;
+    } else {
+        double v[3] = { x[0] - c->origin[0], x[1] - c->origin[1], x[2] - c->origin[2] };
+        r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        double r = sqrt(r2);
+        double zf = v[0] * c->view[0] + v[1] * c->view[1] + v[2] * c->view[2];
+        if (!(zf > 0.0)) return;
+        double X = (v[0] * c->U[0] + v[1] * c->U[1] + v[2] * c->U[2]) / zf;
+        double Y = (v[0] * c->V[0] + v[1] * c->V[1] + v[2] * c->V[2]) / zf;
+        double sx = 0.5 * (X / (t->tan_half * t->aspect) + 1.0);
+        double sy = 0.5 * (Y / t->tan_half + 1.0);
+        if (!(sx >= 0.0 && sx < 1.0 && sy >= 0.0 && sy < 1.0)) return;
+        px = (int)floor(sx * c->width);
+        py = (int)floor(sy * c->height);
+        if (px >= c->width || py >= c->height) return;
+        for (int k = 0; k < 3; ++k) dir[k] = -v[k] / r;
+        double cos_t = zf / r;
+        geom = 1.0 / (t->A_pix * r2 * cos_t * cos_t * cos_t);
+    }
+    double f;
+    if (vk.lambertian) {
+        double co = vk.sign * dir[vk.axis];
+        if (!(co > 0.0)) return;
+        f = co / OR_PI;
+    } else {
+        f = 1.0 / (4.0 * OR_PI);
+    }
+    int face;
+    double tl = exit_distance(s, x, dir, &face);
+    if (face < 0) return;
+    if (s->wall_mask & (1 << face)) return;
+    if (c->kind == 2 && tl * tl > r2) return; /* eye inside the box: not supported, skip */
+    double T = exp(-optical_depth(s, t, x, dir, tl, bin));
+    double val = w * f * T * geom;
+    size_t idx = ((size_t)py * c->width + px) * t->B + bin;
+#pragma omp atomic
+    film[idx] += val;
+    cnt[OC_CONNECTIONS]++;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* One photon path. */
+typedef struct {
+    double face[2][6][OR_MAX_BINS];
+    double absorbed[OR_MAX_DYES + 1][OR_MAX_BINS];
+    double emitted[OR_MAX_DYES][OR_MAX_BINS];
+    uint64_t cnt[OR_NCOUNTERS];
+} local_tally;
+
+static int sample_emitter(const tables *t, int n, double u)
+{
+    for (int k = 0; k < n; ++k) if ((double)t->em_cdf32[k] > u) return k;
+    return n - 1;
+}
+
+/* lambda' = min{ i : CDF_d[i] > u }, decided on the fp32-rounded CDF. */
+static int sample_emission_bin(const tables *t, int d, double u)
+{
+    for (int i = 0; i < t->B; ++i) if ((double)t->cdf32[d][i] > u) return i;
+    return t->B - 1;
+}
+
+static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *p, uint64_t pid,
+                           local_tally *lt, double *film)
+{
+    uint64_t *cnt = lt->cnt;
+    cnt[OC_PATHS]++;
+    /* spawn (Eq. 12: p(x_n), p(lambda_x)) */
+    block4 S0 = rng_block(p->seed, p->medium_id, pid, STEP_SPAWN, 0);
+    int ek = sample_emitter(t, s->n_emitters, S0.u[0]);
+    const or_emitter *em = &s->emitters[ek];
+    double x[3], w[3];
+    for (int k = 0; k < 3; ++k) x[k] = em->origin[k] + S0.u[1] * em->eu[k] + S0.u[2] * em->ev[k];
+    int bin = t->em_bin[ek];
+    double wt = 1.0;
+    if (em->kind == 1) {
+        block4 S1 = rng_block(p->seed, p->medium_id, pid, STEP_SPAWN, 1);
+        int ax; double sg;
+        normal_axis(em->dir, &ax, &sg);
+        cosine_dir(S0.u[3], S1.u[0], ax, sg, w);
+        vtx_kind vk = { 1, ax, sg };
+        connect_sensor(s, t, x, bin, wt, vk, film, cnt);
+    } else {
+        for (int k = 0; k < 3; ++k) w[k] = em->dir[k];
+    }
+    int64_t n_events = 0;
+    int n_inel = 0;
+    int fl = 0;
+    for (int64_t step = 0;; ++step) {
+        if (step >= p->max_steps) { cnt[OC_STEP_BUDGET]++; break; }
+        cnt[OC_STEPS]++;
+        block4 B0 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 0);
+        double sb = t->majorant[bin];
+        double tf = sb > 0.0 ? -log(1.0 - B0.u[0]) / sb : INFINITY;
+        int face;
+        double te = exit_distance(s, x, w, &face);
+        if (tf >= te) {
+            for (int k = 0; k < 3; ++k) x[k] += te * w[k];
+            if (s->wall_mask & (1 << face)) {
+                /* Lambertian wall: a real event */
+                if (n_events == p->max_events) { cnt[OC_CAP_HITS]++; break; }
+                n_events++;
+                cnt[OC_EVENTS]++;
+                cnt[OC_WALL_BOUNCES]++;
+                block4 B1 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 1);
+                if (p->analog) {
+                    if (!(B1.u[3] < s->wall_albedo)) { cnt[OC_ABSORBED_DEAD]++; break; }
+                } else {
+                    wt *= s->wall_albedo;
+                    if (wt == 0.0) { cnt[OC_ABSORBED_DEAD]++; break; }
+                }
+                int ax = face / 2;
+                double sg = (face & 1) ? -1.0 : 1.0;   /* inward normal */
+                /* snap onto the wall plane */
+                x[ax] = (face & 1) ? s->hi[ax] : s->lo[ax];
+                cosine_dir(B0.u[2], B0.u[3], ax, sg, w);
+                vtx_kind vk = { 1, ax, sg };
+                connect_sensor(s, t, x, bin, wt, vk, film, cnt);
+                if (n_events >= p->n_rr) {
+                    double q = wt < 1.0 ? wt : 1.0;
+                    if (!(B1.u[2] < q)) { cnt[OC_RR_KILLS]++; break; }
+                    wt /= q;
+                }
+                continue;
+            }
+            lt->face[fl][face][bin] += wt;
+            cnt[OC_ESCAPES]++;
+            break;
+        }
+        for (int k = 0; k < 3; ++k) x[k] += tf * w[k];
+        coeffs c = coeffs_at(s, t, x, bin);
+        if (c.total > sb) cnt[OC_MAJORANT_VIOLATIONS]++;
+        if (!(B0.u[1] * sb < c.total)) { cnt[OC_NULLS]++; continue; }
+        /* real collision */
+        if (n_events == p->max_events) { cnt[OC_CAP_HITS]++; break; }
+        n_events++;
+        cnt[OC_EVENTS]++;
+        block4 B1 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 1);
+        /* particle type in proportion to its coefficient (Sec. 4.1) */
+        double ue = B0.u[2] * c.total;
+        double acc = c.scat;
+        int ev = -1;          /* -1 scatter, 0..D-1 dye, D background */
+        if (!(ue < acc)) {
+            ev = s->n_dyes;
+            for (int d = 0; d < s->n_dyes; ++d) {
+                acc += c.dye[d];
+                if (ue < acc) { ev = d; break; }
+            }
+        }
+        if (ev < 0) {
+            cnt[OC_SCATTERS]++;
+            iso_dir(B0.u[3], B1.u[0], w);
+            vtx_kind vk = { 0, 0, 0.0 };
+            connect_sensor(s, t, x, bin, wt, vk, film, cnt);
+        } else if (ev < s->n_dyes) {
+            cnt[OC_DYE_ABSORPTIONS]++;
+            lt->absorbed[ev][bin] += wt;
+            if (p->max_inelastic >= 0 && n_inel >= p->max_inelastic) { cnt[OC_VF_REJECTED]++; break; }
+            if (p->analog) {
+                if (!(B1.u[3] < t->qy[ev])) { cnt[OC_ABSORBED_DEAD]++; break; }
+            } else {
+                wt *= t->qy[ev];
+                if (wt == 0.0) { cnt[OC_ABSORBED_DEAD]++; break; }
+            }
+            bin = sample_emission_bin(t, ev, B1.u[1]);
+            lt->emitted[ev][bin] += wt;
+            cnt[OC_EMISSIONS]++;
+            n_inel++;
+            fl = 1;
+            iso_dir(B0.u[3], B1.u[0], w);
+            vtx_kind vk = { 0, 0, 0.0 };
+            connect_sensor(s, t, x, bin, wt, vk, film, cnt);
+        } else {
+            lt->absorbed[s->n_dyes][bin] += wt;
+            cnt[OC_ABSORBED_DEAD]++;
+            break;
+        }
+        if (n_events >= p->n_rr) {
+            double q = wt < 1.0 ? wt : 1.0;
+            if (!(B1.u[2] < q)) { cnt[OC_RR_KILLS]++; break; }
+            wt /= q;
+        }
+    }
+    return (uint32_t)n_events;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Exported API (ctypes). Return 0 on success, negative on invalid input. */
+
+int or_render(const or_scene *s, const or_params *p, or_result *r)
+{
+    if (!s || !p || !r) return -1;
+    if (s->n_bins <= 0 || s->n_bins > OR_MAX_BINS) return -1;
+    if (s->n_dyes < 0 || s->n_dyes > OR_MAX_DYES) return -1;
+    if (s->n_emitters <= 0 || s->n_emitters > OR_MAX_EMITTERS) return -1;
+    tables *t = (tables *)malloc(sizeof(tables));
+    build_tables(s, t);
+    int B = s->n_bins, D = s->n_dyes;
+    memset(r->face, 0, sizeof(double) * 2 * 6 * B);
+    memset(r->absorbed, 0, sizeof(double) * (D + 1) * B);
+    if (D > 0) memset(r->emitted, 0, sizeof(double) * D * B);
+    memset(r->counters, 0, sizeof(uint64_t) * OR_NCOUNTERS);
+    if (r->film && s->sensor.kind)
+        memset(r->film, 0, sizeof(double) * (size_t)s->sensor.width * s->sensor.height * B);
+#ifdef _OPENMP
+    if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+#endif
+    int64_t N = (int64_t)p->n_paths;
+#pragma omp parallel
+    {
+        local_tally *lt = (local_tally *)calloc(1, sizeof(local_tally));
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < N; ++i) {
+            uint32_t ne = trace_path(s, t, p, p->path_offset + (uint64_t)i, lt, r->film);
+            if (r->path_events) r->path_events[i] = ne;
+        }
+#pragma omp critical
+        {
+            for (int fl = 0; fl < 2; ++fl)
+                for (int f = 0; f < 6; ++f)
+                    for (int b = 0; b < B; ++b) r->face[(fl * 6 + f) * B + b] += lt->face[fl][f][b];
+            for (int d = 0; d <= D; ++d)
+                for (int b = 0; b < B; ++b) r->absorbed[d * B + b] += lt->absorbed[d][b];
+            for (int d = 0; d < D; ++d)
+                for (int b = 0; b < B; ++b) r->emitted[d * B + b] += lt->emitted[d][b];
+            for (int k = 0; k < OR_NCOUNTERS; ++k) r->counters[k] += lt->cnt[k];
+        }
+        free(lt);
+    }
+    /* tallies are per launched path */
+    double inv = N > 0 ? 1.0 / (double)N : 0.0;
+    for (int i = 0; i < 2 * 6 * B; ++i) r->face[i] *= inv;
+    for (int i = 0; i < (D + 1) * B; ++i) r->absorbed[i] *= inv;
+    for (int i = 0; i < D * B; ++i) r->emitted[i] *= inv;
+    if (r->film && s->sensor.kind) {
+        size_t n = (size_t)s->sensor.width * s->sensor.height * B;
+        for (size_t i = 0; i < n; ++i) r->film[i] *= inv;
+    }
+    free(t);
+    return 0;
+}
+
+/* Raw Philox blocks, for statistical tests of the generator. */
+void or_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr /*[n][4]*/, int64_t n,
+               uint32_t *out /*[n][4]*/)
+{
+    uint32_t key[2] = { seed, medium };
+    for (int64_t i = 0; i < n; ++i) philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
+/* Emission-bin sampling for the scene's dye d at n given uniforms (fp32-decided CDF). */
+int or_sample_emission(const or_scene *s, int d, const double *u, int64_t n, int32_t *out)
+{
+    if (d < 0 || d >= s->n_dyes) return -1;
+    tables *t = (tables *)malloc(sizeof(tables));
+    build_tables(s, t);
+    for (int64_t i = 0; i < n; ++i) out[i] = sample_emission_bin(t, d, u[i]);
+    free(t);
+    return 0;
+}
+
+void or_iso_dir(const double *u1, const double *u2, int64_t n, double *out /*[n][3]*/)
+{
+    for (int64_t i = 0; i < n; ++i) iso_dir(u1[i], u2[i], out + 3 * i);
+}
+
+void or_cosine_dir(const double *u1, const double *u2, int64_t n, int axis, double sign,
+                   double *out)
+{
+    for (int64_t i = 0; i < n; ++i) cosine_dir(u1[i], u2[i], axis, sign, out + 3 * i);
+}
+
+/* Optical depth along [x0, x0 + L w] at bin (exact, Eq. 6), and the majorant table. */
+double or_optical_depth(const or_scene *s, const double *x0, const double *w, double L, int bin)
+{
+    tables *t = (tables *)malloc(sizeof(tables));
+    build_tables(s, t);
+    double tau = optical_depth(s, t, x0, w, L, bin);
+    free(t);
+    return tau;
+}
+
+void or_majorant(const or_scene *s, double *out)
+{
+    tables *t = (tables *)malloc(sizeof(tables));
+    build_tables(s, t);
+    for (int i = 0; i < s->n_bins; ++i) out[i] = t->majorant[i];
+    free(t);
+}
+
+int or_counters_count(void) { return OR_NCOUNTERS; }

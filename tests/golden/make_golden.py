@@ -1,0 +1,33 @@
+"""Writes the stored oracle outputs under tests/golden/ (calls only oracle/ and scenegen).
+
+Run from the repository root:  python tests/golden/make_golden.py
+The fixture pins the oracle against accidental drift (tests/test_golden.py) and gives the GPU
+parity tests per-path event counts to measure how often the two sides take identical paths.
+"""
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle  # noqa: E402
+import scenegen as sg  # noqa: E402
+
+
+def main():
+    sc = sg.cfg1_homogeneous_cube(n_paths=512)
+    r = oracle.render(sc, n_threads=1, path_events=True)
+    out = {
+        "scene": "cfg1_homogeneous_cube (scenegen), seed 0, paths 0..511, weighted QY mode",
+        "path_events": [int(v) for v in r["path_events"]],
+        "counters": r["counters"],
+        "face_total": [float(v) for v in r["face"].sum(axis=2).ravel()],
+        "emitted_total": float(r["emitted"].sum()),
+    }
+    with open(os.path.join(HERE, "cfg1_512_paths.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

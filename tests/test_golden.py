@@ -1,0 +1,19 @@
+"""The oracle reproduces its stored outputs (tests/golden/make_golden.py wrote them)."""
+import json
+import os
+
+import numpy as np
+
+import oracle
+import scenegen as sg
+
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def test_oracle_matches_stored_cfg1_paths():
+    with open(os.path.join(HERE, "cfg1_512_paths.json")) as f:
+        g = json.load(f)
+    r = oracle.render(sg.cfg1_homogeneous_cube(n_paths=512), n_threads=2, path_events=True)
+    assert [int(v) for v in r["path_events"]] == g["path_events"]
+    assert r["counters"] == g["counters"]
+    assert np.allclose(r["face"].sum(axis=2).ravel(), g["face_total"], rtol=1e-12, atol=1e-15)
