@@ -1,0 +1,342 @@
+"""Benchmark: medium events/s of the GPU light tracer on the Cornell-box workload.
+
+Workload (one step): the 4-sphere Cornell box, 4 Gaussian dyes on 128^3 fp32 grids, Lambertian
+walls, a ceiling light with 4 lines, 512x512 pinhole film x 81 bins, 16 paths per pixel
+(4,194,304 photon paths). `value` is whole-job events/s of the forward (wavefront) form with the
+scene resident in HBM; `forms` also reports the plain one-thread-per-path kernel on the same
+paths (same estimator, same paths, hence equal RMSE). `e2e` runs the same step through the C ABI
+from pinned host buffers: grid upload, flr_set_medium, flr_render and the film read-back.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank traces its own path-id range (weak scaling, no collective on the data
+path); timing is the max over ranks. --impl reference times the CPU oracle (fp64, the machine's host
+cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenegen as sg  # noqa: E402
+
+METRIC = "medium events/s (fwd, batched, adjoint) vs plain GPU kernel at equal RMSE"
+WORKLOAD = "cornell box: 4 dye spheres, 128^3 x4 fp32 grids, 512x512 pinhole x 81 bins, 16 spp"
+
+# 32-bit lane operations per unit of work ("ALU roofline"): a Philox4x32-10 block,
+# a tracking step, a real event, a sensor connection and a ratio-tracking step.
+OPS_PHILOX = 112
+OPS_STEP = OPS_PHILOX + 55
+OPS_EVENT = OPS_PHILOX + 30
+OPS_CONNECT = 45
+OPS_CONNECT_STEP = OPS_PHILOX // 4 + 36
+
+
+def algorithmic_ops(c):
+    return (c["steps"] * OPS_STEP + c["events"] * OPS_EVENT + c["connections"] * OPS_CONNECT
+            + c["connect_steps"] * OPS_CONNECT_STEP)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def start_clock_sampler(gpu_index, path):
+    cmd = ["nvidia-smi", f"--id={gpu_index}",
+           "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(cmd, stdout=f, stderr=subprocess.DEVNULL), f
+    except (OSError, FileNotFoundError):
+        return None, None
+
+
+def stop_clock_sampler(proc, f, path):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    f.close()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_oracle_rate(sc, n_paths, n_threads=0, film=True):
+    import oracle
+    t = time.perf_counter()
+    r = oracle.render(sc, n_paths=n_paths, n_threads=n_threads, film=film)
+    dt = time.perf_counter() - t
+    c = r["counters"]
+    return {"events": c["events"], "paths": c["paths"], "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    sc = sg.cfg2_cornell_box()
+    n_sample = args.ref_paths
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        cpu_oracle_rate(sc, max(n_sample // 8, 1024))
+    ev, sec = 0, 0.0
+    for _ in range(args.steps):
+        r = cpu_oracle_rate(sc, n_sample)
+        ev += r["events"]
+        sec += r["seconds"]
+    value = ev / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "paths_per_step": n_sample,
+                   "note": "CPU oracle on a bounded sample of the same scene"},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n_sample} paths of the Cornell-box workload per step"},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1706_03024_gb300 import build as B
+    from paper_1706_03024_gb300 import native as N
+    from paper_1706_03024_gb300.scene import Scene
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    B.build()
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    sc = sg.cfg2_cornell_box()
+    n_paths = sc["params"]["n_paths"]
+    S = Scene(sc, device=local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    offset = rank * n_paths  # each rank its own path-id range
+
+    def one_step(form):
+        S.render(form=form, path_offset=offset, regroup=args.regroup)
+
+    def timed(form, steps, sampler_path=None):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        events = 0
+        counters = None
+        barrier()
+        torch.cuda.synchronize()
+        proc = f = None
+        if sampler_path:
+            proc, f = start_clock_sampler(local, sampler_path)
+        for i in range(steps):
+            flush.fill_(float(i))          # evict the scene and film from L2 between steps
+            evs[i][0].record(stream)
+            one_step(form)
+            evs[i][1].record(stream)
+            r = S.read() if i == steps - 1 else None
+            if r is not None:
+                counters = r["counters"]
+        torch.cuda.synchronize()
+        barrier()
+        clocks = stop_clock_sampler(proc, f, sampler_path) if sampler_path else None
+        ms = [a.elapsed_time(b) for a, b in evs]
+        events = counters["events"]
+        return ms, events, counters, clocks
+
+    for _ in range(args.warmup):
+        one_step("wavefront")
+        one_step("plain")
+    torch.cuda.synchronize()
+
+    ms_w, ev_w, cnt_w, clocks = timed("wavefront", args.steps,
+                                      os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                                      if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                                      else f"/tmp/clocks_rank{rank}.csv")
+    ms_p, ev_p, cnt_p, _ = timed("plain", max(1, min(args.steps, args.plain_steps)))
+
+    def reduce_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def reduce_sum(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    step_ms_w = reduce_max(sum(ms_w) / len(ms_w))
+    step_ms_p = reduce_max(sum(ms_p) / len(ms_p))
+    total_ev_w = reduce_sum(float(ev_w))
+    total_ev_p = reduce_sum(float(ev_p))
+    value = total_ev_w / (step_ms_w / 1000.0)
+    plain_value = total_ev_p / (step_ms_p / 1000.0)
+    paths_per_s = reduce_sum(float(n_paths)) / (step_ms_w / 1000.0)
+
+    # --- end to end through the C ABI with host buffers ------------------------------------
+    md = sc["medium"]
+    conc_h = torch.from_numpy(np.ascontiguousarray(md["conc"])).pin_memory()
+    solv_h = torch.from_numpy(np.ascontiguousarray(md["solvent"])).pin_memory()
+    conc_d = torch.empty_like(conc_h, device=dev)
+    solv_d = torch.empty_like(solv_h, device=dev)
+    film_h = torch.empty(S.film_tensor().shape, dtype=torch.float32).pin_memory()
+    h2d = conc_h.numel() * 4 + solv_h.numel()
+    d2h = film_h.numel() * 4 + 2 * 6 * S.B * 8
+
+    def e2e_step():
+        conc_d.copy_(conc_h, non_blocking=True)
+        solv_d.copy_(solv_h, non_blocking=True)
+        S.set_medium(md, grids={"conc": conc_d, "solvent": solv_d})
+        f = S.render(form="wavefront", path_offset=offset, regroup=args.regroup)
+        film_h.copy_(f, non_blocking=True)
+        return S.read()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_events = 0
+    for _ in range(args.e2e_steps):
+        e2e_events += e2e_step()["counters"]["events"]
+    torch.cuda.synchronize()
+    e2e_s = reduce_max((time.perf_counter() - t0) / args.e2e_steps)
+    e2e_value = reduce_sum(float(e2e_events / args.e2e_steps)) / e2e_s
+
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = sms * 128 * sm_max * 1e6
+    ops = algorithmic_ops(cnt_w)
+    achieved = ops / (sum(ms_w) / len(ms_w) / 1000.0)
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "trace_wavefront_cornell_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        r = cpu_oracle_rate(sc, args.cpu_paths)
+        cpu = {"value": r["events"] / r["seconds"], "unit": "events/s",
+               "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"{args.cpu_paths} paths of the same workload (fp64, all host cores), "
+                         f"{r['seconds']:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms_w,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "paths_per_gpu": n_paths, "form": "wavefront",
+                       "regroup": args.regroup,
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "events_per_step": ev_w, "parallelism": f"paths sharded over {world} GPU(s)"},
+            "paths_per_s": paths_per_s,
+            "forms": {
+                "wavefront": {"events_per_s": value, "ms_per_step": step_ms_w},
+                "plain": {"events_per_s": plain_value, "ms_per_step": step_ms_p,
+                          "steps": len(ms_p)},
+                "speedup_vs_plain": value / plain_value,
+                "equal_rmse": "same estimator and the same path ids in both forms",
+            },
+            "counters_per_step": cnt_w,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic,
+                         "note": f"32-bit lane ops from counters x per-unit counts; peak = {sms} SMs"
+                                 f" x 128 lanes x {sm_max:.0f} MHz"},
+            "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps + len(ms_p),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--regroup", type=int, default=0)
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-paths", type=int, default=1 << 17)
+    ap.add_argument("--ref-paths", type=int, default=1 << 16)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,201 @@
+/*
+ * fluoro.h -- C ABI of the GB300 (sm_103a) fluorescent participating-media light tracer.
+ *
+ * Method: Abdellah et al., "A Physically Plausible Model for Rendering Highly Scattering
+ * Fluorescent Participating Media" (arXiv 1706.03024). Photons of one wavelength each are traced
+ * through a scattering medium holding fluorescent dyes (Sec. 4.1); at a dye absorption the photon
+ * is re-emitted with probability QY at a wavelength drawn from the dye's normalised emission
+ * spectrum (Eq. 10), isotropically (Sec. 2.1); transmittance follows Beer-Lambert (Eq. 6); the
+ * sensor is reached by three-point connections (Eq. 3-5); the estimator averages over paths and
+ * source lines (Eq. 12).
+ *
+ * Conventions for every entry point:
+ *   - Return value: FLR_OK (0) or a negative FLR_ERR_* code. Nothing throws across the ABI.
+ *     flr_last_error(ctx) gives a one-line description of the last failure on that context.
+ *   - "host" pointers are CPU memory read during the call and not retained. "device" pointers
+ *     are CUDA global memory on the context's device, owned by the caller, and must stay valid
+ *     until the work queued on the given stream has finished.
+ *   - Streams are passed as void* holding a cudaStream_t (NULL = the legacy default stream).
+ *     Render calls are asynchronous on that stream; flr_read_tallies and flr_status synchronise.
+ *   - Spectra are sampled on a uniform grid of n_bins bin centres lambda_i = lambda0 + i dlambda.
+ *   - Faces of the box are numbered (-x, +x, -y, +y, -z, +z) = 0..5.
+ *   - Voxel grids are fp32 [nz][ny][nx] (x fastest) spanning the medium's box; lookups take the
+ *     nearest voxel (piecewise-constant field).
+ *   - One context is used by one host thread at a time.
+ */
+#ifndef FLUORO_H
+#define FLUORO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FLR_OK 0
+#define FLR_ERR_ARG (-1)     /* invalid argument; nothing was changed or launched           */
+#define FLR_ERR_CUDA (-2)    /* a CUDA call failed; see flr_last_error                       */
+#define FLR_ERR_OOM (-3)     /* device allocation failed                                     */
+#define FLR_ERR_BUDGET (-4)  /* a device loop budget ran out (paths were cut short)          */
+#define FLR_ERR_STATE (-5)   /* call out of order (e.g. render before a medium is set)       */
+
+#define FLR_MAX_BINS 128
+#define FLR_MAX_DYES 1024           /* dye table size                                      */
+#define FLR_MAX_DYES_PER_MEDIUM 4
+#define FLR_MAX_SOURCES 64
+#define FLR_MAX_LINES 8
+#define FLR_MAX_EMITTERS 32         /* spectral lines over all sources of one medium       */
+#define FLR_NCOUNTERS 20
+
+#define FLR_SOURCE_COLLIMATED 0
+#define FLR_SOURCE_LAMBERTIAN 1
+
+#define FLR_SENSOR_NONE 0
+#define FLR_SENSOR_ORTHO 1
+#define FLR_SENSOR_PINHOLE 2
+
+#define FLR_FORM_PLAIN 0      /* one thread per path, nested loops                          */
+#define FLR_FORM_WAVEFRONT 1  /* persistent, path regeneration, sensor connections regrouped */
+
+/* Counter indices of flr_read_tallies' counters array. */
+enum {
+    FLR_C_PATHS = 0, FLR_C_EVENTS, FLR_C_NULLS, FLR_C_ESCAPES, FLR_C_ABSORBED_DEAD,
+    FLR_C_RR_KILLS, FLR_C_CAP_HITS, FLR_C_STEP_BUDGET, FLR_C_CONNECTIONS, FLR_C_VF_REJECTED,
+    FLR_C_WALL_BOUNCES, FLR_C_EMISSIONS, FLR_C_SCATTERS, FLR_C_DYE_ABSORPTIONS, FLR_C_STEPS,
+    FLR_C_MAJORANT_VIOLATIONS, /* tracking points where sigma_t exceeded the majorant          */
+    FLR_C_CONNECT_STEPS,       /* ratio-tracking steps of sensor connections                    */
+    FLR_C_CONNECT_BUDGET,      /* connections cut by the ratio-tracking step budget             */
+    FLR_C_NONFINITE,           /* paths ended because a weight or position became non-finite   */
+    FLR_C_RESERVED
+};
+
+typedef struct flr_ctx flr_ctx;
+
+/* A light source: a parallelogram origin + a*eu + b*ev (a, b uniform in [0,1); eu = ev = 0 gives
+ * a point or pencil beam) emitting n_lines monochromatic lines (Sec. 5: each scene is lit at the
+ * dyes' excitation peaks). COLLIMATED sources emit along dir; LAMBERTIAN sources emit a cosine
+ * distribution about the axis-aligned normal dir. A line is chosen with probability proportional
+ * to its power over all lines of the medium's sources (p(lambda_x), Eq. 12); each line snaps to
+ * the nearest bin centre (ties to the lower bin). */
+typedef struct flr_source {
+    int kind;
+    float origin[3], eu[3], ev[3], dir[3];
+    int n_lines;
+    float lambda_nm[FLR_MAX_LINES];
+    float power[FLR_MAX_LINES];
+} flr_source;
+
+/* A participating medium in an axis-aligned box (Sec. 4.1: solvent particles plus dyes).
+ *   sigma_t(x, lambda) = s(x) (sigma_s + sigma_a0) + sum_d eps_d a_d(lambda) c_d(x)
+ * with s(x) the solvent mask (1 where no mask is given), eps_d a_d the dye's absorption
+ * (set by flr_set_dyes) and c_d the concentration (grid or uniform). Faces whose bit is set in
+ * wall_mask are Lambertian walls of albedo wall_albedo; the others are open. */
+typedef struct flr_medium {
+    float lo[3], hi[3];          /* box, cm                                                    */
+    int dims[3];                 /* nx, ny, nz of the grids; ignored when no grid is given     */
+    int n_dyes;                  /* 0..FLR_MAX_DYES_PER_MEDIUM                                 */
+    int dye_ids[FLR_MAX_DYES_PER_MEDIUM];        /* rows of the dye table                     */
+    const float *conc[FLR_MAX_DYES_PER_MEDIUM];  /* device grids, or NULL => conc_uniform[d]  */
+    float conc_uniform[FLR_MAX_DYES_PER_MEDIUM];
+    const uint8_t *solvent;      /* device [nz][ny][nx] 0/1 mask, or NULL (solvent everywhere) */
+    float sigma_s, sigma_a0;     /* solvent scattering and flat background absorption, cm^-1  */
+    int wall_mask;
+    float wall_albedo;
+    int source_first, source_count;  /* rows of the source table; count 0 = all sources      */
+} flr_medium;
+
+/* The sensor. ORTHO: a film rectangle origin + s U + t V (s, t in [0,1)) recording radiance
+ * that travels along +view (unit, normal to the film); pixel (px, py) = (floor(s W), floor(t H)).
+ * PINHOLE: eye at origin, orthonormal right U, up V, forward view, vertical field of view
+ * fov_y_deg, aspect W/H; image-plane coordinates at unit distance map to pixels with row 0 at
+ * the bottom. Both films record radiance averaged over the pixel's area on the film (pinhole:
+ * on the unit-distance image plane). The eye must lie outside the medium's box. */
+typedef struct flr_sensor {
+    int kind;
+    int width, height;
+    float origin[3], U[3], V[3], view[3];
+    float fov_y_deg;
+} flr_sensor;
+
+/* Per-render parameters. */
+typedef struct flr_params {
+    uint64_t n_paths;            /* photon paths to trace                                      */
+    uint64_t path_offset;        /* first path id (paths are path_offset .. +n_paths-1)         */
+    uint32_t seed;               /* Philox key word 0                                          */
+    uint32_t medium_id;          /* Philox key word 1                                          */
+    int n_rr;                    /* Russian roulette once a path has n_rr real events           */
+    int max_inelastic;           /* <0: unlimited re-emissions; k: the (k+1)-th dye absorption
+                                    ends the path (k = 1 is the paper's single inelastic event,
+                                    Sec. 4.1 and V_f of Eq. 9)                                 */
+    int analog;                  /* 0: weight *= QY (and wall albedo); 1: survival coins        */
+    int form;                    /* FLR_FORM_PLAIN or FLR_FORM_WAVEFRONT                        */
+    int64_t max_events;          /* a real collision once n_events == max_events ends the path */
+    int64_t max_steps;           /* tracking-step budget per path                               */
+    float *film;                 /* device [H][W][n_bins] fp32, or NULL                         */
+    uint32_t *path_events;       /* device [n_paths] real events per path, or NULL              */
+    int accumulate;              /* 0: clear tallies and film first; 1: add to them             */
+    int block_size;              /* threads per block; 0 = library default                     */
+    int blocks_per_sm;           /* resident blocks per SM; 0 = occupancy maximum               */
+    int regroup_interval;        /* wavefront: tracking steps between connection flushes; 0 auto */
+} flr_params;
+
+/* Create a context on CUDA device `cuda_device`. Allocates the small tally buffers. */
+int flr_create(flr_ctx **out, int cuda_device);
+/* Release a context and everything it allocated (not caller-owned buffers). NULL is allowed. */
+void flr_destroy(flr_ctx *ctx);
+
+/* Spectral grid (Sec. 4.2: per-wavelength transport; the paper samples every 1 nm, this library
+ * takes any uniform grid of 1..FLR_MAX_BINS bins). Resets the dye table. */
+int flr_set_spectrum(flr_ctx *ctx, float lambda0_nm, float dlambda_nm, int n_bins);
+
+/* Dye table (Sec. 4.1, Eq. 10). host abs_shape [n][n_bins]: absorption (excitation) spectrum
+ * a_d, peak-normalised; host emit_spec [n][n_bins]: emission spectrum f_m, any positive scale;
+ * host eps [n]: napierian absorption coefficient in cm^-1 per unit concentration at the
+ * absorption peak; host qy [n] in [0,1]. The emission pmf is f_m(lambda_i) / sum_j f_m(lambda_j);
+ * the library builds each dye's CDF in fp64 and rounds it to fp32. FLR_ERR_ARG on negative or
+ * non-finite values, an all-zero emission spectrum, QY outside [0,1] or n outside 1..FLR_MAX_DYES. */
+int flr_set_dyes(flr_ctx *ctx, int n, const float *abs_shape, const float *emit_spec,
+                 const float *eps, const float *qy);
+
+/* Light sources (host array of n, copied). */
+int flr_set_sources(flr_ctx *ctx, int n, const flr_source *sources);
+
+/* The medium of single-scene renders. Copies the dye grids (device, caller-owned, read here only)
+ * into a library-owned interleaved layout and reads their maxima back to build the per-bin
+ * majorant, so this call synchronises the device. Grids must be finite and non-negative. */
+int flr_set_medium(flr_ctx *ctx, const flr_medium *medium);
+
+/* The sensor (host struct, copied). kind NONE disables the film. */
+int flr_set_sensor(flr_ctx *ctx, const flr_sensor *sensor);
+
+/* Trace p->n_paths paths of the single scene on `stream`: face, absorption and emission tallies
+ * accumulate inside the context (read them with flr_read_tallies); film contributions are added
+ * to p->film already divided by p->n_paths. */
+int flr_render(flr_ctx *ctx, const flr_params *p, void *stream);
+
+/* Synchronise `stream` and copy out the tallies accumulated since the last clear, divided by the
+ * number of paths traced since then. host face [2][6][n_bins] (escaped weight per
+ * [fluoresced][face][bin]); host absorbed [n_dyes+1][n_bins] (last row: background absorption);
+ * host emitted [n_dyes][n_bins]; host counters [FLR_NCOUNTERS] (raw counts). Any output may be
+ * NULL. n_dyes is the current medium's. */
+int flr_read_tallies(flr_ctx *ctx, double *face, double *absorbed, double *emitted,
+                     uint64_t *counters, void *stream);
+
+/* Synchronise the device and report the device error word (FLR_OK if clean). */
+int flr_status(flr_ctx *ctx);
+const char *flr_last_error(flr_ctx *ctx);
+
+/* Diagnostics. Philox4x32-10 (Salmon et al., SC'11) blocks for device counters ctr [n][4] under
+ * the key (seed, medium) into device out [n][4]. */
+int flr_debug_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, int64_t n,
+                     uint32_t *out, void *stream);
+/* Emission bins drawn by the current medium's dye slot `dye` for device uniforms u [n]
+ * (24-bit values in [0,1)) into device out [n]: min{ i : CDF[i] > u } (Eq. 10). */
+int flr_debug_sample_emission(flr_ctx *ctx, int dye, const float *u, int64_t n, int32_t *out,
+                              void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLUORO_H */

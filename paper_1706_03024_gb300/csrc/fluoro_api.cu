@@ -1,0 +1,627 @@
+// fluoro_api.cu -- host side of the C ABI declared in include/fluoro.h.
+//
+// Validates inputs, builds the per-medium spectral tables (absorption per unit concentration,
+// emission CDFs of Eq. 10, per-bin majorant), lays the dye grids out interleaved in HBM, and
+// launches the sm_103a kernels of fluoro_kernels.cu. No compute runs on the host beyond these
+// small tables.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fluoro.h"
+#include "fluoro_internal.cuh"
+
+using namespace flr;
+
+struct flr_ctx {
+    int device = 0;
+    std::string err;
+    int B = 0;
+    double lambda0 = 0.0, dlambda = 0.0;
+    int n_dyes = 0;
+    std::vector<float> abs_shape, emit_spec, eps, qy;
+    std::vector<flr_source> sources;
+    bool medium_set = false;
+    flr_medium medium{};
+    float cmax[MAXD] = {0, 0, 0, 0};
+    float smax = 1.0f;
+    float4 *d_grid = nullptr;
+    size_t grid_cap = 0;
+    bool sensor_set = false;
+    flr_sensor sensor{};
+    bool tables_dirty = true;
+    float *d_tables = nullptr;
+    unsigned long long *d_tallies = nullptr;
+    unsigned long long *d_counters = nullptr;
+    int *d_error = nullptr;
+    unsigned long long *d_work = nullptr;
+    unsigned int *d_scratch = nullptr;  // [0] max bits, [1] flag, [2] any
+    uint64_t paths_since_clear = 0;
+    std::vector<float> h_tables;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int fail(flr_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(flr_ctx *ctx, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? FLR_ERR_OOM : FLR_ERR_CUDA, m);
+}
+
+bool finite3(const float *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Nearest bin centre, ties to the lower bin.
+int snap_bin(double lambda_nm, double l0, double dl, int B)
+{
+    const double b = (lambda_nm - l0) / dl;
+    int k = (int)std::ceil(b - 0.5);
+    return std::min(std::max(k, 0), B - 1);
+}
+
+float round_up_f32(double v)
+{
+    float f = (float)v;
+    if ((double)f < v) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+long long nvox(const flr_medium &m) { return (long long)m.dims[0] * m.dims[1] * m.dims[2]; }
+
+bool medium_has_grid(const flr_medium &m)
+{
+    for (int d = 0; d < m.n_dyes; ++d)
+        if (m.conc[d]) return true;
+    return false;
+}
+
+// Per-medium spectral tables (host fp64, stored fp32).
+void build_tables(flr_ctx *ctx)
+{
+    const int B = ctx->B;
+    const flr_medium &m = ctx->medium;
+    ctx->h_tables.assign(tab_size(B), 0.0f);
+    float *sig = ctx->h_tables.data() + tab_sig_a(B);
+    float *cdf = ctx->h_tables.data() + tab_cdf(B);
+    float *maj = ctx->h_tables.data() + tab_majorant(B);
+    float *qy = ctx->h_tables.data() + tab_qy(B);
+    for (int b = 0; b < B; ++b) {
+        double mj = (double)ctx->smax * ((double)m.sigma_s + (double)m.sigma_a0);
+        for (int d = 0; d < m.n_dyes; ++d) {
+            const int id = m.dye_ids[d];
+            const double s = (double)ctx->eps[id] * (double)ctx->abs_shape[(size_t)id * B + b];
+            sig[d * B + b] = (float)s;
+            mj += s * (double)ctx->cmax[d];
+        }
+        maj[b] = mj > 0.0 ? round_up_f32(mj * (1.0 + 1e-6)) : 0.0f;
+    }
+    for (int d = 0; d < m.n_dyes; ++d) {
+        const int id = m.dye_ids[d];
+        const float *f = ctx->emit_spec.data() + (size_t)id * B;
+        double tot = 0.0;
+        for (int b = 0; b < B; ++b) tot += (double)f[b];
+        double run = 0.0;
+        for (int b = 0; b < B; ++b) {
+            run += (double)f[b];
+            cdf[d * B + b] = (float)(run / tot);
+        }
+        cdf[d * B + B - 1] = 1.0f;
+        qy[d] = ctx->qy[id];
+    }
+}
+
+int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film)
+{
+    const flr_medium &m = ctx->medium;
+    std::memset(&S, 0, sizeof(S));
+    S.B = ctx->B;
+    S.D = m.n_dyes;
+    for (int k = 0; k < 3; ++k) {
+        S.lo[k] = m.lo[k];
+        S.hi[k] = m.hi[k];
+        S.dims[k] = std::max(m.dims[k], 1);
+        S.vox_scale[k] = (float)((double)S.dims[k] / ((double)m.hi[k] - (double)m.lo[k]));
+    }
+    S.grid = medium_has_grid(m) ? ctx->d_grid : nullptr;
+    S.solvent = m.solvent;
+    S.homogeneous = (S.grid == nullptr && S.solvent == nullptr) ? 1 : 0;
+    for (int d = 0; d < MAXD; ++d) S.conc_uniform[d] = d < m.n_dyes ? m.conc_uniform[d] : 0.0f;
+    S.sigma_s = m.sigma_s;
+    S.sigma_a0 = m.sigma_a0;
+    S.wall_mask = m.wall_mask;
+    S.wall_albedo = m.wall_albedo;
+    S.tables = ctx->d_tables;
+    // emitters: every line of the medium's sources, chosen in proportion to power
+    int first = m.source_first, count = m.source_count;
+    if (count == 0) { first = 0; count = (int)ctx->sources.size(); }
+    if (first < 0 || count < 0 || first + count > (int)ctx->sources.size() || count == 0)
+        return fail(ctx, FLR_ERR_STATE, "medium references sources that are not set");
+    std::vector<double> pw;
+    int n = 0;
+    for (int s = first; s < first + count; ++s) {
+        const flr_source &src = ctx->sources[s];
+        for (int l = 0; l < src.n_lines; ++l) {
+            if (n >= FLR_MAX_EMITTERS) return fail(ctx, FLR_ERR_ARG, "more than 32 source lines");
+            EmitterDev &e = S.em[n];
+            for (int k = 0; k < 3; ++k) {
+                e.origin[k] = src.origin[k];
+                e.eu[k] = src.eu[k];
+                e.ev[k] = src.ev[k];
+                e.dir[k] = src.dir[k];
+            }
+            e.kind = src.kind;
+            e.bin = snap_bin(src.lambda_nm[l], ctx->lambda0, ctx->dlambda, ctx->B);
+            int ax = 0;
+            for (int k = 1; k < 3; ++k)
+                if (std::fabs(src.dir[k]) > std::fabs(src.dir[ax])) ax = k;
+            e.axis = ax;
+            e.sign = src.dir[ax] > 0.0f ? 1.0f : -1.0f;
+            pw.push_back((double)src.power[l]);
+            ++n;
+        }
+    }
+    double tot = 0.0;
+    for (double v : pw) tot += v;
+    if (!(tot > 0.0)) return fail(ctx, FLR_ERR_ARG, "total source power must be positive");
+    double run = 0.0;
+    for (int k = 0; k < n; ++k) {
+        run += pw[k];
+        S.em_cdf[k] = (float)(run / tot);
+    }
+    S.em_cdf[n - 1] = 1.0f;
+    S.n_emitters = n;
+    // sensor
+    const flr_sensor &c = ctx->sensor;
+    S.sensor_kind = (ctx->sensor_set && with_film) ? c.kind : FLR_SENSOR_NONE;
+    if (S.sensor_kind != FLR_SENSOR_NONE) {
+        S.W = c.width;
+        S.H = c.height;
+        for (int k = 0; k < 3; ++k) {
+            S.s_origin[k] = c.origin[k];
+            S.s_view[k] = c.view[k];
+        }
+        if (c.kind == FLR_SENSOR_ORTHO) {
+            double uu = 0, vv = 0;
+            for (int k = 0; k < 3; ++k) {
+                uu += (double)c.U[k] * c.U[k];
+                vv += (double)c.V[k] * c.V[k];
+            }
+            for (int k = 0; k < 3; ++k) {
+                S.s_U[k] = (float)(c.U[k] / uu);
+                S.s_V[k] = (float)(c.V[k] / vv);
+            }
+            S.inv_A_pix = (float)((double)c.width * c.height / (std::sqrt(uu) * std::sqrt(vv)));
+        } else {
+            for (int k = 0; k < 3; ++k) {
+                S.s_U[k] = c.U[k];
+                S.s_V[k] = c.V[k];
+            }
+            const double ty = std::tan(0.5 * (double)c.fov_y_deg * M_PI / 180.0);
+            const double tx = ty * (double)c.width / (double)c.height;
+            S.tan_x = (float)tx;
+            S.tan_y = (float)ty;
+            S.inv_A_pix = (float)((double)c.width * c.height / ((2.0 * tx) * (2.0 * ty)));
+        }
+    }
+    return FLR_OK;
+}
+
+int prepare_tables(flr_ctx *ctx)
+{
+    if (!ctx->tables_dirty) return FLR_OK;
+    build_tables(ctx);
+    cudaError_t e = cudaMemcpy(ctx->d_tables, ctx->h_tables.data(), sizeof(float) * ctx->h_tables.size(),
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload spectral tables");
+    ctx->tables_dirty = false;
+    return FLR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int flr_create(flr_ctx **out, int cuda_device)
+{
+    if (!out) return FLR_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || cuda_device < 0 || cuda_device >= n) {
+        cudaGetLastError();
+        return FLR_ERR_ARG;
+    }
+    flr_ctx *ctx = new flr_ctx();
+    ctx->device = cuda_device;
+    DeviceGuard g(cuda_device);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tables, sizeof(float) * tab_size(FLR_MAX_BINS));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tallies, sizeof(unsigned long long) * tal_size(FLR_MAX_BINS));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counters, sizeof(unsigned long long) * FLR_NCOUNTERS);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_error, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_work, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_scratch, sizeof(unsigned int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_tallies, 0, sizeof(unsigned long long) * tal_size(FLR_MAX_BINS));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * FLR_NCOUNTERS);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_error, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        flr_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? FLR_ERR_OOM : FLR_ERR_CUDA;
+    }
+    *out = ctx;
+    return FLR_OK;
+}
+
+void flr_destroy(flr_ctx *ctx)
+{
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaFree(ctx->d_tables);
+    cudaFree(ctx->d_tallies);
+    cudaFree(ctx->d_counters);
+    cudaFree(ctx->d_error);
+    cudaFree(ctx->d_work);
+    cudaFree(ctx->d_scratch);
+    cudaFree(ctx->d_grid);
+    delete ctx;
+}
+
+int flr_set_spectrum(flr_ctx *ctx, float lambda0_nm, float dlambda_nm, int n_bins)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (!(std::isfinite(lambda0_nm) && std::isfinite(dlambda_nm) && dlambda_nm > 0.0f) ||
+        n_bins < 1 || n_bins > FLR_MAX_BINS)
+        return fail(ctx, FLR_ERR_ARG, "spectrum: need finite lambda0, dlambda > 0, 1..128 bins");
+    ctx->B = n_bins;
+    ctx->lambda0 = lambda0_nm;
+    ctx->dlambda = dlambda_nm;
+    ctx->n_dyes = 0;
+    ctx->abs_shape.clear();
+    ctx->emit_spec.clear();
+    ctx->eps.clear();
+    ctx->qy.clear();
+    ctx->medium_set = false;
+    ctx->tables_dirty = true;
+    return FLR_OK;
+}
+
+int flr_set_dyes(flr_ctx *ctx, int n, const float *abs_shape, const float *emit_spec,
+                 const float *eps, const float *qy)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (ctx->B <= 0) return fail(ctx, FLR_ERR_STATE, "set the spectrum before the dyes");
+    if (n < 1 || n > FLR_MAX_DYES || !abs_shape || !emit_spec || !eps || !qy)
+        return fail(ctx, FLR_ERR_ARG, "dyes: need 1..1024 dyes and four host arrays");
+    const int B = ctx->B;
+    for (int d = 0; d < n; ++d) {
+        double tot = 0.0;
+        for (int b = 0; b < B; ++b) {
+            const float a = abs_shape[(size_t)d * B + b], e = emit_spec[(size_t)d * B + b];
+            if (!(std::isfinite(a) && a >= 0.0f && std::isfinite(e) && e >= 0.0f))
+                return fail(ctx, FLR_ERR_ARG, "dyes: spectra must be finite and non-negative");
+            tot += e;
+        }
+        if (!(tot > 0.0)) return fail(ctx, FLR_ERR_ARG, "dyes: an emission spectrum sums to zero");
+        if (!(std::isfinite(eps[d]) && eps[d] >= 0.0f))
+            return fail(ctx, FLR_ERR_ARG, "dyes: eps must be finite and non-negative");
+        if (!(qy[d] >= 0.0f && qy[d] <= 1.0f)) return fail(ctx, FLR_ERR_ARG, "dyes: QY outside [0,1]");
+    }
+    ctx->n_dyes = n;
+    ctx->abs_shape.assign(abs_shape, abs_shape + (size_t)n * B);
+    ctx->emit_spec.assign(emit_spec, emit_spec + (size_t)n * B);
+    ctx->eps.assign(eps, eps + n);
+    ctx->qy.assign(qy, qy + n);
+    if (ctx->medium_set) {
+        for (int d = 0; d < ctx->medium.n_dyes; ++d)
+            if (ctx->medium.dye_ids[d] >= n) ctx->medium_set = false;
+    }
+    ctx->tables_dirty = true;
+    return FLR_OK;
+}
+
+int flr_set_sources(flr_ctx *ctx, int n, const flr_source *s)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (n < 1 || n > FLR_MAX_SOURCES || !s) return fail(ctx, FLR_ERR_ARG, "sources: need 1..64");
+    for (int i = 0; i < n; ++i) {
+        const flr_source &q = s[i];
+        if (q.kind != FLR_SOURCE_COLLIMATED && q.kind != FLR_SOURCE_LAMBERTIAN)
+            return fail(ctx, FLR_ERR_ARG, "sources: unknown kind");
+        if (!(finite3(q.origin) && finite3(q.eu) && finite3(q.ev) && finite3(q.dir)))
+            return fail(ctx, FLR_ERR_ARG, "sources: non-finite geometry");
+        const double len = std::sqrt((double)q.dir[0] * q.dir[0] + (double)q.dir[1] * q.dir[1] +
+                                     (double)q.dir[2] * q.dir[2]);
+        if (std::fabs(len - 1.0) > 1e-5) return fail(ctx, FLR_ERR_ARG, "sources: dir must be a unit vector");
+        if (q.kind == FLR_SOURCE_LAMBERTIAN) {
+            int nz = 0;
+            for (int k = 0; k < 3; ++k) nz += q.dir[k] != 0.0f;
+            if (nz != 1) return fail(ctx, FLR_ERR_ARG, "sources: Lambertian normals must be axis-aligned");
+        }
+        if (q.n_lines < 1 || q.n_lines > FLR_MAX_LINES)
+            return fail(ctx, FLR_ERR_ARG, "sources: 1..8 lines per source");
+        for (int l = 0; l < q.n_lines; ++l)
+            if (!(std::isfinite(q.lambda_nm[l]) && std::isfinite(q.power[l]) && q.power[l] >= 0.0f))
+                return fail(ctx, FLR_ERR_ARG, "sources: bad line");
+    }
+    ctx->sources.assign(s, s + n);
+    return FLR_OK;
+}
+
+int flr_set_medium(flr_ctx *ctx, const flr_medium *m)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (!m) return fail(ctx, FLR_ERR_ARG, "medium: NULL");
+    if (ctx->B <= 0) return fail(ctx, FLR_ERR_STATE, "set the spectrum before the medium");
+    if (m->n_dyes < 0 || m->n_dyes > MAXD) return fail(ctx, FLR_ERR_ARG, "medium: 0..4 dyes");
+    for (int k = 0; k < 3; ++k)
+        if (!(std::isfinite(m->lo[k]) && std::isfinite(m->hi[k]) && m->hi[k] > m->lo[k]))
+            return fail(ctx, FLR_ERR_ARG, "medium: box must have hi > lo");
+    for (int d = 0; d < m->n_dyes; ++d) {
+        if (m->dye_ids[d] < 0 || m->dye_ids[d] >= ctx->n_dyes)
+            return fail(ctx, FLR_ERR_ARG, "medium: dye id outside the dye table");
+        if (!m->conc[d] && !(std::isfinite(m->conc_uniform[d]) && m->conc_uniform[d] >= 0.0f))
+            return fail(ctx, FLR_ERR_ARG, "medium: uniform concentration must be finite and >= 0");
+    }
+    if (!(std::isfinite(m->sigma_s) && m->sigma_s >= 0.0f && std::isfinite(m->sigma_a0) && m->sigma_a0 >= 0.0f))
+        return fail(ctx, FLR_ERR_ARG, "medium: sigma_s and sigma_a0 must be finite and >= 0");
+    if (m->wall_mask < 0 || m->wall_mask > 63 || !(m->wall_albedo >= 0.0f && m->wall_albedo <= 1.0f))
+        return fail(ctx, FLR_ERR_ARG, "medium: wall mask 0..63 and albedo in [0,1]");
+    const bool grids = medium_has_grid(*m) || m->solvent;
+    if (grids) {
+        for (int k = 0; k < 3; ++k)
+            if (m->dims[k] < 1 || m->dims[k] > 4096) return fail(ctx, FLR_ERR_ARG, "medium: dims 1..4096");
+        for (int d = 0; d < m->n_dyes; ++d)
+            if (m->conc[d] && !is_device_pointer(m->conc[d]))
+                return fail(ctx, FLR_ERR_ARG, "medium: concentration grids must be device memory");
+        if (m->solvent && !is_device_pointer(m->solvent))
+            return fail(ctx, FLR_ERR_ARG, "medium: solvent mask must be device memory");
+    }
+    DeviceGuard g(ctx->device);
+    flr_medium mm = *m;
+    if (!grids) mm.dims[0] = mm.dims[1] = mm.dims[2] = 1;
+    const long long n = nvox(mm);
+    float cmax[MAXD] = {0, 0, 0, 0};
+    float smax = 1.0f;
+    cudaError_t e;
+    if (medium_has_grid(mm)) {
+        if ((size_t)n > ctx->grid_cap) {
+            cudaFree(ctx->d_grid);
+            ctx->d_grid = nullptr;
+            ctx->grid_cap = 0;
+            e = cudaMalloc(&ctx->d_grid, sizeof(float4) * (size_t)n);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate the interleaved grid");
+            ctx->grid_cap = (size_t)n;
+        }
+        e = launch_pack_grid(mm.conc, mm.conc_uniform, mm.n_dyes, n, ctx->d_grid, 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "pack grids");
+    }
+    for (int d = 0; d < mm.n_dyes; ++d) {
+        if (!mm.conc[d]) { cmax[d] = mm.conc_uniform[d]; continue; }
+        unsigned int h[2] = {0, 0};
+        e = cudaMemset(ctx->d_scratch, 0, sizeof(unsigned int) * 4);
+        if (e == cudaSuccess) e = launch_grid_max(mm.conc[d], n, ctx->d_scratch, (int *)(ctx->d_scratch + 1), 0);
+        if (e == cudaSuccess) e = cudaMemcpy(h, ctx->d_scratch, sizeof(h), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "grid maximum");
+        if (h[1]) return fail(ctx, FLR_ERR_ARG, "medium: concentration grid has negative or non-finite values");
+        std::memcpy(&cmax[d], &h[0], sizeof(float));
+    }
+    if (mm.solvent) {
+        unsigned int h = 0;
+        e = cudaMemset(ctx->d_scratch, 0, sizeof(unsigned int) * 4);
+        if (e == cudaSuccess) e = launch_solvent_any(mm.solvent, n, ctx->d_scratch + 2, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(&h, ctx->d_scratch + 2, sizeof(h), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "solvent mask");
+        smax = h ? 1.0f : 0.0f;
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set medium");
+    ctx->medium = mm;
+    std::memcpy(ctx->cmax, cmax, sizeof(cmax));
+    ctx->smax = smax;
+    ctx->medium_set = true;
+    ctx->tables_dirty = true;
+    return FLR_OK;
+}
+
+int flr_set_sensor(flr_ctx *ctx, const flr_sensor *c)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (!c) return fail(ctx, FLR_ERR_ARG, "sensor: NULL");
+    if (c->kind == FLR_SENSOR_NONE) {
+        ctx->sensor = *c;
+        ctx->sensor_set = false;
+        return FLR_OK;
+    }
+    if (c->kind != FLR_SENSOR_ORTHO && c->kind != FLR_SENSOR_PINHOLE)
+        return fail(ctx, FLR_ERR_ARG, "sensor: unknown kind");
+    if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384)
+        return fail(ctx, FLR_ERR_ARG, "sensor: width and height 1..16384");
+    if (!(finite3(c->origin) && finite3(c->U) && finite3(c->V) && finite3(c->view)))
+        return fail(ctx, FLR_ERR_ARG, "sensor: non-finite geometry");
+    if (c->kind == FLR_SENSOR_PINHOLE && !(c->fov_y_deg > 0.0f && c->fov_y_deg < 179.0f))
+        return fail(ctx, FLR_ERR_ARG, "sensor: pinhole field of view in (0, 179) degrees");
+    if (c->kind == FLR_SENSOR_ORTHO) {
+        const double uu = (double)c->U[0] * c->U[0] + (double)c->U[1] * c->U[1] + (double)c->U[2] * c->U[2];
+        const double vv = (double)c->V[0] * c->V[0] + (double)c->V[1] * c->V[1] + (double)c->V[2] * c->V[2];
+        if (!(uu > 0.0 && vv > 0.0)) return fail(ctx, FLR_ERR_ARG, "sensor: film edges must be non-zero");
+    }
+    ctx->sensor = *c;
+    ctx->sensor_set = true;
+    return FLR_OK;
+}
+
+int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (!p) return fail(ctx, FLR_ERR_ARG, "params: NULL");
+    if (ctx->B <= 0 || !ctx->medium_set) return fail(ctx, FLR_ERR_STATE, "render: spectrum, dyes and medium must be set");
+    if (ctx->sources.empty()) return fail(ctx, FLR_ERR_STATE, "render: no sources");
+    if (p->form != FLR_FORM_PLAIN && p->form != FLR_FORM_WAVEFRONT) return fail(ctx, FLR_ERR_ARG, "params: unknown form");
+    if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || (p->block_size & 31)))
+        return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
+    if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
+        return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
+    if (p->film && !is_device_pointer(p->film)) return fail(ctx, FLR_ERR_ARG, "params: film must be device memory");
+    if (p->path_events && !is_device_pointer(p->path_events))
+        return fail(ctx, FLR_ERR_ARG, "params: path_events must be device memory");
+    if (ctx->sensor_set && ctx->sensor.kind == FLR_SENSOR_PINHOLE) {
+        const float *o = ctx->sensor.origin;
+        bool inside = true;
+        for (int k = 0; k < 3; ++k) inside = inside && o[k] >= ctx->medium.lo[k] && o[k] <= ctx->medium.hi[k];
+        if (inside) return fail(ctx, FLR_ERR_ARG, "sensor: the pinhole must lie outside the medium box");
+    }
+    DeviceGuard g(ctx->device);
+    int rc = prepare_tables(ctx);
+    if (rc != FLR_OK) return rc;
+    SceneDev S;
+    rc = fill_scene(ctx, S, p->film != nullptr);
+    if (rc != FLR_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!p->accumulate) {
+        e = cudaMemsetAsync(ctx->d_tallies, 0, sizeof(unsigned long long) * tal_size(FLR_MAX_BINS), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * FLR_NCOUNTERS, st);
+        if (e == cudaSuccess && p->film && S.sensor_kind != FLR_SENSOR_NONE)
+            e = cudaMemsetAsync(p->film, 0, sizeof(float) * (size_t)S.W * S.H * S.B, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "clear tallies");
+        ctx->paths_since_clear = 0;
+    }
+    if (p->n_paths == 0) return FLR_OK;
+    e = cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reset work counter");
+    RunDev R;
+    std::memset(&R, 0, sizeof(R));
+    R.n_paths = p->n_paths;
+    R.path_offset = p->path_offset;
+    R.seed = p->seed;
+    R.medium_id = p->medium_id;
+    R.n_rr = p->n_rr;
+    R.max_inelastic = p->max_inelastic;
+    R.analog = p->analog;
+    R.max_events = p->max_events;
+    R.max_steps = p->max_steps;
+    R.film_scale = (float)(1.0 / (double)p->n_paths);
+    R.film = S.sensor_kind != FLR_SENSOR_NONE ? p->film : nullptr;
+    R.path_events = p->path_events;
+    R.tallies = ctx->d_tallies;
+    R.counters = ctx->d_counters;
+    R.error_word = ctx->d_error;
+    R.work_counter = ctx->d_work;
+    R.regroup = p->regroup_interval;
+    e = launch_trace(S, R, p->form, p->block_size, p->blocks_per_sm, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch trace kernel");
+    ctx->paths_since_clear += p->n_paths;
+    return FLR_OK;
+}
+
+int flr_read_tallies(flr_ctx *ctx, double *face, double *absorbed, double *emitted,
+                     uint64_t *counters, void *stream)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (ctx->B <= 0) return fail(ctx, FLR_ERR_STATE, "read: no spectrum");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before reading tallies");
+    const int B = ctx->B;
+    std::vector<unsigned long long> t(tal_size(FLR_MAX_BINS));
+    unsigned long long c[FLR_NCOUNTERS];
+    e = cudaMemcpy(t.data(), ctx->d_tallies, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(c, ctx->d_counters, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read tallies");
+    const double inv = ctx->paths_since_clear ? 1.0 / ((double)ctx->paths_since_clear * TALLY_ONE) : 0.0;
+    const int D = ctx->medium_set ? ctx->medium.n_dyes : 0;
+    if (face)
+        for (int i = 0; i < 12 * B; ++i) face[i] = (double)t[tal_face(B) + i] * inv;
+    if (absorbed) {
+        for (int d = 0; d < D; ++d)
+            for (int b = 0; b < B; ++b) absorbed[d * B + b] = (double)t[tal_absorbed(B) + d * B + b] * inv;
+        for (int b = 0; b < B; ++b) absorbed[D * B + b] = (double)t[tal_absorbed(B) + D * B + b] * inv;
+    }
+    if (emitted)
+        for (int d = 0; d < D; ++d)
+            for (int b = 0; b < B; ++b) emitted[d * B + b] = (double)t[tal_emitted(B) + d * B + b] * inv;
+    if (counters)
+        for (int k = 0; k < FLR_NCOUNTERS; ++k) counters[k] = c[k];
+    return FLR_OK;
+}
+
+int flr_status(flr_ctx *ctx)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device status");
+    int w = 0;
+    e = cudaMemcpy(&w, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read error word");
+    if (w) return fail(ctx, FLR_ERR_BUDGET, "device error word set");
+    return FLR_OK;
+}
+
+const char *flr_last_error(flr_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+int flr_debug_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, int64_t n, uint32_t *out,
+                     void *stream)
+{
+    if (n < 0 || (n > 0 && (!ctr || !out))) return FLR_ERR_ARG;
+    if (n == 0) return FLR_OK;
+    if (!is_device_pointer(ctr) || !is_device_pointer(out)) return FLR_ERR_ARG;
+    return launch_philox(seed, medium, ctr, n, out, (cudaStream_t)stream) == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
+}
+
+int flr_debug_sample_emission(flr_ctx *ctx, int dye, const float *u, int64_t n, int32_t *out, void *stream)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (!ctx->medium_set) return fail(ctx, FLR_ERR_STATE, "sample: no medium");
+    if (dye < 0 || dye >= ctx->medium.n_dyes || n < 0) return fail(ctx, FLR_ERR_ARG, "sample: bad dye or n");
+    if (n == 0) return FLR_OK;
+    if (!is_device_pointer(u) || !is_device_pointer(out)) return fail(ctx, FLR_ERR_ARG, "sample: device buffers");
+    DeviceGuard g(ctx->device);
+    int rc = prepare_tables(ctx);
+    if (rc != FLR_OK) return rc;
+    SceneDev S;
+    std::memset(&S, 0, sizeof(S));
+    S.B = ctx->B;
+    S.tables = ctx->d_tables;
+    cudaError_t e = launch_sample_emission(S, dye, u, n, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? FLR_OK : cuda_fail(ctx, e, "sample emission");
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// fluoro_internal.cuh -- structures shared by the C-ABI host code and the sm_103a kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fluoro.h"
+
+namespace flr {
+
+constexpr int MAXD = FLR_MAX_DYES_PER_MEDIUM;
+constexpr uint32_t STEP_SPAWN = 0xFFFFFFFFu;
+constexpr int MAX_CONNECT_STEPS = 1 << 16;   // ratio-tracking steps per sensor connection
+constexpr float RT_RR_THRESHOLD = 1e-3f;     // roulette on the transmittance estimate below this
+
+// Layout of the per-medium spectral tables (fp32, global memory, staged into shared memory):
+//   sig_a[MAXD][B]   eps_d * a_d(lambda_b), per unit concentration      (Sec. 4.1)
+//   cdf[MAXD][B]     emission CDF, fp64-built and rounded, last = 1      (Eq. 10)
+//   majorant[B]      sigma_bar(lambda_b) >= sigma_t(x, lambda_b) for all x
+//   qy[MAXD]
+__host__ __device__ constexpr int tab_sig_a(int B) { return 0; }
+__host__ __device__ constexpr int tab_cdf(int B) { return MAXD * B; }
+__host__ __device__ constexpr int tab_majorant(int B) { return 2 * MAXD * B; }
+__host__ __device__ constexpr int tab_qy(int B) { return 2 * MAXD * B + B; }
+__host__ __device__ constexpr int tab_size(int B) { return 2 * MAXD * B + B + MAXD; }
+
+// Fixed-point tallies (u64, 2^-24 units of photon weight): face[2][6][B], absorbed[MAXD+1][B],
+// emitted[MAXD][B]. Integer sums make every launch form and thread order give identical bits.
+__host__ __device__ constexpr int tal_face(int B) { return 0; }
+__host__ __device__ constexpr int tal_absorbed(int B) { return 12 * B; }
+__host__ __device__ constexpr int tal_emitted(int B) { return 12 * B + (MAXD + 1) * B; }
+__host__ __device__ constexpr int tal_size(int B) { return 12 * B + (2 * MAXD + 1) * B; }
+constexpr double TALLY_ONE = 16777216.0;  // 2^24
+
+struct EmitterDev {
+    float origin[3], eu[3], ev[3], dir[3];
+    int kind, bin, axis;
+    float sign;
+};
+
+// Scene description passed by value to the kernels (lives in the constant bank).
+struct SceneDev {
+    int B, D;
+    float lo[3], hi[3], vox_scale[3];  // vox_scale = dims / (hi - lo)
+    int dims[3];
+    int homogeneous;                   // no grid and no solvent mask
+    const float4 *grid;                // [nvox] interleaved concentrations of the medium's dyes
+    const uint8_t *solvent;            // [nvox] or nullptr
+    float conc_uniform[MAXD];
+    float sigma_s, sigma_a0;
+    int wall_mask;
+    float wall_albedo;
+    const float *tables;               // tab_size(B) floats
+    int n_emitters;
+    float em_cdf[FLR_MAX_EMITTERS];
+    EmitterDev em[FLR_MAX_EMITTERS];
+    int sensor_kind, W, H;
+    float s_origin[3], s_U[3], s_V[3], s_view[3];  // ortho: U, V pre-divided by |U|^2, |V|^2
+    float tan_x, tan_y, inv_A_pix;
+};
+
+// Per-launch run parameters.
+struct RunDev {
+    uint64_t n_paths, path_offset;
+    uint32_t seed, medium_id;
+    int n_rr, max_inelastic, analog;
+    long long max_events, max_steps;
+    float film_scale;                  // 1 / n_paths
+    float *film;
+    uint32_t *path_events;
+    unsigned long long *tallies;       // tal_size(B)
+    unsigned long long *counters;      // FLR_NCOUNTERS
+    int *error_word;
+    unsigned long long *work_counter;  // dynamic path distribution (wavefront form)
+    int regroup;                       // wavefront: tracking steps between connection flushes
+};
+
+// Host-side launchers (fluoro_kernels.cu).
+cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block, int blocks_per_sm,
+                         cudaStream_t st);
+cudaError_t launch_grid_max(const float *g, long long n, unsigned int *out_bits, int *neg_flag,
+                            cudaStream_t st);
+cudaError_t launch_pack_grid(const float *const *conc, const float *uniform, int D, long long n,
+                             float4 *out, cudaStream_t st);
+cudaError_t launch_solvent_any(const uint8_t *s, long long n, unsigned int *out, cudaStream_t st);
+cudaError_t launch_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, long long n,
+                          uint32_t *out, cudaStream_t st);
+cudaError_t launch_sample_emission(const SceneDev &S, int dye, const float *u, long long n,
+                                   int32_t *out, cudaStream_t st);
+int trace_block_default();
+int trace_smem_bytes(int B, int form, int block);
+int occupancy_blocks_per_sm(int B, int form, int block);
+
+}  // namespace flr

@@ -1,0 +1,859 @@
+// fluoro_kernels.cu -- sm_103a kernels of the fluorescent participating-media light tracer.
+//
+// Light (photon) tracing of the per-wavelength fluorescent RTE (Sec. 4.2, Eq. 9 and 11) with the
+// estimator structure of Eq. 12:
+//   spawn      a photon of unit power at a source line chosen in proportion to power
+//   free flight  delta tracking against the per-wavelength majorant (Eq. 6 sampled exactly)
+//   collision  particle type in proportion to its coefficient: solvent scatterer, dye d
+//              (eps_d a_d(lambda) c_d), or background absorber (Sec. 4.1)
+//   scatter    isotropic (Sec. 2.1)
+//   dye        weight *= QY (or a QY coin), new wavelength from the emission CDF (Eq. 10),
+//              isotropic direction (Sec. 2.1)
+//   walls      Lambertian reflection
+//   roulette   once n_events >= n_rr, survive with q = min(1, w), w /= q
+//   sensor     every scatter, emission, wall and Lambertian-light vertex connects to the film:
+//              intensity x transmittance (ratio tracking, Eq. 6) x importance (Eq. 3-5)
+//   tallies    escaped weight per [fluoresced][face][bin]; absorbed / emitted per dye and bin
+//
+// Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by (seed, medium), counter
+// (path_lo, step, slot, path_hi). Slot 0 of a tracking step gives (u_dist, u_real, u_event,
+// u_dir1), slot 1 (u_dir2, u_emit, u_rr, u_coin), slots 2.. feed the step's sensor connection.
+// Spawn uses step 0xFFFFFFFF. Uniforms are 24-bit: u = (x >> 8) 2^-24.
+#include <cfloat>
+#include <cstdint>
+
+#include "fluoro_internal.cuh"
+
+namespace flr {
+
+namespace {
+
+constexpr float INV_4PI = 0.0795774715459476679f;
+constexpr float INV_PI = 0.318309886183790672f;
+constexpr float TWO_PI = 6.28318530717958648f;
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10: ten rounds, each two 32x32->64 products of the even words with the round
+// multipliers, mixed with the odd words and the key; the key advances by the Weyl constants.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+struct U4 { float a, b, c, d; };
+
+__device__ __forceinline__ U4 draw(uint32_t seed, uint32_t medium, uint64_t pid, uint32_t step,
+                                   uint32_t slot)
+{
+    const uint4 o = philox(make_uint4((uint32_t)pid, step, slot, (uint32_t)(pid >> 32)), seed, medium);
+    return U4{u24(o.x), u24(o.y), u24(o.z), u24(o.w)};
+}
+
+// ---------------------------------------------------------------------------------------------
+// Shared-memory view: spectral tables, block tallies, block counters.
+struct Smem {
+    const float *sig_a, *cdf, *maj, *qy;
+    unsigned long long *tal;
+    unsigned long long *cnt;
+};
+
+// Frequent counters live in registers; the rest go straight to shared memory.
+struct RegCnt {
+    uint32_t steps, nulls, events, scatters, connections, connect_steps;
+};
+
+__device__ __forceinline__ void cnt_add(const Smem &sm, int k, unsigned long long v = 1ull)
+{
+    atomicAdd(&sm.cnt[k], v);
+}
+
+__device__ __forceinline__ void tally_add(const Smem &sm, int idx, float w)
+{
+    const unsigned long long fx = __float2ull_rn(w * 16777216.0f);
+    if (fx) atomicAdd(&sm.tal[idx], fx);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Medium (Sec. 4.1): sigma_t = s(x)(sigma_s + sigma_a0) + sum_d sig_a[d][b] c_d(x), nearest voxel.
+struct Coeffs {
+    float scat, bg, total;
+    float dye[MAXD];
+};
+
+__device__ __forceinline__ int voxel_of(const SceneDev &S, float3 x)
+{
+    int ix = __float2int_rd((x.x - S.lo[0]) * S.vox_scale[0]);
+    int iy = __float2int_rd((x.y - S.lo[1]) * S.vox_scale[1]);
+    int iz = __float2int_rd((x.z - S.lo[2]) * S.vox_scale[2]);
+    ix = min(max(ix, 0), S.dims[0] - 1);
+    iy = min(max(iy, 0), S.dims[1] - 1);
+    iz = min(max(iz, 0), S.dims[2] - 1);
+    return (iz * S.dims[1] + iy) * S.dims[0] + ix;
+}
+
+__device__ __forceinline__ Coeffs coeffs_at(const SceneDev &S, const Smem &sm, float3 x, int b)
+{
+    float s = 1.0f;
+    float4 c = make_float4(S.conc_uniform[0], S.conc_uniform[1], S.conc_uniform[2], S.conc_uniform[3]);
+    if (!S.homogeneous) {
+        const int v = voxel_of(S, x);
+        if (S.grid) c = __ldg(&S.grid[v]);
+        if (S.solvent) s = __ldg(&S.solvent[v]) ? 1.0f : 0.0f;
+    }
+    Coeffs k;
+    k.scat = s * S.sigma_s;
+    k.bg = s * S.sigma_a0;
+    k.total = k.scat + k.bg;
+    const float cc[4] = {c.x, c.y, c.z, c.w};
+    const int B = S.B;
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d) {
+        k.dye[d] = (d < S.D) ? sm.sig_a[d * B + b] * cc[d] : 0.0f;
+        k.total += k.dye[d];
+    }
+    return k;
+}
+
+__device__ __forceinline__ float sigma_t_at(const SceneDev &S, const Smem &sm, float3 x, int b)
+{
+    return coeffs_at(S, sm, x, b).total;
+}
+
+// Distance to leave the box along w (inverse direction given), face index 0..5 or -1; ties to
+// the lowest face index.
+__device__ __forceinline__ float exit_distance(const SceneDev &S, float3 x, float3 w, float3 iw,
+                                               int &face)
+{
+    float best = FLT_MAX;
+    face = -1;
+    const float xs[3] = {x.x, x.y, x.z}, ws[3] = {w.x, w.y, w.z}, is[3] = {iw.x, iw.y, iw.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (ws[k] == 0.0f) continue;
+        const bool pos = ws[k] > 0.0f;
+        float t = ((pos ? S.hi[k] : S.lo[k]) - xs[k]) * is[k];
+        t = fmaxf(t, 0.0f);
+        if (t < best) { best = t; face = 2 * k + (pos ? 1 : 0); }
+    }
+    return best;
+}
+
+__device__ __forceinline__ float3 inv_dir(float3 w)
+{
+    return make_float3(w.x != 0.0f ? __frcp_rn(w.x) : 0.0f, w.y != 0.0f ? __frcp_rn(w.y) : 0.0f,
+                       w.z != 0.0f ? __frcp_rn(w.z) : 0.0f);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Directions (Sec. 2.1: isotropic scattering and emission; Lambertian walls and lights).
+__device__ __forceinline__ float3 iso_dir(float u1, float u2)
+{
+    const float z = 1.0f - 2.0f * u1;
+    float s, c;
+    __sincosf(TWO_PI * u2, &s, &c);
+    const float r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+    return make_float3(r * c, r * s, z);
+}
+
+// Cosine-weighted about sign * e_axis, tangents e_{axis+1}, e_{axis+2}.
+__device__ __forceinline__ float3 cosine_dir(float u1, float u2, int axis, float sign)
+{
+    const float r = sqrtf(u1);
+    float s, c;
+    __sincosf(TWO_PI * u2, &s, &c);
+    const float zl = sqrtf(fmaxf(0.0f, 1.0f - u1));
+    float v[3];
+    v[axis] = sign * zl;
+    v[(axis + 1) % 3] = r * c;
+    v[(axis + 2) % 3] = r * s;
+    return make_float3(v[0], v[1], v[2]);
+}
+
+__device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+// ---------------------------------------------------------------------------------------------
+// Sensor connection (Eq. 3-6). `lamb` < 0: isotropic vertex, intensity w/(4 pi); otherwise a
+// Lambertian vertex with normal sign*e_axis (lamb = 2*axis + (sign > 0)), intensity w cos/pi.
+// Transmittance: analytic in homogeneous media, else ratio tracking
+//   T = prod_k (1 - sigma_t(x_k)/sigma_bar) over majorant-distributed points x_k,
+// with roulette (survival 1/2) once the estimate falls below RT_RR_THRESHOLD.
+struct ConnResult { int pix; float val; };
+
+__device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                        float3 x, int b, float w, int lamb, uint64_t pid,
+                                        uint32_t step, RegCnt &rc)
+{
+    float3 dir;
+    float geom, r2 = 0.0f;
+    int px, py;
+    if (S.sensor_kind == FLR_SENSOR_ORTHO) {
+        dir = make_float3(S.s_view[0], S.s_view[1], S.s_view[2]);
+        const float dx = x.x - S.s_origin[0], dy = x.y - S.s_origin[1], dz = x.z - S.s_origin[2];
+        const float su = dx * S.s_U[0] + dy * S.s_U[1] + dz * S.s_U[2];
+        const float sv = dx * S.s_V[0] + dy * S.s_V[1] + dz * S.s_V[2];
+        if (!(su >= 0.0f && su < 1.0f && sv >= 0.0f && sv < 1.0f)) return;
+        px = min(__float2int_rd(su * (float)S.W), S.W - 1);
+        py = min(__float2int_rd(sv * (float)S.H), S.H - 1);
+        geom = S.inv_A_pix;
+    } else {
+        const float vx = x.x - S.s_origin[0], vy = x.y - S.s_origin[1], vz = x.z - S.s_origin[2];
+        r2 = vx * vx + vy * vy + vz * vz;
+        const float zf = vx * S.s_view[0] + vy * S.s_view[1] + vz * S.s_view[2];
+        if (!(zf > 0.0f)) return;
+        const float izf = __frcp_rn(zf);
+        const float X = (vx * S.s_U[0] + vy * S.s_U[1] + vz * S.s_U[2]) * izf;
+        const float Y = (vx * S.s_V[0] + vy * S.s_V[1] + vz * S.s_V[2]) * izf;
+        const float sx = 0.5f * (X / S.tan_x + 1.0f);
+        const float sy = 0.5f * (Y / S.tan_y + 1.0f);
+        if (!(sx >= 0.0f && sx < 1.0f && sy >= 0.0f && sy < 1.0f)) return;
+        px = min(__float2int_rd(sx * (float)S.W), S.W - 1);
+        py = min(__float2int_rd(sy * (float)S.H), S.H - 1);
+        const float ir = rsqrtf(r2);
+        dir = make_float3(-vx * ir, -vy * ir, -vz * ir);
+        const float ct = zf * ir;
+        geom = S.inv_A_pix / (r2 * ct * ct * ct);
+    }
+    float f;
+    if (lamb >= 0) {
+        const int axis = lamb >> 1;
+        const float co = (lamb & 1) ? comp(dir, axis) : -comp(dir, axis);
+        if (!(co > 0.0f)) return;
+        f = co * INV_PI;
+    } else {
+        f = INV_4PI;
+    }
+    int face;
+    const float3 idr = inv_dir(dir);
+    const float tl = exit_distance(S, x, dir, idr, face);
+    if (face < 0) return;
+    if (S.wall_mask & (1 << face)) return;
+    if (S.sensor_kind == FLR_SENSOR_PINHOLE && tl * tl > r2) return;
+    rc.connections++;
+    const float sb = sm.maj[b];
+    float T = 1.0f;
+    if (sb > 0.0f) {
+        if (S.homogeneous) {
+            T = __expf(-sigma_t_at(S, sm, x, b) * tl);
+        } else {
+            const float isb = __frcp_rn(sb);
+            float t = 0.0f;
+            U4 blk = U4{0, 0, 0, 0};
+            uint32_t j = 0;
+            int it = 0;
+            for (; it < MAX_CONNECT_STEPS; ++it) {
+                if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
+                const uint32_t q = j & 3u;
+                const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
+                ++j;
+                t -= __logf(1.0f - u) * isb;
+                if (t >= tl) break;
+                rc.connect_steps++;
+                const float3 p = make_float3(x.x + t * dir.x, x.y + t * dir.y, x.z + t * dir.z);
+                T *= fmaxf(0.0f, 1.0f - sigma_t_at(S, sm, p, b) * isb);
+                if (T < RT_RR_THRESHOLD) {
+                    if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
+                    const uint32_t q2 = j & 3u;
+                    const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
+                    ++j;
+                    if (u2 < 0.5f) {
+                        T *= 2.0f;
+                    } else {
+                        T = 0.0f;
+                        break;
+                    }
+                }
+            }
+            if (it == MAX_CONNECT_STEPS) {
+                T = 0.0f;
+                cnt_add(sm, FLR_C_CONNECT_BUDGET);
+            }
+        }
+    }
+    const float val = w * f * T * geom * R.film_scale;
+    if (val > 0.0f) atomicAdd(&R.film[((size_t)py * S.W + px) * S.B + b], val);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Path state and one tracking step.
+struct Path {
+    float3 x, w, iw;
+    float wt;
+    int bin;
+    uint32_t step;
+    int n_events, n_inel, fl;
+    uint64_t pid;
+    bool alive;
+};
+
+// A connection requested by a step: position, bin, weight, vertex kind, and the RNG coordinates.
+struct Conn {
+    float3 x;
+    float w;
+    int bin, lamb;
+    uint64_t pid;
+    uint32_t step;
+    bool valid;
+};
+
+__device__ __forceinline__ int sample_cdf(const float *cdf, int B, float u)
+{
+    // min{ i : cdf[i] > u }; cdf is non-decreasing with cdf[B-1] = 1 > u.
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cdf[mid] > u) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void finish(const RunDev &R, Path &p)
+{
+    p.alive = false;
+    if (R.path_events) R.path_events[p.pid - R.path_offset] = (uint32_t)p.n_events;
+}
+
+__device__ __forceinline__ Conn spawn(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                      uint64_t pid, Path &p)
+{
+    cnt_add(sm, FLR_C_PATHS);
+    const U4 s0 = draw(R.seed, R.medium_id, pid, STEP_SPAWN, 0u);
+    int k = 0;
+    while (k < S.n_emitters - 1 && !(S.em_cdf[k] > s0.a)) ++k;
+    const EmitterDev &e = S.em[k];
+    p.x = make_float3(e.origin[0] + s0.b * e.eu[0] + s0.c * e.ev[0],
+                      e.origin[1] + s0.b * e.eu[1] + s0.c * e.ev[1],
+                      e.origin[2] + s0.b * e.eu[2] + s0.c * e.ev[2]);
+    p.bin = e.bin;
+    p.wt = 1.0f;
+    p.step = 0;
+    p.n_events = 0;
+    p.n_inel = 0;
+    p.fl = 0;
+    p.pid = pid;
+    p.alive = true;
+    Conn c;
+    c.valid = false;
+    if (e.kind == FLR_SOURCE_LAMBERTIAN) {
+        const U4 s1 = draw(R.seed, R.medium_id, pid, STEP_SPAWN, 1u);
+        p.w = cosine_dir(s0.d, s1.a, e.axis, e.sign);
+        if (S.sensor_kind != FLR_SENSOR_NONE) {
+            c = Conn{p.x, p.wt, p.bin, 2 * e.axis + (e.sign > 0.0f ? 1 : 0), pid, STEP_SPAWN, true};
+        }
+    } else {
+        p.w = make_float3(e.dir[0], e.dir[1], e.dir[2]);
+    }
+    p.iw = inv_dir(p.w);
+    return c;
+}
+
+// One tracking step (null or real collision, wall bounce or escape). Returns the connection the
+// step asks for, if any.
+__device__ __forceinline__ Conn track_step(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                           Path &p, RegCnt &rc)
+{
+    Conn c;
+    c.valid = false;
+    if ((long long)p.step >= R.max_steps) {
+        cnt_add(sm, FLR_C_STEP_BUDGET);
+        finish(R, p);
+        return c;
+    }
+    rc.steps++;
+    const U4 b0 = draw(R.seed, R.medium_id, p.pid, p.step, 0u);
+    const float sb = sm.maj[p.bin];
+    const float tf = sb > 0.0f ? -__logf(1.0f - b0.a) / sb : FLT_MAX;
+    int face;
+    const float te = exit_distance(S, p.x, p.w, p.iw, face);
+    const uint32_t step = p.step;
+    p.step++;
+    if (tf >= te) {
+        p.x = make_float3(p.x.x + te * p.w.x, p.x.y + te * p.w.y, p.x.z + te * p.w.z);
+        if (face < 0) {  // no direction component: cannot happen for unit directions
+            cnt_add(sm, FLR_C_NONFINITE);
+            finish(R, p);
+            return c;
+        }
+        if (S.wall_mask & (1 << face)) {
+            if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
+            p.n_events++;
+            rc.events++;
+            cnt_add(sm, FLR_C_WALL_BOUNCES);
+            const U4 b1 = draw(R.seed, R.medium_id, p.pid, step, 1u);
+            if (R.analog) {
+                if (!(b1.d < S.wall_albedo)) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+            } else {
+                p.wt *= S.wall_albedo;
+                if (p.wt == 0.0f) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+            }
+            const int ax = face >> 1;
+            const float sg = (face & 1) ? -1.0f : 1.0f;
+            if (ax == 0) p.x.x = (face & 1) ? S.hi[0] : S.lo[0];
+            else if (ax == 1) p.x.y = (face & 1) ? S.hi[1] : S.lo[1];
+            else p.x.z = (face & 1) ? S.hi[2] : S.lo[2];
+            p.w = cosine_dir(b0.c, b0.d, ax, sg);
+            p.iw = inv_dir(p.w);
+            if (S.sensor_kind != FLR_SENSOR_NONE)
+                c = Conn{p.x, p.wt, p.bin, 2 * ax + (sg > 0.0f ? 1 : 0), p.pid, step, true};
+            if (p.n_events >= R.n_rr) {
+                const float q = fminf(p.wt, 1.0f);
+                if (!(b1.c < q)) { cnt_add(sm, FLR_C_RR_KILLS); finish(R, p); return c; }
+                p.wt /= q;
+            }
+            return c;
+        }
+        tally_add(sm, tal_face(S.B) + (p.fl * 6 + face) * S.B + p.bin, p.wt);
+        cnt_add(sm, FLR_C_ESCAPES);
+        finish(R, p);
+        return c;
+    }
+    p.x = make_float3(p.x.x + tf * p.w.x, p.x.y + tf * p.w.y, p.x.z + tf * p.w.z);
+    const Coeffs k = coeffs_at(S, sm, p.x, p.bin);
+    if (k.total > sb) cnt_add(sm, FLR_C_MAJORANT_VIOLATIONS);
+    if (!(b0.b * sb < k.total)) {
+        rc.nulls++;
+        return c;
+    }
+    if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
+    p.n_events++;
+    rc.events++;
+    const U4 b1 = draw(R.seed, R.medium_id, p.pid, step, 1u);
+    // particle type in proportion to its coefficient (Sec. 4.1)
+    const float ue = b0.c * k.total;
+    float acc = k.scat;
+    int ev = -1;
+    if (!(ue < acc)) {
+        ev = S.D;
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) {
+            if (d < S.D && ev == S.D) {
+                acc += k.dye[d];
+                if (ue < acc) ev = d;
+            }
+        }
+    }
+    if (ev < 0) {
+        rc.scatters++;
+        p.w = iso_dir(b0.d, b1.a);
+        p.iw = inv_dir(p.w);
+        if (S.sensor_kind != FLR_SENSOR_NONE) c = Conn{p.x, p.wt, p.bin, -1, p.pid, step, true};
+    } else if (ev < S.D) {
+        cnt_add(sm, FLR_C_DYE_ABSORPTIONS);
+        tally_add(sm, tal_absorbed(S.B) + ev * S.B + p.bin, p.wt);
+        if (R.max_inelastic >= 0 && p.n_inel >= R.max_inelastic) {
+            cnt_add(sm, FLR_C_VF_REJECTED);
+            finish(R, p);
+            return c;
+        }
+        if (R.analog) {
+            if (!(b1.d < sm.qy[ev])) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+        } else {
+            p.wt *= sm.qy[ev];
+            if (p.wt == 0.0f) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+        }
+        p.bin = sample_cdf(sm.cdf + ev * S.B, S.B, b1.b);
+        tally_add(sm, tal_emitted(S.B) + ev * S.B + p.bin, p.wt);
+        cnt_add(sm, FLR_C_EMISSIONS);
+        p.n_inel++;
+        p.fl = 1;
+        p.w = iso_dir(b0.d, b1.a);
+        p.iw = inv_dir(p.w);
+        if (S.sensor_kind != FLR_SENSOR_NONE) c = Conn{p.x, p.wt, p.bin, -1, p.pid, step, true};
+    } else {
+        tally_add(sm, tal_absorbed(S.B) + S.D * S.B + p.bin, p.wt);
+        cnt_add(sm, FLR_C_ABSORBED_DEAD);
+        finish(R, p);
+        return c;
+    }
+    if (p.n_events >= R.n_rr) {
+        const float q = fminf(p.wt, 1.0f);
+        if (!(b1.c < q)) { cnt_add(sm, FLR_C_RR_KILLS); finish(R, p); return c; }
+        p.wt /= q;
+    }
+    if (!(isfinite(p.wt) && isfinite(p.x.x) && isfinite(p.x.y) && isfinite(p.x.z))) {
+        cnt_add(sm, FLR_C_NONFINITE);
+        finish(R, p);
+        c.valid = false;
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Block prologue / epilogue: stage tables, zero and flush block tallies and counters.
+struct SmemLayout {
+    int tab_floats, tal_off_bytes, cnt_off_bytes, queue_off_bytes, total_bytes;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int B, int form, int block)
+{
+    SmemLayout L;
+    L.tab_floats = tab_size(B);
+    int off = ((L.tab_floats * 4 + 15) / 16) * 16;
+    L.tal_off_bytes = off;
+    off += tal_size(B) * 8;
+    L.cnt_off_bytes = off;
+    off += FLR_NCOUNTERS * 8;
+    off = ((off + 15) / 16) * 16;
+    L.queue_off_bytes = off;
+    if (form == FLR_FORM_WAVEFRONT) off += 2 * block * 32 + 16;
+    L.total_bytes = off;
+    return L;
+}
+
+__device__ __forceinline__ Smem block_prologue(const SceneDev &S, unsigned char *raw, const SmemLayout &L)
+{
+    float *tab = reinterpret_cast<float *>(raw);
+    for (int i = threadIdx.x; i < L.tab_floats; i += blockDim.x) tab[i] = S.tables[i];
+    unsigned long long *tal = reinterpret_cast<unsigned long long *>(raw + L.tal_off_bytes);
+    for (int i = threadIdx.x; i < tal_size(S.B); i += blockDim.x) tal[i] = 0ull;
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(raw + L.cnt_off_bytes);
+    for (int i = threadIdx.x; i < FLR_NCOUNTERS; i += blockDim.x) cnt[i] = 0ull;
+    __syncthreads();
+    Smem sm;
+    sm.sig_a = tab + tab_sig_a(S.B);
+    sm.cdf = tab + tab_cdf(S.B);
+    sm.maj = tab + tab_majorant(S.B);
+    sm.qy = tab + tab_qy(S.B);
+    sm.tal = tal;
+    sm.cnt = cnt;
+    return sm;
+}
+
+__device__ __forceinline__ unsigned warp_sum(unsigned v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void block_epilogue(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                               const RegCnt &rc)
+{
+    const unsigned vals[6] = {rc.steps, rc.nulls, rc.events, rc.scatters, rc.connections,
+                              rc.connect_steps};
+    const int idx[6] = {FLR_C_STEPS, FLR_C_NULLS, FLR_C_EVENTS, FLR_C_SCATTERS, FLR_C_CONNECTIONS,
+                        FLR_C_CONNECT_STEPS};
+    // 32-bit per-thread counters; warp sums are widened before they can overflow
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        unsigned long long v = vals[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&sm.cnt[idx[i]], v);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < tal_size(S.B); i += blockDim.x)
+        if (sm.tal[i]) atomicAdd(&R.tallies[i], sm.tal[i]);
+    for (int i = threadIdx.x; i < FLR_NCOUNTERS; i += blockDim.x)
+        if (sm.cnt[i]) atomicAdd(&R.counters[i], sm.cnt[i]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Plain form: one thread per path, grid-stride over path ids, connections made inline.
+__global__ void __launch_bounds__(256) k_trace_plain(SceneDev S, RunDev R)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L);
+    RegCnt rc = {0, 0, 0, 0, 0, 0};
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
+        Path p;
+        Conn c = spawn(S, R, sm, R.path_offset + i, p);
+        if (c.valid) connect(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
+        while (p.alive) {
+            c = track_step(S, R, sm, p, rc);
+            if (c.valid) connect(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
+        }
+    }
+    block_epilogue(S, R, sm, rc);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Wavefront form: persistent blocks; each thread regenerates a new path (dynamic queue) as soon
+// as its path ends; sensor connections are pushed to a block queue and made in batches of
+// blockDim, so the ratio-tracking marches run with full warps instead of a few lanes of a
+// tracking warp. Each thread steps until it has queued one connection or made `regroup` steps.
+struct Queue {
+    float *x, *y, *z, *w;
+    int *bin_lamb;
+    uint32_t *pid_lo, *pid_hi, *step;
+    int *head_tail;  // [0] head, [1] tail (monotone; capacity 2 * blockDim)
+};
+
+__device__ __forceinline__ void queue_push(const Queue &q, int cap, const Conn &c)
+{
+    const int slot = atomicAdd(&q.head_tail[1], 1) % cap;
+    q.x[slot] = c.x.x;
+    q.y[slot] = c.x.y;
+    q.z[slot] = c.x.z;
+    q.w[slot] = c.w;
+    q.bin_lamb[slot] = (c.bin & 0xFFFF) | ((c.lamb + 1) << 16);
+    q.pid_lo[slot] = (uint32_t)c.pid;
+    q.pid_hi[slot] = (uint32_t)(c.pid >> 32);
+    q.step[slot] = c.step;
+}
+
+__device__ __forceinline__ void queue_drain(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                            const Queue &q, int cap, int min_batch, RegCnt &rc)
+{
+    // called by the whole block after a __syncthreads(); drains batches of >= min_batch entries
+    while (true) {
+        const int head = q.head_tail[0], tail = q.head_tail[1];
+        const int n = tail - head;
+        if (n <= 0 || n < min_batch) break;
+        const int take = min(n, (int)blockDim.x);
+        if ((int)threadIdx.x < take) {
+            const int slot = (head + (int)threadIdx.x) % cap;
+            const int bl = q.bin_lamb[slot];
+            const uint64_t pid = ((uint64_t)q.pid_hi[slot] << 32) | q.pid_lo[slot];
+            connect(S, R, sm, make_float3(q.x[slot], q.y[slot], q.z[slot]), bl & 0xFFFF, q.w[slot],
+                    (bl >> 16) - 1, pid, q.step[slot], rc);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) q.head_tail[0] = head + take;
+        __syncthreads();
+    }
+    // rebase the ring counters (by a multiple of the capacity) so they never overflow
+    if (threadIdx.x == 0) {
+        const int base = q.head_tail[0] - q.head_tail[0] % cap;
+        q.head_tail[0] -= base;
+        q.head_tail[1] -= base;
+    }
+    // every thread has read head/tail before anyone pushes again
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_trace_wavefront(SceneDev S, RunDev R)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L);
+    const int cap = 2 * blockDim.x;
+    Queue q;
+    {
+        unsigned char *base = smem_raw + L.queue_off_bytes;
+        q.x = reinterpret_cast<float *>(base);
+        q.y = q.x + cap;
+        q.z = q.y + cap;
+        q.w = q.z + cap;
+        q.bin_lamb = reinterpret_cast<int *>(q.w + cap);
+        q.pid_lo = reinterpret_cast<uint32_t *>(q.bin_lamb + cap);
+        q.pid_hi = q.pid_lo + cap;
+        q.step = q.pid_hi + cap;
+        q.head_tail = reinterpret_cast<int *>(q.step + cap);
+        if (threadIdx.x == 0) { q.head_tail[0] = 0; q.head_tail[1] = 0; }
+    }
+    __shared__ int s_active;
+    __syncthreads();
+    RegCnt rc = {0, 0, 0, 0, 0, 0};
+    Path p;
+    p.alive = false;
+    bool exhausted = false;
+    const int regroup = R.regroup > 0 ? R.regroup : 8;
+    for (long long round = 0;; ++round) {
+        // stepping phase: at most `regroup` steps or one queued connection per thread
+        for (int s = 0; s < regroup; ++s) {
+            if (!p.alive) {
+                if (exhausted) break;
+                const unsigned long long i = atomicAdd(R.work_counter, 1ull);
+                if (i >= R.n_paths) { exhausted = true; break; }
+                const Conn c = spawn(S, R, sm, R.path_offset + i, p);
+                if (c.valid) { queue_push(q, cap, c); break; }
+                continue;
+            }
+            const Conn c = track_step(S, R, sm, p, rc);
+            if (c.valid) { queue_push(q, cap, c); break; }
+        }
+        if (threadIdx.x == 0) s_active = 0;
+        __syncthreads();
+        if (p.alive || !exhausted) atomicOr(&s_active, 1);
+        __syncthreads();
+        const bool any = s_active != 0;
+        // regrouped connection phase: full batches while work remains, everything at the end
+        queue_drain(S, R, sm, q, cap, any ? (int)blockDim.x : 1, rc);
+        if (!any) break;
+    }
+    block_epilogue(S, R, sm, rc);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Utility kernels.
+__global__ void k_grid_max(const float *__restrict__ g, long long n, unsigned int *out_bits,
+                           int *neg_flag)
+{
+    float m = 0.0f;
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float v = g[i];
+        if (!(v >= 0.0f) || !isfinite(v)) bad = true; else m = fmaxf(m, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(m));
+    if (bad) atomicOr(neg_flag, 1);
+}
+
+struct PackArgs {
+    const float *conc[MAXD];
+    float uniform[MAXD];
+    int D;
+};
+
+__global__ void k_pack_grid(PackArgs a, long long n, float4 *__restrict__ out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d)
+            if (d < a.D) v[d] = a.conc[d] ? a.conc[d][i] : a.uniform[d];
+        out[i] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+__global__ void k_solvent_any(const uint8_t *__restrict__ s, long long n, unsigned int *out)
+{
+    unsigned any = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        any |= s[i] ? 1u : 0u;
+    if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(out, 1u);
+}
+
+__global__ void k_philox(uint32_t seed, uint32_t medium, const uint4 *__restrict__ ctr, long long n,
+                         uint4 *__restrict__ out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = philox(ctr[i], seed, medium);
+}
+
+__global__ void k_sample_emission(const float *__restrict__ cdf, int B, const float *__restrict__ u,
+                                  long long n, int32_t *__restrict__ out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = sample_cdf(cdf, B, u[i]);
+}
+
+int num_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Launchers.
+int trace_block_default() { return 256; }
+
+int trace_smem_bytes(int B, int form, int block) { return smem_layout(B, form, block).total_bytes; }
+
+int occupancy_blocks_per_sm(int B, int form, int block)
+{
+    int n = 0;
+    const int smem = trace_smem_bytes(B, form, block);
+    if (form == FLR_FORM_WAVEFRONT)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront, block, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_plain, block, smem);
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block, int blocks_per_sm,
+                         cudaStream_t st)
+{
+    if (block <= 0) block = trace_block_default();
+    const int smem = trace_smem_bytes(S.B, form, block);
+    const int occ = occupancy_blocks_per_sm(S.B, form, block);
+    if (blocks_per_sm <= 0 || blocks_per_sm > occ) blocks_per_sm = occ;
+    long long grid = (long long)num_sms() * blocks_per_sm;
+    if (form == FLR_FORM_PLAIN) {
+        const long long need = ((long long)R.n_paths + block - 1) / block;
+        if (need < grid) grid = need;
+    }
+    if (grid < 1) grid = 1;
+    if (form == FLR_FORM_WAVEFRONT)
+        k_trace_wavefront<<<(unsigned)grid, block, smem, st>>>(S, R);
+    else
+        k_trace_plain<<<(unsigned)grid, block, smem, st>>>(S, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_max(const float *g, long long n, unsigned int *out_bits, int *neg_flag,
+                            cudaStream_t st)
+{
+    long long blocks = (n + 255) / 256;
+    const long long cap = (long long)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_grid_max<<<(unsigned)blocks, 256, 0, st>>>(g, n, out_bits, neg_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_grid(const float *const *conc, const float *uniform, int D, long long n,
+                             float4 *out, cudaStream_t st)
+{
+    PackArgs a;
+    for (int d = 0; d < MAXD; ++d) {
+        a.conc[d] = d < D ? conc[d] : nullptr;
+        a.uniform[d] = d < D ? uniform[d] : 0.0f;
+    }
+    a.D = D;
+    long long blocks = (n + 255) / 256;
+    const long long cap = (long long)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_pack_grid<<<(unsigned)blocks, 256, 0, st>>>(a, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solvent_any(const uint8_t *s, long long n, unsigned int *out, cudaStream_t st)
+{
+    long long blocks = (n + 255) / 256;
+    const long long cap = (long long)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_solvent_any<<<(unsigned)blocks, 256, 0, st>>>(s, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, long long n,
+                          uint32_t *out, cudaStream_t st)
+{
+    long long blocks = (n + 255) / 256;
+    const long long cap = (long long)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_philox<<<(unsigned)blocks, 256, 0, st>>>(seed, medium, reinterpret_cast<const uint4 *>(ctr), n,
+                                                reinterpret_cast<uint4 *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_emission(const SceneDev &S, int dye, const float *u, long long n,
+                                   int32_t *out, cudaStream_t st)
+{
+    long long blocks = (n + 255) / 256;
+    const long long cap = (long long)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_sample_emission<<<(unsigned)blocks, 256, 0, st>>>(S.tables + tab_cdf(S.B) + dye * S.B, S.B, u,
+                                                         n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace flr

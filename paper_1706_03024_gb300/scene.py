@@ -1,0 +1,191 @@
+"""Scene marshalling: a scene description dict (the layout scenegen documents) -> C-ABI calls.
+
+PyTorch provides device memory and streams only. Grids are copied to CUDA tensors here; the
+library's own kernels do every step of the transport.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import native as N
+
+_KINDS = {"collimated": N.FLR_SOURCE_COLLIMATED, "lambertian": N.FLR_SOURCE_LAMBERTIAN}
+_SENSORS = {"none": N.FLR_SENSOR_NONE, "ortho": N.FLR_SENSOR_ORTHO, "pinhole": N.FLR_SENSOR_PINHOLE}
+_FORMS = {"plain": N.FLR_FORM_PLAIN, "wavefront": N.FLR_FORM_WAVEFRONT}
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def make_source(src):
+    s = N.flr_source()
+    s.kind = _KINDS[src["kind"]]
+    s.origin[:] = src["origin"]
+    s.eu[:] = src["eu"]
+    s.ev[:] = src["ev"]
+    s.dir[:] = src["dir"]
+    lines = list(src["lines_nm"])
+    if not 1 <= len(lines) <= N.FLR_MAX_LINES:
+        raise ValueError("1..8 lines per source")
+    s.n_lines = len(lines)
+    for i, (lam, pw) in enumerate(zip(lines, src["power"])):
+        s.lambda_nm[i] = float(lam)
+        s.power[i] = float(pw)
+    return s
+
+
+def make_sensor(sn):
+    c = N.flr_sensor()
+    c.kind = _SENSORS[sn["kind"]]
+    c.width = int(sn["width"])
+    c.height = int(sn["height"])
+    c.origin[:] = sn["origin"]
+    c.U[:] = sn["U"]
+    c.V[:] = sn["V"]
+    c.view[:] = sn["view"]
+    c.fov_y_deg = float(sn["fov_y_deg"])
+    return c
+
+
+class Scene:
+    """One context holding one single-scene medium. Use render() / read()."""
+
+    def __init__(self, scene, device=0, grids=None):
+        """scene: scenegen dict. grids: optional dict of already-resident CUDA tensors
+        {'conc': [D,nz,ny,nx] f32, 'solvent': [nz,ny,nx] u8} used instead of copying."""
+        self.device = device
+        self.desc = scene
+        self.ctx = N.flr_create(device)
+        self._keep = []
+        sp, dy, md = scene["spectrum"], scene["dyes"], scene["medium"]
+        self.B = int(sp["n_bins"])
+        N.check(N.flr_set_spectrum(self.ctx, sp["lambda0"], sp["dlambda"], self.B), self.ctx,
+                "flr_set_spectrum")
+        self.set_dyes(dy)
+        srcs = scene["sources"]
+        arr = (N.flr_source * len(srcs))(*[make_source(s) for s in srcs])
+        N.check(N.flr_set_sources(self.ctx, len(srcs), arr), self.ctx, "flr_set_sources")
+        self.D = int(np.asarray(dy["eps"]).shape[0])
+        self.set_medium(md, grids)
+        self.sensor = scene["sensor"]
+        N.check(N.flr_set_sensor(self.ctx, make_sensor(self.sensor)), self.ctx, "flr_set_sensor")
+        self.film = None
+
+    def set_dyes(self, dy):
+        a = np.ascontiguousarray(dy["abs_shape"], np.float32)
+        e = np.ascontiguousarray(dy["emit_spec"], np.float32)
+        eps = np.ascontiguousarray(dy["eps"], np.float32)
+        qy = np.ascontiguousarray(dy["qy"], np.float32)
+        N.check(N.flr_set_dyes(self.ctx, eps.shape[0], _np_ptr(a), _np_ptr(e), _np_ptr(eps),
+                               _np_ptr(qy)), self.ctx, "flr_set_dyes")
+
+    def set_medium(self, md, grids=None):
+        m = N.flr_medium()
+        m.lo[:] = md["lo"]
+        m.hi[:] = md["hi"]
+        D = self.D
+        m.n_dyes = D
+        for d in range(D):
+            m.dye_ids[d] = d
+        cu = np.asarray(md["conc_uniform"], np.float32)
+        for d in range(D):
+            m.conc_uniform[d] = float(cu[d]) if d < cu.shape[0] else 0.0
+        dev = torch.device("cuda", self.device)
+        conc_t = None
+        solv_t = None
+        if grids is not None:
+            conc_t = grids.get("conc")
+            solv_t = grids.get("solvent")
+        else:
+            if md.get("conc") is not None:
+                conc_t = torch.from_numpy(np.ascontiguousarray(md["conc"], np.float32)).to(dev)
+            if md.get("solvent") is not None:
+                solv_t = torch.from_numpy(np.ascontiguousarray(md["solvent"], np.uint8)).to(dev)
+        self.conc_t, self.solv_t = conc_t, solv_t
+        if conc_t is not None:
+            Dg, nz, ny, nx = conc_t.shape
+            m.dims[:] = (nx, ny, nz)
+            for d in range(D):
+                m.conc[d] = conc_t[d].data_ptr()
+        elif solv_t is not None:
+            nz, ny, nx = solv_t.shape
+            m.dims[:] = (nx, ny, nz)
+        if solv_t is not None:
+            m.solvent = solv_t.data_ptr()
+        m.sigma_s = float(md["sigma_s"])
+        m.sigma_a0 = float(md["sigma_a0"])
+        m.wall_mask = int(md["wall_mask"])
+        m.wall_albedo = float(md["wall_albedo"])
+        N.check(N.flr_set_medium(self.ctx, m), self.ctx, "flr_set_medium")
+
+    def film_tensor(self):
+        sn = self.sensor
+        if sn["kind"] == "none":
+            return None
+        if self.film is None:
+            self.film = torch.zeros((sn["height"], sn["width"], self.B), dtype=torch.float32,
+                                    device=torch.device("cuda", self.device))
+        return self.film
+
+    def render(self, n_paths=None, path_offset=0, seed=None, medium_id=0, form="plain",
+               analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
+               film=True, path_events=None, accumulate=False, block_size=0, blocks_per_sm=0,
+               regroup=0, stream=None):
+        pp = dict(self.desc["params"])
+        for k, v in (("n_paths", n_paths), ("seed", seed), ("analog", analog),
+                     ("max_inelastic", max_inelastic), ("n_rr", n_rr), ("max_events", max_events),
+                     ("max_steps", max_steps)):
+            if v is not None:
+                pp[k] = v
+        p = N.flr_params()
+        p.n_paths = int(pp["n_paths"])
+        p.path_offset = int(path_offset)
+        p.seed = int(pp["seed"])
+        p.medium_id = int(medium_id)
+        p.n_rr = int(pp["n_rr"])
+        p.max_inelastic = int(pp["max_inelastic"])
+        p.analog = int(pp["analog"])
+        p.form = _FORMS[form] if isinstance(form, str) else int(form)
+        p.max_events = int(pp["max_events"])
+        p.max_steps = int(pp.get("max_steps", 100_000_000))
+        f = self.film_tensor() if film else None
+        p.film = f.data_ptr() if f is not None else None
+        p.path_events = path_events.data_ptr() if path_events is not None else None
+        p.accumulate = 1 if accumulate else 0
+        p.block_size = int(block_size)
+        p.blocks_per_sm = int(blocks_per_sm)
+        p.regroup_interval = int(regroup)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        N.check(N.flr_render(self.ctx, p, st.cuda_stream), self.ctx, "flr_render")
+        return f
+
+    def read(self, stream=None):
+        B, D = self.B, self.D
+        face = np.zeros((2, 6, B))
+        absorbed = np.zeros((D + 1, B))
+        emitted = np.zeros((max(D, 1), B))
+        counters = np.zeros(N.FLR_NCOUNTERS, np.uint64)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        N.check(N.flr_read_tallies(self.ctx, _np_ptr(face), _np_ptr(absorbed), _np_ptr(emitted),
+                                   _np_ptr(counters), st.cuda_stream), self.ctx,
+                "flr_read_tallies")
+        return {"face": face, "absorbed": absorbed, "emitted": emitted[:D],
+                "counters": {n: int(v) for n, v in zip(N.COUNTER_NAMES, counters)}}
+
+    def status(self):
+        return N.flr_status(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            N.flr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

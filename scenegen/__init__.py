@@ -117,7 +117,7 @@ def pinhole_sensor(width, height, eye, right, up, forward, fov_y_deg):
 
 
 def params(n_paths, seed=0, n_rr=5, max_events=1_000_000, max_inelastic=-1, analog=0,
-           max_steps=100_000_000):
+           max_steps=10_000_000):
     return {"n_paths": int(n_paths), "seed": int(seed), "n_rr": int(n_rr),
             "max_events": int(max_events), "max_inelastic": int(max_inelastic),
             "analog": int(analog), "max_steps": int(max_steps)}

@@ -1,0 +1,62 @@
+"""Helpers for the GPU parity tests: run the CUDA path and the oracle on the same path ids."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1706_03024_gb300 import build as B
+from paper_1706_03024_gb300.scene import Scene
+from tests.stats import batch_mean_se, parity_verdict
+
+
+def require_gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for -m gpu tests (there is no CPU path)")
+    B.build()
+
+
+def gpu_batches(scene, K, n_per, form="plain", scene_obj=None, film=True, **kw):
+    S = scene_obj or Scene(scene)
+    outs = []
+    for k in range(K):
+        f = S.render(n_paths=n_per, path_offset=k * n_per, form=form, film=film, **kw)
+        r = S.read()
+        r["film"] = f.double().cpu().numpy() if (f is not None and film) else None
+        outs.append(r)
+    return outs
+
+
+def oracle_batches(scene, K, n_per, film=True, **kw):
+    return [oracle.render(scene, n_paths=n_per, path_offset=k * n_per, film=film, **kw)
+            for k in range(K)]
+
+
+def totals(outs, key):
+    return np.sum([o[key] for o in outs], axis=0) / len(outs)
+
+
+def compare_integrated(g, o, rel=5e-3, floor=1e-3):
+    """Same-seed integrated tallies: relative difference <= rel where the value is at least
+    `floor` of the largest; returns the worst relative difference."""
+    g, o = np.asarray(g, np.float64), np.asarray(o, np.float64)
+    big = np.abs(o) >= floor * max(np.abs(o).max(), 1e-300)
+    worst = 0.0
+    if big.any():
+        worst = float((np.abs(g[big] - o[big]) / np.abs(o[big])).max())
+    return worst
+
+
+def bin_parity(g_outs, o_outs, key, min_nonzero=None):
+    gs = np.stack([x[key] for x in g_outs])
+    os_ = np.stack([x[key] for x in o_outs])
+    K = gs.shape[0]
+    if min_nonzero is None:
+        min_nonzero = (3 * K) // 4
+    mg, sg = batch_mean_se(gs)
+    mo, so = batch_mean_se(os_)
+    populated = ((gs != 0).sum(axis=0) >= min_nonzero) & ((os_ != 0).sum(axis=0) >= min_nonzero)
+    sg = np.where(populated, sg, 0.0)
+    so = np.where(populated, so, 0.0)
+    return parity_verdict(mg, sg, mo, so)

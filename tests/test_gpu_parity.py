@@ -1,0 +1,328 @@
+"""GPU (C ABI, sm_103a kernels) against the CPU oracle on the same seeded inputs.
+
+Criteria: per spectral bin and per pixel, z = (gpu - oracle) / sqrt(SE_gpu^2 + SE_oracle^2) from
+K batch means (batches = disjoint path-id ranges): at most 1 % of populated bins beyond 3, none
+beyond 5.5, reduced chi-square in [0.8, 1.2] when >= 50 bins are populated. Integrated tallies
+(same seeds, so nearly identical paths) agree within 0.5 % relative. Bit-exact where the work is
+integer: Philox blocks, emission bins, fixed-point tallies between launch forms.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenegen as sg
+from paper_1706_03024_gb300 import native as N
+from paper_1706_03024_gb300.scene import Scene
+from tests.gpu_common import (bin_parity, compare_integrated, gpu_batches, oracle_batches,
+                              require_gpu, totals)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+# ------------------------------------------------------------------------------------------
+# Bit-exact integer work
+
+
+def test_philox_bitwise_against_oracle():
+    n = 1_000_000
+    rng = np.random.default_rng(11)
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:1000] = 0
+    ctr[:1000, 0] = np.arange(1000)
+    for seed, med in ((0, 0), (12345, 77), (0xFFFFFFFF, 0xFFFFFFFF)):
+        want = oracle.philox(seed, med, ctr)
+        c = torch.from_numpy(ctr.view(np.int32)).cuda()
+        out = torch.empty_like(c)
+        assert N.flr_debug_philox(seed, med, c.data_ptr(), n, out.data_ptr(), 0) == N.FLR_OK
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want)
+
+
+def test_emission_bins_bitwise_against_oracle():
+    sc = sg.cfg2_cornell_box(width=16, height=16, grid=16)
+    S = Scene(sc)
+    rng = np.random.default_rng(4)
+    u = (rng.integers(0, 2 ** 24, size=200_000) / 2.0 ** 24)
+    # include every fp32 CDF value itself and its neighbours: the decision boundaries
+    edges = []
+    for d in range(4):
+        f = sc["dyes"]["emit_spec"][d].astype(np.float64)
+        cdf = np.cumsum(f) / f.sum()
+        for c in cdf.astype(np.float32):
+            for k in (-1, 0, 1):
+                v = np.float64(c) + k * 2.0 ** -24
+                if 0.0 <= v < 1.0:
+                    edges.append(np.floor(v * 2 ** 24) / 2 ** 24)
+    u = np.concatenate([u, np.array(edges), [0.0, 1 - 2.0 ** -24]]).astype(np.float32)
+    ut = torch.from_numpy(u).cuda()
+    out = torch.empty(u.shape[0], dtype=torch.int32, device="cuda")
+    for d in range(4):
+        assert N.flr_debug_sample_emission(S.ctx, d, ut.data_ptr(), u.shape[0], out.data_ptr(),
+                                           0) == N.FLR_OK
+        torch.cuda.synchronize()
+        want = oracle.sample_emission(sc, d, u.astype(np.float64))
+        assert np.array_equal(out.cpu().numpy(), want), d
+
+
+# ------------------------------------------------------------------------------------------
+# Statistical parity on the workloads
+
+
+def _check_workload(sc, K, n_per, forms=("plain",), film_min_nonzero=None, path_id_frac=0.99,
+                    **kw):
+    o = oracle_batches(sc, K, n_per, path_events=True, **kw)
+    o_events = np.concatenate([x["path_events"] for x in o])
+    S = Scene(sc)
+    results = {}
+    for form in forms:
+        pe = torch.zeros(K * n_per, dtype=torch.int32, device="cuda")
+        g = []
+        for k in range(K):
+            f = S.render(n_paths=n_per, path_offset=k * n_per, form=form,
+                         path_events=pe[k * n_per:(k + 1) * n_per], **kw)
+            r = S.read()
+            r["film"] = f.double().cpu().numpy() if f is not None else None
+            g.append(r)
+        g_events = pe.cpu().numpy().astype(np.uint32)
+        same = float((g_events == o_events).mean())
+        assert same >= path_id_frac, (form, same)
+        for key in ("face", "absorbed", "emitted"):
+            v = bin_parity(g, o, key)
+            assert v["ok"], (form, key, v)
+            worst = compare_integrated(totals(g, key).sum(axis=-1), totals(o, key).sum(axis=-1))
+            assert worst <= 5e-3, (form, key, worst)
+        if sc["sensor"]["kind"] != "none":
+            v = bin_parity(g, o, "film", film_min_nonzero)
+            assert v["ok"], (form, "film", v)
+            gf, of = totals(g, "film"), totals(o, "film")
+            assert abs(gf.sum() - of.sum()) <= 5e-3 * of.sum() + 4 * np.sqrt(
+                np.var([x["film"].sum() for x in g]) / K + np.var([x["film"].sum() for x in o]) / K)
+        c = g[-1]["counters"]
+        for name in ("majorant_violations", "nonfinite", "connect_budget", "step_budget"):
+            assert c[name] == 0, (form, name, c[name])
+        results[form] = g
+    return results
+
+
+def test_cfg1_homogeneous_cube_parity():
+    sc = sg.cfg1_homogeneous_cube(n_paths=100_000)
+    res = _check_workload(sc, 32, 100_000 // 32, forms=("plain", "wavefront"))
+    # plain and wavefront launch forms trace the same paths: fixed-point tallies bit-identical
+    for a, b in zip(res["plain"], res["wavefront"]):
+        for key in ("face", "absorbed", "emitted"):
+            assert np.array_equal(a[key], b[key])
+        ca, cb = dict(a["counters"]), dict(b["counters"])
+        assert ca == cb
+        assert np.allclose(a["film"], b["film"], rtol=1e-5, atol=1e-7 * a["film"].max())
+
+
+def test_cfg1_analog_and_single_inelastic_parity():
+    sc = sg.cfg1_homogeneous_cube(n_paths=64_000)
+    _check_workload(sc, 32, 2000, forms=("wavefront",), analog=1)
+    _check_workload(sc, 32, 2000, forms=("plain",), max_inelastic=1)
+
+
+def test_cfg2_cornell_box_reduced_parity():
+    sc = sg.cfg2_cornell_box(width=48, height=48, grid=48, n_paths=1)
+    _check_workload(sc, 32, 6000, forms=("plain", "wavefront"), path_id_frac=0.97)
+
+
+def test_cfg4_blobby_grid_ortho_parity():
+    sc = sg.cfg4_adjoint(grid=24, width=24, height=24, n_paths=1)
+    _check_workload(sc, 32, 4000, forms=("wavefront",), path_id_frac=0.97)
+
+
+def test_cfg5_light_sheet_reduced_parity():
+    sc = sg.cfg5_light_sheet(grid=32, width=32, height=32, n_blobs=40, n_paths=1,
+                             sigma_t_ref=20.0)
+    _check_workload(sc, 32, 1500, forms=("wavefront",), path_id_frac=0.95)
+
+
+def test_cfg3_media_parity_sample():
+    media = sg.cfg3_batched_media(n_media=6, seed=0, max_edge=24)
+    for m in media[:6]:
+        _check_workload(m, 16, 1500, forms=("plain",), path_id_frac=0.97)
+
+
+def test_uncollided_transmission_gpu_closed_form():
+    rng = np.random.default_rng(5)
+    n = 6
+    conc = rng.uniform(0.0, 2.0, size=(2, n, n, n)).astype(np.float32)
+    solvent = (rng.random((n, n, n)) < 0.7).astype(np.uint8)
+    dyes = sg.make_dyes([490.0, 500.0], [15.0, 30.0], [620.0, 650.0], [15.0, 15.0],
+                        eps=[0.4, 0.3], qy=[0.5, 0.5])
+    x, y = 0.41, 0.77
+    sc = {"spectrum": sg.spectrum(), "dyes": dyes,
+          "medium": sg.grid_medium(conc, solvent, sigma_s=0.8),
+          "sources": [sg.pencil_beam((x, y, 1.0), (0, 0, -1), [490.0])],
+          "sensor": sg.no_sensor(), "params": sg.params(1_000_000, seed=3)}
+    S = Scene(sc)
+    S.render(max_events=0)
+    r = S.read()
+    T = r["face"][:, sg.FACE_NZ, :].sum()
+    b = int(math.ceil((490 - sg.LAMBDA0) / sg.DLAMBDA - 0.5))
+    tau = oracle.optical_depth(sc, np.array([x, y, 1.0]), np.array([0, 0, -1.0]), 1.0, b)
+    exact = math.exp(-tau)
+    assert abs(T - exact) <= 3 * math.sqrt(exact * (1 - exact) / 1_000_000), (T, exact)
+
+
+# ------------------------------------------------------------------------------------------
+# Edge cases
+
+
+def test_empty_ragged_and_single_path_launches():
+    sc = sg.cfg1_homogeneous_cube(n_paths=1)
+    S = Scene(sc)
+    S.render(n_paths=0)
+    r = S.read()
+    assert r["face"].sum() == 0 and r["counters"]["paths"] == 0
+    for n in (1, 31, 257, 1001):
+        pe = torch.zeros(n, dtype=torch.int32, device="cuda")
+        for form in ("plain", "wavefront"):
+            S.render(n_paths=n, path_offset=12345, form=form, path_events=pe)
+            r = S.read()
+            o = oracle.render(sc, n_paths=n, path_offset=12345, path_events=True)
+            assert r["counters"]["paths"] == n
+            same = (pe.cpu().numpy().astype(np.uint32) == o["path_events"]).mean()
+            assert same >= 0.97, (n, form, same)
+
+
+def test_scattering_only_conserves_exactly_and_empty_medium():
+    sc = sg.cfg1_homogeneous_cube(n_paths=50_000)
+    sc["dyes"]["eps"] = np.zeros(1, np.float32)
+    S = Scene(sc)
+    for form in ("plain", "wavefront"):
+        S.render(form=form)
+        r = S.read()
+        assert r["face"].sum() == 1.0
+        assert r["counters"]["escapes"] == 50_000
+    sc2 = sg.cfg1_homogeneous_cube(n_paths=1000)
+    sc2["medium"]["sigma_s"] = 0.0
+    sc2["dyes"]["eps"] = np.zeros(1, np.float32)
+    S2 = Scene(sc2)
+    S2.render()
+    r = S2.read()
+    assert r["face"][0, sg.FACE_NZ].sum() == 1.0
+    assert r["counters"]["events"] == 0
+
+
+def test_maximum_bins_and_dyes():
+    B = 128
+    lam0, dl = 380.0, 400.0 / (B - 1)
+    lam = lam0 + dl * np.arange(B)
+    peaks = [(440, 480), (490, 520), (540, 600), (600, 660)]
+    dyes = {"abs_shape": np.stack([np.exp(-0.5 * ((lam - a) / 15) ** 2) for a, _ in peaks]
+                                  ).astype(np.float32),
+            "emit_spec": np.stack([np.exp(-0.5 * ((lam - e) / 20) ** 2) for _, e in peaks]
+                                  ).astype(np.float32),
+            "eps": np.array([1.0, 2.0, 1.5, 0.5], np.float32),
+            "qy": np.array([0.9, 0.5, 0.7, 0.3], np.float32)}
+    sc = {"spectrum": {"lambda0": lam0, "dlambda": dl, "n_bins": B}, "dyes": dyes,
+          "medium": sg.homogeneous_medium(4, conc=1.0, sigma_s=10.0),
+          "sources": [sg.pencil_beam((0.5, 0.5, 1.0), (0, 0, -1), [440.0, 490.0, 540.0, 600.0])],
+          "sensor": sg.ortho_sensor(16, 16, (0, 0, 1), (1, 0, 0), (0, 1, 0), (0, 0, 1)),
+          "params": sg.params(1)}
+    o = oracle_batches(sc, 16, 2000)
+    g = gpu_batches(sc, 16, 2000, form="wavefront")
+    for key in ("face", "absorbed", "emitted"):
+        assert bin_parity(g, o, key)["ok"], key
+        assert compare_integrated(totals(g, key).sum(-1), totals(o, key).sum(-1)) <= 5e-3
+
+
+def test_invalid_arguments_are_rejected():
+    sc = sg.cfg1_homogeneous_cube(n_paths=10)
+    S = Scene(sc)
+    ctx = S.ctx
+    a = np.ones((1, 81), np.float32)
+    e = np.ones((1, 81), np.float32)
+    eps = np.ones(1, np.float32)
+    bad_qy = np.array([1.5], np.float32)
+    import ctypes as C
+    p = lambda arr: arr.ctypes.data_as(C.c_void_p)  # noqa: E731
+    assert N.flr_set_dyes(ctx, 1, p(a), p(e), p(eps), p(bad_qy)) == N.FLR_ERR_ARG
+    zero_em = np.zeros((1, 81), np.float32)
+    assert N.flr_set_dyes(ctx, 1, p(a), p(zero_em), p(eps), p(np.ones(1, np.float32))) == \
+        N.FLR_ERR_ARG
+    host_grid = np.ones((4, 4, 4), np.float32)
+    m = N.flr_medium()
+    m.lo[:] = (0, 0, 0)
+    m.hi[:] = (1, 1, 1)
+    m.dims[:] = (4, 4, 4)
+    m.n_dyes = 1
+    m.conc[0] = host_grid.ctypes.data
+    assert N.flr_set_medium(ctx, m) == N.FLR_ERR_ARG
+    assert "device memory" in N.flr_last_error(ctx)
+    neg = torch.full((4, 4, 4), -1.0, device="cuda")
+    m.conc[0] = neg.data_ptr()
+    assert N.flr_set_medium(ctx, m) == N.FLR_ERR_ARG
+    par = N.flr_params()
+    par.n_paths = 10
+    par.max_steps = 100
+    par.block_size = 300
+    assert N.flr_render(ctx, par, 0) == N.FLR_ERR_ARG
+    par.block_size = 0
+    par.form = 7
+    assert N.flr_render(ctx, par, 0) == N.FLR_ERR_ARG
+    cam = N.flr_sensor()
+    cam.kind = N.FLR_SENSOR_PINHOLE
+    cam.width = cam.height = 8
+    cam.origin[:] = (0.5, 0.5, 0.5)
+    cam.U[:] = (1, 0, 0)
+    cam.V[:] = (0, 0, 1)
+    cam.view[:] = (0, 1, 0)
+    cam.fov_y_deg = 40
+    assert N.flr_set_sensor(ctx, cam) == N.FLR_OK
+    par.form = 0
+    assert N.flr_render(ctx, par, 0) == N.FLR_ERR_ARG
+    fresh = N.flr_create(0)
+    assert N.flr_render(fresh, par, 0) == N.FLR_ERR_STATE
+    N.flr_destroy(fresh)
+    assert S.status() == N.FLR_OK
+
+
+# ------------------------------------------------------------------------------------------
+# Full-size workload (the benchmarked configuration): sampled paths and invariants
+
+
+def test_cfg2_full_size_sampled_paths_and_invariants():
+    sc = sg.cfg2_cornell_box()  # 512 x 512 pinhole, 16 spp, 128^3 grids
+    n = sc["params"]["n_paths"]
+    assert n == 512 * 512 * 16
+    S = Scene(sc)
+    pe = torch.zeros(n, dtype=torch.int32, device="cuda")
+    film = S.render(form="wavefront", path_events=pe)
+    r = S.read()
+    c = r["counters"]
+    ends = (c["escapes"] + c["absorbed_dead"] + c["rr_kills"] + c["cap_hits"] + c["step_budget"]
+            + c["vf_rejected"])
+    assert c["paths"] == n and ends == n
+    for name in ("majorant_violations", "nonfinite", "connect_budget", "step_budget"):
+        assert c[name] == 0, name
+    f = film.double()
+    assert torch.isfinite(f).all() and (f >= 0).all() and f.sum() > 0
+    # sampled paths: the oracle traces single paths with the same ids
+    rng = np.random.default_rng(2)
+    ids = np.sort(rng.choice(n, size=200, replace=False))
+    ev = pe.cpu().numpy().astype(np.uint32)
+    same = 0
+    for pid in ids:
+        o = oracle.render(sc, n_paths=1, path_offset=int(pid), film=False, path_events=True,
+                          n_threads=1)
+        same += int(o["path_events"][0] == ev[pid])
+    assert same >= 0.95 * len(ids), same
+    # integrated escape through the open front vs an oracle sample of the same paths
+    o = oracle.render(sc, n_paths=65536, film=False)
+    S2 = Scene(sc)
+    S2.render(n_paths=65536, film=False, form="wavefront")
+    g = S2.read()
+    for key in ("face", "absorbed", "emitted"):
+        assert compare_integrated(g[key].sum(-1), o[key].sum(-1), rel=1e-2) <= 1e-2, key
