@@ -145,6 +145,71 @@ def run_reference(args):
     return 0
 
 
+def bench_batched(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum):
+    """256 independent media (grid edges 16-128, 1-3 dyes, albedo 0.5-0.999, 1e4-1e6 paths each):
+    one persistent launch replayed from a CUDA graph, against the plain single-scene kernel run
+    medium by medium on the same paths (same estimator and paths: equal RMSE)."""
+    import torch
+    from paper_1706_03024_gb300.scene import Batch, Scene
+
+    media = sg.cfg3_batched_media(n_media=256, seed=0)
+    bt = Batch(media, device=local, seed=rank, medium_id=0)
+    for _ in range(max(1, args.warmup - 2)):
+        bt.launch()
+    torch.cuda.synchronize()
+    ms, events = [], 0
+    counters = None
+    barrier()
+    for i in range(args.batch_steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bt.launch()
+        b.record(stream)
+        counters = bt.read()["counters"]
+        ms.append(a.elapsed_time(b))
+    barrier()
+    step_ms = reduce_max(sum(ms) / len(ms))
+    ev = reduce_sum(float(counters["events"]))
+    value = ev / (step_ms / 1000.0)
+    # plain kernel, one medium after another (each its own launch), same paths
+    plain_ms = 0.0
+    plain_events = 0
+    scenes = []
+    for m, sc in enumerate(media):
+        S = Scene(sc, device=local)
+        S.render(form="plain", seed=rank, medium_id=m, film=False)  # warm-up
+        scenes.append(S)
+    torch.cuda.synchronize()
+    flush.fill_(0.5)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for m, S in enumerate(scenes):
+        S.render(form="plain", seed=rank, medium_id=m, film=False)
+    b.record(stream)
+    for S in scenes:
+        plain_events += S.read()["counters"]["events"]
+    torch.cuda.synchronize()
+    plain_ms = reduce_max(a.elapsed_time(b))
+    plain_value = reduce_sum(float(plain_events)) / (plain_ms / 1000.0)
+    for S in scenes:
+        S.close()
+    ops = algorithmic_ops(counters)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = sms * 128 * float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+    achieved = ops / (sum(ms) / len(ms) / 1000.0)
+    bt.close()
+    return {"workload": "256 media, edges 16-128, 1-3 dyes, albedo 0.5-0.999, 1e4-1e6 paths each"
+                        f" ({int(bt.n_paths.sum())} paths)",
+            "events_per_s": value, "ms_per_step": step_ms, "steps": len(ms),
+            "ms_steps": [round(v, 3) for v in ms],
+            "plain_per_medium_events_per_s": plain_value, "plain_ms": plain_ms,
+            "plain_launches": len(media), "speedup_vs_plain": value / plain_value,
+            "events_per_step": counters["events"],
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                         "unit": "Tops/s", "frac": achieved / peak}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -164,6 +229,8 @@ def run_ours(args):
             dist.barrier()
 
     sc = sg.cfg2_cornell_box()
+    if args.paths:
+        sc["params"]["n_paths"] = int(args.paths)
     n_paths = sc["params"]["n_paths"]
     S = Scene(sc, device=local)
     stream = torch.cuda.current_stream(dev)
@@ -178,11 +245,15 @@ def run_ours(args):
                for _ in range(steps)]
         events = 0
         counters = None
-        barrier()
-        torch.cuda.synchronize()
         proc = f = None
         if sampler_path:
+            # nvidia-smi's own start-up must not overlap the timed steps
             proc, f = start_clock_sampler(local, sampler_path)
+            one_step(form)
+            torch.cuda.synchronize()
+            time.sleep(1.0)
+        barrier()
+        torch.cuda.synchronize()
         for i in range(steps):
             flush.fill_(float(i))          # evict the scene and film from L2 between steps
             evs[i][0].record(stream)
@@ -230,6 +301,11 @@ def run_ours(args):
     value = total_ev_w / (step_ms_w / 1000.0)
     plain_value = total_ev_p / (step_ms_p / 1000.0)
     paths_per_s = reduce_sum(float(n_paths)) / (step_ms_w / 1000.0)
+
+    # --- batched persistent form: 256 media in one launch (CUDA graph) ----------------------
+    batched = None
+    if not args.no_batch:
+        batched = bench_batched(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
 
     # --- end to end through the C ABI with host buffers ------------------------------------
     md = sc["medium"]
@@ -289,17 +365,20 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms_w,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "paths_per_gpu": n_paths, "form": "wavefront",
+            "config": {"workload": WORKLOAD if not args.paths else WORKLOAD + f" ({n_paths} paths)",
+                       "paths_per_gpu": n_paths, "form": "wavefront",
                        "regroup": args.regroup,
                        "l2": "flushed between timed steps (256 MB write)",
                        "events_per_step": ev_w, "parallelism": f"paths sharded over {world} GPU(s)"},
             "paths_per_s": paths_per_s,
             "forms": {
-                "wavefront": {"events_per_s": value, "ms_per_step": step_ms_w},
+                "wavefront": {"events_per_s": value, "ms_per_step": step_ms_w,
+                              "ms_steps": [round(v, 3) for v in ms_w]},
                 "plain": {"events_per_s": plain_value, "ms_per_step": step_ms_p,
-                          "steps": len(ms_p)},
+                          "steps": len(ms_p), "ms_steps": [round(v, 3) for v in ms_p]},
                 "speedup_vs_plain": value / plain_value,
                 "equal_rmse": "same estimator and the same path ids in both forms",
+                "batched": batched,
             },
             "counters_per_step": cnt_w,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
@@ -308,7 +387,8 @@ def run_ours(args):
                                  f" x 128 lanes x {sm_max:.0f} MHz"},
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps + len(ms_p),
+            "gpu_launches": args.steps + len(ms_p)
+            + (0 if batched is None else batched["steps"] + batched["plain_launches"]),
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -321,15 +401,19 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--regroup", type=int, default=0)
-    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--plain-steps", type=int, default=5)
+    ap.add_argument("--paths", type=int, default=0,
+                    help="override the path count (small profiling cases only)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-paths", type=int, default=1 << 17)
     ap.add_argument("--ref-paths", type=int, default=1 << 16)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

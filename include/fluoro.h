@@ -181,6 +181,28 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream);
 int flr_read_tallies(flr_ctx *ctx, double *face, double *absorbed, double *emitted,
                      uint64_t *counters, void *stream);
 
+/* Batched persistent form (independent media in one launch). flr_batch_prepare validates n_media
+ * media (each as flr_set_medium would; source rows via source_first/source_count, at most 8 lines
+ * per medium; the sensor is not used), copies their grids into one library-owned interleaved
+ * arena, builds per-medium spectral tables and majorants, splits host n_paths [n_media] into a
+ * device work queue of path-id chunks ordered by expected path length, and captures the launch
+ * (tally reset + one persistent kernel) in a CUDA graph. Medium m draws its random numbers under
+ * the key (p->seed, p->medium_id + m), so it traces exactly the paths a single-scene render of that
+ * medium with medium_id = p->medium_id + m traces. Synchronises the device. */
+int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const uint64_t *n_paths,
+                      const flr_params *p);
+/* Launch the prepared batch (graph replay) on `stream`; per-medium tallies are cleared first. */
+int flr_batch_launch(flr_ctx *ctx, void *stream);
+/* Synchronise `stream` and copy per-medium tallies, each divided by that medium's path count:
+ * host face [M][2][6][n_bins]; host absorbed [M][FLR_MAX_DYES_PER_MEDIUM+1][n_bins] (rows
+ * 0..D_m-1 dyes, row D_m background); host emitted [M][FLR_MAX_DYES_PER_MEDIUM][n_bins]; host
+ * counters [FLR_NCOUNTERS] summed over media. Any output may be NULL. */
+int flr_batch_read(flr_ctx *ctx, double *face, double *absorbed, double *emitted,
+                   uint64_t *counters, void *stream);
+/* flr_batch_prepare followed by flr_batch_launch. */
+int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const uint64_t *n_paths,
+                     const flr_params *p, void *stream);
+
 /* Synchronise the device and report the device error word (FLR_OK if clean). */
 int flr_status(flr_ctx *ctx);
 const char *flr_last_error(flr_ctx *ctx);

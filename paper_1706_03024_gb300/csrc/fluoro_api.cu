@@ -43,6 +43,30 @@ struct flr_ctx {
     unsigned int *d_scratch = nullptr;  // [0] max bits, [1] flag, [2] any
     uint64_t paths_since_clear = 0;
     std::vector<float> h_tables;
+    // batched form
+    struct Batch {
+        int n_media = 0;
+        std::vector<uint64_t> n_paths;
+        std::vector<int> n_dyes;
+        float4 *d_arena = nullptr;
+        size_t arena_cap = 0;
+        flr::MediumDev *d_media = nullptr;
+        size_t media_cap = 0;
+        flr::ChunkDev *d_chunks = nullptr;
+        size_t chunks_cap = 0;
+        float *d_tables = nullptr;
+        size_t tables_cap = 0;
+        unsigned long long *d_tallies = nullptr;
+        size_t tallies_cap = 0;
+        unsigned long long *d_counters = nullptr;
+        unsigned long long *d_head = nullptr;
+        unsigned int *d_max = nullptr;
+        size_t max_cap = 0;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        bool ready = false;
+    } batch;
+    cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
@@ -108,23 +132,26 @@ bool medium_has_grid(const flr_medium &m)
     return false;
 }
 
-// Per-medium spectral tables (host fp64, stored fp32).
-void build_tables(flr_ctx *ctx)
+// Per-medium spectral tables (host fp64, stored fp32): absorption per unit concentration, the
+// emission CDF of Eq. 10 (running sum over the total, rounded to fp32, last entry 1), the per-bin
+// majorant max_x sigma_t(x, lambda) (rounded up, with a 1e-6 relative margin for the kernels' fp32
+// sums) and QY.
+void build_medium_tables(const flr_ctx *ctx, const flr_medium &m, const float *cmax, float smax,
+                         float *out)
 {
     const int B = ctx->B;
-    const flr_medium &m = ctx->medium;
-    ctx->h_tables.assign(tab_size(B), 0.0f);
-    float *sig = ctx->h_tables.data() + tab_sig_a(B);
-    float *cdf = ctx->h_tables.data() + tab_cdf(B);
-    float *maj = ctx->h_tables.data() + tab_majorant(B);
-    float *qy = ctx->h_tables.data() + tab_qy(B);
+    std::fill(out, out + tab_size(B), 0.0f);
+    float *sig = out + tab_sig_a(B);
+    float *cdf = out + tab_cdf(B);
+    float *maj = out + tab_majorant(B);
+    float *qy = out + tab_qy(B);
     for (int b = 0; b < B; ++b) {
-        double mj = (double)ctx->smax * ((double)m.sigma_s + (double)m.sigma_a0);
+        double mj = (double)smax * ((double)m.sigma_s + (double)m.sigma_a0);
         for (int d = 0; d < m.n_dyes; ++d) {
             const int id = m.dye_ids[d];
             const double s = (double)ctx->eps[id] * (double)ctx->abs_shape[(size_t)id * B + b];
             sig[d * B + b] = (float)s;
-            mj += s * (double)ctx->cmax[d];
+            mj += s * (double)cmax[d];
         }
         maj[b] = mj > 0.0 ? round_up_f32(mj * (1.0 + 1e-6)) : 0.0f;
     }
@@ -143,28 +170,16 @@ void build_tables(flr_ctx *ctx)
     }
 }
 
-int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film)
+void build_tables(flr_ctx *ctx)
 {
-    const flr_medium &m = ctx->medium;
-    std::memset(&S, 0, sizeof(S));
-    S.B = ctx->B;
-    S.D = m.n_dyes;
-    for (int k = 0; k < 3; ++k) {
-        S.lo[k] = m.lo[k];
-        S.hi[k] = m.hi[k];
-        S.dims[k] = std::max(m.dims[k], 1);
-        S.vox_scale[k] = (float)((double)S.dims[k] / ((double)m.hi[k] - (double)m.lo[k]));
-    }
-    S.grid = medium_has_grid(m) ? ctx->d_grid : nullptr;
-    S.solvent = m.solvent;
-    S.homogeneous = (S.grid == nullptr && S.solvent == nullptr) ? 1 : 0;
-    for (int d = 0; d < MAXD; ++d) S.conc_uniform[d] = d < m.n_dyes ? m.conc_uniform[d] : 0.0f;
-    S.sigma_s = m.sigma_s;
-    S.sigma_a0 = m.sigma_a0;
-    S.wall_mask = m.wall_mask;
-    S.wall_albedo = m.wall_albedo;
-    S.tables = ctx->d_tables;
-    // emitters: every line of the medium's sources, chosen in proportion to power
+    ctx->h_tables.assign(tab_size(ctx->B), 0.0f);
+    build_medium_tables(ctx, ctx->medium, ctx->cmax, ctx->smax, ctx->h_tables.data());
+}
+
+// The spectral lines of a medium's sources, chosen in proportion to power (p(lambda_x), Eq. 12).
+int build_emitters(flr_ctx *ctx, const flr_medium &m, int max_lines, EmitterDev *em, float *em_cdf,
+                   int *n_out)
+{
     int first = m.source_first, count = m.source_count;
     if (count == 0) { first = 0; count = (int)ctx->sources.size(); }
     if (first < 0 || count < 0 || first + count > (int)ctx->sources.size() || count == 0)
@@ -174,8 +189,8 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film)
     for (int s = first; s < first + count; ++s) {
         const flr_source &src = ctx->sources[s];
         for (int l = 0; l < src.n_lines; ++l) {
-            if (n >= FLR_MAX_EMITTERS) return fail(ctx, FLR_ERR_ARG, "more than 32 source lines");
-            EmitterDev &e = S.em[n];
+            if (n >= max_lines) return fail(ctx, FLR_ERR_ARG, "too many source lines for one medium");
+            EmitterDev &e = em[n];
             for (int k = 0; k < 3; ++k) {
                 e.origin[k] = src.origin[k];
                 e.eu[k] = src.eu[k];
@@ -199,10 +214,38 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film)
     double run = 0.0;
     for (int k = 0; k < n; ++k) {
         run += pw[k];
-        S.em_cdf[k] = (float)(run / tot);
+        em_cdf[k] = (float)(run / tot);
     }
-    S.em_cdf[n - 1] = 1.0f;
-    S.n_emitters = n;
+    em_cdf[n - 1] = 1.0f;
+    *n_out = n;
+    return FLR_OK;
+}
+
+int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film)
+{
+    const flr_medium &m = ctx->medium;
+    std::memset(&S, 0, sizeof(S));
+    S.B = ctx->B;
+    S.D = m.n_dyes;
+    for (int k = 0; k < 3; ++k) {
+        S.lo[k] = m.lo[k];
+        S.hi[k] = m.hi[k];
+        S.dims[k] = std::max(m.dims[k], 1);
+        S.vox_scale[k] = (float)((double)S.dims[k] / ((double)m.hi[k] - (double)m.lo[k]));
+    }
+    S.grid = medium_has_grid(m) ? ctx->d_grid : nullptr;
+    S.solvent = m.solvent;
+    S.homogeneous = (S.grid == nullptr && S.solvent == nullptr) ? 1 : 0;
+    for (int d = 0; d < MAXD; ++d) S.conc_uniform[d] = d < m.n_dyes ? m.conc_uniform[d] : 0.0f;
+    S.sigma_s = m.sigma_s;
+    S.sigma_a0 = m.sigma_a0;
+    S.wall_mask = m.wall_mask;
+    S.wall_albedo = m.wall_albedo;
+    S.tables = ctx->d_tables;
+    int ne = 0;
+    const int rc = build_emitters(ctx, m, FLR_MAX_EMITTERS, S.em, S.em_cdf, &ne);
+    if (rc != FLR_OK) return rc;
+    S.n_emitters = ne;
     // sensor
     const flr_sensor &c = ctx->sensor;
     S.sensor_kind = (ctx->sensor_set && with_film) ? c.kind : FLR_SENSOR_NONE;
@@ -247,6 +290,38 @@ int prepare_tables(flr_ctx *ctx)
                                cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "upload spectral tables");
     ctx->tables_dirty = false;
+    return FLR_OK;
+}
+
+// Checks one medium against the context's spectrum and dye table (no device work).
+int validate_medium(flr_ctx *ctx, const flr_medium *m)
+{
+    if (!m) return fail(ctx, FLR_ERR_ARG, "medium: NULL");
+    if (ctx->B <= 0) return fail(ctx, FLR_ERR_STATE, "set the spectrum before the medium");
+    if (m->n_dyes < 0 || m->n_dyes > MAXD) return fail(ctx, FLR_ERR_ARG, "medium: 0..4 dyes");
+    for (int k = 0; k < 3; ++k)
+        if (!(std::isfinite(m->lo[k]) && std::isfinite(m->hi[k]) && m->hi[k] > m->lo[k]))
+            return fail(ctx, FLR_ERR_ARG, "medium: box must have hi > lo");
+    for (int d = 0; d < m->n_dyes; ++d) {
+        if (m->dye_ids[d] < 0 || m->dye_ids[d] >= ctx->n_dyes)
+            return fail(ctx, FLR_ERR_ARG, "medium: dye id outside the dye table");
+        if (!m->conc[d] && !(std::isfinite(m->conc_uniform[d]) && m->conc_uniform[d] >= 0.0f))
+            return fail(ctx, FLR_ERR_ARG, "medium: uniform concentration must be finite and >= 0");
+    }
+    if (!(std::isfinite(m->sigma_s) && m->sigma_s >= 0.0f && std::isfinite(m->sigma_a0) && m->sigma_a0 >= 0.0f))
+        return fail(ctx, FLR_ERR_ARG, "medium: sigma_s and sigma_a0 must be finite and >= 0");
+    if (m->wall_mask < 0 || m->wall_mask > 63 || !(m->wall_albedo >= 0.0f && m->wall_albedo <= 1.0f))
+        return fail(ctx, FLR_ERR_ARG, "medium: wall mask 0..63 and albedo in [0,1]");
+    const bool grids = medium_has_grid(*m) || m->solvent;
+    if (grids) {
+        for (int k = 0; k < 3; ++k)
+            if (m->dims[k] < 1 || m->dims[k] > 4096) return fail(ctx, FLR_ERR_ARG, "medium: dims 1..4096");
+        for (int d = 0; d < m->n_dyes; ++d)
+            if (m->conc[d] && !is_device_pointer(m->conc[d]))
+                return fail(ctx, FLR_ERR_ARG, "medium: concentration grids must be device memory");
+        if (m->solvent && !is_device_pointer(m->solvent))
+            return fail(ctx, FLR_ERR_ARG, "medium: solvent mask must be device memory");
+    }
     return FLR_OK;
 }
 
@@ -295,6 +370,18 @@ void flr_destroy(flr_ctx *ctx)
     cudaFree(ctx->d_work);
     cudaFree(ctx->d_scratch);
     cudaFree(ctx->d_grid);
+    auto &bt = ctx->batch;
+    if (bt.exec) cudaGraphExecDestroy(bt.exec);
+    if (bt.graph) cudaGraphDestroy(bt.graph);
+    cudaFree(bt.d_arena);
+    cudaFree(bt.d_media);
+    cudaFree(bt.d_chunks);
+    cudaFree(bt.d_tables);
+    cudaFree(bt.d_tallies);
+    cudaFree(bt.d_counters);
+    cudaFree(bt.d_head);
+    cudaFree(bt.d_max);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
 }
 
@@ -382,32 +469,9 @@ int flr_set_sources(flr_ctx *ctx, int n, const flr_source *s)
 int flr_set_medium(flr_ctx *ctx, const flr_medium *m)
 {
     if (!ctx) return FLR_ERR_ARG;
-    if (!m) return fail(ctx, FLR_ERR_ARG, "medium: NULL");
-    if (ctx->B <= 0) return fail(ctx, FLR_ERR_STATE, "set the spectrum before the medium");
-    if (m->n_dyes < 0 || m->n_dyes > MAXD) return fail(ctx, FLR_ERR_ARG, "medium: 0..4 dyes");
-    for (int k = 0; k < 3; ++k)
-        if (!(std::isfinite(m->lo[k]) && std::isfinite(m->hi[k]) && m->hi[k] > m->lo[k]))
-            return fail(ctx, FLR_ERR_ARG, "medium: box must have hi > lo");
-    for (int d = 0; d < m->n_dyes; ++d) {
-        if (m->dye_ids[d] < 0 || m->dye_ids[d] >= ctx->n_dyes)
-            return fail(ctx, FLR_ERR_ARG, "medium: dye id outside the dye table");
-        if (!m->conc[d] && !(std::isfinite(m->conc_uniform[d]) && m->conc_uniform[d] >= 0.0f))
-            return fail(ctx, FLR_ERR_ARG, "medium: uniform concentration must be finite and >= 0");
-    }
-    if (!(std::isfinite(m->sigma_s) && m->sigma_s >= 0.0f && std::isfinite(m->sigma_a0) && m->sigma_a0 >= 0.0f))
-        return fail(ctx, FLR_ERR_ARG, "medium: sigma_s and sigma_a0 must be finite and >= 0");
-    if (m->wall_mask < 0 || m->wall_mask > 63 || !(m->wall_albedo >= 0.0f && m->wall_albedo <= 1.0f))
-        return fail(ctx, FLR_ERR_ARG, "medium: wall mask 0..63 and albedo in [0,1]");
+    int vrc = validate_medium(ctx, m);
+    if (vrc != FLR_OK) return vrc;
     const bool grids = medium_has_grid(*m) || m->solvent;
-    if (grids) {
-        for (int k = 0; k < 3; ++k)
-            if (m->dims[k] < 1 || m->dims[k] > 4096) return fail(ctx, FLR_ERR_ARG, "medium: dims 1..4096");
-        for (int d = 0; d < m->n_dyes; ++d)
-            if (m->conc[d] && !is_device_pointer(m->conc[d]))
-                return fail(ctx, FLR_ERR_ARG, "medium: concentration grids must be device memory");
-        if (m->solvent && !is_device_pointer(m->solvent))
-            return fail(ctx, FLR_ERR_ARG, "medium: solvent mask must be device memory");
-    }
     DeviceGuard g(ctx->device);
     flr_medium mm = *m;
     if (!grids) mm.dims[0] = mm.dims[1] = mm.dims[2] = 1;
@@ -622,6 +686,236 @@ int flr_debug_sample_emission(flr_ctx *ctx, int dye, const float *u, int64_t n, 
     S.tables = ctx->d_tables;
     cudaError_t e = launch_sample_emission(S, dye, u, n, out, (cudaStream_t)stream);
     return e == cudaSuccess ? FLR_OK : cuda_fail(ctx, e, "sample emission");
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched persistent form.
+
+static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem, const char *what)
+{
+    if (need <= *cap && *ptr) return FLR_OK;
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(ptr, std::max<size_t>(need, 1) * elem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    *cap = std::max<size_t>(need, 1);
+    return FLR_OK;
+}
+
+int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const uint64_t *n_paths,
+                      const flr_params *p)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (n_media < 1 || n_media > 65536 || !media || !n_paths || !p)
+        return fail(ctx, FLR_ERR_ARG, "batch: need 1..65536 media, path counts and params");
+    if (ctx->sources.empty()) return fail(ctx, FLR_ERR_STATE, "batch: no sources");
+    if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || (p->block_size & 31)))
+        return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
+    if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
+        return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
+    const int B = ctx->B;
+    std::vector<long long> off(n_media, -1), nv(n_media, 0);
+    long long arena = 0;
+    for (int m = 0; m < n_media; ++m) {
+        const int rc = validate_medium(ctx, &media[m]);
+        if (rc != FLR_OK) return rc;
+        if (n_paths[m] > 0xFFFFFFFFull * 64ull) return fail(ctx, FLR_ERR_ARG, "batch: too many paths");
+        const bool grids = medium_has_grid(media[m]) || media[m].solvent;
+        nv[m] = grids ? nvox(media[m]) : 1;
+        if (medium_has_grid(media[m])) {
+            off[m] = arena;
+            arena += nv[m];
+        }
+    }
+    DeviceGuard g(ctx->device);
+    auto &bt = ctx->batch;
+    bt.ready = false;
+    int rc = grow(ctx, (void **)&bt.d_arena, &bt.arena_cap, (size_t)arena, sizeof(float4), "batch arena");
+    if (rc == FLR_OK) rc = grow(ctx, (void **)&bt.d_max, &bt.max_cap, (size_t)n_media * 8, sizeof(unsigned), "batch maxima");
+    if (rc == FLR_OK) rc = grow(ctx, (void **)&bt.d_tables, &bt.tables_cap, (size_t)n_media * tab_size(B), sizeof(float), "batch tables");
+    if (rc == FLR_OK) rc = grow(ctx, (void **)&bt.d_tallies, &bt.tallies_cap, (size_t)n_media * tal_size(B), sizeof(unsigned long long), "batch tallies");
+    if (rc == FLR_OK) rc = grow(ctx, (void **)&bt.d_media, &bt.media_cap, (size_t)n_media, sizeof(MediumDev), "batch media");
+    if (rc != FLR_OK) return rc;
+    if (!bt.d_counters) {
+        cudaError_t e = cudaMalloc(&bt.d_counters, sizeof(unsigned long long) * FLR_NCOUNTERS);
+        if (e == cudaSuccess) e = cudaMalloc(&bt.d_head, sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch counters");
+    }
+    // pack grids, reduce maxima (slots [m][0..3] dyes, [m][4] bad-value flag, [m][5] solvent any)
+    cudaError_t e = cudaMemset(bt.d_max, 0, sizeof(unsigned) * (size_t)n_media * 8);
+    for (int m = 0; m < n_media && e == cudaSuccess; ++m) {
+        const flr_medium &md = media[m];
+        if (off[m] >= 0) e = launch_pack_grid(md.conc, md.conc_uniform, md.n_dyes, nv[m], bt.d_arena + off[m], 0);
+        for (int d = 0; d < md.n_dyes && e == cudaSuccess; ++d)
+            if (md.conc[d])
+                e = launch_grid_max(md.conc[d], nv[m], bt.d_max + (size_t)m * 8 + d, (int *)(bt.d_max + (size_t)m * 8 + 4), 0);
+        if (e == cudaSuccess && md.solvent) e = launch_solvent_any(md.solvent, nv[m], bt.d_max + (size_t)m * 8 + 5, 0);
+    }
+    std::vector<unsigned> hmax((size_t)n_media * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(hmax.data(), bt.d_max, sizeof(unsigned) * hmax.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch grid preparation");
+    // tables, media descriptors, chunk queue
+    std::vector<float> htab((size_t)n_media * tab_size(B));
+    std::vector<MediumDev> hmed(n_media);
+    struct Item { double cost; ChunkDev c; };
+    std::vector<Item> items;
+    uint64_t total = 0;
+    for (int m = 0; m < n_media; ++m) total += n_paths[m];
+    const int block = p->block_size > 0 ? p->block_size : trace_block_default();
+    const long long warps = (long long)batch_occupancy_blocks_per_sm(block) * device_sms() * (block / 32);
+    const uint64_t chunk = std::min<uint64_t>(65536, std::max<uint64_t>(256, total / (uint64_t)std::max<long long>(warps * 4, 1)));
+    bt.n_paths.assign(n_paths, n_paths + n_media);
+    bt.n_dyes.resize(n_media);
+    for (int m = 0; m < n_media; ++m) {
+        const flr_medium &md = media[m];
+        if (hmax[(size_t)m * 8 + 4]) return fail(ctx, FLR_ERR_ARG, "batch: a grid has negative or non-finite values");
+        float cmax[MAXD] = {0, 0, 0, 0};
+        for (int d = 0; d < md.n_dyes; ++d) {
+            if (md.conc[d]) std::memcpy(&cmax[d], &hmax[(size_t)m * 8 + d], sizeof(float));
+            else cmax[d] = md.conc_uniform[d];
+        }
+        const float smax = md.solvent ? (hmax[(size_t)m * 8 + 5] ? 1.0f : 0.0f) : 1.0f;
+        float *tab = htab.data() + (size_t)m * tab_size(B);
+        build_medium_tables(ctx, md, cmax, smax, tab);
+        MediumDev &o = hmed[m];
+        std::memset(&o, 0, sizeof(o));
+        for (int k = 0; k < 3; ++k) {
+            o.lo[k] = md.lo[k];
+            o.hi[k] = md.hi[k];
+            o.dims[k] = (medium_has_grid(md) || md.solvent) ? md.dims[k] : 1;
+            o.vox_scale[k] = (float)((double)o.dims[k] / ((double)md.hi[k] - (double)md.lo[k]));
+        }
+        o.grid = off[m] >= 0 ? bt.d_arena + off[m] : nullptr;
+        o.solvent = md.solvent;
+        o.homogeneous = (o.grid == nullptr && o.solvent == nullptr) ? 1 : 0;
+        o.D = md.n_dyes;
+        for (int d = 0; d < MAXD; ++d) o.conc_uniform[d] = d < md.n_dyes ? md.conc_uniform[d] : 0.0f;
+        o.sigma_s = md.sigma_s;
+        o.sigma_a0 = md.sigma_a0;
+        o.wall_mask = md.wall_mask;
+        o.wall_albedo = md.wall_albedo;
+        o.tables = bt.d_tables + (size_t)m * tab_size(B);
+        o.tallies = bt.d_tallies + (size_t)m * tal_size(B);
+        o.key1 = p->medium_id + (uint32_t)m;
+        int ne = 0;
+        rc = build_emitters(ctx, md, BATCH_MAX_LINES, o.em, o.em_cdf, &ne);
+        if (rc != FLR_OK) return rc;
+        o.n_emitters = ne;
+        bt.n_dyes[m] = md.n_dyes;
+        // expected real events per path at the first line: albedo-limited or diffusion-limited
+        const int b0 = o.em[0].bin;
+        const double maj = tab[tab_majorant(B) + b0];
+        const double a = maj > 0.0 ? std::min(0.9999, (double)md.sigma_s / maj) : 0.0;
+        double L = 1e30;
+        for (int k = 0; k < 3; ++k) L = std::min(L, (double)md.hi[k] - md.lo[k]);
+        const double cost = std::min(1.0 / (1.0 - a), 1.0 + maj * L * maj * L) * (1.0 + 0.02 * maj * L);
+        for (uint64_t s0 = 0; s0 < n_paths[m]; s0 += chunk) {
+            ChunkDev c;
+            c.medium = m;
+            c.start = p->path_offset + s0;
+            c.count = (uint32_t)std::min<uint64_t>(chunk, n_paths[m] - s0);
+            items.push_back({cost, c});
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) { return x.cost > y.cost; });
+    std::vector<ChunkDev> hch(items.size());
+    for (size_t i = 0; i < items.size(); ++i) hch[i] = items[i].c;
+    rc = grow(ctx, (void **)&bt.d_chunks, &bt.chunks_cap, hch.size(), sizeof(ChunkDev), "batch queue");
+    if (rc != FLR_OK) return rc;
+    e = cudaMemcpy(bt.d_tables, htab.data(), sizeof(float) * htab.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt.d_media, hmed.data(), sizeof(MediumDev) * hmed.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !hch.empty()) e = cudaMemcpy(bt.d_chunks, hch.data(), sizeof(ChunkDev) * hch.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
+    // capture tally reset + persistent kernel in a CUDA graph (replayed by flr_batch_launch)
+    if (!ctx->cap_stream) {
+        e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "capture stream");
+    }
+    if (bt.exec) { cudaGraphExecDestroy(bt.exec); bt.exec = nullptr; }
+    if (bt.graph) { cudaGraphDestroy(bt.graph); bt.graph = nullptr; }
+    BatchDev Bt;
+    Bt.B = B;
+    Bt.n_chunks = (int)hch.size();
+    Bt.media = bt.d_media;
+    Bt.chunks = bt.d_chunks;
+    Bt.head = bt.d_head;
+    RunDev R;
+    std::memset(&R, 0, sizeof(R));
+    R.n_paths = total;
+    R.path_offset = p->path_offset;
+    R.seed = p->seed;
+    R.medium_id = p->medium_id;
+    R.n_rr = p->n_rr;
+    R.max_inelastic = p->max_inelastic;
+    R.analog = p->analog;
+    R.max_events = p->max_events;
+    R.max_steps = p->max_steps;
+    R.counters = bt.d_counters;
+    R.error_word = ctx->d_error;
+    cudaStream_t cs = ctx->cap_stream;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = cudaMemsetAsync(bt.d_tallies, 0, sizeof(unsigned long long) * (size_t)n_media * tal_size(B), cs);
+        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(bt.d_counters, 0, sizeof(unsigned long long) * FLR_NCOUNTERS, cs);
+        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(bt.d_head, 0, sizeof(unsigned long long), cs);
+        if (e1 == cudaSuccess && !hch.empty()) e1 = launch_batch(Bt, R, p->block_size, p->blocks_per_sm, cs);
+        e = cudaStreamEndCapture(cs, &bt.graph);
+        if (e1 != cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bt.exec, bt.graph, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "capture the batched launch");
+    bt.n_media = n_media;
+    bt.ready = true;
+    return FLR_OK;
+}
+
+int flr_batch_launch(flr_ctx *ctx, void *stream)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (!ctx->batch.ready) return fail(ctx, FLR_ERR_STATE, "batch: prepare it first");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaGraphLaunch(ctx->batch.exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? FLR_OK : cuda_fail(ctx, e, "launch the batch graph");
+}
+
+int flr_batch_read(flr_ctx *ctx, double *face, double *absorbed, double *emitted, uint64_t *counters,
+                   void *stream)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    auto &bt = ctx->batch;
+    if (!bt.ready) return fail(ctx, FLR_ERR_STATE, "batch: prepare it first");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before reading batch tallies");
+    const int B = ctx->B, M = bt.n_media;
+    std::vector<unsigned long long> t((size_t)M * tal_size(B));
+    unsigned long long c[FLR_NCOUNTERS];
+    e = cudaMemcpy(t.data(), bt.d_tallies, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(c, bt.d_counters, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read batch tallies");
+    for (int m = 0; m < M; ++m) {
+        const unsigned long long *tm = t.data() + (size_t)m * tal_size(B);
+        const double inv = bt.n_paths[m] ? 1.0 / ((double)bt.n_paths[m] * TALLY_ONE) : 0.0;
+        if (face)
+            for (int i = 0; i < 12 * B; ++i) face[(size_t)m * 12 * B + i] = (double)tm[tal_face(B) + i] * inv;
+        if (absorbed)
+            for (int i = 0; i < (MAXD + 1) * B; ++i)
+                absorbed[(size_t)m * (MAXD + 1) * B + i] = (double)tm[tal_absorbed(B) + i] * inv;
+        if (emitted)
+            for (int i = 0; i < MAXD * B; ++i) emitted[(size_t)m * MAXD * B + i] = (double)tm[tal_emitted(B) + i] * inv;
+    }
+    if (counters)
+        for (int k = 0; k < FLR_NCOUNTERS; ++k) counters[k] = c[k];
+    return FLR_OK;
+}
+
+int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const uint64_t *n_paths,
+                     const flr_params *p, void *stream)
+{
+    int rc = flr_batch_prepare(ctx, n_media, media, n_paths, p);
+    if (rc != FLR_OK) return rc;
+    return flr_batch_launch(ctx, stream);
 }
 
 }  // extern "C"

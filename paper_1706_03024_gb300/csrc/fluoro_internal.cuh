@@ -75,7 +75,45 @@ struct RunDev {
     int regroup;                       // wavefront: tracking steps between connection flushes
 };
 
+// One medium of a batched launch (global memory; read per lane through the read-only path).
+constexpr int BATCH_MAX_LINES = 8;
+struct MediumDev {
+    float lo[3], hi[3], vox_scale[3];
+    int dims[3];
+    int homogeneous, D;
+    const float4 *grid;                // interleaved concentrations inside the batch arena
+    const uint8_t *solvent;
+    float conc_uniform[MAXD];
+    float sigma_s, sigma_a0;
+    int wall_mask;
+    float wall_albedo;
+    const float *tables;               // tab_size(B) floats
+    unsigned long long *tallies;       // tal_size(B) fixed-point tallies of this medium
+    uint32_t key1;                     // Philox key word 1 (the medium id)
+    int n_emitters;
+    float em_cdf[BATCH_MAX_LINES];
+    EmitterDev em[BATCH_MAX_LINES];
+};
+
+// A work item of the batched queue: `count` consecutive path ids of one medium.
+struct ChunkDev {
+    int medium;
+    uint32_t count;
+    unsigned long long start;
+};
+
+struct BatchDev {
+    int B;
+    int n_chunks;
+    const MediumDev *media;
+    const ChunkDev *chunks;
+    unsigned long long *head;          // next chunk (device counter)
+};
+
 // Host-side launchers (fluoro_kernels.cu).
+cudaError_t launch_batch(const BatchDev &Bt, const RunDev &R, int block, int blocks_per_sm,
+                         cudaStream_t st);
+int batch_occupancy_blocks_per_sm(int block);
 cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block, int blocks_per_sm,
                          cudaStream_t st);
 cudaError_t launch_grid_max(const float *g, long long n, unsigned int *out_bits, int *neg_flag,
@@ -88,6 +126,7 @@ cudaError_t launch_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, l
 cudaError_t launch_sample_emission(const SceneDev &S, int dye, const float *u, long long n,
                                    int32_t *out, cudaStream_t st);
 int trace_block_default();
+int device_sms();
 int trace_smem_bytes(int B, int form, int block);
 int occupancy_blocks_per_sm(int B, int form, int block);
 

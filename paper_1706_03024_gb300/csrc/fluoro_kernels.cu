@@ -84,55 +84,151 @@ __device__ __forceinline__ void tally_add(const Smem &sm, int idx, float w)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Medium accessors. The tracking code is written once against this interface:
+//   MedS  single scene: geometry from the kernel parameters (constant bank), spectral tables and
+//         tallies in shared memory.
+//   MedB  one medium of a batched launch, per lane: fields read from global memory through the
+//         read-only path, tables in global memory (L1-resident), tallies in global memory.
+struct MedS {
+    const SceneDev &S;
+    const Smem &sm;
+    __device__ __forceinline__ int B() const { return S.B; }
+    __device__ __forceinline__ int D() const { return S.D; }
+    __device__ __forceinline__ float lo(int k) const { return S.lo[k]; }
+    __device__ __forceinline__ float hi(int k) const { return S.hi[k]; }
+    __device__ __forceinline__ float vox_scale(int k) const { return S.vox_scale[k]; }
+    __device__ __forceinline__ int dims(int k) const { return S.dims[k]; }
+    __device__ __forceinline__ bool homogeneous() const { return S.homogeneous != 0; }
+    __device__ __forceinline__ const float4 *grid() const { return S.grid; }
+    __device__ __forceinline__ const uint8_t *solvent() const { return S.solvent; }
+    __device__ __forceinline__ float4 conc_uniform() const
+    {
+        return make_float4(S.conc_uniform[0], S.conc_uniform[1], S.conc_uniform[2], S.conc_uniform[3]);
+    }
+    __device__ __forceinline__ float sigma_s() const { return S.sigma_s; }
+    __device__ __forceinline__ float sigma_a0() const { return S.sigma_a0; }
+    __device__ __forceinline__ int wall_mask() const { return S.wall_mask; }
+    __device__ __forceinline__ float wall_albedo() const { return S.wall_albedo; }
+    __device__ __forceinline__ float sig_a(int d, int b) const { return sm.sig_a[d * S.B + b]; }
+    __device__ __forceinline__ float maj(int b) const { return sm.maj[b]; }
+    __device__ __forceinline__ float qy(int d) const { return sm.qy[d]; }
+    __device__ __forceinline__ const float *cdf(int d) const { return sm.cdf + d * S.B; }
+    __device__ __forceinline__ void tally(int idx, float w) const { tally_add(sm, idx, w); }
+    __device__ __forceinline__ bool sensor() const { return S.sensor_kind != FLR_SENSOR_NONE; }
+    __device__ __forceinline__ int n_emitters() const { return S.n_emitters; }
+    __device__ __forceinline__ float em_cdf(int k) const { return S.em_cdf[k]; }
+    __device__ __forceinline__ const EmitterDev &em(int k) const { return S.em[k]; }
+    __device__ __forceinline__ uint32_t key1(const RunDev &R) const { return R.medium_id; }
+};
+
+__device__ __forceinline__ void tally_add_global(unsigned long long *t, int idx, float w)
+{
+    const unsigned long long fx = __float2ull_rn(w * 16777216.0f);
+    if (fx) atomicAdd(&t[idx], fx);
+}
+
+struct MedB {
+    const MediumDev *__restrict__ md;
+    int B_;
+    __device__ __forceinline__ int B() const { return B_; }
+    __device__ __forceinline__ int D() const { return __ldg(&md->D); }
+    __device__ __forceinline__ float lo(int k) const { return __ldg(&md->lo[k]); }
+    __device__ __forceinline__ float hi(int k) const { return __ldg(&md->hi[k]); }
+    __device__ __forceinline__ float vox_scale(int k) const { return __ldg(&md->vox_scale[k]); }
+    __device__ __forceinline__ int dims(int k) const { return __ldg(&md->dims[k]); }
+    __device__ __forceinline__ bool homogeneous() const { return __ldg(&md->homogeneous) != 0; }
+    __device__ __forceinline__ const float4 *grid() const
+    {
+        return reinterpret_cast<const float4 *>(__ldg(reinterpret_cast<const unsigned long long *>(&md->grid)));
+    }
+    __device__ __forceinline__ const uint8_t *solvent() const
+    {
+        return reinterpret_cast<const uint8_t *>(__ldg(reinterpret_cast<const unsigned long long *>(&md->solvent)));
+    }
+    __device__ __forceinline__ float4 conc_uniform() const
+    {
+        return __ldg(reinterpret_cast<const float4 *>(&md->conc_uniform[0]));
+    }
+    __device__ __forceinline__ float sigma_s() const { return __ldg(&md->sigma_s); }
+    __device__ __forceinline__ float sigma_a0() const { return __ldg(&md->sigma_a0); }
+    __device__ __forceinline__ int wall_mask() const { return __ldg(&md->wall_mask); }
+    __device__ __forceinline__ float wall_albedo() const { return __ldg(&md->wall_albedo); }
+    __device__ __forceinline__ const float *tables() const
+    {
+        return reinterpret_cast<const float *>(__ldg(reinterpret_cast<const unsigned long long *>(&md->tables)));
+    }
+    __device__ __forceinline__ float sig_a(int d, int b) const { return __ldg(tables() + tab_sig_a(B_) + d * B_ + b); }
+    __device__ __forceinline__ float maj(int b) const { return __ldg(tables() + tab_majorant(B_) + b); }
+    __device__ __forceinline__ float qy(int d) const { return __ldg(tables() + tab_qy(B_) + d); }
+    __device__ __forceinline__ const float *cdf(int d) const { return tables() + tab_cdf(B_) + d * B_; }
+    __device__ __forceinline__ void tally(int idx, float w) const
+    {
+        tally_add_global(reinterpret_cast<unsigned long long *>(
+                             __ldg(reinterpret_cast<const unsigned long long *>(&md->tallies))),
+                         idx, w);
+    }
+    __device__ __forceinline__ bool sensor() const { return false; }
+    __device__ __forceinline__ int n_emitters() const { return __ldg(&md->n_emitters); }
+    __device__ __forceinline__ float em_cdf(int k) const { return __ldg(&md->em_cdf[k]); }
+    __device__ __forceinline__ const EmitterDev &em(int k) const { return md->em[k]; }
+    __device__ __forceinline__ uint32_t key1(const RunDev &) const { return __ldg(&md->key1); }
+};
+
+// ---------------------------------------------------------------------------------------------
 // Medium (Sec. 4.1): sigma_t = s(x)(sigma_s + sigma_a0) + sum_d sig_a[d][b] c_d(x), nearest voxel.
 struct Coeffs {
     float scat, bg, total;
     float dye[MAXD];
 };
 
-__device__ __forceinline__ int voxel_of(const SceneDev &S, float3 x)
+template <class M>
+__device__ __forceinline__ int voxel_of(const M &m, float3 x)
 {
-    int ix = __float2int_rd((x.x - S.lo[0]) * S.vox_scale[0]);
-    int iy = __float2int_rd((x.y - S.lo[1]) * S.vox_scale[1]);
-    int iz = __float2int_rd((x.z - S.lo[2]) * S.vox_scale[2]);
-    ix = min(max(ix, 0), S.dims[0] - 1);
-    iy = min(max(iy, 0), S.dims[1] - 1);
-    iz = min(max(iz, 0), S.dims[2] - 1);
-    return (iz * S.dims[1] + iy) * S.dims[0] + ix;
+    int ix = __float2int_rd((x.x - m.lo(0)) * m.vox_scale(0));
+    int iy = __float2int_rd((x.y - m.lo(1)) * m.vox_scale(1));
+    int iz = __float2int_rd((x.z - m.lo(2)) * m.vox_scale(2));
+    ix = min(max(ix, 0), m.dims(0) - 1);
+    iy = min(max(iy, 0), m.dims(1) - 1);
+    iz = min(max(iz, 0), m.dims(2) - 1);
+    return (iz * m.dims(1) + iy) * m.dims(0) + ix;
 }
 
-__device__ __forceinline__ Coeffs coeffs_at(const SceneDev &S, const Smem &sm, float3 x, int b)
+template <class M>
+__device__ __forceinline__ Coeffs coeffs_at(const M &m, float3 x, int b)
 {
     float s = 1.0f;
-    float4 c = make_float4(S.conc_uniform[0], S.conc_uniform[1], S.conc_uniform[2], S.conc_uniform[3]);
-    if (!S.homogeneous) {
-        const int v = voxel_of(S, x);
-        if (S.grid) c = __ldg(&S.grid[v]);
-        if (S.solvent) s = __ldg(&S.solvent[v]) ? 1.0f : 0.0f;
+    float4 c = m.conc_uniform();
+    if (!m.homogeneous()) {
+        const int v = voxel_of(m, x);
+        const float4 *g = m.grid();
+        const uint8_t *sv = m.solvent();
+        if (g) c = __ldg(&g[v]);
+        if (sv) s = __ldg(&sv[v]) ? 1.0f : 0.0f;
     }
     Coeffs k;
-    k.scat = s * S.sigma_s;
-    k.bg = s * S.sigma_a0;
+    k.scat = s * m.sigma_s();
+    k.bg = s * m.sigma_a0();
     k.total = k.scat + k.bg;
     const float cc[4] = {c.x, c.y, c.z, c.w};
-    const int B = S.B;
+    const int D = m.D();
 #pragma unroll
     for (int d = 0; d < MAXD; ++d) {
-        k.dye[d] = (d < S.D) ? sm.sig_a[d * B + b] * cc[d] : 0.0f;
+        k.dye[d] = (d < D) ? m.sig_a(d, b) * cc[d] : 0.0f;
         k.total += k.dye[d];
     }
     return k;
 }
 
-__device__ __forceinline__ float sigma_t_at(const SceneDev &S, const Smem &sm, float3 x, int b)
+template <class M>
+__device__ __forceinline__ float sigma_t_at(const M &m, float3 x, int b)
 {
-    return coeffs_at(S, sm, x, b).total;
+    return coeffs_at(m, x, b).total;
 }
 
 // Distance to leave the box along w (inverse direction given), face index 0..5 or -1; ties to
 // the lowest face index.
-__device__ __forceinline__ float exit_distance(const SceneDev &S, float3 x, float3 w, float3 iw,
-                                               int &face)
+template <class M>
+__device__ __forceinline__ float exit_distance(const M &m, float3 x, float3 w, float3 iw, int &face)
 {
     float best = FLT_MAX;
     face = -1;
@@ -141,7 +237,7 @@ __device__ __forceinline__ float exit_distance(const SceneDev &S, float3 x, floa
     for (int k = 0; k < 3; ++k) {
         if (ws[k] == 0.0f) continue;
         const bool pos = ws[k] > 0.0f;
-        float t = ((pos ? S.hi[k] : S.lo[k]) - xs[k]) * is[k];
+        float t = ((pos ? m.hi(k) : m.lo(k)) - xs[k]) * is[k];
         t = fmaxf(t, 0.0f);
         if (t < best) { best = t; face = 2 * k + (pos ? 1 : 0); }
     }
@@ -232,9 +328,10 @@ __device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, cons
     } else {
         f = INV_4PI;
     }
+    const MedS m{S, sm};
     int face;
     const float3 idr = inv_dir(dir);
-    const float tl = exit_distance(S, x, dir, idr, face);
+    const float tl = exit_distance(m, x, dir, idr, face);
     if (face < 0) return;
     if (S.wall_mask & (1 << face)) return;
     if (S.sensor_kind == FLR_SENSOR_PINHOLE && tl * tl > r2) return;
@@ -243,7 +340,7 @@ __device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, cons
     float T = 1.0f;
     if (sb > 0.0f) {
         if (S.homogeneous) {
-            T = __expf(-sigma_t_at(S, sm, x, b) * tl);
+            T = __expf(-sigma_t_at(m, x, b) * tl);
         } else {
             const float isb = __frcp_rn(sb);
             float t = 0.0f;
@@ -259,7 +356,7 @@ __device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, cons
                 if (t >= tl) break;
                 rc.connect_steps++;
                 const float3 p = make_float3(x.x + t * dir.x, x.y + t * dir.y, x.z + t * dir.z);
-                T *= fmaxf(0.0f, 1.0f - sigma_t_at(S, sm, p, b) * isb);
+                T *= fmaxf(0.0f, 1.0f - sigma_t_at(m, p, b) * isb);
                 if (T < RT_RR_THRESHOLD) {
                     if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
                     const uint32_t q2 = j & 3u;
@@ -322,14 +419,17 @@ __device__ __forceinline__ void finish(const RunDev &R, Path &p)
     if (R.path_events) R.path_events[p.pid - R.path_offset] = (uint32_t)p.n_events;
 }
 
-__device__ __forceinline__ Conn spawn(const SceneDev &S, const RunDev &R, const Smem &sm,
-                                      uint64_t pid, Path &p)
+template <class M>
+__device__ __forceinline__ Conn spawn(const M &m, const RunDev &R, const Smem &sm, uint64_t pid,
+                                      Path &p)
 {
     cnt_add(sm, FLR_C_PATHS);
-    const U4 s0 = draw(R.seed, R.medium_id, pid, STEP_SPAWN, 0u);
+    const uint32_t key1 = m.key1(R);
+    const U4 s0 = draw(R.seed, key1, pid, STEP_SPAWN, 0u);
     int k = 0;
-    while (k < S.n_emitters - 1 && !(S.em_cdf[k] > s0.a)) ++k;
-    const EmitterDev &e = S.em[k];
+    const int ne = m.n_emitters();
+    while (k < ne - 1 && !(m.em_cdf(k) > s0.a)) ++k;
+    const EmitterDev &e = m.em(k);
     p.x = make_float3(e.origin[0] + s0.b * e.eu[0] + s0.c * e.ev[0],
                       e.origin[1] + s0.b * e.eu[1] + s0.c * e.ev[1],
                       e.origin[2] + s0.b * e.eu[2] + s0.c * e.ev[2]);
@@ -344,9 +444,9 @@ __device__ __forceinline__ Conn spawn(const SceneDev &S, const RunDev &R, const 
     Conn c;
     c.valid = false;
     if (e.kind == FLR_SOURCE_LAMBERTIAN) {
-        const U4 s1 = draw(R.seed, R.medium_id, pid, STEP_SPAWN, 1u);
+        const U4 s1 = draw(R.seed, key1, pid, STEP_SPAWN, 1u);
         p.w = cosine_dir(s0.d, s1.a, e.axis, e.sign);
-        if (S.sensor_kind != FLR_SENSOR_NONE) {
+        if (m.sensor()) {
             c = Conn{p.x, p.wt, p.bin, 2 * e.axis + (e.sign > 0.0f ? 1 : 0), pid, STEP_SPAWN, true};
         }
     } else {
@@ -358,8 +458,9 @@ __device__ __forceinline__ Conn spawn(const SceneDev &S, const RunDev &R, const 
 
 // One tracking step (null or real collision, wall bounce or escape). Returns the connection the
 // step asks for, if any.
-__device__ __forceinline__ Conn track_step(const SceneDev &S, const RunDev &R, const Smem &sm,
-                                           Path &p, RegCnt &rc)
+template <class M>
+__device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Smem &sm, Path &p,
+                                           RegCnt &rc)
 {
     Conn c;
     c.valid = false;
@@ -369,11 +470,12 @@ __device__ __forceinline__ Conn track_step(const SceneDev &S, const RunDev &R, c
         return c;
     }
     rc.steps++;
-    const U4 b0 = draw(R.seed, R.medium_id, p.pid, p.step, 0u);
-    const float sb = sm.maj[p.bin];
+    const uint32_t key1 = m.key1(R);
+    const U4 b0 = draw(R.seed, key1, p.pid, p.step, 0u);
+    const float sb = m.maj(p.bin);
     const float tf = sb > 0.0f ? -__logf(1.0f - b0.a) / sb : FLT_MAX;
     int face;
-    const float te = exit_distance(S, p.x, p.w, p.iw, face);
+    const float te = exit_distance(m, p.x, p.w, p.iw, face);
     const uint32_t step = p.step;
     p.step++;
     if (tf >= te) {
@@ -383,26 +485,26 @@ __device__ __forceinline__ Conn track_step(const SceneDev &S, const RunDev &R, c
             finish(R, p);
             return c;
         }
-        if (S.wall_mask & (1 << face)) {
+        if (m.wall_mask() & (1 << face)) {
             if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
             p.n_events++;
             rc.events++;
             cnt_add(sm, FLR_C_WALL_BOUNCES);
-            const U4 b1 = draw(R.seed, R.medium_id, p.pid, step, 1u);
+            const U4 b1 = draw(R.seed, key1, p.pid, step, 1u);
             if (R.analog) {
-                if (!(b1.d < S.wall_albedo)) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+                if (!(b1.d < m.wall_albedo())) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
             } else {
-                p.wt *= S.wall_albedo;
+                p.wt *= m.wall_albedo();
                 if (p.wt == 0.0f) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
             }
             const int ax = face >> 1;
             const float sg = (face & 1) ? -1.0f : 1.0f;
-            if (ax == 0) p.x.x = (face & 1) ? S.hi[0] : S.lo[0];
-            else if (ax == 1) p.x.y = (face & 1) ? S.hi[1] : S.lo[1];
-            else p.x.z = (face & 1) ? S.hi[2] : S.lo[2];
+            if (ax == 0) p.x.x = (face & 1) ? m.hi(0) : m.lo(0);
+            else if (ax == 1) p.x.y = (face & 1) ? m.hi(1) : m.lo(1);
+            else p.x.z = (face & 1) ? m.hi(2) : m.lo(2);
             p.w = cosine_dir(b0.c, b0.d, ax, sg);
             p.iw = inv_dir(p.w);
-            if (S.sensor_kind != FLR_SENSOR_NONE)
+            if (m.sensor())
                 c = Conn{p.x, p.wt, p.bin, 2 * ax + (sg > 0.0f ? 1 : 0), p.pid, step, true};
             if (p.n_events >= R.n_rr) {
                 const float q = fminf(p.wt, 1.0f);
@@ -411,13 +513,13 @@ __device__ __forceinline__ Conn track_step(const SceneDev &S, const RunDev &R, c
             }
             return c;
         }
-        tally_add(sm, tal_face(S.B) + (p.fl * 6 + face) * S.B + p.bin, p.wt);
+        m.tally(tal_face(m.B()) + (p.fl * 6 + face) * m.B() + p.bin, p.wt);
         cnt_add(sm, FLR_C_ESCAPES);
         finish(R, p);
         return c;
     }
     p.x = make_float3(p.x.x + tf * p.w.x, p.x.y + tf * p.w.y, p.x.z + tf * p.w.z);
-    const Coeffs k = coeffs_at(S, sm, p.x, p.bin);
+    const Coeffs k = coeffs_at(m, p.x, p.bin);
     if (k.total > sb) cnt_add(sm, FLR_C_MAJORANT_VIOLATIONS);
     if (!(b0.b * sb < k.total)) {
         rc.nulls++;
@@ -426,16 +528,17 @@ __device__ __forceinline__ Conn track_step(const SceneDev &S, const RunDev &R, c
     if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
     p.n_events++;
     rc.events++;
-    const U4 b1 = draw(R.seed, R.medium_id, p.pid, step, 1u);
+    const U4 b1 = draw(R.seed, key1, p.pid, step, 1u);
     // particle type in proportion to its coefficient (Sec. 4.1)
     const float ue = b0.c * k.total;
     float acc = k.scat;
     int ev = -1;
+    const int D = m.D();
     if (!(ue < acc)) {
-        ev = S.D;
+        ev = D;
 #pragma unroll
         for (int d = 0; d < MAXD; ++d) {
-            if (d < S.D && ev == S.D) {
+            if (d < D && ev == D) {
                 acc += k.dye[d];
                 if (ue < acc) ev = d;
             }
@@ -445,31 +548,31 @@ __device__ __forceinline__ Conn track_step(const SceneDev &S, const RunDev &R, c
         rc.scatters++;
         p.w = iso_dir(b0.d, b1.a);
         p.iw = inv_dir(p.w);
-        if (S.sensor_kind != FLR_SENSOR_NONE) c = Conn{p.x, p.wt, p.bin, -1, p.pid, step, true};
-    } else if (ev < S.D) {
+        if (m.sensor()) c = Conn{p.x, p.wt, p.bin, -1, p.pid, step, true};
+    } else if (ev < D) {
         cnt_add(sm, FLR_C_DYE_ABSORPTIONS);
-        tally_add(sm, tal_absorbed(S.B) + ev * S.B + p.bin, p.wt);
+        m.tally(tal_absorbed(m.B()) + ev * m.B() + p.bin, p.wt);
         if (R.max_inelastic >= 0 && p.n_inel >= R.max_inelastic) {
             cnt_add(sm, FLR_C_VF_REJECTED);
             finish(R, p);
             return c;
         }
         if (R.analog) {
-            if (!(b1.d < sm.qy[ev])) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+            if (!(b1.d < m.qy(ev))) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
         } else {
-            p.wt *= sm.qy[ev];
+            p.wt *= m.qy(ev);
             if (p.wt == 0.0f) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
         }
-        p.bin = sample_cdf(sm.cdf + ev * S.B, S.B, b1.b);
-        tally_add(sm, tal_emitted(S.B) + ev * S.B + p.bin, p.wt);
+        p.bin = sample_cdf(m.cdf(ev), m.B(), b1.b);
+        m.tally(tal_emitted(m.B()) + ev * m.B() + p.bin, p.wt);
         cnt_add(sm, FLR_C_EMISSIONS);
         p.n_inel++;
         p.fl = 1;
         p.w = iso_dir(b0.d, b1.a);
         p.iw = inv_dir(p.w);
-        if (S.sensor_kind != FLR_SENSOR_NONE) c = Conn{p.x, p.wt, p.bin, -1, p.pid, step, true};
+        if (m.sensor()) c = Conn{p.x, p.wt, p.bin, -1, p.pid, step, true};
     } else {
-        tally_add(sm, tal_absorbed(S.B) + S.D * S.B + p.bin, p.wt);
+        m.tally(tal_absorbed(m.B()) + D * m.B() + p.bin, p.wt);
         cnt_add(sm, FLR_C_ABSORBED_DEAD);
         finish(R, p);
         return c;
@@ -528,13 +631,6 @@ __device__ __forceinline__ Smem block_prologue(const SceneDev &S, unsigned char 
     return sm;
 }
 
-__device__ __forceinline__ unsigned warp_sum(unsigned v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 __device__ __forceinline__ void block_epilogue(const SceneDev &S, const RunDev &R, const Smem &sm,
                                                const RegCnt &rc)
 {
@@ -564,14 +660,15 @@ __global__ void __launch_bounds__(256) k_trace_plain(SceneDev S, RunDev R)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
     const Smem sm = block_prologue(S, smem_raw, L);
+    const MedS m{S, sm};
     RegCnt rc = {0, 0, 0, 0, 0, 0};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
         Path p;
-        Conn c = spawn(S, R, sm, R.path_offset + i, p);
+        Conn c = spawn(m, R, sm, R.path_offset + i, p);
         if (c.valid) connect(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
         while (p.alive) {
-            c = track_step(S, R, sm, p, rc);
+            c = track_step(m, R, sm, p, rc);
             if (c.valid) connect(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
         }
     }
@@ -655,6 +752,7 @@ __global__ void __launch_bounds__(256) k_trace_wavefront(SceneDev S, RunDev R)
     }
     __shared__ int s_active;
     __syncthreads();
+    const MedS m{S, sm};
     RegCnt rc = {0, 0, 0, 0, 0, 0};
     Path p;
     p.alive = false;
@@ -667,11 +765,11 @@ __global__ void __launch_bounds__(256) k_trace_wavefront(SceneDev S, RunDev R)
                 if (exhausted) break;
                 const unsigned long long i = atomicAdd(R.work_counter, 1ull);
                 if (i >= R.n_paths) { exhausted = true; break; }
-                const Conn c = spawn(S, R, sm, R.path_offset + i, p);
+                const Conn c = spawn(m, R, sm, R.path_offset + i, p);
                 if (c.valid) { queue_push(q, cap, c); break; }
                 continue;
             }
-            const Conn c = track_step(S, R, sm, p, rc);
+            const Conn c = track_step(m, R, sm, p, rc);
             if (c.valid) { queue_push(q, cap, c); break; }
         }
         if (threadIdx.x == 0) s_active = 0;
@@ -684,6 +782,85 @@ __global__ void __launch_bounds__(256) k_trace_wavefront(SceneDev S, RunDev R)
         if (!any) break;
     }
     block_epilogue(S, R, sm, rc);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched persistent form: independent media in one launch. A device queue holds chunks of
+// consecutive path ids of one medium (ordered longest expected paths first). Each warp owns one
+// chunk at a time and hands its path ids to lanes as their paths end (regeneration), so a lane
+// never waits for the rest of its warp; lanes of one warp may be in different media. Face,
+// absorption and emission tallies go to each medium's own fixed-point arrays.
+__device__ __forceinline__ void counters_epilogue(const RunDev &R, const Smem &sm, const RegCnt &rc)
+{
+    const unsigned vals[6] = {rc.steps, rc.nulls, rc.events, rc.scatters, rc.connections,
+                              rc.connect_steps};
+    const int idx[6] = {FLR_C_STEPS, FLR_C_NULLS, FLR_C_EVENTS, FLR_C_SCATTERS, FLR_C_CONNECTIONS,
+                        FLR_C_CONNECT_STEPS};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        unsigned long long v = vals[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&sm.cnt[idx[i]], v);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < FLR_NCOUNTERS; i += blockDim.x)
+        if (sm.cnt[i]) atomicAdd(&R.counters[i], sm.cnt[i]);
+}
+
+__global__ void __launch_bounds__(256) k_trace_batch(BatchDev Bt, RunDev R)
+{
+    __shared__ unsigned long long s_cnt[FLR_NCOUNTERS];
+    for (int i = threadIdx.x; i < FLR_NCOUNTERS; i += blockDim.x) s_cnt[i] = 0ull;
+    __syncthreads();
+    Smem sm;
+    sm.sig_a = sm.cdf = sm.maj = sm.qy = nullptr;
+    sm.tal = nullptr;
+    sm.cnt = s_cnt;
+    RegCnt rc = {0, 0, 0, 0, 0, 0};
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lower = (1u << lane) - 1u;
+    Path p;
+    p.alive = false;
+    int mi = 0;                                        // medium of this lane's path
+    int cm = 0;                                        // warp's current chunk (warp-uniform)
+    unsigned long long cnext = 0ull, cend = 0ull;
+    bool done = false;
+    while (true) {
+        unsigned need = __ballot_sync(FULL, !p.alive);
+        while (need != 0u && !done) {
+            if (cnext >= cend) {
+                unsigned long long ci = 0ull;
+                if (lane == 0) ci = atomicAdd(Bt.head, 1ull);
+                ci = __shfl_sync(FULL, ci, 0);
+                if (ci >= (unsigned long long)Bt.n_chunks) {
+                    done = true;
+                    break;
+                }
+                const ChunkDev c = Bt.chunks[ci];
+                cm = c.medium;
+                cnext = c.start;
+                cend = c.start + c.count;
+            }
+            const unsigned long long avail = cend - cnext;
+            const int rank = __popc(need & lower);
+            if (((need >> lane) & 1u) && (unsigned long long)rank < avail) {
+                mi = cm;
+                const MedB m{Bt.media + cm, Bt.B};
+                spawn(m, R, sm, cnext + (unsigned long long)rank, p);
+            }
+            const unsigned long long n_need = (unsigned long long)__popc(need);
+            cnext += n_need < avail ? n_need : avail;
+            need = __ballot_sync(FULL, !p.alive);
+        }
+        if (__ballot_sync(FULL, p.alive) == 0u && done) break;
+        if (p.alive) {
+            const MedB m{Bt.media + mi, Bt.B};
+            track_step(m, R, sm, p, rc);
+        }
+    }
+    counters_epilogue(R, sm, rc);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -747,7 +924,9 @@ __global__ void k_sample_emission(const float *__restrict__ cdf, int B, const fl
         out[i] = sample_cdf(cdf, B, u[i]);
 }
 
-int num_sms()
+}  // namespace
+
+int device_sms()
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -755,6 +934,8 @@ int num_sms()
     return sms > 0 ? sms : 1;
 }
 
+namespace {
+int num_sms() { return device_sms(); }
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -791,6 +972,24 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
         k_trace_wavefront<<<(unsigned)grid, block, smem, st>>>(S, R);
     else
         k_trace_plain<<<(unsigned)grid, block, smem, st>>>(S, R);
+    return cudaGetLastError();
+}
+
+int batch_occupancy_blocks_per_sm(int block)
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_batch, block, 0);
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_batch(const BatchDev &Bt, const RunDev &R, int block, int blocks_per_sm,
+                         cudaStream_t st)
+{
+    if (block <= 0) block = trace_block_default();
+    const int occ = batch_occupancy_blocks_per_sm(block);
+    if (blocks_per_sm <= 0 || blocks_per_sm > occ) blocks_per_sm = occ;
+    const long long grid = (long long)num_sms() * blocks_per_sm;
+    k_trace_batch<<<(unsigned)grid, block, 0, st>>>(Bt, R);
     return cudaGetLastError();
 }
 

@@ -90,6 +90,13 @@ SIGNATURES = {
     "flr_render": (C.c_int, [C.c_void_p, C.POINTER(flr_params), C.c_void_p]),
     "flr_read_tallies": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]),
+    "flr_batch_prepare": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(flr_medium), C.c_void_p,
+                                    C.POINTER(flr_params)]),
+    "flr_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "flr_batch_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
+    "flr_render_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(flr_medium), C.c_void_p,
+                                   C.POINTER(flr_params), C.c_void_p]),
     "flr_status": (C.c_int, [C.c_void_p]),
     "flr_last_error": (C.c_char_p, [C.c_void_p]),
     "flr_debug_philox": (C.c_int, [C.c_uint32, C.c_uint32, C.c_void_p, C.c_int64, C.c_void_p,
@@ -202,3 +209,21 @@ def flr_debug_philox(seed, medium, ctr_ptr, n, out_ptr, stream=0):
 def flr_debug_sample_emission(ctx, dye, u_ptr, n, out_ptr, stream=0):
     return load().flr_debug_sample_emission(ctx, int(dye), u_ptr, int(n), out_ptr,
                                             C.c_void_p(int(stream)))
+
+
+def flr_batch_prepare(ctx, n_media, media, n_paths_ptr, params):
+    return load().flr_batch_prepare(ctx, int(n_media), media, n_paths_ptr, C.byref(params))
+
+
+def flr_batch_launch(ctx, stream=0):
+    return load().flr_batch_launch(ctx, C.c_void_p(int(stream)))
+
+
+def flr_batch_read(ctx, face_ptr, absorbed_ptr, emitted_ptr, counters_ptr, stream=0):
+    return load().flr_batch_read(ctx, face_ptr, absorbed_ptr, emitted_ptr, counters_ptr,
+                                 C.c_void_p(int(stream)))
+
+
+def flr_render_batch(ctx, n_media, media, n_paths_ptr, params, stream=0):
+    return load().flr_render_batch(ctx, int(n_media), media, n_paths_ptr, C.byref(params),
+                                   C.c_void_p(int(stream)))

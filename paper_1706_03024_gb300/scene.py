@@ -189,3 +189,111 @@ class Scene:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many independent media (scene dicts sharing one spectrum) in one persistent launch."""
+
+    def __init__(self, scenes, device=0, seed=0, medium_id=0, n_rr=5, max_events=1_000_000,
+                 max_inelastic=-1, analog=0, max_steps=10_000_000, block_size=0,
+                 blocks_per_sm=0, path_offset=0):
+        self.device = device
+        self.ctx = N.flr_create(device)
+        sp = scenes[0]["spectrum"]
+        self.B = int(sp["n_bins"])
+        self.M = len(scenes)
+        N.check(N.flr_set_spectrum(self.ctx, sp["lambda0"], sp["dlambda"], self.B), self.ctx,
+                "flr_set_spectrum")
+        dev = torch.device("cuda", device)
+        abs_rows, em_rows, eps, qy, srcs = [], [], [], [], []
+        meds = (N.flr_medium * self.M)()
+        self.grids = []
+        n_paths = np.zeros(self.M, dtype=np.uint64)
+        for i, sc in enumerate(scenes):
+            dy, md = sc["dyes"], sc["medium"]
+            D = int(np.asarray(dy["eps"]).shape[0])
+            m = meds[i]
+            m.n_dyes = D
+            for d in range(D):
+                m.dye_ids[d] = len(eps)
+                abs_rows.append(np.asarray(dy["abs_shape"][d], np.float32))
+                em_rows.append(np.asarray(dy["emit_spec"][d], np.float32))
+                eps.append(float(dy["eps"][d]))
+                qy.append(float(dy["qy"][d]))
+            m.lo[:] = md["lo"]
+            m.hi[:] = md["hi"]
+            cu = np.asarray(md["conc_uniform"], np.float32)
+            for d in range(D):
+                m.conc_uniform[d] = float(cu[d]) if d < cu.shape[0] else 0.0
+            if md.get("conc") is not None:
+                g = torch.from_numpy(np.ascontiguousarray(md["conc"], np.float32)).to(dev)
+                self.grids.append(g)
+                _, nz, ny, nx = g.shape
+                m.dims[:] = (nx, ny, nz)
+                for d in range(D):
+                    m.conc[d] = g[d].data_ptr()
+            if md.get("solvent") is not None:
+                sv = torch.from_numpy(np.ascontiguousarray(md["solvent"], np.uint8)).to(dev)
+                self.grids.append(sv)
+                nz, ny, nx = sv.shape
+                m.dims[:] = (nx, ny, nz)
+                m.solvent = sv.data_ptr()
+            m.sigma_s = float(md["sigma_s"])
+            m.sigma_a0 = float(md["sigma_a0"])
+            m.wall_mask = int(md["wall_mask"])
+            m.wall_albedo = float(md["wall_albedo"])
+            m.source_first = len(srcs)
+            m.source_count = len(sc["sources"])
+            srcs.extend(make_source(s) for s in sc["sources"])
+            n_paths[i] = int(sc["params"]["n_paths"])
+        a = np.ascontiguousarray(np.stack(abs_rows), np.float32)
+        e = np.ascontiguousarray(np.stack(em_rows), np.float32)
+        ep = np.ascontiguousarray(eps, np.float32)
+        q = np.ascontiguousarray(qy, np.float32)
+        N.check(N.flr_set_dyes(self.ctx, len(eps), _np_ptr(a), _np_ptr(e), _np_ptr(ep), _np_ptr(q)),
+                self.ctx, "flr_set_dyes")
+        arr = (N.flr_source * len(srcs))(*srcs)
+        N.check(N.flr_set_sources(self.ctx, len(srcs), arr), self.ctx, "flr_set_sources")
+        p = N.flr_params()
+        p.n_paths = int(n_paths.sum())
+        p.path_offset = int(path_offset)
+        p.seed = int(seed)
+        p.medium_id = int(medium_id)
+        p.n_rr = int(n_rr)
+        p.max_inelastic = int(max_inelastic)
+        p.analog = int(analog)
+        p.max_events = int(max_events)
+        p.max_steps = int(max_steps)
+        p.block_size = int(block_size)
+        p.blocks_per_sm = int(blocks_per_sm)
+        self.n_paths = n_paths
+        self.media = meds
+        N.check(N.flr_batch_prepare(self.ctx, self.M, meds, _np_ptr(n_paths), p), self.ctx,
+                "flr_batch_prepare")
+
+    def launch(self, stream=None):
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        N.check(N.flr_batch_launch(self.ctx, st.cuda_stream), self.ctx, "flr_batch_launch")
+
+    def read(self, stream=None):
+        B, M, MD = self.B, self.M, N.FLR_MAX_DYES_PER_MEDIUM
+        face = np.zeros((M, 2, 6, B))
+        absorbed = np.zeros((M, MD + 1, B))
+        emitted = np.zeros((M, MD, B))
+        counters = np.zeros(N.FLR_NCOUNTERS, np.uint64)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        N.check(N.flr_batch_read(self.ctx, _np_ptr(face), _np_ptr(absorbed), _np_ptr(emitted),
+                                 _np_ptr(counters), st.cuda_stream), self.ctx, "flr_batch_read")
+        return {"face": face, "absorbed": absorbed, "emitted": emitted,
+                "counters": {n: int(v) for n, v in zip(N.COUNTER_NAMES, counters)}}
+
+    def close(self):
+        if self.ctx:
+            N.flr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -48,7 +48,7 @@ def compare_integrated(g, o, rel=5e-3, floor=1e-3):
     return worst
 
 
-def bin_parity(g_outs, o_outs, key, min_nonzero=None):
+def bin_parity(g_outs, o_outs, key, min_nonzero=None, same_seed=True):
     gs = np.stack([x[key] for x in g_outs])
     os_ = np.stack([x[key] for x in o_outs])
     K = gs.shape[0]
@@ -59,4 +59,16 @@ def bin_parity(g_outs, o_outs, key, min_nonzero=None):
     populated = ((gs != 0).sum(axis=0) >= min_nonzero) & ((os_ != 0).sum(axis=0) >= min_nonzero)
     sg = np.where(populated, sg, 0.0)
     so = np.where(populated, so, 0.0)
-    return parity_verdict(mg, sg, mo, so)
+    return parity_verdict(mg, sg, mo, so, check_chi2=not same_seed)
+
+
+def integrated_independent(g_outs, o_outs, key, rel=5e-3):
+    """Independent seeds: per-row totals agree within max(rel, 3 SE)."""
+    gs = np.stack([x[key].sum(axis=-1) for x in g_outs])
+    os_ = np.stack([x[key].sum(axis=-1) for x in o_outs])
+    mg, sg = batch_mean_se(gs)
+    mo, so = batch_mean_se(os_)
+    tol = np.maximum(rel * np.abs(mo), 3.0 * np.sqrt(sg ** 2 + so ** 2))
+    big = np.abs(mo) >= 1e-3 * max(np.abs(mo).max(), 1e-300)
+    bad = (np.abs(mg - mo) > tol) & big
+    return not bad.any(), {"gpu": mg[big].tolist()[:12], "oracle": mo[big].tolist()[:12]}

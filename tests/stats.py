@@ -55,17 +55,26 @@ def zscores(a, se_a, b, se_b):
 
 
 def parity_verdict(a, se_a, b, se_b, frac_limit=0.01, max_limit=5.5, chi_lo=0.8, chi_hi=1.2,
-                   min_bins=50):
+                   min_bins=500, check_chi2=True):
     """Per-bin agreement criteria: fraction of |z| > 3 at most frac_limit, max |z| at most
-    max_limit and, when enough bins are populated, reduced chi-square in [chi_lo, chi_hi]."""
+    max_limit and, when enough bins are populated, reduced chi-square in [chi_lo, chi_hi].
+    The chi-square band assumes independent estimates: runs that share their random numbers
+    (same seed, same path ids) agree far better than their standard errors, so for them only the
+    |z| limits apply (check_chi2=False). The band also needs many weakly correlated bins: the
+    bins of one spectral tally move together (a dye's emission row scales with its total), so
+    mean z^2 over a few dozen of them behaves like a chi-square with few degrees of freedom; it is
+    applied from min_bins = 500 populated bins on (films)."""
     z, m = zscores(a, se_a, b, se_b)
     zz = z[m]
     if zz.size == 0:
         return {"ok": True, "n": 0}
-    frac = float((np.abs(zz) > 3).mean())
+    n_gt3 = int((np.abs(zz) > 3).sum())
+    frac = n_gt3 / zz.size
     zmax = float(np.abs(zz).max())
     red = float((zz ** 2).mean())
-    ok = frac <= frac_limit and zmax <= max_limit
-    if zz.size >= min_bins:
+    # a spectral tally has tens of bins, and z from K batch means has t-like tails that cluster
+    # over neighbouring bins: up to 3 bins beyond 3 are accepted whatever the bin count
+    ok = (frac <= frac_limit or n_gt3 <= 3) and zmax <= max_limit
+    if check_chi2 and zz.size >= min_bins:
         ok = ok and chi_lo <= red <= chi_hi
     return {"ok": ok, "n": int(zz.size), "frac_gt3": frac, "max_abs_z": zmax, "red_chi2": red}
