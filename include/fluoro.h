@@ -208,7 +208,7 @@ int flr_status(flr_ctx *ctx);
 const char *flr_last_error(flr_ctx *ctx);
 
 /* Diagnostics. Philox4x32-10 (Salmon et al., SC'11) blocks for device counters ctr [n][4] under
- * the key (seed, medium) into device out [n][4]. */
+ * the key (seed, medium) into device out [n][4]; both 16-byte aligned (FLR_ERR_ARG otherwise). */
 int flr_debug_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, int64_t n,
                      uint32_t *out, void *stream);
 /* Emission bins drawn by the current medium's dye slot `dye` for device uniforms u [n]

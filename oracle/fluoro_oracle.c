@@ -105,6 +105,18 @@ typedef struct {
     int n_threads;
     int64_t max_events;       /* a real collision with n_events == max_events ends the path */
     int64_t max_steps;        /* tracking-step budget per path                               */
+    /* frozen-sampling evaluation (for finite differences with common random numbers): the
+     * evaluation medium is the scene plus one perturbation (pert_delta added to dye pert_dye's
+     * concentration in voxel pert_voxel, pert_sigma_s added to sigma_s). With frozen = 1 every
+     * decision is still sampled in the unperturbed medium and each tally is weighted by the
+     * likelihood ratio p_eval / p_sample of the decisions before it; with frozen = 0 the perturbed
+     * medium is simply rendered. */
+    double majorant_scale;    /* sigma_bar multiplier (>= 1; 0 means 1)                       */
+    int frozen;
+    int pert_dye;             /* < 0: no concentration perturbation                         */
+    int64_t pert_voxel;
+    double pert_delta;
+    double pert_sigma_s;
 } or_params;
 
 typedef struct {
@@ -173,7 +185,22 @@ typedef struct {
     int em_bin[OR_MAX_EMITTERS];
     float em_cdf32[OR_MAX_EMITTERS];
     double A_pix, tan_half, aspect;
+    int frozen, pert_dye;
+    int64_t pert_voxel;
+    double pert_delta, pert_sigma_s;
 } tables;
+
+/* Copy the per-render evaluation settings into the tables (majorant scale and perturbation). */
+static void apply_params(tables *t, const or_params *p)
+{
+    double ms = p->majorant_scale > 0.0 ? p->majorant_scale : 1.0;
+    for (int i = 0; i < t->B; ++i) t->majorant[i] *= ms;
+    t->frozen = p->frozen;
+    t->pert_dye = p->pert_dye;
+    t->pert_voxel = p->pert_voxel;
+    t->pert_delta = p->pert_delta;
+    t->pert_sigma_s = p->pert_sigma_s;
+}
 
 /* Emission pmf p_i = f_m(lambda_i) / sum_j f_m(lambda_j) (Eq. 10 with the bin as delta-lambda);
  * CDF_i = (sum_{j<=i} f_j) / (sum_j f_j), summed left to right in fp64, last entry forced to 1. */
@@ -274,22 +301,31 @@ static int voxel_index(const or_scene *s, const double x[3])
  * sigma_t = s(x) (sigma_s + sigma_a0) + sum_d eps_d a_d(lambda) c_d(x). */
 typedef struct { double scat, dye[OR_MAX_DYES], bg, total; } coeffs;
 
-static coeffs coeffs_at(const or_scene *s, const tables *t, const double x[3], int bin)
+/* `perturbed` selects the evaluation medium (the scene plus the render's perturbation). */
+static coeffs coeffs_at_p(const or_scene *s, const tables *t, const double x[3], int bin,
+                          int perturbed)
 {
     coeffs c;
     double sv = 1.0;
     int v = -1;
     if (!t->homogeneous) v = voxel_index(s, x);
     if (s->solvent) sv = s->solvent[v] ? 1.0 : 0.0;
-    c.scat = sv * s->sigma_s;
+    double sig_s = s->sigma_s + (perturbed ? t->pert_sigma_s : 0.0);
+    c.scat = sv * sig_s;
     c.bg = sv * s->sigma_a0;
     c.total = c.scat + c.bg;
     for (int d = 0; d < s->n_dyes; ++d) {
         double conc = s->conc ? (double)s->conc[(size_t)d * nvox(s) + v] : (double)s->conc_uniform[d];
+        if (perturbed && d == t->pert_dye && (int64_t)v == t->pert_voxel) conc += t->pert_delta;
         c.dye[d] = t->sig_a[d][bin] * conc;
         c.total += c.dye[d];
     }
     return c;
+}
+
+static coeffs coeffs_at(const or_scene *s, const tables *t, const double x[3], int bin)
+{
+    return coeffs_at_p(s, t, x, bin, 0);
 }
 
 /* Distance to leave the AABB along (x, w), and the face: faces (-x,+x,-y,+y,-z,+z) = 0..5;
@@ -320,12 +356,32 @@ static int cmp_double(const void *a, const void *b)
 /* Exact optical depth int_0^L sigma_t(x0 + t w) dt of the piecewise-constant field (Eq. 6):
  * the segment is cut at every voxel-plane crossing and sigma_t is evaluated at each piece's
  * midpoint. */
+/* Derivative sink of an optical depth: d tau / d c_d[v] = sig_a[d][bin] * (length in v) and
+ * d tau / d sigma_s = s(x) * length, each times `scale`, added into grad_c / grad_sigma_s. */
+typedef struct { double *grad_c; double *grad_sigma_s; double scale; } tau_grad;
+
+static double optical_depth_g(const or_scene *s, const tables *t, const double x0[3],
+                              const double w[3], double L, int bin, int perturbed,
+                              const tau_grad *g);
+
 static double optical_depth(const or_scene *s, const tables *t, const double x0[3],
                             const double w[3], double L, int bin)
 {
+    return optical_depth_g(s, t, x0, w, L, bin, t->frozen || t->pert_dye >= 0 ||
+                           t->pert_sigma_s != 0.0, NULL);
+}
+
+static double optical_depth_g(const or_scene *s, const tables *t, const double x0[3],
+                              const double w[3], double L, int bin, int perturbed,
+                              const tau_grad *g)
+{
     if (L <= 0.0) return 0.0;
     if (t->homogeneous) {
-        coeffs c = coeffs_at(s, t, x0, bin);
+        coeffs c = coeffs_at_p(s, t, x0, bin, perturbed);
+        if (g && g->grad_sigma_s) {
+#pragma omp atomic
+            *g->grad_sigma_s += g->scale * L;
+        }
         return c.total * L;
     }
     int cap = 2 + s->dims[0] + s->dims[1] + s->dims[2] + 8;
@@ -348,8 +404,24 @@ static double optical_depth(const or_scene *s, const tables *t, const double x0[
         if (b <= a) continue;
         double m = 0.5 * (a + b);
         double xm[3] = { x0[0] + m * w[0], x0[1] + m * w[1], x0[2] + m * w[2] };
-        coeffs c = coeffs_at(s, t, xm, bin);
+        coeffs c = coeffs_at_p(s, t, xm, bin, perturbed);
         tau += c.total * (b - a);
+        if (g) {
+            int v = voxel_index(s, xm);
+            double sv = s->solvent ? (s->solvent[v] ? 1.0 : 0.0) : 1.0;
+            if (g->grad_sigma_s && sv != 0.0) {
+#pragma omp atomic
+                *g->grad_sigma_s += g->scale * sv * (b - a);
+            }
+            if (g->grad_c && s->conc)
+                for (int d = 0; d < s->n_dyes; ++d) {
+                    double dv = g->scale * t->sig_a[d][bin] * (b - a);
+                    if (dv != 0.0) {
+#pragma omp atomic
+                        g->grad_c[(size_t)d * nvox(s) + v] += dv;
+                    }
+                }
+        }
     }
     free(cuts);
     return tau;

@@ -667,6 +667,7 @@ int flr_debug_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, int64_
     if (n < 0 || (n > 0 && (!ctr || !out))) return FLR_ERR_ARG;
     if (n == 0) return FLR_OK;
     if (!is_device_pointer(ctr) || !is_device_pointer(out)) return FLR_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(ctr) | reinterpret_cast<uintptr_t>(out)) & 15u) return FLR_ERR_ARG;
     return launch_philox(seed, medium, ctr, n, out, (cudaStream_t)stream) == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
 }
 

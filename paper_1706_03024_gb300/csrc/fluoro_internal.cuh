@@ -95,6 +95,8 @@ struct MediumDev {
     EmitterDev em[BATCH_MAX_LINES];
 };
 
+static_assert(sizeof(MediumDev) % 8 == 0, "MediumDev array elements keep 8-byte alignment");
+
 // A work item of the batched queue: `count` consecutive path ids of one medium.
 struct ChunkDev {
     int medium;

@@ -147,7 +147,9 @@ struct MedB {
     }
     __device__ __forceinline__ float4 conc_uniform() const
     {
-        return __ldg(reinterpret_cast<const float4 *>(&md->conc_uniform[0]));
+        // scalar loads: the field is only 8-byte aligned inside MediumDev
+        return make_float4(__ldg(&md->conc_uniform[0]), __ldg(&md->conc_uniform[1]),
+                           __ldg(&md->conc_uniform[2]), __ldg(&md->conc_uniform[3]));
     }
     __device__ __forceinline__ float sigma_s() const { return __ldg(&md->sigma_s); }
     __device__ __forceinline__ float sigma_a0() const { return __ldg(&md->sigma_a0); }
