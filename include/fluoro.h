@@ -42,7 +42,7 @@ extern "C" {
 #define FLR_MAX_BINS 128
 #define FLR_MAX_DYES 1024           /* dye table size                                      */
 #define FLR_MAX_DYES_PER_MEDIUM 4
-#define FLR_MAX_SOURCES 64
+#define FLR_MAX_SOURCES 65536
 #define FLR_MAX_LINES 8
 #define FLR_MAX_EMITTERS 32         /* spectral lines over all sources of one medium       */
 #define FLR_NCOUNTERS 20

@@ -233,6 +233,7 @@ static int nvox(const or_scene *s) { return s->dims[0] * s->dims[1] * s->dims[2]
 static void build_tables(const or_scene *s, tables *t)
 {
     memset(t, 0, sizeof(*t));
+    t->pert_dye = -1;
     t->B = s->n_bins;
     t->D = s->n_dyes;
     t->homogeneous = (s->conc == NULL && s->solvent == NULL);
@@ -469,11 +470,54 @@ static void normal_axis(const double n[3], int *k, double *sign)
  * The connecting segment must leave the box through an open (non-wall) face. */
 typedef struct { int lambertian; int axis; double sign; } vtx_kind;
 
+/* Adjoint bookkeeping of one path: its tracking decisions and sensor connections in order. */
+typedef struct {
+    int64_t step;
+    int kind;               /* 0 null, 1 scatter, 2 dye absorption, 3 background absorption */
+    int voxel, bin, dye;
+    double sigma_t, sigma_bar, solvent, conc;
+} dec_rec;
+
+typedef struct {
+    int64_t step;
+    double a;               /* adjoint-weighted contribution: A[pixel][bin] * value / N       */
+    double x[3], dir[3], L;
+    int bin;
+} con_rec;
+
+typedef struct {
+    const double *adj;      /* [H][W][B] dL/dI                                                */
+    double inv_n;
+    int64_t cur_step;       /* step of the decision or vertex being processed                 */
+    dec_rec *dec;
+    int64_t n_dec, cap_dec;
+    con_rec *con;
+    int64_t n_con, cap_con;
+} adj_path;
+
+static void adj_push_dec(adj_path *A, dec_rec r)
+{
+    if (A->n_dec == A->cap_dec) {
+        A->cap_dec = A->cap_dec ? 2 * A->cap_dec : 64;
+        A->dec = (dec_rec *)realloc(A->dec, sizeof(dec_rec) * (size_t)A->cap_dec);
+    }
+    A->dec[A->n_dec++] = r;
+}
+
+static void adj_push_con(adj_path *A, con_rec r)
+{
+    if (A->n_con == A->cap_con) {
+        A->cap_con = A->cap_con ? 2 * A->cap_con : 64;
+        A->con = (con_rec *)realloc(A->con, sizeof(con_rec) * (size_t)A->cap_con);
+    }
+    A->con[A->n_con++] = r;
+}
+
 static void connect_sensor(const or_scene *s, const tables *t, const double x[3], int bin,
-                           double w, vtx_kind vk, double *film, uint64_t *cnt)
+                           double w, vtx_kind vk, double *film, uint64_t *cnt, adj_path *A)
 {
     const or_sensor *c = &s->sensor;
-    if (c->kind == 0 || film == NULL) return;
+    if (c->kind == 0 || (film == NULL && A == NULL)) return;
     double dir[3], geom, r2 = 0.0;
     int px, py;
     if (c->kind == 1) {
@@ -522,8 +566,19 @@ static void connect_sensor(const or_scene *s, const tables *t, const double x[3]
     double T = exp(-optical_depth(s, t, x, dir, tl, bin));
     double val = w * f * T * geom;
     size_t idx = ((size_t)py * c->width + px) * t->B + bin;
+    if (film) {
 #pragma omp atomic
-    film[idx] += val;
+        film[idx] += val;
+    }
+    if (A) {
+        con_rec r;
+        r.step = A->cur_step;
+        r.a = A->adj[idx] * val * A->inv_n;
+        for (int k = 0; k < 3; ++k) { r.x[k] = x[k]; r.dir[k] = dir[k]; }
+        r.L = tl;
+        r.bin = bin;
+        if (r.a != 0.0) adj_push_con(A, r);
+    }
     cnt[OC_CONNECTIONS]++;
 }
 
@@ -550,10 +605,16 @@ static int sample_emission_bin(const tables *t, int d, double u)
 }
 
 static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *p, uint64_t pid,
-                           local_tally *lt, double *film)
+                           local_tally *lt, double *film, adj_path *A)
 {
     uint64_t *cnt = lt->cnt;
     cnt[OC_PATHS]++;
+    /* frozen sampling: decisions in the base medium, tallies times W = p_eval / p_sample */
+    const int has_pert = t->pert_dye >= 0 || t->pert_sigma_s != 0.0;
+    const int samp_pert = has_pert && !t->frozen;
+    const int weigh = has_pert && t->frozen;
+    double W = 1.0;
+    if (A) A->cur_step = -1;
     /* spawn (Eq. 12: p(x_n), p(lambda_x)) */
     block4 S0 = rng_block(p->seed, p->medium_id, pid, STEP_SPAWN, 0);
     int ek = sample_emitter(t, s->n_emitters, S0.u[0]);
@@ -568,7 +629,7 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
         normal_axis(em->dir, &ax, &sg);
         cosine_dir(S0.u[3], S1.u[0], ax, sg, w);
         vtx_kind vk = { 1, ax, sg };
-        connect_sensor(s, t, x, bin, wt, vk, film, cnt);
+        connect_sensor(s, t, x, bin, wt, vk, film, cnt, A);
     } else {
         for (int k = 0; k < 3; ++k) w[k] = em->dir[k];
     }
@@ -577,6 +638,7 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
     int fl = 0;
     for (int64_t step = 0;; ++step) {
         if (step >= p->max_steps) { cnt[OC_STEP_BUDGET]++; break; }
+        if (A) A->cur_step = step;
         cnt[OC_STEPS]++;
         block4 B0 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 0);
         double sb = t->majorant[bin];
@@ -604,7 +666,7 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
                 x[ax] = (face & 1) ? s->hi[ax] : s->lo[ax];
                 cosine_dir(B0.u[2], B0.u[3], ax, sg, w);
                 vtx_kind vk = { 1, ax, sg };
-                connect_sensor(s, t, x, bin, wt, vk, film, cnt);
+                connect_sensor(s, t, x, bin, wt * W, vk, film, cnt, A);
                 if (n_events >= p->n_rr) {
                     double q = wt < 1.0 ? wt : 1.0;
                     if (!(B1.u[2] < q)) { cnt[OC_RR_KILLS]++; break; }
@@ -612,14 +674,26 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
                 }
                 continue;
             }
-            lt->face[fl][face][bin] += wt;
+            lt->face[fl][face][bin] += wt * W;
             cnt[OC_ESCAPES]++;
             break;
         }
         for (int k = 0; k < 3; ++k) x[k] += tf * w[k];
-        coeffs c = coeffs_at(s, t, x, bin);
+        coeffs c = coeffs_at_p(s, t, x, bin, samp_pert);
+        coeffs ce = c;
+        if (weigh) ce = coeffs_at_p(s, t, x, bin, 1);
         if (c.total > sb) cnt[OC_MAJORANT_VIOLATIONS]++;
-        if (!(B0.u[1] * sb < c.total)) { cnt[OC_NULLS]++; continue; }
+        int vox = t->homogeneous ? -1 : voxel_index(s, x);
+        double solv = s->solvent ? (s->solvent[vox] ? 1.0 : 0.0) : 1.0;
+        if (!(B0.u[1] * sb < c.total)) {
+            cnt[OC_NULLS]++;
+            if (weigh) W *= (1.0 - ce.total / sb) / (1.0 - c.total / sb);
+            if (A) {
+                dec_rec r = { step, 0, vox, bin, -1, c.total, sb, solv, 0.0 };
+                adj_push_dec(A, r);
+            }
+            continue;
+        }
         /* real collision */
         if (n_events == p->max_events) { cnt[OC_CAP_HITS]++; break; }
         n_events++;
@@ -636,14 +710,27 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
                 if (ue < acc) { ev = d; break; }
             }
         }
+        if (weigh) {
+            /* probability of "real collision, then this particle" is sigma_e / sigma_bar */
+            double pe = ev < 0 ? ce.scat / c.scat : (ev < s->n_dyes ? ce.dye[ev] / c.dye[ev] : ce.bg / c.bg);
+            W *= pe;
+        }
+        if (A) {
+            double conc = 0.0;
+            if (ev >= 0 && ev < s->n_dyes)
+                conc = s->conc ? (double)s->conc[(size_t)ev * nvox(s) + vox] : (double)s->conc_uniform[ev];
+            dec_rec r = { step, ev < 0 ? 1 : (ev < s->n_dyes ? 2 : 3), vox, bin, ev, c.total, sb, solv,
+                          conc };
+            adj_push_dec(A, r);
+        }
         if (ev < 0) {
             cnt[OC_SCATTERS]++;
             iso_dir(B0.u[3], B1.u[0], w);
             vtx_kind vk = { 0, 0, 0.0 };
-            connect_sensor(s, t, x, bin, wt, vk, film, cnt);
+            connect_sensor(s, t, x, bin, wt * W, vk, film, cnt, A);
         } else if (ev < s->n_dyes) {
             cnt[OC_DYE_ABSORPTIONS]++;
-            lt->absorbed[ev][bin] += wt;
+            lt->absorbed[ev][bin] += wt * W;
             if (p->max_inelastic >= 0 && n_inel >= p->max_inelastic) { cnt[OC_VF_REJECTED]++; break; }
             if (p->analog) {
                 if (!(B1.u[3] < t->qy[ev])) { cnt[OC_ABSORBED_DEAD]++; break; }
@@ -652,15 +739,15 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
                 if (wt == 0.0) { cnt[OC_ABSORBED_DEAD]++; break; }
             }
             bin = sample_emission_bin(t, ev, B1.u[1]);
-            lt->emitted[ev][bin] += wt;
+            lt->emitted[ev][bin] += wt * W;
             cnt[OC_EMISSIONS]++;
             n_inel++;
             fl = 1;
             iso_dir(B0.u[3], B1.u[0], w);
             vtx_kind vk = { 0, 0, 0.0 };
-            connect_sensor(s, t, x, bin, wt, vk, film, cnt);
+            connect_sensor(s, t, x, bin, wt * W, vk, film, cnt, A);
         } else {
-            lt->absorbed[s->n_dyes][bin] += wt;
+            lt->absorbed[s->n_dyes][bin] += wt * W;
             cnt[OC_ABSORBED_DEAD]++;
             break;
         }
@@ -684,6 +771,7 @@ int or_render(const or_scene *s, const or_params *p, or_result *r)
     if (s->n_emitters <= 0 || s->n_emitters > OR_MAX_EMITTERS) return -1;
     tables *t = (tables *)malloc(sizeof(tables));
     build_tables(s, t);
+    apply_params(t, p);
     int B = s->n_bins, D = s->n_dyes;
     memset(r->face, 0, sizeof(double) * 2 * 6 * B);
     memset(r->absorbed, 0, sizeof(double) * (D + 1) * B);
@@ -700,7 +788,7 @@ int or_render(const or_scene *s, const or_params *p, or_result *r)
         local_tally *lt = (local_tally *)calloc(1, sizeof(local_tally));
 #pragma omp for schedule(dynamic, 64)
         for (int64_t i = 0; i < N; ++i) {
-            uint32_t ne = trace_path(s, t, p, p->path_offset + (uint64_t)i, lt, r->film);
+            uint32_t ne = trace_path(s, t, p, p->path_offset + (uint64_t)i, lt, r->film, NULL);
             if (r->path_events) r->path_events[i] = ne;
         }
 #pragma omp critical
@@ -778,3 +866,97 @@ void or_majorant(const or_scene *s, double *out)
 }
 
 int or_counters_count(void) { return OR_NCOUNTERS; }
+
+/* Reference gradient of sum_j adj[j] * I_j with respect to every dye concentration voxel and
+ * sigma_s, for the frozen-sampling estimator I_j of or_render over the same paths (same seed,
+ * path ids and majorant). Per path, each tracking decision contributes d log p(decision) times
+ * the adjoint-weighted sensor contributions that follow it:
+ *   null collision:      d log(1 - sigma_t/sigma_bar) = -d sigma_t / (sigma_bar - sigma_t)
+ *   real, particle e:    d log(sigma_e / sigma_bar)   =  d sigma_e / sigma_e
+ * and each sensor contribution its own transmittance derivative d log T = -d tau (Eq. 6, the
+ * exact piecewise-constant optical depth). d sigma_t / d c_d[v] = eps_d a_d(lambda) inside voxel
+ * v; d sigma_t / d sigma_s = s(x). grad_c [n_dyes][nz][ny][nx] (grid scenes only; may be NULL),
+ * grad_sigma_s [1]. */
+int or_adjoint(const or_scene *s, const or_params *p, const double *adj, double *grad_c,
+               double *grad_sigma_s)
+{
+    if (!s || !p || !adj || !grad_sigma_s) return -1;
+    if (s->sensor.kind == 0) return -1;
+    if (s->n_bins <= 0 || s->n_bins > OR_MAX_BINS || s->n_dyes > OR_MAX_DYES) return -1;
+    if (s->n_emitters <= 0 || s->n_emitters > OR_MAX_EMITTERS) return -1;
+    tables *t = (tables *)malloc(sizeof(tables));
+    build_tables(s, t);
+    apply_params(t, p);
+    t->pert_dye = -1;
+    t->pert_sigma_s = 0.0;
+    t->frozen = 0;
+    const int D = s->n_dyes;
+    const int have_grid = s->conc != NULL && grad_c != NULL;
+    const size_t nv = have_grid ? (size_t)nvox(s) : 0;
+    if (have_grid) memset(grad_c, 0, sizeof(double) * (size_t)D * nv);
+    *grad_sigma_s = 0.0;
+#ifdef _OPENMP
+    if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+#endif
+    const int64_t N = (int64_t)p->n_paths;
+    const double inv_n = N > 0 ? 1.0 / (double)N : 0.0;
+#pragma omp parallel
+    {
+        local_tally *lt = (local_tally *)calloc(1, sizeof(local_tally));
+        adj_path A;
+        memset(&A, 0, sizeof(A));
+        A.adj = adj;
+        A.inv_n = inv_n;
+#pragma omp for schedule(dynamic, 32)
+        for (int64_t i = 0; i < N; ++i) {
+            A.n_dec = 0;
+            A.n_con = 0;
+            trace_path(s, t, p, p->path_offset + (uint64_t)i, lt, NULL, &A);
+            double total = 0.0;
+            for (int64_t k = 0; k < A.n_con; ++k) total += A.con[k].a;
+            if (total == 0.0 && A.n_con == 0) continue;
+            double pre = 0.0;
+            int64_t ci = 0;
+            for (int64_t k = 0; k < A.n_dec; ++k) {
+                const dec_rec *r = &A.dec[k];
+                while (ci < A.n_con && A.con[ci].step < r->step) pre += A.con[ci++].a;
+                const double suffix = total - pre;
+                if (suffix == 0.0) continue;
+                if (r->kind == 0) {
+                    const double den = r->sigma_bar - r->sigma_t;
+                    if (have_grid)
+                        for (int d = 0; d < D; ++d) {
+                            const double g = -suffix * t->sig_a[d][r->bin] / den;
+                            if (g != 0.0) {
+#pragma omp atomic
+                                grad_c[(size_t)d * nv + r->voxel] += g;
+                            }
+                        }
+                    if (r->solvent != 0.0) {
+                        const double g = -suffix * r->solvent / den;
+#pragma omp atomic
+                        *grad_sigma_s += g;
+                    }
+                } else if (r->kind == 1) {
+                    const double g = suffix / s->sigma_s;
+#pragma omp atomic
+                    *grad_sigma_s += g;
+                } else if (r->kind == 2 && have_grid) {
+                    const double g = suffix / r->conc;
+#pragma omp atomic
+                    grad_c[(size_t)r->dye * nv + r->voxel] += g;
+                }
+            }
+            for (int64_t k = 0; k < A.n_con; ++k) {
+                const con_rec *c = &A.con[k];
+                tau_grad g = { have_grid ? grad_c : NULL, grad_sigma_s, -c->a };
+                optical_depth_g(s, t, c->x, c->dir, c->L, c->bin, 0, &g);
+            }
+        }
+        free(A.dec);
+        free(A.con);
+        free(lt);
+    }
+    free(t);
+    return 0;
+}

@@ -60,7 +60,9 @@ class Params(C.Structure):
     _fields_ = [("n_paths", C.c_uint64), ("path_offset", C.c_uint64), ("seed", C.c_uint32),
                 ("medium_id", C.c_uint32), ("n_rr", C.c_int), ("max_inelastic", C.c_int),
                 ("analog", C.c_int), ("n_threads", C.c_int), ("max_events", C.c_int64),
-                ("max_steps", C.c_int64)]
+                ("max_steps", C.c_int64), ("majorant_scale", C.c_double), ("frozen", C.c_int),
+                ("pert_dye", C.c_int), ("pert_voxel", C.c_int64), ("pert_delta", C.c_double),
+                ("pert_sigma_s", C.c_double)]
 
 
 class Result(C.Structure):
@@ -106,6 +108,9 @@ def lib():
             L.or_optical_depth.restype = C.c_double
             L.or_majorant.argtypes = [C.POINTER(Scene), C.c_void_p]
             L.or_majorant.restype = None
+            L.or_adjoint.argtypes = [C.POINTER(Scene), C.POINTER(Params), C.c_void_p,
+                                     C.c_void_p, C.c_void_p]
+            L.or_adjoint.restype = C.c_int
             _lib = L
     return _lib
 
@@ -194,12 +199,22 @@ class _SceneHolder:
 
 def render(scene, n_paths=None, path_offset=0, seed=None, medium_id=0, n_threads=0,
            analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
-           film=True, path_events=False):
+           film=True, path_events=False, majorant_scale=1.0, frozen=False, pert=None):
     """Run the oracle; returns a dict of fp64 tallies normalised per launched path:
     face [2,6,B], absorbed [D+1,B], emitted [D,B], film [H,W,B] (or None), counters (dict),
-    path_events u32[n] (or None)."""
+    path_events u32[n] (or None).
+    pert = (dye, voxel, delta, d_sigma_s) evaluates the scene with that perturbation (dye None for
+    none); with frozen=True the decisions are still sampled in the unperturbed scene and every
+    tally carries the likelihood ratio of the decisions before it."""
     L = lib()
     h = _SceneHolder(scene)
+    p = _params(scene, n_paths, path_offset, seed, medium_id, n_threads, analog, max_inelastic,
+                n_rr, max_events, max_steps, majorant_scale, frozen, pert)
+    return _render(L, h, scene, p, film, path_events)
+
+
+def _params(scene, n_paths, path_offset, seed, medium_id, n_threads, analog, max_inelastic, n_rr,
+            max_events, max_steps, majorant_scale, frozen, pert):
     pp = dict(scene["params"])
     for k, v in (("n_paths", n_paths), ("seed", seed), ("analog", analog),
                  ("max_inelastic", max_inelastic), ("n_rr", n_rr), ("max_events", max_events),
@@ -217,6 +232,16 @@ def render(scene, n_paths=None, path_offset=0, seed=None, medium_id=0, n_threads
     p.n_threads = int(n_threads)
     p.max_events = int(pp["max_events"])
     p.max_steps = int(pp.get("max_steps", 100_000_000))
+    p.majorant_scale = float(majorant_scale)
+    p.frozen = 1 if frozen else 0
+    p.pert_dye = -1 if pert is None or pert[0] is None else int(pert[0])
+    p.pert_voxel = 0 if pert is None or pert[0] is None else int(pert[1])
+    p.pert_delta = 0.0 if pert is None or pert[0] is None else float(pert[2])
+    p.pert_sigma_s = 0.0 if pert is None else float(pert[3] if len(pert) > 3 else 0.0)
+    return p
+
+
+def _render(L, h, scene, p, film, path_events):
     B, D = h.n_bins, h.n_dyes
     face = np.zeros((2, 6, B))
     absorbed = np.zeros((D + 1, B))
@@ -291,3 +316,26 @@ def majorant(scene):
     out = np.zeros(h.n_bins)
     lib().or_majorant(C.byref(h.scene), out.ctypes.data)
     return out
+
+
+def adjoint(scene, adj, n_paths=None, path_offset=0, seed=None, medium_id=0, n_threads=0,
+            analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
+            majorant_scale=1.0):
+    """Reference gradient of sum(adj * film) over the same paths render() traces:
+    returns (grad_conc [D,nz,ny,nx] or None, grad_sigma_s)."""
+    L = lib()
+    h = _SceneHolder(scene)
+    p = _params(scene, n_paths, path_offset, seed, medium_id, n_threads, analog, max_inelastic,
+                n_rr, max_events, max_steps, majorant_scale, False, None)
+    adj = np.ascontiguousarray(adj, dtype=np.float64)
+    sn = scene["sensor"]
+    assert adj.shape == (sn["height"], sn["width"], h.n_bins)
+    gc = None
+    if h.conc is not None:
+        gc = np.zeros(h.conc.shape, dtype=np.float64)
+    gs = np.zeros(1, dtype=np.float64)
+    rc = L.or_adjoint(C.byref(h.scene), C.byref(p), adj.ctypes.data,
+                      gc.ctypes.data if gc is not None else None, gs.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle adjoint rejected the scene")
+    return gc, float(gs[0])

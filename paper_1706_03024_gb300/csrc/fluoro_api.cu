@@ -441,7 +441,7 @@ int flr_set_dyes(flr_ctx *ctx, int n, const float *abs_shape, const float *emit_
 int flr_set_sources(flr_ctx *ctx, int n, const flr_source *s)
 {
     if (!ctx) return FLR_ERR_ARG;
-    if (n < 1 || n > FLR_MAX_SOURCES || !s) return fail(ctx, FLR_ERR_ARG, "sources: need 1..64");
+    if (n < 1 || n > FLR_MAX_SOURCES || !s) return fail(ctx, FLR_ERR_ARG, "sources: need 1..65536");
     for (int i = 0; i < n; ++i) {
         const flr_source &q = s[i];
         if (q.kind != FLR_SOURCE_COLLIMATED && q.kind != FLR_SOURCE_LAMBERTIAN)

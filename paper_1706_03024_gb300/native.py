@@ -22,7 +22,7 @@ FLR_ERR_STATE = -5
 FLR_MAX_BINS = 128
 FLR_MAX_DYES = 1024
 FLR_MAX_DYES_PER_MEDIUM = 4
-FLR_MAX_SOURCES = 64
+FLR_MAX_SOURCES = 65536
 FLR_MAX_LINES = 8
 FLR_MAX_EMITTERS = 32
 FLR_NCOUNTERS = 20
