@@ -227,3 +227,4 @@ def flr_batch_read(ctx, face_ptr, absorbed_ptr, emitted_ptr, counters_ptr, strea
 def flr_render_batch(ctx, n_media, media, n_paths_ptr, params, stream=0):
     return load().flr_render_batch(ctx, int(n_media), media, n_paths_ptr, C.byref(params),
                                    C.c_void_p(int(stream)))
+
