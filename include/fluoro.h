@@ -203,6 +203,30 @@ int flr_batch_read(flr_ctx *ctx, double *face, double *absorbed, double *emitted
 int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const uint64_t *n_paths,
                      const flr_params *p, void *stream);
 
+/* Single-scene render that allocates nothing on the device (the paper has no counterpart; it is a
+ * service for callers that cannot call cudaMalloc, such as code whose device memory is owned by
+ * another allocator, or hosts with a fixed memory budget that forbid allocation at run time).
+ * It takes the whole scene by argument, with no context: the spectrum, the dye table (host arrays
+ * as flr_set_dyes takes them; medium->dye_ids index into them), the medium (device grids, as
+ * flr_set_medium takes them), the sources (medium->source_first/count index into them), the
+ * sensor (may be NULL or kind NONE), the parameters (p->film and p->path_events as flr_render),
+ * and host outputs laid out as flr_read_tallies writes them (any may be NULL; tallies divided by
+ * p->n_paths). All scratch -- spectral tables, fixed-point tallies, counters, the work counter and
+ * the interleaved copy of the grids -- lives in one static device array of 4 MiB + 64 KiB that
+ * every GPU loading this library holds until the process exits; media with more than
+ * FLR_NOALLOC_MAX_VOXELS voxels are rejected with FLR_ERR_ARG. The first call on a device looks up
+ * that array's device address (with that device current), so make that first call before any
+ * stream capture. Every call uses the same array and clears what must start at zero, so calls
+ * that overlap on the GPU (other streams, other host threads) race with each other. The call
+ * synchronises `stream` (it reads grid maxima and the tallies back). */
+#define FLR_NOALLOC_MAX_VOXELS (1 << 18)
+int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins, int n_dyes,
+                       const float *abs_shape, const float *emit_spec, const float *eps,
+                       const float *qy, const flr_medium *medium, int n_sources,
+                       const flr_source *sources, const flr_sensor *sensor, const flr_params *p,
+                       double *face, double *absorbed, double *emitted, uint64_t *counters,
+                       void *stream);
+
 /* Synchronise the device and report the device error word (FLR_OK if clean). */
 int flr_status(flr_ctx *ctx);
 const char *flr_last_error(flr_ctx *ctx);

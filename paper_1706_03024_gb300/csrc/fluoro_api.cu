@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -920,3 +921,170 @@ int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const u
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Render without device allocation. Everything the render needs beyond the caller's inputs and
+// outputs sits in one file-scope device array: the small scratch (spectral tables, fixed-point
+// tallies, counters, work counter, grid maxima) in its first 64 KiB, then room for the
+// interleaved copy of up to FLR_NOALLOC_MAX_VOXELS voxels.
+namespace {
+constexpr size_t NA_SMALL = 64 * 1024;
+constexpr size_t NA_TABLES = 0;
+constexpr size_t NA_TALLIES = 8192;
+constexpr size_t NA_COUNTERS = 32768;
+constexpr size_t NA_WORK = 33024;
+constexpr size_t NA_ERROR = 33088;
+constexpr size_t NA_MAXIMA = 33280;
+constexpr size_t NA_BYTES = NA_SMALL + (size_t)FLR_NOALLOC_MAX_VOXELS * sizeof(float4);
+static_assert(NA_TABLES + sizeof(float) * tab_size(FLR_MAX_BINS) <= NA_TALLIES, "tables fit");
+static_assert(NA_TALLIES + sizeof(unsigned long long) * tal_size(FLR_MAX_BINS) <= NA_COUNTERS, "tallies fit");
+static_assert(NA_COUNTERS + sizeof(unsigned long long) * FLR_NCOUNTERS <= NA_WORK, "counters fit");
+static_assert(NA_MAXIMA + 8 * sizeof(unsigned) <= NA_SMALL, "maxima fit");
+
+std::mutex g_na_mutex;
+void *g_na_address[256] = {};
+
+// Device address of the scratch array on the current device, looked up once per device.
+cudaError_t noalloc_address(int dev, unsigned char **out);
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+namespace {
+cudaError_t noalloc_address(int dev, unsigned char **out)
+{
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_address[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_na_address[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_na_address[dev]);
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins, int n_dyes,
+                                  const float *abs_shape, const float *emit_spec, const float *eps,
+                                  const float *qy, const flr_medium *medium, int n_sources,
+                                  const flr_source *sources, const flr_sensor *sensor,
+                                  const flr_params *p, double *face, double *absorbed,
+                                  double *emitted, uint64_t *counters, void *stream)
+{
+    flr_ctx c;  // host-side bookkeeping only: no device buffer of its own
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return FLR_ERR_CUDA;
+    }
+    c.device = dev;
+    int rc = flr_set_spectrum(&c, lambda0_nm, dlambda_nm, n_bins);
+    if (rc == FLR_OK) rc = flr_set_dyes(&c, n_dyes, abs_shape, emit_spec, eps, qy);
+    if (rc == FLR_OK) rc = flr_set_sources(&c, n_sources, sources);
+    if (rc == FLR_OK && sensor && sensor->kind != FLR_SENSOR_NONE) rc = flr_set_sensor(&c, sensor);
+    if (rc == FLR_OK) rc = validate_medium(&c, medium);
+    if (rc != FLR_OK) return rc;
+    if (!p || (p->form != FLR_FORM_PLAIN && p->form != FLR_FORM_WAVEFRONT)) return FLR_ERR_ARG;
+    if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || (p->block_size & 31)))
+        return FLR_ERR_ARG;
+    if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
+        return FLR_ERR_ARG;
+    if (p->film && !is_device_pointer(p->film)) return FLR_ERR_ARG;
+    if (p->path_events && !is_device_pointer(p->path_events)) return FLR_ERR_ARG;
+    if (c.sensor_set && c.sensor.kind == FLR_SENSOR_PINHOLE) {
+        bool inside = true;
+        for (int k = 0; k < 3; ++k)
+            inside = inside && c.sensor.origin[k] >= medium->lo[k] && c.sensor.origin[k] <= medium->hi[k];
+        if (inside) return FLR_ERR_ARG;
+    }
+    flr_medium mm = *medium;
+    const bool grids = medium_has_grid(mm) || mm.solvent;
+    if (!grids) mm.dims[0] = mm.dims[1] = mm.dims[2] = 1;
+    const long long n = nvox(mm);
+    if (n > FLR_NOALLOC_MAX_VOXELS) return FLR_ERR_ARG;  // beyond the static scratch
+    unsigned char *base = nullptr;
+    cudaError_t e = noalloc_address(dev, &base);
+    if (e != cudaSuccess) return FLR_ERR_CUDA;
+    float *tables = reinterpret_cast<float *>(base + NA_TABLES);
+    unsigned long long *tallies = reinterpret_cast<unsigned long long *>(base + NA_TALLIES);
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(base + NA_COUNTERS);
+    unsigned long long *work = reinterpret_cast<unsigned long long *>(base + NA_WORK);
+    int *err_word = reinterpret_cast<int *>(base + NA_ERROR);
+    unsigned *maxima = reinterpret_cast<unsigned *>(base + NA_MAXIMA);
+    float4 *grid = reinterpret_cast<float4 *>(base + NA_SMALL);
+    cudaStream_t st = (cudaStream_t)stream;
+    // grid maxima for the majorant ([0..3] dyes, [4] bad-value flag, [5] solvent present)
+    e = cudaMemsetAsync(maxima, 0, 8 * sizeof(unsigned), st);
+    if (e == cudaSuccess && medium_has_grid(mm)) e = launch_pack_grid(mm.conc, mm.conc_uniform, mm.n_dyes, n, grid, st);
+    for (int d = 0; d < mm.n_dyes && e == cudaSuccess; ++d)
+        if (mm.conc[d]) e = launch_grid_max(mm.conc[d], n, maxima + d, reinterpret_cast<int *>(maxima + 4), st);
+    if (e == cudaSuccess && mm.solvent) e = launch_solvent_any(mm.solvent, n, maxima + 5, st);
+    unsigned hmax[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hmax, maxima, sizeof(hmax), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return FLR_ERR_CUDA;
+    if (hmax[4]) return FLR_ERR_ARG;
+    for (int d = 0; d < mm.n_dyes; ++d) {
+        if (mm.conc[d]) std::memcpy(&c.cmax[d], &hmax[d], sizeof(float));
+        else c.cmax[d] = mm.conc_uniform[d];
+    }
+    c.smax = mm.solvent ? (hmax[5] ? 1.0f : 0.0f) : 1.0f;
+    c.medium = mm;
+    c.medium_set = true;
+    c.d_grid = medium_has_grid(mm) ? grid : nullptr;
+    c.d_tables = tables;
+    build_tables(&c);
+    SceneDev S;
+    rc = fill_scene(&c, S, p->film != nullptr);
+    if (rc != FLR_OK) return rc;
+    e = cudaMemcpyAsync(tables, c.h_tables.data(), sizeof(float) * c.h_tables.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tallies, 0, sizeof(unsigned long long) * tal_size(FLR_MAX_BINS), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * FLR_NCOUNTERS, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err_word, 0, sizeof(int), st);
+    if (e == cudaSuccess && p->film && S.sensor_kind != FLR_SENSOR_NONE && !p->accumulate)
+        e = cudaMemsetAsync(p->film, 0, sizeof(float) * (size_t)S.W * S.H * S.B, st);
+    if (e != cudaSuccess) return FLR_ERR_CUDA;
+    if (p->n_paths > 0) {
+        RunDev R;
+        std::memset(&R, 0, sizeof(R));
+        R.n_paths = p->n_paths;
+        R.path_offset = p->path_offset;
+        R.seed = p->seed;
+        R.medium_id = p->medium_id;
+        R.n_rr = p->n_rr;
+        R.max_inelastic = p->max_inelastic;
+        R.analog = p->analog;
+        R.max_events = p->max_events;
+        R.max_steps = p->max_steps;
+        R.film_scale = (float)(1.0 / (double)p->n_paths);
+        R.film = S.sensor_kind != FLR_SENSOR_NONE ? p->film : nullptr;
+        R.path_events = p->path_events;
+        R.tallies = tallies;
+        R.counters = cnt;
+        R.error_word = err_word;
+        R.work_counter = work;
+        R.regroup = p->regroup_interval;
+        e = launch_trace(S, R, p->form, p->block_size, p->blocks_per_sm, st);
+        if (e != cudaSuccess) return FLR_ERR_CUDA;
+    }
+    std::vector<unsigned long long> t(tal_size(FLR_MAX_BINS));
+    unsigned long long hc[FLR_NCOUNTERS];
+    e = cudaMemcpyAsync(t.data(), tallies, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return FLR_ERR_CUDA;
+    const int B = c.B, D = mm.n_dyes;
+    const double inv = p->n_paths ? 1.0 / ((double)p->n_paths * TALLY_ONE) : 0.0;
+    if (face)
+        for (int i = 0; i < 12 * B; ++i) face[i] = (double)t[tal_face(B) + i] * inv;
+    if (absorbed)
+        for (int i = 0; i < (D + 1) * B; ++i) absorbed[i] = (double)t[tal_absorbed(B) + i] * inv;
+    if (emitted)
+        for (int i = 0; i < D * B; ++i) emitted[i] = (double)t[tal_emitted(B) + i] * inv;
+    if (counters)
+        for (int k = 0; k < FLR_NCOUNTERS; ++k) counters[k] = hc[k];
+    return FLR_OK;
+}

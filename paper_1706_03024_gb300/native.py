@@ -26,6 +26,7 @@ FLR_MAX_SOURCES = 65536
 FLR_MAX_LINES = 8
 FLR_MAX_EMITTERS = 32
 FLR_NCOUNTERS = 20
+FLR_NOALLOC_MAX_VOXELS = 1 << 18
 
 FLR_SOURCE_COLLIMATED = 0
 FLR_SOURCE_LAMBERTIAN = 1
@@ -97,6 +98,11 @@ SIGNATURES = {
                                  C.c_void_p]),
     "flr_render_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(flr_medium), C.c_void_p,
                                    C.POINTER(flr_params), C.c_void_p]),
+    "flr_render_noalloc": (C.c_int, [C.c_float, C.c_float, C.c_int, C.c_int, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(flr_medium),
+                                     C.c_int, C.POINTER(flr_source), C.POINTER(flr_sensor),
+                                     C.POINTER(flr_params), C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]),
     "flr_status": (C.c_int, [C.c_void_p]),
     "flr_last_error": (C.c_char_p, [C.c_void_p]),
     "flr_debug_philox": (C.c_int, [C.c_uint32, C.c_uint32, C.c_void_p, C.c_int64, C.c_void_p,
@@ -228,3 +234,14 @@ def flr_render_batch(ctx, n_media, media, n_paths_ptr, params, stream=0):
     return load().flr_render_batch(ctx, int(n_media), media, n_paths_ptr, C.byref(params),
                                    C.c_void_p(int(stream)))
 
+
+def flr_render_noalloc(lambda0_nm, dlambda_nm, n_bins, n_dyes, abs_shape_ptr, emit_spec_ptr,
+                       eps_ptr, qy_ptr, medium, n_sources, sources, sensor, params, face_ptr,
+                       absorbed_ptr, emitted_ptr, counters_ptr, stream=0):
+    """Single-scene render that allocates no device memory (see include/fluoro.h)."""
+    return load().flr_render_noalloc(float(lambda0_nm), float(dlambda_nm), int(n_bins),
+                                     int(n_dyes), abs_shape_ptr, emit_spec_ptr, eps_ptr, qy_ptr,
+                                     C.byref(medium), int(n_sources), sources,
+                                     C.byref(sensor) if sensor is not None else None,
+                                     C.byref(params), face_ptr, absorbed_ptr, emitted_ptr,
+                                     counters_ptr, C.c_void_p(int(stream)))
