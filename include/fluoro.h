@@ -181,6 +181,21 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream);
 int flr_read_tallies(flr_ctx *ctx, double *face, double *absorbed, double *emitted,
                      uint64_t *counters, void *stream);
 
+/* Adjoint of the single-scene render by path replay (the paper has no derivatives; the estimator
+ * differentiated is the one flr_render evaluates). For the same paths as flr_render with the same
+ * p (n_paths, path_offset, seed, medium_id and every mode flag), adds to device grad_conc
+ * [n_dyes][nz][ny][nx] (the medium's grid layout; may be NULL, and must be NULL for a medium
+ * without grids) and device grad_sigma_s [1] (may be NULL) the gradient of
+ * L = sum_j adj_film[j] * film[j] with respect to every concentration voxel and sigma_s, with the
+ * sampling decisions held at the current values (frozen-sampling estimator): null collisions
+ * score -d sigma_t/(sigma_bar - sigma_t), real collisions with particle e score
+ * d sigma_e/sigma_e (Sec. 4.1 shares), each score multiplied by the adjoint-weighted film
+ * contributions that follow it; every contribution adds its ratio-tracking transmittance
+ * derivative (Eq. 6). device adj_film [H][W][n_bins] (the sensor's film layout). The gradients are
+ * zeroed first unless p->accumulate. Requires a sensor; asynchronous on `stream`. */
+int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float *grad_conc,
+                float *grad_sigma_s, void *stream);
+
 /* Batched persistent form (independent media in one launch). flr_batch_prepare validates n_media
  * media (each as flr_set_medium would; source rows via source_first/source_count, at most 8 lines
  * per medium; the sensor is not used), copies their grids into one library-owned interleaved

@@ -691,6 +691,65 @@ int flr_debug_sample_emission(flr_ctx *ctx, int dye, const float *u, int64_t n, 
 }
 
 // ---------------------------------------------------------------------------------------------
+// Adjoint by path replay.
+
+int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float *grad_conc,
+                float *grad_sigma_s, void *stream)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (!p || !adj_film) return fail(ctx, FLR_ERR_ARG, "adjoint: params and adj_film are required");
+    if (ctx->B <= 0 || !ctx->medium_set || ctx->sources.empty())
+        return fail(ctx, FLR_ERR_STATE, "adjoint: spectrum, dyes, medium and sources must be set");
+    if (!ctx->sensor_set) return fail(ctx, FLR_ERR_STATE, "adjoint: needs a sensor");
+    if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || (p->block_size & 31)))
+        return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
+    if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
+        return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
+    if (!is_device_pointer(adj_film)) return fail(ctx, FLR_ERR_ARG, "adjoint: adj_film must be device memory");
+    if (grad_conc && !medium_has_grid(ctx->medium))
+        return fail(ctx, FLR_ERR_ARG, "adjoint: grad_conc needs a medium with concentration grids");
+    if (grad_conc && !is_device_pointer(grad_conc)) return fail(ctx, FLR_ERR_ARG, "adjoint: grad_conc must be device memory");
+    if (grad_sigma_s && !is_device_pointer(grad_sigma_s))
+        return fail(ctx, FLR_ERR_ARG, "adjoint: grad_sigma_s must be device memory");
+    DeviceGuard g(ctx->device);
+    int rc = prepare_tables(ctx);
+    if (rc != FLR_OK) return rc;
+    SceneDev S;
+    rc = fill_scene(ctx, S, true);
+    if (rc != FLR_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nv = nvox(ctx->medium);
+    cudaError_t e = cudaSuccess;
+    if (!p->accumulate) {
+        if (grad_conc) e = cudaMemsetAsync(grad_conc, 0, sizeof(float) * (size_t)ctx->medium.n_dyes * nv, st);
+        if (e == cudaSuccess && grad_sigma_s) e = cudaMemsetAsync(grad_sigma_s, 0, sizeof(float), st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "clear gradients");
+    }
+    if (p->n_paths == 0) return FLR_OK;
+    RunDev R;
+    std::memset(&R, 0, sizeof(R));
+    R.n_paths = p->n_paths;
+    R.path_offset = p->path_offset;
+    R.seed = p->seed;
+    R.medium_id = p->medium_id;
+    R.n_rr = p->n_rr;
+    R.max_inelastic = p->max_inelastic;
+    R.analog = p->analog;
+    R.max_events = p->max_events;
+    R.max_steps = p->max_steps;
+    R.film_scale = (float)(1.0 / (double)p->n_paths);
+    R.error_word = ctx->d_error;
+    AdjDev A;
+    A.adj = adj_film;
+    A.grad_c = grad_conc;
+    A.nvox = nv;
+    A.grad_sigma_s = grad_sigma_s;
+    e = launch_adjoint(S, R, A, p->block_size, p->blocks_per_sm, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch adjoint kernel");
+    return FLR_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Batched persistent form.
 
 static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem, const char *what)

@@ -112,7 +112,18 @@ struct BatchDev {
     unsigned long long *head;          // next chunk (device counter)
 };
 
+// Adjoint inputs and outputs (device): adj [H][W][B] = dL/dI; grad_c [D][nvox] (or nullptr);
+// grad_sigma_s [1] (or nullptr).
+struct AdjDev {
+    const float *adj;
+    float *grad_c;
+    long long nvox;
+    float *grad_sigma_s;
+};
+
 // Host-side launchers (fluoro_kernels.cu).
+cudaError_t launch_adjoint(const SceneDev &S, const RunDev &R, const AdjDev &A, int block,
+                           int blocks_per_sm, cudaStream_t st);
 cudaError_t launch_batch(const BatchDev &Bt, const RunDev &R, int block, int blocks_per_sm,
                          cudaStream_t st);
 int batch_occupancy_blocks_per_sm(int block);

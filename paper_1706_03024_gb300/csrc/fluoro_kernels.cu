@@ -285,21 +285,28 @@ __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (
 // Transmittance: analytic in homogeneous media, else ratio tracking
 //   T = prod_k (1 - sigma_t(x_k)/sigma_bar) over majorant-distributed points x_k,
 // with roulette (survival 1/2) once the estimate falls below RT_RR_THRESHOLD.
-struct ConnResult { int pix; float val; };
-
-__device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, const Smem &sm,
-                                        float3 x, int b, float w, int lamb, uint64_t pid,
-                                        uint32_t step, RegCnt &rc)
-{
+// Geometry of a connection: direction to the sensor, distance to leave the box, intensity x
+// importance (f * geom) and the film pixel; ok = false when the vertex does not see the sensor.
+struct ConnGeom {
     float3 dir;
+    float tl, gf;
+    int pix;
+    bool ok;
+};
+
+__device__ __forceinline__ ConnGeom connect_geom(const SceneDev &S, const Smem &sm, float3 x, int lamb)
+{
+    ConnGeom g;
+    g.ok = false;
     float geom, r2 = 0.0f;
     int px, py;
+    float3 dir;
     if (S.sensor_kind == FLR_SENSOR_ORTHO) {
         dir = make_float3(S.s_view[0], S.s_view[1], S.s_view[2]);
         const float dx = x.x - S.s_origin[0], dy = x.y - S.s_origin[1], dz = x.z - S.s_origin[2];
         const float su = dx * S.s_U[0] + dy * S.s_U[1] + dz * S.s_U[2];
         const float sv = dx * S.s_V[0] + dy * S.s_V[1] + dz * S.s_V[2];
-        if (!(su >= 0.0f && su < 1.0f && sv >= 0.0f && sv < 1.0f)) return;
+        if (!(su >= 0.0f && su < 1.0f && sv >= 0.0f && sv < 1.0f)) return g;
         px = min(__float2int_rd(su * (float)S.W), S.W - 1);
         py = min(__float2int_rd(sv * (float)S.H), S.H - 1);
         geom = S.inv_A_pix;
@@ -307,13 +314,13 @@ __device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, cons
         const float vx = x.x - S.s_origin[0], vy = x.y - S.s_origin[1], vz = x.z - S.s_origin[2];
         r2 = vx * vx + vy * vy + vz * vz;
         const float zf = vx * S.s_view[0] + vy * S.s_view[1] + vz * S.s_view[2];
-        if (!(zf > 0.0f)) return;
+        if (!(zf > 0.0f)) return g;
         const float izf = __frcp_rn(zf);
         const float X = (vx * S.s_U[0] + vy * S.s_U[1] + vz * S.s_U[2]) * izf;
         const float Y = (vx * S.s_V[0] + vy * S.s_V[1] + vz * S.s_V[2]) * izf;
         const float sx = 0.5f * (X / S.tan_x + 1.0f);
         const float sy = 0.5f * (Y / S.tan_y + 1.0f);
-        if (!(sx >= 0.0f && sx < 1.0f && sy >= 0.0f && sy < 1.0f)) return;
+        if (!(sx >= 0.0f && sx < 1.0f && sy >= 0.0f && sy < 1.0f)) return g;
         px = min(__float2int_rd(sx * (float)S.W), S.W - 1);
         py = min(__float2int_rd(sy * (float)S.H), S.H - 1);
         const float ir = rsqrtf(r2);
@@ -325,7 +332,7 @@ __device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, cons
     if (lamb >= 0) {
         const int axis = lamb >> 1;
         const float co = (lamb & 1) ? comp(dir, axis) : -comp(dir, axis);
-        if (!(co > 0.0f)) return;
+        if (!(co > 0.0f)) return g;
         f = co * INV_PI;
     } else {
         f = INV_4PI;
@@ -334,52 +341,88 @@ __device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, cons
     int face;
     const float3 idr = inv_dir(dir);
     const float tl = exit_distance(m, x, dir, idr, face);
-    if (face < 0) return;
-    if (S.wall_mask & (1 << face)) return;
-    if (S.sensor_kind == FLR_SENSOR_PINHOLE && tl * tl > r2) return;
-    rc.connections++;
+    if (face < 0) return g;
+    if (S.wall_mask & (1 << face)) return g;
+    if (S.sensor_kind == FLR_SENSOR_PINHOLE && tl * tl > r2) return g;
+    g.dir = dir;
+    g.tl = tl;
+    g.gf = f * geom;
+    g.pix = py * S.W + px;
+    g.ok = true;
+    return g;
+}
+
+// Transmittance estimate along the connection (Eq. 6): analytic in homogeneous media, else ratio
+// tracking T = prod_k (1 - sigma_t(x_k)/sigma_bar) over majorant-distributed points with roulette
+// (survival 1/2) below RT_RR_THRESHOLD. The sink G sees every ratio-tracking point (the adjoint
+// accumulates d log T there); NoSink is the forward's.
+struct NoSink {
+    __device__ __forceinline__ void point(float3, int, float, float) const {}
+    __device__ __forceinline__ void homogeneous(float) const {}
+};
+
+template <class G>
+__device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                               float3 x, float3 dir, float tl, int b, uint64_t pid,
+                                               uint32_t step, RegCnt &rc, const G &sink)
+{
+    const MedS m{S, sm};
     const float sb = sm.maj[b];
     float T = 1.0f;
-    if (sb > 0.0f) {
-        if (S.homogeneous) {
-            T = __expf(-sigma_t_at(m, x, b) * tl);
-        } else {
-            const float isb = __frcp_rn(sb);
-            float t = 0.0f;
-            U4 blk = U4{0, 0, 0, 0};
-            uint32_t j = 0;
-            int it = 0;
-            for (; it < MAX_CONNECT_STEPS; ++it) {
-                if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
-                const uint32_t q = j & 3u;
-                const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
-                ++j;
-                t -= __logf(1.0f - u) * isb;
-                if (t >= tl) break;
-                rc.connect_steps++;
-                const float3 p = make_float3(x.x + t * dir.x, x.y + t * dir.y, x.z + t * dir.z);
-                T *= fmaxf(0.0f, 1.0f - sigma_t_at(m, p, b) * isb);
-                if (T < RT_RR_THRESHOLD) {
-                    if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
-                    const uint32_t q2 = j & 3u;
-                    const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
-                    ++j;
-                    if (u2 < 0.5f) {
-                        T *= 2.0f;
-                    } else {
-                        T = 0.0f;
-                        break;
-                    }
-                }
-            }
-            if (it == MAX_CONNECT_STEPS) {
+    if (!(sb > 0.0f)) return T;
+    if (S.homogeneous) {
+        sink.homogeneous(tl);
+        return __expf(-sigma_t_at(m, x, b) * tl);
+    }
+    const float isb = __frcp_rn(sb);
+    float t = 0.0f;
+    U4 blk = U4{0, 0, 0, 0};
+    uint32_t j = 0;
+    int it = 0;
+    for (; it < MAX_CONNECT_STEPS; ++it) {
+        if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
+        const uint32_t q = j & 3u;
+        const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
+        ++j;
+        t -= __logf(1.0f - u) * isb;
+        if (t >= tl) break;
+        rc.connect_steps++;
+        const float3 p = make_float3(x.x + t * dir.x, x.y + t * dir.y, x.z + t * dir.z);
+        const float st = sigma_t_at(m, p, b);
+        sink.point(p, b, st, sb);
+        T *= fmaxf(0.0f, 1.0f - st * isb);
+        if (T < RT_RR_THRESHOLD) {
+            if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
+            const uint32_t q2 = j & 3u;
+            const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
+            ++j;
+            if (u2 < 0.5f) {
+                T *= 2.0f;
+            } else {
                 T = 0.0f;
-                cnt_add(sm, FLR_C_CONNECT_BUDGET);
+                break;
             }
         }
     }
-    const float val = w * f * T * geom * R.film_scale;
-    if (val > 0.0f) atomicAdd(&R.film[((size_t)py * S.W + px) * S.B + b], val);
+    if (it == MAX_CONNECT_STEPS) {
+        T = 0.0f;
+        cnt_add(sm, FLR_C_CONNECT_BUDGET);
+    }
+    return T;
+}
+
+// Sensor connection (Eq. 3-6). `lamb` < 0: isotropic vertex, intensity w/(4 pi); otherwise a
+// Lambertian vertex with normal sign*e_axis (lamb = 2*axis + (sign > 0)), intensity w cos/pi.
+__device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                        float3 x, int b, float w, int lamb, uint64_t pid,
+                                        uint32_t step, RegCnt &rc)
+{
+    const ConnGeom g = connect_geom(S, sm, x, lamb);
+    if (!g.ok) return;
+    rc.connections++;
+    const float T = transmittance(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, NoSink{});
+    const float val = w * g.gf * T * R.film_scale;
+    if (val > 0.0f) atomicAdd(&R.film[(size_t)g.pix * S.B + b], val);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -458,11 +501,17 @@ __device__ __forceinline__ Conn spawn(const M &m, const RunDev &R, const Smem &s
     return c;
 }
 
+// Observer of the tracking decisions (the adjoint replay scores them); NoObs is the forward's.
+struct NoObs {
+    __device__ __forceinline__ void null_event(float3, int, const Coeffs &, float) const {}
+    __device__ __forceinline__ void real_event(float3, int, const Coeffs &, int) const {}
+};
+
 // One tracking step (null or real collision, wall bounce or escape). Returns the connection the
 // step asks for, if any.
-template <class M>
+template <class M, class Obs = NoObs>
 __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Smem &sm, Path &p,
-                                           RegCnt &rc)
+                                           RegCnt &rc, const Obs &obs = Obs())
 {
     Conn c;
     c.valid = false;
@@ -525,6 +574,7 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
     if (k.total > sb) cnt_add(sm, FLR_C_MAJORANT_VIOLATIONS);
     if (!(b0.b * sb < k.total)) {
         rc.nulls++;
+        obs.null_event(p.x, p.bin, k, sb);
         return c;
     }
     if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
@@ -546,6 +596,7 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
             }
         }
     }
+    obs.real_event(p.x, p.bin, k, ev);
     if (ev < 0) {
         rc.scatters++;
         p.w = iso_dir(b0.d, b1.a);
@@ -787,6 +838,143 @@ __global__ void __launch_bounds__(256) k_trace_wavefront(SceneDev S, RunDev R)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Adjoint (path replay). For L = sum_j adj_j I_j of the film estimator over the same paths, with
+// decisions frozen at the current parameters, dL/dtheta per path is
+//   sum_i d log p(decision_i) * (adjoint-weighted contributions after decision i)
+//   + sum_k a_k d log T_k,
+// where null collisions score -d sigma_t / (sigma_bar - sigma_t), a real collision with particle e
+// scores d sigma_e / sigma_e, and T_k is the ratio-tracking transmittance of contribution k
+// (d log T = sum over its points of -d sigma_t / (sigma_bar - sigma_t)). d sigma_t / d c_d[v] is
+// eps_d a_d(lambda) inside voxel v, d sigma_t / d sigma_s is s(x). Each path is replayed twice from
+// its Philox key: pass 1 sums its contributions a_k = adj[pixel][bin] * value_k; pass 2 walks the
+// decisions again with the suffix sum and re-marches each contribution with a gradient sink.
+struct AdjSink {
+    const SceneDev &S;
+    const Smem &sm;
+    const AdjDev &A;
+    float scale;
+    float *gsig;
+    __device__ __forceinline__ void point(float3 p, int b, float st, float sb) const
+    {
+        const float den = sb - st;
+        if (!(den > 0.0f)) return;
+        const float q = -scale / den;
+        const MedS m{S, sm};
+        const int v = voxel_of(m, p);
+        if (A.grad_c && S.grid)
+            for (int d = 0; d < S.D; ++d) {
+                const float g = q * sm.sig_a[d * S.B + b];
+                if (g != 0.0f) atomicAdd(&A.grad_c[(size_t)d * A.nvox + v], g);
+            }
+        const float sv = S.solvent ? (__ldg(&S.solvent[v]) ? 1.0f : 0.0f) : 1.0f;
+        *gsig += q * sv;
+    }
+    __device__ __forceinline__ void homogeneous(float tl) const { *gsig += -scale * tl; }
+};
+
+struct AdjObs {
+    const SceneDev &S;
+    const Smem &sm;
+    const AdjDev &A;
+    float suffix;
+    float *gsig;
+    __device__ __forceinline__ void null_event(float3 x, int b, const Coeffs &k, float sb) const
+    {
+        if (suffix == 0.0f) return;
+        const float den = sb - k.total;
+        if (!(den > 0.0f)) return;
+        const float q = -suffix / den;
+        const MedS m{S, sm};
+        int v = 0;
+        if (!S.homogeneous) v = voxel_of(m, x);
+        if (A.grad_c && S.grid)
+            for (int d = 0; d < S.D; ++d) {
+                const float g = q * sm.sig_a[d * S.B + b];
+                if (g != 0.0f) atomicAdd(&A.grad_c[(size_t)d * A.nvox + v], g);
+            }
+        const float sv = S.solvent ? (__ldg(&S.solvent[v]) ? 1.0f : 0.0f) : 1.0f;
+        *gsig += q * sv;
+    }
+    __device__ __forceinline__ void real_event(float3 x, int b, const Coeffs &k, int ev) const
+    {
+        if (suffix == 0.0f) return;
+        if (ev < 0) {
+            *gsig += suffix / S.sigma_s;
+        } else if (ev < S.D && A.grad_c && S.grid && k.dye[ev] > 0.0f) {
+            const MedS m{S, sm};
+            const int v = voxel_of(m, x);
+            atomicAdd(&A.grad_c[(size_t)ev * A.nvox + v], suffix * sm.sig_a[ev * S.B + b] / k.dye[ev]);
+        }
+    }
+};
+
+__device__ __forceinline__ float adjoint_weight(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                                const AdjDev &A, const Conn &c, RegCnt &rc)
+{
+    const ConnGeom g = connect_geom(S, sm, c.x, c.lamb);
+    if (!g.ok) return 0.0f;
+    const float T = transmittance(S, R, sm, c.x, g.dir, g.tl, c.bin, c.pid, c.step, rc, NoSink{});
+    const float val = c.w * g.gf * T * R.film_scale;
+    if (!(val > 0.0f)) return 0.0f;
+    return __ldg(&A.adj[(size_t)g.pix * S.B + c.bin]) * val;
+}
+
+__device__ __forceinline__ void adjoint_march(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                              const AdjDev &A, const Conn &c, float a, float *gsig,
+                                              RegCnt &rc)
+{
+    const ConnGeom g = connect_geom(S, sm, c.x, c.lamb);
+    if (!g.ok) return;
+    transmittance(S, R, sm, c.x, g.dir, g.tl, c.bin, c.pid, c.step, rc, AdjSink{S, sm, A, a, gsig});
+}
+
+__global__ void __launch_bounds__(256) k_adjoint(SceneDev S, RunDev R, AdjDev A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L);
+    const MedS m{S, sm};
+    RegCnt rc = {0, 0, 0, 0, 0, 0};
+    float gsig = 0.0f;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
+        const uint64_t pid = R.path_offset + i;
+        // pass 1: total adjoint-weighted contribution of the path
+        Path p;
+        Conn c = spawn(m, R, sm, pid, p);
+        float total = 0.0f;
+        bool any = false;
+        if (c.valid) { const float a = adjoint_weight(S, R, sm, A, c, rc); total += a; any |= a != 0.0f; }
+        while (p.alive) {
+            c = track_step(m, R, sm, p, rc);
+            if (c.valid) { const float a = adjoint_weight(S, R, sm, A, c, rc); total += a; any |= a != 0.0f; }
+        }
+        if (!any) continue;
+        // pass 2: scores times suffix sums, and transmittance derivatives
+        float pre = 0.0f;
+        c = spawn(m, R, sm, pid, p);
+        if (c.valid) {
+            const float a = adjoint_weight(S, R, sm, A, c, rc);
+            if (a != 0.0f) adjoint_march(S, R, sm, A, c, a, &gsig, rc);
+            pre += a;
+        }
+        AdjObs obs{S, sm, A, total - pre, &gsig};
+        while (p.alive) {
+            c = track_step(m, R, sm, p, rc, obs);
+            if (c.valid) {
+                const float a = adjoint_weight(S, R, sm, A, c, rc);
+                if (a != 0.0f) adjoint_march(S, R, sm, A, c, a, &gsig, rc);
+                pre += a;
+                obs.suffix = total - pre;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gsig += __shfl_xor_sync(0xffffffffu, gsig, o);
+    if ((threadIdx.x & 31) == 0 && gsig != 0.0f && A.grad_sigma_s) atomicAdd(A.grad_sigma_s, gsig);
+}
+
+// ---------------------------------------------------------------------------------------------
 // Batched persistent form: independent media in one launch. A device queue holds chunks of
 // consecutive path ids of one medium (ordered longest expected paths first). Each warp owns one
 // chunk at a time and hands its path ids to lanes as their paths end (regeneration), so a lane
@@ -992,6 +1180,23 @@ cudaError_t launch_batch(const BatchDev &Bt, const RunDev &R, int block, int blo
     if (blocks_per_sm <= 0 || blocks_per_sm > occ) blocks_per_sm = occ;
     const long long grid = (long long)num_sms() * blocks_per_sm;
     k_trace_batch<<<(unsigned)grid, block, 0, st>>>(Bt, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const SceneDev &S, const RunDev &R, const AdjDev &A, int block,
+                           int blocks_per_sm, cudaStream_t st)
+{
+    if (block <= 0) block = trace_block_default();
+    const int smem = trace_smem_bytes(S.B, FLR_FORM_PLAIN, block);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint, block, smem);
+    if (occ < 1) occ = 1;
+    if (blocks_per_sm <= 0 || blocks_per_sm > occ) blocks_per_sm = occ;
+    long long grid = (long long)num_sms() * blocks_per_sm;
+    const long long need = ((long long)R.n_paths + block - 1) / block;
+    if (need < grid) grid = need;
+    if (grid < 1) grid = 1;
+    k_adjoint<<<(unsigned)grid, block, smem, st>>>(S, R, A);
     return cudaGetLastError();
 }
 

@@ -91,6 +91,8 @@ SIGNATURES = {
     "flr_render": (C.c_int, [C.c_void_p, C.POINTER(flr_params), C.c_void_p]),
     "flr_read_tallies": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]),
+    "flr_adjoint": (C.c_int, [C.c_void_p, C.POINTER(flr_params), C.c_void_p, C.c_void_p,
+                              C.c_void_p, C.c_void_p]),
     "flr_batch_prepare": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(flr_medium), C.c_void_p,
                                     C.POINTER(flr_params)]),
     "flr_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -215,6 +217,11 @@ def flr_debug_philox(seed, medium, ctr_ptr, n, out_ptr, stream=0):
 def flr_debug_sample_emission(ctx, dye, u_ptr, n, out_ptr, stream=0):
     return load().flr_debug_sample_emission(ctx, int(dye), u_ptr, int(n), out_ptr,
                                             C.c_void_p(int(stream)))
+
+
+def flr_adjoint(ctx, params, adj_ptr, grad_conc_ptr, grad_sigma_s_ptr, stream=0):
+    return load().flr_adjoint(ctx, C.byref(params), adj_ptr, grad_conc_ptr, grad_sigma_s_ptr,
+                              C.c_void_p(int(stream)))
 
 
 def flr_batch_prepare(ctx, n_media, media, n_paths_ptr, params):

@@ -131,10 +131,17 @@ class Scene:
                                     device=torch.device("cuda", self.device))
         return self.film
 
-    def render(self, n_paths=None, path_offset=0, seed=None, medium_id=0, form="plain",
-               analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
-               film=True, path_events=None, accumulate=False, block_size=0, blocks_per_sm=0,
-               regroup=0, stream=None):
+    def set_medium_values(self, conc, sigma_s):
+        """Re-upload the medium from a CUDA concentration tensor [D,nz,ny,nx] and a sigma_s."""
+        md = dict(self.desc["medium"])
+        md["sigma_s"] = float(sigma_s)
+        self.desc = dict(self.desc)
+        self.desc["medium"] = md
+        self.set_medium(md, grids={"conc": conc, "solvent": self.solv_t})
+
+    def _params(self, n_paths=None, path_offset=0, seed=None, medium_id=0, form="plain",
+                analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
+                accumulate=False, block_size=0, blocks_per_sm=0, regroup=0):
         pp = dict(self.desc["params"])
         for k, v in (("n_paths", n_paths), ("seed", seed), ("analog", analog),
                      ("max_inelastic", max_inelastic), ("n_rr", n_rr), ("max_events", max_events),
@@ -152,16 +159,38 @@ class Scene:
         p.form = _FORMS[form] if isinstance(form, str) else int(form)
         p.max_events = int(pp["max_events"])
         p.max_steps = int(pp.get("max_steps", 100_000_000))
-        f = self.film_tensor() if film else None
-        p.film = f.data_ptr() if f is not None else None
-        p.path_events = path_events.data_ptr() if path_events is not None else None
         p.accumulate = 1 if accumulate else 0
         p.block_size = int(block_size)
         p.blocks_per_sm = int(blocks_per_sm)
         p.regroup_interval = int(regroup)
+        return p
+
+    def render(self, n_paths=None, path_offset=0, seed=None, medium_id=0, form="plain",
+               analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
+               film=True, path_events=None, accumulate=False, block_size=0, blocks_per_sm=0,
+               regroup=0, stream=None):
+        p = self._params(n_paths, path_offset, seed, medium_id, form, analog, max_inelastic, n_rr,
+                         max_events, max_steps, accumulate, block_size, blocks_per_sm, regroup)
+        f = self.film_tensor() if film else None
+        p.film = f.data_ptr() if f is not None else None
+        p.path_events = path_events.data_ptr() if path_events is not None else None
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         N.check(N.flr_render(self.ctx, p, st.cuda_stream), self.ctx, "flr_render")
         return f
+
+    def adjoint(self, adj, grad_conc=None, grad_sigma_s=None, n_paths=None, path_offset=0,
+                seed=None, medium_id=0, analog=None, max_inelastic=None, n_rr=None,
+                max_events=None, max_steps=None, accumulate=False, block_size=0, stream=None):
+        """Path-replay gradient of sum(adj * film) for the paths render() traces with the same
+        arguments; writes into grad_conc [D,nz,ny,nx] and grad_sigma_s [1] (CUDA f32 tensors)."""
+        p = self._params(n_paths, path_offset, seed, medium_id, "plain", analog, max_inelastic,
+                         n_rr, max_events, max_steps, accumulate, block_size)
+        adj = adj.contiguous()
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        N.check(N.flr_adjoint(self.ctx, p, adj.data_ptr(),
+                              grad_conc.data_ptr() if grad_conc is not None else None,
+                              grad_sigma_s.data_ptr() if grad_sigma_s is not None else None,
+                              st.cuda_stream), self.ctx, "flr_adjoint")
 
     def read(self, stream=None):
         B, D = self.B, self.D
@@ -189,6 +218,37 @@ class Scene:
             self.close()
         except Exception:
             pass
+
+
+class FluoroRender(torch.autograd.Function):
+    """film = render(conc, sigma_s) through flr_render; backward is flr_adjoint (path replay of
+    the same paths, gradient of the frozen-sampling estimator).
+
+    Usage: film = FluoroRender.apply(conc, sigma_s, scene, opts) with conc a CUDA f32 tensor
+    [D,nz,ny,nx], sigma_s a 0-d tensor, scene a Scene and opts the render keyword arguments
+    (n_paths, seed, path_offset, ...)."""
+
+    @staticmethod
+    def forward(ctx, conc, sigma_s, scene, opts):
+        conc_c = conc.detach().contiguous()
+        scene.set_medium_values(conc_c, float(sigma_s))
+        film = scene.render(form=opts.get("form", "wavefront"),
+                            **{k: v for k, v in opts.items() if k != "form"}).clone()
+        ctx.save_for_backward(conc_c, sigma_s.detach())
+        ctx.scene = scene
+        ctx.opts = opts
+        return film
+
+    @staticmethod
+    def backward(ctx, grad_film):
+        conc, sigma_s = ctx.saved_tensors
+        S = ctx.scene
+        S.set_medium_values(conc, float(sigma_s))
+        gc = torch.empty_like(conc) if ctx.needs_input_grad[0] else None
+        gs = torch.empty(1, dtype=torch.float32, device=conc.device)
+        opts = {k: v for k, v in ctx.opts.items() if k not in ("form", "regroup")}
+        S.adjoint(grad_film.float(), gc, gs, **opts)
+        return gc, gs.reshape(()).to(sigma_s.dtype), None, None
 
 
 class Batch:

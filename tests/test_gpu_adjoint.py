@@ -1,0 +1,159 @@
+"""Path-replay adjoint on the GPU (flr_adjoint, FluoroRender) against the oracle's reference
+gradient, a closed form, central differences with common random numbers, and its own linearity.
+
+The oracle's gradient (tests/test_oracle_adjoint.py) is pinned to frozen-sampling central
+differences and a closed form; the GPU's must agree with it statistically (the GPU estimates each
+transmittance by ratio tracking, the oracle evaluates it exactly, so per path they differ).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenegen as sg
+from paper_1706_03024_gb300.scene import FluoroRender, Scene
+from tests.gpu_common import require_gpu
+from tests.stats import batch_mean_se, parity_verdict
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def adjoint_scene(n=12, W=12, sigma_s=10.0, n_paths=4000):
+    rng = np.random.default_rng(100)
+    conc = np.stack([sg.blob_field(rng, n, 8, (1.5, 3.5)) for _ in range(2)])
+    conc /= conc.reshape(2, -1).mean(axis=1)[:, None, None, None]
+    dyes = sg.make_dyes([470.0, 560.0], [15.0, 15.0], [520.0, 610.0], [20.0, 20.0],
+                        eps=[1.5, 1.0], qy=[0.8, 0.6])
+    return {"spectrum": sg.spectrum(), "dyes": dyes,
+            "medium": sg.grid_medium(conc.astype(np.float32), None, sigma_s=sigma_s),
+            "sources": [sg.rect_source("collimated", (0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1),
+                                       [470.0, 560.0])],
+            "sensor": sg.ortho_sensor(W, W, (0, 0, 1), (1, 0, 0), (0, 1, 0), (0, 0, 1)),
+            "params": sg.params(n_paths, seed=1)}
+
+
+def gpu_adjoint(S, adj, n, offset=0, seed=None):
+    gc = torch.zeros(S.conc_t.shape, dtype=torch.float32, device="cuda")
+    gs = torch.zeros(1, dtype=torch.float32, device="cuda")
+    S.adjoint(torch.from_numpy(adj.astype(np.float32)).cuda(), gc, gs, n_paths=n,
+              path_offset=offset, seed=seed)
+    return gc.double().cpu().numpy(), float(gs.item())
+
+
+def test_adjoint_matches_oracle_reference_gradient():
+    sc = adjoint_scene()
+    S = Scene(sc)
+    rng = np.random.default_rng(5)
+    adj = rng.normal(size=(12, 12, sg.N_BINS))
+    K, n = 16, 4000
+    g = [gpu_adjoint(S, adj, n, k * n) for k in range(K)]
+    o = [oracle.adjoint(sc, adj, n_paths=n, path_offset=k * n) for k in range(K)]
+    mg, sg_ = batch_mean_se([x[0] for x in g])
+    mo, so = batch_mean_se([x[0] for x in o])
+    v = parity_verdict(mg, sg_, mo, so, check_chi2=False)
+    assert v["ok"], v
+    # the per-dye total and the sigma_s derivative
+    for d in range(2):
+        a, sa = batch_mean_se([x[0][d].sum() for x in g])
+        b, sb = batch_mean_se([x[0][d].sum() for x in o])
+        assert abs(a - b) <= 3 * math.hypot(sa, sb), (d, a, b)
+    a, sa = batch_mean_se([x[1] for x in g])
+    b, sb = batch_mean_se([x[1] for x in o])
+    assert abs(a - b) <= 3 * math.hypot(sa, sb), (a, b)
+    assert np.abs(mo).max() > 0
+
+
+def test_adjoint_closed_form_column():
+    """Lambertian point light on the floor of a non-scattering absorbing grid, ortho camera above:
+    E[dI/dc_v] = -sigma_a h I on the light's column, and exactly zero elsewhere."""
+    n, W = 6, 6
+    rng = np.random.default_rng(9)
+    conc = rng.uniform(0.2, 1.5, size=(1, n, n, n)).astype(np.float32)
+    dyes = sg.make_dyes([490.0], [15.0], [620.0], [15.0], eps=[0.7], qy=[0.0])
+    p = (0.55, 0.25, 0.0)
+    sc = {"spectrum": sg.spectrum(), "dyes": dyes, "medium": sg.grid_medium(conc, None),
+          "sources": [sg.rect_source("lambertian", p, (0, 0, 0), (0, 0, 0), (0, 0, 1), [490.0])],
+          "sensor": sg.ortho_sensor(W, W, (0, 0, 1), (1, 0, 0), (0, 1, 0), (0, 0, 1)),
+          "params": sg.params(20000, seed=2)}
+    b = int(math.ceil((490 - sg.LAMBDA0) / sg.DLAMBDA - 0.5))
+    px, py = int(p[0] * W), int(p[1] * W)
+    ix, iy = int(p[0] * n), int(p[1] * n)
+    sa = float(dyes["eps"][0]) * float(dyes["abs_shape"][0, b])
+    I = math.exp(-sa * conc[0, :, iy, ix].astype(np.float64).sum() / n) / math.pi * W * W
+    adj = np.zeros((W, W, sg.N_BINS))
+    adj[py, px, b] = 1.0
+    S = Scene(sc)
+    K, N = 16, 20000
+    runs = [gpu_adjoint(S, adj, N, k * N) for k in range(K)]
+    m, se = batch_mean_se([r[0] for r in runs])
+    want = np.zeros_like(m)
+    want[0, :, iy, ix] = -sa / n * I
+    mask = np.zeros(m.shape, bool)
+    mask[0, :, iy, ix] = True
+    assert (m[~mask] == 0).all()
+    assert np.all(np.abs(m[mask] - want[mask]) <= 3.5 * se[mask] + 1e-6 * I), (m[mask], want[mask])
+    ms, ss = batch_mean_se([r[1] for r in runs])
+    assert abs(ms + I) <= 3.5 * ss + 1e-6 * I
+
+
+def test_autograd_function_and_central_difference_in_sigma_s():
+    sc = adjoint_scene(n_paths=200_000)
+    S = Scene(sc)
+    conc = torch.from_numpy(sc["medium"]["conc"]).cuda()
+    target_sc = adjoint_scene(n_paths=200_000)
+    target = Scene(target_sc).render(form="wavefront", seed=99).clone() * 1.3
+    opts = {"n_paths": 200_000, "seed": 3}
+    c = conc.clone().requires_grad_(True)
+    s = torch.tensor(10.0, dtype=torch.float64, requires_grad=True)
+    film = FluoroRender.apply(c, s, S, opts)
+    loss = ((film.double() - target.double()) ** 2).sum()
+    loss.backward()
+    # backward equals flr_adjoint with adj = dL/dI = 2 (I - T)
+    adj = (2.0 * (film.detach().double() - target.double())).float()
+    gc = torch.zeros_like(conc)
+    gs = torch.zeros(1, device="cuda")
+    S.set_medium_values(conc, 10.0)
+    S.adjoint(adj, gc, gs, **opts)
+    assert torch.allclose(c.grad, gc, rtol=1e-3, atol=1e-6 * float(gc.abs().max()))
+    assert abs(float(s.grad) - float(gs)) <= 1e-3 * abs(float(gs))
+    # central difference in sigma_s with common random numbers (a smooth enough direction: every
+    # free-flight length rescales with the majorant)
+    h = 0.02 * 10.0
+
+    def L(sig):
+        S.set_medium_values(conc, sig)
+        f = S.render(form="wavefront", **opts)
+        return float(((f.double() - target.double()) ** 2).sum())
+    fd = (L(10.0 + h) - L(10.0 - h)) / (2 * h)
+    g = float(s.grad)
+    assert np.sign(fd) == np.sign(g) and abs(fd - g) <= 0.25 * abs(g), (fd, g)
+
+
+def test_adjoint_full_size_linearity_and_finiteness():
+    """The 64^3 x 2 dyes / 256x256 / 32 spp workload: gradients are finite and linear in the
+    adjoint film (a property that holds at any size)."""
+    sc = sg.cfg4_adjoint()
+    S = Scene(sc)
+    n = sc["params"]["n_paths"]
+    rng = np.random.default_rng(1)
+    a1 = torch.from_numpy(rng.normal(size=(256, 256, sg.N_BINS)).astype(np.float32)).cuda()
+    a2 = torch.from_numpy(rng.normal(size=(256, 256, sg.N_BINS)).astype(np.float32)).cuda()
+    out = []
+    for adj in (a1, a2, a1 + 2.0 * a2):
+        gc = torch.zeros(S.conc_t.shape, device="cuda")
+        gs = torch.zeros(1, device="cuda")
+        S.adjoint(adj, gc, gs, n_paths=n)
+        out.append((gc.double(), float(gs)))
+    assert all(torch.isfinite(o[0]).all() for o in out)
+    comb = out[0][0] + 2.0 * out[1][0]
+    scale = float(comb.abs().max())
+    assert scale > 0
+    assert torch.allclose(out[2][0], comb, rtol=1e-3, atol=1e-4 * scale)
+    assert abs(out[2][1] - (out[0][1] + 2 * out[1][1])) <= 1e-3 * (abs(out[0][1]) + 2 * abs(out[1][1]))
