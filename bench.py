@@ -152,7 +152,7 @@ def bench_batched(args, local, rank, flush, stream, barrier, reduce_max, reduce_
     import torch
     from paper_1706_03024_gb300.scene import Batch, Scene
 
-    media = sg.cfg3_batched_media(n_media=256, seed=0)
+    media = sg.cfg3_batched_media(n_media=args.batch_media, seed=0)
     bt = Batch(media, device=local, seed=rank, medium_id=0)
     for _ in range(max(1, args.warmup - 2)):
         bt.launch()
@@ -208,6 +208,55 @@ def bench_batched(args, local, rank, flush, stream, barrier, reduce_max, reduce_
             "events_per_step": counters["events"],
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                          "unit": "Tops/s", "frac": achieved / peak}}
+
+
+def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum):
+    """Gradient of sum((I - T)^2) over the 256x256x81 film w.r.t. 2 x 64^3 concentrations and
+    sigma_s (32 paths per pixel): the forward (wavefront and plain) and the path-replay adjoint on
+    the same paths, so every form carries the same estimator."""
+    import torch
+    from paper_1706_03024_gb300.scene import Scene
+
+    sc = sg.cfg4_adjoint(field_seed=0, seed=rank)
+    if args.adjoint_paths:
+        sc["params"]["n_paths"] = int(args.adjoint_paths)
+    n = sc["params"]["n_paths"]
+    tgt_sc = sg.cfg4_adjoint(field_seed=1, seed=1000 + rank)
+    tgt_sc["params"]["n_paths"] = min(8 * n, 1 << 24)
+    T = Scene(tgt_sc, device=local).render(form="wavefront").clone()
+    S = Scene(sc, device=local)
+    gc = torch.zeros(S.conc_t.shape, dtype=torch.float32, device=torch.device("cuda", local))
+    gs = torch.zeros(1, dtype=torch.float32, device=gc.device)
+    film = S.render(form="wavefront")
+    adj = (2.0 * (film - T)).contiguous()
+    S.adjoint(adj, gc, gs)
+    torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        ms = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return reduce_max(sum(ms) / len(ms)), ms
+
+    barrier()
+    fwd_ms, _ = timed(lambda: S.render(form="wavefront"), args.adjoint_steps)
+    events = S.read()["counters"]["events"]
+    plain_ms, _ = timed(lambda: S.render(form="plain"), args.adjoint_steps)
+    adj_ms, adj_steps = timed(lambda: S.adjoint(adj, gc, gs), args.adjoint_steps)
+    ev = reduce_sum(float(events))
+    return {"workload": f"2 x 64^3 blob dyes, 256x256x81 ortho film, {n} paths, loss sum((I-T)^2)",
+            "adjoint_events_per_s": ev / (adj_ms / 1000.0), "adjoint_ms": adj_ms,
+            "adjoint_ms_steps": [round(v, 3) for v in adj_steps],
+            "forward_wavefront_events_per_s": ev / (fwd_ms / 1000.0), "forward_wavefront_ms": fwd_ms,
+            "plain_events_per_s": ev / (plain_ms / 1000.0), "plain_ms": plain_ms,
+            "adjoint_vs_plain": plain_ms / adj_ms, "events_per_step": events,
+            "grad_sigma_s": float(gs.item()), "grad_conc_abs_max": float(gc.abs().max().item())}
 
 
 def run_ours(args):
@@ -307,6 +356,11 @@ def run_ours(args):
     if not args.no_batch:
         batched = bench_batched(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
 
+    # --- adjoint (path replay) -------------------------------------------------------------
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
+
     # --- end to end through the C ABI with host buffers ------------------------------------
     md = sc["medium"]
     conc_h = torch.from_numpy(np.ascontiguousarray(md["conc"])).pin_memory()
@@ -379,6 +433,7 @@ def run_ours(args):
                 "speedup_vs_plain": value / plain_value,
                 "equal_rmse": "same estimator and the same path ids in both forms",
                 "batched": batched,
+                "adjoint": adjoint,
             },
             "counters_per_step": cnt_w,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
@@ -388,7 +443,8 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps + len(ms_p)
-            + (0 if batched is None else batched["steps"] + batched["plain_launches"]),
+            + (0 if batched is None else batched["steps"] + batched["plain_launches"])
+            + (0 if adjoint is None else 3 * args.adjoint_steps),
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -414,6 +470,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--batch-media", type=int, default=256,
+                    help="media in the batched workload (fewer for small profiling cases only)")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=3)
+    ap.add_argument("--adjoint-paths", type=int, default=0,
+                    help="override the adjoint path count (small profiling cases only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
