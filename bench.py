@@ -105,6 +105,20 @@ def measured_peaks():
         return {}
 
 
+def kernel_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, or None once the kernel source has
+    changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            info = json.load(f)
+        with open(os.path.join(ROOT, info["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError, KeyError):
+        return None
+    return info.get("bytes_per_launch") if sha == info.get("source_sha256") else None
+
+
 def cpu_oracle_rate(sc, n_paths, n_threads=0, film=True):
     import oracle
     t = time.perf_counter()
@@ -397,13 +411,7 @@ def run_ours(args):
     peak_ops = sms * 128 * sm_max * 1e6
     ops = algorithmic_ops(cnt_w)
     achieved = ops / (sum(ms_w) / len(ms_w) / 1000.0)
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "trace_wavefront_cornell_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = kernel_traffic("trace_wavefront_cornell_traffic.json")
 
     cpu = None
     if rank == 0 and not args.no_cpu:
