@@ -241,9 +241,10 @@ def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_
     S = Scene(sc, device=local)
     gc = torch.zeros(S.conc_t.shape, dtype=torch.float32, device=torch.device("cuda", local))
     gs = torch.zeros(1, dtype=torch.float32, device=gc.device)
-    film = S.render(form="wavefront")
+    mc = args.macro_cell
+    film = S.render(form="wavefront", macro_cell=mc)
     adj = (2.0 * (film - T)).contiguous()
-    S.adjoint(adj, gc, gs)
+    S.adjoint(adj, gc, gs, macro_cell=mc)
     torch.cuda.synchronize()
 
     def timed(fn, steps):
@@ -259,12 +260,13 @@ def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_
         return reduce_max(sum(ms) / len(ms)), ms
 
     barrier()
-    fwd_ms, _ = timed(lambda: S.render(form="wavefront"), args.adjoint_steps)
+    fwd_ms, _ = timed(lambda: S.render(form="wavefront", macro_cell=mc), args.adjoint_steps)
     events = S.read()["counters"]["events"]
     plain_ms, _ = timed(lambda: S.render(form="plain"), args.adjoint_steps)
-    adj_ms, adj_steps = timed(lambda: S.adjoint(adj, gc, gs), args.adjoint_steps)
+    adj_ms, adj_steps = timed(lambda: S.adjoint(adj, gc, gs, macro_cell=mc), args.adjoint_steps)
     ev = reduce_sum(float(events))
     return {"workload": f"2 x 64^3 blob dyes, 256x256x81 ortho film, {n} paths, loss sum((I-T)^2)",
+            "macro_cell": mc,
             "adjoint_events_per_s": ev / (adj_ms / 1000.0), "adjoint_ms": adj_ms,
             "adjoint_ms_steps": [round(v, 3) for v in adj_steps],
             "forward_wavefront_events_per_s": ev / (fwd_ms / 1000.0), "forward_wavefront_ms": fwd_ms,
@@ -301,7 +303,9 @@ def run_ours(args):
     offset = rank * n_paths  # each rank its own path-id range
 
     def one_step(form):
-        S.render(form=form, path_offset=offset, regroup=args.regroup)
+        # the plain kernel is the baseline: one thread per path, one majorant per bin
+        S.render(form=form, path_offset=offset, regroup=args.regroup,
+                 macro_cell=args.macro_cell if form == "wavefront" else 0)
 
     def timed(form, steps, sampler_path=None):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -342,6 +346,24 @@ def run_ours(args):
                                       if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
                                       else f"/tmp/clocks_rank{rank}.csv")
     ms_p, ev_p, cnt_p, _ = timed("plain", max(1, min(args.steps, args.plain_steps)))
+
+    # equal-RMSE check: each form's one-step film against a 16x-path reference (independent seed)
+    rmse = None
+    if not args.no_rmse:
+        ref = torch.zeros_like(S.film_tensor())
+        n_ref = 16
+        for k in range(n_ref):
+            S.render(form="wavefront", seed=7777, path_offset=k * n_paths,
+                     macro_cell=args.macro_cell)
+            ref += S.film_tensor() / n_ref
+        out = {}
+        for form in ("plain", "wavefront"):
+            one_step(form)
+            f = S.film_tensor()
+            out[form] = float(torch.sqrt(torch.mean((f.double() - ref.double()) ** 2)))
+        rmse = {"plain": out["plain"], "wavefront": out["wavefront"],
+                "reference_paths": n_ref * n_paths,
+                "ratio_wavefront_over_plain": out["wavefront"] / out["plain"]}
 
     def reduce_max(x):
         if world == 1:
@@ -389,7 +411,8 @@ def run_ours(args):
         conc_d.copy_(conc_h, non_blocking=True)
         solv_d.copy_(solv_h, non_blocking=True)
         S.set_medium(md, grids={"conc": conc_d, "solvent": solv_d})
-        f = S.render(form="wavefront", path_offset=offset, regroup=args.regroup)
+        f = S.render(form="wavefront", path_offset=offset, regroup=args.regroup,
+                     macro_cell=args.macro_cell)
         film_h.copy_(f, non_blocking=True)
         return S.read()
 
@@ -428,7 +451,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if not args.paths else WORKLOAD + f" ({n_paths} paths)",
-                       "paths_per_gpu": n_paths, "form": "wavefront",
+                       "paths_per_gpu": n_paths, "form": "wavefront", "macro_cell": args.macro_cell,
                        "regroup": args.regroup,
                        "l2": "flushed between timed steps (256 MB write)",
                        "events_per_step": ev_w, "parallelism": f"paths sharded over {world} GPU(s)"},
@@ -439,7 +462,10 @@ def run_ours(args):
                 "plain": {"events_per_s": plain_value, "ms_per_step": step_ms_p,
                           "steps": len(ms_p), "ms_steps": [round(v, 3) for v in ms_p]},
                 "speedup_vs_plain": value / plain_value,
-                "equal_rmse": "same estimator and the same path ids in both forms",
+                "equal_rmse": "same estimator and path ids; film RMSE against a 16x-path reference"
+                              " in `rmse` (the local majorants of the wavefront form also lower the"
+                              " transmittance estimate's variance)",
+                "rmse": rmse,
                 "batched": batched,
                 "adjoint": adjoint,
             },
@@ -469,6 +495,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--regroup", type=int, default=0)
+    ap.add_argument("--macro-cell", type=int, default=8,
+                    help="local-majorant cell edge in voxels for the optimised forms (0: global)")
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--paths", type=int, default=0,
                     help="override the path count (small profiling cases only)")
@@ -477,6 +505,7 @@ def main():
     ap.add_argument("--ref-paths", type=int, default=1 << 16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-rmse", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--batch-media", type=int, default=256,
                     help="media in the batched workload (fewer for small profiling cases only)")

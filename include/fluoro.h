@@ -137,6 +137,11 @@ typedef struct flr_params {
     int block_size;              /* threads per block; 0 = library default                     */
     int blocks_per_sm;           /* resident blocks per SM; 0 = occupancy maximum               */
     int regroup_interval;        /* wavefront: tracking steps between connection flushes; 0 auto */
+    int macro_cell;              /* > 0: free flights and transmittance marches use local
+                                    majorants over cells of macro_cell^3 voxels (each the maximum
+                                    of sigma_t over the cell and a one-voxel halo), walked by DDA;
+                                    0: one majorant per bin. Same estimator, fewer null steps in
+                                    sparse media. Single-scene renders and the adjoint only. */
 } flr_params;
 
 /* Create a context on CUDA device `cuda_device`. Allocates the small tally buffers. */
@@ -229,7 +234,7 @@ int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const u
  * p->n_paths). All scratch -- spectral tables, fixed-point tallies, counters, the work counter and
  * the interleaved copy of the grids -- lives in one static device array of 4 MiB + 64 KiB that
  * every GPU loading this library holds until the process exits; media with more than
- * FLR_NOALLOC_MAX_VOXELS voxels are rejected with FLR_ERR_ARG. The first call on a device looks up
+ * FLR_NOALLOC_MAX_VOXELS voxels are rejected with FLR_ERR_ARG; p->macro_cell is ignored (one majorant per bin). The first call on a device looks up
  * that array's device address (with that device current), so make that first call before any
  * stream capture. Every call uses the same array and clears what must start at zero, so calls
  * that overlap on the GPU (other streams, other host threads) race with each other. The call

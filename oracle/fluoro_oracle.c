@@ -117,6 +117,9 @@ typedef struct {
     int64_t pert_voxel;
     double pert_delta;
     double pert_sigma_s;
+    /* free flights against a grid of local majorants: cells of macro_cell^3 voxels, each the
+     * maximum of sigma_t over its voxels and a one-voxel halo; 0 = one majorant per bin */
+    int macro_cell;
 } or_params;
 
 typedef struct {
@@ -188,12 +191,69 @@ typedef struct {
     int frozen, pert_dye;
     int64_t pert_voxel;
     double pert_delta, pert_sigma_s;
+    double maj_scale;
+    /* local majorants (macro cells) */
+    int mc, mdims[3];
+    double *mc_cmax;                         /* [cells][n_dyes] */
+    double *mc_smax;                         /* [cells]         */
 } tables;
 
+static int nvox(const or_scene *s);
+
+/* Maxima of each dye's concentration and of the solvent mask over every macro cell (its
+ * macro_cell^3 voxels plus a one-voxel halo). */
+static void build_macro(const or_scene *s, tables *t, int cell)
+{
+    t->mc = 0;
+    if (cell <= 0 || t->homogeneous) return;
+    int64_t nc = 1;
+    for (int k = 0; k < 3; ++k) {
+        t->mdims[k] = (s->dims[k] + cell - 1) / cell;
+        nc *= t->mdims[k];
+    }
+    t->mc = cell;
+    t->mc_cmax = (double *)calloc((size_t)nc * (s->n_dyes > 0 ? s->n_dyes : 1), sizeof(double));
+    t->mc_smax = (double *)calloc((size_t)nc, sizeof(double));
+    for (int cz = 0; cz < t->mdims[2]; ++cz)
+        for (int cy = 0; cy < t->mdims[1]; ++cy)
+            for (int cx = 0; cx < t->mdims[0]; ++cx) {
+                int64_t c = ((int64_t)cz * t->mdims[1] + cy) * t->mdims[0] + cx;
+                int lo[3] = { cx * cell - 1, cy * cell - 1, cz * cell - 1 };
+                int hi[3] = { (cx + 1) * cell, (cy + 1) * cell, (cz + 1) * cell };
+                for (int k = 0; k < 3; ++k) {
+                    if (lo[k] < 0) lo[k] = 0;
+                    if (hi[k] > s->dims[k] - 1) hi[k] = s->dims[k] - 1;
+                }
+                double sm = s->solvent ? 0.0 : 1.0;
+                for (int z = lo[2]; z <= hi[2]; ++z)
+                    for (int y = lo[1]; y <= hi[1]; ++y)
+                        for (int x = lo[0]; x <= hi[0]; ++x) {
+                            int v = (z * s->dims[1] + y) * s->dims[0] + x;
+                            if (s->solvent && s->solvent[v]) sm = 1.0;
+                            for (int d = 0; d < s->n_dyes; ++d) {
+                                double cv = s->conc ? (double)s->conc[(size_t)d * nvox(s) + v]
+                                                    : (double)s->conc_uniform[d];
+                                if (cv > t->mc_cmax[c * s->n_dyes + d]) t->mc_cmax[c * s->n_dyes + d] = cv;
+                            }
+                        }
+                t->mc_smax[c] = sm;
+            }
+}
+
+static void free_macro(tables *t)
+{
+    free(t->mc_cmax);
+    free(t->mc_smax);
+    t->mc_cmax = t->mc_smax = NULL;
+}
+
 /* Copy the per-render evaluation settings into the tables (majorant scale and perturbation). */
+static void apply_params_macro(const or_scene *s, tables *t, const or_params *p);
+
 static void apply_params(tables *t, const or_params *p)
 {
     double ms = p->majorant_scale > 0.0 ? p->majorant_scale : 1.0;
+    t->maj_scale = ms;
     for (int i = 0; i < t->B; ++i) t->majorant[i] *= ms;
     t->frozen = p->frozen;
     t->pert_dye = p->pert_dye;
@@ -324,10 +384,6 @@ static coeffs coeffs_at_p(const or_scene *s, const tables *t, const double x[3],
     return c;
 }
 
-static coeffs coeffs_at(const or_scene *s, const tables *t, const double x[3], int bin)
-{
-    return coeffs_at_p(s, t, x, bin, 0);
-}
 
 /* Distance to leave the AABB along (x, w), and the face: faces (-x,+x,-y,+y,-z,+z) = 0..5;
  * ties go to the lowest face index. */
@@ -604,6 +660,69 @@ static int sample_emission_bin(const tables *t, int d, double u)
     return t->B - 1;
 }
 
+static void apply_params_macro(const or_scene *s, tables *t, const or_params *p)
+{
+    build_macro(s, t, p->macro_cell);
+}
+
+/* Local majorant of macro cell c: the maximum of sigma_t over the cell (Sec. 4.1 coefficients). */
+static double cell_majorant(const or_scene *s, const tables *t, int64_t c, int bin)
+{
+    double m = t->mc_smax[c] * (s->sigma_s + s->sigma_a0);
+    for (int d = 0; d < s->n_dyes; ++d) m += t->sig_a[d][bin] * t->mc_cmax[c * s->n_dyes + d];
+    return m * t->maj_scale;
+}
+
+/* Free flight against local majorants: the optical budget tau = -ln(1 - u) is spent cell by cell
+ * along the ray (each cell at its own majorant); returns the tentative collision distance, or
+ * INFINITY when the budget outlasts the distance te to the box boundary, and the local majorant
+ * at the tentative point. */
+static double macro_flight(const or_scene *s, const tables *t, const double x[3], const double w[3],
+                           int bin, double tau, double te, double *sb_out)
+{
+    int c[3], stp[3];
+    double tmax[3], tdel[3];
+    for (int k = 0; k < 3; ++k) {
+        double cs = t->mc * (s->hi[k] - s->lo[k]) / (double)s->dims[k];
+        int ck = (int)floor((x[k] - s->lo[k]) / cs);
+        if (ck < 0) ck = 0;
+        if (ck > t->mdims[k] - 1) ck = t->mdims[k] - 1;
+        c[k] = ck;
+        if (w[k] > 0.0) {
+            stp[k] = 1;
+            tmax[k] = (s->lo[k] + (ck + 1) * cs - x[k]) / w[k];
+            tdel[k] = cs / w[k];
+        } else if (w[k] < 0.0) {
+            stp[k] = -1;
+            tmax[k] = (s->lo[k] + ck * cs - x[k]) / w[k];
+            tdel[k] = -cs / w[k];
+        } else {
+            stp[k] = 0;
+            tmax[k] = INFINITY;
+            tdel[k] = INFINITY;
+        }
+    }
+    double t0 = 0.0;
+    for (;;) {
+        int64_t cell = ((int64_t)c[2] * t->mdims[1] + c[1]) * t->mdims[0] + c[0];
+        double sbc = cell_majorant(s, t, cell, bin);
+        int ax = 0;
+        for (int k = 1; k < 3; ++k) if (tmax[k] < tmax[ax]) ax = k;
+        double t1 = tmax[ax] < te ? tmax[ax] : te;
+        if (t1 < t0) t1 = t0;
+        if (sbc > 0.0 && tau < sbc * (t1 - t0)) {
+            *sb_out = sbc;
+            return t0 + tau / sbc;
+        }
+        tau -= sbc * (t1 - t0);
+        t0 = t1;
+        if (t1 >= te) { *sb_out = sbc; return INFINITY; }
+        c[ax] += stp[ax];
+        if (c[ax] < 0 || c[ax] >= t->mdims[ax]) { *sb_out = sbc; return INFINITY; }
+        tmax[ax] += tdel[ax];
+    }
+}
+
 static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *p, uint64_t pid,
                            local_tally *lt, double *film, adj_path *A)
 {
@@ -641,10 +760,15 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
         if (A) A->cur_step = step;
         cnt[OC_STEPS]++;
         block4 B0 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 0);
-        double sb = t->majorant[bin];
-        double tf = sb > 0.0 ? -log(1.0 - B0.u[0]) / sb : INFINITY;
         int face;
         double te = exit_distance(s, x, w, &face);
+        double sb, tf;
+        if (t->mc) {
+            tf = macro_flight(s, t, x, w, bin, -log(1.0 - B0.u[0]), te, &sb);
+        } else {
+            sb = t->majorant[bin];
+            tf = sb > 0.0 ? -log(1.0 - B0.u[0]) / sb : INFINITY;
+        }
         if (tf >= te) {
             for (int k = 0; k < 3; ++k) x[k] += te * w[k];
             if (s->wall_mask & (1 << face)) {
@@ -772,6 +896,7 @@ int or_render(const or_scene *s, const or_params *p, or_result *r)
     tables *t = (tables *)malloc(sizeof(tables));
     build_tables(s, t);
     apply_params(t, p);
+    apply_params_macro(s, t, p);
     int B = s->n_bins, D = s->n_dyes;
     memset(r->face, 0, sizeof(double) * 2 * 6 * B);
     memset(r->absorbed, 0, sizeof(double) * (D + 1) * B);
@@ -813,6 +938,7 @@ int or_render(const or_scene *s, const or_params *p, or_result *r)
         size_t n = (size_t)s->sensor.width * s->sensor.height * B;
         for (size_t i = 0; i < n; ++i) r->film[i] *= inv;
     }
+    free_macro(t);
     free(t);
     return 0;
 }
@@ -887,6 +1013,7 @@ int or_adjoint(const or_scene *s, const or_params *p, const double *adj, double 
     tables *t = (tables *)malloc(sizeof(tables));
     build_tables(s, t);
     apply_params(t, p);
+    apply_params_macro(s, t, p);
     t->pert_dye = -1;
     t->pert_sigma_s = 0.0;
     t->frozen = 0;
@@ -957,6 +1084,7 @@ int or_adjoint(const or_scene *s, const or_params *p, const double *adj, double 
         free(A.con);
         free(lt);
     }
+    free_macro(t);
     free(t);
     return 0;
 }

@@ -44,6 +44,12 @@ struct flr_ctx {
     unsigned int *d_scratch = nullptr;  // [0] max bits, [1] flag, [2] any
     uint64_t paths_since_clear = 0;
     std::vector<float> h_tables;
+    // local majorants of the current medium (built on demand for one cell size)
+    float4 *d_mc_c = nullptr;
+    float *d_mc_s = nullptr;
+    size_t mc_cap = 0;
+    int mc_cell = 0;
+    int mc_dims[3] = {0, 0, 0};
     // batched form
     struct Batch {
         int n_media = 0;
@@ -222,7 +228,7 @@ int build_emitters(flr_ctx *ctx, const flr_medium &m, int max_lines, EmitterDev 
     return FLR_OK;
 }
 
-int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film)
+int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film, int macro_cell = 0)
 {
     const flr_medium &m = ctx->medium;
     std::memset(&S, 0, sizeof(S));
@@ -247,6 +253,17 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film)
     const int rc = build_emitters(ctx, m, FLR_MAX_EMITTERS, S.em, S.em_cdf, &ne);
     if (rc != FLR_OK) return rc;
     S.n_emitters = ne;
+    if (macro_cell > 0 && !S.homogeneous && ctx->mc_cell == macro_cell) {
+        S.mc = macro_cell;
+        for (int k = 0; k < 3; ++k) {
+            S.mc_dims[k] = ctx->mc_dims[k];
+            const double cs = (double)macro_cell * ((double)m.hi[k] - (double)m.lo[k]) / (double)S.dims[k];
+            S.mc_size[k] = (float)cs;
+            S.mc_inv[k] = (float)(1.0 / cs);
+        }
+        S.mc_c = ctx->d_mc_c;
+        S.mc_s = ctx->d_mc_s;
+    }
     // sensor
     const flr_sensor &c = ctx->sensor;
     S.sensor_kind = (ctx->sensor_set && with_film) ? c.kind : FLR_SENSOR_NONE;
@@ -280,6 +297,42 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film)
             S.inv_A_pix = (float)((double)c.width * c.height / ((2.0 * tx) * (2.0 * ty)));
         }
     }
+    return FLR_OK;
+}
+
+// Local-majorant grid of the current medium for cells of `cell`^3 voxels (built on `st` when the
+// cell size differs from the one built last; the medium's packed grid must be current).
+int prepare_macro(flr_ctx *ctx, int cell, cudaStream_t st)
+{
+    const flr_medium &m = ctx->medium;
+    const bool grids = medium_has_grid(m) || m.solvent;
+    if (cell <= 0 || !grids || ctx->mc_cell == cell) return FLR_OK;
+    int md[3];
+    size_t n = 1;
+    for (int k = 0; k < 3; ++k) {
+        md[k] = (m.dims[k] + cell - 1) / cell;
+        n *= (size_t)md[k];
+    }
+    if (n > ctx->mc_cap) {
+        cudaFree(ctx->d_mc_c);
+        cudaFree(ctx->d_mc_s);
+        ctx->d_mc_c = nullptr;
+        ctx->d_mc_s = nullptr;
+        ctx->mc_cap = 0;
+        cudaError_t e = cudaMalloc(&ctx->d_mc_c, sizeof(float4) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_mc_s, sizeof(float) * n);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate the local-majorant grid");
+        ctx->mc_cap = n;
+    }
+    float4 uni = make_float4(0.f, 0.f, 0.f, 0.f);
+    float u[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int d = 0; d < m.n_dyes; ++d) u[d] = m.conc_uniform[d];
+    uni = make_float4(u[0], u[1], u[2], u[3]);
+    cudaError_t e = launch_build_macro(medium_has_grid(m) ? ctx->d_grid : nullptr, uni, m.solvent,
+                                       m.dims, cell, md, ctx->d_mc_c, ctx->d_mc_s, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "build the local-majorant grid");
+    ctx->mc_cell = cell;
+    for (int k = 0; k < 3; ++k) ctx->mc_dims[k] = md[k];
     return FLR_OK;
 }
 
@@ -371,6 +424,8 @@ void flr_destroy(flr_ctx *ctx)
     cudaFree(ctx->d_work);
     cudaFree(ctx->d_scratch);
     cudaFree(ctx->d_grid);
+    cudaFree(ctx->d_mc_c);
+    cudaFree(ctx->d_mc_s);
     auto &bt = ctx->batch;
     if (bt.exec) cudaGraphExecDestroy(bt.exec);
     if (bt.graph) cudaGraphDestroy(bt.graph);
@@ -517,6 +572,7 @@ int flr_set_medium(flr_ctx *ctx, const flr_medium *m)
     ctx->smax = smax;
     ctx->medium_set = true;
     ctx->tables_dirty = true;
+    ctx->mc_cell = 0;
     return FLR_OK;
 }
 
@@ -558,6 +614,7 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
         return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
+    if (p->macro_cell < 0 || p->macro_cell > 4096) return fail(ctx, FLR_ERR_ARG, "params: macro_cell 0..4096");
     if (p->film && !is_device_pointer(p->film)) return fail(ctx, FLR_ERR_ARG, "params: film must be device memory");
     if (p->path_events && !is_device_pointer(p->path_events))
         return fail(ctx, FLR_ERR_ARG, "params: path_events must be device memory");
@@ -570,10 +627,12 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     DeviceGuard g(ctx->device);
     int rc = prepare_tables(ctx);
     if (rc != FLR_OK) return rc;
-    SceneDev S;
-    rc = fill_scene(ctx, S, p->film != nullptr);
-    if (rc != FLR_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    rc = prepare_macro(ctx, p->macro_cell, st);
+    if (rc != FLR_OK) return rc;
+    SceneDev S;
+    rc = fill_scene(ctx, S, p->film != nullptr, p->macro_cell);
+    if (rc != FLR_OK) return rc;
     cudaError_t e = cudaSuccess;
     if (!p->accumulate) {
         e = cudaMemsetAsync(ctx->d_tallies, 0, sizeof(unsigned long long) * tal_size(FLR_MAX_BINS), st);
@@ -711,13 +770,16 @@ int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float 
     if (grad_conc && !is_device_pointer(grad_conc)) return fail(ctx, FLR_ERR_ARG, "adjoint: grad_conc must be device memory");
     if (grad_sigma_s && !is_device_pointer(grad_sigma_s))
         return fail(ctx, FLR_ERR_ARG, "adjoint: grad_sigma_s must be device memory");
+    if (p->macro_cell < 0 || p->macro_cell > 4096) return fail(ctx, FLR_ERR_ARG, "params: macro_cell 0..4096");
     DeviceGuard g(ctx->device);
     int rc = prepare_tables(ctx);
     if (rc != FLR_OK) return rc;
-    SceneDev S;
-    rc = fill_scene(ctx, S, true);
-    if (rc != FLR_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    rc = prepare_macro(ctx, p->macro_cell, st);
+    if (rc != FLR_OK) return rc;
+    SceneDev S;
+    rc = fill_scene(ctx, S, true, p->macro_cell);
+    if (rc != FLR_OK) return rc;
     const long long nv = nvox(ctx->medium);
     cudaError_t e = cudaSuccess;
     if (!p->accumulate) {

@@ -57,6 +57,12 @@ struct SceneDev {
     int sensor_kind, W, H;
     float s_origin[3], s_U[3], s_V[3], s_view[3];  // ortho: U, V pre-divided by |U|^2, |V|^2
     float tan_x, tan_y, inv_A_pix;
+    // local majorants (macro cells); mc == 0: one majorant per bin
+    int mc;
+    int mc_dims[3];
+    float mc_size[3], mc_inv[3];       // cell edge (cm) and its inverse
+    const float4 *mc_c;                // per-cell maximum concentration of each dye
+    const float *mc_s;                 // per-cell maximum of the solvent mask
 };
 
 // Per-launch run parameters.
@@ -129,6 +135,9 @@ cudaError_t launch_batch(const BatchDev &Bt, const RunDev &R, int block, int blo
 int batch_occupancy_blocks_per_sm(int block);
 cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block, int blocks_per_sm,
                          cudaStream_t st);
+cudaError_t launch_build_macro(const float4 *grid, float4 uniform, const uint8_t *solvent,
+                               const int dims[3], int cell, const int mdims[3], float4 *out_c,
+                               float *out_s, cudaStream_t st);
 cudaError_t launch_grid_max(const float *g, long long n, unsigned int *out_bits, int *neg_flag,
                             cudaStream_t st);
 cudaError_t launch_pack_grid(const float *const *conc, const float *uniform, int D, long long n,

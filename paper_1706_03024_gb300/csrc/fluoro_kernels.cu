@@ -119,6 +119,12 @@ struct MedS {
     __device__ __forceinline__ float em_cdf(int k) const { return S.em_cdf[k]; }
     __device__ __forceinline__ const EmitterDev &em(int k) const { return S.em[k]; }
     __device__ __forceinline__ uint32_t key1(const RunDev &R) const { return R.medium_id; }
+    __device__ __forceinline__ bool macro() const { return S.mc > 0; }
+    __device__ __forceinline__ int mc_dims(int k) const { return S.mc_dims[k]; }
+    __device__ __forceinline__ float mc_size(int k) const { return S.mc_size[k]; }
+    __device__ __forceinline__ float mc_inv(int k) const { return S.mc_inv[k]; }
+    __device__ __forceinline__ float4 mc_conc(int c) const { return __ldg(&S.mc_c[c]); }
+    __device__ __forceinline__ float mc_solvent(int c) const { return __ldg(&S.mc_s[c]); }
 };
 
 __device__ __forceinline__ void tally_add_global(unsigned long long *t, int idx, float w)
@@ -174,6 +180,12 @@ struct MedB {
     __device__ __forceinline__ float em_cdf(int k) const { return __ldg(&md->em_cdf[k]); }
     __device__ __forceinline__ const EmitterDev &em(int k) const { return md->em[k]; }
     __device__ __forceinline__ uint32_t key1(const RunDev &) const { return __ldg(&md->key1); }
+    __device__ __forceinline__ bool macro() const { return false; }
+    __device__ __forceinline__ int mc_dims(int) const { return 1; }
+    __device__ __forceinline__ float mc_size(int) const { return 1.0f; }
+    __device__ __forceinline__ float mc_inv(int) const { return 1.0f; }
+    __device__ __forceinline__ float4 mc_conc(int) const { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ __forceinline__ float mc_solvent(int) const { return 0.0f; }
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -250,6 +262,87 @@ __device__ __forceinline__ float3 inv_dir(float3 w)
 {
     return make_float3(w.x != 0.0f ? __frcp_rn(w.x) : 0.0f, w.y != 0.0f ? __frcp_rn(w.y) : 0.0f,
                        w.z != 0.0f ? __frcp_rn(w.z) : 0.0f);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Local majorants. Cell c covers macro_cell^3 voxels; its majorant is evaluated with exactly the
+// operation order of coeffs_at (solvent scattering, solvent absorption, then each dye), so with
+// cell maxima of every input the fp32 result bounds sigma_t anywhere in the cell (IEEE rounding is
+// monotone). A DDA walks the cells along a ray spending an optical budget tau = -ln(1 - u).
+template <class M>
+__device__ __forceinline__ float cell_majorant(const M &m, int cell, int b)
+{
+    const float sv = m.mc_solvent(cell);
+    const float4 c = m.mc_conc(cell);
+    float total = sv * m.sigma_s() + sv * m.sigma_a0();
+    const float cc[4] = {c.x, c.y, c.z, c.w};
+    const int D = m.D();
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d) total += (d < D) ? m.sig_a(d, b) * cc[d] : 0.0f;
+    return total;
+}
+
+struct Dda {
+    int c[3], stp[3];
+    float tmax[3], tdel[3];
+    float t;
+};
+
+template <class M>
+__device__ __forceinline__ void dda_init(const M &m, Dda &d, float3 x, float3 w, float3 iw)
+{
+    const float xs[3] = {x.x, x.y, x.z}, ws[3] = {w.x, w.y, w.z}, is[3] = {iw.x, iw.y, iw.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float cs = m.mc_size(k);
+        int ck = __float2int_rd((xs[k] - m.lo(k)) * m.mc_inv(k));
+        ck = min(max(ck, 0), m.mc_dims(k) - 1);
+        d.c[k] = ck;
+        if (ws[k] > 0.0f) {
+            d.stp[k] = 1;
+            d.tmax[k] = (m.lo(k) + (float)(ck + 1) * cs - xs[k]) * is[k];
+            d.tdel[k] = cs * is[k];
+        } else if (ws[k] < 0.0f) {
+            d.stp[k] = -1;
+            d.tmax[k] = (m.lo(k) + (float)ck * cs - xs[k]) * is[k];
+            d.tdel[k] = -cs * is[k];
+        } else {
+            d.stp[k] = 0;
+            d.tmax[k] = FLT_MAX;
+            d.tdel[k] = FLT_MAX;
+        }
+    }
+    d.t = 0.0f;
+}
+
+// Spends tau from d.t on; returns the tentative distance (and its cell's majorant in sb), or
+// FLT_MAX once t_end is reached first.
+template <class M>
+__device__ __forceinline__ float dda_advance(const M &m, Dda &d, int b, float tau, float t_end, float &sb)
+{
+    for (int guard = 0; guard < (1 << 16); ++guard) {
+        const int cell = (d.c[2] * m.mc_dims(1) + d.c[1]) * m.mc_dims(0) + d.c[0];
+        const float sbc = cell_majorant(m, cell, b);
+        int ax = 0;
+        if (d.tmax[1] < d.tmax[ax]) ax = 1;
+        if (d.tmax[2] < d.tmax[ax]) ax = 2;
+        float t1 = fminf(d.tmax[ax], t_end);
+        t1 = fmaxf(t1, d.t);
+        const float opt = sbc * (t1 - d.t);
+        if (sbc > 0.0f && tau < opt) {
+            d.t += tau / sbc;
+            sb = sbc;
+            return d.t;
+        }
+        tau -= opt;
+        d.t = t1;
+        if (t1 >= t_end) { sb = sbc; return FLT_MAX; }
+        d.c[ax] += d.stp[ax];
+        if (d.c[ax] < 0 || d.c[ax] >= m.mc_dims(ax)) { sb = sbc; return FLT_MAX; }
+        d.tmax[ax] += d.tdel[ax];
+    }
+    sb = 0.0f;
+    return FLT_MAX;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -373,6 +466,45 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
     if (S.homogeneous) {
         sink.homogeneous(tl);
         return __expf(-sigma_t_at(m, x, b) * tl);
+    }
+    if (S.mc > 0) {
+        // ratio tracking against the local majorants: one uniform per tentative point
+        Dda dd;
+        dda_init(m, dd, x, dir, inv_dir(dir));
+        U4 blk = U4{0, 0, 0, 0};
+        uint32_t j = 0;
+        int it = 0;
+        for (; it < MAX_CONNECT_STEPS; ++it) {
+            if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
+            const uint32_t q = j & 3u;
+            const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
+            ++j;
+            float sbc;
+            const float t = dda_advance(m, dd, b, -__logf(1.0f - u), tl, sbc);
+            if (t >= tl) break;
+            rc.connect_steps++;
+            const float3 p = make_float3(x.x + t * dir.x, x.y + t * dir.y, x.z + t * dir.z);
+            const float st = sigma_t_at(m, p, b);
+            sink.point(p, b, st, sbc);
+            T *= fmaxf(0.0f, 1.0f - st / sbc);
+            if (T < RT_RR_THRESHOLD) {
+                if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
+                const uint32_t q2 = j & 3u;
+                const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
+                ++j;
+                if (u2 < 0.5f) {
+                    T *= 2.0f;
+                } else {
+                    T = 0.0f;
+                    break;
+                }
+            }
+        }
+        if (it == MAX_CONNECT_STEPS) {
+            T = 0.0f;
+            cnt_add(sm, FLR_C_CONNECT_BUDGET);
+        }
+        return T;
     }
     const float isb = __frcp_rn(sb);
     float t = 0.0f;
@@ -523,10 +655,17 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
     rc.steps++;
     const uint32_t key1 = m.key1(R);
     const U4 b0 = draw(R.seed, key1, p.pid, p.step, 0u);
-    const float sb = m.maj(p.bin);
-    const float tf = sb > 0.0f ? -__logf(1.0f - b0.a) / sb : FLT_MAX;
     int face;
     const float te = exit_distance(m, p.x, p.w, p.iw, face);
+    float sb, tf;
+    if (m.macro()) {
+        Dda dd;
+        dda_init(m, dd, p.x, p.w, p.iw);
+        tf = dda_advance(m, dd, p.bin, -__logf(1.0f - b0.a), te, sb);
+    } else {
+        sb = m.maj(p.bin);
+        tf = sb > 0.0f ? -__logf(1.0f - b0.a) / sb : FLT_MAX;
+    }
     const uint32_t step = p.step;
     p.step++;
     if (tf >= te) {
@@ -1071,6 +1210,40 @@ __global__ void k_grid_max(const float *__restrict__ g, long long n, unsigned in
     if (bad) atomicOr(neg_flag, 1);
 }
 
+// Per-cell maxima (cell plus a one-voxel halo) of each dye's concentration and of the solvent
+// mask; one thread per cell.
+__global__ void k_build_macro(const float4 *__restrict__ grid, float4 uniform,
+                              const uint8_t *__restrict__ solvent, int nx, int ny, int nz, int cell,
+                              int mx, int my, int mz, float4 *__restrict__ out_c,
+                              float *__restrict__ out_s)
+{
+    const long long ncell = (long long)mx * my * mz;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int cx = (int)(c % mx), cy = (int)((c / mx) % my), cz = (int)(c / ((long long)mx * my));
+        const int x0 = max(cx * cell - 1, 0), x1 = min((cx + 1) * cell, nx - 1);
+        const int y0 = max(cy * cell - 1, 0), y1 = min((cy + 1) * cell, ny - 1);
+        const int z0 = max(cz * cell - 1, 0), z1 = min((cz + 1) * cell, nz - 1);
+        float4 m = grid ? make_float4(0.f, 0.f, 0.f, 0.f) : uniform;
+        float sm = solvent ? 0.0f : 1.0f;
+        for (int z = z0; z <= z1; ++z)
+            for (int y = y0; y <= y1; ++y)
+                for (int x = x0; x <= x1; ++x) {
+                    const long long v = ((long long)z * ny + y) * nx + x;
+                    if (grid) {
+                        const float4 g = grid[v];
+                        m.x = fmaxf(m.x, g.x);
+                        m.y = fmaxf(m.y, g.y);
+                        m.z = fmaxf(m.z, g.z);
+                        m.w = fmaxf(m.w, g.w);
+                    }
+                    if (solvent && solvent[v]) sm = 1.0f;
+                }
+        out_c[c] = m;
+        out_s[c] = sm;
+    }
+}
+
 struct PackArgs {
     const float *conc[MAXD];
     float uniform[MAXD];
@@ -1197,6 +1370,20 @@ cudaError_t launch_adjoint(const SceneDev &S, const RunDev &R, const AdjDev &A, 
     if (need < grid) grid = need;
     if (grid < 1) grid = 1;
     k_adjoint<<<(unsigned)grid, block, smem, st>>>(S, R, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_macro(const float4 *grid, float4 uniform, const uint8_t *solvent,
+                               const int dims[3], int cell, const int mdims[3], float4 *out_c,
+                               float *out_s, cudaStream_t st)
+{
+    const long long ncell = (long long)mdims[0] * mdims[1] * mdims[2];
+    long long blocks = (ncell + 127) / 128;
+    const long long cap = (long long)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_build_macro<<<(unsigned)blocks, 128, 0, st>>>(grid, uniform, solvent, dims[0], dims[1], dims[2],
+                                                     cell, mdims[0], mdims[1], mdims[2], out_c, out_s);
     return cudaGetLastError();
 }
 

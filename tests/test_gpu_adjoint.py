@@ -39,22 +39,24 @@ def adjoint_scene(n=12, W=12, sigma_s=10.0, n_paths=4000):
             "params": sg.params(n_paths, seed=1)}
 
 
-def gpu_adjoint(S, adj, n, offset=0, seed=None):
+def gpu_adjoint(S, adj, n, offset=0, seed=None, macro_cell=0):
     gc = torch.zeros(S.conc_t.shape, dtype=torch.float32, device="cuda")
     gs = torch.zeros(1, dtype=torch.float32, device="cuda")
     S.adjoint(torch.from_numpy(adj.astype(np.float32)).cuda(), gc, gs, n_paths=n,
-              path_offset=offset, seed=seed)
+              path_offset=offset, seed=seed, macro_cell=macro_cell)
     return gc.double().cpu().numpy(), float(gs.item())
 
 
-def test_adjoint_matches_oracle_reference_gradient():
+@pytest.mark.parametrize("macro_cell", [0, 3])
+def test_adjoint_matches_oracle_reference_gradient(macro_cell):
     sc = adjoint_scene()
     S = Scene(sc)
     rng = np.random.default_rng(5)
     adj = rng.normal(size=(12, 12, sg.N_BINS))
     K, n = 16, 4000
-    g = [gpu_adjoint(S, adj, n, k * n) for k in range(K)]
-    o = [oracle.adjoint(sc, adj, n_paths=n, path_offset=k * n) for k in range(K)]
+    g = [gpu_adjoint(S, adj, n, k * n, macro_cell=macro_cell) for k in range(K)]
+    o = [oracle.adjoint(sc, adj, n_paths=n, path_offset=k * n, macro_cell=macro_cell)
+         for k in range(K)]
     mg, sg_ = batch_mean_se([x[0] for x in g])
     mo, so = batch_mean_se([x[0] for x in o])
     v = parity_verdict(mg, sg_, mo, so, check_chi2=False)

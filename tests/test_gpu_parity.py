@@ -154,6 +154,18 @@ def test_cfg2_cornell_box_reduced_parity():
     _check_workload(sc, 32, 6000, forms=("plain", "wavefront"), path_id_frac=0.97)
 
 
+def test_cfg2_macro_cell_parity():
+    """Local majorants (cells of 4^3 voxels): the oracle walks the same cells in fp64."""
+    sc = sg.cfg2_cornell_box(width=48, height=48, grid=48, n_paths=1)
+    _check_workload(sc, 32, 6000, forms=("plain", "wavefront"), path_id_frac=0.95, macro_cell=4)
+
+
+def test_cfg5_macro_cell_parity():
+    sc = sg.cfg5_light_sheet(grid=32, width=32, height=32, n_blobs=40, n_paths=1,
+                             sigma_t_ref=20.0)
+    _check_workload(sc, 32, 1500, forms=("wavefront",), path_id_frac=0.95, macro_cell=8)
+
+
 def test_cfg4_blobby_grid_ortho_parity():
     sc = sg.cfg4_adjoint(grid=24, width=24, height=24, n_paths=1)
     _check_workload(sc, 32, 4000, forms=("wavefront",), path_id_frac=0.97)

@@ -616,3 +616,53 @@ def test_thread_count_does_not_change_results():
     assert np.allclose(a["face"], b["face"], rtol=1e-12, atol=1e-15)
     assert np.allclose(a["film"], b["film"], rtol=1e-10, atol=1e-12)
     assert a["counters"] == b["counters"]
+
+
+# ------------------------------------------------------------------------------------------
+# Local (macro-cell) majorants: the same estimator with fewer null collisions
+
+
+def test_macro_cell_flight_reproduces_uncollided_transmission():
+    """Delta tracking against per-cell majorants still samples the exact free-flight law (Eq. 6):
+    the uncollided transmission through a random grid with a solvent mask matches
+    exp(-column sum) for several cell sizes, with no majorant violation."""
+    rng = np.random.default_rng(15)
+    n = 12
+    conc = rng.uniform(0.0, 2.0, size=(2, n, n, n)).astype(np.float32)
+    conc[:, :, :, : n // 2] *= 0.05
+    solvent = (rng.random((n, n, n)) < 0.6).astype(np.uint8)
+    dyes = sg.make_dyes([490.0, 500.0], [15.0, 30.0], [620.0, 650.0], [15.0, 15.0],
+                        eps=[0.3, 0.25], qy=[0.5, 0.5])
+    x, y = 0.31, 0.64
+    sc = {"spectrum": sg.spectrum(), "dyes": dyes,
+          "medium": sg.grid_medium(conc, solvent, sigma_s=0.6),
+          "sources": [sg.pencil_beam((x, y, 1.0), (0, 0, -1), [490.0])],
+          "sensor": sg.no_sensor(), "params": sg.params(200_000, seed=4)}
+    b = bin_of(490)
+    exact = math.exp(-oracle.optical_depth(sc, np.array([x, y, 1.0]), np.array([0, 0, -1.0]), 1.0,
+                                           b))
+    for cell in (1, 3, 5, 12):
+        r = oracle.render(sc, max_events=0, macro_cell=cell)
+        T = r["face"][:, sg.FACE_NZ, :].sum()
+        assert abs(T - exact) <= 3 * binomial_se(exact, 200_000), (cell, T, exact)
+        assert r["counters"]["majorant_violations"] == 0
+
+
+def test_macro_cell_render_matches_global_majorant_render():
+    """Cornell box: local and global majorants estimate the same tallies and film (independent
+    paths, batch-means z), with far fewer tracking steps."""
+    sc = sg.cfg2_cornell_box(width=16, height=16, grid=32, n_paths=1)
+    K, n = 16, 3000
+    a = batched(sc, K, n)
+    b = [oracle.render(sc, n_paths=n, path_offset=k * n, seed=11, macro_cell=4) for k in range(K)]
+    for key in ("face", "emitted"):
+        ma, sa = batch_mean_se([o[key].sum() for o in a])
+        mb, sb = batch_mean_se([o[key].sum() for o in b])
+        assert abs(ma - mb) <= 3 * math.sqrt(sa ** 2 + sb ** 2), (key, ma, mb)
+    ma, sa = batch_mean_se([o["film"].sum() for o in a])
+    mb, sb = batch_mean_se([o["film"].sum() for o in b])
+    assert abs(ma - mb) <= 3 * math.sqrt(sa ** 2 + sb ** 2)
+    steps_a = sum(o["counters"]["steps"] for o in a)
+    steps_b = sum(o["counters"]["steps"] for o in b)
+    assert steps_b < 0.5 * steps_a
+    assert all(o["counters"]["majorant_violations"] == 0 for o in b)
