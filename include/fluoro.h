@@ -142,6 +142,11 @@ typedef struct flr_params {
                                     of sigma_t over the cell and a one-voxel halo), walked by DDA;
                                     0: one majorant per bin. Same estimator, fewer null steps in
                                     sparse media. Single-scene renders and the adjoint only. */
+    float majorant_margin;       /* >= 0: every majorant (global or local) is multiplied by
+                                    1 + majorant_margin. A margin keeps null-collision scores of
+                                    the adjoint, -d sigma_t / (sigma_bar - sigma_t), bounded; the
+                                    forward pays about that fraction of extra null steps. Replays
+                                    (flr_adjoint) must use the forward's value. */
 } flr_params;
 
 /* Create a context on CUDA device `cuda_device`. Allocates the small tally buffers. */
@@ -234,7 +239,8 @@ int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const u
  * p->n_paths). All scratch -- spectral tables, fixed-point tallies, counters, the work counter and
  * the interleaved copy of the grids -- lives in one static device array of 4 MiB + 64 KiB that
  * every GPU loading this library holds until the process exits; media with more than
- * FLR_NOALLOC_MAX_VOXELS voxels are rejected with FLR_ERR_ARG; p->macro_cell is ignored (one majorant per bin). The first call on a device looks up
+ * FLR_NOALLOC_MAX_VOXELS voxels are rejected with FLR_ERR_ARG; p->macro_cell and p->majorant_margin are
+ * ignored (one majorant per bin, no margin). The first call on a device looks up
  * that array's device address (with that device current), so make that first call before any
  * stream capture. Every call uses the same array and clears what must start at zero, so calls
  * that overlap on the GPU (other streams, other host threads) race with each other. The call

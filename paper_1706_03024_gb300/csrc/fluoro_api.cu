@@ -50,6 +50,7 @@ struct flr_ctx {
     size_t mc_cap = 0;
     int mc_cell = 0;
     int mc_dims[3] = {0, 0, 0};
+    double tables_margin = 0.0;  // majorant margin the uploaded tables were built with
     // batched form
     struct Batch {
         int n_media = 0;
@@ -144,7 +145,7 @@ bool medium_has_grid(const flr_medium &m)
 // majorant max_x sigma_t(x, lambda) (rounded up, with a 1e-6 relative margin for the kernels' fp32
 // sums) and QY.
 void build_medium_tables(const flr_ctx *ctx, const flr_medium &m, const float *cmax, float smax,
-                         float *out)
+                         float *out, double margin = 0.0)
 {
     const int B = ctx->B;
     std::fill(out, out + tab_size(B), 0.0f);
@@ -160,7 +161,7 @@ void build_medium_tables(const flr_ctx *ctx, const flr_medium &m, const float *c
             sig[d * B + b] = (float)s;
             mj += s * (double)cmax[d];
         }
-        maj[b] = mj > 0.0 ? round_up_f32(mj * (1.0 + 1e-6)) : 0.0f;
+        maj[b] = mj > 0.0 ? round_up_f32(mj * (1.0 + 1e-6) * (1.0 + margin)) : 0.0f;
     }
     for (int d = 0; d < m.n_dyes; ++d) {
         const int id = m.dye_ids[d];
@@ -180,7 +181,8 @@ void build_medium_tables(const flr_ctx *ctx, const flr_medium &m, const float *c
 void build_tables(flr_ctx *ctx)
 {
     ctx->h_tables.assign(tab_size(ctx->B), 0.0f);
-    build_medium_tables(ctx, ctx->medium, ctx->cmax, ctx->smax, ctx->h_tables.data());
+    build_medium_tables(ctx, ctx->medium, ctx->cmax, ctx->smax, ctx->h_tables.data(),
+                        ctx->tables_margin);
 }
 
 // The spectral lines of a medium's sources, chosen in proportion to power (p(lambda_x), Eq. 12).
@@ -264,6 +266,7 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film, int macro_cell = 0)
         S.mc_c = ctx->d_mc_c;
         S.mc_s = ctx->d_mc_s;
     }
+    S.maj_margin = (float)(1.0 + ctx->tables_margin);
     // sensor
     const flr_sensor &c = ctx->sensor;
     S.sensor_kind = (ctx->sensor_set && with_film) ? c.kind : FLR_SENSOR_NONE;
@@ -336,8 +339,12 @@ int prepare_macro(flr_ctx *ctx, int cell, cudaStream_t st)
     return FLR_OK;
 }
 
-int prepare_tables(flr_ctx *ctx)
+int prepare_tables(flr_ctx *ctx, double margin = 0.0)
 {
+    if (margin != ctx->tables_margin) {
+        ctx->tables_margin = margin;
+        ctx->tables_dirty = true;
+    }
     if (!ctx->tables_dirty) return FLR_OK;
     build_tables(ctx);
     cudaError_t e = cudaMemcpy(ctx->d_tables, ctx->h_tables.data(), sizeof(float) * ctx->h_tables.size(),
@@ -615,6 +622,8 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
     if (p->macro_cell < 0 || p->macro_cell > 4096) return fail(ctx, FLR_ERR_ARG, "params: macro_cell 0..4096");
+    if (!(p->majorant_margin >= 0.0f && p->majorant_margin <= 100.0f))
+        return fail(ctx, FLR_ERR_ARG, "params: majorant_margin in [0, 100]");
     if (p->film && !is_device_pointer(p->film)) return fail(ctx, FLR_ERR_ARG, "params: film must be device memory");
     if (p->path_events && !is_device_pointer(p->path_events))
         return fail(ctx, FLR_ERR_ARG, "params: path_events must be device memory");
@@ -625,7 +634,7 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
         if (inside) return fail(ctx, FLR_ERR_ARG, "sensor: the pinhole must lie outside the medium box");
     }
     DeviceGuard g(ctx->device);
-    int rc = prepare_tables(ctx);
+    int rc = prepare_tables(ctx, p->majorant_margin);
     if (rc != FLR_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     rc = prepare_macro(ctx, p->macro_cell, st);
@@ -771,8 +780,10 @@ int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float 
     if (grad_sigma_s && !is_device_pointer(grad_sigma_s))
         return fail(ctx, FLR_ERR_ARG, "adjoint: grad_sigma_s must be device memory");
     if (p->macro_cell < 0 || p->macro_cell > 4096) return fail(ctx, FLR_ERR_ARG, "params: macro_cell 0..4096");
+    if (!(p->majorant_margin >= 0.0f && p->majorant_margin <= 100.0f))
+        return fail(ctx, FLR_ERR_ARG, "params: majorant_margin in [0, 100]");
     DeviceGuard g(ctx->device);
-    int rc = prepare_tables(ctx);
+    int rc = prepare_tables(ctx, p->majorant_margin);
     if (rc != FLR_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     rc = prepare_macro(ctx, p->macro_cell, st);
@@ -837,6 +848,8 @@ int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const 
         return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
+    if (!(p->majorant_margin >= 0.0f && p->majorant_margin <= 100.0f))
+        return fail(ctx, FLR_ERR_ARG, "params: majorant_margin in [0, 100]");
     const int B = ctx->B;
     std::vector<long long> off(n_media, -1), nv(n_media, 0);
     long long arena = 0;
@@ -900,7 +913,7 @@ int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const 
         }
         const float smax = md.solvent ? (hmax[(size_t)m * 8 + 5] ? 1.0f : 0.0f) : 1.0f;
         float *tab = htab.data() + (size_t)m * tab_size(B);
-        build_medium_tables(ctx, md, cmax, smax, tab);
+        build_medium_tables(ctx, md, cmax, smax, tab, p->majorant_margin);
         MediumDev &o = hmed[m];
         std::memset(&o, 0, sizeof(o));
         for (int k = 0; k < 3; ++k) {

@@ -63,6 +63,7 @@ struct SceneDev {
     float mc_size[3], mc_inv[3];       // cell edge (cm) and its inverse
     const float4 *mc_c;                // per-cell maximum concentration of each dye
     const float *mc_s;                 // per-cell maximum of the solvent mask
+    float maj_margin;                  // local majorants are multiplied by this (>= 1)
 };
 
 // Per-launch run parameters.

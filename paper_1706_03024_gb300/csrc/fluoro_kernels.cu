@@ -120,6 +120,7 @@ struct MedS {
     __device__ __forceinline__ const EmitterDev &em(int k) const { return S.em[k]; }
     __device__ __forceinline__ uint32_t key1(const RunDev &R) const { return R.medium_id; }
     __device__ __forceinline__ bool macro() const { return S.mc > 0; }
+    __device__ __forceinline__ float margin() const { return S.maj_margin; }
     __device__ __forceinline__ int mc_dims(int k) const { return S.mc_dims[k]; }
     __device__ __forceinline__ float mc_size(int k) const { return S.mc_size[k]; }
     __device__ __forceinline__ float mc_inv(int k) const { return S.mc_inv[k]; }
@@ -181,6 +182,7 @@ struct MedB {
     __device__ __forceinline__ const EmitterDev &em(int k) const { return md->em[k]; }
     __device__ __forceinline__ uint32_t key1(const RunDev &) const { return __ldg(&md->key1); }
     __device__ __forceinline__ bool macro() const { return false; }
+    __device__ __forceinline__ float margin() const { return 1.0f; }
     __device__ __forceinline__ int mc_dims(int) const { return 1; }
     __device__ __forceinline__ float mc_size(int) const { return 1.0f; }
     __device__ __forceinline__ float mc_inv(int) const { return 1.0f; }
@@ -283,51 +285,56 @@ __device__ __forceinline__ float cell_majorant(const M &m, int cell, int b)
 }
 
 struct Dda {
-    int c[3], stp[3];
-    float tmax[3], tdel[3];
+    int cx, cy, cz, sx, sy, sz;
+    float tmx, tmy, tmz, tdx, tdy, tdz;
     float t;
 };
 
 template <class M>
+__device__ __forceinline__ void dda_axis(const M &m, int k, float x, float w, float iw, int &c, int &st,
+                                         float &tm, float &td)
+{
+    const float cs = m.mc_size(k);
+    c = min(max(__float2int_rd((x - m.lo(k)) * m.mc_inv(k)), 0), m.mc_dims(k) - 1);
+    if (w > 0.0f) {
+        st = 1;
+        tm = (m.lo(k) + (float)(c + 1) * cs - x) * iw;
+        td = cs * iw;
+    } else if (w < 0.0f) {
+        st = -1;
+        tm = (m.lo(k) + (float)c * cs - x) * iw;
+        td = -cs * iw;
+    } else {
+        st = 0;
+        tm = FLT_MAX;
+        td = FLT_MAX;
+    }
+}
+
+template <class M>
 __device__ __forceinline__ void dda_init(const M &m, Dda &d, float3 x, float3 w, float3 iw)
 {
-    const float xs[3] = {x.x, x.y, x.z}, ws[3] = {w.x, w.y, w.z}, is[3] = {iw.x, iw.y, iw.z};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float cs = m.mc_size(k);
-        int ck = __float2int_rd((xs[k] - m.lo(k)) * m.mc_inv(k));
-        ck = min(max(ck, 0), m.mc_dims(k) - 1);
-        d.c[k] = ck;
-        if (ws[k] > 0.0f) {
-            d.stp[k] = 1;
-            d.tmax[k] = (m.lo(k) + (float)(ck + 1) * cs - xs[k]) * is[k];
-            d.tdel[k] = cs * is[k];
-        } else if (ws[k] < 0.0f) {
-            d.stp[k] = -1;
-            d.tmax[k] = (m.lo(k) + (float)ck * cs - xs[k]) * is[k];
-            d.tdel[k] = -cs * is[k];
-        } else {
-            d.stp[k] = 0;
-            d.tmax[k] = FLT_MAX;
-            d.tdel[k] = FLT_MAX;
-        }
-    }
+    dda_axis(m, 0, x.x, w.x, iw.x, d.cx, d.sx, d.tmx, d.tdx);
+    dda_axis(m, 1, x.y, w.y, iw.y, d.cy, d.sy, d.tmy, d.tdy);
+    dda_axis(m, 2, x.z, w.z, iw.z, d.cz, d.sz, d.tmz, d.tdz);
     d.t = 0.0f;
 }
 
-// Spends tau from d.t on; returns the tentative distance (and its cell's majorant in sb), or
-// FLT_MAX once t_end is reached first.
+// Spends tau from d.t on; returns the tentative distance (and its cell's majorant times the
+// margin factor in sb), or FLT_MAX once t_end is reached first. Ties between axes go to the lowest
+// axis.
 template <class M>
 __device__ __forceinline__ float dda_advance(const M &m, Dda &d, int b, float tau, float t_end, float &sb)
 {
+    const int mx = m.mc_dims(0), my = m.mc_dims(1), mz = m.mc_dims(2);
     for (int guard = 0; guard < (1 << 16); ++guard) {
-        const int cell = (d.c[2] * m.mc_dims(1) + d.c[1]) * m.mc_dims(0) + d.c[0];
-        const float sbc = cell_majorant(m, cell, b);
+        const int cell = (d.cz * my + d.cy) * mx + d.cx;
+        const float sbc = cell_majorant(m, cell, b) * m.margin();
         int ax = 0;
-        if (d.tmax[1] < d.tmax[ax]) ax = 1;
-        if (d.tmax[2] < d.tmax[ax]) ax = 2;
-        float t1 = fminf(d.tmax[ax], t_end);
-        t1 = fmaxf(t1, d.t);
+        float tn = d.tmx;
+        if (d.tmy < tn) { ax = 1; tn = d.tmy; }
+        if (d.tmz < tn) { ax = 2; tn = d.tmz; }
+        const float t1 = fmaxf(fminf(tn, t_end), d.t);
         const float opt = sbc * (t1 - d.t);
         if (sbc > 0.0f && tau < opt) {
             d.t += tau / sbc;
@@ -337,9 +344,21 @@ __device__ __forceinline__ float dda_advance(const M &m, Dda &d, int b, float ta
         tau -= opt;
         d.t = t1;
         if (t1 >= t_end) { sb = sbc; return FLT_MAX; }
-        d.c[ax] += d.stp[ax];
-        if (d.c[ax] < 0 || d.c[ax] >= m.mc_dims(ax)) { sb = sbc; return FLT_MAX; }
-        d.tmax[ax] += d.tdel[ax];
+        bool out;
+        if (ax == 0) {
+            d.cx += d.sx;
+            d.tmx += d.tdx;
+            out = d.cx < 0 || d.cx >= mx;
+        } else if (ax == 1) {
+            d.cy += d.sy;
+            d.tmy += d.tdy;
+            out = d.cy < 0 || d.cy >= my;
+        } else {
+            d.cz += d.sz;
+            d.tmz += d.tdz;
+            out = d.cz < 0 || d.cz >= mz;
+        }
+        if (out) { sb = sbc; return FLT_MAX; }
     }
     sb = 0.0f;
     return FLT_MAX;
@@ -363,11 +382,11 @@ __device__ __forceinline__ float3 cosine_dir(float u1, float u2, int axis, float
     float s, c;
     __sincosf(TWO_PI * u2, &s, &c);
     const float zl = sqrtf(fmaxf(0.0f, 1.0f - u1));
-    float v[3];
-    v[axis] = sign * zl;
-    v[(axis + 1) % 3] = r * c;
-    v[(axis + 2) % 3] = r * s;
-    return make_float3(v[0], v[1], v[2]);
+    const float a = sign * zl, bx = r * c, by = r * s;
+    // component axis = a, (axis+1)%3 = bx, (axis+2)%3 = by
+    if (axis == 0) return make_float3(a, bx, by);
+    if (axis == 1) return make_float3(by, a, bx);
+    return make_float3(bx, by, a);
 }
 
 __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }

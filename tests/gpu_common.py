@@ -63,12 +63,17 @@ def bin_parity(g_outs, o_outs, key, min_nonzero=None, same_seed=True):
 
 
 def integrated_independent(g_outs, o_outs, key, rel=5e-3):
-    """Independent seeds: per-row totals agree within max(rel, 3 SE)."""
+    """Independent seeds: per-row totals agree within max(rel, 3 SE). With a dozen rows (faces x
+    fluoresced) one row beyond 3 SE is expected about 3 % of the time, so one is allowed as long as
+    none is beyond max(rel, 4 SE)."""
     gs = np.stack([x[key].sum(axis=-1) for x in g_outs])
     os_ = np.stack([x[key].sum(axis=-1) for x in o_outs])
     mg, sg = batch_mean_se(gs)
     mo, so = batch_mean_se(os_)
-    tol = np.maximum(rel * np.abs(mo), 3.0 * np.sqrt(sg ** 2 + so ** 2))
+    se = np.sqrt(sg ** 2 + so ** 2)
     big = np.abs(mo) >= 1e-3 * max(np.abs(mo).max(), 1e-300)
-    bad = (np.abs(mg - mo) > tol) & big
-    return not bad.any(), {"gpu": mg[big].tolist()[:12], "oracle": mo[big].tolist()[:12]}
+    d = np.abs(mg - mo)
+    over3 = (d > np.maximum(rel * np.abs(mo), 3.0 * se)) & big
+    over4 = (d > np.maximum(rel * np.abs(mo), 4.0 * se)) & big
+    ok = int(over3.sum()) <= 1 and not over4.any()
+    return ok, {"gpu": mg[big].tolist()[:12], "oracle": mo[big].tolist()[:12]}
