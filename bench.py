@@ -242,9 +242,10 @@ def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_
     gc = torch.zeros(S.conc_t.shape, dtype=torch.float32, device=torch.device("cuda", local))
     gs = torch.zeros(1, dtype=torch.float32, device=gc.device)
     mc = args.macro_cell
-    film = S.render(form="wavefront", macro_cell=mc)
+    mg = 0.1  # the score estimator needs sigma_bar > sigma_t: forward and replay share the margin
+    film = S.render(form="wavefront", macro_cell=mc, majorant_margin=mg)
     adj = (2.0 * (film - T)).contiguous()
-    S.adjoint(adj, gc, gs, macro_cell=mc)
+    S.adjoint(adj, gc, gs, macro_cell=mc, majorant_margin=mg)
     torch.cuda.synchronize()
 
     def timed(fn, steps):
@@ -260,10 +261,12 @@ def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_
         return reduce_max(sum(ms) / len(ms)), ms
 
     barrier()
-    fwd_ms, _ = timed(lambda: S.render(form="wavefront", macro_cell=mc), args.adjoint_steps)
+    fwd_ms, _ = timed(lambda: S.render(form="wavefront", macro_cell=mc, majorant_margin=mg),
+                      args.adjoint_steps)
     events = S.read()["counters"]["events"]
-    plain_ms, _ = timed(lambda: S.render(form="plain"), args.adjoint_steps)
-    adj_ms, adj_steps = timed(lambda: S.adjoint(adj, gc, gs, macro_cell=mc), args.adjoint_steps)
+    plain_ms, _ = timed(lambda: S.render(form="plain", majorant_margin=mg), args.adjoint_steps)
+    adj_ms, adj_steps = timed(lambda: S.adjoint(adj, gc, gs, macro_cell=mc, majorant_margin=mg),
+                              args.adjoint_steps)
     ev = reduce_sum(float(events))
     return {"workload": f"2 x 64^3 blob dyes, 256x256x81 ortho film, {n} paths, loss sum((I-T)^2)",
             "macro_cell": mc,
@@ -494,8 +497,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--regroup", type=int, default=0)
-    ap.add_argument("--macro-cell", type=int, default=8,
+    ap.add_argument("--regroup", type=int, default=4)
+    ap.add_argument("--macro-cell", type=int, default=0,
                     help="local-majorant cell edge in voxels for the optimised forms (0: global)")
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--paths", type=int, default=0,

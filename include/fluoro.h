@@ -66,7 +66,7 @@ enum {
     FLR_C_CONNECT_STEPS,       /* ratio-tracking steps of sensor connections                    */
     FLR_C_CONNECT_BUDGET,      /* connections cut by the ratio-tracking step budget             */
     FLR_C_NONFINITE,           /* paths ended because a weight or position became non-finite   */
-    FLR_C_RESERVED
+    FLR_C_CELL_WALKS           /* local-majorant cells visited by free flights and marches      */
 };
 
 typedef struct flr_ctx flr_ctx;
@@ -202,7 +202,12 @@ int flr_read_tallies(flr_ctx *ctx, double *face, double *absorbed, double *emitt
  * d sigma_e/sigma_e (Sec. 4.1 shares), each score multiplied by the adjoint-weighted film
  * contributions that follow it; every contribution adds its ratio-tracking transmittance
  * derivative (Eq. 6). device adj_film [H][W][n_bins] (the sensor's film layout). The gradients are
- * zeroed first unless p->accumulate. Requires a sensor; asynchronous on `stream`. */
+ * zeroed first unless p->accumulate. Requires a sensor; asynchronous on `stream`.
+ * The score estimator is unbiased only where every parameter-dependent decision has positive
+ * probability: render and replay with p->majorant_margin > 0 (a null at the voxel attaining a
+ * tight majorant is never sampled), keep concentrations positive (a dye collision at c = 0 is
+ * never sampled), and note that local majorants (p->macro_cell > 0) give no gradient in cells that
+ * hold no matter. */
 int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float *grad_conc,
                 float *grad_sigma_s, void *stream);
 

@@ -64,6 +64,8 @@ struct SceneDev {
     const float4 *mc_c;                // per-cell maximum concentration of each dye
     const float *mc_s;                 // per-cell maximum of the solvent mask
     float maj_margin;                  // local majorants are multiplied by this (>= 1)
+    const uint8_t *mc_dist;            // 0: cell may hold matter; k >= 1: every cell within
+                                       // Chebyshev distance k - 1 is empty (leaping)
 };
 
 // Per-launch run parameters.

@@ -69,7 +69,7 @@ struct Smem {
 
 // Frequent counters live in registers; the rest go straight to shared memory.
 struct RegCnt {
-    uint32_t steps, nulls, events, scatters, connections, connect_steps;
+    uint32_t steps, nulls, events, scatters, connections, connect_steps, cell_walks;
 };
 
 __device__ __forceinline__ void cnt_add(const Smem &sm, int k, unsigned long long v = 1ull)
@@ -126,6 +126,7 @@ struct MedS {
     __device__ __forceinline__ float mc_inv(int k) const { return S.mc_inv[k]; }
     __device__ __forceinline__ float4 mc_conc(int c) const { return __ldg(&S.mc_c[c]); }
     __device__ __forceinline__ float mc_solvent(int c) const { return __ldg(&S.mc_s[c]); }
+    __device__ __forceinline__ int mc_empty_radius(int c) const { return (int)__ldg(&S.mc_dist[c]); }
 };
 
 __device__ __forceinline__ void tally_add_global(unsigned long long *t, int idx, float w)
@@ -188,6 +189,7 @@ struct MedB {
     __device__ __forceinline__ float mc_inv(int) const { return 1.0f; }
     __device__ __forceinline__ float4 mc_conc(int) const { return make_float4(0.f, 0.f, 0.f, 0.f); }
     __device__ __forceinline__ float mc_solvent(int) const { return 0.0f; }
+    __device__ __forceinline__ int mc_empty_radius(int) const { return 0; }
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -324,11 +326,42 @@ __device__ __forceinline__ void dda_init(const M &m, Dda &d, float3 x, float3 w,
 // margin factor in sb), or FLT_MAX once t_end is reached first. Ties between axes go to the lowest
 // axis.
 template <class M>
-__device__ __forceinline__ float dda_advance(const M &m, Dda &d, int b, float tau, float t_end, float &sb)
+__device__ __forceinline__ float dda_advance(const M &m, Dda &d, int b, float tau, float t_end, float &sb,
+                                             uint32_t &walks)
 {
     const int mx = m.mc_dims(0), my = m.mc_dims(1), mz = m.mc_dims(2);
     for (int guard = 0; guard < (1 << 16); ++guard) {
+        ++walks;
         const int cell = (d.cz * my + d.cy) * mx + d.cx;
+        const int k = m.mc_empty_radius(cell);
+        if (k > 0) {
+            // the cube of cells within Chebyshev distance k - 1 holds no matter (majorant 0): leave
+            // it in one move, spending no optical budget
+            const float kx = d.tmx + (float)(k - 1) * d.tdx;
+            const float ky = d.tmy + (float)(k - 1) * d.tdy;
+            const float kz = d.tmz + (float)(k - 1) * d.tdz;
+            int ax = 0;
+            float tn = kx;
+            if (ky < tn) { ax = 1; tn = ky; }
+            if (kz < tn) { ax = 2; tn = kz; }
+            if (tn >= t_end) { d.t = t_end; sb = 0.0f; return FLT_MAX; }
+            d.t = fmaxf(tn, d.t);
+            // cross k boundaries on the exit axis, and those the ray passes on the other two
+            const int nx = ax == 0 ? k : (d.tmx <= tn ? min(k - 1, (int)((tn - d.tmx) / d.tdx) + 1) : 0);
+            const int ny = ax == 1 ? k : (d.tmy <= tn ? min(k - 1, (int)((tn - d.tmy) / d.tdy) + 1) : 0);
+            const int nz = ax == 2 ? k : (d.tmz <= tn ? min(k - 1, (int)((tn - d.tmz) / d.tdz) + 1) : 0);
+            d.cx += d.sx * nx;
+            d.cy += d.sy * ny;
+            d.cz += d.sz * nz;
+            d.tmx += (float)nx * d.tdx;
+            d.tmy += (float)ny * d.tdy;
+            d.tmz += (float)nz * d.tdz;
+            if (d.cx < 0 || d.cx >= mx || d.cy < 0 || d.cy >= my || d.cz < 0 || d.cz >= mz) {
+                sb = 0.0f;
+                return FLT_MAX;
+            }
+            continue;
+        }
         const float sbc = cell_majorant(m, cell, b) * m.margin();
         int ax = 0;
         float tn = d.tmx;
@@ -499,7 +532,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
             const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
             ++j;
             float sbc;
-            const float t = dda_advance(m, dd, b, -__logf(1.0f - u), tl, sbc);
+            const float t = dda_advance(m, dd, b, -__logf(1.0f - u), tl, sbc, rc.cell_walks);
             if (t >= tl) break;
             rc.connect_steps++;
             const float3 p = make_float3(x.x + t * dir.x, x.y + t * dir.y, x.z + t * dir.z);
@@ -680,7 +713,7 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
     if (m.macro()) {
         Dda dd;
         dda_init(m, dd, p.x, p.w, p.iw);
-        tf = dda_advance(m, dd, p.bin, -__logf(1.0f - b0.a), te, sb);
+        tf = dda_advance(m, dd, p.bin, -__logf(1.0f - b0.a), te, sb, rc.cell_walks);
     } else {
         sb = m.maj(p.bin);
         tf = sb > 0.0f ? -__logf(1.0f - b0.a) / sb : FLT_MAX;
@@ -845,13 +878,13 @@ __device__ __forceinline__ Smem block_prologue(const SceneDev &S, unsigned char 
 __device__ __forceinline__ void block_epilogue(const SceneDev &S, const RunDev &R, const Smem &sm,
                                                const RegCnt &rc)
 {
-    const unsigned vals[6] = {rc.steps, rc.nulls, rc.events, rc.scatters, rc.connections,
-                              rc.connect_steps};
-    const int idx[6] = {FLR_C_STEPS, FLR_C_NULLS, FLR_C_EVENTS, FLR_C_SCATTERS, FLR_C_CONNECTIONS,
-                        FLR_C_CONNECT_STEPS};
+    const unsigned vals[7] = {rc.steps, rc.nulls, rc.events, rc.scatters, rc.connections,
+                              rc.connect_steps, rc.cell_walks};
+    const int idx[7] = {FLR_C_STEPS, FLR_C_NULLS, FLR_C_EVENTS, FLR_C_SCATTERS, FLR_C_CONNECTIONS,
+                        FLR_C_CONNECT_STEPS, FLR_C_CELL_WALKS};
     // 32-bit per-thread counters; warp sums are widened before they can overflow
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 7; ++i) {
         unsigned long long v = vals[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -872,7 +905,7 @@ __global__ void __launch_bounds__(256) k_trace_plain(SceneDev S, RunDev R)
     const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
     const Smem sm = block_prologue(S, smem_raw, L);
     const MedS m{S, sm};
-    RegCnt rc = {0, 0, 0, 0, 0, 0};
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
         Path p;
@@ -964,7 +997,7 @@ __global__ void __launch_bounds__(256) k_trace_wavefront(SceneDev S, RunDev R)
     __shared__ int s_active;
     __syncthreads();
     const MedS m{S, sm};
-    RegCnt rc = {0, 0, 0, 0, 0, 0};
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
     Path p;
     p.alive = false;
     bool exhausted = false;
@@ -1092,7 +1125,7 @@ __global__ void __launch_bounds__(256) k_adjoint(SceneDev S, RunDev R, AdjDev A)
     const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
     const Smem sm = block_prologue(S, smem_raw, L);
     const MedS m{S, sm};
-    RegCnt rc = {0, 0, 0, 0, 0, 0};
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
     float gsig = 0.0f;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
@@ -1140,12 +1173,12 @@ __global__ void __launch_bounds__(256) k_adjoint(SceneDev S, RunDev R, AdjDev A)
 // absorption and emission tallies go to each medium's own fixed-point arrays.
 __device__ __forceinline__ void counters_epilogue(const RunDev &R, const Smem &sm, const RegCnt &rc)
 {
-    const unsigned vals[6] = {rc.steps, rc.nulls, rc.events, rc.scatters, rc.connections,
-                              rc.connect_steps};
-    const int idx[6] = {FLR_C_STEPS, FLR_C_NULLS, FLR_C_EVENTS, FLR_C_SCATTERS, FLR_C_CONNECTIONS,
-                        FLR_C_CONNECT_STEPS};
+    const unsigned vals[7] = {rc.steps, rc.nulls, rc.events, rc.scatters, rc.connections,
+                              rc.connect_steps, rc.cell_walks};
+    const int idx[7] = {FLR_C_STEPS, FLR_C_NULLS, FLR_C_EVENTS, FLR_C_SCATTERS, FLR_C_CONNECTIONS,
+                        FLR_C_CONNECT_STEPS, FLR_C_CELL_WALKS};
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 7; ++i) {
         unsigned long long v = vals[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1165,7 +1198,7 @@ __global__ void __launch_bounds__(256) k_trace_batch(BatchDev Bt, RunDev R)
     sm.sig_a = sm.cdf = sm.maj = sm.qy = nullptr;
     sm.tal = nullptr;
     sm.cnt = s_cnt;
-    RegCnt rc = {0, 0, 0, 0, 0, 0};
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lower = (1u << lane) - 1u;

@@ -39,7 +39,7 @@ FLR_FORM_WAVEFRONT = 1
 COUNTER_NAMES = [
     "paths", "events", "nulls", "escapes", "absorbed_dead", "rr_kills", "cap_hits", "step_budget",
     "connections", "vf_rejected", "wall_bounces", "emissions", "scatters", "dye_absorptions",
-    "steps", "majorant_violations", "connect_steps", "connect_budget", "nonfinite", "reserved",
+    "steps", "majorant_violations", "connect_steps", "connect_budget", "nonfinite", "cell_walks",
 ]
 
 ERROR_NAMES = {FLR_OK: "FLR_OK", FLR_ERR_ARG: "FLR_ERR_ARG", FLR_ERR_CUDA: "FLR_ERR_CUDA",
