@@ -142,6 +142,12 @@ typedef struct flr_params {
                                     of sigma_t over the cell and a one-voxel halo), walked by DDA;
                                     0: one majorant per bin. Same estimator, fewer null steps in
                                     sparse media. Single-scene renders and the adjoint only. */
+    int skip_cell;               /* > 0 (with macro_cell = 0): after a null collision where
+                                    sigma_t = 0, leave the largest cube of skip_cell^3-voxel cells
+                                    around it that holds no matter and restart the free flight at
+                                    its boundary (exact: every tentative collision inside would be
+                                    a null); transmittance marches leap the same way. Gives no
+                                    gradient for voxels in such cubes. 0: off. */
     float majorant_margin;       /* >= 0: every majorant (global or local) is multiplied by
                                     1 + majorant_margin. A margin keeps null-collision scores of
                                     the adjoint, -d sigma_t / (sigma_bar - sigma_t), bounded; the

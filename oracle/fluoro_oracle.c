@@ -120,6 +120,10 @@ typedef struct {
     /* free flights against a grid of local majorants: cells of macro_cell^3 voxels, each the
      * maximum of sigma_t over its voxels and a one-voxel halo; 0 = one majorant per bin */
     int macro_cell;
+    /* > 0 (with macro_cell = 0): after a null collision where sigma_t = 0, leave the largest cube
+     * of skip_cell^3-voxel cells around it that holds no matter and restart the free flight at its
+     * boundary (memoryless: every tentative collision inside would be a null) */
+    int skip_cell;
 } or_params;
 
 typedef struct {
@@ -196,6 +200,8 @@ typedef struct {
     int mc, mdims[3];
     double *mc_cmax;                         /* [cells][n_dyes] */
     double *mc_smax;                         /* [cells]         */
+    int sk, sdims[3];
+    unsigned char *sk_dist;                  /* Chebyshev distance to a cell with matter */
 } tables;
 
 static int nvox(const or_scene *s);
@@ -244,7 +250,99 @@ static void free_macro(tables *t)
 {
     free(t->mc_cmax);
     free(t->mc_smax);
+    free(t->sk_dist);
     t->mc_cmax = t->mc_smax = NULL;
+    t->sk_dist = NULL;
+}
+
+/* Empty-space distances over cells of `cell`^3 voxels: a cell holds matter if any voxel of it or
+ * of its one-voxel halo has solvent (with sigma_s + sigma_a0 > 0) or a positive concentration;
+ * every other cell stores its Chebyshev distance (in cells, at most 255) to the nearest such
+ * cell, found by breadth-first search over the 26 neighbours. */
+static void build_skip(const or_scene *s, tables *t, int cell)
+{
+    t->sk = 0;
+    if (cell <= 0 || t->homogeneous) return;
+    int64_t nc = 1;
+    for (int k = 0; k < 3; ++k) {
+        t->sdims[k] = (s->dims[k] + cell - 1) / cell;
+        nc *= t->sdims[k];
+    }
+    t->sk = cell;
+    t->sk_dist = (unsigned char *)malloc((size_t)nc);
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);
+    int64_t head = 0, tail = 0;
+    const int solvent_matter = (s->sigma_s + s->sigma_a0) > 0.0;
+    for (int cz = 0; cz < t->sdims[2]; ++cz)
+        for (int cy = 0; cy < t->sdims[1]; ++cy)
+            for (int cx = 0; cx < t->sdims[0]; ++cx) {
+                int64_t c = ((int64_t)cz * t->sdims[1] + cy) * t->sdims[0] + cx;
+                int lo[3] = { cx * cell - 1, cy * cell - 1, cz * cell - 1 };
+                int hi[3] = { (cx + 1) * cell, (cy + 1) * cell, (cz + 1) * cell };
+                for (int k = 0; k < 3; ++k) {
+                    if (lo[k] < 0) lo[k] = 0;
+                    if (hi[k] > s->dims[k] - 1) hi[k] = s->dims[k] - 1;
+                }
+                int matter = 0;
+                for (int z = lo[2]; z <= hi[2] && !matter; ++z)
+                    for (int y = lo[1]; y <= hi[1] && !matter; ++y)
+                        for (int x = lo[0]; x <= hi[0] && !matter; ++x) {
+                            int v = (z * s->dims[1] + y) * s->dims[0] + x;
+                            if ((s->solvent ? s->solvent[v] != 0 : 1) && solvent_matter) matter = 1;
+                            for (int d = 0; d < s->n_dyes && !matter; ++d) {
+                                double cv = s->conc ? (double)s->conc[(size_t)d * nvox(s) + v]
+                                                    : (double)s->conc_uniform[d];
+                                if (cv > 0.0) matter = 1;
+                            }
+                        }
+                t->sk_dist[c] = matter ? 0 : 255;
+                if (matter) queue[tail++] = c;
+            }
+    while (head < tail) {
+        int64_t c = queue[head++];
+        int cx = (int)(c % t->sdims[0]), cy = (int)((c / t->sdims[0]) % t->sdims[1]);
+        int cz = (int)(c / ((int64_t)t->sdims[0] * t->sdims[1]));
+        int next = t->sk_dist[c] + 1;
+        if (next >= 255) continue;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int x = cx + dx, y = cy + dy, z = cz + dz;
+                    if (x < 0 || y < 0 || z < 0 || x >= t->sdims[0] || y >= t->sdims[1] || z >= t->sdims[2])
+                        continue;
+                    int64_t j = ((int64_t)z * t->sdims[1] + y) * t->sdims[0] + x;
+                    if (t->sk_dist[j] == 255) {
+                        t->sk_dist[j] = (unsigned char)next;
+                        queue[tail++] = j;
+                    }
+                }
+    }
+    free(queue);
+}
+
+/* Distance along (x, w) to leave the empty cube around x (0 if x's cell may hold matter). */
+static double empty_cube_exit(const or_scene *s, const tables *t, const double x[3], const double w[3])
+{
+    int c[3];
+    for (int k = 0; k < 3; ++k) {
+        double cs = t->sk * (s->hi[k] - s->lo[k]) / (double)s->dims[k];
+        int ck = (int)floor((x[k] - s->lo[k]) / cs);
+        if (ck < 0) ck = 0;
+        if (ck > t->sdims[k] - 1) ck = t->sdims[k] - 1;
+        c[k] = ck;
+    }
+    int kd = t->sk_dist[((int64_t)c[2] * t->sdims[1] + c[1]) * t->sdims[0] + c[0]];
+    if (kd == 0) return 0.0;
+    double best = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        double cs = t->sk * (s->hi[k] - s->lo[k]) / (double)s->dims[k];
+        double tk;
+        if (w[k] > 0.0) tk = (s->lo[k] + (c[k] + kd) * cs - x[k]) / w[k];
+        else if (w[k] < 0.0) tk = (s->lo[k] + (c[k] - kd + 1) * cs - x[k]) / w[k];
+        else continue;
+        if (tk < best) best = tk;
+    }
+    return best > 0.0 ? best : 0.0;
 }
 
 /* Copy the per-render evaluation settings into the tables (majorant scale and perturbation). */
@@ -663,6 +761,7 @@ static int sample_emission_bin(const tables *t, int d, double u)
 static void apply_params_macro(const or_scene *s, tables *t, const or_params *p)
 {
     build_macro(s, t, p->macro_cell);
+    if (p->macro_cell <= 0) build_skip(s, t, p->skip_cell);
 }
 
 /* Local majorant of macro cell c: the maximum of sigma_t over the cell (Sec. 4.1 coefficients). */
@@ -815,6 +914,14 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
             if (A) {
                 dec_rec r = { step, 0, vox, bin, -1, c.total, sb, solv, 0.0 };
                 adj_push_dec(A, r);
+            }
+            if (t->sk && c.total == 0.0) {
+                /* leave the empty cube: every tentative collision inside it would be a null */
+                int f2;
+                double te2 = exit_distance(s, x, w, &f2);
+                double tl = empty_cube_exit(s, t, x, w);
+                if (tl > te2) tl = te2;
+                for (int k = 0; k < 3; ++k) x[k] += tl * w[k];
             }
             continue;
         }

@@ -62,7 +62,7 @@ class Params(C.Structure):
                 ("analog", C.c_int), ("n_threads", C.c_int), ("max_events", C.c_int64),
                 ("max_steps", C.c_int64), ("majorant_scale", C.c_double), ("frozen", C.c_int),
                 ("pert_dye", C.c_int), ("pert_voxel", C.c_int64), ("pert_delta", C.c_double),
-                ("pert_sigma_s", C.c_double), ("macro_cell", C.c_int)]
+                ("pert_sigma_s", C.c_double), ("macro_cell", C.c_int), ("skip_cell", C.c_int)]
 
 
 class Result(C.Structure):
@@ -200,7 +200,7 @@ class _SceneHolder:
 def render(scene, n_paths=None, path_offset=0, seed=None, medium_id=0, n_threads=0,
            analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
            film=True, path_events=False, majorant_scale=1.0, frozen=False, pert=None,
-           macro_cell=0):
+           macro_cell=0, skip_cell=0):
     """Run the oracle; returns a dict of fp64 tallies normalised per launched path:
     face [2,6,B], absorbed [D+1,B], emitted [D,B], film [H,W,B] (or None), counters (dict),
     path_events u32[n] (or None).
@@ -212,6 +212,7 @@ def render(scene, n_paths=None, path_offset=0, seed=None, medium_id=0, n_threads
     p = _params(scene, n_paths, path_offset, seed, medium_id, n_threads, analog, max_inelastic,
                 n_rr, max_events, max_steps, majorant_scale, frozen, pert)
     p.macro_cell = int(macro_cell)
+    p.skip_cell = int(skip_cell)
     return _render(L, h, scene, p, film, path_events)
 
 
@@ -322,7 +323,7 @@ def majorant(scene):
 
 def adjoint(scene, adj, n_paths=None, path_offset=0, seed=None, medium_id=0, n_threads=0,
             analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
-            majorant_scale=1.0, macro_cell=0):
+            majorant_scale=1.0, macro_cell=0, skip_cell=0):
     """Reference gradient of sum(adj * film) over the same paths render() traces:
     returns (grad_conc [D,nz,ny,nx] or None, grad_sigma_s)."""
     L = lib()
@@ -330,6 +331,7 @@ def adjoint(scene, adj, n_paths=None, path_offset=0, seed=None, medium_id=0, n_t
     p = _params(scene, n_paths, path_offset, seed, medium_id, n_threads, analog, max_inelastic,
                 n_rr, max_events, max_steps, majorant_scale, False, None)
     p.macro_cell = int(macro_cell)
+    p.skip_cell = int(skip_cell)
     adj = np.ascontiguousarray(adj, dtype=np.float64)
     sn = scene["sensor"]
     assert adj.shape == (sn["height"], sn["width"], h.n_bins)

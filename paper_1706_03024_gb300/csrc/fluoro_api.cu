@@ -231,7 +231,7 @@ int build_emitters(flr_ctx *ctx, const flr_medium &m, int max_lines, EmitterDev 
     return FLR_OK;
 }
 
-int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film, int macro_cell = 0)
+int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film, int macro_cell = 0, int skip_cell = 0)
 {
     const flr_medium &m = ctx->medium;
     std::memset(&S, 0, sizeof(S));
@@ -256,11 +256,12 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film, int macro_cell = 0)
     const int rc = build_emitters(ctx, m, FLR_MAX_EMITTERS, S.em, S.em_cdf, &ne);
     if (rc != FLR_OK) return rc;
     S.n_emitters = ne;
-    if (macro_cell > 0 && !S.homogeneous && ctx->mc_cell == macro_cell) {
-        S.mc = macro_cell;
+    const int cell = macro_cell > 0 ? macro_cell : skip_cell;
+    if (cell > 0 && !S.homogeneous && ctx->mc_cell == cell) {
+        if (macro_cell > 0) S.mc = macro_cell; else S.sk = skip_cell;
         for (int k = 0; k < 3; ++k) {
             S.mc_dims[k] = ctx->mc_dims[k];
-            const double cs = (double)macro_cell * ((double)m.hi[k] - (double)m.lo[k]) / (double)S.dims[k];
+            const double cs = (double)cell * ((double)m.hi[k] - (double)m.lo[k]) / (double)S.dims[k];
             S.mc_size[k] = (float)cs;
             S.mc_inv[k] = (float)(1.0 / cs);
         }
@@ -668,7 +669,8 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
         return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
-    if (p->macro_cell < 0 || p->macro_cell > 4096) return fail(ctx, FLR_ERR_ARG, "params: macro_cell 0..4096");
+    if (p->macro_cell < 0 || p->macro_cell > 4096 || p->skip_cell < 0 || p->skip_cell > 4096)
+        return fail(ctx, FLR_ERR_ARG, "params: macro_cell and skip_cell 0..4096");
     if (!(p->majorant_margin >= 0.0f && p->majorant_margin <= 100.0f))
         return fail(ctx, FLR_ERR_ARG, "params: majorant_margin in [0, 100]");
     if (p->film && !is_device_pointer(p->film)) return fail(ctx, FLR_ERR_ARG, "params: film must be device memory");
@@ -684,10 +686,10 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     int rc = prepare_tables(ctx, p->majorant_margin);
     if (rc != FLR_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    rc = prepare_macro(ctx, p->macro_cell, st);
+    rc = prepare_macro(ctx, p->macro_cell > 0 ? p->macro_cell : p->skip_cell, st);
     if (rc != FLR_OK) return rc;
     SceneDev S;
-    rc = fill_scene(ctx, S, p->film != nullptr, p->macro_cell);
+    rc = fill_scene(ctx, S, p->film != nullptr, p->macro_cell, p->skip_cell);
     if (rc != FLR_OK) return rc;
     cudaError_t e = cudaSuccess;
     if (!p->accumulate) {
@@ -826,17 +828,18 @@ int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float 
     if (grad_conc && !is_device_pointer(grad_conc)) return fail(ctx, FLR_ERR_ARG, "adjoint: grad_conc must be device memory");
     if (grad_sigma_s && !is_device_pointer(grad_sigma_s))
         return fail(ctx, FLR_ERR_ARG, "adjoint: grad_sigma_s must be device memory");
-    if (p->macro_cell < 0 || p->macro_cell > 4096) return fail(ctx, FLR_ERR_ARG, "params: macro_cell 0..4096");
+    if (p->macro_cell < 0 || p->macro_cell > 4096 || p->skip_cell < 0 || p->skip_cell > 4096)
+        return fail(ctx, FLR_ERR_ARG, "params: macro_cell and skip_cell 0..4096");
     if (!(p->majorant_margin >= 0.0f && p->majorant_margin <= 100.0f))
         return fail(ctx, FLR_ERR_ARG, "params: majorant_margin in [0, 100]");
     DeviceGuard g(ctx->device);
     int rc = prepare_tables(ctx, p->majorant_margin);
     if (rc != FLR_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    rc = prepare_macro(ctx, p->macro_cell, st);
+    rc = prepare_macro(ctx, p->macro_cell > 0 ? p->macro_cell : p->skip_cell, st);
     if (rc != FLR_OK) return rc;
     SceneDev S;
-    rc = fill_scene(ctx, S, true, p->macro_cell);
+    rc = fill_scene(ctx, S, true, p->macro_cell, p->skip_cell);
     if (rc != FLR_OK) return rc;
     const long long nv = nvox(ctx->medium);
     cudaError_t e = cudaSuccess;

@@ -57,8 +57,9 @@ struct SceneDev {
     int sensor_kind, W, H;
     float s_origin[3], s_U[3], s_V[3], s_view[3];  // ortho: U, V pre-divided by |U|^2, |V|^2
     float tan_x, tan_y, inv_A_pix;
-    // local majorants (macro cells); mc == 0: one majorant per bin
-    int mc;
+    // local majorants (macro cells); mc == 0: one majorant per bin. sk > 0: empty-space leaps
+    // after null collisions (global majorant) over the same cell grid
+    int mc, sk;
     int mc_dims[3];
     float mc_size[3], mc_inv[3];       // cell edge (cm) and its inverse
     const float4 *mc_c;                // per-cell maximum concentration of each dye

@@ -127,6 +127,7 @@ struct MedS {
     __device__ __forceinline__ float4 mc_conc(int c) const { return __ldg(&S.mc_c[c]); }
     __device__ __forceinline__ float mc_solvent(int c) const { return __ldg(&S.mc_s[c]); }
     __device__ __forceinline__ int mc_empty_radius(int c) const { return (int)__ldg(&S.mc_dist[c]); }
+    __device__ __forceinline__ bool skip() const { return S.sk > 0; }
 };
 
 __device__ __forceinline__ void tally_add_global(unsigned long long *t, int idx, float w)
@@ -190,6 +191,7 @@ struct MedB {
     __device__ __forceinline__ float4 mc_conc(int) const { return make_float4(0.f, 0.f, 0.f, 0.f); }
     __device__ __forceinline__ float mc_solvent(int) const { return 0.0f; }
     __device__ __forceinline__ int mc_empty_radius(int) const { return 0; }
+    __device__ __forceinline__ bool skip() const { return false; }
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -397,6 +399,29 @@ __device__ __forceinline__ float dda_advance(const M &m, Dda &d, int b, float ta
     return FLT_MAX;
 }
 
+// Distance along (x, w) to leave the empty cube of cells around x (0 when x's cell may hold
+// matter): the cube of cells within Chebyshev distance k - 1 of x's cell, k its stored distance.
+template <class M>
+__device__ __forceinline__ float empty_cube_exit(const M &m, float3 x, float3 w, float3 iw)
+{
+    const int cx = min(max(__float2int_rd((x.x - m.lo(0)) * m.mc_inv(0)), 0), m.mc_dims(0) - 1);
+    const int cy = min(max(__float2int_rd((x.y - m.lo(1)) * m.mc_inv(1)), 0), m.mc_dims(1) - 1);
+    const int cz = min(max(__float2int_rd((x.z - m.lo(2)) * m.mc_inv(2)), 0), m.mc_dims(2) - 1);
+    const int k = m.mc_empty_radius((cz * m.mc_dims(1) + cy) * m.mc_dims(0) + cx);
+    if (k == 0) return 0.0f;
+    float best = FLT_MAX;
+    const float xs[3] = {x.x, x.y, x.z}, ws[3] = {w.x, w.y, w.z}, is[3] = {iw.x, iw.y, iw.z};
+    const int cs_[3] = {cx, cy, cz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (ws[a] == 0.0f) continue;
+        const float edge = ws[a] > 0.0f ? (float)(cs_[a] + k) : (float)(cs_[a] - k + 1);
+        const float t = (m.lo(a) + edge * m.mc_size(a) - xs[a]) * is[a];
+        best = fminf(best, t);
+    }
+    return fmaxf(best, 0.0f);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Directions (Sec. 2.1: isotropic scattering and emission; Lambertian walls and lights).
 __device__ __forceinline__ float3 iso_dir(float u1, float u2)
@@ -575,6 +600,14 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
         const float st = sigma_t_at(m, p, b);
         sink.point(p, b, st, sb);
         T *= fmaxf(0.0f, 1.0f - st * isb);
+        if (S.sk > 0 && st == 0.0f) {
+            // no matter in the cube around this point: continue sampling from its far side
+            const float tl2 = empty_cube_exit(m, p, dir, inv_dir(dir));
+            if (tl2 > 0.0f) {
+                t += tl2;
+                rc.cell_walks++;
+            }
+        }
         if (T < RT_RR_THRESHOLD) {
             if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
             const uint32_t q2 = j & 3u;
@@ -766,6 +799,16 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
     if (!(b0.b * sb < k.total)) {
         rc.nulls++;
         obs.null_event(p.x, p.bin, k, sb);
+        if (m.skip() && k.total == 0.0f) {
+            // every tentative collision in the empty cube around here would be a null: leave it
+            float tl = empty_cube_exit(m, p.x, p.w, p.iw);
+            if (tl > 0.0f) {
+                int f2;
+                tl = fminf(tl, exit_distance(m, p.x, p.w, p.iw, f2));
+                p.x = make_float3(p.x.x + tl * p.w.x, p.x.y + tl * p.w.y, p.x.z + tl * p.w.z);
+                rc.cell_walks++;
+            }
+        }
         return c;
     }
     if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }

@@ -142,7 +142,7 @@ class Scene:
     def _params(self, n_paths=None, path_offset=0, seed=None, medium_id=0, form="plain",
                 analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
                 accumulate=False, block_size=0, blocks_per_sm=0, regroup=0, macro_cell=0,
-                majorant_margin=0.0):
+                majorant_margin=0.0, skip_cell=0):
         pp = dict(self.desc["params"])
         for k, v in (("n_paths", n_paths), ("seed", seed), ("analog", analog),
                      ("max_inelastic", max_inelastic), ("n_rr", n_rr), ("max_events", max_events),
@@ -165,16 +165,17 @@ class Scene:
         p.blocks_per_sm = int(blocks_per_sm)
         p.regroup_interval = int(regroup)
         p.macro_cell = int(macro_cell)
+        p.skip_cell = int(skip_cell)
         p.majorant_margin = float(majorant_margin)
         return p
 
     def render(self, n_paths=None, path_offset=0, seed=None, medium_id=0, form="plain",
                analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
                film=True, path_events=None, accumulate=False, block_size=0, blocks_per_sm=0,
-               regroup=0, macro_cell=0, majorant_margin=0.0, stream=None):
+               regroup=0, macro_cell=0, majorant_margin=0.0, skip_cell=0, stream=None):
         p = self._params(n_paths, path_offset, seed, medium_id, form, analog, max_inelastic, n_rr,
                          max_events, max_steps, accumulate, block_size, blocks_per_sm, regroup,
-                         macro_cell, majorant_margin)
+                         macro_cell, majorant_margin, skip_cell)
         f = self.film_tensor() if film else None
         p.film = f.data_ptr() if f is not None else None
         p.path_events = path_events.data_ptr() if path_events is not None else None
@@ -185,12 +186,12 @@ class Scene:
     def adjoint(self, adj, grad_conc=None, grad_sigma_s=None, n_paths=None, path_offset=0,
                 seed=None, medium_id=0, analog=None, max_inelastic=None, n_rr=None,
                 max_events=None, max_steps=None, accumulate=False, block_size=0, macro_cell=0,
-                majorant_margin=0.0, stream=None):
+                majorant_margin=0.0, skip_cell=0, stream=None):
         """Path-replay gradient of sum(adj * film) for the paths render() traces with the same
         arguments; writes into grad_conc [D,nz,ny,nx] and grad_sigma_s [1] (CUDA f32 tensors)."""
         p = self._params(n_paths, path_offset, seed, medium_id, "plain", analog, max_inelastic,
                          n_rr, max_events, max_steps, accumulate, block_size, macro_cell=macro_cell,
-                         majorant_margin=majorant_margin)
+                         majorant_margin=majorant_margin, skip_cell=skip_cell)
         adj = adj.contiguous()
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         N.check(N.flr_adjoint(self.ctx, p, adj.data_ptr(),

@@ -160,6 +160,13 @@ def test_cfg2_macro_cell_parity():
     _check_workload(sc, 32, 6000, forms=("plain", "wavefront"), path_id_frac=0.95, macro_cell=4)
 
 
+def test_cfg2_empty_space_leap_parity():
+    """Leaps out of empty cubes after null collisions (cells of 2^3 voxels); the oracle leaps the
+    same way in fp64."""
+    sc = sg.cfg2_cornell_box(width=48, height=48, grid=48, n_paths=1)
+    _check_workload(sc, 32, 6000, forms=("plain", "wavefront"), path_id_frac=0.95, skip_cell=2)
+
+
 def test_cfg5_macro_cell_parity():
     sc = sg.cfg5_light_sheet(grid=32, width=32, height=32, n_blobs=40, n_paths=1,
                              sigma_t_ref=20.0)

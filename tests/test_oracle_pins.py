@@ -666,3 +666,45 @@ def test_macro_cell_render_matches_global_majorant_render():
     steps_b = sum(o["counters"]["steps"] for o in b)
     assert steps_b < 0.5 * steps_a
     assert all(o["counters"]["majorant_violations"] == 0 for o in b)
+
+
+# ------------------------------------------------------------------------------------------
+# Empty-space leaps after null collisions (memoryless free flights)
+
+
+def test_empty_space_leaps_reproduce_uncollided_transmission():
+    """A beam crossing a grid whose matter fills only some regions (solvent mask and dyes zero
+    elsewhere): leaving empty cubes after nulls keeps the exact uncollided transmission."""
+    rng = np.random.default_rng(21)
+    n = 16
+    conc = rng.uniform(0.0, 2.0, size=(1, n, n, n)).astype(np.float32)
+    solvent = np.zeros((n, n, n), np.uint8)
+    solvent[4:7, :, :] = 1
+    solvent[11:13, :, :] = 1
+    conc[0][solvent == 0] = 0.0
+    dyes = sg.make_dyes([490.0], [15.0], [620.0], [15.0], eps=[0.5], qy=[0.5])
+    x, y = 0.43, 0.58
+    sc = {"spectrum": sg.spectrum(), "dyes": dyes,
+          "medium": sg.grid_medium(conc, solvent, sigma_s=1.5),
+          "sources": [sg.pencil_beam((x, y, 1.0), (0, 0, -1), [490.0])],
+          "sensor": sg.no_sensor(), "params": sg.params(200_000, seed=6)}
+    exact = math.exp(-oracle.optical_depth(sc, np.array([x, y, 1.0]), np.array([0, 0, -1.0]), 1.0,
+                                           bin_of(490)))
+    base = oracle.render(sc, max_events=0)
+    for cell in (1, 2, 4):
+        r = oracle.render(sc, max_events=0, skip_cell=cell)
+        T = r["face"][:, sg.FACE_NZ, :].sum()
+        assert abs(T - exact) <= 3 * binomial_se(exact, 200_000), (cell, T, exact)
+        assert r["counters"]["steps"] < base["counters"]["steps"]
+
+
+def test_empty_space_leaps_match_plain_tracking_on_cornell_box():
+    sc = sg.cfg2_cornell_box(width=16, height=16, grid=32, n_paths=1)
+    K, n = 16, 3000
+    a = batched(sc, K, n)
+    b = [oracle.render(sc, n_paths=n, path_offset=k * n, seed=13, skip_cell=2) for k in range(K)]
+    for key in ("face", "emitted", "film"):
+        ma, sa = batch_mean_se([o[key].sum() for o in a])
+        mb, sb = batch_mean_se([o[key].sum() for o in b])
+        assert abs(ma - mb) <= 3 * math.sqrt(sa ** 2 + sb ** 2), (key, ma, mb)
+    assert sum(o["counters"]["steps"] for o in b) < 0.6 * sum(o["counters"]["steps"] for o in a)
