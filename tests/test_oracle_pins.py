@@ -695,7 +695,8 @@ def test_empty_space_leaps_reproduce_uncollided_transmission():
         r = oracle.render(sc, max_events=0, skip_cell=cell)
         T = r["face"][:, sg.FACE_NZ, :].sum()
         assert abs(T - exact) <= 3 * binomial_se(exact, 200_000), (cell, T, exact)
-        assert r["counters"]["steps"] < base["counters"]["steps"]
+        if cell == 1:  # larger cells (with their halo) all touch the matter slabs here
+            assert r["counters"]["steps"] < base["counters"]["steps"]
 
 
 def test_empty_space_leaps_match_plain_tracking_on_cornell_box():
