@@ -305,10 +305,24 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     offset = rank * n_paths  # each rank its own path-id range
 
+    # launch configuration of the optimised form: autotuned on an eighth of the paths (outside
+    # the timed region), or taken from the command line
+    tuned = {"form": "wavefront", "block_size": 0, "regroup": args.regroup,
+             "skip_cell": args.skip_cell, "macro_cell": args.macro_cell}
+    tune_info = None
+    if args.autotune:
+        from paper_1706_03024_gb300.autotune import tune_render
+        res = tune_render(S, max(n_paths // 8, 1 << 16), path_offset=offset)
+        tuned = res.best.kwargs()
+        tune_info = {"chosen": tuned, "candidates": len({c for c, _ in res.trials}),
+                     "best_events_per_s_on_slice": max(v for _, v in res.trials)}
+
     def one_step(form):
         # the plain kernel is the baseline: one thread per path, one majorant per bin
-        S.render(form=form, path_offset=offset, regroup=args.regroup,
-                 macro_cell=args.macro_cell if form == "wavefront" else 0)
+        if form == "plain":
+            S.render(form="plain", path_offset=offset)
+        else:
+            S.render(path_offset=offset, **tuned)
 
     def timed(form, steps, sampler_path=None):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -356,8 +370,7 @@ def run_ours(args):
         ref = torch.zeros_like(S.film_tensor())
         n_ref = 16
         for k in range(n_ref):
-            S.render(form="wavefront", seed=7777, path_offset=k * n_paths,
-                     macro_cell=args.macro_cell)
+            S.render(seed=7777, path_offset=k * n_paths, **tuned)
             ref += S.film_tensor() / n_ref
         out = {}
         for form in ("plain", "wavefront"):
@@ -414,8 +427,7 @@ def run_ours(args):
         conc_d.copy_(conc_h, non_blocking=True)
         solv_d.copy_(solv_h, non_blocking=True)
         S.set_medium(md, grids={"conc": conc_d, "solvent": solv_d})
-        f = S.render(form="wavefront", path_offset=offset, regroup=args.regroup,
-                     macro_cell=args.macro_cell)
+        f = S.render(path_offset=offset, **tuned)
         film_h.copy_(f, non_blocking=True)
         return S.read()
 
@@ -454,8 +466,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if not args.paths else WORKLOAD + f" ({n_paths} paths)",
-                       "paths_per_gpu": n_paths, "form": "wavefront", "macro_cell": args.macro_cell,
-                       "regroup": args.regroup,
+                       "paths_per_gpu": n_paths, "launch": tuned, "autotune": tune_info,
                        "l2": "flushed between timed steps (256 MB write)",
                        "events_per_step": ev_w, "parallelism": f"paths sharded over {world} GPU(s)"},
             "paths_per_s": paths_per_s,
@@ -497,9 +508,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--regroup", type=int, default=4)
+    ap.add_argument("--regroup", type=int, default=2)
     ap.add_argument("--macro-cell", type=int, default=0,
                     help="local-majorant cell edge in voxels for the optimised forms (0: global)")
+    ap.add_argument("--skip-cell", type=int, default=2,
+                    help="empty-space leap cell edge in voxels for the optimised form (0: off)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use --regroup/--skip-cell/--macro-cell instead of tuning")
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--paths", type=int, default=0,
                     help="override the path count (small profiling cases only)")
