@@ -56,6 +56,7 @@ extern "C" {
 
 #define FLR_FORM_PLAIN 0      /* one thread per path, nested loops                          */
 #define FLR_FORM_WAVEFRONT 1  /* persistent, path regeneration, sensor connections regrouped */
+#define FLR_FORM_WAVEFRONT_WARP 2  /* as WAVEFRONT, regrouping per warp instead of per block */
 
 /* Counter indices of flr_read_tallies' counters array. */
 enum {
@@ -128,7 +129,7 @@ typedef struct flr_params {
                                     ends the path (k = 1 is the paper's single inelastic event,
                                     Sec. 4.1 and V_f of Eq. 9)                                 */
     int analog;                  /* 0: weight *= QY (and wall albedo); 1: survival coins        */
-    int form;                    /* FLR_FORM_PLAIN or FLR_FORM_WAVEFRONT                        */
+    int form;                    /* FLR_FORM_PLAIN, FLR_FORM_WAVEFRONT or FLR_FORM_WAVEFRONT_WARP */
     int64_t max_events;          /* a real collision once n_events == max_events ends the path */
     int64_t max_steps;           /* tracking-step budget per path                               */
     float *film;                 /* device [H][W][n_bins] fp32, or NULL                         */

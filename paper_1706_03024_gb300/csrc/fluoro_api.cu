@@ -664,7 +664,8 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     if (!p) return fail(ctx, FLR_ERR_ARG, "params: NULL");
     if (ctx->B <= 0 || !ctx->medium_set) return fail(ctx, FLR_ERR_STATE, "render: spectrum, dyes and medium must be set");
     if (ctx->sources.empty()) return fail(ctx, FLR_ERR_STATE, "render: no sources");
-    if (p->form != FLR_FORM_PLAIN && p->form != FLR_FORM_WAVEFRONT) return fail(ctx, FLR_ERR_ARG, "params: unknown form");
+    if (p->form != FLR_FORM_PLAIN && p->form != FLR_FORM_WAVEFRONT && p->form != FLR_FORM_WAVEFRONT_WARP)
+        return fail(ctx, FLR_ERR_ARG, "params: unknown form");
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || (p->block_size & 31)))
         return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
@@ -1170,7 +1171,9 @@ extern "C" int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins
     if (rc == FLR_OK && sensor && sensor->kind != FLR_SENSOR_NONE) rc = flr_set_sensor(&c, sensor);
     if (rc == FLR_OK) rc = validate_medium(&c, medium);
     if (rc != FLR_OK) return rc;
-    if (!p || (p->form != FLR_FORM_PLAIN && p->form != FLR_FORM_WAVEFRONT)) return FLR_ERR_ARG;
+    if (!p || (p->form != FLR_FORM_PLAIN && p->form != FLR_FORM_WAVEFRONT &&
+               p->form != FLR_FORM_WAVEFRONT_WARP))
+        return FLR_ERR_ARG;
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || (p->block_size & 31)))
         return FLR_ERR_ARG;
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)

@@ -895,6 +895,7 @@ __host__ __device__ inline SmemLayout smem_layout(int B, int form, int block)
     off = ((off + 15) / 16) * 16;
     L.queue_off_bytes = off;
     if (form == FLR_FORM_WAVEFRONT) off += 2 * block * 32 + 16;
+    if (form == FLR_FORM_WAVEFRONT_WARP) off += 2 * block * 32 + (block / 32) * 8;
     L.total_bytes = off;
     return L;
 }
@@ -1066,6 +1067,83 @@ __global__ void __launch_bounds__(256) k_trace_wavefront(SceneDev S, RunDev R)
         const bool any = s_active != 0;
         // regrouped connection phase: full batches while work remains, everything at the end
         queue_drain(S, R, sm, q, cap, any ? (int)blockDim.x : 1, rc);
+        if (!any) break;
+    }
+    block_epilogue(S, R, sm, rc);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Wavefront form with per-warp regrouping: each warp owns a ring of 64 connection records in
+// shared memory and makes them in batches of 32, synchronising only its own lanes; warps never
+// wait for each other until the block's final tally flush.
+__global__ void __launch_bounds__(256) k_trace_wavefront_warp(SceneDev S, RunDev R)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT_WARP, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L);
+    const MedS m{S, sm};
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int CAP = 64;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    Queue q;
+    {
+        unsigned char *base = smem_raw + L.queue_off_bytes;
+        float *f = reinterpret_cast<float *>(base) + warp * CAP * 8;
+        q.x = f;
+        q.y = q.x + CAP;
+        q.z = q.y + CAP;
+        q.w = q.z + CAP;
+        q.bin_lamb = reinterpret_cast<int *>(q.w + CAP);
+        q.pid_lo = reinterpret_cast<uint32_t *>(q.bin_lamb + CAP);
+        q.pid_hi = q.pid_lo + CAP;
+        q.step = q.pid_hi + CAP;
+        q.head_tail = reinterpret_cast<int *>(base + (size_t)nwarps * CAP * 32) + 2 * warp;
+        if (lane == 0) { q.head_tail[0] = 0; q.head_tail[1] = 0; }
+    }
+    __syncwarp();
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
+    Path p;
+    p.alive = false;
+    bool exhausted = false;
+    const int regroup = R.regroup > 0 ? R.regroup : 8;
+    while (true) {
+        for (int s = 0; s < regroup; ++s) {
+            if (!p.alive) {
+                if (exhausted) break;
+                const unsigned long long i = atomicAdd(R.work_counter, 1ull);
+                if (i >= R.n_paths) { exhausted = true; break; }
+                const Conn c = spawn(m, R, sm, R.path_offset + i, p);
+                if (c.valid) { queue_push(q, CAP, c); break; }
+                continue;
+            }
+            const Conn c = track_step(m, R, sm, p, rc);
+            if (c.valid) { queue_push(q, CAP, c); break; }
+        }
+        __syncwarp();
+        const bool any = __any_sync(FULL, p.alive || !exhausted);
+        // full batches while work remains, everything at the end
+        while (true) {
+            const int head = q.head_tail[0], tail = q.head_tail[1];
+            const int n = tail - head;
+            if (n <= 0 || (any && n < 32)) break;
+            const int take = min(n, 32);
+            if (lane < take) {
+                const int slot = (head + lane) % CAP;
+                const int bl = q.bin_lamb[slot];
+                const uint64_t pid = ((uint64_t)q.pid_hi[slot] << 32) | q.pid_lo[slot];
+                connect(S, R, sm, make_float3(q.x[slot], q.y[slot], q.z[slot]), bl & 0xFFFF, q.w[slot],
+                        (bl >> 16) - 1, pid, q.step[slot], rc);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const int h = head + take;
+                const int base = h - h % CAP;
+                q.head_tail[0] = h - base;
+                q.head_tail[1] = tail - base;
+            }
+            __syncwarp();
+        }
         if (!any) break;
     }
     block_epilogue(S, R, sm, rc);
@@ -1408,6 +1486,8 @@ int occupancy_blocks_per_sm(int B, int form, int block)
     const int smem = trace_smem_bytes(B, form, block);
     if (form == FLR_FORM_WAVEFRONT)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront, block, smem);
+    else if (form == FLR_FORM_WAVEFRONT_WARP)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront_warp, block, smem);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_plain, block, smem);
     return n > 0 ? n : 1;
@@ -1428,6 +1508,8 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
     if (grid < 1) grid = 1;
     if (form == FLR_FORM_WAVEFRONT)
         k_trace_wavefront<<<(unsigned)grid, block, smem, st>>>(S, R);
+    else if (form == FLR_FORM_WAVEFRONT_WARP)
+        k_trace_wavefront_warp<<<(unsigned)grid, block, smem, st>>>(S, R);
     else
         k_trace_plain<<<(unsigned)grid, block, smem, st>>>(S, R);
     return cudaGetLastError();

@@ -35,6 +35,7 @@ FLR_SENSOR_ORTHO = 1
 FLR_SENSOR_PINHOLE = 2
 FLR_FORM_PLAIN = 0
 FLR_FORM_WAVEFRONT = 1
+FLR_FORM_WAVEFRONT_WARP = 2
 
 COUNTER_NAMES = [
     "paths", "events", "nulls", "escapes", "absorbed_dead", "rr_kills", "cap_hits", "step_budget",

@@ -14,7 +14,8 @@ from . import native as N
 
 _KINDS = {"collimated": N.FLR_SOURCE_COLLIMATED, "lambertian": N.FLR_SOURCE_LAMBERTIAN}
 _SENSORS = {"none": N.FLR_SENSOR_NONE, "ortho": N.FLR_SENSOR_ORTHO, "pinhole": N.FLR_SENSOR_PINHOLE}
-_FORMS = {"plain": N.FLR_FORM_PLAIN, "wavefront": N.FLR_FORM_WAVEFRONT}
+_FORMS = {"plain": N.FLR_FORM_PLAIN, "wavefront": N.FLR_FORM_WAVEFRONT,
+          "wavefront_warp": N.FLR_FORM_WAVEFRONT_WARP}
 
 
 def _np_ptr(a):

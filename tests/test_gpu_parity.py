@@ -133,14 +133,14 @@ def _check_workload(sc, K, n_per, forms=("plain",), film_min_nonzero=None, path_
 
 def test_cfg1_homogeneous_cube_parity():
     sc = sg.cfg1_homogeneous_cube(n_paths=100_000)
-    res = _check_workload(sc, 32, 100_000 // 32, forms=("plain", "wavefront"))
-    # plain and wavefront launch forms trace the same paths: fixed-point tallies bit-identical
-    for a, b in zip(res["plain"], res["wavefront"]):
-        for key in ("face", "absorbed", "emitted"):
-            assert np.array_equal(a[key], b[key])
-        ca, cb = dict(a["counters"]), dict(b["counters"])
-        assert ca == cb
-        assert np.allclose(a["film"], b["film"], rtol=1e-5, atol=1e-7 * a["film"].max())
+    res = _check_workload(sc, 32, 100_000 // 32, forms=("plain", "wavefront", "wavefront_warp"))
+    # every launch form traces the same paths: fixed-point tallies bit-identical
+    for other in ("wavefront", "wavefront_warp"):
+        for a, b in zip(res["plain"], res[other]):
+            for key in ("face", "absorbed", "emitted"):
+                assert np.array_equal(a[key], b[key]), (other, key)
+            assert dict(a["counters"]) == dict(b["counters"]), other
+            assert np.allclose(a["film"], b["film"], rtol=1e-5, atol=1e-7 * a["film"].max())
 
 
 def test_cfg1_analog_and_single_inelastic_parity():
@@ -164,7 +164,7 @@ def test_cfg2_empty_space_leap_parity():
     """Leaps out of empty cubes after null collisions (cells of 2^3 voxels); the oracle leaps the
     same way in fp64."""
     sc = sg.cfg2_cornell_box(width=48, height=48, grid=48, n_paths=1)
-    _check_workload(sc, 32, 6000, forms=("plain", "wavefront"), path_id_frac=0.95, skip_cell=2)
+    _check_workload(sc, 32, 6000, forms=("plain", "wavefront_warp"), path_id_frac=0.95, skip_cell=2)
 
 
 def test_cfg5_macro_cell_parity():
