@@ -35,17 +35,18 @@ METRIC = "medium events/s (fwd, batched, adjoint) vs plain GPU kernel at equal R
 WORKLOAD = "cornell box: 4 dye spheres, 128^3 x4 fp32 grids, 512x512 pinhole x 81 bins, 16 spp"
 
 # 32-bit lane operations per unit of work ("ALU roofline"): a Philox4x32-10 block,
-# a tracking step, a real event, a sensor connection and a ratio-tracking step.
+# a tracking step, a real event, a sensor connection, a ratio-tracking step and a cell walk.
 OPS_PHILOX = 112
 OPS_STEP = OPS_PHILOX + 55
 OPS_EVENT = OPS_PHILOX + 30
 OPS_CONNECT = 45
 OPS_CONNECT_STEP = OPS_PHILOX // 4 + 36
+OPS_CELL_WALK = 30   # an empty-space leap or a local-majorant cell visit
 
 
 def algorithmic_ops(c):
     return (c["steps"] * OPS_STEP + c["events"] * OPS_EVENT + c["connections"] * OPS_CONNECT
-            + c["connect_steps"] * OPS_CONNECT_STEP)
+            + c["connect_steps"] * OPS_CONNECT_STEP + c.get("cell_walks", 0) * OPS_CELL_WALK)
 
 
 def dist_env():
@@ -307,7 +308,7 @@ def run_ours(args):
 
     # launch configuration of the optimised form: autotuned on an eighth of the paths (outside
     # the timed region), or taken from the command line
-    tuned = {"form": "wavefront", "block_size": 0, "regroup": args.regroup,
+    tuned = {"form": args.form, "block_size": 0, "regroup": args.regroup,
              "skip_cell": args.skip_cell, "macro_cell": args.macro_cell}
     tune_info = None
     if args.autotune:
@@ -508,7 +509,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--regroup", type=int, default=2)
+    ap.add_argument("--form", default="wavefront_warp",
+                    choices=["wavefront", "wavefront_warp"],
+                    help="optimised form when not autotuning")
+    ap.add_argument("--regroup", type=int, default=1)
     ap.add_argument("--macro-cell", type=int, default=0,
                     help="local-majorant cell edge in voxels for the optimised forms (0: global)")
     ap.add_argument("--skip-cell", type=int, default=2,

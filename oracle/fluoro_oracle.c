@@ -257,8 +257,8 @@ static void free_macro(tables *t)
 
 /* Empty-space distances over cells of `cell`^3 voxels: a cell holds matter if any voxel of it or
  * of its one-voxel halo has solvent (with sigma_s + sigma_a0 > 0) or a positive concentration;
- * every other cell stores its Chebyshev distance (in cells, at most 255) to the nearest such
- * cell, found by breadth-first search over the 26 neighbours. */
+ * every other cell stores its Chebyshev distance (in cells) to the nearest such cell, found by
+ * breadth-first search over the 26 neighbours and capped at 31. */
 static void build_skip(const or_scene *s, tables *t, int cell)
 {
     t->sk = 0;
@@ -318,6 +318,8 @@ static void build_skip(const or_scene *s, tables *t, int cell)
                 }
     }
     free(queue);
+    for (int64_t c = 0; c < nc; ++c)
+        if (t->sk_dist[c] > 31) t->sk_dist[c] = 31;
 }
 
 /* Distance along (x, w) to leave the empty cube around x (0 if x's cell may hold matter). */

@@ -48,6 +48,8 @@ struct flr_ctx {
     float4 *d_mc_c = nullptr;
     float *d_mc_s = nullptr;
     uint8_t *d_mc_dist = nullptr;
+    uint8_t *d_mc_tmp = nullptr;
+    size_t mc_tmp_cap = 0;
     size_t mc_cap = 0;
     int mc_cell = 0;
     int mc_dims[3] = {0, 0, 0};
@@ -340,47 +342,20 @@ int prepare_macro(flr_ctx *ctx, int cell, cudaStream_t st)
     cudaError_t e = launch_build_macro(medium_has_grid(m) ? ctx->d_grid : nullptr, uni, m.solvent,
                                        m.dims, cell, md, ctx->d_mc_c, ctx->d_mc_s, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "build the local-majorant grid");
-    // Chebyshev distance (in cells, capped at 255) from every empty cell to the nearest cell that
-    // may hold matter, by breadth-first search on the host
-    std::vector<float4> hc(n);
-    std::vector<float> hs(n);
-    e = cudaMemcpyAsync(hc.data(), ctx->d_mc_c, sizeof(float4) * n, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), ctx->d_mc_s, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "read the local-majorant grid");
-    const bool solvent_matter = ((double)m.sigma_s + (double)m.sigma_a0) > 0.0;
-    std::vector<uint8_t> dist(n, 255);
-    std::vector<size_t> frontier;
-    for (size_t i = 0; i < n; ++i) {
-        const float4 c = hc[i];
-        const bool occupied = (solvent_matter && hs[i] > 0.0f) || c.x > 0.0f || c.y > 0.0f ||
-                              c.z > 0.0f || c.w > 0.0f;
-        if (occupied) {
-            dist[i] = 0;
-            frontier.push_back(i);
-        }
+    // Chebyshev distance (in cells, capped at 31) from every empty cell to the nearest cell that
+    // may hold matter, by repeated 26-neighbour relaxation on the device
+    const int solvent_matter = ((double)m.sigma_s + (double)m.sigma_a0) > 0.0 ? 1 : 0;
+    if (n > ctx->mc_tmp_cap) {
+        cudaFree(ctx->d_mc_tmp);
+        ctx->d_mc_tmp = nullptr;
+        ctx->mc_tmp_cap = 0;
+        e = cudaMalloc(&ctx->d_mc_tmp, n);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate the distance scratch");
+        ctx->mc_tmp_cap = n;
     }
-    for (int level = 1; level < 255 && !frontier.empty(); ++level) {
-        std::vector<size_t> next;
-        for (size_t i : frontier) {
-            const int cx = (int)(i % md[0]), cy = (int)((i / md[0]) % md[1]), cz = (int)(i / ((size_t)md[0] * md[1]));
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int x = cx + dx, y = cy + dy, z = cz + dz;
-                        if (x < 0 || y < 0 || z < 0 || x >= md[0] || y >= md[1] || z >= md[2]) continue;
-                        const size_t j = ((size_t)z * md[1] + y) * md[0] + x;
-                        if (dist[j] == 255) {
-                            dist[j] = (uint8_t)level;
-                            next.push_back(j);
-                        }
-                    }
-        }
-        frontier.swap(next);
-    }
-    e = cudaMemcpyAsync(ctx->d_mc_dist, dist.data(), n, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload the empty-space distances");
+    e = launch_empty_distance(ctx->d_mc_c, ctx->d_mc_s, md, solvent_matter, 31, ctx->d_mc_dist,
+                              ctx->d_mc_tmp, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "empty-space distances");
     ctx->mc_cell = cell;
     for (int k = 0; k < 3; ++k) ctx->mc_dims[k] = md[k];
     return FLR_OK;
@@ -481,6 +456,7 @@ void flr_destroy(flr_ctx *ctx)
     cudaFree(ctx->d_mc_c);
     cudaFree(ctx->d_mc_s);
     cudaFree(ctx->d_mc_dist);
+    cudaFree(ctx->d_mc_tmp);
     auto &bt = ctx->batch;
     if (bt.exec) cudaGraphExecDestroy(bt.exec);
     if (bt.graph) cudaGraphDestroy(bt.graph);

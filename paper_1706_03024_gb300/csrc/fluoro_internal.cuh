@@ -142,6 +142,9 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
 cudaError_t launch_build_macro(const float4 *grid, float4 uniform, const uint8_t *solvent,
                                const int dims[3], int cell, const int mdims[3], float4 *out_c,
                                float *out_s, cudaStream_t st);
+cudaError_t launch_empty_distance(const float4 *mc, const float *ms, const int mdims[3],
+                                  int solvent_matter, int cap, uint8_t *out, uint8_t *tmp,
+                                  cudaStream_t st);
 cudaError_t launch_grid_max(const float *g, long long n, unsigned int *out_bits, int *neg_flag,
                             cudaStream_t st);
 cudaError_t launch_pack_grid(const float *const *conc, const float *uniform, int D, long long n,

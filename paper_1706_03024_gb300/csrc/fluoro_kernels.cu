@@ -1417,6 +1417,47 @@ __global__ void k_build_macro(const float4 *__restrict__ grid, float4 uniform,
     }
 }
 
+// Empty-space distances on the cell grid: a cell holds matter if its maxima (cell plus halo) show
+// solvent (with sigma_s + sigma_a0 > 0) or any positive concentration; k_dist_init marks those 0
+// and the others `cap`; each k_dist_relax pass lowers every cell to 1 + the minimum of its 26
+// neighbours, so `cap` passes give the Chebyshev distance to matter, capped at `cap`.
+__global__ void k_dist_init(const float4 *__restrict__ mc, const float *__restrict__ ms, long long n,
+                            int solvent_matter, int cap, uint8_t *__restrict__ out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 c = mc[i];
+        const bool matter = (solvent_matter && ms[i] > 0.0f) || c.x > 0.0f || c.y > 0.0f ||
+                            c.z > 0.0f || c.w > 0.0f;
+        out[i] = matter ? 0 : (uint8_t)cap;
+    }
+}
+
+__global__ void k_dist_relax(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int mx, int my,
+                             int mz)
+{
+    const long long n = (long long)mx * my * mz;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % mx), y = (int)((i / mx) % my), z = (int)(i / ((long long)mx * my));
+        int best = in[i];
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int zz = z + dz;
+            if (zz < 0 || zz >= mz) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int yy = y + dy;
+                if (yy < 0 || yy >= my) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int xx = x + dx;
+                    if (xx < 0 || xx >= mx) continue;
+                    best = min(best, (int)in[((long long)zz * my + yy) * mx + xx] + 1);
+                }
+            }
+        }
+        out[i] = (uint8_t)best;
+    }
+}
+
 struct PackArgs {
     const float *conc[MAXD];
     float uniform[MAXD];
@@ -1561,6 +1602,28 @@ cudaError_t launch_build_macro(const float4 *grid, float4 uniform, const uint8_t
     if (blocks < 1) blocks = 1;
     k_build_macro<<<(unsigned)blocks, 128, 0, st>>>(grid, uniform, solvent, dims[0], dims[1], dims[2],
                                                      cell, mdims[0], mdims[1], mdims[2], out_c, out_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_empty_distance(const float4 *mc, const float *ms, const int mdims[3],
+                                  int solvent_matter, int cap, uint8_t *out, uint8_t *tmp,
+                                  cudaStream_t st)
+{
+    const long long n = (long long)mdims[0] * mdims[1] * mdims[2];
+    long long blocks = (n + 255) / 256;
+    const long long lim = (long long)num_sms() * 16;
+    if (blocks > lim) blocks = lim;
+    if (blocks < 1) blocks = 1;
+    k_dist_init<<<(unsigned)blocks, 256, 0, st>>>(mc, ms, n, solvent_matter, cap, out);
+    const int passes = min(cap, max(mdims[0], max(mdims[1], mdims[2])));
+    uint8_t *a = out, *b = tmp;
+    for (int i = 0; i < passes; ++i) {
+        k_dist_relax<<<(unsigned)blocks, 256, 0, st>>>(a, b, mdims[0], mdims[1], mdims[2]);
+        uint8_t *t = a;
+        a = b;
+        b = t;
+    }
+    if (a != out) cudaMemcpyAsync(out, a, (size_t)n, cudaMemcpyDeviceToDevice, st);
     return cudaGetLastError();
 }
 
