@@ -89,7 +89,8 @@ __device__ __forceinline__ void tally_add(const Smem &sm, int idx, float w)
 //         tallies in shared memory.
 //   MedB  one medium of a batched launch, per lane: fields read from global memory through the
 //         read-only path, tables in global memory (L1-resident), tallies in global memory.
-struct MedS {
+template <bool OPT>
+struct MedS_ {
     const SceneDev &S;
     const Smem &sm;
     __device__ __forceinline__ int B() const { return S.B; }
@@ -119,7 +120,7 @@ struct MedS {
     __device__ __forceinline__ float em_cdf(int k) const { return S.em_cdf[k]; }
     __device__ __forceinline__ const EmitterDev &em(int k) const { return S.em[k]; }
     __device__ __forceinline__ uint32_t key1(const RunDev &R) const { return R.medium_id; }
-    __device__ __forceinline__ bool macro() const { return S.mc > 0; }
+    __device__ __forceinline__ bool macro() const { return OPT && S.mc > 0; }
     __device__ __forceinline__ float margin() const { return S.maj_margin; }
     __device__ __forceinline__ int mc_dims(int k) const { return S.mc_dims[k]; }
     __device__ __forceinline__ float mc_size(int k) const { return S.mc_size[k]; }
@@ -127,8 +128,10 @@ struct MedS {
     __device__ __forceinline__ float4 mc_conc(int c) const { return __ldg(&S.mc_c[c]); }
     __device__ __forceinline__ float mc_solvent(int c) const { return __ldg(&S.mc_s[c]); }
     __device__ __forceinline__ int mc_empty_radius(int c) const { return (int)__ldg(&S.mc_dist[c]); }
-    __device__ __forceinline__ bool skip() const { return S.sk > 0; }
+    __device__ __forceinline__ bool skip() const { return OPT && S.sk > 0; }
 };
+// OPT = false compiles the local-majorant and empty-space paths out (the plain baseline kernel)
+using MedS = MedS_<true>;
 
 __device__ __forceinline__ void tally_add_global(unsigned long long *t, int idx, float w)
 {
@@ -531,12 +534,12 @@ struct NoSink {
     __device__ __forceinline__ void homogeneous(float) const {}
 };
 
-template <class G>
+template <class G, bool OPT = true>
 __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &R, const Smem &sm,
                                                float3 x, float3 dir, float tl, int b, uint64_t pid,
                                                uint32_t step, RegCnt &rc, const G &sink)
 {
-    const MedS m{S, sm};
+    const MedS_<OPT> m{S, sm};
     const float sb = sm.maj[b];
     float T = 1.0f;
     if (!(sb > 0.0f)) return T;
@@ -544,7 +547,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
         sink.homogeneous(tl);
         return __expf(-sigma_t_at(m, x, b) * tl);
     }
-    if (S.mc > 0) {
+    if (OPT && S.mc > 0) {
         // ratio tracking against the local majorants: one uniform per tentative point
         Dda dd;
         dda_init(m, dd, x, dir, inv_dir(dir));
@@ -600,7 +603,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
         const float st = sigma_t_at(m, p, b);
         sink.point(p, b, st, sb);
         T *= fmaxf(0.0f, 1.0f - st * isb);
-        if (S.sk > 0 && st == 0.0f) {
+        if (OPT && S.sk > 0 && st == 0.0f) {
             // no matter in the cube around this point: continue sampling from its far side
             const float tl2 = empty_cube_exit(m, p, dir, inv_dir(dir));
             if (tl2 > 0.0f) {
@@ -630,6 +633,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
 
 // Sensor connection (Eq. 3-6). `lamb` < 0: isotropic vertex, intensity w/(4 pi); otherwise a
 // Lambertian vertex with normal sign*e_axis (lamb = 2*axis + (sign > 0)), intensity w cos/pi.
+template <bool OPT = true>
 __device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, const Smem &sm,
                                         float3 x, int b, float w, int lamb, uint64_t pid,
                                         uint32_t step, RegCnt &rc)
@@ -637,7 +641,7 @@ __device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, cons
     const ConnGeom g = connect_geom(S, sm, x, lamb);
     if (!g.ok) return;
     rc.connections++;
-    const float T = transmittance(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, NoSink{});
+    const float T = transmittance<NoSink, OPT>(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, NoSink{});
     const float val = w * g.gf * T * R.film_scale;
     if (val > 0.0f) atomicAdd(&R.film[(size_t)g.pix * S.B + b], val);
 }
@@ -943,21 +947,22 @@ __device__ __forceinline__ void block_epilogue(const SceneDev &S, const RunDev &
 
 // ---------------------------------------------------------------------------------------------
 // Plain form: one thread per path, grid-stride over path ids, connections made inline.
+template <bool OPT>
 __global__ void __launch_bounds__(256) k_trace_plain(SceneDev S, RunDev R)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
     const Smem sm = block_prologue(S, smem_raw, L);
-    const MedS m{S, sm};
+    const MedS_<OPT> m{S, sm};
     RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
         Path p;
         Conn c = spawn(m, R, sm, R.path_offset + i, p);
-        if (c.valid) connect(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
+        if (c.valid) connect<OPT>(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
         while (p.alive) {
             c = track_step(m, R, sm, p, rc);
-            if (c.valid) connect(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
+            if (c.valid) connect<OPT>(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
         }
     }
     block_epilogue(S, R, sm, rc);
@@ -1530,7 +1535,7 @@ int occupancy_blocks_per_sm(int B, int form, int block)
     else if (form == FLR_FORM_WAVEFRONT_WARP)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront_warp, block, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_plain, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_plain<true>, block, smem);
     return n > 0 ? n : 1;
 }
 
@@ -1551,8 +1556,10 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
         k_trace_wavefront<<<(unsigned)grid, block, smem, st>>>(S, R);
     else if (form == FLR_FORM_WAVEFRONT_WARP)
         k_trace_wavefront_warp<<<(unsigned)grid, block, smem, st>>>(S, R);
+    else if (S.mc > 0 || S.sk > 0)
+        k_trace_plain<true><<<(unsigned)grid, block, smem, st>>>(S, R);
     else
-        k_trace_plain<<<(unsigned)grid, block, smem, st>>>(S, R);
+        k_trace_plain<false><<<(unsigned)grid, block, smem, st>>>(S, R);
     return cudaGetLastError();
 }
 
