@@ -744,6 +744,9 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
     rc.steps++;
     const uint32_t key1 = m.key1(R);
     const U4 b0 = draw(R.seed, key1, p.pid, p.step, 0u);
+    // The second block serves real events and wall bounces only, but some lane of a warp nearly
+    // always needs it: drawing it here, beside the first, overlaps the two Philox chains.
+    const U4 b1 = draw(R.seed, key1, p.pid, p.step, 1u);
     int face;
     const float te = exit_distance(m, p.x, p.w, p.iw, face);
     float sb, tf;
@@ -769,7 +772,6 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
             p.n_events++;
             rc.events++;
             cnt_add(sm, FLR_C_WALL_BOUNCES);
-            const U4 b1 = draw(R.seed, key1, p.pid, step, 1u);
             if (R.analog) {
                 if (!(b1.d < m.wall_albedo())) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
             } else {
@@ -818,7 +820,6 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
     if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
     p.n_events++;
     rc.events++;
-    const U4 b1 = draw(R.seed, key1, p.pid, step, 1u);
     // particle type in proportion to its coefficient (Sec. 4.1)
     const float ue = b0.c * k.total;
     float acc = k.scat;
@@ -887,6 +888,12 @@ struct SmemLayout {
     int tab_floats, tal_off_bytes, cnt_off_bytes, queue_off_bytes, total_bytes;
 };
 
+// Per-warp connection queue of the warp-regrouped form: capacity and drain threshold. A drain starts
+// once WQ_DRAIN records wait; one tracking round adds at most 32, so the queue never wraps.
+constexpr int WQ_CAP = 128;
+constexpr int WQ_DRAIN = 96;
+static_assert(WQ_DRAIN + 31 < WQ_CAP, "warp queue overflow");
+
 __host__ __device__ inline SmemLayout smem_layout(int B, int form, int block)
 {
     SmemLayout L;
@@ -899,7 +906,7 @@ __host__ __device__ inline SmemLayout smem_layout(int B, int form, int block)
     off = ((off + 15) / 16) * 16;
     L.queue_off_bytes = off;
     if (form == FLR_FORM_WAVEFRONT) off += 2 * block * 32 + 16;
-    if (form == FLR_FORM_WAVEFRONT_WARP) off += 2 * block * 32 + (block / 32) * 8;
+    if (form == FLR_FORM_WAVEFRONT_WARP) off += (block / 32) * (WQ_CAP * 32 + 8);
     L.total_bytes = off;
     return L;
 }
@@ -1078,9 +1085,106 @@ __global__ void __launch_bounds__(256) k_trace_wavefront(SceneDev S, RunDev R)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Wavefront form with per-warp regrouping: each warp owns a ring of 64 connection records in
-// shared memory and makes them in batches of 32, synchronising only its own lanes; warps never
-// wait for each other until the block's final tally flush.
+// Wavefront form with per-warp regrouping and pull-based connection drains. Each warp queues its
+// lanes' sensor connections in shared memory (up to WQ_CAP records). Once WQ_DRAIN records are
+// waiting (or the work is done) the warp drains the queue: every lane advances its own
+// ratio-tracking march by one step per iteration and claims the next record as soon as its march
+// ends, so the lanes stay busy until the queue runs dry instead of waiting for the longest march
+// of a fixed batch. The marches consume their random numbers exactly as transmittance() does, so
+// every launch form gives the same film up to the order of the fp32 film atomics.
+struct March {
+    float3 x, dir;
+    float tl, t, T, isb, wg;
+    int b, pix, it;
+    uint32_t j, step;
+    uint64_t pid;
+    U4 blk;
+};
+
+__device__ __forceinline__ void march_deposit(const SceneDev &S, const RunDev &R, const March &mc)
+{
+    const float val = mc.wg * mc.T * R.film_scale;
+    if (val > 0.0f) atomicAdd(&R.film[(size_t)mc.pix * S.B + mc.b], val);
+}
+
+// Starts the connection of one queued vertex; returns true if a ratio-tracking march remains (the
+// connections that need no march are deposited here).
+__device__ __forceinline__ bool march_begin(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                            float3 x, int b, float w, int lamb, uint64_t pid,
+                                            uint32_t step, March &mc, RegCnt &rc)
+{
+    const ConnGeom g = connect_geom(S, sm, x, lamb);
+    if (!g.ok) return false;
+    rc.connections++;
+    mc.wg = w * g.gf;
+    mc.pix = g.pix;
+    mc.b = b;
+    const float sb = sm.maj[b];
+    if (!(sb > 0.0f) || S.homogeneous || S.mc > 0) {
+        mc.T = transmittance(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, NoSink{});
+        march_deposit(S, R, mc);
+        return false;
+    }
+    mc.x = x;
+    mc.dir = g.dir;
+    mc.tl = g.tl;
+    mc.t = 0.0f;
+    mc.T = 1.0f;
+    mc.isb = __frcp_rn(sb);
+    mc.j = 0;
+    mc.it = 0;
+    mc.pid = pid;
+    mc.step = step;
+    return true;
+}
+
+__device__ __forceinline__ float march_uniform(const RunDev &R, March &mc)
+{
+    if ((mc.j & 3u) == 0u) mc.blk = draw(R.seed, R.medium_id, mc.pid, mc.step, 2u + (mc.j >> 2));
+    const uint32_t q = mc.j & 3u;
+    ++mc.j;
+    return q == 0 ? mc.blk.a : (q == 1 ? mc.blk.b : (q == 2 ? mc.blk.c : mc.blk.d));
+}
+
+// One ratio-tracking step (the body of transmittance()'s loop); returns false when the march ends.
+__device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                           March &mc, RegCnt &rc)
+{
+    if (mc.it >= MAX_CONNECT_STEPS) {
+        cnt_add(sm, FLR_C_CONNECT_BUDGET);
+        return false;
+    }
+    ++mc.it;
+    const float u = march_uniform(R, mc);
+    mc.t -= __logf(1.0f - u) * mc.isb;
+    if (mc.t >= mc.tl) {
+        march_deposit(S, R, mc);
+        return false;
+    }
+    rc.connect_steps++;
+    const MedS m{S, sm};
+    const float3 p = make_float3(mc.x.x + mc.t * mc.dir.x, mc.x.y + mc.t * mc.dir.y,
+                                 mc.x.z + mc.t * mc.dir.z);
+    const float st = sigma_t_at(m, p, mc.b);
+    mc.T *= fmaxf(0.0f, 1.0f - st * mc.isb);
+    if (S.sk > 0 && st == 0.0f) {
+        const float tl2 = empty_cube_exit(m, p, mc.dir, inv_dir(mc.dir));
+        if (tl2 > 0.0f) {
+            mc.t += tl2;
+            rc.cell_walks++;
+        }
+    }
+    if (mc.T < RT_RR_THRESHOLD) {
+        const float u2 = march_uniform(R, mc);
+        if (u2 < 0.5f) {
+            mc.T *= 2.0f;
+        } else {
+            return false;
+        }
+    }
+    return true;
+}
+
 __global__ void __launch_bounds__(256) k_trace_wavefront_warp(SceneDev S, RunDev R)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1088,22 +1192,22 @@ __global__ void __launch_bounds__(256) k_trace_wavefront_warp(SceneDev S, RunDev
     const Smem sm = block_prologue(S, smem_raw, L);
     const MedS m{S, sm};
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int CAP = 64;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
+    const unsigned lower = (1u << lane) - 1u;
     Queue q;
     {
         unsigned char *base = smem_raw + L.queue_off_bytes;
-        float *f = reinterpret_cast<float *>(base) + warp * CAP * 8;
+        float *f = reinterpret_cast<float *>(base) + warp * WQ_CAP * 8;
         q.x = f;
-        q.y = q.x + CAP;
-        q.z = q.y + CAP;
-        q.w = q.z + CAP;
-        q.bin_lamb = reinterpret_cast<int *>(q.w + CAP);
-        q.pid_lo = reinterpret_cast<uint32_t *>(q.bin_lamb + CAP);
-        q.pid_hi = q.pid_lo + CAP;
-        q.step = q.pid_hi + CAP;
-        q.head_tail = reinterpret_cast<int *>(base + (size_t)nwarps * CAP * 32) + 2 * warp;
+        q.y = q.x + WQ_CAP;
+        q.z = q.y + WQ_CAP;
+        q.w = q.z + WQ_CAP;
+        q.bin_lamb = reinterpret_cast<int *>(q.w + WQ_CAP);
+        q.pid_lo = reinterpret_cast<uint32_t *>(q.bin_lamb + WQ_CAP);
+        q.pid_hi = q.pid_lo + WQ_CAP;
+        q.step = q.pid_hi + WQ_CAP;
+        q.head_tail = reinterpret_cast<int *>(base + (size_t)nwarps * WQ_CAP * 32) + 2 * warp;
         if (lane == 0) { q.head_tail[0] = 0; q.head_tail[1] = 0; }
     }
     __syncwarp();
@@ -1111,42 +1215,50 @@ __global__ void __launch_bounds__(256) k_trace_wavefront_warp(SceneDev S, RunDev
     Path p;
     p.alive = false;
     bool exhausted = false;
-    const int regroup = R.regroup > 0 ? R.regroup : 8;
+    const int regroup = R.regroup > 0 ? R.regroup : 1;
     while (true) {
+        // tracking: at most `regroup` steps or one queued connection per lane
         for (int s = 0; s < regroup; ++s) {
             if (!p.alive) {
                 if (exhausted) break;
                 const unsigned long long i = atomicAdd(R.work_counter, 1ull);
                 if (i >= R.n_paths) { exhausted = true; break; }
                 const Conn c = spawn(m, R, sm, R.path_offset + i, p);
-                if (c.valid) { queue_push(q, CAP, c); break; }
+                if (c.valid) { queue_push(q, WQ_CAP, c); break; }
                 continue;
             }
             const Conn c = track_step(m, R, sm, p, rc);
-            if (c.valid) { queue_push(q, CAP, c); break; }
+            if (c.valid) { queue_push(q, WQ_CAP, c); break; }
         }
         __syncwarp();
         const bool any = __any_sync(FULL, p.alive || !exhausted);
-        // full batches while work remains, everything at the end
-        while (true) {
-            const int head = q.head_tail[0], tail = q.head_tail[1];
-            const int n = tail - head;
-            if (n <= 0 || (any && n < 32)) break;
-            const int take = min(n, 32);
-            if (lane < take) {
-                const int slot = (head + lane) % CAP;
-                const int bl = q.bin_lamb[slot];
-                const uint64_t pid = ((uint64_t)q.pid_hi[slot] << 32) | q.pid_lo[slot];
-                connect(S, R, sm, make_float3(q.x[slot], q.y[slot], q.z[slot]), bl & 0xFFFF, q.w[slot],
-                        (bl >> 16) - 1, pid, q.step[slot], rc);
+        const int avail = q.head_tail[1];
+        if (avail >= WQ_DRAIN || (!any && avail > 0)) {
+            // pull-based drain of all `avail` records
+            // Lanes claim new records only every fourth iteration: a march draws a Philox block
+            // every fourth step, so claims in step keep the draws of all lanes in the same
+            // iterations instead of spreading them over four divergent ones, and the set-up of
+            // new marches runs for several lanes at once.
+            March mc;
+            bool active = false;
+            int claimed = 0;
+            for (uint32_t iter = 0;; ++iter) {
+                const unsigned need = (iter & 3u) == 0u ? __ballot_sync(FULL, !active) : 0u;
+                if (need != 0u && !active) {
+                    const int k = claimed + __popc(need & lower);
+                    if (k < avail) {
+                        const int bl = q.bin_lamb[k];
+                        const uint64_t pid = ((uint64_t)q.pid_hi[k] << 32) | q.pid_lo[k];
+                        active = march_begin(S, R, sm, make_float3(q.x[k], q.y[k], q.z[k]), bl & 0xFFFF,
+                                             q.w[k], (bl >> 16) - 1, pid, q.step[k], mc, rc);
+                    }
+                }
+                claimed += __popc(need);
+                if (active) active = march_step(S, R, sm, mc, rc);
+                if (!__any_sync(FULL, active) && claimed >= avail) break;
             }
             __syncwarp();
-            if (lane == 0) {
-                const int h = head + take;
-                const int base = h - h % CAP;
-                q.head_tail[0] = h - base;
-                q.head_tail[1] = tail - base;
-            }
+            if (lane == 0) q.head_tail[1] = 0;
             __syncwarp();
         }
         if (!any) break;
@@ -1526,10 +1638,29 @@ int trace_block_default() { return 256; }
 
 int trace_smem_bytes(int B, int form, int block) { return smem_layout(B, form, block).total_bytes; }
 
+namespace {
+// Opts a trace kernel into dynamic shared memory above the default 48 KB (the warp-regrouped
+// form's queues reach about 59 KB at 128 bins and 256 threads).
+cudaError_t allow_smem(int form, int smem)
+{
+    if (smem <= 48 * 1024) return cudaSuccess;
+    if (form == FLR_FORM_WAVEFRONT)
+        return cudaFuncSetAttribute(k_trace_wavefront, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (form == FLR_FORM_WAVEFRONT_WARP)
+        return cudaFuncSetAttribute(k_trace_wavefront_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smem);
+    cudaError_t e = cudaFuncSetAttribute(k_trace_plain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_trace_plain<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+}  // namespace
+
 int occupancy_blocks_per_sm(int B, int form, int block)
 {
     int n = 0;
     const int smem = trace_smem_bytes(B, form, block);
+    if (allow_smem(form, smem) != cudaSuccess) return 1;
     if (form == FLR_FORM_WAVEFRONT)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront, block, smem);
     else if (form == FLR_FORM_WAVEFRONT_WARP)
@@ -1544,6 +1675,8 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
 {
     if (block <= 0) block = trace_block_default();
     const int smem = trace_smem_bytes(S.B, form, block);
+    const cudaError_t ea = allow_smem(form, smem);
+    if (ea != cudaSuccess) return ea;
     const int occ = occupancy_blocks_per_sm(S.B, form, block);
     if (blocks_per_sm <= 0 || blocks_per_sm > occ) blocks_per_sm = occ;
     long long grid = (long long)num_sms() * blocks_per_sm;
