@@ -72,9 +72,12 @@ struct RegCnt {
     uint32_t steps, nulls, events, scatters, connections, connect_steps, cell_walks;
 };
 
-__device__ __forceinline__ void cnt_add(const Smem &sm, int k, unsigned long long v = 1ull)
+// Adds one per calling lane. The lanes that arrive together add once, through their lowest lane,
+// instead of queueing on one shared-memory word.
+__device__ __forceinline__ void cnt_add(const Smem &sm, int k)
 {
-    atomicAdd(&sm.cnt[k], v);
+    const unsigned mask = __activemask();
+    if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(&sm.cnt[k], (unsigned long long)__popc(mask));
 }
 
 __device__ __forceinline__ void tally_add(const Smem &sm, int idx, float w)
@@ -809,8 +812,7 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
             // every tentative collision in the empty cube around here would be a null: leave it
             float tl = empty_cube_exit(m, p.x, p.w, p.iw);
             if (tl > 0.0f) {
-                int f2;
-                tl = fminf(tl, exit_distance(m, p.x, p.w, p.iw, f2));
+                tl = fminf(tl, te - tf);
                 p.x = make_float3(p.x.x + tl * p.w.x, p.x.y + tl * p.w.y, p.x.z + tl * p.w.z);
                 rc.cell_walks++;
             }
