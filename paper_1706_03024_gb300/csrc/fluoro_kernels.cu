@@ -494,15 +494,15 @@ __device__ __forceinline__ ConnGeom connect_geom(const SceneDev &S, const Smem &
         const float izf = __frcp_rn(zf);
         const float X = (vx * S.s_U[0] + vy * S.s_U[1] + vz * S.s_U[2]) * izf;
         const float Y = (vx * S.s_V[0] + vy * S.s_V[1] + vz * S.s_V[2]) * izf;
-        const float sx = 0.5f * (X / S.tan_x + 1.0f);
-        const float sy = 0.5f * (Y / S.tan_y + 1.0f);
+        const float sx = 0.5f * (X * __frcp_rn(S.tan_x) + 1.0f);
+        const float sy = 0.5f * (Y * __frcp_rn(S.tan_y) + 1.0f);
         if (!(sx >= 0.0f && sx < 1.0f && sy >= 0.0f && sy < 1.0f)) return g;
         px = min(__float2int_rd(sx * (float)S.W), S.W - 1);
         py = min(__float2int_rd(sy * (float)S.H), S.H - 1);
         const float ir = rsqrtf(r2);
         dir = make_float3(-vx * ir, -vy * ir, -vz * ir);
         const float ct = zf * ir;
-        geom = S.inv_A_pix / (r2 * ct * ct * ct);
+        geom = S.inv_A_pix * __frcp_rn(r2 * ct * ct * ct);
     }
     float f;
     if (lamb >= 0) {
@@ -759,7 +759,7 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
         tf = dda_advance(m, dd, p.bin, -__logf(1.0f - b0.a), te, sb, rc.cell_walks);
     } else {
         sb = m.maj(p.bin);
-        tf = sb > 0.0f ? -__logf(1.0f - b0.a) / sb : FLT_MAX;
+        tf = sb > 0.0f ? -__logf(1.0f - b0.a) * __frcp_rn(sb) : FLT_MAX;
     }
     const uint32_t step = p.step;
     p.step++;
@@ -793,7 +793,7 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
             if (p.n_events >= R.n_rr) {
                 const float q = fminf(p.wt, 1.0f);
                 if (!(b1.c < q)) { cnt_add(sm, FLR_C_RR_KILLS); finish(R, p); return c; }
-                p.wt /= q;
+                p.wt = p.wt < 1.0f ? 1.0f : p.wt;   // w / min(w, 1), exactly
             }
             return c;
         }
@@ -874,7 +874,7 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
     if (p.n_events >= R.n_rr) {
         const float q = fminf(p.wt, 1.0f);
         if (!(b1.c < q)) { cnt_add(sm, FLR_C_RR_KILLS); finish(R, p); return c; }
-        p.wt /= q;
+        p.wt = p.wt < 1.0f ? 1.0f : p.wt;   // w / min(w, 1), exactly
     }
     if (!(isfinite(p.wt) && isfinite(p.x.x) && isfinite(p.x.y) && isfinite(p.x.z))) {
         cnt_add(sm, FLR_C_NONFINITE);
@@ -1187,7 +1187,7 @@ __device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, c
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_trace_wavefront_warp(SceneDev S, RunDev R)
+__global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, RunDev R)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT_WARP, blockDim.x);
