@@ -42,6 +42,11 @@ struct flr_ctx {
     int *d_error = nullptr;
     unsigned long long *d_work = nullptr;
     unsigned int *d_scratch = nullptr;  // [0] max bits, [1] flag, [2] any
+    // two-pass adjoint replay (warp-regrouped form): per-path contributions of one path chunk
+    float *d_adj_ak = nullptr;
+    size_t adj_ak_cap = 0;
+    float *d_adj_ovf = nullptr;
+    size_t adj_ovf_cap = 0;
     uint64_t paths_since_clear = 0;
     std::vector<float> h_tables;
     // local majorants of the current medium (built on demand for one cell size)
@@ -452,6 +457,8 @@ void flr_destroy(flr_ctx *ctx)
     cudaFree(ctx->d_error);
     cudaFree(ctx->d_work);
     cudaFree(ctx->d_scratch);
+    cudaFree(ctx->d_adj_ak);
+    cudaFree(ctx->d_adj_ovf);
     cudaFree(ctx->d_grid);
     cudaFree(ctx->d_mc_c);
     cudaFree(ctx->d_mc_s);
@@ -787,6 +794,12 @@ int flr_debug_sample_emission(flr_ctx *ctx, int dye, const float *u, int64_t n, 
 // ---------------------------------------------------------------------------------------------
 // Adjoint by path replay.
 
+static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem, const char *what);
+
+// Contributions kept per path between the two adjoint passes, and paths replayed per pass pair.
+constexpr int ADJ_K = 32;
+constexpr uint64_t ADJ_CHUNK = 1ull << 21;
+
 int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float *grad_conc,
                 float *grad_sigma_s, void *stream)
 {
@@ -795,6 +808,8 @@ int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float 
     if (ctx->B <= 0 || !ctx->medium_set || ctx->sources.empty())
         return fail(ctx, FLR_ERR_STATE, "adjoint: spectrum, dyes, medium and sources must be set");
     if (!ctx->sensor_set) return fail(ctx, FLR_ERR_STATE, "adjoint: needs a sensor");
+    if (p->form != FLR_FORM_PLAIN && p->form != FLR_FORM_WAVEFRONT && p->form != FLR_FORM_WAVEFRONT_WARP)
+        return fail(ctx, FLR_ERR_ARG, "params: unknown form");
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || (p->block_size & 31)))
         return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
@@ -840,12 +855,41 @@ int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float 
     R.film_scale = (float)(1.0 / (double)p->n_paths);
     R.error_word = ctx->d_error;
     AdjDev A;
+    std::memset(&A, 0, sizeof(A));
     A.adj = adj_film;
     A.grad_c = grad_conc;
     A.nvox = nv;
     A.grad_sigma_s = grad_sigma_s;
-    e = launch_adjoint(S, R, A, p->block_size, p->blocks_per_sm, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch adjoint kernel");
+    if (p->form == FLR_FORM_PLAIN) {
+        e = launch_adjoint(S, R, A, p->block_size, p->blocks_per_sm, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "launch adjoint kernel");
+        return FLR_OK;
+    }
+    // warp-regrouped two-pass replay over chunks of at most ADJ_CHUNK paths
+    const uint64_t chunk = std::min<uint64_t>(ADJ_CHUNK, p->n_paths);
+    rc = grow(ctx, (void **)&ctx->d_adj_ak, &ctx->adj_ak_cap, (size_t)chunk * ADJ_K, sizeof(float),
+              "adjoint contributions");
+    if (rc != FLR_OK) return rc;
+    rc = grow(ctx, (void **)&ctx->d_adj_ovf, &ctx->adj_ovf_cap, (size_t)chunk, sizeof(float),
+              "adjoint contributions");
+    if (rc != FLR_OK) return rc;
+    A.ak = ctx->d_adj_ak;
+    A.ovf = ctx->d_adj_ovf;
+    A.K = ADJ_K;
+    R.work_counter = ctx->d_work;
+    R.regroup = p->regroup_interval;
+    for (uint64_t off = 0; off < p->n_paths; off += chunk) {
+        const uint64_t n = std::min<uint64_t>(chunk, p->n_paths - off);
+        R.n_paths = n;
+        R.path_offset = p->path_offset + off;
+        e = cudaMemsetAsync(A.ak, 0, sizeof(float) * (size_t)n * ADJ_K, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(A.ovf, 0, sizeof(float) * (size_t)n, st);
+        for (int pass = 1; pass <= 2 && e == cudaSuccess; ++pass) {
+            e = cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), st);
+            if (e == cudaSuccess) e = launch_adjoint_warp(S, R, A, pass, p->block_size, p->blocks_per_sm, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "launch adjoint kernels");
+    }
     return FLR_OK;
 }
 

@@ -129,11 +129,19 @@ struct AdjDev {
     float *grad_c;
     long long nvox;
     float *grad_sigma_s;
+    // two-pass replay of the warp-regrouped form: a_k of the first K connections of each path of
+    // the launch ([n_paths][K], zeroed before pass 1) and the sum of the later ones ([n_paths])
+    float *ak;
+    float *ovf;
+    int K;
 };
 
 // Host-side launchers (fluoro_kernels.cu).
 cudaError_t launch_adjoint(const SceneDev &S, const RunDev &R, const AdjDev &A, int block,
                            int blocks_per_sm, cudaStream_t st);
+// pass 1 (weights) or pass 2 (gradients) of the warp-regrouped adjoint; R.work_counter zeroed
+cudaError_t launch_adjoint_warp(const SceneDev &S, const RunDev &R, const AdjDev &A, int pass,
+                                int block, int blocks_per_sm, cudaStream_t st);
 cudaError_t launch_batch(const BatchDev &Bt, const RunDev &R, int block, int blocks_per_sm,
                          cudaStream_t st);
 int batch_occupancy_blocks_per_sm(int block);

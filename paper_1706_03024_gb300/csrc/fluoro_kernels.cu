@@ -1087,188 +1087,6 @@ __global__ void __launch_bounds__(256) k_trace_wavefront(SceneDev S, RunDev R)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Wavefront form with per-warp regrouping and pull-based connection drains. Each warp queues its
-// lanes' sensor connections in shared memory (up to WQ_CAP records). Once WQ_DRAIN records are
-// waiting (or the work is done) the warp drains the queue: every lane advances its own
-// ratio-tracking march by one step per iteration and claims the next record as soon as its march
-// ends, so the lanes stay busy until the queue runs dry instead of waiting for the longest march
-// of a fixed batch. The marches consume their random numbers exactly as transmittance() does, so
-// every launch form gives the same film up to the order of the fp32 film atomics.
-struct March {
-    float3 x, dir;
-    float tl, t, T, isb, wg;
-    int b, pix, it;
-    uint32_t j, step;
-    uint64_t pid;
-    U4 blk;
-};
-
-__device__ __forceinline__ void march_deposit(const SceneDev &S, const RunDev &R, const March &mc)
-{
-    const float val = mc.wg * mc.T * R.film_scale;
-    if (val > 0.0f) atomicAdd(&R.film[(size_t)mc.pix * S.B + mc.b], val);
-}
-
-// Starts the connection of one queued vertex; returns true if a ratio-tracking march remains (the
-// connections that need no march are deposited here).
-__device__ __forceinline__ bool march_begin(const SceneDev &S, const RunDev &R, const Smem &sm,
-                                            float3 x, int b, float w, int lamb, uint64_t pid,
-                                            uint32_t step, March &mc, RegCnt &rc)
-{
-    const ConnGeom g = connect_geom(S, sm, x, lamb);
-    if (!g.ok) return false;
-    rc.connections++;
-    mc.wg = w * g.gf;
-    mc.pix = g.pix;
-    mc.b = b;
-    const float sb = sm.maj[b];
-    if (!(sb > 0.0f) || S.homogeneous || S.mc > 0) {
-        mc.T = transmittance(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, NoSink{});
-        march_deposit(S, R, mc);
-        return false;
-    }
-    mc.x = x;
-    mc.dir = g.dir;
-    mc.tl = g.tl;
-    mc.t = 0.0f;
-    mc.T = 1.0f;
-    mc.isb = __frcp_rn(sb);
-    mc.j = 0;
-    mc.it = 0;
-    mc.pid = pid;
-    mc.step = step;
-    return true;
-}
-
-__device__ __forceinline__ float march_uniform(const RunDev &R, March &mc)
-{
-    if ((mc.j & 3u) == 0u) mc.blk = draw(R.seed, R.medium_id, mc.pid, mc.step, 2u + (mc.j >> 2));
-    const uint32_t q = mc.j & 3u;
-    ++mc.j;
-    return q == 0 ? mc.blk.a : (q == 1 ? mc.blk.b : (q == 2 ? mc.blk.c : mc.blk.d));
-}
-
-// One ratio-tracking step (the body of transmittance()'s loop); returns false when the march ends.
-__device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, const Smem &sm,
-                                           March &mc, RegCnt &rc)
-{
-    if (mc.it >= MAX_CONNECT_STEPS) {
-        cnt_add(sm, FLR_C_CONNECT_BUDGET);
-        return false;
-    }
-    ++mc.it;
-    const float u = march_uniform(R, mc);
-    mc.t -= __logf(1.0f - u) * mc.isb;
-    if (mc.t >= mc.tl) {
-        march_deposit(S, R, mc);
-        return false;
-    }
-    rc.connect_steps++;
-    const MedS m{S, sm};
-    const float3 p = make_float3(mc.x.x + mc.t * mc.dir.x, mc.x.y + mc.t * mc.dir.y,
-                                 mc.x.z + mc.t * mc.dir.z);
-    const float st = sigma_t_at(m, p, mc.b);
-    mc.T *= fmaxf(0.0f, 1.0f - st * mc.isb);
-    if (S.sk > 0 && st == 0.0f) {
-        const float tl2 = empty_cube_exit(m, p, mc.dir, inv_dir(mc.dir));
-        if (tl2 > 0.0f) {
-            mc.t += tl2;
-            rc.cell_walks++;
-        }
-    }
-    if (mc.T < RT_RR_THRESHOLD) {
-        const float u2 = march_uniform(R, mc);
-        if (u2 < 0.5f) {
-            mc.T *= 2.0f;
-        } else {
-            return false;
-        }
-    }
-    return true;
-}
-
-__global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, RunDev R)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT_WARP, blockDim.x);
-    const Smem sm = block_prologue(S, smem_raw, L);
-    const MedS m{S, sm};
-    constexpr unsigned FULL = 0xffffffffu;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    const unsigned lower = (1u << lane) - 1u;
-    Queue q;
-    {
-        unsigned char *base = smem_raw + L.queue_off_bytes;
-        float *f = reinterpret_cast<float *>(base) + warp * WQ_CAP * 8;
-        q.x = f;
-        q.y = q.x + WQ_CAP;
-        q.z = q.y + WQ_CAP;
-        q.w = q.z + WQ_CAP;
-        q.bin_lamb = reinterpret_cast<int *>(q.w + WQ_CAP);
-        q.pid_lo = reinterpret_cast<uint32_t *>(q.bin_lamb + WQ_CAP);
-        q.pid_hi = q.pid_lo + WQ_CAP;
-        q.step = q.pid_hi + WQ_CAP;
-        q.head_tail = reinterpret_cast<int *>(base + (size_t)nwarps * WQ_CAP * 32) + 2 * warp;
-        if (lane == 0) { q.head_tail[0] = 0; q.head_tail[1] = 0; }
-    }
-    __syncwarp();
-    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
-    Path p;
-    p.alive = false;
-    bool exhausted = false;
-    const int regroup = R.regroup > 0 ? R.regroup : 1;
-    while (true) {
-        // tracking: at most `regroup` steps or one queued connection per lane
-        for (int s = 0; s < regroup; ++s) {
-            if (!p.alive) {
-                if (exhausted) break;
-                const unsigned long long i = atomicAdd(R.work_counter, 1ull);
-                if (i >= R.n_paths) { exhausted = true; break; }
-                const Conn c = spawn(m, R, sm, R.path_offset + i, p);
-                if (c.valid) { queue_push(q, WQ_CAP, c); break; }
-                continue;
-            }
-            const Conn c = track_step(m, R, sm, p, rc);
-            if (c.valid) { queue_push(q, WQ_CAP, c); break; }
-        }
-        __syncwarp();
-        const bool any = __any_sync(FULL, p.alive || !exhausted);
-        const int avail = q.head_tail[1];
-        if (avail >= WQ_DRAIN || (!any && avail > 0)) {
-            // pull-based drain of all `avail` records
-            // Lanes claim new records only every fourth iteration: a march draws a Philox block
-            // every fourth step, so claims in step keep the draws of all lanes in the same
-            // iterations instead of spreading them over four divergent ones, and the set-up of
-            // new marches runs for several lanes at once.
-            March mc;
-            bool active = false;
-            int claimed = 0;
-            for (uint32_t iter = 0;; ++iter) {
-                const unsigned need = (iter & 3u) == 0u ? __ballot_sync(FULL, !active) : 0u;
-                if (need != 0u && !active) {
-                    const int k = claimed + __popc(need & lower);
-                    if (k < avail) {
-                        const int bl = q.bin_lamb[k];
-                        const uint64_t pid = ((uint64_t)q.pid_hi[k] << 32) | q.pid_lo[k];
-                        active = march_begin(S, R, sm, make_float3(q.x[k], q.y[k], q.z[k]), bl & 0xFFFF,
-                                             q.w[k], (bl >> 16) - 1, pid, q.step[k], mc, rc);
-                    }
-                }
-                claimed += __popc(need);
-                if (active) active = march_step(S, R, sm, mc, rc);
-                if (!__any_sync(FULL, active) && claimed >= avail) break;
-            }
-            __syncwarp();
-            if (lane == 0) q.head_tail[1] = 0;
-            __syncwarp();
-        }
-        if (!any) break;
-    }
-    block_epilogue(S, R, sm, rc);
-}
-
-// ---------------------------------------------------------------------------------------------
 // Adjoint (path replay). For L = sum_j adj_j I_j of the film estimator over the same paths, with
 // decisions frozen at the current parameters, dL/dtheta per path is
 //   sum_i d log p(decision_i) * (adjoint-weighted contributions after decision i)
@@ -1403,6 +1221,281 @@ __global__ void __launch_bounds__(256) k_adjoint(SceneDev S, RunDev R, AdjDev A)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gsig += __shfl_xor_sync(0xffffffffu, gsig, o);
     if ((threadIdx.x & 31) == 0 && gsig != 0.0f && A.grad_sigma_s) atomicAdd(A.grad_sigma_s, gsig);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Wavefront form with per-warp regrouping and pull-based connection drains. Each warp queues its
+// lanes' sensor connections in shared memory (up to WQ_CAP records). Once WQ_DRAIN records are
+// waiting (or the work is done) the warp drains the queue: every lane advances its own
+// ratio-tracking march by one step per iteration and claims the next record as soon as its march
+// ends, so the lanes stay busy until the queue runs dry instead of waiting for the longest march
+// of a fixed batch. The marches consume their random numbers exactly as transmittance() does, so
+// every launch form gives the same film up to the order of the fp32 film atomics.
+//
+// The same kernel runs the two passes of the adjoint replay (MODE):
+//   WM_RENDER       film contributions (the forward);
+//   WM_ADJ_WEIGHTS  pass 1: the adjoint-weighted contribution a_k = adj[pixel][bin] * value_k of
+//                   the k-th connection of each path, stored per path (the first ADJ_K of them;
+//                   the rest summed per path);
+//   WM_ADJ_GRAD     pass 2: replays each path with the decision scores times the suffix sums of
+//                   its a_k (read back in path order) and queues the transmittance-derivative
+//                   march of every contribution with a_k != 0 (scaled by a_k).
+constexpr int WM_RENDER = 0;
+constexpr int WM_ADJ_WEIGHTS = 1;
+constexpr int WM_ADJ_GRAD = 2;
+constexpr int WQ_ORD_MAX = (1 << 21) - 1;   // connection ordinals carried by a queue record
+
+struct March {
+    float3 x, dir;
+    float tl, t, T, isb, wg;   // wg: intensity x importance (render, pass 1) or a_k (pass 2)
+    int b, pix, it, ord;
+    uint32_t j, step;
+    uint64_t pid;
+    U4 blk;
+};
+
+// A queued connection record: position, weight (pass 2: a_k), bin, vertex kind, ordinal along
+// its path, RNG coordinates. bin < 256 (FLR_MAX_BINS), vertex kind + 1 in 0..6.
+__device__ __forceinline__ void wq_push(const Queue &q, const Conn &c, float w, int ord)
+{
+    const int slot = atomicAdd(&q.head_tail[1], 1) % WQ_CAP;
+    q.x[slot] = c.x.x;
+    q.y[slot] = c.x.y;
+    q.z[slot] = c.x.z;
+    q.w[slot] = w;
+    q.bin_lamb[slot] = (c.bin & 0xFF) | ((c.lamb + 1) << 8) | (min(ord, WQ_ORD_MAX) << 11);
+    q.pid_lo[slot] = (uint32_t)c.pid;
+    q.pid_hi[slot] = (uint32_t)(c.pid >> 32);
+    q.step[slot] = c.step;
+}
+
+// The end of a march that reached the sensor side of the box.
+template <int MODE>
+__device__ __forceinline__ void march_deposit(const SceneDev &S, const RunDev &R, const AdjDev &A,
+                                              const March &mc)
+{
+    if (MODE == WM_ADJ_GRAD) return;
+    const float val = mc.wg * mc.T * R.film_scale;
+    if (!(val > 0.0f)) return;
+    if (MODE == WM_RENDER) {
+        atomicAdd(&R.film[(size_t)mc.pix * S.B + mc.b], val);
+    } else {
+        const float a = __ldg(&A.adj[(size_t)mc.pix * S.B + mc.b]) * val;
+        if (a == 0.0f) return;
+        const uint64_t i = mc.pid - R.path_offset;
+        if (mc.ord < A.K) A.ak[i * A.K + mc.ord] = a;
+        else atomicAdd(&A.ovf[i], a);
+    }
+}
+
+// Starts the connection of one queued vertex; returns true if a ratio-tracking march remains (the
+// connections that need no march are finished here).
+template <int MODE>
+__device__ __forceinline__ bool march_begin(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                            const AdjDev &A, float3 x, int b, float w, int lamb,
+                                            int ord, uint64_t pid, uint32_t step, March &mc,
+                                            RegCnt &rc, float &gsig)
+{
+    const ConnGeom g = connect_geom(S, sm, x, lamb);
+    if (!g.ok) return false;
+    if (MODE != WM_ADJ_GRAD) rc.connections++;
+    mc.wg = MODE == WM_ADJ_GRAD ? w : w * g.gf;
+    mc.pix = g.pix;
+    mc.b = b;
+    if (MODE == WM_ADJ_WEIGHTS) mc.ord = ord;
+    mc.pid = pid;
+    const float sb = sm.maj[b];
+    if (!(sb > 0.0f) || S.homogeneous || S.mc > 0) {
+        if (MODE == WM_ADJ_GRAD) {
+            transmittance(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, AdjSink{S, sm, A, w, &gsig});
+        } else {
+            mc.T = transmittance(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, NoSink{});
+            march_deposit<MODE>(S, R, A, mc);
+        }
+        return false;
+    }
+    mc.x = x;
+    mc.dir = g.dir;
+    mc.tl = g.tl;
+    mc.t = 0.0f;
+    mc.T = 1.0f;
+    mc.isb = __frcp_rn(sb);
+    mc.j = 0;
+    mc.it = 0;
+    mc.step = step;
+    return true;
+}
+
+__device__ __forceinline__ float march_uniform(const RunDev &R, March &mc)
+{
+    if ((mc.j & 3u) == 0u) mc.blk = draw(R.seed, R.medium_id, mc.pid, mc.step, 2u + (mc.j >> 2));
+    const uint32_t q = mc.j & 3u;
+    ++mc.j;
+    return q == 0 ? mc.blk.a : (q == 1 ? mc.blk.b : (q == 2 ? mc.blk.c : mc.blk.d));
+}
+
+// One ratio-tracking step (the body of transmittance()'s loop); returns false when the march ends.
+template <int MODE>
+__device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                           const AdjDev &A, March &mc, RegCnt &rc, float &gsig)
+{
+    if (mc.it >= MAX_CONNECT_STEPS) {
+        cnt_add(sm, FLR_C_CONNECT_BUDGET);
+        return false;
+    }
+    ++mc.it;
+    const float u = march_uniform(R, mc);
+    mc.t -= __logf(1.0f - u) * mc.isb;
+    if (mc.t >= mc.tl) {
+        march_deposit<MODE>(S, R, A, mc);
+        return false;
+    }
+    rc.connect_steps++;
+    const MedS m{S, sm};
+    const float3 p = make_float3(mc.x.x + mc.t * mc.dir.x, mc.x.y + mc.t * mc.dir.y,
+                                 mc.x.z + mc.t * mc.dir.z);
+    const float st = sigma_t_at(m, p, mc.b);
+    if (MODE == WM_ADJ_GRAD) AdjSink{S, sm, A, mc.wg, &gsig}.point(p, mc.b, st, sm.maj[mc.b]);
+    mc.T *= fmaxf(0.0f, 1.0f - st * mc.isb);
+    if (S.sk > 0 && st == 0.0f) {
+        const float tl2 = empty_cube_exit(m, p, mc.dir, inv_dir(mc.dir));
+        if (tl2 > 0.0f) {
+            mc.t += tl2;
+            rc.cell_walks++;
+        }
+    }
+    if (mc.T < RT_RR_THRESHOLD) {
+        const float u2 = march_uniform(R, mc);
+        if (u2 < 0.5f) {
+            mc.T *= 2.0f;
+        } else {
+            return false;
+        }
+    }
+    return true;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, RunDev R, AdjDev A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT_WARP, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L);
+    const MedS m{S, sm};
+    constexpr unsigned FULL = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const unsigned lower = (1u << lane) - 1u;
+    Queue q;
+    {
+        unsigned char *base = smem_raw + L.queue_off_bytes;
+        float *f = reinterpret_cast<float *>(base) + warp * WQ_CAP * 8;
+        q.x = f;
+        q.y = q.x + WQ_CAP;
+        q.z = q.y + WQ_CAP;
+        q.w = q.z + WQ_CAP;
+        q.bin_lamb = reinterpret_cast<int *>(q.w + WQ_CAP);
+        q.pid_lo = reinterpret_cast<uint32_t *>(q.bin_lamb + WQ_CAP);
+        q.pid_hi = q.pid_lo + WQ_CAP;
+        q.step = q.pid_hi + WQ_CAP;
+        q.head_tail = reinterpret_cast<int *>(base + (size_t)nwarps * WQ_CAP * 32) + 2 * warp;
+        if (lane == 0) { q.head_tail[0] = 0; q.head_tail[1] = 0; }
+    }
+    __syncwarp();
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
+    Path p;
+    p.alive = false;
+    bool exhausted = false;
+    int ord = 0;                       // connections of the lane's path so far (adjoint passes)
+    float tot = 0.0f, pre = 0.0f;      // pass 2: sum of the path's a_k, and of those seen so far
+    float gsig = 0.0f;                 // pass 2: this lane's share of dL/dsigma_s
+    const int regroup = R.regroup > 0 ? R.regroup : 1;
+    while (true) {
+        // tracking: at most `regroup` steps or one queued connection per lane
+        for (int s = 0; s < regroup; ++s) {
+            Conn c;
+            if (!p.alive) {
+                if (exhausted) break;
+                const unsigned long long i = atomicAdd(R.work_counter, 1ull);
+                if (i >= R.n_paths) { exhausted = true; break; }
+                c = spawn(m, R, sm, R.path_offset + i, p);
+                ord = 0;
+                if (MODE == WM_ADJ_GRAD) {
+                    // the path's contributions from pass 1, summed in path order
+                    const float *ak = A.ak + i * A.K;
+                    const float ov = A.ovf[i];
+                    bool any = ov != 0.0f;
+                    tot = 0.0f;
+                    for (int k = 0; k < A.K; ++k) {
+                        const float a = ak[k];
+                        tot += a;
+                        any |= a != 0.0f;
+                    }
+                    tot += ov;
+                    pre = 0.0f;
+                    if (!any) { p.alive = false; continue; }   // nothing to differentiate
+                }
+            } else if (MODE == WM_ADJ_GRAD) {
+                c = track_step(m, R, sm, p, rc, AdjObs{S, sm, A, tot - pre, &gsig});
+            } else {
+                c = track_step(m, R, sm, p, rc);
+            }
+            if (!c.valid) continue;
+            if (MODE == WM_ADJ_GRAD) {
+                const float a = ord < A.K ? __ldg(&A.ak[(p.pid - R.path_offset) * A.K + ord])
+                                          : adjoint_weight(S, R, sm, A, c, rc);
+                ++ord;
+                pre += a;
+                if (a != 0.0f) { wq_push(q, c, a, 0); break; }
+            } else {
+                wq_push(q, c, c.w, MODE == WM_ADJ_WEIGHTS ? ord : 0);
+                if (MODE == WM_ADJ_WEIGHTS) ++ord;
+                break;
+            }
+        }
+        __syncwarp();
+        const bool any = __any_sync(FULL, p.alive || !exhausted);
+        const int avail = q.head_tail[1];
+        if (avail >= WQ_DRAIN || (!any && avail > 0)) {
+            // pull-based drain of all `avail` records
+            // Lanes claim new records only every fourth iteration: a march draws a Philox block
+            // every fourth step, so claims in step keep the draws of all lanes in the same
+            // iterations instead of spreading them over four divergent ones, and the set-up of
+            // new marches runs for several lanes at once.
+            March mc;
+            bool active = false;
+            int claimed = 0;
+            for (uint32_t iter = 0;; ++iter) {
+                const unsigned need = (iter & 3u) == 0u ? __ballot_sync(FULL, !active) : 0u;
+                if (need != 0u && !active) {
+                    const int k = claimed + __popc(need & lower);
+                    if (k < avail) {
+                        const int bl = q.bin_lamb[k];
+                        const uint64_t pid = ((uint64_t)q.pid_hi[k] << 32) | q.pid_lo[k];
+                        active = march_begin<MODE>(S, R, sm, A, make_float3(q.x[k], q.y[k], q.z[k]),
+                                                   bl & 0xFF, q.w[k], ((bl >> 8) & 7) - 1,
+                                                   MODE == WM_ADJ_WEIGHTS ? (int)((unsigned)bl >> 11) : 0,
+                                                   pid, q.step[k], mc, rc,
+                                                   gsig);
+                    }
+                }
+                claimed += __popc(need);
+                if (active) active = march_step<MODE>(S, R, sm, A, mc, rc, gsig);
+                if (!__any_sync(FULL, active) && claimed >= avail) break;
+            }
+            __syncwarp();
+            if (lane == 0) q.head_tail[1] = 0;
+            __syncwarp();
+        }
+        if (!any) break;
+    }
+    if (MODE == WM_RENDER) {
+        block_epilogue(S, R, sm, rc);
+    } else if (MODE == WM_ADJ_GRAD) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gsig += __shfl_xor_sync(FULL, gsig, o);
+        if (lane == 0 && gsig != 0.0f && A.grad_sigma_s) atomicAdd(A.grad_sigma_s, gsig);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1648,9 +1741,17 @@ cudaError_t allow_smem(int form, int smem)
     if (smem <= 48 * 1024) return cudaSuccess;
     if (form == FLR_FORM_WAVEFRONT)
         return cudaFuncSetAttribute(k_trace_wavefront, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (form == FLR_FORM_WAVEFRONT_WARP)
-        return cudaFuncSetAttribute(k_trace_wavefront_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    smem);
+    if (form == FLR_FORM_WAVEFRONT_WARP) {
+        cudaError_t e = cudaFuncSetAttribute(k_trace_wavefront_warp<WM_RENDER>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_trace_wavefront_warp<WM_ADJ_WEIGHTS>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_trace_wavefront_warp<WM_ADJ_GRAD>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        return e;
+    }
     cudaError_t e = cudaFuncSetAttribute(k_trace_plain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem);
     if (e != cudaSuccess) return e;
@@ -1666,7 +1767,7 @@ int occupancy_blocks_per_sm(int B, int form, int block)
     if (form == FLR_FORM_WAVEFRONT)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront, block, smem);
     else if (form == FLR_FORM_WAVEFRONT_WARP)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront_warp, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront_warp<WM_RENDER>, block, smem);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_plain<true>, block, smem);
     return n > 0 ? n : 1;
@@ -1690,7 +1791,7 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
     if (form == FLR_FORM_WAVEFRONT)
         k_trace_wavefront<<<(unsigned)grid, block, smem, st>>>(S, R);
     else if (form == FLR_FORM_WAVEFRONT_WARP)
-        k_trace_wavefront_warp<<<(unsigned)grid, block, smem, st>>>(S, R);
+        k_trace_wavefront_warp<WM_RENDER><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
     else if (S.mc > 0 || S.sk > 0)
         k_trace_plain<true><<<(unsigned)grid, block, smem, st>>>(S, R);
     else
@@ -1730,6 +1831,28 @@ cudaError_t launch_adjoint(const SceneDev &S, const RunDev &R, const AdjDev &A, 
     if (need < grid) grid = need;
     if (grid < 1) grid = 1;
     k_adjoint<<<(unsigned)grid, block, smem, st>>>(S, R, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_warp(const SceneDev &S, const RunDev &R, const AdjDev &A, int pass,
+                                int block, int blocks_per_sm, cudaStream_t st)
+{
+    if (block <= 0) block = trace_block_default();
+    const int smem = trace_smem_bytes(S.B, FLR_FORM_WAVEFRONT_WARP, block);
+    const cudaError_t ea = allow_smem(FLR_FORM_WAVEFRONT_WARP, smem);
+    if (ea != cudaSuccess) return ea;
+    int occ = 0;
+    if (pass == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_wavefront_warp<WM_ADJ_WEIGHTS>, block, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_wavefront_warp<WM_ADJ_GRAD>, block, smem);
+    if (occ < 1) occ = 1;
+    if (blocks_per_sm <= 0 || blocks_per_sm > occ) blocks_per_sm = occ;
+    const long long grid = (long long)num_sms() * blocks_per_sm;
+    if (pass == 1)
+        k_trace_wavefront_warp<WM_ADJ_WEIGHTS><<<(unsigned)grid, block, smem, st>>>(S, R, A);
+    else
+        k_trace_wavefront_warp<WM_ADJ_GRAD><<<(unsigned)grid, block, smem, st>>>(S, R, A);
     return cudaGetLastError();
 }
 

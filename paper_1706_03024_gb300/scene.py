@@ -187,12 +187,15 @@ class Scene:
     def adjoint(self, adj, grad_conc=None, grad_sigma_s=None, n_paths=None, path_offset=0,
                 seed=None, medium_id=0, analog=None, max_inelastic=None, n_rr=None,
                 max_events=None, max_steps=None, accumulate=False, block_size=0, macro_cell=0,
-                majorant_margin=0.0, skip_cell=0, stream=None):
+                majorant_margin=0.0, skip_cell=0, form="wavefront_warp", regroup=0, stream=None):
         """Path-replay gradient of sum(adj * film) for the paths render() traces with the same
-        arguments; writes into grad_conc [D,nz,ny,nx] and grad_sigma_s [1] (CUDA f32 tensors)."""
-        p = self._params(n_paths, path_offset, seed, medium_id, "plain", analog, max_inelastic,
-                         n_rr, max_events, max_steps, accumulate, block_size, macro_cell=macro_cell,
-                         majorant_margin=majorant_margin, skip_cell=skip_cell)
+        arguments; writes into grad_conc [D,nz,ny,nx] and grad_sigma_s [1] (CUDA f32 tensors).
+        form "plain": one thread replays a whole path twice; "wavefront_warp" (or "wavefront"):
+        two warp-regrouped passes, contributions first, then the gradients."""
+        p = self._params(n_paths, path_offset, seed, medium_id, form, analog, max_inelastic,
+                         n_rr, max_events, max_steps, accumulate, block_size, regroup=regroup,
+                         macro_cell=macro_cell, majorant_margin=majorant_margin,
+                         skip_cell=skip_cell)
         adj = adj.contiguous()
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         N.check(N.flr_adjoint(self.ctx, p, adj.data_ptr(),
@@ -234,7 +237,7 @@ class FluoroRender(torch.autograd.Function):
 
     Usage: film = FluoroRender.apply(conc, sigma_s, scene, opts) with conc a CUDA f32 tensor
     [D,nz,ny,nx], sigma_s a 0-d tensor, scene a Scene and opts the render keyword arguments
-    (n_paths, seed, path_offset, ...)."""
+    (n_paths, seed, path_offset, form, ...; "adjoint_form" picks the replay's form)."""
 
     @staticmethod
     def forward(ctx, conc, sigma_s, scene, opts):
@@ -243,8 +246,9 @@ class FluoroRender(torch.autograd.Function):
         opts.setdefault("majorant_margin", 0.1)
         conc_c = conc.detach().contiguous()
         scene.set_medium_values(conc_c, float(sigma_s))
-        film = scene.render(form=opts.get("form", "wavefront"),
-                            **{k: v for k, v in opts.items() if k != "form"}).clone()
+        film = scene.render(form=opts.get("form", "wavefront_warp"),
+                            **{k: v for k, v in opts.items()
+                               if k not in ("form", "adjoint_form")}).clone()
         ctx.save_for_backward(conc_c, sigma_s.detach())
         ctx.scene = scene
         ctx.opts = opts
@@ -257,8 +261,9 @@ class FluoroRender(torch.autograd.Function):
         S.set_medium_values(conc, float(sigma_s))
         gc = torch.empty_like(conc) if ctx.needs_input_grad[0] else None
         gs = torch.empty(1, dtype=torch.float32, device=conc.device)
-        opts = {k: v for k, v in ctx.opts.items() if k not in ("form", "regroup")}
-        S.adjoint(grad_film.float(), gc, gs, **opts)
+        opts = {k: v for k, v in ctx.opts.items() if k not in ("form", "regroup", "adjoint_form")}
+        S.adjoint(grad_film.float(), gc, gs, form=ctx.opts.get("adjoint_form", "wavefront_warp"),
+                  **opts)
         return gc, gs.reshape(()).to(sigma_s.dtype), None, None
 
 
