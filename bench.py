@@ -227,8 +227,9 @@ def bench_batched(args, local, rank, flush, stream, barrier, reduce_max, reduce_
 
 def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum):
     """Gradient of sum((I - T)^2) over the 256x256x81 film w.r.t. 2 x 64^3 concentrations and
-    sigma_s (32 paths per pixel): the forward (wavefront and plain) and the path-replay adjoint on
-    the same paths, so every form carries the same estimator."""
+    sigma_s (32 paths per pixel): the forward (warp-regrouped and plain) and the path-replay
+    adjoint (two warp-regrouped passes, and the one-thread replay) on the same paths, so every form
+    carries the same estimator."""
     import torch
     from paper_1706_03024_gb300.scene import Scene
 
@@ -238,13 +239,13 @@ def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_
     n = sc["params"]["n_paths"]
     tgt_sc = sg.cfg4_adjoint(field_seed=1, seed=1000 + rank)
     tgt_sc["params"]["n_paths"] = min(8 * n, 1 << 24)
-    T = Scene(tgt_sc, device=local).render(form="wavefront").clone()
+    T = Scene(tgt_sc, device=local).render(form="wavefront_warp").clone()
     S = Scene(sc, device=local)
     gc = torch.zeros(S.conc_t.shape, dtype=torch.float32, device=torch.device("cuda", local))
     gs = torch.zeros(1, dtype=torch.float32, device=gc.device)
     mc = args.macro_cell
     mg = 0.1  # the score estimator needs sigma_bar > sigma_t: forward and replay share the margin
-    film = S.render(form="wavefront", macro_cell=mc, majorant_margin=mg)
+    film = S.render(form="wavefront_warp", macro_cell=mc, majorant_margin=mg)
     adj = (2.0 * (film - T)).contiguous()
     S.adjoint(adj, gc, gs, macro_cell=mc, majorant_margin=mg)
     torch.cuda.synchronize()
@@ -262,20 +263,26 @@ def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_
         return reduce_max(sum(ms) / len(ms)), ms
 
     barrier()
-    fwd_ms, _ = timed(lambda: S.render(form="wavefront", macro_cell=mc, majorant_margin=mg),
+    fwd_ms, _ = timed(lambda: S.render(form="wavefront_warp", macro_cell=mc, majorant_margin=mg),
                       args.adjoint_steps)
     events = S.read()["counters"]["events"]
     plain_ms, _ = timed(lambda: S.render(form="plain", majorant_margin=mg), args.adjoint_steps)
     adj_ms, adj_steps = timed(lambda: S.adjoint(adj, gc, gs, macro_cell=mc, majorant_margin=mg),
                               args.adjoint_steps)
+    adj_plain_ms, _ = timed(lambda: S.adjoint(adj, gc, gs, macro_cell=mc, majorant_margin=mg,
+                                              form="plain"), args.adjoint_steps)
     ev = reduce_sum(float(events))
+    chunks = -(-n // (1 << 21))   # the replay runs its two passes per chunk of 2^21 paths
     return {"workload": f"2 x 64^3 blob dyes, 256x256x81 ortho film, {n} paths, loss sum((I-T)^2)",
             "macro_cell": mc,
             "adjoint_events_per_s": ev / (adj_ms / 1000.0), "adjoint_ms": adj_ms,
             "adjoint_ms_steps": [round(v, 3) for v in adj_steps],
-            "forward_wavefront_events_per_s": ev / (fwd_ms / 1000.0), "forward_wavefront_ms": fwd_ms,
+            "adjoint_plain_replay_ms": adj_plain_ms,
+            "adjoint_speedup_vs_plain_replay": adj_plain_ms / adj_ms,
+            "forward_warp_events_per_s": ev / (fwd_ms / 1000.0), "forward_warp_ms": fwd_ms,
             "plain_events_per_s": ev / (plain_ms / 1000.0), "plain_ms": plain_ms,
-            "adjoint_vs_plain": plain_ms / adj_ms, "events_per_step": events,
+            "adjoint_over_forward": adj_ms / fwd_ms, "events_per_step": events,
+            "launches_per_step": 3 + 2 * chunks,
             "grad_sigma_s": float(gs.item()), "grad_conc_abs_max": float(gc.abs().max().item())}
 
 
@@ -450,7 +457,7 @@ def run_ours(args):
     peak_ops = sms * 128 * sm_max * 1e6
     ops = algorithmic_ops(cnt_w)
     achieved = ops / (sum(ms_w) / len(ms_w) / 1000.0)
-    traffic = kernel_traffic("trace_wavefront_cornell_traffic.json")
+    traffic = kernel_traffic("trace_wavefront_warp_cornell_traffic.json")
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -493,7 +500,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps + len(ms_p)
             + (0 if batched is None else batched["steps"] + batched["plain_launches"])
-            + (0 if adjoint is None else 3 * args.adjoint_steps),
+            + (0 if adjoint is None else adjoint["launches_per_step"] * args.adjoint_steps),
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

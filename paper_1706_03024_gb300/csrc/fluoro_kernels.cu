@@ -1413,6 +1413,29 @@ __global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, Run
     while (true) {
         // tracking: at most `regroup` steps or one queued connection per lane
         for (int s = 0; s < regroup; ++s) {
+            if (MODE != WM_ADJ_GRAD) {
+                if (!p.alive) {
+                    if (exhausted) break;
+                    const unsigned long long i = atomicAdd(R.work_counter, 1ull);
+                    if (i >= R.n_paths) { exhausted = true; break; }
+                    const Conn c = spawn(m, R, sm, R.path_offset + i, p);
+                    ord = 0;
+                    if (c.valid) {
+                        wq_push(q, c, c.w, ord);
+                        if (MODE == WM_ADJ_WEIGHTS) ++ord;
+                        break;
+                    }
+                    continue;
+                }
+                const Conn c = track_step(m, R, sm, p, rc);
+                if (c.valid) {
+                    wq_push(q, c, c.w, MODE == WM_ADJ_WEIGHTS ? ord : 0);
+                    if (MODE == WM_ADJ_WEIGHTS) ++ord;
+                    break;
+                }
+                continue;
+            }
+            // pass 2 of the adjoint
             Conn c;
             if (!p.alive) {
                 if (exhausted) break;
@@ -1420,38 +1443,28 @@ __global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, Run
                 if (i >= R.n_paths) { exhausted = true; break; }
                 c = spawn(m, R, sm, R.path_offset + i, p);
                 ord = 0;
-                if (MODE == WM_ADJ_GRAD) {
-                    // the path's contributions from pass 1, summed in path order
-                    const float *ak = A.ak + i * A.K;
-                    const float ov = A.ovf[i];
-                    bool any = ov != 0.0f;
-                    tot = 0.0f;
-                    for (int k = 0; k < A.K; ++k) {
-                        const float a = ak[k];
-                        tot += a;
-                        any |= a != 0.0f;
-                    }
-                    tot += ov;
-                    pre = 0.0f;
-                    if (!any) { p.alive = false; continue; }   // nothing to differentiate
+                // the path's contributions from pass 1, summed in path order
+                const float *ak = A.ak + i * A.K;
+                const float ov = A.ovf[i];
+                bool nz = ov != 0.0f;
+                tot = 0.0f;
+                for (int k = 0; k < A.K; ++k) {
+                    const float a = ak[k];
+                    tot += a;
+                    nz |= a != 0.0f;
                 }
-            } else if (MODE == WM_ADJ_GRAD) {
-                c = track_step(m, R, sm, p, rc, AdjObs{S, sm, A, tot - pre, &gsig});
+                tot += ov;
+                pre = 0.0f;
+                if (!nz) { p.alive = false; continue; }   // nothing to differentiate
             } else {
-                c = track_step(m, R, sm, p, rc);
+                c = track_step(m, R, sm, p, rc, AdjObs{S, sm, A, tot - pre, &gsig});
             }
             if (!c.valid) continue;
-            if (MODE == WM_ADJ_GRAD) {
-                const float a = ord < A.K ? __ldg(&A.ak[(p.pid - R.path_offset) * A.K + ord])
-                                          : adjoint_weight(S, R, sm, A, c, rc);
-                ++ord;
-                pre += a;
-                if (a != 0.0f) { wq_push(q, c, a, 0); break; }
-            } else {
-                wq_push(q, c, c.w, MODE == WM_ADJ_WEIGHTS ? ord : 0);
-                if (MODE == WM_ADJ_WEIGHTS) ++ord;
-                break;
-            }
+            const float a = ord < A.K ? __ldg(&A.ak[(p.pid - R.path_offset) * A.K + ord])
+                                      : adjoint_weight(S, R, sm, A, c, rc);
+            ++ord;
+            pre += a;
+            if (a != 0.0f) { wq_push(q, c, a, 0); break; }
         }
         __syncwarp();
         const bool any = __any_sync(FULL, p.alive || !exhausted);
