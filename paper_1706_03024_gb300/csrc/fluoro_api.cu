@@ -166,7 +166,7 @@ void build_medium_tables(const flr_ctx *ctx, const flr_medium &m, const float *c
         for (int d = 0; d < m.n_dyes; ++d) {
             const int id = m.dye_ids[d];
             const double s = (double)ctx->eps[id] * (double)ctx->abs_shape[(size_t)id * B + b];
-            sig[d * B + b] = (float)s;
+            sig[tab_sig_a_at(B, d, b)] = (float)s;
             mj += s * (double)cmax[d];
         }
         maj[b] = mj > 0.0 ? round_up_f32(mj * (1.0 + 1e-6) * (1.0 + margin)) : 0.0f;

@@ -14,15 +14,19 @@ constexpr int MAX_CONNECT_STEPS = 1 << 16;   // ratio-tracking steps per sensor 
 constexpr float RT_RR_THRESHOLD = 1e-3f;     // roulette on the transmittance estimate below this
 
 // Layout of the per-medium spectral tables (fp32, global memory, staged into shared memory):
-//   sig_a[MAXD][B]   eps_d * a_d(lambda_b), per unit concentration      (Sec. 4.1)
+//   sig_a[B][MAXD]   eps_d * a_d(lambda_b), per unit concentration      (Sec. 4.1); the MAXD
+//                    dyes of one bin are one 16-byte vector
 //   cdf[MAXD][B]     emission CDF, fp64-built and rounded, last = 1      (Eq. 10)
 //   majorant[B]      sigma_bar(lambda_b) >= sigma_t(x, lambda_b) for all x
 //   qy[MAXD]
+// The size is padded to a multiple of 4 floats so that consecutive media's tables stay 16-byte
+// aligned.
 __host__ __device__ constexpr int tab_sig_a(int B) { return 0; }
+__host__ __device__ constexpr int tab_sig_a_at(int B, int d, int b) { return b * MAXD + d; }
 __host__ __device__ constexpr int tab_cdf(int B) { return MAXD * B; }
 __host__ __device__ constexpr int tab_majorant(int B) { return 2 * MAXD * B; }
 __host__ __device__ constexpr int tab_qy(int B) { return 2 * MAXD * B + B; }
-__host__ __device__ constexpr int tab_size(int B) { return 2 * MAXD * B + B + MAXD; }
+__host__ __device__ constexpr int tab_size(int B) { return (2 * MAXD * B + B + MAXD + 3) & ~3; }
 
 // Fixed-point tallies (u64, 2^-24 units of photon weight): face[2][6][B], absorbed[MAXD+1][B],
 // emitted[MAXD][B]. Integer sums make every launch form and thread order give identical bits.

@@ -113,7 +113,8 @@ struct MedS_ {
     __device__ __forceinline__ float sigma_a0() const { return S.sigma_a0; }
     __device__ __forceinline__ int wall_mask() const { return S.wall_mask; }
     __device__ __forceinline__ float wall_albedo() const { return S.wall_albedo; }
-    __device__ __forceinline__ float sig_a(int d, int b) const { return sm.sig_a[d * S.B + b]; }
+    __device__ __forceinline__ float sig_a(int d, int b) const { return sm.sig_a[tab_sig_a_at(S.B, d, b)]; }
+    __device__ __forceinline__ float4 sig_a4(int b) const { return reinterpret_cast<const float4 *>(sm.sig_a)[b]; }
     __device__ __forceinline__ float maj(int b) const { return sm.maj[b]; }
     __device__ __forceinline__ float qy(int d) const { return sm.qy[d]; }
     __device__ __forceinline__ const float *cdf(int d) const { return sm.cdf + d * S.B; }
@@ -174,7 +175,11 @@ struct MedB {
     {
         return reinterpret_cast<const float *>(__ldg(reinterpret_cast<const unsigned long long *>(&md->tables)));
     }
-    __device__ __forceinline__ float sig_a(int d, int b) const { return __ldg(tables() + tab_sig_a(B_) + d * B_ + b); }
+    __device__ __forceinline__ float sig_a(int d, int b) const { return __ldg(tables() + tab_sig_a(B_) + tab_sig_a_at(B_, d, b)); }
+    __device__ __forceinline__ float4 sig_a4(int b) const
+    {
+        return __ldg(reinterpret_cast<const float4 *>(tables() + tab_sig_a(B_)) + b);
+    }
     __device__ __forceinline__ float maj(int b) const { return __ldg(tables() + tab_majorant(B_) + b); }
     __device__ __forceinline__ float qy(int d) const { return __ldg(tables() + tab_qy(B_) + d); }
     __device__ __forceinline__ const float *cdf(int d) const { return tables() + tab_cdf(B_) + d * B_; }
@@ -236,10 +241,12 @@ __device__ __forceinline__ Coeffs coeffs_at(const M &m, float3 x, int b)
     k.bg = s * m.sigma_a0();
     k.total = k.scat + k.bg;
     const float cc[4] = {c.x, c.y, c.z, c.w};
+    const float4 sa = m.sig_a4(b);
+    const float ss[4] = {sa.x, sa.y, sa.z, sa.w};
     const int D = m.D();
 #pragma unroll
     for (int d = 0; d < MAXD; ++d) {
-        k.dye[d] = (d < D) ? m.sig_a(d, b) * cc[d] : 0.0f;
+        k.dye[d] = (d < D) ? ss[d] * cc[d] : 0.0f;
         k.total += k.dye[d];
     }
     return k;
@@ -1112,7 +1119,7 @@ struct AdjSink {
         const int v = voxel_of(m, p);
         if (A.grad_c && S.grid)
             for (int d = 0; d < S.D; ++d) {
-                const float g = q * sm.sig_a[d * S.B + b];
+                const float g = q * sm.sig_a[tab_sig_a_at(S.B, d, b)];
                 if (g != 0.0f) atomicAdd(&A.grad_c[(size_t)d * A.nvox + v], g);
             }
         const float sv = S.solvent ? (__ldg(&S.solvent[v]) ? 1.0f : 0.0f) : 1.0f;
@@ -1138,7 +1145,7 @@ struct AdjObs {
         if (!S.homogeneous) v = voxel_of(m, x);
         if (A.grad_c && S.grid)
             for (int d = 0; d < S.D; ++d) {
-                const float g = q * sm.sig_a[d * S.B + b];
+                const float g = q * sm.sig_a[tab_sig_a_at(S.B, d, b)];
                 if (g != 0.0f) atomicAdd(&A.grad_c[(size_t)d * A.nvox + v], g);
             }
         const float sv = S.solvent ? (__ldg(&S.solvent[v]) ? 1.0f : 0.0f) : 1.0f;
@@ -1152,7 +1159,7 @@ struct AdjObs {
         } else if (ev < S.D && A.grad_c && S.grid && k.dye[ev] > 0.0f) {
             const MedS m{S, sm};
             const int v = voxel_of(m, x);
-            atomicAdd(&A.grad_c[(size_t)ev * A.nvox + v], suffix * sm.sig_a[ev * S.B + b] / k.dye[ev]);
+            atomicAdd(&A.grad_c[(size_t)ev * A.nvox + v], suffix * sm.sig_a[tab_sig_a_at(S.B, ev, b)] / k.dye[ev]);
         }
     }
 };
@@ -1177,7 +1184,7 @@ __device__ __forceinline__ void adjoint_march(const SceneDev &S, const RunDev &R
     transmittance(S, R, sm, c.x, g.dir, g.tl, c.bin, c.pid, c.step, rc, AdjSink{S, sm, A, a, gsig});
 }
 
-__global__ void __launch_bounds__(256) k_adjoint(SceneDev S, RunDev R, AdjDev A)
+__global__ void __launch_bounds__(256, 1) k_adjoint(SceneDev S, RunDev R, AdjDev A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
