@@ -92,7 +92,10 @@ __device__ __forceinline__ void tally_add(const Smem &sm, int idx, float w)
 //         tallies in shared memory.
 //   MedB  one medium of a batched launch, per lane: fields read from global memory through the
 //         read-only path, tables in global memory (L1-resident), tallies in global memory.
-template <bool OPT>
+// OPT = false compiles the local-majorant and empty-space paths out (the plain baseline kernel);
+// MC = false compiles the local-majorant path alone out (launched whenever the scene has none:
+// the smaller code keeps the warp-regrouped kernel's loops in the instruction cache).
+template <bool OPT, bool MC = OPT>
 struct MedS_ {
     const SceneDev &S;
     const Smem &sm;
@@ -124,7 +127,7 @@ struct MedS_ {
     __device__ __forceinline__ float em_cdf(int k) const { return S.em_cdf[k]; }
     __device__ __forceinline__ const EmitterDev &em(int k) const { return S.em[k]; }
     __device__ __forceinline__ uint32_t key1(const RunDev &R) const { return R.medium_id; }
-    __device__ __forceinline__ bool macro() const { return OPT && S.mc > 0; }
+    __device__ __forceinline__ bool macro() const { return OPT && MC && S.mc > 0; }
     __device__ __forceinline__ float margin() const { return S.maj_margin; }
     __device__ __forceinline__ int mc_dims(int k) const { return S.mc_dims[k]; }
     __device__ __forceinline__ float mc_size(int k) const { return S.mc_size[k]; }
@@ -134,7 +137,6 @@ struct MedS_ {
     __device__ __forceinline__ int mc_empty_radius(int c) const { return (int)__ldg(&S.mc_dist[c]); }
     __device__ __forceinline__ bool skip() const { return OPT && S.sk > 0; }
 };
-// OPT = false compiles the local-majorant and empty-space paths out (the plain baseline kernel)
 using MedS = MedS_<true>;
 
 __device__ __forceinline__ void tally_add_global(unsigned long long *t, int idx, float w)
@@ -544,12 +546,12 @@ struct NoSink {
     __device__ __forceinline__ void homogeneous(float) const {}
 };
 
-template <class G, bool OPT = true>
+template <class G, bool OPT = true, bool MC = OPT>
 __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &R, const Smem &sm,
                                                float3 x, float3 dir, float tl, int b, uint64_t pid,
                                                uint32_t step, RegCnt &rc, const G &sink)
 {
-    const MedS_<OPT> m{S, sm};
+    const MedS_<OPT, MC> m{S, sm};
     const float sb = sm.maj[b];
     float T = 1.0f;
     if (!(sb > 0.0f)) return T;
@@ -557,7 +559,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
         sink.homogeneous(tl);
         return __expf(-sigma_t_at(m, x, b) * tl);
     }
-    if (OPT && S.mc > 0) {
+    if (OPT && MC && S.mc > 0) {
         // ratio tracking against the local majorants: one uniform per tentative point
         Dda dd;
         dda_init(m, dd, x, dir, inv_dir(dir));
@@ -1164,12 +1166,14 @@ struct AdjObs {
     }
 };
 
+template <bool MC = true>
 __device__ __forceinline__ float adjoint_weight(const SceneDev &S, const RunDev &R, const Smem &sm,
                                                 const AdjDev &A, const Conn &c, RegCnt &rc)
 {
     const ConnGeom g = connect_geom(S, sm, c.x, c.lamb);
     if (!g.ok) return 0.0f;
-    const float T = transmittance(S, R, sm, c.x, g.dir, g.tl, c.bin, c.pid, c.step, rc, NoSink{});
+    const float T = transmittance<NoSink, true, MC>(S, R, sm, c.x, g.dir, g.tl, c.bin, c.pid, c.step,
+                                                    rc, NoSink{});
     const float val = c.w * g.gf * T * R.film_scale;
     if (!(val > 0.0f)) return 0.0f;
     return __ldg(&A.adj[(size_t)g.pix * S.B + c.bin]) * val;
@@ -1295,9 +1299,20 @@ __device__ __forceinline__ void march_deposit(const SceneDev &S, const RunDev &R
     }
 }
 
+// Transmittance of a connection that needs no march: the bin has no extinction anywhere, or the
+// medium is homogeneous (Eq. 6 in closed form); the same cases, in the same way, as transmittance().
+template <class G>
+__device__ __forceinline__ float transmittance_closed(const SceneDev &S, const Smem &sm, float3 x,
+                                                      float tl, int b, const G &sink)
+{
+    if (!(sm.maj[b] > 0.0f)) return 1.0f;
+    sink.homogeneous(tl);
+    return __expf(-sigma_t_at(MedS_<false>{S, sm}, x, b) * tl);
+}
+
 // Starts the connection of one queued vertex; returns true if a ratio-tracking march remains (the
 // connections that need no march are finished here).
-template <int MODE>
+template <int MODE, bool MC>
 __device__ __forceinline__ bool march_begin(const SceneDev &S, const RunDev &R, const Smem &sm,
                                             const AdjDev &A, float3 x, int b, float w, int lamb,
                                             int ord, uint64_t pid, uint32_t step, March &mc,
@@ -1312,11 +1327,16 @@ __device__ __forceinline__ bool march_begin(const SceneDev &S, const RunDev &R, 
     if (MODE == WM_ADJ_WEIGHTS) mc.ord = ord;
     mc.pid = pid;
     const float sb = sm.maj[b];
-    if (!(sb > 0.0f) || S.homogeneous || S.mc > 0) {
+    if (!(sb > 0.0f) || S.homogeneous || (MC && S.mc > 0)) {
+        const bool closed = !(sb > 0.0f) || S.homogeneous;
         if (MODE == WM_ADJ_GRAD) {
-            transmittance(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, AdjSink{S, sm, A, w, &gsig});
+            const AdjSink sink{S, sm, A, w, &gsig};
+            if (closed) transmittance_closed(S, sm, x, g.tl, b, sink);
+            else transmittance<AdjSink, true, MC>(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, sink);
         } else {
-            mc.T = transmittance(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, NoSink{});
+            mc.T = closed ? transmittance_closed(S, sm, x, g.tl, b, NoSink{})
+                          : transmittance<NoSink, true, MC>(S, R, sm, x, g.dir, g.tl, b, pid, step, rc,
+                                                            NoSink{});
             march_deposit<MODE>(S, R, A, mc);
         }
         return false;
@@ -1382,13 +1402,13 @@ __device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, c
     return true;
 }
 
-template <int MODE>
+template <int MODE, bool MC>
 __global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, RunDev R, AdjDev A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT_WARP, blockDim.x);
     const Smem sm = block_prologue(S, smem_raw, L);
-    const MedS m{S, sm};
+    const MedS_<true, MC> m{S, sm};
     constexpr unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
@@ -1468,7 +1488,7 @@ __global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, Run
             }
             if (!c.valid) continue;
             const float a = ord < A.K ? __ldg(&A.ak[(p.pid - R.path_offset) * A.K + ord])
-                                      : adjoint_weight(S, R, sm, A, c, rc);
+                                      : adjoint_weight<MC>(S, R, sm, A, c, rc);
             ++ord;
             pre += a;
             if (a != 0.0f) { wq_push(q, c, a, 0); break; }
@@ -1492,7 +1512,7 @@ __global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, Run
                     if (k < avail) {
                         const int bl = q.bin_lamb[k];
                         const uint64_t pid = ((uint64_t)q.pid_hi[k] << 32) | q.pid_lo[k];
-                        active = march_begin<MODE>(S, R, sm, A, make_float3(q.x[k], q.y[k], q.z[k]),
+                        active = march_begin<MODE, MC>(S, R, sm, A, make_float3(q.x[k], q.y[k], q.z[k]),
                                                    bl & 0xFF, q.w[k], ((bl >> 8) & 7) - 1,
                                                    MODE == WM_ADJ_WEIGHTS ? (int)((unsigned)bl >> 11) : 0,
                                                    pid, q.step[k], mc, rc,
@@ -1762,15 +1782,15 @@ cudaError_t allow_smem(int form, int smem)
     if (form == FLR_FORM_WAVEFRONT)
         return cudaFuncSetAttribute(k_trace_wavefront, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (form == FLR_FORM_WAVEFRONT_WARP) {
-        cudaError_t e = cudaFuncSetAttribute(k_trace_wavefront_warp<WM_RENDER>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_trace_wavefront_warp<WM_ADJ_WEIGHTS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_trace_wavefront_warp<WM_ADJ_GRAD>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        return e;
+        void (*const ks[])(SceneDev, RunDev, AdjDev) = {
+            k_trace_wavefront_warp<WM_RENDER, false>, k_trace_wavefront_warp<WM_RENDER, true>,
+            k_trace_wavefront_warp<WM_ADJ_WEIGHTS, false>, k_trace_wavefront_warp<WM_ADJ_WEIGHTS, true>,
+            k_trace_wavefront_warp<WM_ADJ_GRAD, false>, k_trace_wavefront_warp<WM_ADJ_GRAD, true>};
+        for (auto k : ks) {
+            const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
     cudaError_t e = cudaFuncSetAttribute(k_trace_plain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem);
@@ -1787,7 +1807,7 @@ int occupancy_blocks_per_sm(int B, int form, int block)
     if (form == FLR_FORM_WAVEFRONT)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront, block, smem);
     else if (form == FLR_FORM_WAVEFRONT_WARP)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront_warp<WM_RENDER>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront_warp<WM_RENDER, false>, block, smem);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_plain<true>, block, smem);
     return n > 0 ? n : 1;
@@ -1811,7 +1831,12 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
     if (form == FLR_FORM_WAVEFRONT)
         k_trace_wavefront<<<(unsigned)grid, block, smem, st>>>(S, R);
     else if (form == FLR_FORM_WAVEFRONT_WARP)
-        k_trace_wavefront_warp<WM_RENDER><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
+    {
+        if (S.mc > 0)
+            k_trace_wavefront_warp<WM_RENDER, true><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
+        else
+            k_trace_wavefront_warp<WM_RENDER, false><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
+    }
     else if (S.mc > 0 || S.sk > 0)
         k_trace_plain<true><<<(unsigned)grid, block, smem, st>>>(S, R);
     else
@@ -1862,17 +1887,16 @@ cudaError_t launch_adjoint_warp(const SceneDev &S, const RunDev &R, const AdjDev
     const cudaError_t ea = allow_smem(FLR_FORM_WAVEFRONT_WARP, smem);
     if (ea != cudaSuccess) return ea;
     int occ = 0;
+    void (*k)(SceneDev, RunDev, AdjDev);
     if (pass == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_wavefront_warp<WM_ADJ_WEIGHTS>, block, smem);
+        k = S.mc > 0 ? k_trace_wavefront_warp<WM_ADJ_WEIGHTS, true> : k_trace_wavefront_warp<WM_ADJ_WEIGHTS, false>;
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_wavefront_warp<WM_ADJ_GRAD>, block, smem);
+        k = S.mc > 0 ? k_trace_wavefront_warp<WM_ADJ_GRAD, true> : k_trace_wavefront_warp<WM_ADJ_GRAD, false>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, smem);
     if (occ < 1) occ = 1;
     if (blocks_per_sm <= 0 || blocks_per_sm > occ) blocks_per_sm = occ;
     const long long grid = (long long)num_sms() * blocks_per_sm;
-    if (pass == 1)
-        k_trace_wavefront_warp<WM_ADJ_WEIGHTS><<<(unsigned)grid, block, smem, st>>>(S, R, A);
-    else
-        k_trace_wavefront_warp<WM_ADJ_GRAD><<<(unsigned)grid, block, smem, st>>>(S, R, A);
+    k<<<(unsigned)grid, block, smem, st>>>(S, R, A);
     return cudaGetLastError();
 }
 
