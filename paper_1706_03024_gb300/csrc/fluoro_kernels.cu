@@ -469,7 +469,8 @@ __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (
 // Lambertian vertex with normal sign*e_axis (lamb = 2*axis + (sign > 0)), intensity w cos/pi.
 // Transmittance: analytic in homogeneous media, else ratio tracking
 //   T = prod_k (1 - sigma_t(x_k)/sigma_bar) over majorant-distributed points x_k,
-// with roulette (survival 1/2) once the estimate falls below RT_RR_THRESHOLD.
+// with roulette once the estimate falls below RT_RR_THRESHOLD (survival T / RT_RR_THRESHOLD; in the
+// adjoint replay survival 1/2 below RT_RR_ADJ_THRESHOLD).
 // Geometry of a connection: direction to the sensor, distance to leave the box, intensity x
 // importance (f * geom) and the film pixel; ok = false when the vertex does not see the sensor.
 struct ConnGeom {
@@ -539,14 +540,14 @@ __device__ __forceinline__ ConnGeom connect_geom(const SceneDev &S, const Smem &
 
 // Transmittance estimate along the connection (Eq. 6): analytic in homogeneous media, else ratio
 // tracking T = prod_k (1 - sigma_t(x_k)/sigma_bar) over majorant-distributed points with roulette
-// (survival 1/2) below RT_RR_THRESHOLD. The sink G sees every ratio-tracking point (the adjoint
+// below RT_RR_THRESHOLD (ADJ: the adjoint's rule). The sink G sees every ratio-tracking point (the adjoint
 // accumulates d log T there); NoSink is the forward's.
 struct NoSink {
     __device__ __forceinline__ void point(float3, int, float, float) const {}
     __device__ __forceinline__ void homogeneous(float) const {}
 };
 
-template <class G, bool OPT = true, bool MC = OPT>
+template <class G, bool OPT = true, bool MC = OPT, bool ADJ = false>
 __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &R, const Smem &sm,
                                                float3 x, float3 dir, float tl, int b, uint64_t pid,
                                                uint32_t step, RegCnt &rc, const G &sink)
@@ -579,13 +580,13 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
             const float st = sigma_t_at(m, p, b);
             sink.point(p, b, st, sbc);
             T *= fmaxf(0.0f, 1.0f - st / sbc);
-            if (T < RT_RR_THRESHOLD) {
+            if (T < (ADJ ? RT_RR_ADJ_THRESHOLD : RT_RR_THRESHOLD)) {
                 if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
                 const uint32_t q2 = j & 3u;
                 const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
                 ++j;
-                if (u2 < 0.5f) {
-                    T *= 2.0f;
+                if (ADJ ? u2 < 0.5f : u2 * RT_RR_THRESHOLD < T) {
+                    T = ADJ ? 2.0f * T : RT_RR_THRESHOLD;
                 } else {
                     T = 0.0f;
                     break;
@@ -623,13 +624,13 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
                 rc.cell_walks++;
             }
         }
-        if (T < RT_RR_THRESHOLD) {
+        if (T < (ADJ ? RT_RR_ADJ_THRESHOLD : RT_RR_THRESHOLD)) {
             if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
             const uint32_t q2 = j & 3u;
             const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
             ++j;
-            if (u2 < 0.5f) {
-                T *= 2.0f;
+            if (ADJ ? u2 < 0.5f : u2 * RT_RR_THRESHOLD < T) {
+                T = ADJ ? 2.0f * T : RT_RR_THRESHOLD;
             } else {
                 T = 0.0f;
                 break;
@@ -1172,8 +1173,8 @@ __device__ __forceinline__ float adjoint_weight(const SceneDev &S, const RunDev 
 {
     const ConnGeom g = connect_geom(S, sm, c.x, c.lamb);
     if (!g.ok) return 0.0f;
-    const float T = transmittance<NoSink, true, MC>(S, R, sm, c.x, g.dir, g.tl, c.bin, c.pid, c.step,
-                                                    rc, NoSink{});
+    const float T = transmittance<NoSink, true, MC, true>(S, R, sm, c.x, g.dir, g.tl, c.bin, c.pid,
+                                                          c.step, rc, NoSink{});
     const float val = c.w * g.gf * T * R.film_scale;
     if (!(val > 0.0f)) return 0.0f;
     return __ldg(&A.adj[(size_t)g.pix * S.B + c.bin]) * val;
@@ -1185,7 +1186,8 @@ __device__ __forceinline__ void adjoint_march(const SceneDev &S, const RunDev &R
 {
     const ConnGeom g = connect_geom(S, sm, c.x, c.lamb);
     if (!g.ok) return;
-    transmittance(S, R, sm, c.x, g.dir, g.tl, c.bin, c.pid, c.step, rc, AdjSink{S, sm, A, a, gsig});
+    transmittance<AdjSink, true, true, true>(S, R, sm, c.x, g.dir, g.tl, c.bin, c.pid, c.step, rc,
+                                             AdjSink{S, sm, A, a, gsig});
 }
 
 __global__ void __launch_bounds__(256, 1) k_adjoint(SceneDev S, RunDev R, AdjDev A)
@@ -1332,11 +1334,11 @@ __device__ __forceinline__ bool march_begin(const SceneDev &S, const RunDev &R, 
         if (MODE == WM_ADJ_GRAD) {
             const AdjSink sink{S, sm, A, w, &gsig};
             if (closed) transmittance_closed(S, sm, x, g.tl, b, sink);
-            else transmittance<AdjSink, true, MC>(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, sink);
+            else transmittance<AdjSink, true, MC, true>(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, sink);
         } else {
             mc.T = closed ? transmittance_closed(S, sm, x, g.tl, b, NoSink{})
-                          : transmittance<NoSink, true, MC>(S, R, sm, x, g.dir, g.tl, b, pid, step, rc,
-                                                            NoSink{});
+                          : transmittance<NoSink, true, MC, MODE != WM_RENDER>(
+                                S, R, sm, x, g.dir, g.tl, b, pid, step, rc, NoSink{});
             march_deposit<MODE>(S, R, A, mc);
         }
         return false;
@@ -1391,10 +1393,11 @@ __device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, c
             rc.cell_walks++;
         }
     }
-    if (mc.T < RT_RR_THRESHOLD) {
+    constexpr bool ADJ = MODE != WM_RENDER;
+    if (mc.T < (ADJ ? RT_RR_ADJ_THRESHOLD : RT_RR_THRESHOLD)) {
         const float u2 = march_uniform(R, mc);
-        if (u2 < 0.5f) {
-            mc.T *= 2.0f;
+        if (ADJ ? u2 < 0.5f : u2 * RT_RR_THRESHOLD < mc.T) {
+            mc.T = ADJ ? 2.0f * mc.T : RT_RR_THRESHOLD;
         } else {
             return false;
         }
