@@ -47,6 +47,8 @@ struct flr_ctx {
     size_t adj_ak_cap = 0;
     float *d_adj_ovf = nullptr;
     size_t adj_ovf_cap = 0;
+    unsigned long long *d_adj_tal = nullptr;  // the replays' tallies (written, never read)
+    size_t adj_tal_cap = 0;
     uint64_t paths_since_clear = 0;
     std::vector<float> h_tables;
     // local majorants of the current medium (built on demand for one cell size)
@@ -459,6 +461,7 @@ void flr_destroy(flr_ctx *ctx)
     cudaFree(ctx->d_scratch);
     cudaFree(ctx->d_adj_ak);
     cudaFree(ctx->d_adj_ovf);
+    cudaFree(ctx->d_adj_tal);
     cudaFree(ctx->d_grid);
     cudaFree(ctx->d_mc_c);
     cudaFree(ctx->d_mc_s);
@@ -873,6 +876,10 @@ int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float 
     rc = grow(ctx, (void **)&ctx->d_adj_ovf, &ctx->adj_ovf_cap, (size_t)chunk, sizeof(float),
               "adjoint contributions");
     if (rc != FLR_OK) return rc;
+    rc = grow(ctx, (void **)&ctx->d_adj_tal, &ctx->adj_tal_cap, (size_t)tal_size(FLR_MAX_BINS),
+              sizeof(unsigned long long), "adjoint tallies");
+    if (rc != FLR_OK) return rc;
+    R.tallies = ctx->d_adj_tal;
     A.ak = ctx->d_adj_ak;
     A.ovf = ctx->d_adj_ovf;
     A.K = ADJ_K;

@@ -63,8 +63,9 @@ __device__ __forceinline__ U4 draw(uint32_t seed, uint32_t medium, uint64_t pid,
 // Shared-memory view: spectral tables, block tallies, block counters.
 struct Smem {
     const float *sig_a, *cdf, *maj, *qy;
-    unsigned long long *tal;
+    unsigned long long *tal;   // shared memory, or the launch's global tallies (tal_global)
     unsigned long long *cnt;
+    bool tal_global;
 };
 
 // Frequent counters live in registers; the rest go straight to shared memory.
@@ -898,12 +899,16 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
 // Block prologue / epilogue: stage tables, zero and flush block tallies and counters.
 struct SmemLayout {
     int tab_floats, tal_off_bytes, cnt_off_bytes, queue_off_bytes, total_bytes;
+    bool tal_global;   // tallies go straight to global memory (their shared space holds queues)
 };
 
 // Per-warp connection queue of the warp-regrouped form: capacity and drain threshold. A drain starts
-// once WQ_DRAIN records wait; one tracking round adds at most 32, so the queue never wraps.
-constexpr int WQ_CAP = 128;
-constexpr int WQ_DRAIN = 96;
+// once WQ_DRAIN records wait; one tracking round adds at most 32, so the queue never wraps. Longer
+// queues drain less often and amortise each drain's tail: 416 records of 32 B per warp fill the
+// shared memory of two 256-thread blocks per SM (measured on the Cornell box: 128 -> 256 -> 320
+// records gave 26.0 -> 24.0 -> 23.6 ms per step).
+constexpr int WQ_CAP = 416;
+constexpr int WQ_DRAIN = 384;
 static_assert(WQ_DRAIN + 31 < WQ_CAP, "warp queue overflow");
 
 __host__ __device__ inline SmemLayout smem_layout(int B, int form, int block)
@@ -912,7 +917,8 @@ __host__ __device__ inline SmemLayout smem_layout(int B, int form, int block)
     L.tab_floats = tab_size(B);
     int off = ((L.tab_floats * 4 + 15) / 16) * 16;
     L.tal_off_bytes = off;
-    off += tal_size(B) * 8;
+    L.tal_global = form == FLR_FORM_WAVEFRONT_WARP;
+    if (!L.tal_global) off += tal_size(B) * 8;
     L.cnt_off_bytes = off;
     off += FLR_NCOUNTERS * 8;
     off = ((off + 15) / 16) * 16;
@@ -923,12 +929,15 @@ __host__ __device__ inline SmemLayout smem_layout(int B, int form, int block)
     return L;
 }
 
-__device__ __forceinline__ Smem block_prologue(const SceneDev &S, unsigned char *raw, const SmemLayout &L)
+__device__ __forceinline__ Smem block_prologue(const SceneDev &S, unsigned char *raw, const SmemLayout &L,
+                                               unsigned long long *global_tal)
 {
     float *tab = reinterpret_cast<float *>(raw);
     for (int i = threadIdx.x; i < L.tab_floats; i += blockDim.x) tab[i] = S.tables[i];
-    unsigned long long *tal = reinterpret_cast<unsigned long long *>(raw + L.tal_off_bytes);
-    for (int i = threadIdx.x; i < tal_size(S.B); i += blockDim.x) tal[i] = 0ull;
+    unsigned long long *tal = L.tal_global ? global_tal
+                                           : reinterpret_cast<unsigned long long *>(raw + L.tal_off_bytes);
+    if (!L.tal_global)
+        for (int i = threadIdx.x; i < tal_size(S.B); i += blockDim.x) tal[i] = 0ull;
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(raw + L.cnt_off_bytes);
     for (int i = threadIdx.x; i < FLR_NCOUNTERS; i += blockDim.x) cnt[i] = 0ull;
     __syncthreads();
@@ -939,6 +948,7 @@ __device__ __forceinline__ Smem block_prologue(const SceneDev &S, unsigned char 
     sm.qy = tab + tab_qy(S.B);
     sm.tal = tal;
     sm.cnt = cnt;
+    sm.tal_global = L.tal_global;
     return sm;
 }
 
@@ -958,8 +968,9 @@ __device__ __forceinline__ void block_epilogue(const SceneDev &S, const RunDev &
         if ((threadIdx.x & 31) == 0 && v) atomicAdd(&sm.cnt[idx[i]], v);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < tal_size(S.B); i += blockDim.x)
-        if (sm.tal[i]) atomicAdd(&R.tallies[i], sm.tal[i]);
+    if (!sm.tal_global)
+        for (int i = threadIdx.x; i < tal_size(S.B); i += blockDim.x)
+            if (sm.tal[i]) atomicAdd(&R.tallies[i], sm.tal[i]);
     for (int i = threadIdx.x; i < FLR_NCOUNTERS; i += blockDim.x)
         if (sm.cnt[i]) atomicAdd(&R.counters[i], sm.cnt[i]);
 }
@@ -971,7 +982,7 @@ __global__ void __launch_bounds__(256) k_trace_plain(SceneDev S, RunDev R)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
-    const Smem sm = block_prologue(S, smem_raw, L);
+    const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
     const MedS_<OPT> m{S, sm};
     RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -1046,7 +1057,7 @@ __global__ void __launch_bounds__(256) k_trace_wavefront(SceneDev S, RunDev R)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT, blockDim.x);
-    const Smem sm = block_prologue(S, smem_raw, L);
+    const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
     const int cap = 2 * blockDim.x;
     Queue q;
     {
@@ -1194,7 +1205,7 @@ __global__ void __launch_bounds__(256, 1) k_adjoint(SceneDev S, RunDev R, AdjDev
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
-    const Smem sm = block_prologue(S, smem_raw, L);
+    const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
     const MedS m{S, sm};
     RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
     float gsig = 0.0f;
@@ -1410,7 +1421,7 @@ __global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, Run
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT_WARP, blockDim.x);
-    const Smem sm = block_prologue(S, smem_raw, L);
+    const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
     const MedS_<true, MC> m{S, sm};
     constexpr unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1501,15 +1512,15 @@ __global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, Run
         const int avail = q.head_tail[1];
         if (avail >= WQ_DRAIN || (!any && avail > 0)) {
             // pull-based drain of all `avail` records
-            // Lanes claim new records only every fourth iteration: a march draws a Philox block
-            // every fourth step, so claims in step keep the draws of all lanes in the same
-            // iterations instead of spreading them over four divergent ones, and the set-up of
-            // new marches runs for several lanes at once.
+            // Lanes claim new records only every second iteration: claims in step keep the lanes'
+            // Philox draws (one per four march steps) in two phases instead of four, and the
+            // set-up of new marches runs for several lanes at once (measured: every iteration
+            // 25.8, every second 25.2, every fourth 26.0 ms per step with 128-record queues).
             March mc;
             bool active = false;
             int claimed = 0;
             for (uint32_t iter = 0;; ++iter) {
-                const unsigned need = (iter & 3u) == 0u ? __ballot_sync(FULL, !active) : 0u;
+                const unsigned need = (iter & 1u) == 0u ? __ballot_sync(FULL, !active) : 0u;
                 if (need != 0u && !active) {
                     const int k = claimed + __popc(need & lower);
                     if (k < avail) {
