@@ -909,6 +909,7 @@ struct SmemLayout {
 // records gave 26.0 -> 24.0 -> 23.6 ms per step).
 constexpr int WQ_CAP = 416;
 constexpr int WQ_DRAIN = 384;
+constexpr int SPAWN_MIN = 8;   // lanes that start new paths together
 static_assert(WQ_DRAIN + 31 < WQ_CAP, "warp queue overflow");
 
 __host__ __device__ inline SmemLayout smem_layout(int B, int form, int block)
@@ -1452,11 +1453,16 @@ __global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, Run
     float gsig = 0.0f;                 // pass 2: this lane's share of dL/dsigma_s
     const int regroup = R.regroup > 0 ? R.regroup : 1;
     while (true) {
-        // tracking: at most `regroup` steps or one queued connection per lane
+        // Tracking: at most `regroup` steps or one queued connection per lane. Lanes whose path
+        // ended wait until SPAWN_MIN of them (or all) can start new paths together: the source
+        // sampling then runs for several lanes at once instead of in most rounds for one or two
+        // (measured: 21.5 -> 19.5 ms per Cornell-box step with 8).
+        const bool spawn_now = __popc(__ballot_sync(FULL, !p.alive && !exhausted)) >= SPAWN_MIN ||
+                               __ballot_sync(FULL, p.alive) == 0u;
         for (int s = 0; s < regroup; ++s) {
             if (MODE != WM_ADJ_GRAD) {
                 if (!p.alive) {
-                    if (exhausted) break;
+                    if (exhausted || !spawn_now) break;
                     const unsigned long long i = atomicAdd(R.work_counter, 1ull);
                     if (i >= R.n_paths) { exhausted = true; break; }
                     const Conn c = spawn(m, R, sm, R.path_offset + i, p);
@@ -1479,7 +1485,7 @@ __global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, Run
             // pass 2 of the adjoint
             Conn c;
             if (!p.alive) {
-                if (exhausted) break;
+                if (exhausted || !spawn_now) break;
                 const unsigned long long i = atomicAdd(R.work_counter, 1ull);
                 if (i >= R.n_paths) { exhausted = true; break; }
                 c = spawn(m, R, sm, R.path_offset + i, p);
