@@ -162,6 +162,7 @@ void build_medium_tables(const flr_ctx *ctx, const flr_medium &m, const float *c
     float *sig = out + tab_sig_a(B);
     float *cdf = out + tab_cdf(B);
     float *maj = out + tab_majorant(B);
+    float *imaj = out + tab_inv_majorant(B);
     float *qy = out + tab_qy(B);
     for (int b = 0; b < B; ++b) {
         double mj = (double)smax * ((double)m.sigma_s + (double)m.sigma_a0);
@@ -172,6 +173,7 @@ void build_medium_tables(const flr_ctx *ctx, const flr_medium &m, const float *c
             mj += s * (double)cmax[d];
         }
         maj[b] = mj > 0.0 ? round_up_f32(mj * (1.0 + 1e-6) * (1.0 + margin)) : 0.0f;
+        imaj[b] = maj[b] > 0.0f ? (float)(1.0 / (double)maj[b]) : 0.0f;
     }
     for (int d = 0; d < m.n_dyes; ++d) {
         const int id = m.dye_ids[d];
@@ -309,6 +311,8 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film, int macro_cell = 0, in
             const double tx = ty * (double)c.width / (double)c.height;
             S.tan_x = (float)tx;
             S.tan_y = (float)ty;
+            S.inv_tan_x = (float)(1.0 / tx);
+            S.inv_tan_y = (float)(1.0 / ty);
             S.inv_A_pix = (float)((double)c.width * c.height / ((2.0 * tx) * (2.0 * ty)));
         }
     }

@@ -24,6 +24,7 @@ constexpr float RT_RR_ADJ_THRESHOLD = 1e-3f;
 //                    dyes of one bin are one 16-byte vector
 //   cdf[MAXD][B]     emission CDF, fp64-built and rounded, last = 1      (Eq. 10)
 //   majorant[B]      sigma_bar(lambda_b) >= sigma_t(x, lambda_b) for all x
+//   inv_majorant[B]  1 / sigma_bar(lambda_b) (0 where sigma_bar = 0)
 //   qy[MAXD]
 // The size is padded to a multiple of 4 floats so that consecutive media's tables stay 16-byte
 // aligned.
@@ -31,8 +32,9 @@ __host__ __device__ constexpr int tab_sig_a(int B) { return 0; }
 __host__ __device__ constexpr int tab_sig_a_at(int B, int d, int b) { return b * MAXD + d; }
 __host__ __device__ constexpr int tab_cdf(int B) { return MAXD * B; }
 __host__ __device__ constexpr int tab_majorant(int B) { return 2 * MAXD * B; }
-__host__ __device__ constexpr int tab_qy(int B) { return 2 * MAXD * B + B; }
-__host__ __device__ constexpr int tab_size(int B) { return (2 * MAXD * B + B + MAXD + 3) & ~3; }
+__host__ __device__ constexpr int tab_inv_majorant(int B) { return 2 * MAXD * B + B; }
+__host__ __device__ constexpr int tab_qy(int B) { return 2 * MAXD * B + 2 * B; }
+__host__ __device__ constexpr int tab_size(int B) { return (2 * MAXD * B + 2 * B + MAXD + 3) & ~3; }
 
 // Fixed-point tallies (u64, 2^-24 units of photon weight): face[2][6][B], absorbed[MAXD+1][B],
 // emitted[MAXD][B]. Integer sums make every launch form and thread order give identical bits.
@@ -67,6 +69,7 @@ struct SceneDev {
     int sensor_kind, W, H;
     float s_origin[3], s_U[3], s_V[3], s_view[3];  // ortho: U, V pre-divided by |U|^2, |V|^2
     float tan_x, tan_y, inv_A_pix;
+    float inv_tan_x, inv_tan_y;
     // local majorants (macro cells); mc == 0: one majorant per bin. sk > 0: empty-space leaps
     // after null collisions (global majorant) over the same cell grid
     int mc, sk;

@@ -62,7 +62,7 @@ __device__ __forceinline__ U4 draw(uint32_t seed, uint32_t medium, uint64_t pid,
 // ---------------------------------------------------------------------------------------------
 // Shared-memory view: spectral tables, block tallies, block counters.
 struct Smem {
-    const float *sig_a, *cdf, *maj, *qy;
+    const float *sig_a, *cdf, *maj, *inv_maj, *qy;
     unsigned long long *tal;   // shared memory, or the launch's global tallies (tal_global)
     unsigned long long *cnt;
     bool tal_global;
@@ -120,6 +120,7 @@ struct MedS_ {
     __device__ __forceinline__ float sig_a(int d, int b) const { return sm.sig_a[tab_sig_a_at(S.B, d, b)]; }
     __device__ __forceinline__ float4 sig_a4(int b) const { return reinterpret_cast<const float4 *>(sm.sig_a)[b]; }
     __device__ __forceinline__ float maj(int b) const { return sm.maj[b]; }
+    __device__ __forceinline__ float inv_maj(int b) const { return sm.inv_maj[b]; }
     __device__ __forceinline__ float qy(int d) const { return sm.qy[d]; }
     __device__ __forceinline__ const float *cdf(int d) const { return sm.cdf + d * S.B; }
     __device__ __forceinline__ void tally(int idx, float w) const { tally_add(sm, idx, w); }
@@ -184,6 +185,7 @@ struct MedB {
         return __ldg(reinterpret_cast<const float4 *>(tables() + tab_sig_a(B_)) + b);
     }
     __device__ __forceinline__ float maj(int b) const { return __ldg(tables() + tab_majorant(B_) + b); }
+    __device__ __forceinline__ float inv_maj(int b) const { return __ldg(tables() + tab_inv_majorant(B_) + b); }
     __device__ __forceinline__ float qy(int d) const { return __ldg(tables() + tab_qy(B_) + d); }
     __device__ __forceinline__ const float *cdf(int d) const { return tables() + tab_cdf(B_) + d * B_; }
     __device__ __forceinline__ void tally(int idx, float w) const
@@ -466,7 +468,7 @@ __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (
 // Geometry of a connection: direction to the sensor, distance to leave the box, intensity x
 // importance (f * geom) and the film pixel; ok = false when the vertex does not see the sensor.
 struct ConnGeom {
-    float3 dir;
+    float3 dir, idr;   // direction to the sensor and its componentwise inverse
     float tl, gf;
     int pix;
     bool ok;
@@ -496,8 +498,8 @@ __device__ __forceinline__ ConnGeom connect_geom(const SceneDev &S, const Smem &
         const float izf = __frcp_rn(zf);
         const float X = (vx * S.s_U[0] + vy * S.s_U[1] + vz * S.s_U[2]) * izf;
         const float Y = (vx * S.s_V[0] + vy * S.s_V[1] + vz * S.s_V[2]) * izf;
-        const float sx = 0.5f * (X * __frcp_rn(S.tan_x) + 1.0f);
-        const float sy = 0.5f * (Y * __frcp_rn(S.tan_y) + 1.0f);
+        const float sx = 0.5f * (X * S.inv_tan_x + 1.0f);
+        const float sy = 0.5f * (Y * S.inv_tan_y + 1.0f);
         if (!(sx >= 0.0f && sx < 1.0f && sy >= 0.0f && sy < 1.0f)) return g;
         px = min(__float2int_rd(sx * (float)S.W), S.W - 1);
         py = min(__float2int_rd(sy * (float)S.H), S.H - 1);
@@ -523,6 +525,7 @@ __device__ __forceinline__ ConnGeom connect_geom(const SceneDev &S, const Smem &
     if (S.wall_mask & (1 << face)) return g;
     if (S.sensor_kind == FLR_SENSOR_PINHOLE && tl * tl > r2) return g;
     g.dir = dir;
+    g.idr = idr;
     g.tl = tl;
     g.gf = f * geom;
     g.pix = py * S.W + px;
@@ -591,7 +594,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
         }
         return T;
     }
-    const float isb = __frcp_rn(sb);
+    const float isb = sm.inv_maj[b];
     float t = 0.0f;
     U4 blk = U4{0, 0, 0, 0};
     uint32_t j = 0;
@@ -761,7 +764,7 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
         tf = dda_advance(m, dd, p.bin, -__logf(1.0f - b0.a), te, sb, rc.cell_walks);
     } else {
         sb = m.maj(p.bin);
-        tf = sb > 0.0f ? -__logf(1.0f - b0.a) * __frcp_rn(sb) : FLT_MAX;
+        tf = sb > 0.0f ? -__logf(1.0f - b0.a) * m.inv_maj(p.bin) : FLT_MAX;
     }
     const uint32_t step = p.step;
     p.step++;
@@ -947,6 +950,7 @@ __device__ __forceinline__ Smem block_prologue(const SceneDev &S, unsigned char 
     sm.sig_a = tab + tab_sig_a(S.B);
     sm.cdf = tab + tab_cdf(S.B);
     sm.maj = tab + tab_majorant(S.B);
+    sm.inv_maj = tab + tab_inv_majorant(S.B);
     sm.qy = tab + tab_qy(S.B);
     sm.tal = tal;
     sm.cnt = cnt;
@@ -1272,7 +1276,7 @@ constexpr int WM_ADJ_GRAD = 2;
 constexpr int WQ_ORD_MAX = (1 << 21) - 1;   // connection ordinals carried by a queue record
 
 struct March {
-    float3 x, dir;
+    float3 x, dir, idir;
     float tl, t, T, isb, wg;   // wg: intensity x importance (render, pass 1) or a_k (pass 2)
     int b, pix, it, ord;
     uint32_t j, step;
@@ -1361,7 +1365,8 @@ __device__ __forceinline__ bool march_begin(const SceneDev &S, const RunDev &R, 
     mc.tl = g.tl;
     mc.t = 0.0f;
     mc.T = 1.0f;
-    mc.isb = __frcp_rn(sb);
+    mc.isb = sm.inv_maj[b];
+    mc.idir = g.idr;
     mc.j = 0;
     mc.it = 0;
     mc.step = step;
@@ -1400,7 +1405,7 @@ __device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, c
     if (MODE == WM_ADJ_GRAD) AdjSink{S, sm, A, mc.wg, &gsig}.point(p, mc.b, st, sm.maj[mc.b]);
     mc.T *= fmaxf(0.0f, 1.0f - st * mc.isb);
     if (S.sk > 0 && st == 0.0f) {
-        const float tl2 = empty_cube_exit(m, p, mc.dir, inv_dir(mc.dir));
+        const float tl2 = empty_cube_exit(m, p, mc.dir, mc.idir);
         if (tl2 > 0.0f) {
             mc.t += tl2;
             rc.cell_walks++;
@@ -1589,7 +1594,7 @@ __global__ void __launch_bounds__(256) k_trace_batch(BatchDev Bt, RunDev R)
     for (int i = threadIdx.x; i < FLR_NCOUNTERS; i += blockDim.x) s_cnt[i] = 0ull;
     __syncthreads();
     Smem sm;
-    sm.sig_a = sm.cdf = sm.maj = sm.qy = nullptr;
+    sm.sig_a = sm.cdf = sm.maj = sm.inv_maj = sm.qy = nullptr;
     sm.tal = nullptr;
     sm.cnt = s_cnt;
     RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
