@@ -457,10 +457,10 @@ __device__ __forceinline__ float empty_cube_exit(const M &m, float3 x, float3 w,
 // Cosine-weighted about sign * e_axis, tangents e_{axis+1}, e_{axis+2}.
 __device__ __forceinline__ float3 cosine_dir(float u1, float u2, int axis, float sign)
 {
-    const float r = sqrtf(u1);
+    const float r = sqrt_approx(u1);
     float s, c;
     __sincosf(TWO_PI * u2, &s, &c);
-    const float zl = sqrtf(fmaxf(0.0f, 1.0f - u1));
+    const float zl = sqrt_approx(fmaxf(0.0f, 1.0f - u1));
     const float a = sign * zl, bx = r * c, by = r * s;
     // component axis = a, (axis+1)%3 = bx, (axis+2)%3 = by
     if (axis == 0) return make_float3(a, bx, by);
