@@ -700,6 +700,7 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     R.path_offset = p->path_offset;
     R.seed = p->seed;
     R.medium_id = p->medium_id;
+    set_round_keys(R);
     R.n_rr = p->n_rr;
     R.max_inelastic = p->max_inelastic;
     R.analog = p->analog;
@@ -854,6 +855,7 @@ int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float 
     R.path_offset = p->path_offset;
     R.seed = p->seed;
     R.medium_id = p->medium_id;
+    set_round_keys(R);
     R.n_rr = p->n_rr;
     R.max_inelastic = p->max_inelastic;
     R.analog = p->analog;
@@ -1066,6 +1068,7 @@ int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const 
     R.path_offset = p->path_offset;
     R.seed = p->seed;
     R.medium_id = p->medium_id;
+    set_round_keys(R);
     R.n_rr = p->n_rr;
     R.max_inelastic = p->max_inelastic;
     R.analog = p->analog;
@@ -1274,6 +1277,7 @@ extern "C" int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins
         R.path_offset = p->path_offset;
         R.seed = p->seed;
         R.medium_id = p->medium_id;
+        set_round_keys(R);
         R.n_rr = p->n_rr;
         R.max_inelastic = p->max_inelastic;
         R.analog = p->analog;

@@ -96,7 +96,21 @@ struct RunDev {
     int *error_word;
     unsigned long long *work_counter;  // dynamic path distribution (wavefront form)
     int regroup;                       // wavefront: tracking steps between connection flushes
+    uint32_t rk[20];                   // Philox round keys of (seed, medium_id): k0[10], k1[10]
 };
+
+// Fills RunDev::rk with the Philox4x32-10 key schedule of (seed, medium_id): round r uses
+// k0 = seed + r * 0x9E3779B9 and k1 = medium_id + r * 0xBB67AE85 (mod 2^32).
+inline void set_round_keys(RunDev &R)
+{
+    uint32_t k0 = R.seed, k1 = R.medium_id;
+    for (int r = 0; r < 10; ++r) {
+        R.rk[r] = k0;
+        R.rk[10 + r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
 
 // One medium of a batched launch (global memory; read per lane through the read-only path).
 constexpr int BATCH_MAX_LINES = 8;

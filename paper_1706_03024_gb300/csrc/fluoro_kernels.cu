@@ -52,11 +52,27 @@ __device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * (1.0
 
 struct U4 { float a, b, c, d; };
 
+
 __device__ __forceinline__ U4 draw(uint32_t seed, uint32_t medium, uint64_t pid, uint32_t step,
                                    uint32_t slot)
 {
     const uint4 o = philox(make_uint4((uint32_t)pid, step, slot, (uint32_t)(pid >> 32)), seed, medium);
     return U4{u24(o.x), u24(o.y), u24(o.z), u24(o.w)};
+}
+
+// The same Philox4x32-10 block with the launch's key schedule read from the kernel parameters
+// (RunDev::rk, filled by set_round_keys): the round keys of a single-scene launch are constants, so
+// the rounds take them as operands instead of recomputing them for every block.
+__device__ __forceinline__ U4 draw_rk(const RunDev &R, uint64_t pid, uint32_t step, uint32_t slot)
+{
+    uint4 c = make_uint4((uint32_t)pid, step, slot, (uint32_t)(pid >> 32));
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ R.rk[r], lo1, hi0 ^ c.w ^ R.rk[10 + r], lo0);
+    }
+    return U4{u24(c.x), u24(c.y), u24(c.z), u24(c.w)};
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -129,6 +145,10 @@ struct MedS_ {
     __device__ __forceinline__ float em_cdf(int k) const { return S.em_cdf[k]; }
     __device__ __forceinline__ const EmitterDev &em(int k) const { return S.em[k]; }
     __device__ __forceinline__ uint32_t key1(const RunDev &R) const { return R.medium_id; }
+    __device__ __forceinline__ U4 rng(const RunDev &R, uint64_t pid, uint32_t step, uint32_t slot) const
+    {
+        return draw_rk(R, pid, step, slot);
+    }
     __device__ __forceinline__ bool macro() const { return OPT && MC && S.mc > 0; }
     __device__ __forceinline__ float margin() const { return S.maj_margin; }
     __device__ __forceinline__ int mc_dims(int k) const { return S.mc_dims[k]; }
@@ -199,6 +219,10 @@ struct MedB {
     __device__ __forceinline__ float em_cdf(int k) const { return __ldg(&md->em_cdf[k]); }
     __device__ __forceinline__ const EmitterDev &em(int k) const { return md->em[k]; }
     __device__ __forceinline__ uint32_t key1(const RunDev &) const { return __ldg(&md->key1); }
+    __device__ __forceinline__ U4 rng(const RunDev &R, uint64_t pid, uint32_t step, uint32_t slot) const
+    {
+        return draw(R.seed, key1(R), pid, step, slot);
+    }
     __device__ __forceinline__ bool macro() const { return false; }
     __device__ __forceinline__ float margin() const { return 1.0f; }
     __device__ __forceinline__ int mc_dims(int) const { return 1; }
@@ -575,7 +599,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
         uint32_t j = 0;
         int it = 0;
         for (; it < MAX_CONNECT_STEPS; ++it) {
-            if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
+            if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (j >> 2));
             const uint32_t q = j & 3u;
             const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
             ++j;
@@ -588,7 +612,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
             sink.point(p, b, st, sbc);
             T *= fmaxf(0.0f, 1.0f - st / sbc);
             if (T < (ADJ ? RT_RR_ADJ_THRESHOLD : RT_RR_THRESHOLD)) {
-                if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
+                if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (j >> 2));
                 const uint32_t q2 = j & 3u;
                 const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
                 ++j;
@@ -612,7 +636,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
     uint32_t j = 0;
     int it = 0;
     for (; it < MAX_CONNECT_STEPS; ++it) {
-        if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
+        if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (j >> 2));
         const uint32_t q = j & 3u;
         const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
         ++j;
@@ -632,7 +656,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
             }
         }
         if (T < (ADJ ? RT_RR_ADJ_THRESHOLD : RT_RR_THRESHOLD)) {
-            if ((j & 3u) == 0u) blk = draw(R.seed, R.medium_id, pid, step, 2u + (j >> 2));
+            if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (j >> 2));
             const uint32_t q2 = j & 3u;
             const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
             ++j;
@@ -710,8 +734,7 @@ __device__ __forceinline__ Conn spawn(const M &m, const RunDev &R, const Smem &s
                                       Path &p)
 {
     cnt_add(sm, FLR_C_PATHS);
-    const uint32_t key1 = m.key1(R);
-    const U4 s0 = draw(R.seed, key1, pid, STEP_SPAWN, 0u);
+    const U4 s0 = m.rng(R, pid, STEP_SPAWN, 0u);
     int k = 0;
     const int ne = m.n_emitters();
     while (k < ne - 1 && !(m.em_cdf(k) > s0.a)) ++k;
@@ -730,7 +753,7 @@ __device__ __forceinline__ Conn spawn(const M &m, const RunDev &R, const Smem &s
     Conn c;
     c.valid = false;
     if (e.kind == FLR_SOURCE_LAMBERTIAN) {
-        const U4 s1 = draw(R.seed, key1, pid, STEP_SPAWN, 1u);
+        const U4 s1 = m.rng(R, pid, STEP_SPAWN, 1u);
         p.w = cosine_dir(s0.d, s1.a, e.axis, e.sign);
         if (m.sensor()) {
             c = Conn{p.x, p.wt, p.bin, 2 * e.axis + (e.sign > 0.0f ? 1 : 0), pid, STEP_SPAWN, true};
@@ -762,11 +785,10 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
         return c;
     }
     rc.steps++;
-    const uint32_t key1 = m.key1(R);
-    const U4 b0 = draw(R.seed, key1, p.pid, p.step, 0u);
+    const U4 b0 = m.rng(R, p.pid, p.step, 0u);
     // The second block serves real events and wall bounces only, but some lane of a warp nearly
     // always needs it: drawing it here, beside the first, overlaps the two Philox chains.
-    const U4 b1 = draw(R.seed, key1, p.pid, p.step, 1u);
+    const U4 b1 = m.rng(R, p.pid, p.step, 1u);
     int face;
     const float te = exit_distance(m, p.x, p.w, p.iw, face);
     float sb, tf;
@@ -1387,7 +1409,7 @@ __device__ __forceinline__ bool march_begin(const SceneDev &S, const RunDev &R, 
 
 __device__ __forceinline__ float march_uniform(const RunDev &R, March &mc)
 {
-    if ((mc.j & 3u) == 0u) mc.blk = draw(R.seed, R.medium_id, mc.pid, mc.step, 2u + (mc.j >> 2));
+    if ((mc.j & 3u) == 0u) mc.blk = draw_rk(R, mc.pid, mc.step, 2u + (mc.j >> 2));
     const uint32_t q = mc.j & 3u;
     ++mc.j;
     return q == 0 ? mc.blk.a : (q == 1 ? mc.blk.b : (q == 2 ? mc.blk.c : mc.blk.d));
