@@ -4,6 +4,6 @@ TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and bench.py's CPU-bas
 reference legs are the only callers. The product path (paper_1706_03024_gb300) never imports it.
 """
 from .oracle import (  # noqa: F401
-    COUNTER_NAMES, adjoint, build, lib, optical_depth, majorant, philox, render, sample_emission, iso_dir,
-    cosine_dir,
+    COUNTER_NAMES, adjoint, build, lib, optical_depth, majorant, philox, render, render_camera,
+    sample_emission, iso_dir, cosine_dir,
 )

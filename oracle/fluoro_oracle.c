@@ -23,6 +23,9 @@
  *     vertex intensity x transmittance x sensor importance.
  * The transmittance of a connection is the exact line integral of the piecewise-constant
  * extinction (Eq. 6), not an estimate.
+ * paper_mode restricts the light tracer to the paper's single-inelastic model (Sec. 4.1), and
+ * or_render_camera evaluates that model with the paper's camera-side estimator (Eq. 12), so the
+ * two can be checked against each other.
  *
  * Pinned by tests/test_oracle_pins.py against closed forms (Beer-Lambert, uncollided
  * transmission, Chandrasekhar H-function reflectance, thin-dye emission spectrum, slab
@@ -124,6 +127,11 @@ typedef struct {
      * of skip_cell^3-voxel cells around it that holds no matter and restart the free flight at its
      * boundary (memoryless: every tentative collision inside would be a null) */
     int skip_cell;
+    /* 1: the paper's single-inelastic model (Sec. 4.1): excitation light reaches a dye only
+     * uncollided (a scattering or wall bounce before the first emission ends the path), a second
+     * dye absorption ends the path (V_f of Eq. 9), and only vertices after the emission connect
+     * to the sensor (the film holds fluorescence only). */
+    int paper_mode;
 } or_params;
 
 typedef struct {
@@ -849,7 +857,7 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
         normal_axis(em->dir, &ax, &sg);
         cosine_dir(S0.u[3], S1.u[0], ax, sg, w);
         vtx_kind vk = { 1, ax, sg };
-        connect_sensor(s, t, x, bin, wt, vk, film, cnt, A);
+        if (!p->paper_mode) connect_sensor(s, t, x, bin, wt, vk, film, cnt, A);
     } else {
         for (int k = 0; k < 3; ++k) w[k] = em->dir[k];
     }
@@ -873,7 +881,9 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
         if (tf >= te) {
             for (int k = 0; k < 3; ++k) x[k] += te * w[k];
             if (s->wall_mask & (1 << face)) {
-                /* Lambertian wall: a real event */
+                /* Lambertian wall: a real event (in paper mode, excitation light reflected by a
+                 * wall before any emission is dropped) */
+                if (p->paper_mode && !fl) { cnt[OC_VF_REJECTED]++; break; }
                 if (n_events == p->max_events) { cnt[OC_CAP_HITS]++; break; }
                 n_events++;
                 cnt[OC_EVENTS]++;
@@ -958,13 +968,17 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
         }
         if (ev < 0) {
             cnt[OC_SCATTERS]++;
+            if (p->paper_mode && !fl) { cnt[OC_VF_REJECTED]++; break; }  /* excitation scattering */
             iso_dir(B0.u[3], B1.u[0], w);
             vtx_kind vk = { 0, 0, 0.0 };
             connect_sensor(s, t, x, bin, wt * W, vk, film, cnt, A);
         } else if (ev < s->n_dyes) {
             cnt[OC_DYE_ABSORPTIONS]++;
             lt->absorbed[ev][bin] += wt * W;
-            if (p->max_inelastic >= 0 && n_inel >= p->max_inelastic) { cnt[OC_VF_REJECTED]++; break; }
+            if ((p->max_inelastic >= 0 && n_inel >= p->max_inelastic) || (p->paper_mode && n_inel >= 1)) {
+                cnt[OC_VF_REJECTED]++;
+                break;
+            }
             if (p->analog) {
                 if (!(B1.u[3] < t->qy[ev])) { cnt[OC_ABSORBED_DEAD]++; break; }
             } else {
@@ -1048,6 +1062,252 @@ int or_render(const or_scene *s, const or_params *p, or_result *r)
         for (size_t i = 0; i < n; ++i) r->film[i] *= inv;
     }
     free_macro(t);
+    free(t);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Camera-side estimator of the paper's single-inelastic model (Sec. 4.1-4.3; Eq. 9-12).
+ *
+ * A path starts at the sensor: a point uniform in its pixel (pixel = path id mod W*H), a film
+ * bin lambda drawn from the mixture (1/D) sum_d p_d of the dyes' emission pmfs, and the ray from
+ * the sensor through that point. It walks the medium at lambda by delta tracking (scattering
+ * isotropic, walls Lambertian); an absorption at lambda ends it (a dye absorption would be a
+ * second inelastic event, V_f = 0; Eq. 9). At every real collision x it samples the light
+ * (Eq. 12: a line in proportion to its power, p(lambda_x), and a point on it, p(x_n)) and adds
+ * the emission there, the excitation-to-emission term of Eq. 10 per unit volume,
+ *     J(x, lambda) = sum_d QY_d p_d(lambda) sigma_a,d(x, lambda_x) phi_x(x) / (4 pi),
+ * with phi_x the uncollided excitation fluence (L_r of Eq. 5 times G of Eq. 4, transmittance
+ * Eq. 6), divided by sigma_t(x, lambda) (a collision estimator: collisions occur with density
+ * sigma_t T, so the sum estimates the integral of T J along the walk). The film then holds the
+ * radiance of fluorescence averaged over each pixel, per unit of total source power: the same
+ * quantity as the light tracer's film in paper mode. Needs sigma_t(x, lambda) > 0 wherever a
+ * dye is (dyes dissolved in a scattering solvent, the paper's setting), and sources of non-zero
+ * area (a pencil beam has no fluence density a camera path could find).
+ * p_d(b) is the pmf realised by the fp32 CDF table (the one the light tracer samples). */
+#define CAM_SPAWN 0xFFFFFFFEu
+
+static double emission_pmf(const tables *t, int d, int b)
+{
+    return (double)t->cdf32[d][b] - (b > 0 ? (double)t->cdf32[d][b - 1] : 0.0);
+}
+
+/* Uncollided fluence at x at the chosen line's bin, per unit total source power (u[0] picks the
+ * line, u[1], u[2] the point on a Lambertian one). */
+static double excitation_fluence(const or_scene *s, const tables *t, const double x[3],
+                                 const double u[3], int *bin_x)
+{
+    int k = sample_emitter(t, s->n_emitters, u[0]);
+    const or_emitter *e = &s->emitters[k];
+    *bin_x = t->em_bin[k];
+    if (e->kind == 1) {
+        int ax; double sg;
+        normal_axis(e->dir, &ax, &sg);
+        double xn[3], v[3];
+        for (int i = 0; i < 3; ++i) {
+            xn[i] = e->origin[i] + u[1] * e->eu[i] + u[2] * e->ev[i];
+            v[i] = x[i] - xn[i];
+        }
+        double r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        if (!(r2 > 0.0)) return 0.0;
+        double r = sqrt(r2);
+        double cn = sg * v[ax] / r;
+        if (!(cn > 0.0)) return 0.0;
+        double w[3] = { v[0] / r, v[1] / r, v[2] / r };
+        return cn * exp(-optical_depth(s, t, xn, w, r, *bin_x)) / (OR_PI * r2);
+    }
+    /* collimated parallelogram: the point p of the source with x = p + l dir, l >= 0 */
+    double dn = sqrt(e->dir[0] * e->dir[0] + e->dir[1] * e->dir[1] + e->dir[2] * e->dir[2]);
+    double dir[3] = { e->dir[0] / dn, e->dir[1] / dn, e->dir[2] / dn };
+    double n[3] = { e->eu[1] * e->ev[2] - e->eu[2] * e->ev[1], e->eu[2] * e->ev[0] - e->eu[0] * e->ev[2],
+                    e->eu[0] * e->ev[1] - e->eu[1] * e->ev[0] };
+    double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+    double dnd = dir[0] * n[0] + dir[1] * n[1] + dir[2] * n[2];
+    if (!(nn > 0.0) || dnd == 0.0) return 0.0;
+    double xo[3] = { x[0] - e->origin[0], x[1] - e->origin[1], x[2] - e->origin[2] };
+    double l = (xo[0] * n[0] + xo[1] * n[1] + xo[2] * n[2]) / dnd;
+    if (!(l >= 0.0)) return 0.0;
+    double q[3] = { xo[0] - l * dir[0], xo[1] - l * dir[1], xo[2] - l * dir[2] };
+    /* q = a eu + b ev */
+    double c1[3] = { q[1] * e->ev[2] - q[2] * e->ev[1], q[2] * e->ev[0] - q[0] * e->ev[2], q[0] * e->ev[1] - q[1] * e->ev[0] };
+    double c2[3] = { e->eu[1] * q[2] - e->eu[2] * q[1], e->eu[2] * q[0] - e->eu[0] * q[2], e->eu[0] * q[1] - e->eu[1] * q[0] };
+    double a = (c1[0] * n[0] + c1[1] * n[1] + c1[2] * n[2]) / nn;
+    double b = (c2[0] * n[0] + c2[1] * n[1] + c2[2] * n[2]) / nn;
+    if (!(a >= 0.0 && a < 1.0 && b >= 0.0 && b < 1.0)) return 0.0;
+    double pnt[3] = { e->origin[0] + q[0], e->origin[1] + q[1], e->origin[2] + q[2] };
+    double a_perp = fabs(dnd);   /* |eu x ev| |cos(normal, dir)|: the beam's cross-section */
+    return exp(-optical_depth(s, t, pnt, dir, l, *bin_x)) / a_perp;
+}
+
+static void trace_camera(const or_scene *s, const tables *t, const or_params *p, uint64_t pid,
+                         double *film, double film_scale, uint64_t *cnt)
+{
+    const or_sensor *c = &s->sensor;
+    cnt[OC_PATHS]++;
+    const uint64_t npix = (uint64_t)c->width * (uint64_t)c->height;
+    const int pix = (int)(pid % npix);
+    const int px = pix % c->width, py = pix / c->width;
+    block4 S0 = rng_block(p->seed, p->medium_id, pid, CAM_SPAWN, 0);
+    const double fx = (px + S0.u[0]) / c->width, fy = (py + S0.u[1]) / c->height;
+    int dsel = (int)(S0.u[2] * s->n_dyes);
+    if (dsel > s->n_dyes - 1) dsel = s->n_dyes - 1;
+    const int bin = sample_emission_bin(t, dsel, S0.u[3]);
+    double pb = 0.0;
+    for (int d = 0; d < s->n_dyes; ++d) pb += emission_pmf(t, d, bin);
+    pb /= s->n_dyes;
+    if (!(pb > 0.0)) return;
+    double o[3], w[3];
+    if (c->kind == 1) {
+        double vn = sqrt(c->view[0] * c->view[0] + c->view[1] * c->view[1] + c->view[2] * c->view[2]);
+        for (int k = 0; k < 3; ++k) {
+            o[k] = c->origin[k] + fx * c->U[k] + fy * c->V[k];
+            w[k] = -c->view[k] / vn;
+        }
+    } else {
+        double X = (2.0 * fx - 1.0) * t->tan_half * t->aspect, Y = (2.0 * fy - 1.0) * t->tan_half;
+        double d[3], dl = 0.0;
+        for (int k = 0; k < 3; ++k) { d[k] = c->view[k] + X * c->U[k] + Y * c->V[k]; dl += d[k] * d[k]; }
+        dl = sqrt(dl);
+        for (int k = 0; k < 3; ++k) { o[k] = c->origin[k]; w[k] = d[k] / dl; }
+    }
+    /* enter the box; the entry face must be open (walls are opaque from outside) */
+    double t_in = -INFINITY, t_out = INFINITY;
+    int f_in = -1;
+    for (int k = 0; k < 3; ++k) {
+        if (w[k] == 0.0) {
+            if (o[k] < s->lo[k] || o[k] > s->hi[k]) return;
+            continue;
+        }
+        double ta = (s->lo[k] - o[k]) / w[k], tb = (s->hi[k] - o[k]) / w[k];
+        int fa = 2 * k, fb = 2 * k + 1;
+        if (ta > tb) { double tmp = ta; ta = tb; tb = tmp; int fi = fa; fa = fb; fb = fi; }
+        if (ta > t_in) { t_in = ta; f_in = fa; }
+        if (tb < t_out) t_out = tb;
+    }
+    if (!(t_out > t_in) || !(t_out > 0.0)) return;
+    double x[3];
+    if (t_in > 0.0) {
+        if (s->wall_mask & (1 << f_in)) return;
+        for (int k = 0; k < 3; ++k) x[k] = o[k] + t_in * w[k];
+    } else {
+        for (int k = 0; k < 3; ++k) x[k] = o[k];
+    }
+    double beta = 1.0;
+    int64_t n_events = 0;
+    for (int64_t step = 0;; ++step) {
+        if (step >= p->max_steps) { cnt[OC_STEP_BUDGET]++; break; }
+        cnt[OC_STEPS]++;
+        block4 B0 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 0);
+        int face;
+        double te = exit_distance(s, x, w, &face);
+        double sb = t->majorant[bin];
+        double tf = sb > 0.0 ? -log(1.0 - B0.u[0]) / sb : INFINITY;
+        if (tf >= te) {
+            for (int k = 0; k < 3; ++k) x[k] += te * w[k];
+            if (face >= 0 && (s->wall_mask & (1 << face))) {
+                if (n_events == p->max_events) { cnt[OC_CAP_HITS]++; break; }
+                n_events++;
+                cnt[OC_EVENTS]++;
+                cnt[OC_WALL_BOUNCES]++;
+                block4 B2 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 2);
+                if (p->analog) {
+                    if (!(B2.u[0] < s->wall_albedo)) { cnt[OC_ABSORBED_DEAD]++; break; }
+                } else {
+                    beta *= s->wall_albedo;
+                    if (beta == 0.0) { cnt[OC_ABSORBED_DEAD]++; break; }
+                }
+                int ax = face / 2;
+                double sg = (face & 1) ? -1.0 : 1.0;
+                x[ax] = (face & 1) ? s->hi[ax] : s->lo[ax];
+                block4 B1 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 1);
+                cosine_dir(B0.u[3], B1.u[0], ax, sg, w);
+                if (n_events >= p->n_rr) {
+                    double q = beta < 1.0 ? beta : 1.0;
+                    if (!(B2.u[1] < q)) { cnt[OC_RR_KILLS]++; break; }
+                    beta /= q;
+                }
+                continue;
+            }
+            cnt[OC_ESCAPES]++;
+            break;
+        }
+        for (int k = 0; k < 3; ++k) x[k] += tf * w[k];
+        coeffs cf = coeffs_at_p(s, t, x, bin, 0);
+        if (cf.total > sb) cnt[OC_MAJORANT_VIOLATIONS]++;
+        if (!(B0.u[1] * sb < cf.total)) { cnt[OC_NULLS]++; continue; }
+        if (n_events == p->max_events) { cnt[OC_CAP_HITS]++; break; }
+        n_events++;
+        cnt[OC_EVENTS]++;
+        block4 B1 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 1);
+        /* emission at this collision, through one light sample */
+        int bx;
+        double phi = excitation_fluence(s, t, x, &B1.u[1], &bx);
+        if (phi > 0.0) {
+            coeffs cx = coeffs_at_p(s, t, x, bx, 0);
+            double src = 0.0;
+            for (int d = 0; d < s->n_dyes; ++d) src += t->qy[d] * emission_pmf(t, d, bin) * cx.dye[d];
+            double val = beta * src * phi / (4.0 * OR_PI * cf.total * pb) * film_scale;
+            if (val != 0.0) {
+                size_t idx = ((size_t)py * c->width + px) * t->B + bin;
+#pragma omp atomic
+                film[idx] += val;
+                cnt[OC_CONNECTIONS]++;
+            }
+        }
+        /* the event at lambda: scattering continues, any absorption ends the walk */
+        if (!(B0.u[2] * cf.total < cf.scat)) {
+            if (B0.u[2] * cf.total < cf.total - cf.bg) cnt[OC_VF_REJECTED]++;
+            else cnt[OC_ABSORBED_DEAD]++;
+            break;
+        }
+        cnt[OC_SCATTERS]++;
+        iso_dir(B0.u[3], B1.u[0], w);
+        if (n_events >= p->n_rr) {
+            double q = beta < 1.0 ? beta : 1.0;
+            block4 B2 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 2);
+            if (!(B2.u[1] < q)) { cnt[OC_RR_KILLS]++; break; }
+            beta /= q;
+        }
+    }
+}
+
+/* Camera-side render: film [H][W][n_bins] of fluorescence radiance per unit source power.
+ * n_paths and path_offset must be multiples of W*H (each pixel gets the same number of
+ * paths). Returns -2 without a sensor or dyes, -3 for a source of zero area. */
+int or_render_camera(const or_scene *s, const or_params *p, double *film, uint64_t *counters)
+{
+    if (!s || !p || !film || !counters) return -1;
+    if (s->n_bins <= 0 || s->n_bins > OR_MAX_BINS) return -1;
+    if (s->n_dyes <= 0 || s->n_dyes > OR_MAX_DYES || s->sensor.kind == 0) return -2;
+    if (s->n_emitters <= 0 || s->n_emitters > OR_MAX_EMITTERS) return -1;
+    for (int k = 0; k < s->n_emitters; ++k) {
+        const or_emitter *e = &s->emitters[k];
+        double n[3] = { e->eu[1] * e->ev[2] - e->eu[2] * e->ev[1], e->eu[2] * e->ev[0] - e->eu[0] * e->ev[2],
+                        e->eu[0] * e->ev[1] - e->eu[1] * e->ev[0] };
+        if (!(n[0] * n[0] + n[1] * n[1] + n[2] * n[2] > 0.0)) return -3;
+    }
+    const uint64_t npix = (uint64_t)s->sensor.width * (uint64_t)s->sensor.height;
+    if (p->n_paths % npix != 0 || p->path_offset % npix != 0) return -1;
+    tables *t = (tables *)malloc(sizeof(tables));
+    build_tables(s, t);
+    apply_params(t, p);
+    memset(film, 0, sizeof(double) * (size_t)npix * s->n_bins);
+    memset(counters, 0, sizeof(uint64_t) * OR_NCOUNTERS);
+#ifdef _OPENMP
+    if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+#endif
+    const int64_t N = (int64_t)p->n_paths;
+    const double film_scale = N > 0 ? (double)npix / (double)N : 0.0;
+#pragma omp parallel
+    {
+        uint64_t cnt[OR_NCOUNTERS];
+        memset(cnt, 0, sizeof(cnt));
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < N; ++i)
+            trace_camera(s, t, p, p->path_offset + (uint64_t)i, film, film_scale, cnt);
+#pragma omp critical
+        for (int k = 0; k < OR_NCOUNTERS; ++k) counters[k] += cnt[k];
+    }
     free(t);
     return 0;
 }

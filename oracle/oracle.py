@@ -62,7 +62,8 @@ class Params(C.Structure):
                 ("analog", C.c_int), ("n_threads", C.c_int), ("max_events", C.c_int64),
                 ("max_steps", C.c_int64), ("majorant_scale", C.c_double), ("frozen", C.c_int),
                 ("pert_dye", C.c_int), ("pert_voxel", C.c_int64), ("pert_delta", C.c_double),
-                ("pert_sigma_s", C.c_double), ("macro_cell", C.c_int), ("skip_cell", C.c_int)]
+                ("pert_sigma_s", C.c_double), ("macro_cell", C.c_int), ("skip_cell", C.c_int),
+                ("paper_mode", C.c_int)]
 
 
 class Result(C.Structure):
@@ -111,6 +112,9 @@ def lib():
             L.or_adjoint.argtypes = [C.POINTER(Scene), C.POINTER(Params), C.c_void_p,
                                      C.c_void_p, C.c_void_p]
             L.or_adjoint.restype = C.c_int
+            L.or_render_camera.argtypes = [C.POINTER(Scene), C.POINTER(Params), C.c_void_p,
+                                           C.c_void_p]
+            L.or_render_camera.restype = C.c_int
             _lib = L
     return _lib
 
@@ -200,20 +204,41 @@ class _SceneHolder:
 def render(scene, n_paths=None, path_offset=0, seed=None, medium_id=0, n_threads=0,
            analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
            film=True, path_events=False, majorant_scale=1.0, frozen=False, pert=None,
-           macro_cell=0, skip_cell=0):
+           macro_cell=0, skip_cell=0, paper_mode=False):
     """Run the oracle; returns a dict of fp64 tallies normalised per launched path:
     face [2,6,B], absorbed [D+1,B], emitted [D,B], film [H,W,B] (or None), counters (dict),
     path_events u32[n] (or None).
     pert = (dye, voxel, delta, d_sigma_s) evaluates the scene with that perturbation (dye None for
     none); with frozen=True the decisions are still sampled in the unperturbed scene and every
-    tally carries the likelihood ratio of the decisions before it."""
+    tally carries the likelihood ratio of the decisions before it.
+    paper_mode=True: the paper's single-inelastic model (uncollided excitation, one emission,
+    fluorescence-only film)."""
     L = lib()
     h = _SceneHolder(scene)
     p = _params(scene, n_paths, path_offset, seed, medium_id, n_threads, analog, max_inelastic,
                 n_rr, max_events, max_steps, majorant_scale, frozen, pert)
     p.macro_cell = int(macro_cell)
     p.skip_cell = int(skip_cell)
+    p.paper_mode = 1 if paper_mode else 0
     return _render(L, h, scene, p, film, path_events)
+
+
+def render_camera(scene, n_paths, path_offset=0, seed=None, medium_id=0, n_threads=0,
+                  analog=None, n_rr=None, max_events=None, max_steps=None):
+    """Camera-side estimator of the paper's single-inelastic model: returns
+    {"film": [H,W,B] fluorescence radiance per unit source power, "counters": dict}. n_paths and
+    path_offset must be multiples of W*H."""
+    L = lib()
+    h = _SceneHolder(scene)
+    p = _params(scene, n_paths, path_offset, seed, medium_id, n_threads, analog, None, n_rr,
+                max_events, max_steps, 1.0, False, None)
+    sn = scene["sensor"]
+    film = np.zeros((sn["height"], sn["width"], h.n_bins))
+    counters = np.zeros(16, dtype=np.uint64)
+    rc = L.or_render_camera(C.byref(h.scene), C.byref(p), film.ctypes.data, counters.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle camera render rejected the scene (rc={rc})")
+    return {"film": film, "counters": {n: int(v) for n, v in zip(COUNTER_NAMES, counters)}}
 
 
 def _params(scene, n_paths, path_offset, seed, medium_id, n_threads, analog, max_inelastic, n_rr,

@@ -305,3 +305,26 @@ def cfg5_light_sheet(grid=256, width=1024, height=1024, spp=64, seed=0, n_paths=
     n = n_paths if n_paths is not None else width * height * spp
     return {"name": "cfg5_light_sheet", "spectrum": spectrum(), "dyes": dyes, "medium": med,
             "sources": [src], "sensor": cam, "params": params(n, seed=seed)}
+
+
+def paper_mode_scene(n=16, width=8, spp=1000, seed=7, sigma_s=3.0):
+    """Workload of the paper's own (camera-side) estimator: two blobby dyes (absorption 470/560
+    nm, emission 520/610 nm, sigma 20/25 nm) dissolved in a scattering solvent (sigma_s everywhere,
+    so sigma_t > 0 wherever a dye is), Lambertian walls (rho 0.7) on the +-x faces, a uniform
+    collimated beam over the -z face carrying the two absorption lines, and a pinhole camera
+    (50 deg) looking in through the open -y face. Paths = pixels x spp."""
+    rng = np.random.default_rng(seed)
+    conc = np.stack([blob_field(rng, n, 6, (1.5 * n / 16, 3.0 * n / 16)) for _ in range(2)])
+    conc /= conc.reshape(2, -1).mean(axis=1)[:, None, None, None]
+    dyes = make_dyes([470.0, 560.0], [20.0, 20.0], [520.0, 610.0], [25.0, 25.0], eps=[3.0, 2.0],
+                     qy=[0.8, 0.6])
+    walls = (1 << FACE_NX) | (1 << FACE_PX)
+    med = grid_medium(conc.astype(np.float32), None, sigma_s=sigma_s, wall_mask=walls,
+                      wall_albedo=0.7)
+    beam = rect_source("collimated", (0.0, 0.0, 0.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.0),
+                       (0.0, 0.0, 1.0), [470.0, 560.0])
+    cam = pinhole_sensor(width, width, eye=(0.5, -1.0, 0.5), right=(1, 0, 0), up=(0, 0, 1),
+                         forward=(0, 1, 0), fov_y_deg=50.0)
+    return {"name": "paper_mode_scene", "spectrum": spectrum(), "dyes": dyes, "medium": med,
+            "sources": [beam], "sensor": cam,
+            "params": params(width * width * spp, seed=2)}
