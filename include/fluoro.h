@@ -154,6 +154,13 @@ typedef struct flr_params {
                                     the adjoint, -d sigma_t / (sigma_bar - sigma_t), bounded; the
                                     forward pays about that fraction of extra null steps. Replays
                                     (flr_adjoint) must use the forward's value. */
+    int paper_mode;              /* 1: the paper's single-inelastic model (Sec. 4.1): excitation
+                                    light reaches a dye only uncollided (a scattering event or
+                                    wall bounce before the first emission ends the path), a second
+                                    dye absorption ends the path (V_f of Eq. 9), and only vertices
+                                    after the emission connect to the sensor, so the film holds
+                                    fluorescence alone. Rejected paths count as vf_rejected.
+                                    flr_render and the batch only; 0: the full RTE. */
 } flr_params;
 
 /* Create a context on CUDA device `cuda_device`. Allocates the small tally buffers. */
@@ -189,6 +196,26 @@ int flr_set_sensor(flr_ctx *ctx, const flr_sensor *sensor);
  * accumulate inside the context (read them with flr_read_tallies); film contributions are added
  * to p->film already divided by p->n_paths. */
 int flr_render(flr_ctx *ctx, const flr_params *p, void *stream);
+
+/* The paper's own estimator of its single-inelastic model (Sec. 4.1-4.3, Eq. 12): paths start
+ * at the sensor, at an emission bin drawn from the mixture of the dyes' emission pmfs, and walk
+ * the medium at that wavelength by delta tracking (isotropic scattering, Lambertian walls; an
+ * absorption ends the walk, since a dye absorption would be a second inelastic event). At every
+ * real collision one light sample (a line in proportion to its power, a point on it) gives the
+ * uncollided excitation fluence (Eq. 4-6; transmittance by ratio tracking), and the collision adds
+ * sum_d QY_d p_d(lambda) sigma_a,d(x, lambda_x) fluence / (4 pi sigma_t(x, lambda)) (Eq. 10) to
+ * its pixel and bin. p->film (device [H][W][n_bins], required) receives fluorescence radiance
+ * averaged over each pixel per unit total source power: the quantity flr_render writes with
+ * p->paper_mode = 1. Path id i renders pixel i mod (W*H): p->n_paths and p->path_offset must be
+ * multiples of W*H. Uses n_paths, path_offset, seed, medium_id, n_rr, analog, max_events,
+ * max_steps, film, accumulate (0 clears the film and the counters) and block_size; the rest is
+ * ignored. Requires a sensor and dyes, and sources of non-zero area (a pencil beam has no fluence
+ * density a camera path could meet: FLR_ERR_ARG). sigma_t must be positive wherever a dye is (the
+ * dyes dissolved in a scattering solvent, the paper's setting): the collision estimator cannot
+ * see emission where the medium never collides. Counters: paths, events (real collisions and wall
+ * bounces), nulls, connections (light samples that reached the collision), vf_rejected (dye
+ * absorptions at the emission wavelength), escapes and the budgets. */
+int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream);
 
 /* Synchronise `stream` and copy out the tallies accumulated since the last clear, divided by the
  * number of paths traced since then. host face [2][6][n_bins] (escaped weight per
@@ -252,7 +279,7 @@ int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const u
  * the interleaved copy of the grids -- lives in one static device array of 4 MiB + 64 KiB that
  * every GPU loading this library holds until the process exits; media with more than
  * FLR_NOALLOC_MAX_VOXELS voxels are rejected with FLR_ERR_ARG; p->macro_cell and p->majorant_margin are
- * ignored (one majorant per bin, no margin). The first call on a device looks up
+ * ignored (one majorant per bin, no margin), and so is p->paper_mode. The first call on a device looks up
  * that array's device address (with that device current), so make that first call before any
  * stream capture. Every call uses the same array and clears what must start at zero, so calls
  * that overlap on the GPU (other streams, other host threads) race with each other. The call

@@ -300,6 +300,8 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film, int macro_cell = 0, in
             for (int k = 0; k < 3; ++k) {
                 S.s_U[k] = (float)(c.U[k] / uu);
                 S.s_V[k] = (float)(c.V[k] / vv);
+                S.cam_U[k] = c.U[k];
+                S.cam_V[k] = c.V[k];
             }
             S.inv_A_pix = (float)((double)c.width * c.height / (std::sqrt(uu) * std::sqrt(vv)));
         } else {
@@ -714,9 +716,86 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     R.error_word = ctx->d_error;
     R.work_counter = ctx->d_work;
     R.regroup = p->regroup_interval;
+    R.paper_mode = p->paper_mode ? 1 : 0;
     e = launch_trace(S, R, p->form, p->block_size, p->blocks_per_sm, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch trace kernel");
     ctx->paths_since_clear += p->n_paths;
+    return FLR_OK;
+}
+
+static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem, const char *what);
+
+int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (!p) return fail(ctx, FLR_ERR_ARG, "params: NULL");
+    if (ctx->B <= 0 || !ctx->medium_set) return fail(ctx, FLR_ERR_STATE, "camera: spectrum, dyes and medium must be set");
+    if (ctx->sources.empty()) return fail(ctx, FLR_ERR_STATE, "camera: no sources");
+    if (!ctx->sensor_set || ctx->sensor.kind == FLR_SENSOR_NONE) return fail(ctx, FLR_ERR_STATE, "camera: needs a sensor");
+    if (ctx->medium.n_dyes < 1) return fail(ctx, FLR_ERR_ARG, "camera: the medium has no dyes");
+    if (!p->film || !is_device_pointer(p->film)) return fail(ctx, FLR_ERR_ARG, "camera: p->film must be device memory");
+    if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || (p->block_size & 31)))
+        return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
+    if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
+        return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
+    const uint64_t npix = (uint64_t)ctx->sensor.width * (uint64_t)ctx->sensor.height;
+    if (p->n_paths % npix != 0 || p->path_offset % npix != 0)
+        return fail(ctx, FLR_ERR_ARG, "camera: n_paths and path_offset must be multiples of the pixel count");
+    if (ctx->sensor.kind == FLR_SENSOR_PINHOLE) {
+        const float *o = ctx->sensor.origin;
+        bool inside = true;
+        for (int k = 0; k < 3; ++k) inside = inside && o[k] >= ctx->medium.lo[k] && o[k] <= ctx->medium.hi[k];
+        if (inside) return fail(ctx, FLR_ERR_ARG, "sensor: the pinhole must lie outside the medium box");
+    }
+    {
+        const flr_medium &m = ctx->medium;
+        int first = m.source_first, count = m.source_count;
+        if (count == 0) { first = 0; count = (int)ctx->sources.size(); }
+        for (int k = first; k < first + count && k < (int)ctx->sources.size(); ++k) {
+            const flr_source &src = ctx->sources[k];
+            const double n0 = (double)src.eu[1] * src.ev[2] - (double)src.eu[2] * src.ev[1];
+            const double n1 = (double)src.eu[2] * src.ev[0] - (double)src.eu[0] * src.ev[2];
+            const double n2 = (double)src.eu[0] * src.ev[1] - (double)src.eu[1] * src.ev[0];
+            if (!(n0 * n0 + n1 * n1 + n2 * n2 > 0.0))
+                return fail(ctx, FLR_ERR_ARG, "camera: every source needs a non-zero area (no pencil beams)");
+        }
+    }
+    DeviceGuard g(ctx->device);
+    int rc = prepare_tables(ctx, 0.0);
+    if (rc != FLR_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    SceneDev S;
+    rc = fill_scene(ctx, S, true, 0, 0);
+    if (rc != FLR_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    if (!p->accumulate) {
+        e = cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * FLR_NCOUNTERS, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->film, 0, sizeof(float) * (size_t)S.W * S.H * S.B, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "clear film");
+    }
+    if (p->n_paths == 0) return FLR_OK;
+    // the kernel's block tallies are flushed into a scratch copy: the camera estimator has none
+    rc = grow(ctx, (void **)&ctx->d_adj_tal, &ctx->adj_tal_cap, (size_t)tal_size(FLR_MAX_BINS),
+              sizeof(unsigned long long), "camera tallies");
+    if (rc != FLR_OK) return rc;
+    RunDev R;
+    std::memset(&R, 0, sizeof(R));
+    R.n_paths = p->n_paths;
+    R.path_offset = p->path_offset;
+    R.seed = p->seed;
+    R.medium_id = p->medium_id;
+    set_round_keys(R);
+    R.n_rr = p->n_rr;
+    R.analog = p->analog;
+    R.max_events = p->max_events;
+    R.max_steps = p->max_steps;
+    R.film_scale = (float)((double)npix / (double)p->n_paths);
+    R.film = p->film;
+    R.tallies = ctx->d_adj_tal;
+    R.counters = ctx->d_counters;
+    R.error_word = ctx->d_error;
+    e = launch_camera(S, R, p->block_size, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch camera kernel");
     return FLR_OK;
 }
 
@@ -1074,6 +1153,7 @@ int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const 
     R.analog = p->analog;
     R.max_events = p->max_events;
     R.max_steps = p->max_steps;
+    R.paper_mode = p->paper_mode ? 1 : 0;
     R.counters = bt.d_counters;
     R.error_word = ctx->d_error;
     cudaStream_t cs = ctx->cap_stream;

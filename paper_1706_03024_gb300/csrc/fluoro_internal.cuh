@@ -69,6 +69,7 @@ struct SceneDev {
     int sensor_kind, W, H;
     float s_origin[3], s_U[3], s_V[3], s_view[3];  // ortho: U, V pre-divided by |U|^2, |V|^2
     float tan_x, tan_y, inv_A_pix;
+    float cam_U[3], cam_V[3];          // ortho: full film edges (camera rays start on the film)
     float inv_tan_x, inv_tan_y;
     // local majorants (macro cells); mc == 0: one majorant per bin. sk > 0: empty-space leaps
     // after null collisions (global majorant) over the same cell grid
@@ -96,6 +97,7 @@ struct RunDev {
     int *error_word;
     unsigned long long *work_counter;  // dynamic path distribution (wavefront form)
     int regroup;                       // wavefront: tracking steps between connection flushes
+    int paper_mode;                    // the paper's single-inelastic model (flr_params)
     uint32_t rk[20];                   // Philox round keys of (seed, medium_id): k0[10], k1[10]
 };
 
@@ -166,6 +168,7 @@ struct AdjDev {
 // Host-side launchers (fluoro_kernels.cu).
 cudaError_t launch_adjoint(const SceneDev &S, const RunDev &R, const AdjDev &A, int block,
                            int blocks_per_sm, cudaStream_t st);
+cudaError_t launch_camera(const SceneDev &S, const RunDev &R, int block, cudaStream_t st);
 // pass 1 (weights) or pass 2 (gradients) of the warp-regrouped adjoint; R.work_counter zeroed
 cudaError_t launch_adjoint_warp(const SceneDev &S, const RunDev &R, const AdjDev &A, int pass,
                                 int block, int blocks_per_sm, cudaStream_t st);

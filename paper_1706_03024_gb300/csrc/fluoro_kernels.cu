@@ -578,7 +578,7 @@ struct NoSink {
     __device__ __forceinline__ void homogeneous(float) const {}
 };
 
-template <class G, bool OPT = true, bool MC = OPT, bool ADJ = false>
+template <class G, bool OPT = true, bool MC = OPT, bool ADJ = false, uint32_t SLOT0 = 2u>
 __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &R, const Smem &sm,
                                                float3 x, float3 dir, float tl, int b, uint64_t pid,
                                                uint32_t step, RegCnt &rc, const G &sink)
@@ -599,7 +599,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
         uint32_t j = 0;
         int it = 0;
         for (; it < MAX_CONNECT_STEPS; ++it) {
-            if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (j >> 2));
+            if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, SLOT0 + (j >> 2));
             const uint32_t q = j & 3u;
             const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
             ++j;
@@ -612,7 +612,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
             sink.point(p, b, st, sbc);
             T *= fmaxf(0.0f, 1.0f - st / sbc);
             if (T < (ADJ ? RT_RR_ADJ_THRESHOLD : RT_RR_THRESHOLD)) {
-                if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (j >> 2));
+                if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, SLOT0 + (j >> 2));
                 const uint32_t q2 = j & 3u;
                 const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
                 ++j;
@@ -636,7 +636,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
     uint32_t j = 0;
     int it = 0;
     for (; it < MAX_CONNECT_STEPS; ++it) {
-        if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (j >> 2));
+        if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, SLOT0 + (j >> 2));
         const uint32_t q = j & 3u;
         const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
         ++j;
@@ -656,7 +656,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
             }
         }
         if (T < (ADJ ? RT_RR_ADJ_THRESHOLD : RT_RR_THRESHOLD)) {
-            if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (j >> 2));
+            if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, SLOT0 + (j >> 2));
             const uint32_t q2 = j & 3u;
             const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
             ++j;
@@ -755,7 +755,7 @@ __device__ __forceinline__ Conn spawn(const M &m, const RunDev &R, const Smem &s
     if (e.kind == FLR_SOURCE_LAMBERTIAN) {
         const U4 s1 = m.rng(R, pid, STEP_SPAWN, 1u);
         p.w = cosine_dir(s0.d, s1.a, e.axis, e.sign);
-        if (m.sensor()) {
+        if (m.sensor() && !R.paper_mode) {   // the paper's film holds fluorescence only
             c = Conn{p.x, p.wt, p.bin, 2 * e.axis + (e.sign > 0.0f ? 1 : 0), pid, STEP_SPAWN, true};
         }
     } else {
@@ -818,6 +818,8 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
             finish(R, p);
             return c;
         }
+        // the paper's model drops excitation light reflected by a wall before any emission
+        if (R.paper_mode && !p.fl) { cnt_add(sm, FLR_C_VF_REJECTED); finish(R, p); return c; }
         if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
         p.n_events++;
         rc.events++;
@@ -874,10 +876,12 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
         obs.real_event(p.x, p.bin, k, ev);
         if (ev < 0) {
             rc.scatters++;
+            // the paper's model drops scattered excitation light (Sec. 4.1)
+            if (R.paper_mode && !p.fl) { cnt_add(sm, FLR_C_VF_REJECTED); finish(R, p); return c; }
         } else if (ev < D) {
             cnt_add(sm, FLR_C_DYE_ABSORPTIONS);
             m.tally(tal_absorbed(m.B()) + ev * m.B() + p.bin, p.wt);
-            if (R.max_inelastic >= 0 && p.n_inel >= R.max_inelastic) {
+            if ((R.max_inelastic >= 0 && p.n_inel >= R.max_inelastic) || (R.paper_mode && p.n_inel >= 1)) {
                 cnt_add(sm, FLR_C_VF_REJECTED);
                 finish(R, p);
                 return c;
@@ -1599,6 +1603,230 @@ __global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, Run
 }
 
 // ---------------------------------------------------------------------------------------------
+// Camera-side estimator of the paper's single-inelastic model (Sec. 4.1-4.3, Eq. 12). A path
+// starts at the sensor (pixel = path id mod W*H, a point uniform in it) at an emission bin drawn
+// from the mixture (1/D) sum_d p_d of the dyes' emission pmfs, and walks the medium at that bin by
+// delta tracking: isotropic scattering continues it, Lambertian walls reflect it, an absorption
+// ends it (a dye absorption would be a second inelastic event). At every real collision x one
+// light sample (Eq. 12: a line in proportion to its power, a point on it) estimates the uncollided
+// excitation fluence (Eq. 4-6), and the collision adds
+//     beta * sum_d QY_d p_d(lambda) sigma_a,d(x, lambda_x) fluence / (4 pi sigma_t(x, lambda) p(lambda))
+// to its pixel: collisions occur with density sigma_t T, so the sum estimates the integral of the
+// emission (Eq. 10) times the transmittance along the walk.
+constexpr uint32_t STEP_CAM_SPAWN = 0xFFFFFFFEu;
+
+// p_d(b) as the fp32 CDF table realises it (the pmf the light tracer samples)
+__device__ __forceinline__ float emission_pmf(const Smem &sm, int B, int d, int b)
+{
+    const float *c = sm.cdf + d * B;
+    return c[b] - (b > 0 ? c[b - 1] : 0.0f);
+}
+
+// Uncollided excitation fluence at x per unit total source power, through the line u0 picks and,
+// on a Lambertian line, the point (u1, u2); bx receives the line's bin. Transmittances by ratio
+// tracking with the uniforms of slots 3.. of (pid, step).
+__device__ __forceinline__ float excitation_fluence(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                                    float3 x, float u0, float u1, float u2,
+                                                    uint64_t pid, uint32_t step, int &bx, RegCnt &rc)
+{
+    int k = 0;
+    while (k < S.n_emitters - 1 && !(S.em_cdf[k] > u0)) ++k;
+    const EmitterDev &e = S.em[k];
+    bx = e.bin;
+    if (e.kind == FLR_SOURCE_LAMBERTIAN) {
+        const float3 xn = make_float3(e.origin[0] + u1 * e.eu[0] + u2 * e.ev[0],
+                                      e.origin[1] + u1 * e.eu[1] + u2 * e.ev[1],
+                                      e.origin[2] + u1 * e.eu[2] + u2 * e.ev[2]);
+        const float3 v = make_float3(x.x - xn.x, x.y - xn.y, x.z - xn.z);
+        const float r2 = v.x * v.x + v.y * v.y + v.z * v.z;
+        if (!(r2 > 0.0f)) return 0.0f;
+        const float ir = rsqrtf(r2);
+        const float cn = e.sign * comp(v, e.axis) * ir;
+        if (!(cn > 0.0f)) return 0.0f;
+        const float3 w = make_float3(v.x * ir, v.y * ir, v.z * ir);
+        const float T = transmittance<NoSink, false, false, false, 3u>(S, R, sm, xn, w, r2 * ir, bx, pid,
+                                                                       step, rc, NoSink{});
+        return cn * T * INV_PI / r2;
+    }
+    // collimated parallelogram: the point q of the source with x = q + l dir, l >= 0
+    const float dl = rsqrtf(e.dir[0] * e.dir[0] + e.dir[1] * e.dir[1] + e.dir[2] * e.dir[2]);
+    const float3 dir = make_float3(e.dir[0] * dl, e.dir[1] * dl, e.dir[2] * dl);
+    const float3 eu = make_float3(e.eu[0], e.eu[1], e.eu[2]), ev = make_float3(e.ev[0], e.ev[1], e.ev[2]);
+    const float3 n = make_float3(eu.y * ev.z - eu.z * ev.y, eu.z * ev.x - eu.x * ev.z, eu.x * ev.y - eu.y * ev.x);
+    const float nn = n.x * n.x + n.y * n.y + n.z * n.z;
+    const float dnd = dir.x * n.x + dir.y * n.y + dir.z * n.z;
+    if (!(nn > 0.0f) || dnd == 0.0f) return 0.0f;
+    const float3 xo = make_float3(x.x - e.origin[0], x.y - e.origin[1], x.z - e.origin[2]);
+    const float l = (xo.x * n.x + xo.y * n.y + xo.z * n.z) / dnd;
+    if (!(l >= 0.0f)) return 0.0f;
+    const float3 q = make_float3(xo.x - l * dir.x, xo.y - l * dir.y, xo.z - l * dir.z);
+    const float3 c1 = make_float3(q.y * ev.z - q.z * ev.y, q.z * ev.x - q.x * ev.z, q.x * ev.y - q.y * ev.x);
+    const float3 c2 = make_float3(eu.y * q.z - eu.z * q.y, eu.z * q.x - eu.x * q.z, eu.x * q.y - eu.y * q.x);
+    const float a = (c1.x * n.x + c1.y * n.y + c1.z * n.z) / nn;
+    const float b = (c2.x * n.x + c2.y * n.y + c2.z * n.z) / nn;
+    if (!(a >= 0.0f && a < 1.0f && b >= 0.0f && b < 1.0f)) return 0.0f;
+    const float3 pnt = make_float3(e.origin[0] + q.x, e.origin[1] + q.y, e.origin[2] + q.z);
+    const float T = transmittance<NoSink, false, false, false, 3u>(S, R, sm, pnt, dir, l, bx, pid, step, rc,
+                                                                   NoSink{});
+    return T / fabsf(dnd);   // the beam's cross-section is |eu x ev| |cos(normal, dir)|
+}
+
+__global__ void __launch_bounds__(256) k_trace_camera(SceneDev S, RunDev R)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
+    const MedS_<false> m{S, sm};
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
+    const uint64_t npix = (uint64_t)S.W * (uint64_t)S.H;
+    const float inv_d = 1.0f / (float)S.D;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
+        const uint64_t pid = R.path_offset + i;
+        cnt_add(sm, FLR_C_PATHS);
+        const int pix = (int)(pid % npix);
+        const int px = pix % S.W, py = pix / S.W;
+        const U4 s0 = draw_rk(R, pid, STEP_CAM_SPAWN, 0u);
+        const float fx = ((float)px + s0.a) / (float)S.W, fy = ((float)py + s0.b) / (float)S.H;
+        const int dsel = min((int)(s0.c * (float)S.D), S.D - 1);
+        const int bin = sample_cdf(sm.cdf + dsel * S.B, S.B, s0.d);
+        float pb = 0.0f;
+        for (int d = 0; d < S.D; ++d) pb += emission_pmf(sm, S.B, d, bin);
+        pb *= inv_d;
+        if (!(pb > 0.0f)) continue;
+        float3 o, w;
+        if (S.sensor_kind == FLR_SENSOR_ORTHO) {
+            const float vl = rsqrtf(S.s_view[0] * S.s_view[0] + S.s_view[1] * S.s_view[1] + S.s_view[2] * S.s_view[2]);
+            o = make_float3(S.s_origin[0] + fx * S.cam_U[0] + fy * S.cam_V[0],
+                            S.s_origin[1] + fx * S.cam_U[1] + fy * S.cam_V[1],
+                            S.s_origin[2] + fx * S.cam_U[2] + fy * S.cam_V[2]);
+            w = make_float3(-S.s_view[0] * vl, -S.s_view[1] * vl, -S.s_view[2] * vl);
+        } else {
+            const float X = (2.0f * fx - 1.0f) * S.tan_x, Y = (2.0f * fy - 1.0f) * S.tan_y;
+            const float3 d = make_float3(S.s_view[0] + X * S.s_U[0] + Y * S.s_V[0],
+                                         S.s_view[1] + X * S.s_U[1] + Y * S.s_V[1],
+                                         S.s_view[2] + X * S.s_U[2] + Y * S.s_V[2]);
+            const float dl = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+            o = make_float3(S.s_origin[0], S.s_origin[1], S.s_origin[2]);
+            w = make_float3(d.x * dl, d.y * dl, d.z * dl);
+        }
+        // enter the box; the entry face must be open (walls are opaque from outside)
+        float t_in = -FLT_MAX, t_out = FLT_MAX;
+        int f_in = -1;
+        bool miss = false;
+        {
+            const float os[3] = {o.x, o.y, o.z}, ws[3] = {w.x, w.y, w.z};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (ws[k] == 0.0f) {
+                    if (os[k] < S.lo[k] || os[k] > S.hi[k]) miss = true;
+                    continue;
+                }
+                float ta = (S.lo[k] - os[k]) / ws[k], tb = (S.hi[k] - os[k]) / ws[k];
+                int fa = 2 * k, fb = 2 * k + 1;
+                if (ta > tb) {
+                    const float tt = ta; ta = tb; tb = tt;
+                    const int ff = fa; fa = fb; fb = ff;
+                }
+                if (ta > t_in) { t_in = ta; f_in = fa; }
+                if (tb < t_out) t_out = tb;
+            }
+        }
+        if (miss || !(t_out > t_in) || !(t_out > 0.0f)) continue;
+        float3 x = o;
+        if (t_in > 0.0f) {
+            if (S.wall_mask & (1 << f_in)) continue;
+            x = make_float3(o.x + t_in * w.x, o.y + t_in * w.y, o.z + t_in * w.z);
+        }
+        float3 iw = inv_dir(w);
+        float beta = 1.0f;
+        long long n_events = 0;
+        for (uint32_t step = 0;; ++step) {
+            if ((long long)step >= R.max_steps) { cnt_add(sm, FLR_C_STEP_BUDGET); break; }
+            rc.steps++;
+            const U4 b0 = draw_rk(R, pid, step, 0u);
+            const U4 b1 = draw_rk(R, pid, step, 1u);
+            int face;
+            const float te = exit_distance(m, x, w, iw, face);
+            const float sb = sm.maj[bin];
+            const float tf = sb > 0.0f ? -__logf(1.0f - b0.a) * sm.inv_maj[bin] : FLT_MAX;
+            if (tf >= te) {
+                x = make_float3(x.x + te * w.x, x.y + te * w.y, x.z + te * w.z);
+                if (face >= 0 && (S.wall_mask & (1 << face))) {
+                    if (n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); break; }
+                    n_events++;
+                    rc.events++;
+                    cnt_add(sm, FLR_C_WALL_BOUNCES);
+                    const U4 b2 = draw_rk(R, pid, step, 2u);
+                    if (R.analog) {
+                        if (!(b2.a < S.wall_albedo)) { cnt_add(sm, FLR_C_ABSORBED_DEAD); break; }
+                    } else {
+                        beta *= S.wall_albedo;
+                        if (beta == 0.0f) { cnt_add(sm, FLR_C_ABSORBED_DEAD); break; }
+                    }
+                    const int ax = face >> 1;
+                    const float sg = (face & 1) ? -1.0f : 1.0f;
+                    if (ax == 0) x.x = (face & 1) ? S.hi[0] : S.lo[0];
+                    else if (ax == 1) x.y = (face & 1) ? S.hi[1] : S.lo[1];
+                    else x.z = (face & 1) ? S.hi[2] : S.lo[2];
+                    w = cosine_dir(b0.d, b1.a, ax, sg);
+                    iw = inv_dir(w);
+                    if (n_events >= R.n_rr) {
+                        const float q = fminf(beta, 1.0f);
+                        if (!(b2.b < q)) { cnt_add(sm, FLR_C_RR_KILLS); break; }
+                        beta = beta < 1.0f ? 1.0f : beta;   // beta / min(beta, 1), exactly
+                    }
+                    continue;
+                }
+                cnt_add(sm, FLR_C_ESCAPES);
+                break;
+            }
+            x = make_float3(x.x + tf * w.x, x.y + tf * w.y, x.z + tf * w.z);
+            const Coeffs k = coeffs_at(m, x, bin);
+            if (k.total > sb) cnt_add(sm, FLR_C_MAJORANT_VIOLATIONS);
+            if (!(b0.b * sb < k.total)) { rc.nulls++; continue; }
+            if (n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); break; }
+            n_events++;
+            rc.events++;
+            // emission at this collision through one light sample
+            int bx;
+            const float phi = excitation_fluence(S, R, sm, x, b1.b, b1.c, b1.d, pid, step, bx, rc);
+            if (phi > 0.0f) {
+                const Coeffs kx = coeffs_at(m, x, bx);
+                float src = 0.0f;
+                for (int d = 0; d < S.D; ++d) src += sm.qy[d] * emission_pmf(sm, S.B, d, bin) * kx.dye[d];
+                const float val = beta * src * phi * INV_4PI / (k.total * pb) * R.film_scale;
+                if (val != 0.0f) {
+                    atomicAdd(&R.film[(size_t)pix * S.B + bin], val);
+                    rc.connections++;
+                }
+            }
+            // the event at the emission wavelength: scattering continues, an absorption ends the walk
+            if (!(b0.c * k.total < k.scat)) {
+                cnt_add(sm, b0.c * k.total < k.total - k.bg ? FLR_C_VF_REJECTED : FLR_C_ABSORBED_DEAD);
+                break;
+            }
+            rc.scatters++;
+            {
+                const float z = 1.0f - 2.0f * b0.d;
+                float sn, cs;
+                __sincosf(TWO_PI * b1.a, &sn, &cs);
+                const float r = sqrt_approx(fmaxf(0.0f, 1.0f - z * z));
+                w = make_float3(r * cs, r * sn, z);
+            }
+            iw = inv_dir(w);
+            if (n_events >= R.n_rr) {
+                const float q = fminf(beta, 1.0f);
+                const U4 b2 = draw_rk(R, pid, step, 2u);
+                if (!(b2.b < q)) { cnt_add(sm, FLR_C_RR_KILLS); break; }
+                beta = beta < 1.0f ? 1.0f : beta;
+            }
+        }
+    }
+    block_epilogue(S, R, sm, rc);
+}
+
+// ---------------------------------------------------------------------------------------------
 // Batched persistent form: independent media in one launch. A device queue holds chunks of
 // consecutive path ids of one medium (ordered longest expected paths first). Each warp owns one
 // chunk at a time and hands its path ids to lanes as their paths end (regeneration), so a lane
@@ -1957,6 +2185,21 @@ cudaError_t launch_adjoint_warp(const SceneDev &S, const RunDev &R, const AdjDev
     if (blocks_per_sm <= 0 || blocks_per_sm > occ) blocks_per_sm = occ;
     const long long grid = (long long)num_sms() * blocks_per_sm;
     k<<<(unsigned)grid, block, smem, st>>>(S, R, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_camera(const SceneDev &S, const RunDev &R, int block, cudaStream_t st)
+{
+    if (block <= 0) block = trace_block_default();
+    const int smem = trace_smem_bytes(S.B, FLR_FORM_PLAIN, block);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_camera, block, smem);
+    if (occ < 1) occ = 1;
+    long long grid = (long long)num_sms() * occ;
+    const long long need = ((long long)R.n_paths + block - 1) / block;
+    if (need < grid) grid = need;
+    if (grid < 1) grid = 1;
+    k_trace_camera<<<(unsigned)grid, block, smem, st>>>(S, R);
     return cudaGetLastError();
 }
 

@@ -77,7 +77,7 @@ class flr_params(C.Structure):
                 ("max_steps", C.c_int64), ("film", C.c_void_p), ("path_events", C.c_void_p),
                 ("accumulate", C.c_int), ("block_size", C.c_int), ("blocks_per_sm", C.c_int),
                 ("regroup_interval", C.c_int), ("macro_cell", C.c_int),
-                ("skip_cell", C.c_int), ("majorant_margin", C.c_float)]
+                ("skip_cell", C.c_int), ("majorant_margin", C.c_float), ("paper_mode", C.c_int)]
 
 
 # name -> (restype, argtypes); every symbol include/fluoro.h declares
@@ -91,6 +91,7 @@ SIGNATURES = {
     "flr_set_medium": (C.c_int, [C.c_void_p, C.POINTER(flr_medium)]),
     "flr_set_sensor": (C.c_int, [C.c_void_p, C.POINTER(flr_sensor)]),
     "flr_render": (C.c_int, [C.c_void_p, C.POINTER(flr_params), C.c_void_p]),
+    "flr_render_camera": (C.c_int, [C.c_void_p, C.POINTER(flr_params), C.c_void_p]),
     "flr_read_tallies": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]),
     "flr_adjoint": (C.c_int, [C.c_void_p, C.POINTER(flr_params), C.c_void_p, C.c_void_p,
@@ -195,6 +196,10 @@ def flr_set_sensor(ctx, sensor):
 
 def flr_render(ctx, params, stream=0):
     return load().flr_render(ctx, C.byref(params), C.c_void_p(int(stream)))
+
+
+def flr_render_camera(ctx, params, stream=0):
+    return load().flr_render_camera(ctx, C.byref(params), C.c_void_p(int(stream)))
 
 
 def flr_read_tallies(ctx, face_ptr, absorbed_ptr, emitted_ptr, counters_ptr, stream=0):
