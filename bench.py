@@ -286,6 +286,70 @@ def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_
             "grad_sigma_s": float(gs.item()), "grad_conc_abs_max": float(gc.abs().max().item())}
 
 
+def bench_paper(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum):
+    """The paper's single-inelastic model (Sec. 4.1-4.3) on a 64^3 x 2 blobby-dye scene with a
+    256x256 pinhole film: its own camera-side estimator (flr_render_camera, 16 paths per pixel)
+    against the light tracer in paper mode (4,194,304 paths, warp-regrouped), both timed, and each
+    film's RMSE against a reference averaged from both estimators at 16x the paths, so that the
+    comparison is at equal RMSE: efficiency = 1 / (RMSE^2 x time)."""
+    import torch
+    from paper_1706_03024_gb300.scene import Scene
+
+    sc = sg.paper_mode_scene(n=64, width=256, seed=7)
+    S = Scene(sc, device=local)
+    n_cam = 256 * 256 * 16
+    n_light = 4_194_304
+    off = rank * (1 << 32)
+
+    def cam(seed=None, k=0):
+        return S.render_camera(n_paths=n_cam, path_offset=off + k * n_cam, seed=seed)
+
+    def light(seed=None, k=0):
+        return S.render(n_paths=n_light, path_offset=off + k * n_light, form="wavefront_warp",
+                        paper_mode=True, seed=seed)
+
+    ref = torch.zeros_like(S.film_tensor(), dtype=torch.float64)
+    for k in range(8):
+        ref += cam(seed=4242, k=k + 1).double() / 16
+        ref += light(seed=4243, k=k + 1).double() / 16
+    cam()
+    light()
+    torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        ms = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return reduce_max(sum(ms) / len(ms))
+
+    barrier()
+    cam_ms = timed(cam, args.paper_steps)
+    cam_counters = S.read()["counters"]
+    cam_rmse = float(torch.sqrt(torch.mean((cam().double() - ref) ** 2)))
+    light_ms = timed(light, args.paper_steps)
+    light_counters = S.read()["counters"]
+    light_rmse = float(torch.sqrt(torch.mean((light().double() - ref) ** 2)))
+    eff_cam = 1.0 / (cam_rmse ** 2 * cam_ms)
+    eff_light = 1.0 / (light_rmse ** 2 * light_ms)
+    return {"workload": "2 x 64^3 blob dyes in a scattering solvent, collimated beam, 256x256 pinhole "
+                        "film, the paper's single-inelastic model",
+            "camera": {"paths": n_cam, "ms": cam_ms,
+                       "events_per_s": reduce_sum(float(cam_counters["events"])) / (cam_ms / 1000.0),
+                       "rmse": cam_rmse},
+            "light_paper_mode": {"paths": n_light, "ms": light_ms,
+                                 "events_per_s": reduce_sum(float(light_counters["events"])) / (light_ms / 1000.0),
+                                 "rmse": light_rmse},
+            "camera_over_light_at_equal_rmse": eff_cam / eff_light,
+            "reference": "mean of 8 camera (16 spp) and 8 light-tracer (4.2M paths) films, other seeds",
+            "launches_per_step": 1}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -417,6 +481,9 @@ def run_ours(args):
         batched = bench_batched(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
 
     # --- adjoint (path replay) -------------------------------------------------------------
+    paper = None
+    if not args.no_paper:
+        paper = bench_paper(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
     adjoint = None
     if not args.no_adjoint:
         adjoint = bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
@@ -490,6 +557,7 @@ def run_ours(args):
                 "rmse": rmse,
                 "batched": batched,
                 "adjoint": adjoint,
+                "paper_model": paper,
             },
             "counters_per_step": cnt_w,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
@@ -500,7 +568,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps + len(ms_p)
             + (0 if batched is None else batched["steps"] + batched["plain_launches"])
-            + (0 if adjoint is None else adjoint["launches_per_step"] * args.adjoint_steps),
+            + (0 if adjoint is None else adjoint["launches_per_step"] * args.adjoint_steps)
+            + (0 if paper is None else 2 * args.paper_steps),
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -539,6 +608,9 @@ def main():
     ap.add_argument("--batch-media", type=int, default=256,
                     help="media in the batched workload (fewer for small profiling cases only)")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-paper", action="store_true",
+                    help="skip the paper's own (camera-side) estimator of its single-inelastic model")
+    ap.add_argument("--paper-steps", type=int, default=3)
     ap.add_argument("--adjoint-steps", type=int, default=3)
     ap.add_argument("--adjoint-paths", type=int, default=0,
                     help="override the adjoint path count (small profiling cases only)")
