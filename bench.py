@@ -529,10 +529,13 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu:
         r = cpu_oracle_rate(sc, args.cpu_paths)
+        r1 = cpu_oracle_rate(sc, max(args.cpu_paths // 16, 1024), n_threads=1)
         cpu = {"value": r["events"] / r["seconds"], "unit": "events/s",
                "cores": os.cpu_count() or 1, "kind": "oracle",
                "sample": f"{args.cpu_paths} paths of the same workload (fp64, all host cores), "
-                         f"{r['seconds']:.1f} s"}
+                         f"{r['seconds']:.1f} s",
+               "single_core": {"value": r1["events"] / r1["seconds"], "unit": "events/s",
+                               "sample": f"{r1['paths']} paths on one core, {r1['seconds']:.1f} s"}}
 
     if rank == 0:
         line = {
