@@ -208,8 +208,9 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream);
  * averaged over each pixel per unit total source power: the quantity flr_render writes with
  * p->paper_mode = 1. Path id i renders pixel i mod (W*H): p->n_paths and p->path_offset must be
  * multiples of W*H. Uses n_paths, path_offset, seed, medium_id, n_rr, analog, max_events,
- * max_steps, film, accumulate (0 clears the film and the counters) and block_size; the rest is
- * ignored. Requires a sensor and dyes, and sources of non-zero area (a pencil beam has no fluence
+ * max_steps, film, accumulate (0 clears the film and the counters), block_size and form
+ * (FLR_FORM_PLAIN: one thread per path; the wavefront forms: warp-regrouped light samples, the
+ * same film up to the order of fp32 additions); the rest is ignored. Requires a sensor and dyes, and sources of non-zero area (a pencil beam has no fluence
  * density a camera path could meet: FLR_ERR_ARG). sigma_t must be positive wherever a dye is (the
  * dyes dissolved in a scattering solvent, the paper's setting): the collision estimator cannot
  * see emission where the medium never collides. Counters: paths, events (real collisions and wall

@@ -736,6 +736,8 @@ int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
     if (!p->film || !is_device_pointer(p->film)) return fail(ctx, FLR_ERR_ARG, "camera: p->film must be device memory");
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || (p->block_size & 31)))
         return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
+    if (p->form != FLR_FORM_PLAIN && p->form != FLR_FORM_WAVEFRONT && p->form != FLR_FORM_WAVEFRONT_WARP)
+        return fail(ctx, FLR_ERR_ARG, "params: unknown form");
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
     const uint64_t npix = (uint64_t)ctx->sensor.width * (uint64_t)ctx->sensor.height;
@@ -794,7 +796,9 @@ int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
     R.tallies = ctx->d_adj_tal;
     R.counters = ctx->d_counters;
     R.error_word = ctx->d_error;
-    e = launch_camera(S, R, p->block_size, st);
+    R.work_counter = ctx->d_work;
+    e = cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = launch_camera(S, R, p->form, p->block_size, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch camera kernel");
     return FLR_OK;
 }

@@ -168,7 +168,8 @@ struct AdjDev {
 // Host-side launchers (fluoro_kernels.cu).
 cudaError_t launch_adjoint(const SceneDev &S, const RunDev &R, const AdjDev &A, int block,
                            int blocks_per_sm, cudaStream_t st);
-cudaError_t launch_camera(const SceneDev &S, const RunDev &R, int block, cudaStream_t st);
+// form PLAIN: one thread per camera path; otherwise warp-regrouped (R.work_counter zeroed)
+cudaError_t launch_camera(const SceneDev &S, const RunDev &R, int form, int block, cudaStream_t st);
 // pass 1 (weights) or pass 2 (gradients) of the warp-regrouped adjoint; R.work_counter zeroed
 cudaError_t launch_adjoint_warp(const SceneDev &S, const RunDev &R, const AdjDev &A, int pass,
                                 int block, int blocks_per_sm, cudaStream_t st);

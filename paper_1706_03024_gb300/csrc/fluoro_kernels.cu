@@ -1622,31 +1622,40 @@ __device__ __forceinline__ float emission_pmf(const Smem &sm, int B, int d, int 
     return c[b] - (b > 0 ? c[b - 1] : 0.0f);
 }
 
-// Uncollided excitation fluence at x per unit total source power, through the line u0 picks and,
-// on a Lambertian line, the point (u1, u2); bx receives the line's bin. Transmittances by ratio
-// tracking with the uniforms of slots 3.. of (pid, step).
-__device__ __forceinline__ float excitation_fluence(const SceneDev &S, const RunDev &R, const Smem &sm,
-                                                    float3 x, float u0, float u1, float u2,
-                                                    uint64_t pid, uint32_t step, int &bx, RegCnt &rc)
+// One light sample for the uncollided excitation fluence at x (Eq. 4-6), per unit total source
+// power: the line u0 picks (p(lambda_x) of Eq. 12) and, on a Lambertian line, the point (u1, u2)
+// (p(x_n)). The fluence is geom * T(start -> start + len dir) at the line's bin bx.
+struct LightGeom {
+    float3 start, dir;
+    float len, geom;
+    int bx;
+    bool ok;
+};
+
+__device__ __forceinline__ LightGeom light_geometry(const SceneDev &S, float3 x, float u0, float u1, float u2)
 {
+    LightGeom g;
+    g.ok = false;
     int k = 0;
     while (k < S.n_emitters - 1 && !(S.em_cdf[k] > u0)) ++k;
     const EmitterDev &e = S.em[k];
-    bx = e.bin;
+    g.bx = e.bin;
     if (e.kind == FLR_SOURCE_LAMBERTIAN) {
         const float3 xn = make_float3(e.origin[0] + u1 * e.eu[0] + u2 * e.ev[0],
                                       e.origin[1] + u1 * e.eu[1] + u2 * e.ev[1],
                                       e.origin[2] + u1 * e.eu[2] + u2 * e.ev[2]);
         const float3 v = make_float3(x.x - xn.x, x.y - xn.y, x.z - xn.z);
         const float r2 = v.x * v.x + v.y * v.y + v.z * v.z;
-        if (!(r2 > 0.0f)) return 0.0f;
+        if (!(r2 > 0.0f)) return g;
         const float ir = rsqrtf(r2);
         const float cn = e.sign * comp(v, e.axis) * ir;
-        if (!(cn > 0.0f)) return 0.0f;
-        const float3 w = make_float3(v.x * ir, v.y * ir, v.z * ir);
-        const float T = transmittance<NoSink, false, false, false, 3u>(S, R, sm, xn, w, r2 * ir, bx, pid,
-                                                                       step, rc, NoSink{});
-        return cn * T * INV_PI / r2;
+        if (!(cn > 0.0f)) return g;
+        g.start = xn;
+        g.dir = make_float3(v.x * ir, v.y * ir, v.z * ir);
+        g.len = r2 * ir;
+        g.geom = cn * INV_PI / r2;   // Lambertian radiance 1/(pi A) x cos / r^2 x A
+        g.ok = true;
+        return g;
     }
     // collimated parallelogram: the point q of the source with x = q + l dir, l >= 0
     const float dl = rsqrtf(e.dir[0] * e.dir[0] + e.dir[1] * e.dir[1] + e.dir[2] * e.dir[2]);
@@ -1655,173 +1664,425 @@ __device__ __forceinline__ float excitation_fluence(const SceneDev &S, const Run
     const float3 n = make_float3(eu.y * ev.z - eu.z * ev.y, eu.z * ev.x - eu.x * ev.z, eu.x * ev.y - eu.y * ev.x);
     const float nn = n.x * n.x + n.y * n.y + n.z * n.z;
     const float dnd = dir.x * n.x + dir.y * n.y + dir.z * n.z;
-    if (!(nn > 0.0f) || dnd == 0.0f) return 0.0f;
+    if (!(nn > 0.0f) || dnd == 0.0f) return g;
     const float3 xo = make_float3(x.x - e.origin[0], x.y - e.origin[1], x.z - e.origin[2]);
     const float l = (xo.x * n.x + xo.y * n.y + xo.z * n.z) / dnd;
-    if (!(l >= 0.0f)) return 0.0f;
+    if (!(l >= 0.0f)) return g;
     const float3 q = make_float3(xo.x - l * dir.x, xo.y - l * dir.y, xo.z - l * dir.z);
     const float3 c1 = make_float3(q.y * ev.z - q.z * ev.y, q.z * ev.x - q.x * ev.z, q.x * ev.y - q.y * ev.x);
     const float3 c2 = make_float3(eu.y * q.z - eu.z * q.y, eu.z * q.x - eu.x * q.z, eu.x * q.y - eu.y * q.x);
     const float a = (c1.x * n.x + c1.y * n.y + c1.z * n.z) / nn;
     const float b = (c2.x * n.x + c2.y * n.y + c2.z * n.z) / nn;
-    if (!(a >= 0.0f && a < 1.0f && b >= 0.0f && b < 1.0f)) return 0.0f;
-    const float3 pnt = make_float3(e.origin[0] + q.x, e.origin[1] + q.y, e.origin[2] + q.z);
-    const float T = transmittance<NoSink, false, false, false, 3u>(S, R, sm, pnt, dir, l, bx, pid, step, rc,
-                                                                   NoSink{});
-    return T / fabsf(dnd);   // the beam's cross-section is |eu x ev| |cos(normal, dir)|
+    if (!(a >= 0.0f && a < 1.0f && b >= 0.0f && b < 1.0f)) return g;
+    g.start = make_float3(e.origin[0] + q.x, e.origin[1] + q.y, e.origin[2] + q.z);
+    g.dir = dir;
+    g.len = l;
+    g.geom = 1.0f / fabsf(dnd);   // the beam's cross-section is |eu x ev| |cos(normal, dir)|
+    g.ok = true;
+    return g;
 }
 
+// The emission (Eq. 10) a collision at x sends into `bin` per unit excitation fluence at bx,
+// divided by sigma_t(x, bin) and by the bin's sampling probability (the collision estimator).
+__device__ __forceinline__ float emission_weight(const SceneDev &S, const Smem &sm, float3 x, int bin,
+                                                 int bx, float sigma_t, float pb)
+{
+    const Coeffs kx = coeffs_at(MedS_<false>{S, sm}, x, bx);
+    float src = 0.0f;
+    for (int d = 0; d < S.D; ++d) src += sm.qy[d] * emission_pmf(sm, S.B, d, bin) * kx.dye[d];
+    return src * INV_4PI / (sigma_t * pb);
+}
+
+// A camera path's start: its pixel, emission bin and sampling probability, and the ray into the
+// box (false: the ray misses the box or enters through a wall).
+struct CamStart {
+    float3 x, w;
+    int pix, bin;
+    float pb;
+};
+
+__device__ __forceinline__ bool camera_start(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                             uint64_t pid, CamStart &cs)
+{
+    const uint64_t npix = (uint64_t)S.W * (uint64_t)S.H;
+    cs.pix = (int)(pid % npix);
+    const int px = cs.pix % S.W, py = cs.pix / S.W;
+    const U4 s0 = draw_rk(R, pid, STEP_CAM_SPAWN, 0u);
+    const float fx = ((float)px + s0.a) / (float)S.W, fy = ((float)py + s0.b) / (float)S.H;
+    const int dsel = min((int)(s0.c * (float)S.D), S.D - 1);
+    cs.bin = sample_cdf(sm.cdf + dsel * S.B, S.B, s0.d);
+    float pb = 0.0f;
+    for (int d = 0; d < S.D; ++d) pb += emission_pmf(sm, S.B, d, cs.bin);
+    cs.pb = pb * (1.0f / (float)S.D);
+    if (!(cs.pb > 0.0f)) return false;
+    float3 o, w;
+    if (S.sensor_kind == FLR_SENSOR_ORTHO) {
+        const float vl = rsqrtf(S.s_view[0] * S.s_view[0] + S.s_view[1] * S.s_view[1] + S.s_view[2] * S.s_view[2]);
+        o = make_float3(S.s_origin[0] + fx * S.cam_U[0] + fy * S.cam_V[0],
+                        S.s_origin[1] + fx * S.cam_U[1] + fy * S.cam_V[1],
+                        S.s_origin[2] + fx * S.cam_U[2] + fy * S.cam_V[2]);
+        w = make_float3(-S.s_view[0] * vl, -S.s_view[1] * vl, -S.s_view[2] * vl);
+    } else {
+        const float X = (2.0f * fx - 1.0f) * S.tan_x, Y = (2.0f * fy - 1.0f) * S.tan_y;
+        const float3 d = make_float3(S.s_view[0] + X * S.s_U[0] + Y * S.s_V[0],
+                                     S.s_view[1] + X * S.s_U[1] + Y * S.s_V[1],
+                                     S.s_view[2] + X * S.s_U[2] + Y * S.s_V[2]);
+        const float dl = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+        o = make_float3(S.s_origin[0], S.s_origin[1], S.s_origin[2]);
+        w = make_float3(d.x * dl, d.y * dl, d.z * dl);
+    }
+    // enter the box; the entry face must be open (walls are opaque from outside)
+    float t_in = -FLT_MAX, t_out = FLT_MAX;
+    int f_in = -1;
+    const float os[3] = {o.x, o.y, o.z}, ws[3] = {w.x, w.y, w.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (ws[k] == 0.0f) {
+            if (os[k] < S.lo[k] || os[k] > S.hi[k]) return false;
+            continue;
+        }
+        float ta = (S.lo[k] - os[k]) / ws[k], tb = (S.hi[k] - os[k]) / ws[k];
+        int fa = 2 * k, fb = 2 * k + 1;
+        if (ta > tb) {
+            const float tt = ta; ta = tb; tb = tt;
+            const int ff = fa; fa = fb; fb = ff;
+        }
+        if (ta > t_in) { t_in = ta; f_in = fa; }
+        if (tb < t_out) t_out = tb;
+    }
+    if (!(t_out > t_in) || !(t_out > 0.0f)) return false;
+    cs.x = o;
+    if (t_in > 0.0f) {
+        if (S.wall_mask & (1 << f_in)) return false;
+        cs.x = make_float3(o.x + t_in * w.x, o.y + t_in * w.y, o.z + t_in * w.z);
+    }
+    cs.w = w;
+    return true;
+}
+
+// A camera walk between collisions: the state one lane carries.
+struct CamPath {
+    float3 x, w, iw;
+    float beta, pb;
+    int pix, bin;
+    uint64_t pid;
+    uint32_t step;
+    long long n_events;
+    bool alive;
+};
+
+// What one walk step asks for at a real collision: a light sample (its geometry and weight).
+struct CamRec {
+    LightGeom g;
+    float wt;
+    bool valid;
+};
+
+// One step of a camera walk (free flight, then a wall bounce, an escape or a collision). At a
+// real collision it returns the light sample whose transmittance completes the contribution
+// wt * T, wt including film_scale.
+__device__ __forceinline__ CamRec camera_step(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                              CamPath &cp, RegCnt &rc)
+{
+    const MedS_<false> m{S, sm};
+    CamRec out;
+    out.valid = false;
+    if ((long long)cp.step >= R.max_steps) { cnt_add(sm, FLR_C_STEP_BUDGET); cp.alive = false; return out; }
+    rc.steps++;
+    const uint32_t step = cp.step;
+    cp.step++;
+    const U4 b0 = draw_rk(R, cp.pid, step, 0u);
+    const U4 b1 = draw_rk(R, cp.pid, step, 1u);
+    int face;
+    const float te = exit_distance(m, cp.x, cp.w, cp.iw, face);
+    const float sb = sm.maj[cp.bin];
+    const float tf = sb > 0.0f ? -__logf(1.0f - b0.a) * sm.inv_maj[cp.bin] : FLT_MAX;
+    if (tf >= te) {
+        cp.x = make_float3(cp.x.x + te * cp.w.x, cp.x.y + te * cp.w.y, cp.x.z + te * cp.w.z);
+        if (face >= 0 && (S.wall_mask & (1 << face))) {
+            if (cp.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); cp.alive = false; return out; }
+            cp.n_events++;
+            rc.events++;
+            cnt_add(sm, FLR_C_WALL_BOUNCES);
+            const U4 b2 = draw_rk(R, cp.pid, step, 2u);
+            if (R.analog) {
+                if (!(b2.a < S.wall_albedo)) { cnt_add(sm, FLR_C_ABSORBED_DEAD); cp.alive = false; return out; }
+            } else {
+                cp.beta *= S.wall_albedo;
+                if (cp.beta == 0.0f) { cnt_add(sm, FLR_C_ABSORBED_DEAD); cp.alive = false; return out; }
+            }
+            const int ax = face >> 1;
+            const float sg = (face & 1) ? -1.0f : 1.0f;
+            if (ax == 0) cp.x.x = (face & 1) ? S.hi[0] : S.lo[0];
+            else if (ax == 1) cp.x.y = (face & 1) ? S.hi[1] : S.lo[1];
+            else cp.x.z = (face & 1) ? S.hi[2] : S.lo[2];
+            cp.w = cosine_dir(b0.d, b1.a, ax, sg);
+            cp.iw = inv_dir(cp.w);
+            if (cp.n_events >= R.n_rr) {
+                const float q = fminf(cp.beta, 1.0f);
+                if (!(b2.b < q)) { cnt_add(sm, FLR_C_RR_KILLS); cp.alive = false; return out; }
+                cp.beta = cp.beta < 1.0f ? 1.0f : cp.beta;   // beta / min(beta, 1), exactly
+            }
+            return out;
+        }
+        cnt_add(sm, FLR_C_ESCAPES);
+        cp.alive = false;
+        return out;
+    }
+    cp.x = make_float3(cp.x.x + tf * cp.w.x, cp.x.y + tf * cp.w.y, cp.x.z + tf * cp.w.z);
+    const Coeffs k = coeffs_at(m, cp.x, cp.bin);
+    if (k.total > sb) cnt_add(sm, FLR_C_MAJORANT_VIOLATIONS);
+    if (!(b0.b * sb < k.total)) { rc.nulls++; return out; }
+    if (cp.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); cp.alive = false; return out; }
+    cp.n_events++;
+    rc.events++;
+    // emission at this collision through one light sample
+    out.g = light_geometry(S, cp.x, b1.b, b1.c, b1.d);
+    if (out.g.ok) {
+        out.wt = cp.beta * out.g.geom * emission_weight(S, sm, cp.x, cp.bin, out.g.bx, k.total, cp.pb) *
+                 R.film_scale;
+        out.valid = out.wt != 0.0f;
+    }
+    // the event at the emission wavelength: scattering continues, an absorption ends the walk
+    if (!(b0.c * k.total < k.scat)) {
+        cnt_add(sm, b0.c * k.total < k.total - k.bg ? FLR_C_VF_REJECTED : FLR_C_ABSORBED_DEAD);
+        cp.alive = false;
+        return out;
+    }
+    rc.scatters++;
+    {
+        const float z = 1.0f - 2.0f * b0.d;
+        float sn, cs;
+        __sincosf(TWO_PI * b1.a, &sn, &cs);
+        const float r = sqrt_approx(fmaxf(0.0f, 1.0f - z * z));
+        cp.w = make_float3(r * cs, r * sn, z);
+    }
+    cp.iw = inv_dir(cp.w);
+    if (cp.n_events >= R.n_rr) {
+        const float q = fminf(cp.beta, 1.0f);
+        const U4 b2 = draw_rk(R, cp.pid, step, 2u);
+        if (!(b2.b < q)) { cnt_add(sm, FLR_C_RR_KILLS); cp.alive = false; return out; }
+        cp.beta = cp.beta < 1.0f ? 1.0f : cp.beta;
+    }
+    return out;
+}
+
+// Plain form: one thread per camera path, the light sample's transmittance marched inline
+// (ratio tracking with the uniforms of slots 3.. of its collision step).
 __global__ void __launch_bounds__(256) k_trace_camera(SceneDev S, RunDev R)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
     const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
-    const MedS_<false> m{S, sm};
     RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
-    const uint64_t npix = (uint64_t)S.W * (uint64_t)S.H;
-    const float inv_d = 1.0f / (float)S.D;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
-        const uint64_t pid = R.path_offset + i;
+        CamPath cp;
+        cp.pid = R.path_offset + i;
         cnt_add(sm, FLR_C_PATHS);
-        const int pix = (int)(pid % npix);
-        const int px = pix % S.W, py = pix / S.W;
-        const U4 s0 = draw_rk(R, pid, STEP_CAM_SPAWN, 0u);
-        const float fx = ((float)px + s0.a) / (float)S.W, fy = ((float)py + s0.b) / (float)S.H;
-        const int dsel = min((int)(s0.c * (float)S.D), S.D - 1);
-        const int bin = sample_cdf(sm.cdf + dsel * S.B, S.B, s0.d);
-        float pb = 0.0f;
-        for (int d = 0; d < S.D; ++d) pb += emission_pmf(sm, S.B, d, bin);
-        pb *= inv_d;
-        if (!(pb > 0.0f)) continue;
-        float3 o, w;
-        if (S.sensor_kind == FLR_SENSOR_ORTHO) {
-            const float vl = rsqrtf(S.s_view[0] * S.s_view[0] + S.s_view[1] * S.s_view[1] + S.s_view[2] * S.s_view[2]);
-            o = make_float3(S.s_origin[0] + fx * S.cam_U[0] + fy * S.cam_V[0],
-                            S.s_origin[1] + fx * S.cam_U[1] + fy * S.cam_V[1],
-                            S.s_origin[2] + fx * S.cam_U[2] + fy * S.cam_V[2]);
-            w = make_float3(-S.s_view[0] * vl, -S.s_view[1] * vl, -S.s_view[2] * vl);
+        CamStart cs;
+        if (!camera_start(S, R, sm, cp.pid, cs)) continue;
+        cp.x = cs.x;
+        cp.w = cs.w;
+        cp.iw = inv_dir(cp.w);
+        cp.pix = cs.pix;
+        cp.bin = cs.bin;
+        cp.pb = cs.pb;
+        cp.beta = 1.0f;
+        cp.step = 0;
+        cp.n_events = 0;
+        cp.alive = true;
+        while (cp.alive) {
+            const uint32_t step = cp.step;
+            const CamRec r = camera_step(S, R, sm, cp, rc);
+            if (!r.valid) continue;
+            const float T = transmittance<NoSink, false, false, false, 3u>(S, R, sm, r.g.start, r.g.dir, r.g.len,
+                                                                           r.g.bx, cp.pid, step, rc, NoSink{});
+            const float val = r.wt * T;
+            if (val != 0.0f) {
+                atomicAdd(&R.film[(size_t)cp.pix * S.B + cp.bin], val);
+                rc.connections++;
+            }
+        }
+    }
+    block_epilogue(S, R, sm, rc);
+}
+
+// Warp-regrouped form: the lanes' light samples go to a per-warp shared-memory queue and are
+// marched by whole warps, one march per lane, with pull-based claims as in the light tracer's warp
+// form. The marches draw the same uniforms as transmittance(), so both forms give the same film up
+// to the order of fp32 additions.
+constexpr int CQ_CAP = 160;
+constexpr int CQ_DRAIN = 128;
+constexpr int CQ_WORDS = 13;   // start 3, dir 3, len, weight, pixel, bins, pid lo/hi, step
+static_assert(CQ_DRAIN + 31 < CQ_CAP, "camera queue overflow");
+
+__host__ __device__ inline int camera_queue_offset(int B, int block)
+{
+    return ((smem_layout(B, FLR_FORM_PLAIN, block).total_bytes + 15) / 16) * 16;
+}
+
+__host__ __device__ inline int camera_smem_bytes(int B, int block)
+{
+    return camera_queue_offset(B, block) + (block / 32) * (CQ_CAP * CQ_WORDS * 4 + 8);
+}
+
+__global__ void __launch_bounds__(256, 2) k_trace_camera_warp(SceneDev S, RunDev R)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
+    const MedS_<false> m{S, sm};
+    constexpr unsigned FULL = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const unsigned lower = (1u << lane) - 1u;
+    float *qf = reinterpret_cast<float *>(smem_raw + camera_queue_offset(S.B, blockDim.x)) + warp * CQ_CAP * CQ_WORDS;
+    int *tail = reinterpret_cast<int *>(smem_raw + camera_queue_offset(S.B, blockDim.x) +
+                                        (size_t)nwarps * CQ_CAP * CQ_WORDS * 4) + 2 * warp;
+    if (lane == 0) *tail = 0;
+    __syncwarp();
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
+    CamPath cp;
+    cp.alive = false;
+    bool exhausted = false;
+    while (true) {
+        const bool spawn_now = __popc(__ballot_sync(FULL, !cp.alive && !exhausted)) >= SPAWN_MIN ||
+                               __ballot_sync(FULL, cp.alive) == 0u;
+        if (!cp.alive) {
+            if (!exhausted && spawn_now) {
+                const unsigned long long i = atomicAdd(R.work_counter, 1ull);
+                if (i >= R.n_paths) {
+                    exhausted = true;
+                } else {
+                    cp.pid = R.path_offset + i;
+                    cnt_add(sm, FLR_C_PATHS);
+                    CamStart cs;
+                    if (camera_start(S, R, sm, cp.pid, cs)) {
+                        cp.x = cs.x;
+                        cp.w = cs.w;
+                        cp.iw = inv_dir(cp.w);
+                        cp.pix = cs.pix;
+                        cp.bin = cs.bin;
+                        cp.pb = cs.pb;
+                        cp.beta = 1.0f;
+                        cp.step = 0;
+                        cp.n_events = 0;
+                        cp.alive = true;
+                    }
+                }
+            }
         } else {
-            const float X = (2.0f * fx - 1.0f) * S.tan_x, Y = (2.0f * fy - 1.0f) * S.tan_y;
-            const float3 d = make_float3(S.s_view[0] + X * S.s_U[0] + Y * S.s_V[0],
-                                         S.s_view[1] + X * S.s_U[1] + Y * S.s_V[1],
-                                         S.s_view[2] + X * S.s_U[2] + Y * S.s_V[2]);
-            const float dl = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-            o = make_float3(S.s_origin[0], S.s_origin[1], S.s_origin[2]);
-            w = make_float3(d.x * dl, d.y * dl, d.z * dl);
-        }
-        // enter the box; the entry face must be open (walls are opaque from outside)
-        float t_in = -FLT_MAX, t_out = FLT_MAX;
-        int f_in = -1;
-        bool miss = false;
-        {
-            const float os[3] = {o.x, o.y, o.z}, ws[3] = {w.x, w.y, w.z};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (ws[k] == 0.0f) {
-                    if (os[k] < S.lo[k] || os[k] > S.hi[k]) miss = true;
-                    continue;
-                }
-                float ta = (S.lo[k] - os[k]) / ws[k], tb = (S.hi[k] - os[k]) / ws[k];
-                int fa = 2 * k, fb = 2 * k + 1;
-                if (ta > tb) {
-                    const float tt = ta; ta = tb; tb = tt;
-                    const int ff = fa; fa = fb; fb = ff;
-                }
-                if (ta > t_in) { t_in = ta; f_in = fa; }
-                if (tb < t_out) t_out = tb;
+            const uint32_t step = cp.step;
+            const CamRec r = camera_step(S, R, sm, cp, rc);
+            if (r.valid) {
+                const int slot = atomicAdd(tail, 1);
+                float *f = qf + slot;
+                f[0 * CQ_CAP] = r.g.start.x;
+                f[1 * CQ_CAP] = r.g.start.y;
+                f[2 * CQ_CAP] = r.g.start.z;
+                f[3 * CQ_CAP] = r.g.dir.x;
+                f[4 * CQ_CAP] = r.g.dir.y;
+                f[5 * CQ_CAP] = r.g.dir.z;
+                f[6 * CQ_CAP] = r.g.len;
+                f[7 * CQ_CAP] = r.wt;
+                f[8 * CQ_CAP] = __int_as_float(cp.pix);
+                f[9 * CQ_CAP] = __int_as_float(cp.bin | (r.g.bx << 16));
+                f[10 * CQ_CAP] = __uint_as_float((uint32_t)cp.pid);
+                f[11 * CQ_CAP] = __uint_as_float((uint32_t)(cp.pid >> 32));
+                f[12 * CQ_CAP] = __uint_as_float(step);
             }
         }
-        if (miss || !(t_out > t_in) || !(t_out > 0.0f)) continue;
-        float3 x = o;
-        if (t_in > 0.0f) {
-            if (S.wall_mask & (1 << f_in)) continue;
-            x = make_float3(o.x + t_in * w.x, o.y + t_in * w.y, o.z + t_in * w.z);
-        }
-        float3 iw = inv_dir(w);
-        float beta = 1.0f;
-        long long n_events = 0;
-        for (uint32_t step = 0;; ++step) {
-            if ((long long)step >= R.max_steps) { cnt_add(sm, FLR_C_STEP_BUDGET); break; }
-            rc.steps++;
-            const U4 b0 = draw_rk(R, pid, step, 0u);
-            const U4 b1 = draw_rk(R, pid, step, 1u);
-            int face;
-            const float te = exit_distance(m, x, w, iw, face);
-            const float sb = sm.maj[bin];
-            const float tf = sb > 0.0f ? -__logf(1.0f - b0.a) * sm.inv_maj[bin] : FLT_MAX;
-            if (tf >= te) {
-                x = make_float3(x.x + te * w.x, x.y + te * w.y, x.z + te * w.z);
-                if (face >= 0 && (S.wall_mask & (1 << face))) {
-                    if (n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); break; }
-                    n_events++;
-                    rc.events++;
-                    cnt_add(sm, FLR_C_WALL_BOUNCES);
-                    const U4 b2 = draw_rk(R, pid, step, 2u);
-                    if (R.analog) {
-                        if (!(b2.a < S.wall_albedo)) { cnt_add(sm, FLR_C_ABSORBED_DEAD); break; }
+        __syncwarp();
+        const bool any = __any_sync(FULL, cp.alive || !exhausted);
+        const int avail = *tail;
+        if (avail >= CQ_DRAIN || (!any && avail > 0)) {
+            // pull-based drain; claims every second iteration (see the light tracer's warp form)
+            float3 x0, dir;
+            float tl = 0.0f, t = 0.0f, T = 1.0f, isb = 0.0f, wt = 0.0f;
+            int pix = 0, bin = 0, bx = 0, it = 0;
+            uint32_t j = 0, mstep = 0;
+            uint64_t pid = 0;
+            U4 blk = U4{0.f, 0.f, 0.f, 0.f};
+            bool active = false;
+            int claimed = 0;
+            for (uint32_t iter = 0;; ++iter) {
+                const unsigned need = (iter & 1u) == 0u ? __ballot_sync(FULL, !active) : 0u;
+                if (need != 0u && !active) {
+                    const int k = claimed + __popc(need & lower);
+                    if (k < avail) {
+                        const float *f = qf + k;
+                        x0 = make_float3(f[0 * CQ_CAP], f[1 * CQ_CAP], f[2 * CQ_CAP]);
+                        dir = make_float3(f[3 * CQ_CAP], f[4 * CQ_CAP], f[5 * CQ_CAP]);
+                        tl = f[6 * CQ_CAP];
+                        wt = f[7 * CQ_CAP];
+                        pix = __float_as_int(f[8 * CQ_CAP]);
+                        const int bb = __float_as_int(f[9 * CQ_CAP]);
+                        bin = bb & 0xFFFF;
+                        bx = bb >> 16;
+                        pid = ((uint64_t)__float_as_uint(f[11 * CQ_CAP]) << 32) | __float_as_uint(f[10 * CQ_CAP]);
+                        mstep = __float_as_uint(f[12 * CQ_CAP]);
+                        const float sb = sm.maj[bx];
+                        if (!(sb > 0.0f) || S.homogeneous) {
+                            const float Tc = !(sb > 0.0f) ? 1.0f : __expf(-sigma_t_at(m, x0, bx) * tl);
+                            const float val = wt * Tc;
+                            if (val != 0.0f) {
+                                atomicAdd(&R.film[(size_t)pix * S.B + bin], val);
+                                rc.connections++;
+                            }
+                        } else {
+                            t = 0.0f;
+                            T = 1.0f;
+                            isb = sm.inv_maj[bx];
+                            j = 0;
+                            it = 0;
+                            active = true;
+                        }
+                    }
+                }
+                claimed += __popc(need);
+                if (active) {
+                    // one ratio-tracking step (the body of transmittance()'s loop, slots 3..)
+                    if (it >= MAX_CONNECT_STEPS) {
+                        cnt_add(sm, FLR_C_CONNECT_BUDGET);
+                        active = false;
                     } else {
-                        beta *= S.wall_albedo;
-                        if (beta == 0.0f) { cnt_add(sm, FLR_C_ABSORBED_DEAD); break; }
+                        ++it;
+                        if ((j & 3u) == 0u) blk = draw_rk(R, pid, mstep, 3u + (j >> 2));
+                        const uint32_t q = j & 3u;
+                        const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
+                        ++j;
+                        t -= __logf(1.0f - u) * isb;
+                        if (t >= tl) {
+                            const float val = wt * T;
+                            if (val != 0.0f) {
+                                atomicAdd(&R.film[(size_t)pix * S.B + bin], val);
+                                rc.connections++;
+                            }
+                            active = false;
+                        } else {
+                            rc.connect_steps++;
+                            const float3 pnt = make_float3(x0.x + t * dir.x, x0.y + t * dir.y, x0.z + t * dir.z);
+                            const float st = sigma_t_at(m, pnt, bx);
+                            T *= fmaxf(0.0f, 1.0f - st * isb);
+                            if (T < RT_RR_THRESHOLD) {
+                                if ((j & 3u) == 0u) blk = draw_rk(R, pid, mstep, 3u + (j >> 2));
+                                const uint32_t q2 = j & 3u;
+                                const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
+                                ++j;
+                                if (u2 * RT_RR_THRESHOLD < T) T = RT_RR_THRESHOLD;
+                                else active = false;
+                            }
+                        }
                     }
-                    const int ax = face >> 1;
-                    const float sg = (face & 1) ? -1.0f : 1.0f;
-                    if (ax == 0) x.x = (face & 1) ? S.hi[0] : S.lo[0];
-                    else if (ax == 1) x.y = (face & 1) ? S.hi[1] : S.lo[1];
-                    else x.z = (face & 1) ? S.hi[2] : S.lo[2];
-                    w = cosine_dir(b0.d, b1.a, ax, sg);
-                    iw = inv_dir(w);
-                    if (n_events >= R.n_rr) {
-                        const float q = fminf(beta, 1.0f);
-                        if (!(b2.b < q)) { cnt_add(sm, FLR_C_RR_KILLS); break; }
-                        beta = beta < 1.0f ? 1.0f : beta;   // beta / min(beta, 1), exactly
-                    }
-                    continue;
                 }
-                cnt_add(sm, FLR_C_ESCAPES);
-                break;
+                if (!__any_sync(FULL, active) && claimed >= avail) break;
             }
-            x = make_float3(x.x + tf * w.x, x.y + tf * w.y, x.z + tf * w.z);
-            const Coeffs k = coeffs_at(m, x, bin);
-            if (k.total > sb) cnt_add(sm, FLR_C_MAJORANT_VIOLATIONS);
-            if (!(b0.b * sb < k.total)) { rc.nulls++; continue; }
-            if (n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); break; }
-            n_events++;
-            rc.events++;
-            // emission at this collision through one light sample
-            int bx;
-            const float phi = excitation_fluence(S, R, sm, x, b1.b, b1.c, b1.d, pid, step, bx, rc);
-            if (phi > 0.0f) {
-                const Coeffs kx = coeffs_at(m, x, bx);
-                float src = 0.0f;
-                for (int d = 0; d < S.D; ++d) src += sm.qy[d] * emission_pmf(sm, S.B, d, bin) * kx.dye[d];
-                const float val = beta * src * phi * INV_4PI / (k.total * pb) * R.film_scale;
-                if (val != 0.0f) {
-                    atomicAdd(&R.film[(size_t)pix * S.B + bin], val);
-                    rc.connections++;
-                }
-            }
-            // the event at the emission wavelength: scattering continues, an absorption ends the walk
-            if (!(b0.c * k.total < k.scat)) {
-                cnt_add(sm, b0.c * k.total < k.total - k.bg ? FLR_C_VF_REJECTED : FLR_C_ABSORBED_DEAD);
-                break;
-            }
-            rc.scatters++;
-            {
-                const float z = 1.0f - 2.0f * b0.d;
-                float sn, cs;
-                __sincosf(TWO_PI * b1.a, &sn, &cs);
-                const float r = sqrt_approx(fmaxf(0.0f, 1.0f - z * z));
-                w = make_float3(r * cs, r * sn, z);
-            }
-            iw = inv_dir(w);
-            if (n_events >= R.n_rr) {
-                const float q = fminf(beta, 1.0f);
-                const U4 b2 = draw_rk(R, pid, step, 2u);
-                if (!(b2.b < q)) { cnt_add(sm, FLR_C_RR_KILLS); break; }
-                beta = beta < 1.0f ? 1.0f : beta;
-            }
+            __syncwarp();
+            if (lane == 0) *tail = 0;
+            __syncwarp();
         }
+        if (!any) break;
     }
     block_epilogue(S, R, sm, rc);
 }
@@ -2188,9 +2449,19 @@ cudaError_t launch_adjoint_warp(const SceneDev &S, const RunDev &R, const AdjDev
     return cudaGetLastError();
 }
 
-cudaError_t launch_camera(const SceneDev &S, const RunDev &R, int block, cudaStream_t st)
+cudaError_t launch_camera(const SceneDev &S, const RunDev &R, int form, int block, cudaStream_t st)
 {
     if (block <= 0) block = trace_block_default();
+    if (form != FLR_FORM_PLAIN) {
+        const int smem = camera_smem_bytes(S.B, block);
+        cudaError_t e = cudaFuncSetAttribute(k_trace_camera_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_camera_warp, block, smem);
+        if (occ < 1) occ = 1;
+        k_trace_camera_warp<<<(unsigned)(num_sms() * occ), block, smem, st>>>(S, R);
+        return cudaGetLastError();
+    }
     const int smem = trace_smem_bytes(S.B, FLR_FORM_PLAIN, block);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_camera, block, smem);

@@ -188,11 +188,11 @@ class Scene:
 
     def render_camera(self, n_paths=None, path_offset=0, seed=None, medium_id=0, analog=None,
                       n_rr=None, max_events=None, max_steps=None, accumulate=False, block_size=0,
-                      stream=None):
+                      form="wavefront_warp", stream=None):
         """The paper's camera-side estimator of its single-inelastic model (flr_render_camera):
         returns the film tensor [H, W, B] of fluorescence radiance; n_paths and path_offset must
         be multiples of W*H."""
-        p = self._params(n_paths, path_offset, seed, medium_id, "plain", analog, None, n_rr,
+        p = self._params(n_paths, path_offset, seed, medium_id, form, analog, None, n_rr,
                          max_events, max_steps, accumulate, block_size)
         f = self.film_tensor()
         p.film = f.data_ptr()

@@ -28,9 +28,9 @@ def _gpu():
     require_gpu()
 
 
-def gpu_camera(S, K, n_per, seed=None):
-    return [S.render_camera(n_paths=n_per, path_offset=k * n_per, seed=seed).double().cpu().numpy()
-            for k in range(K)]
+def gpu_camera(S, K, n_per, seed=None, form="wavefront_warp"):
+    return [S.render_camera(n_paths=n_per, path_offset=k * n_per, seed=seed, form=form)
+            .double().cpu().numpy() for k in range(K)]
 
 
 def test_slab_closed_form_gpu_camera_and_light_paper_mode():
@@ -51,11 +51,24 @@ def test_slab_closed_form_gpu_camera_and_light_paper_mode():
         assert abs(mt - want.sum()) <= 3.5 * st + 2e-3 * want.sum(), (mt, want.sum(), st)
 
 
-def test_gpu_camera_matches_oracle_camera():
+def test_camera_forms_agree():
+    """The plain and the warp-regrouped camera forms draw the same random numbers for the same
+    paths: the same film up to the order of fp32 additions."""
+    sc = sg.paper_mode_scene(n=32, width=16)
+    S = Scene(sc)
+    n = 256 * 500
+    a = S.render_camera(n_paths=n, seed=4, form="plain").double().cpu().numpy()
+    b = S.render_camera(n_paths=n, seed=4, form="wavefront_warp").double().cpu().numpy()
+    assert np.allclose(a, b, rtol=1e-4, atol=1e-6 * np.abs(a).max())
+    assert a.sum() > 0
+
+
+@pytest.mark.parametrize("form", ["plain", "wavefront_warp"])
+def test_gpu_camera_matches_oracle_camera(form):
     sc = sg.paper_mode_scene(n=16, width=8)
     S = Scene(sc)
     K, n = 16, 64 * 1000
-    g = gpu_camera(S, K, n, seed=3)
+    g = gpu_camera(S, K, n, seed=3, form=form)
     o = [oracle.render_camera(sc, n_paths=n, path_offset=k * n, seed=3)["film"] for k in range(K)]
     for axis in ((0, 1), 2):
         a, sa = batch_mean_se([x.sum(axis=axis) for x in g])
