@@ -135,7 +135,8 @@ typedef struct flr_params {
     float *film;                 /* device [H][W][n_bins] fp32, or NULL                         */
     uint32_t *path_events;       /* device [n_paths] real events per path, or NULL              */
     int accumulate;              /* 0: clear tallies and film first; 1: add to them             */
-    int block_size;              /* threads per block; 0 = library default                     */
+    int block_size;              /* threads per block; 0 = library default (the warp-regrouped
+                                    form and the adjoint's passes use at most 128)              */
     int blocks_per_sm;           /* resident blocks per SM; 0 = occupancy maximum               */
     int regroup_interval;        /* wavefront: tracking steps between connection flushes; 0 auto */
     int macro_cell;              /* > 0: free flights and transmittance marches use local

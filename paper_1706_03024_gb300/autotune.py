@@ -35,12 +35,14 @@ class Result:
 
 
 def default_candidates(has_grid=True, max_cell=8):
-    """Block- or warp-level regrouping, wavefront depth 1..8, blocks of 128 or 256, empty-space
-    cells 0 (off) .. max_cell, and a few local-majorant cell sizes."""
+    """Block- or warp-level regrouping, wavefront depth 1..8, blocks of 128 or 256 (the warp form:
+    128), empty-space cells 0 (off) .. max_cell, and a few local-majorant cell sizes."""
     cells = [0] + ([c for c in (1, 2, 4, 8) if c <= max_cell] if has_grid else [])
     out = []
     for form, block, regroup, skip in itertools.product(("wavefront", "wavefront_warp"), (256, 128),
                                                         (1, 2, 4, 8), cells):
+        if form == "wavefront_warp" and block > 128:
+            continue   # the warp-regrouped form runs blocks of at most 128 threads
         out.append(Candidate(form, block, regroup, skip, 0))
     if has_grid:
         for block, regroup, mc in itertools.product((256,), (2, 4), (4, 8)):

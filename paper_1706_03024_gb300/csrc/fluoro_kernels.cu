@@ -980,11 +980,14 @@ struct SmemLayout {
 
 // Per-warp connection queue of the warp-regrouped form: capacity and drain threshold. A drain starts
 // once WQ_DRAIN records wait; one tracking round adds at most 32, so the queue never wraps. Longer
-// queues drain less often and amortise each drain's tail: 416 records of 32 B per warp fill the
-// shared memory of two 256-thread blocks per SM (measured on the Cornell box: 128 -> 256 -> 320
-// records gave 26.0 -> 24.0 -> 23.6 ms per step).
-constexpr int WQ_CAP = 416;
-constexpr int WQ_DRAIN = 384;
+// queues drain less often and amortise each drain's tail (measured on the Cornell box: 128 -> 256 ->
+// 320 records gave 26.0 -> 24.0 -> 23.6 ms per step); 320 records of 32 B per warp let five blocks
+// of 128 threads (WARP_BLOCK, at most 102 registers) share an SM's shared memory, which measured
+// 3 % faster than two blocks of 256 with 416-record queues. The adjoint's and the local-majorant
+// instances keep four blocks (128 registers): with five they spill.
+constexpr int WARP_BLOCK = 128;   // threads per block of the warp-regrouped form
+constexpr int WQ_CAP = 320;
+constexpr int WQ_DRAIN = 288;
 constexpr int SPAWN_MIN = 8;   // lanes that start new paths together
 static_assert(WQ_DRAIN + 31 < WQ_CAP, "warp queue overflow");
 
@@ -1497,7 +1500,7 @@ __device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, c
 }
 
 template <int MODE, bool MC>
-__global__ void __launch_bounds__(256, 2) k_trace_wavefront_warp(SceneDev S, RunDev R, AdjDev A)
+__global__ void __launch_bounds__(WARP_BLOCK, (MODE == WM_RENDER && !MC) ? 5 : 4) k_trace_wavefront_warp(SceneDev S, RunDev R, AdjDev A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT_WARP, blockDim.x);
@@ -2401,6 +2404,7 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
                          cudaStream_t st)
 {
     if (block <= 0) block = trace_block_default();
+    if (form == FLR_FORM_WAVEFRONT_WARP) block = std::min(block, WARP_BLOCK);
     const int smem = trace_smem_bytes(S.B, form, block);
     const cudaError_t ea = allow_smem(form, smem);
     if (ea != cudaSuccess) return ea;
@@ -2467,6 +2471,7 @@ cudaError_t launch_adjoint_warp(const SceneDev &S, const RunDev &R, const AdjDev
                                 int block, int blocks_per_sm, cudaStream_t st)
 {
     if (block <= 0) block = trace_block_default();
+    block = std::min(block, WARP_BLOCK);
     const int smem = trace_smem_bytes(S.B, FLR_FORM_WAVEFRONT_WARP, block);
     const cudaError_t ea = allow_smem(FLR_FORM_WAVEFRONT_WARP, smem);
     if (ea != cudaSuccess) return ea;
