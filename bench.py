@@ -350,6 +350,73 @@ def bench_paper(args, local, rank, flush, stream, barrier, reduce_max, reduce_su
             "launches_per_step": 1}
 
 
+def bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum):
+    """The light-sheet workload at full size: 256^3 x 4 blob dyes (268 MB of grids, larger than
+    the L2), albedo 0.999, a 0.05 cm sheet at 488 nm entering the -x face, 1024x1024x81 ortho film
+    (340 MB) viewing it from +z, 64 paths per pixel (67,108,864 paths). The warp-regrouped form in
+    the bench's launch shape, against the plain kernel on the first eighth of the same path ids
+    (same estimator: events/s compares at equal RMSE). Rooflines: ALU from the counters, and HBM
+    on the grid gathers (16 bytes, one float4 of 4 dyes, per tracking and ratio-tracking step)."""
+    import torch
+    from paper_1706_03024_gb300.scene import Scene
+
+    sc = sg.cfg5_light_sheet()
+    n = int(args.sheet_paths) if args.sheet_paths else sc["params"]["n_paths"]
+    off = rank * n
+    S = Scene(sc, device=local)
+    kw = {"form": "wavefront_warp", "block_size": 128, "regroup": 1, "skip_cell": 0,
+          "macro_cell": 0}
+    n_plain = max(n // 8, 1)
+    S.render(n_paths=n, path_offset=off, **kw)                     # warm-up
+    S.render(n_paths=n_plain, path_offset=off, form="plain")
+    torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        ms, counters = [], None
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            counters = S.read()["counters"]
+            ms.append(a.elapsed_time(b))
+        return ms, counters
+
+    barrier()
+    ms, c = timed(lambda: S.render(n_paths=n, path_offset=off, **kw), args.sheet_steps)
+    ms_p, c_p = timed(lambda: S.render(n_paths=n_plain, path_offset=off, form="plain"), 1)
+    step_ms = reduce_max(sum(ms) / len(ms))
+    plain_ms = reduce_max(ms_p[0])
+    value = reduce_sum(float(c["events"])) / (step_ms / 1000.0)
+    plain_value = reduce_sum(float(c_p["events"])) / (plain_ms / 1000.0)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peaks = measured_peaks()
+    peak_ops = sms * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    t = sum(ms) / len(ms) / 1000.0
+    ops = algorithmic_ops(c)
+    gathers = c["steps"] + c["connect_steps"]
+    D = int(sc["dyes"]["abs_shape"].shape[0])
+    alg_bytes = 4 * D * gathers
+    return {"workload": "light sheet: 256^3 x 4 blob dyes, albedo 0.999, 0.05 cm sheet at 488 nm, "
+                        f"1024x1024x81 ortho film, {n} paths",
+            "launch": kw, "events_per_s": value, "paths_per_s": reduce_sum(float(n)) / (step_ms / 1000.0),
+            "ms_per_step": step_ms, "steps": len(ms), "ms_steps": [round(v, 3) for v in ms],
+            "plain_events_per_s": plain_value, "plain_ms": plain_ms, "plain_paths": n_plain,
+            "speedup_vs_plain": value / plain_value,
+            "per_path": {k: c[k] / n for k in ("events", "steps", "connections", "connect_steps")},
+            "roofline_alu": {"bound": "alu", "achieved": ops / t / 1e12, "peak": peak_ops / 1e12,
+                             "unit": "Tops/s", "frac": ops / t / peak_ops},
+            "roofline_hbm_gathers": {"bound": "hbm", "achieved": alg_bytes / t / 1e9, "peak": hbm,
+                                     "unit": "GB/s", "frac": alg_bytes / t / 1e9 / hbm,
+                                     "sector_frac": 8 * alg_bytes / D / t / 1e9 / hbm,
+                                     "bytes_per_gather": 4 * D,
+                                     "traffic": kernel_traffic(
+                                         "trace_wavefront_warp_sheet_traffic.json")},
+            "launches_per_step": 1}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -377,14 +444,14 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     offset = rank * n_paths  # each rank its own path-id range
 
-    # launch configuration of the optimised form: autotuned on an eighth of the paths (outside
+    # launch configuration of the optimised form: autotuned on half of the paths (outside
     # the timed region), or taken from the command line
     tuned = {"form": args.form, "block_size": 0, "regroup": args.regroup,
              "skip_cell": args.skip_cell, "macro_cell": args.macro_cell}
     tune_info = None
     if args.autotune:
         from paper_1706_03024_gb300.autotune import tune_render
-        res = tune_render(S, max(n_paths // 8, 1 << 16), path_offset=offset)
+        res = tune_render(S, max(n_paths // 2, 1 << 16), path_offset=offset, repeats=3)
         tuned = res.best.kwargs()
         tune_info = {"chosen": tuned, "candidates": len({c for c, _ in res.trials}),
                      "best_events_per_s_on_slice": max(v for _, v in res.trials)}
@@ -484,6 +551,9 @@ def run_ours(args):
     paper = None
     if not args.no_paper:
         paper = bench_paper(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
+    sheet = None
+    if not args.no_sheet:
+        sheet = bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
     adjoint = None
     if not args.no_adjoint:
         adjoint = bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
@@ -561,6 +631,7 @@ def run_ours(args):
                 "batched": batched,
                 "adjoint": adjoint,
                 "paper_model": paper,
+                "light_sheet": sheet,
             },
             "counters_per_step": cnt_w,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
@@ -572,7 +643,8 @@ def run_ours(args):
             "gpu_launches": args.steps + len(ms_p)
             + (0 if batched is None else batched["steps"] + batched["plain_launches"])
             + (0 if adjoint is None else adjoint["launches_per_step"] * args.adjoint_steps)
-            + (0 if paper is None else 2 * args.paper_steps),
+            + (0 if paper is None else 2 * args.paper_steps)
+            + (0 if sheet is None else sheet["steps"] + 1),
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -602,7 +674,7 @@ def main():
     ap.add_argument("--paths", type=int, default=0,
                     help="override the path count (small profiling cases only)")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-paths", type=int, default=1 << 17)
+    ap.add_argument("--cpu-paths", type=int, default=1 << 21)
     ap.add_argument("--ref-paths", type=int, default=1 << 16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -615,6 +687,11 @@ def main():
                     help="skip the paper's own (camera-side) estimator of its single-inelastic model")
     ap.add_argument("--paper-steps", type=int, default=3)
     ap.add_argument("--adjoint-steps", type=int, default=3)
+    ap.add_argument("--no-sheet", action="store_true",
+                    help="skip the full-size light-sheet workload (256^3 x 4 grids, 67M paths)")
+    ap.add_argument("--sheet-steps", type=int, default=2)
+    ap.add_argument("--sheet-paths", type=int, default=0,
+                    help="override the light-sheet path count (small profiling cases only)")
     ap.add_argument("--adjoint-paths", type=int, default=0,
                     help="override the adjoint path count (small profiling cases only)")
     args = ap.parse_args()

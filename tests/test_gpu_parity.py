@@ -334,15 +334,7 @@ def test_invalid_arguments_are_rejected():
 # Full-size workload (the benchmarked configuration): sampled paths and invariants
 
 
-def test_cfg2_full_size_sampled_paths_and_invariants():
-    sc = sg.cfg2_cornell_box()  # 512 x 512 pinhole, 16 spp, 128^3 grids
-    n = sc["params"]["n_paths"]
-    assert n == 512 * 512 * 16
-    S = Scene(sc)
-    pe = torch.zeros(n, dtype=torch.int32, device="cuda")
-    film = S.render(form="wavefront", path_events=pe)
-    r = S.read()
-    c = r["counters"]
+def _full_size_invariants(c, n, film):
     ends = (c["escapes"] + c["absorbed_dead"] + c["rr_kills"] + c["cap_hits"] + c["step_budget"]
             + c["vf_rejected"])
     assert c["paths"] == n and ends == n
@@ -350,6 +342,24 @@ def test_cfg2_full_size_sampled_paths_and_invariants():
         assert c[name] == 0, name
     f = film.double()
     assert torch.isfinite(f).all() and (f >= 0).all() and f.sum() > 0
+
+
+# the benchmarked launch shape: warp-regrouped form, blocks of 128, one tracking step per round
+BENCH_LAUNCH = {"form": "wavefront_warp", "block_size": 128, "regroup": 1}
+
+
+@pytest.mark.parametrize("launch", [{"form": "wavefront"}, dict(BENCH_LAUNCH, skip_cell=1)],
+                         ids=["wavefront", "bench_launch"])
+def test_cfg2_full_size_sampled_paths_and_invariants(launch):
+    sc = sg.cfg2_cornell_box()  # 512 x 512 pinhole, 16 spp, 128^3 grids
+    n = sc["params"]["n_paths"]
+    assert n == 512 * 512 * 16
+    S = Scene(sc)
+    pe = torch.zeros(n, dtype=torch.int32, device="cuda")
+    film = S.render(path_events=pe, **launch)
+    r = S.read()
+    c = r["counters"]
+    _full_size_invariants(c, n, film)
     # sampled paths: the oracle traces single paths with the same ids
     rng = np.random.default_rng(2)
     ids = np.sort(rng.choice(n, size=200, replace=False))
@@ -363,7 +373,40 @@ def test_cfg2_full_size_sampled_paths_and_invariants():
     # integrated escape through the open front vs an oracle sample of the same paths
     o = oracle.render(sc, n_paths=65536, film=False)
     S2 = Scene(sc)
-    S2.render(n_paths=65536, film=False, form="wavefront")
+    S2.render(n_paths=65536, film=False, **launch)
     g = S2.read()
+    for key in ("face", "absorbed", "emitted"):
+        assert compare_integrated(g[key].sum(-1), o[key].sum(-1), rel=1e-2) <= 1e-2, key
+
+
+def test_cfg5_light_sheet_full_size_sampled_paths_and_invariants():
+    """The light-sheet workload at full size in the benchmarked launch shape: 256^3 x 4 grids
+    (larger than the L2), 1024 x 1024 x 81 film, 67,108,864 paths. Bookkeeping and film checks on
+    every path; per-path event counts of sampled path ranges against the oracle; integrated
+    tallies of the first 32,768 paths against the oracle's same paths."""
+    sc = sg.cfg5_light_sheet()
+    n = sc["params"]["n_paths"]
+    assert n == 1024 * 1024 * 64
+    S = Scene(sc)
+    pe = torch.zeros(n, dtype=torch.int32, device="cuda")
+    launch = dict(BENCH_LAUNCH, skip_cell=0)
+    film = S.render(path_events=pe, **launch)
+    c = S.read()["counters"]
+    _full_size_invariants(c, n, film)
+    assert film.shape[-1] == 81 and film.shape[0] * film.shape[1] == 1024 * 1024
+    ev = pe.cpu().numpy().astype(np.uint32)
+    assert int(ev.astype(np.int64).sum()) == c["events"]
+    rng = np.random.default_rng(3)
+    starts = np.sort(rng.choice(n // 32, size=8, replace=False)) * 32
+    same = total = 0
+    for s0 in starts:
+        o = oracle.render(sc, n_paths=32, path_offset=int(s0), film=False, path_events=True)
+        same += int((o["path_events"] == ev[s0:s0 + 32]).sum())
+        total += 32
+    assert same >= 0.95 * total, (same, total)
+    m = 32768
+    o = oracle.render(sc, n_paths=m, film=False)
+    S.render(n_paths=m, film=False, **launch)
+    g = S.read()
     for key in ("face", "absorbed", "emitted"):
         assert compare_integrated(g[key].sum(-1), o[key].sum(-1), rel=1e-2) <= 1e-2, key
