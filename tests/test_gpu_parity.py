@@ -367,11 +367,11 @@ def test_cfg2_full_size_sampled_paths_and_invariants(launch):
     same = 0
     for pid in ids:
         o = oracle.render(sc, n_paths=1, path_offset=int(pid), film=False, path_events=True,
-                          n_threads=1)
+                          n_threads=1, skip_cell=launch.get("skip_cell", 0))
         same += int(o["path_events"][0] == ev[pid])
     assert same >= 0.95 * len(ids), same
     # integrated escape through the open front vs an oracle sample of the same paths
-    o = oracle.render(sc, n_paths=65536, film=False)
+    o = oracle.render(sc, n_paths=65536, film=False, skip_cell=launch.get("skip_cell", 0))
     S2 = Scene(sc)
     S2.render(n_paths=65536, film=False, **launch)
     g = S2.read()
