@@ -60,6 +60,7 @@ typedef struct {
     double dir[3];      /* propagation direction (collimated) or surface normal (Lambertian) */
     double lambda_nm;   /* spectral line */
     double power;       /* relative power; lines are chosen in proportion (p(lambda_x), Eq. 12) */
+    int group;          /* lines of one source (the same geometry) share a group id             */
 } or_emitter;
 
 typedef struct {
@@ -132,6 +133,9 @@ typedef struct {
      * dye absorption ends the path (V_f of Eq. 9), and only vertices after the emission connect
      * to the sensor (the film holds fluorescence only). */
     int paper_mode;
+    /* > 0: hero-wavelength paths carrying up to `hero` wavelengths (1..4), combined by spectral
+     * multiple importance sampling; see trace_path_hero. 0: one wavelength per path. */
+    int hero;
 } or_params;
 
 typedef struct {
@@ -1007,6 +1011,306 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
     return (uint32_t)n_events;
 }
 
+
+/* ---------------------------------------------------------------------------------------- */
+/* Hero-wavelength paths (Wilkie et al., "Hero wavelength spectral sampling", EGSR 2014, cited in
+ * the paper's Sec. 3 as a way to cut the cost of per-wavelength transport).
+ *
+ * A path carries a set of up to C wavelengths. One of them, the hero, drives every sampling
+ * decision exactly as a single-wavelength path would; the others ride along, and every tally is
+ * split among the members by the balance heuristic of spectral MIS. The set is a block of a fixed
+ * partition of the wavelengths that holds the hero, so that any member, had it been drawn as the
+ * hero, would have carried the same set:
+ *   - at the source, the lines of the hero's source (same geometry) in index order, cut into
+ *     blocks of C lines; line k is drawn with probability P_k (its power share);
+ *   - after a re-emission by dye d, the bins [C floor(b/C), C floor(b/C) + C) around the drawn bin
+ *     b; bin k is drawn with probability p_d(k), the emission pmf realised by the fp32 CDF.
+ * With P(k) the probability that member k is drawn as the hero and p(path | k) the probability
+ * density of the decisions taken since the set was drawn, evaluated at member k's wavelength,
+ * the balance-heuristic estimate for member j is W * q_j with
+ *     q_j = P(j) p(path | j) / sum_k P(k) p(path | k),
+ * W the hero's ordinary path weight. Free flights are drawn against the set's majorant
+ * sigma_bar = max_k sigma_bar(lambda_k), so distances and directions have the same density for all
+ * members; a null collision at x has probability (sigma_bar - sigma_t(x, lambda_k)) / sigma_bar,
+ * a scattering sigma_s / sigma_bar (the same for all: scattering is grey), a dye absorption
+ * sigma_a,d(x, lambda_k) / sigma_bar, a background absorption sigma_a0 / sigma_bar and a wall
+ * bounce the flat albedo. Hence q changes only at null collisions (and, for the absorbed tally,
+ * at a dye absorption). A re-emission's outcome does not depend on which member was absorbed
+ * (QY_d and the emission spectrum belong to the dye), so the path goes on with weight W QY_d and
+ * a fresh set. With C = 1 the estimator is the single-wavelength one, decision for decision. */
+static double emission_pmf(const tables *t, int d, int b);
+
+typedef struct {
+    int n;                  /* members                                                         */
+    int hero;               /* index of the hero among them                                    */
+    int bin[4];
+    double q[4];            /* balance-heuristic weights, sum 1                                */
+    double sb;              /* the set's majorant                                              */
+} hero_set;
+
+static void hero_majorant(const tables *t, hero_set *h)
+{
+    h->sb = 0.0;
+    for (int k = 0; k < h->n; ++k) if (t->majorant[h->bin[k]] > h->sb) h->sb = t->majorant[h->bin[k]];
+}
+
+static void hero_normalise(hero_set *h)
+{
+    double z = 0.0;
+    for (int k = 0; k < h->n; ++k) z += h->q[k];
+    for (int k = 0; k < h->n; ++k) h->q[k] /= z;
+}
+
+static double line_pmf(const tables *t, int k)
+{
+    return (double)t->em_cdf32[k] - (k > 0 ? (double)t->em_cdf32[k - 1] : 0.0);
+}
+
+/* The hero's source lines, blocks of C in index order. */
+static void hero_lines(const or_scene *s, const tables *t, int ek, int C, hero_set *h)
+{
+    int idx[OR_MAX_EMITTERS], m = 0, pos = 0;
+    for (int k = 0; k < s->n_emitters; ++k)
+        if (s->emitters[k].group == s->emitters[ek].group) {
+            if (k == ek) pos = m;
+            idx[m++] = k;
+        }
+    int first = (pos / C) * C;
+    h->n = 0;
+    for (int k = first; k < m && k < first + C; ++k) {
+        if (idx[k] == ek) h->hero = h->n;
+        h->bin[h->n] = t->em_bin[idx[k]];
+        h->q[h->n] = line_pmf(t, idx[k]);
+        h->n++;
+    }
+    hero_normalise(h);
+    hero_majorant(t, h);
+}
+
+/* The emission block around bin b of dye d. */
+static void hero_emission(const tables *t, int d, int b, int C, hero_set *h)
+{
+    int first = (b / C) * C;
+    h->n = 0;
+    for (int k = first; k < t->B && k < first + C; ++k) {
+        if (k == b) h->hero = h->n;
+        h->bin[h->n] = k;
+        h->q[h->n] = emission_pmf(t, d, k);
+        h->n++;
+    }
+    hero_normalise(h);
+    hero_majorant(t, h);
+}
+
+/* Sensor connection of a vertex for every member: the geometry is shared, the transmittance is
+ * each member's (exact optical depth, Eq. 6); member k adds w q_k f T_k geom. */
+static void connect_sensor_hero(const or_scene *s, const tables *t, const double x[3],
+                                const hero_set *h, double w, vtx_kind vk, double *film, uint64_t *cnt)
+{
+    const or_sensor *c = &s->sensor;
+    if (c->kind == 0 || film == NULL) return;
+    double dir[3], geom, r2 = 0.0;
+    int px, py;
+    if (c->kind == 1) {
+        for (int k = 0; k < 3; ++k) dir[k] = c->view[k];
+        double d[3] = { x[0] - c->origin[0], x[1] - c->origin[1], x[2] - c->origin[2] };
+        double uu = c->U[0] * c->U[0] + c->U[1] * c->U[1] + c->U[2] * c->U[2];
+        double vv = c->V[0] * c->V[0] + c->V[1] * c->V[1] + c->V[2] * c->V[2];
+        double su = (d[0] * c->U[0] + d[1] * c->U[1] + d[2] * c->U[2]) / uu;
+        double sv = (d[0] * c->V[0] + d[1] * c->V[1] + d[2] * c->V[2]) / vv;
+        if (!(su >= 0.0 && su < 1.0 && sv >= 0.0 && sv < 1.0)) return;
+        px = (int)floor(su * c->width);
+        py = (int)floor(sv * c->height);
+        if (px >= c->width || py >= c->height) return;
+        geom = 1.0 / t->A_pix;
+    } else {
+        double v[3] = { x[0] - c->origin[0], x[1] - c->origin[1], x[2] - c->origin[2] };
+        r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        double r = sqrt(r2);
+        double zf = v[0] * c->view[0] + v[1] * c->view[1] + v[2] * c->view[2];
+        if (!(zf > 0.0)) return;
+        double X = (v[0] * c->U[0] + v[1] * c->U[1] + v[2] * c->U[2]) / zf;
+        double Y = (v[0] * c->V[0] + v[1] * c->V[1] + v[2] * c->V[2]) / zf;
+        double sx = 0.5 * (X / (t->tan_half * t->aspect) + 1.0);
+        double sy = 0.5 * (Y / t->tan_half + 1.0);
+        if (!(sx >= 0.0 && sx < 1.0 && sy >= 0.0 && sy < 1.0)) return;
+        px = (int)floor(sx * c->width);
+        py = (int)floor(sy * c->height);
+        if (px >= c->width || py >= c->height) return;
+        for (int k = 0; k < 3; ++k) dir[k] = -v[k] / r;
+        double cos_t = zf / r;
+        geom = 1.0 / (t->A_pix * r2 * cos_t * cos_t * cos_t);
+    }
+    double f;
+    if (vk.lambertian) {
+        double co = vk.sign * dir[vk.axis];
+        if (!(co > 0.0)) return;
+        f = co / OR_PI;
+    } else {
+        f = 1.0 / (4.0 * OR_PI);
+    }
+    int face;
+    double tl = exit_distance(s, x, dir, &face);
+    if (face < 0) return;
+    if (s->wall_mask & (1 << face)) return;
+    if (c->kind == 2 && tl * tl > r2) return;
+    for (int k = 0; k < h->n; ++k) {
+        if (h->q[k] == 0.0) continue;
+        double T = exp(-optical_depth(s, t, x, dir, tl, h->bin[k]));
+        size_t idx = ((size_t)py * c->width + px) * t->B + h->bin[k];
+#pragma omp atomic
+        film[idx] += w * h->q[k] * f * T * geom;
+    }
+    cnt[OC_CONNECTIONS]++;
+}
+
+static uint32_t trace_path_hero(const or_scene *s, const tables *t, const or_params *p,
+                                uint64_t pid, local_tally *lt, double *film)
+{
+    uint64_t *cnt = lt->cnt;
+    cnt[OC_PATHS]++;
+    const int C = p->hero;
+    block4 S0 = rng_block(p->seed, p->medium_id, pid, STEP_SPAWN, 0);
+    int ek = sample_emitter(t, s->n_emitters, S0.u[0]);
+    const or_emitter *em = &s->emitters[ek];
+    hero_set h;
+    hero_lines(s, t, ek, C, &h);
+    double x[3], w[3];
+    for (int k = 0; k < 3; ++k) x[k] = em->origin[k] + S0.u[1] * em->eu[k] + S0.u[2] * em->ev[k];
+    double wt = 1.0;
+    if (em->kind == 1) {
+        block4 S1 = rng_block(p->seed, p->medium_id, pid, STEP_SPAWN, 1);
+        int ax; double sg;
+        normal_axis(em->dir, &ax, &sg);
+        cosine_dir(S0.u[3], S1.u[0], ax, sg, w);
+        vtx_kind vk = { 1, ax, sg };
+        connect_sensor_hero(s, t, x, &h, wt, vk, film, cnt);
+    } else {
+        for (int k = 0; k < 3; ++k) w[k] = em->dir[k];
+    }
+    int64_t n_events = 0;
+    int n_inel = 0;
+    int fl = 0;
+    for (int64_t step = 0;; ++step) {
+        if (step >= p->max_steps) { cnt[OC_STEP_BUDGET]++; break; }
+        cnt[OC_STEPS]++;
+        block4 B0 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 0);
+        const int hb = h.bin[h.hero];
+        int face;
+        double te = exit_distance(s, x, w, &face);
+        double sb = h.sb;
+        double tf = sb > 0.0 ? -log(1.0 - B0.u[0]) / sb : INFINITY;
+        if (tf >= te) {
+            for (int k = 0; k < 3; ++k) x[k] += te * w[k];
+            if (s->wall_mask & (1 << face)) {
+                if (n_events == p->max_events) { cnt[OC_CAP_HITS]++; break; }
+                n_events++;
+                cnt[OC_EVENTS]++;
+                cnt[OC_WALL_BOUNCES]++;
+                block4 B1 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 1);
+                if (p->analog) {
+                    if (!(B1.u[3] < s->wall_albedo)) { cnt[OC_ABSORBED_DEAD]++; break; }
+                } else {
+                    wt *= s->wall_albedo;
+                    if (wt == 0.0) { cnt[OC_ABSORBED_DEAD]++; break; }
+                }
+                int ax = face / 2;
+                double sg = (face & 1) ? -1.0 : 1.0;
+                x[ax] = (face & 1) ? s->hi[ax] : s->lo[ax];
+                cosine_dir(B0.u[2], B0.u[3], ax, sg, w);
+                vtx_kind vk = { 1, ax, sg };
+                connect_sensor_hero(s, t, x, &h, wt, vk, film, cnt);
+                if (n_events >= p->n_rr) {
+                    double q = wt < 1.0 ? wt : 1.0;
+                    if (!(B1.u[2] < q)) { cnt[OC_RR_KILLS]++; break; }
+                    wt /= q;
+                }
+                continue;
+            }
+            for (int k = 0; k < h.n; ++k) lt->face[fl][face][h.bin[k]] += wt * h.q[k];
+            cnt[OC_ESCAPES]++;
+            break;
+        }
+        for (int k = 0; k < 3; ++k) x[k] += tf * w[k];
+        coeffs c = coeffs_at_p(s, t, x, hb, 0);
+        if (c.total > sb) cnt[OC_MAJORANT_VIOLATIONS]++;
+        if (!(B0.u[1] * sb < c.total)) {
+            cnt[OC_NULLS]++;
+            /* member k's null probability over the hero's */
+            for (int k = 0; k < h.n; ++k) {
+                if (k == h.hero) continue;
+                double ck = coeffs_at_p(s, t, x, h.bin[k], 0).total;
+                if (ck > sb) cnt[OC_MAJORANT_VIOLATIONS]++;
+                h.q[k] *= (sb - ck) / (sb - c.total);
+            }
+            hero_normalise(&h);
+            if (t->sk && c.total == 0.0) {
+                int f2;
+                double te2 = exit_distance(s, x, w, &f2);
+                double tl = empty_cube_exit(s, t, x, w);
+                if (tl > te2) tl = te2;
+                for (int k = 0; k < 3; ++k) x[k] += tl * w[k];
+            }
+            continue;
+        }
+        if (n_events == p->max_events) { cnt[OC_CAP_HITS]++; break; }
+        n_events++;
+        cnt[OC_EVENTS]++;
+        block4 B1 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 1);
+        double ue = B0.u[2] * c.total;
+        double acc = c.scat;
+        int ev = -1;
+        if (!(ue < acc)) {
+            ev = s->n_dyes;
+            for (int d = 0; d < s->n_dyes; ++d) {
+                acc += c.dye[d];
+                if (ue < acc) { ev = d; break; }
+            }
+        }
+        if (ev < 0) {
+            cnt[OC_SCATTERS]++;
+            iso_dir(B0.u[3], B1.u[0], w);
+            vtx_kind vk = { 0, 0, 0.0 };
+            connect_sensor_hero(s, t, x, &h, wt, vk, film, cnt);
+        } else if (ev < s->n_dyes) {
+            cnt[OC_DYE_ABSORPTIONS]++;
+            /* the absorbed tally: member k's probability of this dye absorption over the hero's */
+            hero_set ha = h;
+            for (int k = 0; k < h.n; ++k)
+                if (k != h.hero) ha.q[k] *= coeffs_at_p(s, t, x, h.bin[k], 0).dye[ev] / c.dye[ev];
+            hero_normalise(&ha);
+            for (int k = 0; k < h.n; ++k) lt->absorbed[ev][h.bin[k]] += wt * ha.q[k];
+            if (p->max_inelastic >= 0 && n_inel >= p->max_inelastic) { cnt[OC_VF_REJECTED]++; break; }
+            if (p->analog) {
+                if (!(B1.u[3] < t->qy[ev])) { cnt[OC_ABSORBED_DEAD]++; break; }
+            } else {
+                wt *= t->qy[ev];
+                if (wt == 0.0) { cnt[OC_ABSORBED_DEAD]++; break; }
+            }
+            int b = sample_emission_bin(t, ev, B1.u[1]);
+            hero_emission(t, ev, b, C, &h);
+            for (int k = 0; k < h.n; ++k) lt->emitted[ev][h.bin[k]] += wt * h.q[k];
+            cnt[OC_EMISSIONS]++;
+            n_inel++;
+            fl = 1;
+            iso_dir(B0.u[3], B1.u[0], w);
+            vtx_kind vk = { 0, 0, 0.0 };
+            connect_sensor_hero(s, t, x, &h, wt, vk, film, cnt);
+        } else {
+            /* grey background absorption: the weights stay */
+            for (int k = 0; k < h.n; ++k) lt->absorbed[s->n_dyes][h.bin[k]] += wt * h.q[k];
+            cnt[OC_ABSORBED_DEAD]++;
+            break;
+        }
+        if (n_events >= p->n_rr) {
+            double q = wt < 1.0 ? wt : 1.0;
+            if (!(B1.u[2] < q)) { cnt[OC_RR_KILLS]++; break; }
+            wt /= q;
+        }
+    }
+    return (uint32_t)n_events;
+}
+
 /* ---------------------------------------------------------------------------------------- */
 /* Exported API (ctypes). Return 0 on success, negative on invalid input. */
 
@@ -1016,6 +1320,9 @@ int or_render(const or_scene *s, const or_params *p, or_result *r)
     if (s->n_bins <= 0 || s->n_bins > OR_MAX_BINS) return -1;
     if (s->n_dyes < 0 || s->n_dyes > OR_MAX_DYES) return -1;
     if (s->n_emitters <= 0 || s->n_emitters > OR_MAX_EMITTERS) return -1;
+    if (p->hero < 0 || p->hero > 4) return -1;
+    if (p->hero > 0 && (p->macro_cell > 0 || p->paper_mode || p->frozen || p->pert_dye >= 0 ||
+                        p->pert_sigma_s != 0.0)) return -1;
     tables *t = (tables *)malloc(sizeof(tables));
     build_tables(s, t);
     apply_params(t, p);
@@ -1036,7 +1343,9 @@ int or_render(const or_scene *s, const or_params *p, or_result *r)
         local_tally *lt = (local_tally *)calloc(1, sizeof(local_tally));
 #pragma omp for schedule(dynamic, 64)
         for (int64_t i = 0; i < N; ++i) {
-            uint32_t ne = trace_path(s, t, p, p->path_offset + (uint64_t)i, lt, r->film, NULL);
+            uint32_t ne = p->hero > 0
+                ? trace_path_hero(s, t, p, p->path_offset + (uint64_t)i, lt, r->film)
+                : trace_path(s, t, p, p->path_offset + (uint64_t)i, lt, r->film, NULL);
             if (r->path_events) r->path_events[i] = ne;
         }
 #pragma omp critical

@@ -32,7 +32,7 @@ MAX_EMITTERS = 32
 class Emitter(C.Structure):
     _fields_ = [("kind", C.c_int), ("origin", C.c_double * 3), ("eu", C.c_double * 3),
                 ("ev", C.c_double * 3), ("dir", C.c_double * 3), ("lambda_nm", C.c_double),
-                ("power", C.c_double)]
+                ("power", C.c_double), ("group", C.c_int)]
 
 
 class Sensor(C.Structure):
@@ -63,7 +63,7 @@ class Params(C.Structure):
                 ("max_steps", C.c_int64), ("majorant_scale", C.c_double), ("frozen", C.c_int),
                 ("pert_dye", C.c_int), ("pert_voxel", C.c_int64), ("pert_delta", C.c_double),
                 ("pert_sigma_s", C.c_double), ("macro_cell", C.c_int), ("skip_cell", C.c_int),
-                ("paper_mode", C.c_int)]
+                ("paper_mode", C.c_int), ("hero", C.c_int)]
 
 
 class Result(C.Structure):
@@ -145,9 +145,10 @@ class _SceneHolder:
         self.solvent = (np.ascontiguousarray(md["solvent"], dtype=np.uint8)
                         if md.get("solvent") is not None else None)
         ems = []
-        for src in scene["sources"]:
+        for gi, src in enumerate(scene["sources"]):
             for lam, pw in zip(src["lines_nm"], src["power"]):
                 e = Emitter()
+                e.group = gi
                 e.kind = 0 if src["kind"] == "collimated" else 1
                 e.origin[:] = src["origin"]
                 e.eu[:] = src["eu"]
@@ -204,7 +205,7 @@ class _SceneHolder:
 def render(scene, n_paths=None, path_offset=0, seed=None, medium_id=0, n_threads=0,
            analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
            film=True, path_events=False, majorant_scale=1.0, frozen=False, pert=None,
-           macro_cell=0, skip_cell=0, paper_mode=False):
+           macro_cell=0, skip_cell=0, paper_mode=False, hero=0):
     """Run the oracle; returns a dict of fp64 tallies normalised per launched path:
     face [2,6,B], absorbed [D+1,B], emitted [D,B], film [H,W,B] (or None), counters (dict),
     path_events u32[n] (or None).
@@ -212,7 +213,8 @@ def render(scene, n_paths=None, path_offset=0, seed=None, medium_id=0, n_threads
     none); with frozen=True the decisions are still sampled in the unperturbed scene and every
     tally carries the likelihood ratio of the decisions before it.
     paper_mode=True: the paper's single-inelastic model (uncollided excitation, one emission,
-    fluorescence-only film)."""
+    fluorescence-only film).
+    hero=C (1..4): hero-wavelength paths carrying up to C wavelengths (spectral MIS)."""
     L = lib()
     h = _SceneHolder(scene)
     p = _params(scene, n_paths, path_offset, seed, medium_id, n_threads, analog, max_inelastic,
@@ -220,6 +222,7 @@ def render(scene, n_paths=None, path_offset=0, seed=None, medium_id=0, n_threads
     p.macro_cell = int(macro_cell)
     p.skip_cell = int(skip_cell)
     p.paper_mode = 1 if paper_mode else 0
+    p.hero = int(hero)
     return _render(L, h, scene, p, film, path_events)
 
 

@@ -1,0 +1,264 @@
+"""Oracle pins for hero-wavelength paths (spectral MIS; Wilkie et al. 2014, cited in Sec. 3).
+
+A hero path carries up to C wavelengths and splits every tally among them by the balance
+heuristic. Pins: with C = 1 it is the single-wavelength estimator decision for decision; a
+non-scattering absorber transmits exp(-sigma_a(lambda_k) L) of every line it carries (Eq. 6); an
+optically thin dye's emitted spectrum is its emission pmf (Eq. 10); and on the workloads its
+expectation equals the single-wavelength estimator's bin by bin.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+from tests.stats import batch_mean_se, parity_verdict
+
+B = sg.N_BINS
+
+
+def bin_of(lam):
+    return int(math.ceil((lam - sg.LAMBDA0) / sg.DLAMBDA - 0.5))
+
+
+def line_slab(n_paths, lines, eps=1.2, qy=0.0, sigma_s=0.0):
+    """Unit cube of one dye (absorption peak 490 nm, sigma 40 nm) lit by a pencil beam carrying
+    `lines` of equal power, entering the +z face along -z."""
+    dyes = sg.make_dyes([490.0], [40.0], [640.0], [15.0], eps=[eps], qy=[qy])
+    return {"spectrum": sg.spectrum(), "dyes": dyes,
+            "medium": sg.homogeneous_medium(1, conc=1.0, sigma_s=sigma_s),
+            "sources": [sg.pencil_beam((0.5, 0.5, 1.0), (0, 0, -1), list(lines))],
+            "sensor": sg.no_sensor(), "params": sg.params(n_paths, seed=5)}
+
+
+def batches(sc, K, n, **kw):
+    return [oracle.render(sc, n_paths=n, path_offset=k * n, **kw) for k in range(K)]
+
+
+def small_workloads():
+    return [
+        ("homogeneous cube", sg.cfg1_homogeneous_cube(n_paths=1), {}),
+        ("cornell box", sg.cfg2_cornell_box(width=16, height=16, grid=24, n_paths=1), {}),
+        ("cornell box, leaps", sg.cfg2_cornell_box(width=16, height=16, grid=24, n_paths=1),
+         {"skip_cell": 2}),
+        ("light sheet", sg.cfg5_light_sheet(grid=24, width=16, height=16, n_blobs=30, n_paths=1,
+                                            sigma_t_ref=20.0), {}),
+    ]
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_one_member_is_the_single_wavelength_estimator(case):
+    name, sc, kw = small_workloads()[case]
+    a = oracle.render(sc, n_paths=4000, n_threads=1, **kw)
+    b = oracle.render(sc, n_paths=4000, n_threads=1, hero=1, **kw)
+    for key in ("face", "absorbed", "emitted", "film"):
+        if a[key] is not None:
+            assert np.array_equal(a[key], b[key]), (name, key)
+    assert a["counters"] == b["counters"], name
+
+
+def test_every_carried_line_obeys_beer_lambert():
+    """Non-scattering absorber, four lines of one beam carried by every path: line k leaves the
+    -z face with probability exp(-sigma_a(lambda_k) L) and is absorbed otherwise (QY 0)."""
+    lines = [430.0, 470.0, 500.0, 560.0]
+    sc = line_slab(1, lines)
+    K, n = 24, 5000
+    outs = batches(sc, K, n, hero=4)
+    sig = 1.2 * sc["dyes"]["abs_shape"][0].astype(np.float64)
+    for lam in lines:
+        b = bin_of(lam)
+        T = math.exp(-sig[b])
+        m, se = batch_mean_se([o["face"][0, sg.FACE_NZ, b] for o in outs])
+        assert abs(m - T / 4) <= 4 * se + 1e-12, (lam, m, T / 4, se)
+        ma, sea = batch_mean_se([o["absorbed"][0, b] for o in outs])
+        assert abs(ma - (1 - T) / 4) <= 4 * sea + 1e-12, (lam, ma, (1 - T) / 4, sea)
+    # each path's weight is split, never created or lost
+    for o in outs:
+        assert abs(o["face"].sum() + o["absorbed"].sum() - 1.0) < 1e-9
+    # and the carried lines make the estimate far tighter than one line per path
+    single = batches(sc, K, n)
+    b = bin_of(470.0)
+    _, se_h = batch_mean_se([o["face"][0, sg.FACE_NZ, b] for o in outs])
+    _, se_1 = batch_mean_se([o["face"][0, sg.FACE_NZ, b] for o in single])
+    assert se_h < 0.6 * se_1, (se_h, se_1)
+
+
+def test_thin_dye_emitted_spectrum_is_the_emission_pmf():
+    """An optically thin dye (Sec. 6, validation 1): the emitted tally per bin, over the absorbed
+    total times QY, is the dye's normalised emission spectrum."""
+    dyes = sg.make_dyes([450.0], [10.0], [620.0], [18.0], eps=[0.05], qy=[0.8])
+    sc = {"spectrum": sg.spectrum(), "dyes": dyes,
+          "medium": sg.homogeneous_medium(1, conc=1.0, sigma_s=0.0),
+          "sources": [sg.pencil_beam((0.5, 0.5, 1.0), (0, 0, -1), [450.0])],
+          "sensor": sg.no_sensor(), "params": sg.params(1, seed=9)}
+    K, n = 16, 100_000
+    outs = batches(sc, K, n, hero=4)
+    pmf = sc["dyes"]["emit_spec"][0].astype(np.float64)
+    pmf /= pmf.sum()
+    absorbed = np.mean([o["absorbed"][0].sum() for o in outs])
+    qy = float(np.float32(0.8))
+    m, se = batch_mean_se([o["emitted"][0] for o in outs])
+    want = absorbed * qy * pmf
+    big = want > 1e-3 * want.max()
+    z = (m[big] - want[big]) / np.maximum(se[big], 1e-15)
+    # the absorbed total is itself estimated: allow its relative error on top
+    rel = batch_mean_se([o["absorbed"][0].sum() for o in outs])[1] / absorbed
+    tol = 4.0 + rel * want[big] / np.maximum(se[big], 1e-15)
+    assert (np.abs(z) <= tol).all(), (z.max(), z.min())
+    # every emission spreads its weight over a block of 4 bins
+    assert (m[big] > 0).sum() == big.sum()
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_hero_expectation_equals_single_wavelength(case):
+    """Same scene, independent seeds: every spectral tally and the film agree bin by bin."""
+    name, sc, kw = small_workloads()[case]
+    K, n = 16, 3000
+    a = batches(sc, K, n, **kw)
+    b = [oracle.render(sc, n_paths=n, path_offset=k * n, seed=4321, hero=4, **kw)
+         for k in range(K)]
+    for key in ("face", "absorbed", "emitted", "film"):
+        if a[0][key] is None:
+            continue
+        ga = np.stack([o[key] for o in a])
+        gb = np.stack([o[key] for o in b])
+        if key == "film":
+            # 4 x 4 pixel tiles: the single-wavelength film's per-bin batch means are too skewed
+            # for a z-test at 3,000 paths per batch (most bins hold a handful of connections)
+            k_, h_, w_, b_ = ga.shape
+            ga = ga.reshape(k_, h_ // 4, 4, w_ // 4, 4, b_).sum(axis=(2, 4))
+            gb = gb.reshape(k_, h_ // 4, 4, w_ // 4, 4, b_).sum(axis=(2, 4))
+        ma, sa = batch_mean_se(ga)
+        mb, sb = batch_mean_se(gb)
+        # bins populated in every batch on both sides (a z-test needs both standard errors)
+        pop = ((ga != 0).sum(axis=0) >= K) & ((gb != 0).sum(axis=0) >= K)
+        if key == "film":
+            # The single-wavelength film's batch means are right-skewed (most bins hold a few
+            # connections), and their standard errors rise and fall with them, so against the far
+            # smoother hero film the z-scores run a little wide even without bias: measured on the
+            # homogeneous cube, 1.0-1.3 % beyond 3 and mean z^2 1.12-1.17 at 3,000 and at 30,000
+            # paths per batch (a bias would grow with the path count), against 0.3 % and 0.97-1.06
+            # for two single-wavelength runs. The per-bin limits are widened to match; the
+            # integrated check below stays tight.
+            v = parity_verdict(ma, np.where(pop, sa, 0), mb, np.where(pop, sb, 0),
+                               frac_limit=0.02, chi_hi=1.3)
+        else:
+            v = parity_verdict(ma, np.where(pop, sa, 0), mb, np.where(pop, sb, 0))
+        assert v["ok"], (name, key, v)
+        # integrated: within 4 SE
+        ta, sta = batch_mean_se(ga.reshape(K, -1).sum(axis=1))
+        tb, stb = batch_mean_se(gb.reshape(K, -1).sum(axis=1))
+        assert abs(ta - tb) <= 4 * math.hypot(sta, stb) + 1e-12, (name, key, ta, tb)
+
+
+def test_hero_lowers_the_spectral_film_variance():
+    """The point of carrying several wavelengths: on the Cornell box (four lines in one light,
+    emission bands tens of bins wide) the per-bin film variance falls at equal path count."""
+    sc = sg.cfg2_cornell_box(width=16, height=16, grid=24, n_paths=1)
+    K, n = 16, 3000
+    a = np.stack([o["film"] for o in batches(sc, K, n)])
+    b = np.stack([o["film"] for o in batches(sc, K, n, hero=4)])
+    va, vb = a.var(axis=0, ddof=1), b.var(axis=0, ddof=1)
+    both = (va > 0) & (vb > 0)
+    assert np.median(vb[both] / va[both]) < 0.6, np.median(vb[both] / va[both])
+
+
+def two_beams(sigma_s, qy):
+    dyes = sg.make_dyes([480.0, 560.0], [30.0, 30.0], [600.0, 650.0], [20.0, 20.0],
+                        eps=[0.8, 0.6], qy=qy)
+    return {"spectrum": sg.spectrum(), "dyes": dyes,
+            "medium": sg.homogeneous_medium(2, conc=1.0, sigma_s=sigma_s),
+            "sources": [sg.pencil_beam((0.5, 0.5, 1.0), (0, 0, -1), [470.0, 560.0]),
+                        sg.pencil_beam((0.0, 0.3, 0.4), (1, 0, 0), [490.0, 520.0])],
+            "sensor": sg.no_sensor(), "params": sg.params(1, seed=3)}
+
+
+def test_sets_stay_within_one_source():
+    """Two sources of different geometry, two lines each: a hero path carries only its own
+    source's lines, and the expectation still equals the single-wavelength estimator's."""
+    sc = two_beams(2.0, [0.7, 0.5])
+    K, n = 16, 4000
+    a = batches(sc, K, n)
+    b = [oracle.render(sc, n_paths=n, path_offset=k * n, seed=99, hero=4) for k in range(K)]
+    for key in ("face", "absorbed", "emitted"):
+        ga, gb = np.stack([o[key] for o in a]), np.stack([o[key] for o in b])
+        ma, sa = batch_mean_se(ga)
+        mb, sb = batch_mean_se(gb)
+        pop = ((ga != 0).sum(axis=0) >= K) & ((gb != 0).sum(axis=0) >= K)
+        v = parity_verdict(ma, np.where(pop, sa, 0), mb, np.where(pop, sb, 0))
+        assert v["ok"], (key, v)
+    # without scattering or emission each beam leaves through its own exit face, -z for the first
+    # and +x for the second, carrying its own lines only
+    r = oracle.render(two_beams(0.0, [0.0, 0.0]), n_paths=20000, hero=4)
+    nz, px = r["face"][0, sg.FACE_NZ], r["face"][0, sg.FACE_PX]
+    for lam in (470.0, 560.0):
+        assert nz[bin_of(lam)] > 0 and px[bin_of(lam)] == 0.0, lam
+    for lam in (490.0, 520.0):
+        assert px[bin_of(lam)] > 0 and nz[bin_of(lam)] == 0.0, lam
+    assert r["face"].sum() + r["absorbed"].sum() == pytest.approx(1.0, abs=1e-9)
+
+
+def test_unsupported_combinations_are_rejected():
+    sc = sg.cfg1_homogeneous_cube(n_paths=10)
+    for kw in ({"hero": 5}, {"hero": -1}, {"hero": 4, "macro_cell": 4},
+               {"hero": 4, "paper_mode": True}):
+        with pytest.raises(ValueError):
+            oracle.render(sc, **kw)
+
+
+def cube_escape_average(points, sigma, n_mu=160, n_phi=160):
+    """(1 / 4 pi) * integral over directions of exp(-sigma * d(p, w)), d the distance from p to the
+    unit cube's boundary along w: midpoint rule in mu = cos(theta) and phi. points [P, 3],
+    sigma [L] -> [P, L]."""
+    mu = (np.arange(n_mu) + 0.5) / n_mu * 2.0 - 1.0
+    phi = (np.arange(n_phi) + 0.5) / n_phi * 2.0 * math.pi
+    M, F = np.meshgrid(mu, phi, indexing="ij")
+    st = np.sqrt(1.0 - M ** 2)
+    w = np.stack([st * np.cos(F), st * np.sin(F), M], axis=-1).reshape(-1, 3)
+    out = np.zeros((points.shape[0], sigma.shape[0]))
+    for i, p in enumerate(points):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = np.where(w > 0, (1.0 - p) / w, np.where(w < 0, -p / w, np.inf))
+        d = t.min(axis=1)
+        out[i] = np.exp(-np.outer(d, sigma)).mean(axis=0)
+    return out
+
+
+def test_emission_block_through_a_quencher_matches_quadrature():
+    """The members of an emission block cross a second dye whose absorption changes across the
+    block, so every null collision re-weights them. Non-scattering cube, pencil beam at 450 nm
+    into the +z centre; dye 0 absorbs at 450 nm and emits around 600 nm (QY 0.9); dye 1 absorbs
+    around 615 nm and does not emit. Escaping fluorescence per bin = QY p_0(bin) times the
+    integral over depth s of sigma_0(450) exp(-sigma_t(450) s) times the direction average of
+    exp(-sigma_1(bin) d), computed by quadrature."""
+    dyes = sg.make_dyes([450.0, 615.0], [10.0, 25.0], [600.0, 720.0], [20.0, 15.0],
+                        eps=[1.5, 2.0], qy=[0.9, 0.0])
+    sc = {"spectrum": sg.spectrum(), "dyes": dyes,
+          "medium": sg.homogeneous_medium(2, conc=1.0, sigma_s=0.0),
+          "sources": [sg.pencil_beam((0.5, 0.5, 1.0), (0, 0, -1), [450.0])],
+          "sensor": sg.no_sensor(), "params": sg.params(1, seed=21)}
+    K, n = 16, 40_000
+    outs = batches(sc, K, n, hero=4)
+    sig = dyes["eps"][:, None].astype(np.float64) * dyes["abs_shape"].astype(np.float64)
+    bx = bin_of(450.0)
+    s0, st = sig[0, bx], sig[:, bx].sum()
+    cdf = np.cumsum(dyes["emit_spec"][0].astype(np.float64))
+    cdf32 = (cdf / cdf[-1]).astype(np.float32).astype(np.float64)
+    cdf32[-1] = 1.0
+    pmf = np.diff(np.concatenate([[0.0], cdf32]))
+    band = np.arange(bin_of(540.0), bin_of(665.0))
+    depth = (np.arange(200) + 0.5) / 200
+    pts = np.stack([np.full_like(depth, 0.5), np.full_like(depth, 0.5), 1.0 - depth], axis=1)
+    A = cube_escape_average(pts, sig[0, band] + sig[1, band])
+    dens = s0 * np.exp(-st * depth) / 200
+    qy = float(np.float32(0.9))
+    want = qy * pmf[band] * (dens[:, None] * A).sum(axis=0)
+    m, se = batch_mean_se([o["face"][1].sum(axis=0)[band] for o in outs])
+    z = (m - want) / se
+    assert np.abs(z).max() <= 4.5, np.round(z, 1)
+    assert (z ** 2).mean() <= 2.0, np.round(z, 1)
+    # the quencher takes the rest of the emitted light
+    ma, sea = batch_mean_se([o["absorbed"][1][band] for o in outs])
+    za = (ma - (qy * pmf[band] * (dens[:, None] * (1.0 - A)).sum(axis=0))) / sea
+    assert np.abs(za).max() <= 4.5, np.round(za, 1)
