@@ -502,6 +502,7 @@ def run_ours(args):
                                       if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
                                       else f"/tmp/clocks_rank{rank}.csv")
     ms_p, ev_p, cnt_p, _ = timed("plain", max(1, min(args.steps, args.plain_steps)))
+    step_ms_w_local = sum(ms_w) / len(ms_w)
 
     # equal-RMSE check: each form's one-step film against a 16x-path reference (independent seed)
     rmse = None
@@ -519,6 +520,37 @@ def run_ours(args):
         rmse = {"plain": out["plain"], "wavefront": out["wavefront"],
                 "reference_paths": n_ref * n_paths,
                 "ratio_wavefront_over_plain": out["wavefront"] / out["plain"]}
+
+    # hero-wavelength paths (four wavelengths per path, spectral MIS) against one wavelength per
+    # path, both in the plain form with the same empty-space leaps: time per step and film RMSE
+    # against the reference above; efficiency = 1 / (RMSE^2 x time)
+    hero = None
+    if rmse is not None and not args.no_hero:
+        sk = tuned["skip_cell"] if tuned["macro_cell"] == 0 else 0
+        hero_ms = {}
+        hero_rmse = {}
+        for name, kw in (("single", {}), ("hero4", {"hero": 4})):
+            S.render(form="plain", path_offset=offset, skip_cell=sk, **kw)   # warm-up
+            ms_h = []
+            for i in range(args.hero_steps):
+                flush.fill_(float(i))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                S.render(form="plain", path_offset=offset, skip_cell=sk, **kw)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms_h.append(a.elapsed_time(b))
+            hero_ms[name] = sum(ms_h) / len(ms_h)
+            hero_rmse[name] = float(torch.sqrt(torch.mean((S.film_tensor().double() - ref.double()) ** 2)))
+        eff = lambda r, t: 1.0 / (r * r * t)
+        hero = {"form": "plain", "skip_cell": sk, "members": 4,
+                "ms": hero_ms["hero4"], "rmse": hero_rmse["hero4"],
+                "single_ms": hero_ms["single"], "single_rmse": hero_rmse["single"],
+                "efficiency_vs_single_plain": eff(hero_rmse["hero4"], hero_ms["hero4"])
+                / eff(hero_rmse["single"], hero_ms["single"]),
+                "efficiency_vs_warp_single": eff(hero_rmse["hero4"], hero_ms["hero4"])
+                / eff(rmse["wavefront"], step_ms_w_local),
+                "launches": 2 * (args.hero_steps + 1)}
 
     def reduce_max(x):
         if world == 1:
@@ -632,6 +664,7 @@ def run_ours(args):
                 "adjoint": adjoint,
                 "paper_model": paper,
                 "light_sheet": sheet,
+                "hero_wavelength": hero,
             },
             "counters_per_step": cnt_w,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
@@ -644,7 +677,8 @@ def run_ours(args):
             + (0 if batched is None else batched["steps"] + batched["plain_launches"])
             + (0 if adjoint is None else adjoint["launches_per_step"] * args.adjoint_steps)
             + (0 if paper is None else 2 * args.paper_steps)
-            + (0 if sheet is None else sheet["steps"] + 1),
+            + (0 if sheet is None else sheet["steps"] + 1)
+            + (0 if hero is None else 2 * args.hero_steps),
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -687,6 +721,9 @@ def main():
                     help="skip the paper's own (camera-side) estimator of its single-inelastic model")
     ap.add_argument("--paper-steps", type=int, default=3)
     ap.add_argument("--adjoint-steps", type=int, default=3)
+    ap.add_argument("--no-hero", action="store_true",
+                    help="skip the hero-wavelength comparison (needs the film RMSE reference)")
+    ap.add_argument("--hero-steps", type=int, default=2)
     ap.add_argument("--no-sheet", action="store_true",
                     help="skip the full-size light-sheet workload (256^3 x 4 grids, 67M paths)")
     ap.add_argument("--sheet-steps", type=int, default=2)

@@ -162,6 +162,18 @@ typedef struct flr_params {
                                     after the emission connect to the sensor, so the film holds
                                     fluorescence alone. Rejected paths count as vf_rejected.
                                     flr_render and the batch only; 0: the full RTE. */
+    int hero;                    /* 1..4: hero-wavelength paths (spectral multiple importance
+                                    sampling, Wilkie et al. 2014, cited in Sec. 3): a path carries
+                                    up to `hero` wavelengths, the hero's source lines (the lines
+                                    of one source, in blocks of `hero`) and after a re-emission
+                                    the block of `hero` consecutive bins holding the drawn bin;
+                                    the hero takes every decision, free flights use the largest
+                                    member majorant, and every tally and film contribution is
+                                    split among the members by the balance heuristic. Same
+                                    expectation as one wavelength per path; with 1 the same
+                                    paths and tallies. flr_render with FLR_FORM_PLAIN only, no
+                                    macro_cell, no paper_mode (else FLR_ERR_ARG). 0: one
+                                    wavelength per path. */
 } flr_params;
 
 /* Create a context on CUDA device `cuda_device`. Allocates the small tally buffers. */
@@ -281,7 +293,8 @@ int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const u
  * the interleaved copy of the grids -- lives in one static device array of 4 MiB + 64 KiB that
  * every GPU loading this library holds until the process exits; media with more than
  * FLR_NOALLOC_MAX_VOXELS voxels are rejected with FLR_ERR_ARG; p->macro_cell and p->majorant_margin are
- * ignored (one majorant per bin, no margin), and so is p->paper_mode. The first call on a device looks up
+ * ignored (one majorant per bin, no margin), and so is p->paper_mode; p->hero must be 0. The first call
+ * on a device looks up
  * that array's device address (with that device current), so make that first call before any
  * stream capture. Every call uses the same array and clears what must start at zero, so calls
  * that overlap on the GPU (other streams, other host threads) race with each other. The call

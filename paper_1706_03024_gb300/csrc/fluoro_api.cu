@@ -199,7 +199,7 @@ void build_tables(flr_ctx *ctx)
 
 // The spectral lines of a medium's sources, chosen in proportion to power (p(lambda_x), Eq. 12).
 int build_emitters(flr_ctx *ctx, const flr_medium &m, int max_lines, EmitterDev *em, float *em_cdf,
-                   int *n_out)
+                   int *n_out, int *group_first = nullptr, int *group_n = nullptr)
 {
     int first = m.source_first, count = m.source_count;
     if (count == 0) { first = 0; count = (int)ctx->sources.size(); }
@@ -209,8 +209,11 @@ int build_emitters(flr_ctx *ctx, const flr_medium &m, int max_lines, EmitterDev 
     int n = 0;
     for (int s = first; s < first + count; ++s) {
         const flr_source &src = ctx->sources[s];
+        const int g0 = n;
         for (int l = 0; l < src.n_lines; ++l) {
             if (n >= max_lines) return fail(ctx, FLR_ERR_ARG, "too many source lines for one medium");
+            if (group_first) group_first[n] = g0;
+            if (group_n) group_n[n] = src.n_lines;
             EmitterDev &e = em[n];
             for (int k = 0; k < 3; ++k) {
                 e.origin[k] = src.origin[k];
@@ -264,7 +267,8 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film, int macro_cell = 0, in
     S.wall_albedo = m.wall_albedo;
     S.tables = ctx->d_tables;
     int ne = 0;
-    const int rc = build_emitters(ctx, m, FLR_MAX_EMITTERS, S.em, S.em_cdf, &ne);
+    const int rc = build_emitters(ctx, m, FLR_MAX_EMITTERS, S.em, S.em_cdf, &ne, S.em_group_first,
+                                  S.em_group_n);
     if (rc != FLR_OK) return rc;
     S.n_emitters = ne;
     const int cell = macro_cell > 0 ? macro_cell : skip_cell;
@@ -666,6 +670,9 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
         return fail(ctx, FLR_ERR_ARG, "params: macro_cell and skip_cell 0..4096");
     if (!(p->majorant_margin >= 0.0f && p->majorant_margin <= 100.0f))
         return fail(ctx, FLR_ERR_ARG, "params: majorant_margin in [0, 100]");
+    if (p->hero < 0 || p->hero > 4) return fail(ctx, FLR_ERR_ARG, "params: hero must be 0..4");
+    if (p->hero > 0 && (p->form != FLR_FORM_PLAIN || p->macro_cell > 0 || p->paper_mode))
+        return fail(ctx, FLR_ERR_ARG, "params: hero paths need the plain form, no macro cells and no paper mode");
     if (p->film && !is_device_pointer(p->film)) return fail(ctx, FLR_ERR_ARG, "params: film must be device memory");
     if (p->path_events && !is_device_pointer(p->path_events))
         return fail(ctx, FLR_ERR_ARG, "params: path_events must be device memory");
@@ -717,6 +724,7 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     R.work_counter = ctx->d_work;
     R.regroup = p->regroup_interval;
     R.paper_mode = p->paper_mode ? 1 : 0;
+    R.hero = p->hero;
     e = launch_trace(S, R, p->form, p->block_size, p->blocks_per_sm, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch trace kernel");
     ctx->paths_since_clear += p->n_paths;
@@ -740,6 +748,7 @@ int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
         return fail(ctx, FLR_ERR_ARG, "params: unknown form");
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
+    if (p->hero != 0) return fail(ctx, FLR_ERR_ARG, "params: hero paths are for flr_render only");
     const uint64_t npix = (uint64_t)ctx->sensor.width * (uint64_t)ctx->sensor.height;
     if (p->n_paths % npix != 0 || p->path_offset % npix != 0)
         return fail(ctx, FLR_ERR_ARG, "camera: n_paths and path_offset must be multiples of the pixel count");
@@ -905,6 +914,7 @@ int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float 
         return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
+    if (p->hero != 0) return fail(ctx, FLR_ERR_ARG, "params: hero paths are for flr_render only");
     if (!is_device_pointer(adj_film)) return fail(ctx, FLR_ERR_ARG, "adjoint: adj_film must be device memory");
     if (grad_conc && !medium_has_grid(ctx->medium))
         return fail(ctx, FLR_ERR_ARG, "adjoint: grad_conc needs a medium with concentration grids");
@@ -1015,6 +1025,7 @@ int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const 
         return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
+    if (p->hero != 0) return fail(ctx, FLR_ERR_ARG, "params: hero paths are for flr_render only");
     if (!(p->majorant_margin >= 0.0f && p->majorant_margin <= 100.0f))
         return fail(ctx, FLR_ERR_ARG, "params: majorant_margin in [0, 100]");
     const int B = ctx->B;
@@ -1298,6 +1309,7 @@ extern "C" int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins
         return FLR_ERR_ARG;
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return FLR_ERR_ARG;
+    if (p->hero != 0) return FLR_ERR_ARG;   /* hero paths: flr_render only */
     if (p->film && !is_device_pointer(p->film)) return FLR_ERR_ARG;
     if (p->path_events && !is_device_pointer(p->path_events)) return FLR_ERR_ARG;
     if (c.sensor_set && c.sensor.kind == FLR_SENSOR_PINHOLE) {

@@ -66,6 +66,9 @@ struct SceneDev {
     int n_emitters;
     float em_cdf[FLR_MAX_EMITTERS];
     EmitterDev em[FLR_MAX_EMITTERS];
+    // the lines of one source are consecutive emitters: emitter k's source spans emitters
+    // em_group_first[k] .. em_group_first[k] + em_group_n[k] - 1 (hero-wavelength sets)
+    int em_group_first[FLR_MAX_EMITTERS], em_group_n[FLR_MAX_EMITTERS];
     int sensor_kind, W, H;
     float s_origin[3], s_U[3], s_V[3], s_view[3];  // ortho: U, V pre-divided by |U|^2, |V|^2
     float tan_x, tan_y, inv_A_pix;
@@ -98,6 +101,7 @@ struct RunDev {
     unsigned long long *work_counter;  // dynamic path distribution (wavefront form)
     int regroup;                       // wavefront: tracking steps between connection flushes
     int paper_mode;                    // the paper's single-inelastic model (flr_params)
+    int hero;                          // wavelengths per hero path (flr_params); 0 = one
     uint32_t rk[20];                   // Philox round keys of (seed, medium_id): k0[10], k1[10]
 };
 

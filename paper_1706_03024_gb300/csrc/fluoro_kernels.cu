@@ -763,13 +763,14 @@ __device__ __forceinline__ void finish(const RunDev &R, Path &p)
 
 template <class M>
 __device__ __forceinline__ Conn spawn(const M &m, const RunDev &R, const Smem &sm, uint64_t pid,
-                                      Path &p)
+                                      Path &p, int *emitter = nullptr)
 {
     cnt_add(sm, FLR_C_PATHS);
     const U4 s0 = m.rng(R, pid, STEP_SPAWN, 0u);
     int k = 0;
     const int ne = m.n_emitters();
     while (k < ne - 1 && !(m.em_cdf(k) > s0.a)) ++k;
+    if (emitter) *emitter = k;
     const EmitterDev &e = m.em(k);
     p.x = make_float3(e.origin[0] + s0.b * e.eu[0] + s0.c * e.ev[0],
                       e.origin[1] + s0.b * e.eu[1] + s0.c * e.ev[1],
@@ -1074,6 +1075,441 @@ __global__ void __launch_bounds__(256) k_trace_plain(SceneDev S, RunDev R)
         while (p.alive) {
             c = track_step(m, R, sm, p, rc);
             if (c.valid) connect<OPT>(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
+        }
+    }
+    block_epilogue(S, R, sm, rc);
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Hero-wavelength paths (spectral MIS; Wilkie et al., "Hero wavelength spectral sampling", EGSR
+// 2014, which the paper's Sec. 3 cites against the cost of per-wavelength transport). A path carries
+// a set of up to HERO_MAX wavelengths: the hero drives every decision exactly as a single-wavelength
+// path would, and every tally is split among the members by the balance heuristic,
+//     q_j = P(j) p(path | j) / sum_k P(k) p(path | k),
+// P(k) the probability of drawing member k as the hero, p(path | k) the density of the decisions
+// since the set was drawn at member k's wavelength. The set is the block of a fixed partition that
+// holds the hero: the hero's source lines (consecutive emitters of one source) in blocks of C, and
+// after a re-emission the emission bins [C floor(b/C), C floor(b/C) + C). Free flights use the set's
+// majorant max_k sigma_bar(lambda_k), so only null collisions (and, for the absorbed tally, the dye
+// absorption itself) change q; scattering, walls and background absorption are grey. A re-emission
+// does not depend on which member was absorbed, so the path goes on with weight w QY and a fresh
+// set. With C = 1 every decision and tally is the single-wavelength path's.
+constexpr int HERO_MAX = 4;
+
+struct HeroSet {
+    int n, hero;
+    int bin[HERO_MAX];
+    float q[HERO_MAX];   // balance-heuristic weights, sum 1
+    float sb, isb;       // the set's majorant and its tabulated inverse
+};
+
+// The matter at a point, read once for all members: solvent indicator and the dyes' concentrations.
+struct MatterPt {
+    float s;
+    float4 c;
+};
+
+template <class M>
+__device__ __forceinline__ MatterPt matter_at(const M &m, float3 x)
+{
+    MatterPt r{1.0f, m.conc_uniform()};
+    if (!m.homogeneous()) {
+        const int v = voxel_of(m, x);
+        const float4 *g = m.grid();
+        const uint8_t *sv = m.solvent();
+        if (g) r.c = __ldg(&g[v]);
+        if (sv) r.s = __ldg(&sv[v]) ? 1.0f : 0.0f;
+    }
+    return r;
+}
+
+// The coefficients of coeffs_at, in its operation order, from a point already read.
+template <class M>
+__device__ __forceinline__ Coeffs coeffs_of(const M &m, const MatterPt &pt, int b)
+{
+    Coeffs k;
+    k.scat = pt.s * m.sigma_s();
+    k.bg = pt.s * m.sigma_a0();
+    k.total = k.scat + k.bg;
+    const float cc[4] = {pt.c.x, pt.c.y, pt.c.z, pt.c.w};
+    const float4 sa = m.sig_a4(b);
+    const float ss[4] = {sa.x, sa.y, sa.z, sa.w};
+    const int D = m.D();
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d) {
+        k.dye[d] = (d < D) ? ss[d] * cc[d] : 0.0f;
+        k.total += k.dye[d];
+    }
+    return k;
+}
+
+// k.dye[d] for a run-time d, by selects (an indexed read would put the array in local memory).
+__device__ __forceinline__ float dye_of(const Coeffs &k, int d)
+{
+    return d == 0 ? k.dye[0] : (d == 1 ? k.dye[1] : (d == 2 ? k.dye[2] : k.dye[3]));
+}
+
+// Normalises the weights and takes the set's majorant (the member bin with the largest).
+template <class M>
+__device__ __forceinline__ void hero_close(const M &m, HeroSet &h)
+{
+    if (h.n == 1) {
+        h.q[0] = 1.0f;
+    } else {
+        float z = 0.0f;
+#pragma unroll
+        for (int j = 0; j < HERO_MAX; ++j) z += j < h.n ? h.q[j] : 0.0f;
+        const float iz = 1.0f / z;
+#pragma unroll
+        for (int j = 0; j < HERO_MAX; ++j) h.q[j] = j < h.n ? h.q[j] * iz : 0.0f;
+    }
+    int bm = h.bin[0];
+#pragma unroll
+    for (int j = 1; j < HERO_MAX; ++j)
+        if (j < h.n && m.maj(h.bin[j]) > m.maj(bm)) bm = h.bin[j];
+    h.sb = m.maj(bm);
+    h.isb = m.inv_maj(bm);
+}
+
+// The hero's source lines: emitters first .. first + n - 1 of its source, in blocks of C.
+template <class M>
+__device__ __forceinline__ void hero_lines(const M &m, const SceneDev &S, int k, int C, HeroSet &h)
+{
+    const int g0 = S.em_group_first[k], gn = S.em_group_n[k];
+    const int first = g0 + ((k - g0) / C) * C;
+    h.n = min(C, g0 + gn - first);
+    h.hero = k - first;
+#pragma unroll
+    for (int j = 0; j < HERO_MAX; ++j) {
+        const int e = min(first + j, m.n_emitters() - 1);
+        h.bin[j] = S.em[e].bin;
+        h.q[j] = m.em_cdf(e) - (e > 0 ? m.em_cdf(e - 1) : 0.0f);
+    }
+    hero_close(m, h);
+}
+
+// The emission block of bin b of dye d: bins [C floor(b/C), ...), weights the realised pmf.
+template <class M>
+__device__ __forceinline__ void hero_emission(const M &m, int d, int b, int C, HeroSet &h)
+{
+    const int first = (b / C) * C;
+    h.n = min(C, m.B() - first);
+    h.hero = b - first;
+    const float *cdf = m.cdf(d);
+#pragma unroll
+    for (int j = 0; j < HERO_MAX; ++j) {
+        const int bj = min(first + j, m.B() - 1);
+        h.bin[j] = bj;
+        h.q[j] = cdf[bj] - (bj > 0 ? cdf[bj - 1] : 0.0f);
+    }
+    hero_close(m, h);
+}
+
+// Sensor connection of a vertex for every member: shared geometry, one ratio-tracking march against
+// the set's majorant estimating every member's transmittance; the roulette acts on the weighted sum
+// sum_k q_k T_k (with one member: the single-wavelength rule exactly).
+template <class M>
+__device__ __forceinline__ void connect_hero(const M &m, const SceneDev &S, const RunDev &R,
+                                             const Smem &sm, float3 x, const HeroSet &h, float w,
+                                             int lamb, uint64_t pid, uint32_t step, RegCnt &rc)
+{
+    const ConnGeom g = connect_geom(S, sm, x, lamb);
+    if (!g.ok) return;
+    rc.connections++;
+    float T[HERO_MAX];
+#pragma unroll
+    for (int j = 0; j < HERO_MAX; ++j) T[j] = 1.0f;
+    if (S.homogeneous) {
+        const MatterPt pt = matter_at(m, x);
+#pragma unroll
+        for (int j = 0; j < HERO_MAX; ++j)
+            if (j < h.n) T[j] = __expf(-coeffs_of(m, pt, h.bin[j]).total * g.tl);
+    } else if (h.sb > 0.0f) {
+        float t = 0.0f;
+        U4 blk = U4{0, 0, 0, 0};
+        uint32_t jr = 0;
+        int it = 0;
+        for (; it < MAX_CONNECT_STEPS; ++it) {
+            if ((jr & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (jr >> 2));
+            const uint32_t qd = jr & 3u;
+            const float u = qd == 0 ? blk.a : (qd == 1 ? blk.b : (qd == 2 ? blk.c : blk.d));
+            ++jr;
+            t -= __logf(1.0f - u) * h.isb;
+            if (t >= g.tl) break;
+            rc.connect_steps++;
+            const float3 p = make_float3(x.x + t * g.dir.x, x.y + t * g.dir.y, x.z + t * g.dir.z);
+            const MatterPt pt = matter_at(m, p);
+            float Tq = 0.0f, st_h = 0.0f;
+#pragma unroll
+            for (int j = 0; j < HERO_MAX; ++j) {
+                if (j < h.n) {
+                    const float st = coeffs_of(m, pt, h.bin[j]).total;
+                    if (j == h.hero) st_h = st;
+                    T[j] *= fmaxf(0.0f, 1.0f - st * h.isb);
+                    Tq += h.q[j] * T[j];
+                }
+            }
+            if (h.n == 1) Tq = T[0];
+            if (S.sk > 0 && st_h == 0.0f) {
+                // the cube around this point holds no matter at any wavelength
+                const float tl2 = empty_cube_exit(m, p, g.dir, inv_dir(g.dir));
+                if (tl2 > 0.0f) {
+                    t += tl2;
+                    rc.cell_walks++;
+                }
+            }
+            if (Tq < RT_RR_THRESHOLD) {
+                if ((jr & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (jr >> 2));
+                const uint32_t q2 = jr & 3u;
+                const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
+                ++jr;
+                if (u2 * RT_RR_THRESHOLD < Tq) {
+                    if (h.n == 1) {
+                        T[0] = RT_RR_THRESHOLD;
+                    } else {
+                        const float sc = RT_RR_THRESHOLD / Tq;
+#pragma unroll
+                        for (int j = 0; j < HERO_MAX; ++j) T[j] *= sc;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < HERO_MAX; ++j) T[j] = 0.0f;
+                    break;
+                }
+            }
+        }
+        if (it == MAX_CONNECT_STEPS) {
+#pragma unroll
+            for (int j = 0; j < HERO_MAX; ++j) T[j] = 0.0f;
+            cnt_add(sm, FLR_C_CONNECT_BUDGET);
+        }
+    }
+    const float base = w * g.gf;
+#pragma unroll
+    for (int j = 0; j < HERO_MAX; ++j) {
+        if (j < h.n) {
+            const float val = (h.n == 1 ? base * T[j] : base * h.q[j] * T[j]) * R.film_scale;
+            if (val > 0.0f) atomicAdd(&R.film[(size_t)g.pix * S.B + h.bin[j]], val);
+        }
+    }
+}
+
+// Tally w split among the members: row + bin_j gets w q_j.
+template <class M>
+__device__ __forceinline__ void hero_tally(const M &m, int row, const HeroSet &h, float w)
+{
+#pragma unroll
+    for (int j = 0; j < HERO_MAX; ++j)
+        if (j < h.n) m.tally(row + h.bin[j], h.n == 1 ? w : w * h.q[j]);
+}
+
+// One tracking step of a hero path: the single-wavelength step (track_step) with the set's
+// majorant, the weights re-balanced at null collisions and the tallies split among the members.
+template <class M>
+__device__ __forceinline__ Conn track_step_hero(const M &m, const RunDev &R, const Smem &sm, Path &p,
+                                                HeroSet &h, RegCnt &rc)
+{
+    Conn c;
+    c.valid = false;
+    if ((long long)p.step >= R.max_steps) {
+        cnt_add(sm, FLR_C_STEP_BUDGET);
+        finish(R, p);
+        return c;
+    }
+    rc.steps++;
+    const U4 b0 = m.rng(R, p.pid, p.step, 0u);
+    const U4 b1 = m.rng(R, p.pid, p.step, 1u);
+    int face;
+    const float te = exit_distance(m, p.x, p.w, p.iw, face);
+    const float sb = h.sb;
+    const float tf = sb > 0.0f ? -__logf(1.0f - b0.a) * h.isb : FLT_MAX;
+    const uint32_t step = p.step;
+    p.step++;
+    int dax = -1;
+    float dsg = 1.0f, du1 = b0.d, du2 = b1.a;
+    if (tf >= te) {
+        p.x = make_float3(p.x.x + te * p.w.x, p.x.y + te * p.w.y, p.x.z + te * p.w.z);
+        if (face < 0) {
+            cnt_add(sm, FLR_C_NONFINITE);
+            finish(R, p);
+            return c;
+        }
+        if (!(m.wall_mask() & (1 << face))) {
+            hero_tally(m, tal_face(m.B()) + (p.fl * 6 + face) * m.B(), h, p.wt);
+            cnt_add(sm, FLR_C_ESCAPES);
+            finish(R, p);
+            return c;
+        }
+        if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
+        p.n_events++;
+        rc.events++;
+        cnt_add(sm, FLR_C_WALL_BOUNCES);
+        if (R.analog) {
+            if (!(b1.d < m.wall_albedo())) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+        } else {
+            p.wt *= m.wall_albedo();
+            if (p.wt == 0.0f) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+        }
+        dax = face >> 1;
+        dsg = (face & 1) ? -1.0f : 1.0f;
+        if (dax == 0) p.x.x = (face & 1) ? m.hi(0) : m.lo(0);
+        else if (dax == 1) p.x.y = (face & 1) ? m.hi(1) : m.lo(1);
+        else p.x.z = (face & 1) ? m.hi(2) : m.lo(2);
+        du1 = b0.c;
+        du2 = b0.d;
+    } else {
+        p.x = make_float3(p.x.x + tf * p.w.x, p.x.y + tf * p.w.y, p.x.z + tf * p.w.z);
+        const int4 ec = m.skip() ? empty_cell(m, p.x) : make_int4(0, 0, 0, 0);
+        const MatterPt pt = matter_at(m, p.x);
+        const Coeffs k = coeffs_of(m, pt, p.bin);
+        if (k.total > sb) cnt_add(sm, FLR_C_MAJORANT_VIOLATIONS);
+        if (!(b0.b * sb < k.total)) {
+            rc.nulls++;
+            if (h.n > 1) {
+                // member j's null probability over the hero's
+                const float inull = 1.0f / (sb - k.total);
+                float z = 0.0f;
+#pragma unroll
+                for (int j = 0; j < HERO_MAX; ++j) {
+                    if (j < h.n && j != h.hero) {
+                        const float st = coeffs_of(m, pt, h.bin[j]).total;
+                        if (st > sb) cnt_add(sm, FLR_C_MAJORANT_VIOLATIONS);
+                        h.q[j] *= fmaxf(0.0f, sb - st) * inull;
+                    }
+                    z += j < h.n ? h.q[j] : 0.0f;
+                }
+                const float iz = 1.0f / z;
+#pragma unroll
+                for (int j = 0; j < HERO_MAX; ++j) h.q[j] *= iz;
+            }
+            if (m.skip() && k.total == 0.0f) {
+                float tl = empty_cube_exit_at(m, ec, p.x, p.w, p.iw);
+                if (tl > 0.0f) {
+                    tl = fminf(tl, te - tf);
+                    p.x = make_float3(p.x.x + tl * p.w.x, p.x.y + tl * p.w.y, p.x.z + tl * p.w.z);
+                    rc.cell_walks++;
+                }
+            }
+            return c;
+        }
+        if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
+        p.n_events++;
+        rc.events++;
+        const float ue = b0.c * k.total;
+        float acc = k.scat;
+        int ev = -1;
+        const int D = m.D();
+        if (!(ue < acc)) {
+            ev = D;
+#pragma unroll
+            for (int d = 0; d < MAXD; ++d) {
+                if (d < D && ev == D) {
+                    acc += k.dye[d];
+                    if (ue < acc) ev = d;
+                }
+            }
+        }
+        if (ev < 0) {
+            rc.scatters++;
+        } else if (ev < D) {
+            cnt_add(sm, FLR_C_DYE_ABSORPTIONS);
+            {
+                // the absorbed tally: member j's probability of this dye absorption over the hero's
+                HeroSet ha = h;
+                if (h.n > 1) {
+                    const float dh = dye_of(k, ev);   // > 0: the dye was chosen
+                    float z = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < HERO_MAX; ++j) {
+                        if (j < h.n && j != h.hero) ha.q[j] *= dye_of(coeffs_of(m, pt, h.bin[j]), ev) / dh;
+                        z += j < h.n ? ha.q[j] : 0.0f;
+                    }
+                    if (z > 0.0f && z < FLT_MAX) {
+                        const float iz = 1.0f / z;
+#pragma unroll
+                        for (int j = 0; j < HERO_MAX; ++j) ha.q[j] *= iz;
+                    } else {
+                        cnt_add(sm, FLR_C_NONFINITE);
+                    }
+                }
+                hero_tally(m, tal_absorbed(m.B()) + ev * m.B(), ha, p.wt);
+            }
+            if (R.max_inelastic >= 0 && p.n_inel >= R.max_inelastic) {
+                cnt_add(sm, FLR_C_VF_REJECTED);
+                finish(R, p);
+                return c;
+            }
+            if (R.analog) {
+                if (!(b1.d < m.qy(ev))) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+            } else {
+                p.wt *= m.qy(ev);
+                if (p.wt == 0.0f) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+            }
+            p.bin = sample_cdf(m.cdf(ev), m.B(), b1.b);
+            hero_emission(m, ev, p.bin, R.hero, h);
+            hero_tally(m, tal_emitted(m.B()) + ev * m.B(), h, p.wt);
+            cnt_add(sm, FLR_C_EMISSIONS);
+            p.n_inel++;
+            p.fl = 1;
+        } else {
+            hero_tally(m, tal_absorbed(m.B()) + D * m.B(), h, p.wt);
+            cnt_add(sm, FLR_C_ABSORBED_DEAD);
+            finish(R, p);
+            return c;
+        }
+    }
+    {
+        const float u1 = du1;
+        float sn, cs;
+        __sincosf(TWO_PI * du2, &sn, &cs);
+        float a, r;
+        if (dax < 0) {
+            a = 1.0f - 2.0f * u1;
+            r = sqrt_approx(fmaxf(0.0f, 1.0f - a * a));
+        } else {
+            r = sqrt_approx(u1);
+            a = dsg * sqrt_approx(fmaxf(0.0f, 1.0f - u1));
+        }
+        const float bx = r * cs, by = r * sn;
+        p.w = dax == 0 ? make_float3(a, bx, by) : (dax == 1 ? make_float3(by, a, bx) : make_float3(bx, by, a));
+    }
+    p.iw = inv_dir(p.w);
+    if (m.sensor()) c = Conn{p.x, p.wt, p.bin, dax < 0 ? -1 : 2 * dax + (dsg > 0.0f ? 1 : 0), p.pid, step, true};
+    if (p.n_events >= R.n_rr) {
+        const float q = fminf(p.wt, 1.0f);
+        if (!(b1.c < q)) { cnt_add(sm, FLR_C_RR_KILLS); finish(R, p); return c; }
+        p.wt = p.wt < 1.0f ? 1.0f : p.wt;
+    }
+    if (!(isfinite(p.wt) && isfinite(p.x.x) && isfinite(p.x.y) && isfinite(p.x.z))) {
+        cnt_add(sm, FLR_C_NONFINITE);
+        finish(R, p);
+        c.valid = false;
+    }
+    return c;
+}
+
+// Plain form of the hero-wavelength tracer: one thread per path, connections inline. The
+// connection of a step is made after the step, with the set as it stands then (an emission's
+// connection carries the new set; the roulette that follows does not touch the set).
+__global__ void __launch_bounds__(256) k_trace_hero(SceneDev S, RunDev R)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
+    const MedS_<true, false> m{S, sm};
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
+        Path p;
+        HeroSet h;
+        int k = 0;
+        Conn c = spawn(m, R, sm, R.path_offset + i, p, &k);
+        hero_lines(m, S, k, R.hero, h);
+        if (c.valid) connect_hero(m, S, R, sm, c.x, h, c.w, c.lamb, c.pid, c.step, rc);
+        while (p.alive) {
+            c = track_step_hero(m, R, sm, p, h, rc);
+            if (c.valid) connect_hero(m, S, R, sm, c.x, h, c.w, c.lamb, c.pid, c.step, rc);
         }
     }
     block_epilogue(S, R, sm, rc);
@@ -2425,6 +2861,8 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
         else
             k_trace_wavefront_warp<WM_RENDER, false><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
     }
+    else if (R.hero > 0)
+        k_trace_hero<<<(unsigned)grid, block, smem, st>>>(S, R);
     else if (S.mc > 0 || S.sk > 0)
         k_trace_plain<true><<<(unsigned)grid, block, smem, st>>>(S, R);
     else

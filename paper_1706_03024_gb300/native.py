@@ -77,7 +77,8 @@ class flr_params(C.Structure):
                 ("max_steps", C.c_int64), ("film", C.c_void_p), ("path_events", C.c_void_p),
                 ("accumulate", C.c_int), ("block_size", C.c_int), ("blocks_per_sm", C.c_int),
                 ("regroup_interval", C.c_int), ("macro_cell", C.c_int),
-                ("skip_cell", C.c_int), ("majorant_margin", C.c_float), ("paper_mode", C.c_int)]
+                ("skip_cell", C.c_int), ("majorant_margin", C.c_float), ("paper_mode", C.c_int),
+                ("hero", C.c_int)]
 
 
 # name -> (restype, argtypes); every symbol include/fluoro.h declares

@@ -143,7 +143,7 @@ class Scene:
     def _params(self, n_paths=None, path_offset=0, seed=None, medium_id=0, form="plain",
                 analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
                 accumulate=False, block_size=0, blocks_per_sm=0, regroup=0, macro_cell=0,
-                majorant_margin=0.0, skip_cell=0, paper_mode=False):
+                majorant_margin=0.0, skip_cell=0, paper_mode=False, hero=0):
         pp = dict(self.desc["params"])
         for k, v in (("n_paths", n_paths), ("seed", seed), ("analog", analog),
                      ("max_inelastic", max_inelastic), ("n_rr", n_rr), ("max_events", max_events),
@@ -169,16 +169,17 @@ class Scene:
         p.skip_cell = int(skip_cell)
         p.majorant_margin = float(majorant_margin)
         p.paper_mode = 1 if paper_mode else 0
+        p.hero = int(hero)
         return p
 
     def render(self, n_paths=None, path_offset=0, seed=None, medium_id=0, form="plain",
                analog=None, max_inelastic=None, n_rr=None, max_events=None, max_steps=None,
                film=True, path_events=None, accumulate=False, block_size=0, blocks_per_sm=0,
                regroup=0, macro_cell=0, majorant_margin=0.0, skip_cell=0, paper_mode=False,
-               stream=None):
+               hero=0, stream=None):
         p = self._params(n_paths, path_offset, seed, medium_id, form, analog, max_inelastic, n_rr,
                          max_events, max_steps, accumulate, block_size, blocks_per_sm, regroup,
-                         macro_cell, majorant_margin, skip_cell, paper_mode)
+                         macro_cell, majorant_margin, skip_cell, paper_mode, hero)
         f = self.film_tensor() if film else None
         p.film = f.data_ptr() if f is not None else None
         p.path_events = path_events.data_ptr() if path_events is not None else None
