@@ -88,8 +88,11 @@ def test_hero_matches_oracle_hero(case):
     if sc["sensor"]["kind"] != "none":
         v = bin_parity(g, o, "film")
         assert v["ok"], (name, "film", v)
+        # the GPU estimates each connection's transmittance by ratio tracking, the oracle takes
+        # it exactly: same expectation, different noise
         gf, of = totals(g, "film").sum(), totals(o, "film").sum()
-        assert abs(gf - of) <= 1e-2 * of, (name, gf, of)
+        se = np.sqrt(np.var([x["film"].sum() for x in g]) / K + np.var([x["film"].sum() for x in o]) / K)
+        assert abs(gf - of) <= 5e-3 * of + 4 * se, (name, gf, of, se)
     c = g[-1]["counters"]
     for cn in ("majorant_violations", "nonfinite", "connect_budget", "step_budget"):
         assert c[cn] == 0, (name, cn, c[cn])
