@@ -522,35 +522,39 @@ def run_ours(args):
                 "ratio_wavefront_over_plain": out["wavefront"] / out["plain"]}
 
     # hero-wavelength paths (four wavelengths per path, spectral MIS) against one wavelength per
-    # path, both in the plain form with the same empty-space leaps: time per step and film RMSE
-    # against the reference above; efficiency = 1 / (RMSE^2 x time)
+    # path: the warp-regrouped form against the timed warp form above, and the plain forms with
+    # the same empty-space leaps; time per step and film RMSE against the reference above,
+    # efficiency = 1 / (RMSE^2 x time)
     hero = None
-    if rmse is not None and not args.no_hero:
-        sk = tuned["skip_cell"] if tuned["macro_cell"] == 0 else 0
-        hero_ms = {}
-        hero_rmse = {}
-        for name, kw in (("single", {}), ("hero4", {"hero": 4})):
-            S.render(form="plain", path_offset=offset, skip_cell=sk, **kw)   # warm-up
+    if rmse is not None and not args.no_hero and tuned["macro_cell"] == 0:
+        sk = tuned["skip_cell"]
+        warp_kw = {"form": "wavefront_warp", "block_size": 128, "regroup": 1}
+        hero_ms, hero_rmse = {}, {}
+        for name, kw in (("warp_hero4", dict(warp_kw, hero=4)), ("plain_single", {"form": "plain"}),
+                         ("plain_hero4", {"form": "plain", "hero": 4})):
+            S.render(path_offset=offset, skip_cell=sk, **kw)   # warm-up
             ms_h = []
             for i in range(args.hero_steps):
                 flush.fill_(float(i))
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                S.render(form="plain", path_offset=offset, skip_cell=sk, **kw)
+                S.render(path_offset=offset, skip_cell=sk, **kw)
                 b.record(stream)
                 torch.cuda.synchronize()
                 ms_h.append(a.elapsed_time(b))
             hero_ms[name] = sum(ms_h) / len(ms_h)
             hero_rmse[name] = float(torch.sqrt(torch.mean((S.film_tensor().double() - ref.double()) ** 2)))
-        eff = lambda r, t: 1.0 / (r * r * t)
-        hero = {"form": "plain", "skip_cell": sk, "members": 4,
-                "ms": hero_ms["hero4"], "rmse": hero_rmse["hero4"],
-                "single_ms": hero_ms["single"], "single_rmse": hero_rmse["single"],
-                "efficiency_vs_single_plain": eff(hero_rmse["hero4"], hero_ms["hero4"])
-                / eff(hero_rmse["single"], hero_ms["single"]),
-                "efficiency_vs_warp_single": eff(hero_rmse["hero4"], hero_ms["hero4"])
-                / eff(rmse["wavefront"], step_ms_w_local),
-                "launches": 2 * (args.hero_steps + 1)}
+            if name == "warp_hero4":
+                hero_events = S.read()["counters"]["events"]
+        hero_ms["warp_single"], hero_rmse["warp_single"] = step_ms_w_local, rmse["wavefront"]
+        eff = {k: 1.0 / (hero_rmse[k] ** 2 * hero_ms[k]) for k in hero_ms}
+        hero = {"members": 4, "skip_cell": sk, "ms": hero_ms, "rmse": hero_rmse,
+                "warp_hero4_events_per_s": hero_events / (hero_ms["warp_hero4"] / 1000.0),
+                "efficiency_warp_hero4_over_warp_single": eff["warp_hero4"] / eff["warp_single"],
+                "efficiency_plain_hero4_over_plain_single": eff["plain_hero4"] / eff["plain_single"],
+                "equal_rmse_time_ms": {"warp_single": hero_ms["warp_single"],
+                                       "warp_hero4": hero_ms["warp_hero4"] * (hero_rmse["warp_hero4"] / hero_rmse["warp_single"]) ** 2},
+                "launches": 3 * args.hero_steps}
 
     def reduce_max(x):
         if world == 1:
@@ -678,7 +682,7 @@ def run_ours(args):
             + (0 if adjoint is None else adjoint["launches_per_step"] * args.adjoint_steps)
             + (0 if paper is None else 2 * args.paper_steps)
             + (0 if sheet is None else sheet["steps"] + 1)
-            + (0 if hero is None else 2 * args.hero_steps),
+            + (0 if hero is None else hero["launches"]),
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

@@ -171,7 +171,8 @@ typedef struct flr_params {
                                     member majorant, and every tally and film contribution is
                                     split among the members by the balance heuristic. Same
                                     expectation as one wavelength per path; with 1 the same
-                                    paths and tallies. flr_render with FLR_FORM_PLAIN only, no
+                                    paths and tallies. flr_render with FLR_FORM_PLAIN or
+                                    FLR_FORM_WAVEFRONT_WARP (blocks of 128, regroup 1), no
                                     macro_cell, no paper_mode (else FLR_ERR_ARG). 0: one
                                     wavelength per path. */
 } flr_params;

@@ -671,8 +671,8 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     if (!(p->majorant_margin >= 0.0f && p->majorant_margin <= 100.0f))
         return fail(ctx, FLR_ERR_ARG, "params: majorant_margin in [0, 100]");
     if (p->hero < 0 || p->hero > 4) return fail(ctx, FLR_ERR_ARG, "params: hero must be 0..4");
-    if (p->hero > 0 && (p->form != FLR_FORM_PLAIN || p->macro_cell > 0 || p->paper_mode))
-        return fail(ctx, FLR_ERR_ARG, "params: hero paths need the plain form, no macro cells and no paper mode");
+    if (p->hero > 0 && (p->form == FLR_FORM_WAVEFRONT || p->macro_cell > 0 || p->paper_mode))
+        return fail(ctx, FLR_ERR_ARG, "params: hero paths need the plain or warp form, no macro cells and no paper mode");
     if (p->film && !is_device_pointer(p->film)) return fail(ctx, FLR_ERR_ARG, "params: film must be device memory");
     if (p->path_events && !is_device_pointer(p->path_events))
         return fail(ctx, FLR_ERR_ARG, "params: path_events must be device memory");

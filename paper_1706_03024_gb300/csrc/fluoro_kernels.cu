@@ -2076,6 +2076,269 @@ __global__ void __launch_bounds__(WARP_BLOCK, (MODE == WM_RENDER && !MC) ? 5 : 4
     }
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Warp-regrouped form of the hero-wavelength tracer: the tracking round and the pull-based drains
+// of k_trace_wavefront_warp, with records that carry the member set. A record holds the vertex, the
+// path weight, the members' weights q_j and packed bins, the member count, the hero's index and the
+// vertex kind, and the RNG coordinates (13 words). A drain's march estimates every member's
+// transmittance at once (connect_hero's march, step by step), so the film matches the plain hero
+// form's up to the order of the fp32 atomics.
+constexpr int HQ_CAP = 224;
+constexpr int HQ_DRAIN = 192;
+constexpr int HQ_WORDS = 13;
+static_assert(HQ_DRAIN + 31 < HQ_CAP, "hero queue overflow");
+
+struct HQueue {
+    float *x, *y, *z, *w, *q0, *q1, *q2, *q3;
+    uint32_t *bins, *nhl, *pid_lo, *pid_hi, *step;
+    int *head_tail;
+};
+
+__host__ __device__ inline SmemLayout hero_warp_layout(int B, int block)
+{
+    SmemLayout L;
+    L.tab_floats = tab_size(B);
+    int off = ((L.tab_floats * 4 + 15) / 16) * 16;
+    L.tal_off_bytes = off;
+    L.tal_global = true;
+    L.cnt_off_bytes = off;
+    off += FLR_NCOUNTERS * 8;
+    off = ((off + 15) / 16) * 16;
+    L.queue_off_bytes = off;
+    off += (block / 32) * (HQ_CAP * HQ_WORDS * 4 + 8);
+    L.total_bytes = off;
+    return L;
+}
+
+__device__ __forceinline__ void hq_push(const HQueue &q, const Conn &c, const HeroSet &h)
+{
+    const int slot = atomicAdd(&q.head_tail[1], 1);
+    q.x[slot] = c.x.x;
+    q.y[slot] = c.x.y;
+    q.z[slot] = c.x.z;
+    q.w[slot] = c.w;
+    q.q0[slot] = h.q[0];
+    q.q1[slot] = h.n > 1 ? h.q[1] : 0.0f;
+    q.q2[slot] = h.n > 2 ? h.q[2] : 0.0f;
+    q.q3[slot] = h.n > 3 ? h.q[3] : 0.0f;
+    q.bins[slot] = (uint32_t)(h.bin[0] & 0xFF) | ((uint32_t)(h.bin[1] & 0xFF) << 8) |
+                   ((uint32_t)(h.bin[2] & 0xFF) << 16) | ((uint32_t)(h.bin[3] & 0xFF) << 24);
+    q.nhl[slot] = (uint32_t)h.n | ((uint32_t)h.hero << 3) | ((uint32_t)(c.lamb + 1) << 5);
+    q.pid_lo[slot] = (uint32_t)c.pid;
+    q.pid_hi[slot] = (uint32_t)(c.pid >> 32);
+    q.step[slot] = c.step;
+}
+
+struct HMarch {
+    March mc;             // geometry, march state and RNG coordinates (wg: weight x importance)
+    float T[HERO_MAX], q[HERO_MAX];
+    uint32_t bins;
+    int n, hero;
+};
+
+__device__ __forceinline__ int hm_bin(const HMarch &hm, int j) { return (int)((hm.bins >> (8 * j)) & 0xFFu); }
+
+__device__ __forceinline__ void hero_deposit(const SceneDev &S, const RunDev &R, const HMarch &hm)
+{
+#pragma unroll
+    for (int j = 0; j < HERO_MAX; ++j) {
+        if (j < hm.n) {
+            const float val = (hm.n == 1 ? hm.mc.wg * hm.T[j] : hm.mc.wg * hm.q[j] * hm.T[j]) * R.film_scale;
+            if (val > 0.0f) atomicAdd(&R.film[(size_t)hm.mc.pix * S.B + hm_bin(hm, j)], val);
+        }
+    }
+}
+
+// Starts the connection of one queued hero vertex; returns true if a march remains.
+__device__ __forceinline__ bool hero_march_begin(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                                 const HQueue &q, int k, HMarch &hm, RegCnt &rc)
+{
+    const uint32_t nhl = q.nhl[k];
+    const float3 x = make_float3(q.x[k], q.y[k], q.z[k]);
+    const ConnGeom g = connect_geom(S, sm, x, (int)((nhl >> 5) & 7u) - 1);
+    if (!g.ok) return false;
+    rc.connections++;
+    const MedS_<true, false> m{S, sm};
+    hm.n = (int)(nhl & 7u);
+    hm.hero = (int)((nhl >> 3) & 3u);
+    hm.bins = q.bins[k];
+    hm.q[0] = q.q0[k];
+    hm.q[1] = q.q1[k];
+    hm.q[2] = q.q2[k];
+    hm.q[3] = q.q3[k];
+    hm.mc.wg = q.w[k] * g.gf;
+    hm.mc.pix = g.pix;
+    int bm = hm_bin(hm, 0);
+#pragma unroll
+    for (int j = 0; j < HERO_MAX; ++j) {
+        hm.T[j] = 1.0f;
+        if (j > 0 && j < hm.n && m.maj(hm_bin(hm, j)) > m.maj(bm)) bm = hm_bin(hm, j);
+    }
+    const float sb = m.maj(bm);
+    if (S.homogeneous) {
+        const MatterPt pt = matter_at(m, x);
+#pragma unroll
+        for (int j = 0; j < HERO_MAX; ++j)
+            if (j < hm.n) hm.T[j] = __expf(-coeffs_of(m, pt, hm_bin(hm, j)).total * g.tl);
+        hero_deposit(S, R, hm);
+        return false;
+    }
+    if (!(sb > 0.0f)) {
+        hero_deposit(S, R, hm);
+        return false;
+    }
+    hm.mc.x = x;
+    hm.mc.dir = g.dir;
+    hm.mc.idir = g.idr;
+    hm.mc.tl = g.tl;
+    hm.mc.t = 0.0f;
+    hm.mc.isb = m.inv_maj(bm);
+    hm.mc.j = 0;
+    hm.mc.it = 0;
+    hm.mc.pid = ((uint64_t)q.pid_hi[k] << 32) | q.pid_lo[k];
+    hm.mc.step = q.step[k];
+    return true;
+}
+
+// One step of a hero march (the loop body of connect_hero's march); false when the march ends.
+__device__ __forceinline__ bool hero_march_step(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                                HMarch &hm, RegCnt &rc)
+{
+    March &mc = hm.mc;
+    if (mc.it >= MAX_CONNECT_STEPS) {
+        cnt_add(sm, FLR_C_CONNECT_BUDGET);
+        return false;
+    }
+    ++mc.it;
+    const float u = march_uniform(R, mc);
+    mc.t -= __logf(1.0f - u) * mc.isb;
+    if (mc.t >= mc.tl) {
+        hero_deposit(S, R, hm);
+        return false;
+    }
+    rc.connect_steps++;
+    const MedS_<true, false> m{S, sm};
+    const float3 p = make_float3(mc.x.x + mc.t * mc.dir.x, mc.x.y + mc.t * mc.dir.y,
+                                 mc.x.z + mc.t * mc.dir.z);
+    const int4 ec = S.sk > 0 ? empty_cell(m, p) : make_int4(0, 0, 0, 0);
+    const MatterPt pt = matter_at(m, p);
+    float Tq = 0.0f, st_h = 0.0f;
+#pragma unroll
+    for (int j = 0; j < HERO_MAX; ++j) {
+        if (j < hm.n) {
+            const float st = coeffs_of(m, pt, hm_bin(hm, j)).total;
+            if (j == hm.hero) st_h = st;
+            hm.T[j] *= fmaxf(0.0f, 1.0f - st * mc.isb);
+            Tq += hm.q[j] * hm.T[j];
+        }
+    }
+    if (hm.n == 1) Tq = hm.T[0];
+    if (S.sk > 0 && st_h == 0.0f) {
+        const float tl2 = empty_cube_exit_at(m, ec, p, mc.dir, mc.idir);
+        if (tl2 > 0.0f) {
+            mc.t += tl2;
+            rc.cell_walks++;
+        }
+    }
+    if (Tq < RT_RR_THRESHOLD) {
+        const float u2 = march_uniform(R, mc);
+        if (u2 * RT_RR_THRESHOLD < Tq) {
+            if (hm.n == 1) {
+                hm.T[0] = RT_RR_THRESHOLD;
+            } else {
+                const float sc = RT_RR_THRESHOLD / Tq;
+#pragma unroll
+                for (int j = 0; j < HERO_MAX; ++j) hm.T[j] *= sc;
+            }
+        } else {
+            return false;
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(WARP_BLOCK, 4) k_trace_hero_warp(SceneDev S, RunDev R)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = hero_warp_layout(S.B, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
+    const MedS_<true, false> m{S, sm};
+    constexpr unsigned FULL = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const unsigned lower = (1u << lane) - 1u;
+    HQueue q;
+    {
+        unsigned char *base = smem_raw + L.queue_off_bytes;
+        float *f = reinterpret_cast<float *>(base) + warp * HQ_CAP * HQ_WORDS;
+        q.x = f;
+        q.y = q.x + HQ_CAP;
+        q.z = q.y + HQ_CAP;
+        q.w = q.z + HQ_CAP;
+        q.q0 = q.w + HQ_CAP;
+        q.q1 = q.q0 + HQ_CAP;
+        q.q2 = q.q1 + HQ_CAP;
+        q.q3 = q.q2 + HQ_CAP;
+        q.bins = reinterpret_cast<uint32_t *>(q.q3 + HQ_CAP);
+        q.nhl = q.bins + HQ_CAP;
+        q.pid_lo = q.nhl + HQ_CAP;
+        q.pid_hi = q.pid_lo + HQ_CAP;
+        q.step = q.pid_hi + HQ_CAP;
+        q.head_tail = reinterpret_cast<int *>(base + (size_t)nwarps * HQ_CAP * HQ_WORDS * 4) + 2 * warp;
+        if (lane == 0) { q.head_tail[0] = 0; q.head_tail[1] = 0; }
+    }
+    __syncwarp();
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
+    Path p;
+    p.alive = false;
+    HeroSet h;
+    bool exhausted = false;
+    while (true) {
+        const bool spawn_now = __popc(__ballot_sync(FULL, !p.alive && !exhausted)) >= SPAWN_MIN ||
+                               __ballot_sync(FULL, p.alive) == 0u;
+        if (!p.alive) {
+            if (!exhausted && spawn_now) {
+                const unsigned long long i = atomicAdd(R.work_counter, 1ull);
+                if (i >= R.n_paths) {
+                    exhausted = true;
+                } else {
+                    int k = 0;
+                    const Conn c = spawn(m, R, sm, R.path_offset + i, p, &k);
+                    hero_lines(m, S, k, R.hero, h);
+                    if (c.valid) hq_push(q, c, h);
+                }
+            }
+        } else {
+            const Conn c = track_step_hero(m, R, sm, p, h, rc);
+            if (c.valid) hq_push(q, c, h);
+        }
+        __syncwarp();
+        const bool any = __any_sync(FULL, p.alive || !exhausted);
+        const int avail = q.head_tail[1];
+        if (avail >= HQ_DRAIN || (!any && avail > 0)) {
+            HMarch hm;
+            bool active = false;
+            int claimed = 0;
+            for (uint32_t iter = 0;; ++iter) {
+                const unsigned need = (iter & 1u) == 0u ? __ballot_sync(FULL, !active) : 0u;
+                if (need != 0u && !active) {
+                    const int k = claimed + __popc(need & lower);
+                    if (k < avail) active = hero_march_begin(S, R, sm, q, k, hm, rc);
+                }
+                claimed += __popc(need);
+                if (active) active = hero_march_step(S, R, sm, hm, rc);
+                if (!__any_sync(FULL, active) && claimed >= avail) break;
+            }
+            __syncwarp();
+            if (lane == 0) q.head_tail[1] = 0;
+            __syncwarp();
+        }
+        if (!any) break;
+    }
+    block_epilogue(S, R, sm, rc);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Camera-side estimator of the paper's single-inelastic model (Sec. 4.1-4.3, Eq. 12). A path
 // starts at the sensor (pixel = path id mod W*H, a point uniform in it) at an emission bin drawn
@@ -2796,6 +3059,24 @@ int trace_block_default() { return 256; }
 
 int trace_smem_bytes(int B, int form, int block) { return smem_layout(B, form, block).total_bytes; }
 
+cudaError_t launch_hero_warp(const SceneDev &S, const RunDev &R, int block, int blocks_per_sm,
+                             cudaStream_t st)
+{
+    block = WARP_BLOCK;
+    const int smem = hero_warp_layout(S.B, block).total_bytes;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_trace_hero_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_hero_warp, block, smem);
+    if (occ < 1) occ = 1;
+    if (blocks_per_sm <= 0 || blocks_per_sm > occ) blocks_per_sm = occ;
+    const long long grid = (long long)num_sms() * blocks_per_sm;
+    k_trace_hero_warp<<<(unsigned)grid, block, smem, st>>>(S, R);
+    return cudaGetLastError();
+}
+
 namespace {
 // Opts a trace kernel into dynamic shared memory above the default 48 KB (the warp-regrouped
 // form's queues reach about 59 KB at 128 bins and 256 threads).
@@ -2839,6 +3120,7 @@ int occupancy_blocks_per_sm(int B, int form, int block)
 cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block, int blocks_per_sm,
                          cudaStream_t st)
 {
+    if (R.hero > 0 && form == FLR_FORM_WAVEFRONT_WARP) return launch_hero_warp(S, R, block, blocks_per_sm, st);
     if (block <= 0) block = trace_block_default();
     if (form == FLR_FORM_WAVEFRONT_WARP) block = std::min(block, WARP_BLOCK);
     const int smem = trace_smem_bytes(S.B, form, block);

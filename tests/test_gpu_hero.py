@@ -98,14 +98,41 @@ def test_hero_matches_oracle_hero(case):
         assert c[cn] == 0, (name, cn, c[cn])
 
 
+BENCH_LAUNCH = {"form": "wavefront_warp", "block_size": 128, "regroup": 1}
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_warp_form_equals_plain_form(case):
+    """The warp-regrouped hero kernel traces the same paths and marches as the plain one: identical
+    fixed-point tallies, counters and per-path event counts, the same film up to atomic order; with
+    one member it is the single-wavelength warp kernel."""
+    name, sc, kw = workloads()[case]
+    S = Scene(sc)
+    n = 30000
+    for hero, ref in ((4, {"form": "plain", "hero": 4}), (1, dict(BENCH_LAUNCH))):
+        pa = torch.zeros(n, dtype=torch.int32, device="cuda")
+        pb = torch.zeros(n, dtype=torch.int32, device="cuda")
+        fa = S.render(n_paths=n, path_events=pa, **ref, **kw)
+        fa = fa.clone() if fa is not None else None
+        a = S.read()
+        fb = S.render(n_paths=n, path_events=pb, hero=hero, **BENCH_LAUNCH, **kw)
+        b = S.read()
+        assert torch.equal(pa, pb), (name, hero)
+        for key in ("face", "absorbed", "emitted"):
+            assert np.array_equal(_fixed(a[key]), _fixed(b[key])), (name, hero, key)
+        assert a["counters"] == b["counters"], (name, hero)
+        if fa is not None:
+            assert torch.allclose(fa, fb, rtol=1e-4, atol=1e-6 * float(fa.abs().max())), (name, hero)
+
+
 def test_hero_full_size_cornell_box_invariants():
     """The Cornell-box workload at full size (4,194,304 paths, 512 x 512 x 81 film) with four
-    wavelengths per path: bookkeeping, a finite non-negative film, tallies within 1 % of the
-    single-wavelength kernel's on the same paths."""
+    wavelengths per path in the benchmarked launch shape: bookkeeping, a finite non-negative
+    film, tallies within 1 % of the single-wavelength kernel's on the same path ids."""
     sc = sg.cfg2_cornell_box()
     n = sc["params"]["n_paths"]
     S = Scene(sc)
-    film = S.render(form="plain", hero=4, skip_cell=1)
+    film = S.render(hero=4, skip_cell=1, **BENCH_LAUNCH)
     h = S.read()
     c = h["counters"]
     ends = (c["escapes"] + c["absorbed_dead"] + c["rr_kills"] + c["cap_hits"] + c["step_budget"]
@@ -127,8 +154,9 @@ def test_hero_full_size_cornell_box_invariants():
 def test_hero_rejects_unsupported_combinations():
     sc = sg.cfg2_cornell_box(width=16, height=16, grid=16, n_paths=1000)
     S = Scene(sc)
-    for kw in ({"hero": 5}, {"hero": -1}, {"hero": 4, "form": "wavefront_warp"},
-               {"hero": 4, "form": "wavefront"}, {"hero": 4, "form": "plain", "macro_cell": 4},
+    for kw in ({"hero": 5}, {"hero": -1}, {"hero": 4, "form": "wavefront"},
+               {"hero": 4, "form": "wavefront_warp", "macro_cell": 4},
+               {"hero": 4, "form": "plain", "macro_cell": 4},
                {"hero": 4, "form": "plain", "paper_mode": True}):
         p = S._params(1000, **{k: v for k, v in kw.items() if k != "form"},
                       form=kw.get("form", "plain"))
