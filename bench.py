@@ -360,9 +360,10 @@ def bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_su
     import torch
     from paper_1706_03024_gb300.scene import Scene
 
+    from paper_1706_03024_gb300 import shard
     sc = sg.cfg5_light_sheet()
     n = int(args.sheet_paths) if args.sheet_paths else sc["params"]["n_paths"]
-    off = rank * n
+    off, _ = shard.path_range(n, rank)
     S = Scene(sc, device=local)
     kw = {"form": "wavefront_warp", "block_size": 128, "regroup": 1, "skip_cell": 0,
           "macro_cell": 0}
@@ -442,7 +443,8 @@ def run_ours(args):
     S = Scene(sc, device=local)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    offset = rank * n_paths  # each rank its own path-id range
+    from paper_1706_03024_gb300 import shard
+    offset, _ = shard.path_range(n_paths, rank)   # each rank its own path-id range
 
     # launch configuration of the optimised form: autotuned on half of the paths (outside
     # the timed region), or taken from the command line
@@ -557,18 +559,10 @@ def run_ours(args):
                 "launches": 3 * args.hero_steps}
 
     def reduce_max(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return shard.reduce_scalar(x, "max", device=dev)
 
     def reduce_sum(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return shard.reduce_scalar(x, "sum", device=dev)
 
     step_ms_w = reduce_max(sum(ms_w) / len(ms_w))
     step_ms_p = reduce_max(sum(ms_p) / len(ms_p))
