@@ -38,6 +38,8 @@ extern "C" {
 #define FLR_ERR_OOM (-3)     /* device allocation failed                                     */
 #define FLR_ERR_BUDGET (-4)  /* a device loop budget ran out (paths were cut short)          */
 #define FLR_ERR_STATE (-5)   /* call out of order (e.g. render before a medium is set)       */
+#define FLR_ERR_CHECK (-6)   /* checked build: a device index was out of range (the access
+                                was skipped); see flr_last_error                             */
 
 #define FLR_MAX_BINS 128
 #define FLR_MAX_DYES 1024           /* dye table size                                      */
@@ -308,9 +310,20 @@ int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins, int n_dye
                        double *face, double *absorbed, double *emitted, uint64_t *counters,
                        void *stream);
 
-/* Synchronise the device and report the device error word (FLR_OK if clean). */
+/* Synchronise the device and report the device error word (FLR_OK if clean). In the checked
+ * build it also reports, and clears, the first device index found out of range since the last
+ * call (FLR_ERR_CHECK; any context of the process sees it). */
 int flr_status(flr_ctx *ctx);
 const char *flr_last_error(flr_ctx *ctx);
+
+/* 1 if this library is the checked build (libfluoro_checked.so, compiled with FLR_CHECKED): every
+ * grid, table, film, tally, gradient and queue index is tested on the device before its access; a
+ * failed test skips the access and is recorded for flr_status, nothing traps. 0 otherwise. */
+int flr_checked_build(void);
+/* Diagnostics of the checked build: tests `index` in [0, bound) on the device (on `stream`) the
+ * way every checked access is tested, so a violation can be provoked without touching memory.
+ * A no-op in the normal build. FLR_ERR_CUDA if the launch fails. */
+int flr_debug_check(int64_t index, int64_t bound, void *stream);
 
 /* Diagnostics. Philox4x32-10 (Salmon et al., SC'11) blocks for device counters ctr [n][4] under
  * the key (seed, medium) into device out [n][4]; both 16-byte aligned (FLR_ERR_ARG otherwise). */

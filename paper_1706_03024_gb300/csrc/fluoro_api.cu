@@ -854,7 +854,24 @@ int flr_status(flr_ctx *ctx)
     e = cudaMemcpy(&w, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "read error word");
     if (w) return fail(ctx, FLR_ERR_BUDGET, "device error word set");
+    unsigned long long cw = 0ull;
+    e = check_word_take(&cw);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read check word");
+    if (cw) {
+        const int site = (int)((cw >> 56) & 0x7F);
+        const long long idx = (long long)(cw & 0x00FFFFFFFFFFFFFFull);
+        return fail(ctx, FLR_ERR_CHECK, "checked build: index " + std::to_string(idx) +
+                                            " out of range at access site " + std::to_string(site));
+    }
     return FLR_OK;
+}
+
+int flr_checked_build(void) { return checked_build(); }
+
+int flr_debug_check(int64_t index, int64_t bound, void *stream)
+{
+    const cudaError_t e = launch_debug_check((long long)index, (long long)bound, (cudaStream_t)stream);
+    return e == cudaSuccess ? FLR_OK : FLR_ERR_CUDA;
 }
 
 const char *flr_last_error(flr_ctx *ctx)

@@ -198,6 +198,13 @@ cudaError_t launch_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, l
 cudaError_t launch_sample_emission(const SceneDev &S, int dye, const float *u, long long n,
                                    int32_t *out, cudaStream_t st);
 int trace_block_default();
+// Checked build (-DFLR_CHECKED): 1 if this library tests every index before its access
+int checked_build();
+// Reads and clears the first recorded index violation: bit 63 set, site in bits 56..62, index in
+// bits 0..55; 0 when none (always 0 in the normal build)
+cudaError_t check_word_take(unsigned long long *word);
+// Tests `index` in [0, bound) on the device like any checked access (debug entry)
+cudaError_t launch_debug_check(long long index, long long bound, cudaStream_t st);
 int device_sms();
 int trace_smem_bytes(int B, int form, int block);
 int occupancy_blocks_per_sm(int B, int form, int block);

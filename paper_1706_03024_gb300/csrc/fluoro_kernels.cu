@@ -76,6 +76,34 @@ __device__ __forceinline__ U4 draw_rk(const RunDev &R, uint64_t pid, uint32_t st
 }
 
 // ---------------------------------------------------------------------------------------------
+// Checked build (-DFLR_CHECKED, libfluoro_checked.so): every grid, table, film, tally, gradient
+// and queue index is tested before its access. A failed test skips the access and records the
+// first (site, index) in g_check_word, which flr_status reports as FLR_ERR_CHECK; nothing traps.
+// In the normal build FLR_CHK is the constant true: the tests are not compiled.
+enum CheckSite { CK_DEBUG = 1, CK_GRID = 2, CK_FILM = 3, CK_TALLY = 4, CK_GRAD = 5, CK_ADJ_STORE = 6,
+                 CK_QUEUE = 7, CK_CELL = 8 };
+#ifdef FLR_CHECKED
+__device__ unsigned long long g_check_word;
+__device__ __forceinline__ bool check_index(bool ok, int site, long long idx)
+{
+    if (!ok)
+        atomicCAS(&g_check_word, 0ull,
+                  (1ull << 63) | ((unsigned long long)(site & 0x7F) << 56) |
+                      ((unsigned long long)idx & 0x00FFFFFFFFFFFFFFull));
+    return ok;
+}
+#define FLR_CHK(ok, site, idx) check_index((ok), (site), (long long)(idx))
+#else
+#define FLR_CHK(ok, site, idx) true
+#endif
+
+// Film accumulation (fp32 atomics) at index idx of the [H][W][B] film.
+__device__ __forceinline__ void film_add(const SceneDev &S, const RunDev &R, size_t idx, float val)
+{
+    if (FLR_CHK(idx < (size_t)S.W * S.H * S.B, CK_FILM, (long long)idx)) atomicAdd(&R.film[idx], val);
+}
+
+// ---------------------------------------------------------------------------------------------
 // Shared-memory view: spectral tables, block tallies, block counters.
 struct Smem {
     const float *sig_a, *cdf, *maj, *inv_maj, *qy;
@@ -139,7 +167,10 @@ struct MedS_ {
     __device__ __forceinline__ float inv_maj(int b) const { return sm.inv_maj[b]; }
     __device__ __forceinline__ float qy(int d) const { return sm.qy[d]; }
     __device__ __forceinline__ const float *cdf(int d) const { return sm.cdf + d * S.B; }
-    __device__ __forceinline__ void tally(int idx, float w) const { tally_add(sm, idx, w); }
+    __device__ __forceinline__ void tally(int idx, float w) const
+    {
+        if (FLR_CHK(idx >= 0 && idx < tal_size(S.B), CK_TALLY, idx)) tally_add(sm, idx, w);
+    }
     __device__ __forceinline__ bool sensor() const { return S.sensor_kind != FLR_SENSOR_NONE; }
     __device__ __forceinline__ int n_emitters() const { return S.n_emitters; }
     __device__ __forceinline__ float em_cdf(int k) const { return S.em_cdf[k]; }
@@ -154,9 +185,16 @@ struct MedS_ {
     __device__ __forceinline__ int mc_dims(int k) const { return S.mc_dims[k]; }
     __device__ __forceinline__ float mc_size(int k) const { return S.mc_size[k]; }
     __device__ __forceinline__ float mc_inv(int k) const { return S.mc_inv[k]; }
-    __device__ __forceinline__ float4 mc_conc(int c) const { return __ldg(&S.mc_c[c]); }
-    __device__ __forceinline__ float mc_solvent(int c) const { return __ldg(&S.mc_s[c]); }
-    __device__ __forceinline__ int mc_empty_radius(int c) const { return (int)__ldg(&S.mc_dist[c]); }
+    __device__ __forceinline__ bool cell_ok(int c) const
+    {
+        return FLR_CHK(c >= 0 && c < S.mc_dims[0] * S.mc_dims[1] * S.mc_dims[2], CK_CELL, c);
+    }
+    __device__ __forceinline__ float4 mc_conc(int c) const
+    {
+        return cell_ok(c) ? __ldg(&S.mc_c[c]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __device__ __forceinline__ float mc_solvent(int c) const { return cell_ok(c) ? __ldg(&S.mc_s[c]) : 0.0f; }
+    __device__ __forceinline__ int mc_empty_radius(int c) const { return cell_ok(c) ? (int)__ldg(&S.mc_dist[c]) : 0; }
     __device__ __forceinline__ bool skip() const { return OPT && S.sk > 0; }
 };
 using MedS = MedS_<true>;
@@ -210,6 +248,7 @@ struct MedB {
     __device__ __forceinline__ const float *cdf(int d) const { return tables() + tab_cdf(B_) + d * B_; }
     __device__ __forceinline__ void tally(int idx, float w) const
     {
+        if (!FLR_CHK(idx >= 0 && idx < tal_size(B_), CK_TALLY, idx)) return;
         tally_add_global(reinterpret_cast<unsigned long long *>(
                              __ldg(reinterpret_cast<const unsigned long long *>(&md->tallies))),
                          idx, w);
@@ -262,8 +301,10 @@ __device__ __forceinline__ Coeffs coeffs_at(const M &m, float3 x, int b)
         const int v = voxel_of(m, x);
         const float4 *g = m.grid();
         const uint8_t *sv = m.solvent();
-        if (g) c = __ldg(&g[v]);
-        if (sv) s = __ldg(&sv[v]) ? 1.0f : 0.0f;
+        if (FLR_CHK(v >= 0 && v < m.dims(0) * m.dims(1) * m.dims(2), CK_GRID, v)) {
+            if (g) c = __ldg(&g[v]);
+            if (sv) s = __ldg(&sv[v]) ? 1.0f : 0.0f;
+        }
     }
     Coeffs k;
     k.scat = s * m.sigma_s();
@@ -719,7 +760,7 @@ __device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, cons
     rc.connections++;
     const float T = transmittance<NoSink, OPT>(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, NoSink{});
     const float val = w * g.gf * T * R.film_scale;
-    if (val > 0.0f) atomicAdd(&R.film[(size_t)g.pix * S.B + b], val);
+    if (val > 0.0f) film_add(S, R, (size_t)g.pix * S.B + b, val);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1118,8 +1159,10 @@ __device__ __forceinline__ MatterPt matter_at(const M &m, float3 x)
         const int v = voxel_of(m, x);
         const float4 *g = m.grid();
         const uint8_t *sv = m.solvent();
-        if (g) r.c = __ldg(&g[v]);
-        if (sv) r.s = __ldg(&sv[v]) ? 1.0f : 0.0f;
+        if (FLR_CHK(v >= 0 && v < m.dims(0) * m.dims(1) * m.dims(2), CK_GRID, v)) {
+            if (g) r.c = __ldg(&g[v]);
+            if (sv) r.s = __ldg(&sv[v]) ? 1.0f : 0.0f;
+        }
     }
     return r;
 }
@@ -1290,7 +1333,7 @@ __device__ __forceinline__ void connect_hero(const M &m, const SceneDev &S, cons
     for (int j = 0; j < HERO_MAX; ++j) {
         if (j < h.n) {
             const float val = (h.n == 1 ? base * T[j] : base * h.q[j] * T[j]) * R.film_scale;
-            if (val > 0.0f) atomicAdd(&R.film[(size_t)g.pix * S.B + h.bin[j]], val);
+            if (val > 0.0f) film_add(S, R, (size_t)g.pix * S.B + h.bin[j], val);
         }
     }
 }
@@ -1651,7 +1694,7 @@ struct AdjSink {
         if (A.grad_c && S.grid)
             for (int d = 0; d < S.D; ++d) {
                 const float g = q * sm.sig_a[tab_sig_a_at(S.B, d, b)];
-                if (g != 0.0f) atomicAdd(&A.grad_c[(size_t)d * A.nvox + v], g);
+                if (g != 0.0f && FLR_CHK(v >= 0 && v < A.nvox, CK_GRAD, v)) atomicAdd(&A.grad_c[(size_t)d * A.nvox + v], g);
             }
         const float sv = S.solvent ? (__ldg(&S.solvent[v]) ? 1.0f : 0.0f) : 1.0f;
         *gsig += q * sv;
@@ -1677,7 +1720,7 @@ struct AdjObs {
         if (A.grad_c && S.grid)
             for (int d = 0; d < S.D; ++d) {
                 const float g = q * sm.sig_a[tab_sig_a_at(S.B, d, b)];
-                if (g != 0.0f) atomicAdd(&A.grad_c[(size_t)d * A.nvox + v], g);
+                if (g != 0.0f && FLR_CHK(v >= 0 && v < A.nvox, CK_GRAD, v)) atomicAdd(&A.grad_c[(size_t)d * A.nvox + v], g);
             }
         const float sv = S.solvent ? (__ldg(&S.solvent[v]) ? 1.0f : 0.0f) : 1.0f;
         *gsig += q * sv;
@@ -1690,7 +1733,8 @@ struct AdjObs {
         } else if (ev < S.D && A.grad_c && S.grid && k.dye[ev] > 0.0f) {
             const MedS m{S, sm};
             const int v = voxel_of(m, x);
-            atomicAdd(&A.grad_c[(size_t)ev * A.nvox + v], suffix * sm.sig_a[tab_sig_a_at(S.B, ev, b)] / k.dye[ev]);
+            if (FLR_CHK(v >= 0 && v < A.nvox, CK_GRAD, v))
+                atomicAdd(&A.grad_c[(size_t)ev * A.nvox + v], suffix * sm.sig_a[tab_sig_a_at(S.B, ev, b)] / k.dye[ev]);
         }
     }
 };
@@ -1800,6 +1844,7 @@ struct March {
 __device__ __forceinline__ void wq_push(const Queue &q, const Conn &c, float w, int ord)
 {
     const int slot = atomicAdd(&q.head_tail[1], 1) % WQ_CAP;
+    (void)FLR_CHK(q.head_tail[1] <= WQ_CAP, CK_QUEUE, slot);   // a wrap would overwrite a waiting record
     q.x[slot] = c.x.x;
     q.y[slot] = c.x.y;
     q.z[slot] = c.x.z;
@@ -1819,11 +1864,12 @@ __device__ __forceinline__ void march_deposit(const SceneDev &S, const RunDev &R
     const float val = mc.wg * mc.T * R.film_scale;
     if (!(val > 0.0f)) return;
     if (MODE == WM_RENDER) {
-        atomicAdd(&R.film[(size_t)mc.pix * S.B + mc.b], val);
+        film_add(S, R, (size_t)mc.pix * S.B + mc.b, val);
     } else {
         const float a = __ldg(&A.adj[(size_t)mc.pix * S.B + mc.b]) * val;
         if (a == 0.0f) return;
         const uint64_t i = mc.pid - R.path_offset;
+        if (!FLR_CHK(i < R.n_paths, CK_ADJ_STORE, (long long)i)) return;
         if (mc.ord < A.K) A.ak[i * A.K + mc.ord] = a;
         else atomicAdd(&A.ovf[i], a);
     }
@@ -2114,6 +2160,7 @@ __host__ __device__ inline SmemLayout hero_warp_layout(int B, int block)
 __device__ __forceinline__ void hq_push(const HQueue &q, const Conn &c, const HeroSet &h)
 {
     const int slot = atomicAdd(&q.head_tail[1], 1);
+    if (!FLR_CHK(slot < HQ_CAP, CK_QUEUE, slot)) return;
     q.x[slot] = c.x.x;
     q.y[slot] = c.x.y;
     q.z[slot] = c.x.z;
@@ -2145,7 +2192,7 @@ __device__ __forceinline__ void hero_deposit(const SceneDev &S, const RunDev &R,
     for (int j = 0; j < HERO_MAX; ++j) {
         if (j < hm.n) {
             const float val = (hm.n == 1 ? hm.mc.wg * hm.T[j] : hm.mc.wg * hm.q[j] * hm.T[j]) * R.film_scale;
-            if (val > 0.0f) atomicAdd(&R.film[(size_t)hm.mc.pix * S.B + hm_bin(hm, j)], val);
+            if (val > 0.0f) film_add(S, R, (size_t)hm.mc.pix * S.B + hm_bin(hm, j), val);
         }
     }
 }
@@ -2637,7 +2684,7 @@ __global__ void __launch_bounds__(256) k_trace_camera(SceneDev S, RunDev R)
                                                                            r.g.bx, cp.pid, step, rc, NoSink{});
             const float val = r.wt * T;
             if (val != 0.0f) {
-                atomicAdd(&R.film[(size_t)cp.pix * S.B + cp.bin], val);
+                film_add(S, R, (size_t)cp.pix * S.B + cp.bin, val);
                 rc.connections++;
             }
         }
@@ -2714,7 +2761,7 @@ __global__ void __launch_bounds__(256, 2) k_trace_camera_warp(SceneDev S, RunDev
             const CamRec r = camera_step(S, R, sm, cp, rc);
             if (r.valid) {
                 const int slot = atomicAdd(tail, 1);
-                float *f = qf + slot;
+                float *f = qf + (FLR_CHK(slot < CQ_CAP, CK_QUEUE, slot) ? slot : CQ_CAP - 1);
                 f[0 * CQ_CAP] = r.g.start.x;
                 f[1 * CQ_CAP] = r.g.start.y;
                 f[2 * CQ_CAP] = r.g.start.z;
@@ -2764,7 +2811,7 @@ __global__ void __launch_bounds__(256, 2) k_trace_camera_warp(SceneDev S, RunDev
                             const float Tc = !(sb > 0.0f) ? 1.0f : __expf(-sigma_t_at(m, x0, bx) * tl);
                             const float val = wt * Tc;
                             if (val != 0.0f) {
-                                atomicAdd(&R.film[(size_t)pix * S.B + bin], val);
+                                film_add(S, R, (size_t)pix * S.B + bin, val);
                                 rc.connections++;
                             }
                         } else {
@@ -2793,7 +2840,7 @@ __global__ void __launch_bounds__(256, 2) k_trace_camera_warp(SceneDev S, RunDev
                         if (t >= tl) {
                             const float val = wt * T;
                             if (val != 0.0f) {
-                                atomicAdd(&R.film[(size_t)pix * S.B + bin], val);
+                                film_add(S, R, (size_t)pix * S.B + bin, val);
                                 rc.connections++;
                             }
                             active = false;
@@ -3056,6 +3103,41 @@ int num_sms() { return device_sms(); }
 // ---------------------------------------------------------------------------------------------
 // Launchers.
 int trace_block_default() { return 256; }
+
+namespace {
+__global__ void k_debug_check(long long index, long long bound)
+{
+    (void)FLR_CHK(index >= 0 && index < bound, CK_DEBUG, index);
+}
+}  // namespace
+
+int checked_build()
+{
+#ifdef FLR_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+cudaError_t check_word_take(unsigned long long *word)
+{
+    *word = 0ull;
+#ifdef FLR_CHECKED
+    cudaError_t e = cudaMemcpyFromSymbol(word, g_check_word, sizeof(*word));
+    if (e != cudaSuccess || *word == 0ull) return e;
+    const unsigned long long zero = 0ull;
+    return cudaMemcpyToSymbol(g_check_word, &zero, sizeof(zero));
+#else
+    return cudaSuccess;
+#endif
+}
+
+cudaError_t launch_debug_check(long long index, long long bound, cudaStream_t st)
+{
+    k_debug_check<<<1, 1, 0, st>>>(index, bound);
+    return cudaGetLastError();
+}
 
 int trace_smem_bytes(int B, int form, int block) { return smem_layout(B, form, block).total_bytes; }
 

@@ -43,9 +43,10 @@ COUNTER_NAMES = [
     "steps", "majorant_violations", "connect_steps", "connect_budget", "nonfinite", "cell_walks",
 ]
 
+FLR_ERR_CHECK = -6
 ERROR_NAMES = {FLR_OK: "FLR_OK", FLR_ERR_ARG: "FLR_ERR_ARG", FLR_ERR_CUDA: "FLR_ERR_CUDA",
                FLR_ERR_OOM: "FLR_ERR_OOM", FLR_ERR_BUDGET: "FLR_ERR_BUDGET",
-               FLR_ERR_STATE: "FLR_ERR_STATE"}
+               FLR_ERR_STATE: "FLR_ERR_STATE", FLR_ERR_CHECK: "FLR_ERR_CHECK"}
 
 
 class flr_source(C.Structure):
@@ -115,6 +116,8 @@ SIGNATURES = {
                                    C.c_void_p]),
     "flr_debug_sample_emission": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64,
                                             C.c_void_p, C.c_void_p]),
+    "flr_checked_build": (C.c_int, []),
+    "flr_debug_check": (C.c_int, [C.c_int64, C.c_int64, C.c_void_p]),
 }
 
 _lock = threading.Lock()
@@ -122,7 +125,9 @@ _lib = None
 
 
 def library_path():
-    return _build.LIB
+    """libfluoro.so, or libfluoro_checked.so when the environment sets FLR_CHECKED=1 (the build
+    that tests every device index before its access)."""
+    return _build.LIB_CHECKED if os.environ.get("FLR_CHECKED") == "1" else _build.LIB
 
 
 def load(build_if_missing=False):
@@ -130,10 +135,10 @@ def load(build_if_missing=False):
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
+            path = library_path()
             if not os.path.exists(path):
                 if build_if_missing:
-                    _build.build()
+                    _build.build(checked=path == _build.LIB_CHECKED)
                 else:
                     raise RuntimeError(
                         f"{path} is missing: build it with `python -m paper_1706_03024_gb300.build`"
@@ -220,6 +225,14 @@ def flr_last_error(ctx):
 def flr_debug_philox(seed, medium, ctr_ptr, n, out_ptr, stream=0):
     return load().flr_debug_philox(int(seed), int(medium), ctr_ptr, int(n), out_ptr,
                                    C.c_void_p(int(stream)))
+
+
+def flr_checked_build():
+    return load().flr_checked_build()
+
+
+def flr_debug_check(index, bound, stream=0):
+    return load().flr_debug_check(int(index), int(bound), C.c_void_p(int(stream)))
 
 
 def flr_debug_sample_emission(ctx, dye, u_ptr, n, out_ptr, stream=0):

@@ -45,6 +45,18 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(declared_functions()) == set(N.SIGNATURES), "binding and header disagree"
 
 
+def test_checked_build_exports_the_same_symbols(lib):
+    """libfluoro_checked.so (FLR_CHECKED: device index tests) is the same boundary."""
+    B.build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_CHECKED], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\b(flr_\w+)\b", out))
+    assert set(declared_functions()) <= exported
+    chk = C.CDLL(B.LIB_CHECKED)
+    assert chk.flr_checked_build() == 1
+    assert lib.flr_checked_build() == 0
+
+
 def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "sizes.c"
     src.write_text(
