@@ -113,11 +113,14 @@ def kernel_traffic(name):
     try:
         with open(os.path.join(ROOT, "profiles", name)) as f:
             info = json.load(f)
-        with open(os.path.join(ROOT, info["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        h = hashlib.sha256()
+        for src in info["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        sha = h.hexdigest()
     except (OSError, ValueError, KeyError):
         return None
-    return info.get("bytes_per_launch") if sha == info.get("source_sha256") else None
+    return info.get("bytes_per_launch") if sha == info.get("sources_sha256") else None
 
 
 def cpu_oracle_rate(sc, n_paths, n_threads=0, film=True):

