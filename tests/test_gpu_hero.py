@@ -34,6 +34,9 @@ def workloads():
         ("light sheet", sg.cfg5_light_sheet(grid=32, width=24, height=24, n_blobs=40, n_paths=1,
                                             sigma_t_ref=20.0), {}),
         ("two beams", two_beams(2.0, [0.7, 0.5]), {}),
+        ("cornell box, analog, one re-emission",
+         sg.cfg2_cornell_box(width=24, height=24, grid=32, n_paths=1),
+         {"analog": 1, "max_inelastic": 1}),
     ]
 
 
@@ -41,7 +44,7 @@ def _fixed(x):
     return np.round(np.asarray(x, np.float64) * 2.0 ** 24).astype(np.int64)
 
 
-@pytest.mark.parametrize("case", range(5))
+@pytest.mark.parametrize("case", range(6))
 def test_one_member_is_the_plain_kernel(case):
     name, sc, kw = workloads()[case]
     S = Scene(sc)
@@ -62,7 +65,7 @@ def test_one_member_is_the_plain_kernel(case):
         assert torch.allclose(fa, fb, rtol=1e-5, atol=1e-7 * float(fa.abs().max())), name
 
 
-@pytest.mark.parametrize("case", range(5))
+@pytest.mark.parametrize("case", range(6))
 def test_hero_matches_oracle_hero(case):
     name, sc, kw = workloads()[case]
     K, n = 16, 2500
@@ -101,7 +104,7 @@ def test_hero_matches_oracle_hero(case):
 BENCH_LAUNCH = {"form": "wavefront_warp", "block_size": 128, "regroup": 1}
 
 
-@pytest.mark.parametrize("case", range(5))
+@pytest.mark.parametrize("case", range(6))
 def test_warp_form_equals_plain_form(case):
     """The warp-regrouped hero kernel traces the same paths and marches as the plain one: identical
     fixed-point tallies, counters and per-path event counts, the same film up to atomic order; with

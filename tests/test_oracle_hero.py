@@ -262,3 +262,23 @@ def test_emission_block_through_a_quencher_matches_quadrature():
     ma, sea = batch_mean_se([o["absorbed"][1][band] for o in outs])
     za = (ma - (qy * pmf[band] * (dens[:, None] * (1.0 - A)).sum(axis=0))) / sea
     assert np.abs(za).max() <= 4.5, np.round(za, 1)
+
+
+@pytest.mark.parametrize("mode", [{"analog": 1}, {"max_inelastic": 1}, {"analog": 1, "max_inelastic": 0}])
+def test_hero_modes_match_single_wavelength(mode):
+    """Analog coins (QY and wall albedo) and a cap on re-emissions act on the hero's weight and
+    decisions alone; the expectation is still the single-wavelength estimator's."""
+    sc = sg.cfg2_cornell_box(width=16, height=16, grid=24, n_paths=1)
+    K, n = 16, 3000
+    a = batches(sc, K, n, **mode)
+    b = [oracle.render(sc, n_paths=n, path_offset=k * n, seed=777, hero=4, **mode) for k in range(K)]
+    for key in ("face", "absorbed", "emitted"):
+        ga, gb = np.stack([o[key] for o in a]), np.stack([o[key] for o in b])
+        ma, sa = batch_mean_se(ga)
+        mb, sb = batch_mean_se(gb)
+        pop = ((ga != 0).sum(axis=0) >= K) & ((gb != 0).sum(axis=0) >= K)
+        v = parity_verdict(ma, np.where(pop, sa, 0), mb, np.where(pop, sb, 0))
+        assert v["ok"], (mode, key, v)
+        ta, sta = batch_mean_se(ga.reshape(K, -1).sum(axis=1))
+        tb, stb = batch_mean_se(gb.reshape(K, -1).sum(axis=1))
+        assert abs(ta - tb) <= 4 * math.hypot(sta, stb) + 1e-12, (mode, key, ta, tb)
