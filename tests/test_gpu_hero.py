@@ -15,7 +15,7 @@ import scenegen as sg
 from paper_1706_03024_gb300 import native as N
 from paper_1706_03024_gb300.scene import Scene
 from tests.gpu_common import bin_parity, compare_integrated, require_gpu, totals
-from tests.test_oracle_hero import two_beams
+from tests.test_oracle_hero import ragged_spectrum_scene, two_beams
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +37,7 @@ def workloads():
         ("cornell box, analog, one re-emission",
          sg.cfg2_cornell_box(width=24, height=24, grid=32, n_paths=1),
          {"analog": 1, "max_inelastic": 1}),
+        ("ten bins, ragged blocks, five lines", ragged_spectrum_scene(), {}),
     ]
 
 
@@ -44,7 +45,7 @@ def _fixed(x):
     return np.round(np.asarray(x, np.float64) * 2.0 ** 24).astype(np.int64)
 
 
-@pytest.mark.parametrize("case", range(6))
+@pytest.mark.parametrize("case", range(7))
 def test_one_member_is_the_plain_kernel(case):
     name, sc, kw = workloads()[case]
     S = Scene(sc)
@@ -65,7 +66,7 @@ def test_one_member_is_the_plain_kernel(case):
         assert torch.allclose(fa, fb, rtol=1e-5, atol=1e-7 * float(fa.abs().max())), name
 
 
-@pytest.mark.parametrize("case", range(6))
+@pytest.mark.parametrize("case", range(7))
 def test_hero_matches_oracle_hero(case):
     name, sc, kw = workloads()[case]
     K, n = 16, 2500
@@ -104,7 +105,7 @@ def test_hero_matches_oracle_hero(case):
 BENCH_LAUNCH = {"form": "wavefront_warp", "block_size": 128, "regroup": 1}
 
 
-@pytest.mark.parametrize("case", range(6))
+@pytest.mark.parametrize("case", range(7))
 def test_warp_form_equals_plain_form(case):
     """The warp-regrouped hero kernel traces the same paths and marches as the plain one: identical
     fixed-point tallies, counters and per-path event counts, the same film up to atomic order; with

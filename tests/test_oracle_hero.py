@@ -282,3 +282,38 @@ def test_hero_modes_match_single_wavelength(mode):
         ta, sta = batch_mean_se(ga.reshape(K, -1).sum(axis=1))
         tb, stb = batch_mean_se(gb.reshape(K, -1).sum(axis=1))
         assert abs(ta - tb) <= 4 * math.hypot(sta, stb) + 1e-12, (mode, key, ta, tb)
+
+
+def ragged_spectrum_scene(n_paths=1):
+    """Ten bins of 40 nm (the last emission block holds two bins when C = 4), two dyes emitting
+    into the top bins, five beam lines in one source (blocks of four lines and one)."""
+    B, lam0, dl = 10, 400.0, 40.0
+    lam = lam0 + dl * np.arange(B)
+    dyes = {"abs_shape": np.stack([np.exp(-0.5 * ((lam - a) / 60.0) ** 2) for a in (440.0, 560.0)]
+                                  ).astype(np.float32),
+            "emit_spec": np.stack([np.exp(-0.5 * ((lam - e) / 50.0) ** 2) for e in (700.0, 760.0)]
+                                  ).astype(np.float32),
+            "eps": np.array([1.2, 0.8], np.float32), "qy": np.array([0.8, 0.6], np.float32)}
+    return {"spectrum": {"lambda0": lam0, "dlambda": dl, "n_bins": B}, "dyes": dyes,
+            "medium": sg.homogeneous_medium(2, conc=1.0, sigma_s=3.0),
+            "sources": [sg.pencil_beam((0.5, 0.5, 1.0), (0, 0, -1), [400.0, 440.0, 520.0, 600.0, 640.0])],
+            "sensor": sg.ortho_sensor(8, 8, (0, 0, 1), (1, 0, 0), (0, 1, 0), (0, 0, 1)),
+            "params": sg.params(n_paths, seed=4)}
+
+
+def test_ragged_blocks_match_single_wavelength():
+    sc = ragged_spectrum_scene()
+    K, n = 16, 4000
+    a = batches(sc, K, n)
+    b = [oracle.render(sc, n_paths=n, path_offset=k * n, seed=55, hero=4) for k in range(K)]
+    for key in ("face", "absorbed", "emitted", "film"):
+        ga, gb = np.stack([o[key] for o in a]), np.stack([o[key] for o in b])
+        ma, sa = batch_mean_se(ga)
+        mb, sb = batch_mean_se(gb)
+        pop = ((ga != 0).sum(axis=0) >= K) & ((gb != 0).sum(axis=0) >= K)
+        v = parity_verdict(ma, np.where(pop, sa, 0), mb, np.where(pop, sb, 0),
+                           frac_limit=0.02, chi_hi=1.3)
+        assert v["ok"], (key, v)
+        ta, sta = batch_mean_se(ga.reshape(K, -1).sum(axis=1))
+        tb, stb = batch_mean_se(gb.reshape(K, -1).sum(axis=1))
+        assert abs(ta - tb) <= 4 * math.hypot(sta, stb) + 1e-12, (key, ta, tb)
