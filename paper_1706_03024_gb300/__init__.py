@@ -7,11 +7,11 @@ raises if it is missing.
 """
 from . import build  # noqa: F401
 
-__all__ = ["build", "native", "scene", "shard"]
+__all__ = ["build", "native", "scene", "shard", "units"]
 
 
 def __getattr__(name):
-    if name in ("native", "scene", "shard"):
+    if name in ("native", "scene", "shard", "units"):
         import importlib
         return importlib.import_module(f".{name}", __name__)
     raise AttributeError(name)
