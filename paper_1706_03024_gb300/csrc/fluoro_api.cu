@@ -14,8 +14,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fluoro.h"
 #include "fluoro_internal.cuh"
+
+namespace {
+// An NVTX range over one C-ABI call, so that a whole-program trace shows the library's calls
+// around their kernels (a no-op unless a profiling tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 using namespace flr;
 
@@ -575,6 +588,7 @@ int flr_set_sources(flr_ctx *ctx, int n, const flr_source *s)
 
 int flr_set_medium(flr_ctx *ctx, const flr_medium *m)
 {
+    const NvtxRange nvtx_range("flr_set_medium");
     if (!ctx) return FLR_ERR_ARG;
     int vrc = validate_medium(ctx, m);
     if (vrc != FLR_OK) return vrc;
@@ -656,6 +670,7 @@ int flr_set_sensor(flr_ctx *ctx, const flr_sensor *c)
 
 int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
 {
+    const NvtxRange nvtx_range("flr_render");
     if (!ctx) return FLR_ERR_ARG;
     if (!p) return fail(ctx, FLR_ERR_ARG, "params: NULL");
     if (ctx->B <= 0 || !ctx->medium_set) return fail(ctx, FLR_ERR_STATE, "render: spectrum, dyes and medium must be set");
@@ -735,6 +750,7 @@ static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem,
 
 int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
 {
+    const NvtxRange nvtx_range("flr_render_camera");
     if (!ctx) return FLR_ERR_ARG;
     if (!p) return fail(ctx, FLR_ERR_ARG, "params: NULL");
     if (ctx->B <= 0 || !ctx->medium_set) return fail(ctx, FLR_ERR_STATE, "camera: spectrum, dyes and medium must be set");
@@ -815,6 +831,7 @@ int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
 int flr_read_tallies(flr_ctx *ctx, double *face, double *absorbed, double *emitted,
                      uint64_t *counters, void *stream)
 {
+    const NvtxRange nvtx_range("flr_read_tallies");
     if (!ctx) return FLR_ERR_ARG;
     if (ctx->B <= 0) return fail(ctx, FLR_ERR_STATE, "read: no spectrum");
     DeviceGuard g(ctx->device);
@@ -920,6 +937,7 @@ constexpr uint64_t ADJ_CHUNK = 1ull << 21;
 int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float *grad_conc,
                 float *grad_sigma_s, void *stream)
 {
+    const NvtxRange nvtx_range("flr_adjoint");
     if (!ctx) return FLR_ERR_ARG;
     if (!p || !adj_film) return fail(ctx, FLR_ERR_ARG, "adjoint: params and adj_film are required");
     if (ctx->B <= 0 || !ctx->medium_set || ctx->sources.empty())
@@ -1034,6 +1052,7 @@ static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem,
 int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const uint64_t *n_paths,
                       const flr_params *p)
 {
+    const NvtxRange nvtx_range("flr_batch_prepare");
     if (!ctx) return FLR_ERR_ARG;
     if (n_media < 1 || n_media > 65536 || !media || !n_paths || !p)
         return fail(ctx, FLR_ERR_ARG, "batch: need 1..65536 media, path counts and params");
@@ -1207,6 +1226,7 @@ int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const 
 
 int flr_batch_launch(flr_ctx *ctx, void *stream)
 {
+    const NvtxRange nvtx_range("flr_batch_launch");
     if (!ctx) return FLR_ERR_ARG;
     if (!ctx->batch.ready) return fail(ctx, FLR_ERR_STATE, "batch: prepare it first");
     DeviceGuard g(ctx->device);
@@ -1248,6 +1268,7 @@ int flr_batch_read(flr_ctx *ctx, double *face, double *absorbed, double *emitted
 int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const uint64_t *n_paths,
                      const flr_params *p, void *stream)
 {
+    const NvtxRange nvtx_range("flr_render_batch");
     int rc = flr_batch_prepare(ctx, n_media, media, n_paths, p);
     if (rc != FLR_OK) return rc;
     return flr_batch_launch(ctx, stream);
