@@ -95,7 +95,8 @@ typedef struct flr_source {
  * wall_mask are Lambertian walls of albedo wall_albedo; the others are open. */
 typedef struct flr_medium {
     float lo[3], hi[3];          /* box, cm                                                    */
-    int dims[3];                 /* nx, ny, nz of the grids; ignored when no grid is given     */
+    int dims[3];                 /* nx, ny, nz of the grids, each 1..4096 and nx*ny*nz below
+                                    2^31 (FLR_ERR_ARG otherwise); ignored when no grid is given */
     int n_dyes;                  /* 0..FLR_MAX_DYES_PER_MEDIUM                                 */
     int dye_ids[FLR_MAX_DYES_PER_MEDIUM];        /* rows of the dye table                     */
     const float *conc[FLR_MAX_DYES_PER_MEDIUM];  /* device grids, or NULL => conc_uniform[d]  */

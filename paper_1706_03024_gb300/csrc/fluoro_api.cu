@@ -429,6 +429,9 @@ int validate_medium(flr_ctx *ctx, const flr_medium *m)
     if (grids) {
         for (int k = 0; k < 3; ++k)
             if (m->dims[k] < 1 || m->dims[k] > 4096) return fail(ctx, FLR_ERR_ARG, "medium: dims 1..4096");
+        // the kernels index voxels with 32-bit integers
+        if ((long long)m->dims[0] * m->dims[1] * m->dims[2] > 2147483647LL)
+            return fail(ctx, FLR_ERR_ARG, "medium: at most 2^31 - 1 voxels");
         for (int d = 0; d < m->n_dyes; ++d)
             if (m->conc[d] && !is_device_pointer(m->conc[d]))
                 return fail(ctx, FLR_ERR_ARG, "medium: concentration grids must be device memory");

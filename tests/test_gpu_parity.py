@@ -305,6 +305,10 @@ def test_invalid_arguments_are_rejected():
     neg = torch.full((4, 4, 4), -1.0, device="cuda")
     m.conc[0] = neg.data_ptr()
     assert N.flr_set_medium(ctx, m) == N.FLR_ERR_ARG
+    m.dims[:] = (4096, 4096, 128)   # 2^31 voxels: rejected before any grid is read
+    assert N.flr_set_medium(ctx, m) == N.FLR_ERR_ARG
+    assert "2^31" in N.flr_last_error(ctx)
+    m.dims[:] = (4, 4, 4)
     par = N.flr_params()
     par.n_paths = 10
     par.max_steps = 100
