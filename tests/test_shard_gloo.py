@@ -82,3 +82,45 @@ def test_two_gloo_ranks_reproduce_the_whole_job():
     for key in ("face", "absorbed", "emitted", "film"):
         np.testing.assert_allclose(job[key], whole[key], rtol=1e-12, atol=1e-15, err_msg=key)
     assert job["counters"] == whole["counters"]
+
+
+def _worker_with_failure(rank, world, port, out_q):
+    """Rank 1 fails on the host before the reduction (it exits without joining the collective);
+    rank 0 must learn of it as an error from its collective within the group's timeout, not hang."""
+    import datetime
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=10))
+    from paper_1706_03024_gb300 import shard
+    if rank == 1:
+        os._exit(3)   # the failing rank leaves between steps, nothing in flight
+    try:
+        shard.reduce_scalar(1.0, "sum")
+        out_q.put("no error")
+    except Exception as e:   # gloo reports the lost peer (closed connection or timeout)
+        out_q.put("error: " + type(e).__name__)
+
+
+def test_a_failed_rank_is_reported_to_the_others():
+    import multiprocessing as mp
+    import time
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_with_failure, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    try:
+        msg = q.get(timeout=120)
+    finally:
+        for p in procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.kill()
+    assert msg.startswith("error"), msg
+    assert time.time() - t0 < 110
+    assert procs[1].exitcode == 3
