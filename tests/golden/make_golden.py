@@ -28,6 +28,21 @@ def main():
     with open(os.path.join(HERE, "cfg1_512_paths.json"), "w") as f:
         json.dump(out, f, indent=1)
 
+    # hero-wavelength paths (four members) on a small Cornell box
+    sc = sg.cfg2_cornell_box(width=16, height=16, grid=24, n_paths=512)
+    r = oracle.render(sc, n_threads=1, path_events=True, hero=4)
+    out = {
+        "scene": "cfg2_cornell_box(width=16, height=16, grid=24) (scenegen), seed 0, paths 0..511, hero 4",
+        "path_events": [int(v) for v in r["path_events"]],
+        "counters": r["counters"],
+        "face": [float(v) for v in r["face"].ravel()],
+        "absorbed": [float(v) for v in r["absorbed"].ravel()],
+        "emitted": [float(v) for v in r["emitted"].ravel()],
+        "film_total": float(r["film"].sum()),
+    }
+    with open(os.path.join(HERE, "cfg2_hero4_512_paths.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
 
 if __name__ == "__main__":
     main()

@@ -17,3 +17,15 @@ def test_oracle_matches_stored_cfg1_paths():
     assert [int(v) for v in r["path_events"]] == g["path_events"]
     assert r["counters"] == g["counters"]
     assert np.allclose(r["face"].sum(axis=2).ravel(), g["face_total"], rtol=1e-12, atol=1e-15)
+
+
+def test_oracle_matches_stored_hero_paths():
+    with open(os.path.join(HERE, "cfg2_hero4_512_paths.json")) as f:
+        g = json.load(f)
+    sc = sg.cfg2_cornell_box(width=16, height=16, grid=24, n_paths=512)
+    r = oracle.render(sc, n_threads=2, path_events=True, hero=4)
+    assert [int(v) for v in r["path_events"]] == g["path_events"]
+    assert r["counters"] == g["counters"]
+    for key in ("face", "absorbed", "emitted"):
+        assert np.allclose(r[key].ravel(), g[key], rtol=1e-10, atol=1e-15), key
+    assert abs(r["film"].sum() - g["film_total"]) <= 1e-10 * abs(g["film_total"])
