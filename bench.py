@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -34,19 +35,64 @@ import scenegen as sg  # noqa: E402
 METRIC = "medium events/s (fwd, batched, adjoint) vs plain GPU kernel at equal RMSE"
 WORKLOAD = "cornell box: 4 dye spheres, 128^3 x4 fp32 grids, 512x512 pinhole x 81 bins, 16 spp"
 
-# 32-bit lane operations per unit of work ("ALU roofline"): a Philox4x32-10 block,
-# a tracking step, a real event, a sensor connection, a ratio-tracking step and a cell walk.
-OPS_PHILOX = 112
-OPS_STEP = OPS_PHILOX + 55
-OPS_EVENT = OPS_PHILOX + 30
+# Algorithmic work per unit, as the hot-path scope table counts it (32-bit lane operations):
+#   tracking step       one uniform (a quarter of a Philox4x32-10 block, about 15 integer
+#                       operations), one MUFU logarithm and about 10 FP32 operations      -> 26
+#   real event (extra)  three uniforms, sincos and a square root, about 30 FP32           -> 78
+#   sensor connection   projection into the film and visibility                           -> 45
+#   ratio-tracking step as a tracking step                                                -> 26
+# Empty-space leaps and local-majorant cell visits are optimisations of the kernels, not work the
+# method asks for, so they are not counted. MUFU (special-function unit) operations per unit:
+# a logarithm per tracking or ratio-tracking step, sincos and a square root per event, a
+# reciprocal square root and a reciprocal per pinhole connection.
+OPS_STEP = 26
+OPS_EVENT = 78
 OPS_CONNECT = 45
-OPS_CONNECT_STEP = OPS_PHILOX // 4 + 36
-OPS_CELL_WALK = 30   # an empty-space leap or a local-majorant cell visit
+OPS_CONNECT_STEP = 26
+MUFU_STEP, MUFU_EVENT, MUFU_CONNECT, MUFU_CONNECT_STEP = 1, 3, 2, 1
+
+# The kernels' random-number contract (one Philox4x32-10 block per (path, step, slot), so that any
+# decision can be replayed from its counter alone) draws whole blocks: a block is 112 lane
+# operations (10 rounds of 2 mul.lo + 2 mul.hi + 4 xor + 2 key adds, plus 4 x 3 for the uniforms).
+# Counted that way a tracking step is a block + 55, a real event a second block + 30, a
+# ratio-tracking step a quarter block + 36: reported beside the headline as `rng_contract`.
+OPS_PHILOX = 112
+RNG_OPS = {"steps": OPS_PHILOX + 55, "events": OPS_PHILOX + 30, "connections": 45,
+           "connect_steps": OPS_PHILOX // 4 + 36}
 
 
 def algorithmic_ops(c):
     return (c["steps"] * OPS_STEP + c["events"] * OPS_EVENT + c["connections"] * OPS_CONNECT
-            + c["connect_steps"] * OPS_CONNECT_STEP + c.get("cell_walks", 0) * OPS_CELL_WALK)
+            + c["connect_steps"] * OPS_CONNECT_STEP)
+
+
+def mufu_ops(c):
+    return (c["steps"] * MUFU_STEP + c["events"] * MUFU_EVENT + c["connections"] * MUFU_CONNECT
+            + c["connect_steps"] * MUFU_CONNECT_STEP)
+
+
+def rng_contract_ops(c):
+    return sum(c[k] * v for k, v in RNG_OPS.items())
+
+
+def rooflines(c, seconds, sms, sm_mhz):
+    """ALU roofline of one launch from its counters (headline), its MUFU ceiling and the ALU
+    figure under the random-number contract's counts. peak ALU = SMs x 128 lanes x clock; peak
+    MUFU = SMs x 16 x clock."""
+    f = sm_mhz * 1e6
+    alu_peak = sms * 128 * f
+    mufu_peak = sms * 16 * f
+    a = algorithmic_ops(c) / seconds
+    m = mufu_ops(c) / seconds
+    r = rng_contract_ops(c) / seconds
+    note = f"peak = {sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (maximum SM clock)"
+    return ({"bound": "alu", "achieved": a / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
+             "frac": a / alu_peak, "note": note},
+            {"bound": "mufu", "achieved": m / 1e12, "peak": mufu_peak / 1e12, "unit": "Tops/s",
+             "frac": m / mufu_peak, "ceiling_ms": 1000.0 * mufu_ops(c) / mufu_peak,
+             "note": f"peak = {sms} SMs x 16 x {sm_mhz:.0f} MHz"},
+            {"bound": "alu", "achieved": r / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
+             "frac": r / alu_peak, "note": "per-unit counts of the random-number contract"})
 
 
 def dist_env():
@@ -123,10 +169,27 @@ def kernel_traffic(name):
     return info.get("bytes_per_launch") if sha == info.get("sources_sha256") else None
 
 
-def cpu_oracle_rate(sc, n_paths, n_threads=0, film=True):
+def kernel_profile(name):
+    """Utilisation figures of a kernel from a committed ncu summary (issue slots, FP32 pipe, threads
+    per warp instruction, L2 hit rate, L2 reduction requests), or None once the kernel source has
+    changed since they were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            info = json.load(f)
+        h = hashlib.sha256()
+        for src in info["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+    except (OSError, ValueError, KeyError):
+        return None
+    return info.get("metrics") if h.hexdigest() == info.get("sources_sha256") else None
+
+
+def cpu_oracle_rate(sc, n_paths, n_threads=0, film=True, medium_id=0):
     import oracle
     t = time.perf_counter()
-    r = oracle.render(sc, n_paths=n_paths, n_threads=n_threads, film=film)
+    r = oracle.render(sc, n_paths=n_paths, n_threads=n_threads, film=film, medium_id=medium_id)
     dt = time.perf_counter() - t
     c = r["counters"]
     return {"events": c["events"], "paths": c["paths"], "seconds": dt}
@@ -163,19 +226,49 @@ def run_reference(args):
     return 0
 
 
+def cpu_rates(fn, sample, single_fraction=16):
+    """The oracle on the machine's host cores (all of them, then one) on a bounded sample:
+    fn(scale, n_threads) -> (events, paths) runs the sample (scale 1) or a 1/single_fraction
+    slice of it (scale 1/single_fraction)."""
+    out = {}
+    for name, scale, threads in (("all_cores", 1.0, 0), ("single_core", 1.0 / single_fraction, 1)):
+        t = time.perf_counter()
+        ev, paths = fn(scale, threads)
+        dt = time.perf_counter() - t
+        out[name] = {"events_per_s": ev / dt, "paths_per_s": paths / dt, "seconds": dt,
+                     "paths": paths}
+    return {"value": out["all_cores"]["events_per_s"], "unit": "events/s",
+            "cores": os.cpu_count() or 1, "kind": "oracle", "sample": sample,
+            "paths_per_s": out["all_cores"]["paths_per_s"], "seconds": out["all_cores"]["seconds"],
+            "single_core": {"value": out["single_core"]["events_per_s"], "unit": "events/s",
+                            "paths": out["single_core"]["paths"],
+                            "seconds": out["single_core"]["seconds"]}}
+
+
 def bench_batched(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum):
     """256 independent media (grid edges 16-128, 1-3 dyes, albedo 0.5-0.999, 1e4-1e6 paths each):
-    one persistent launch replayed from a CUDA graph, against the plain single-scene kernel run
-    medium by medium on the same paths (same estimator and paths: equal RMSE)."""
+    one persistent launch replayed from a CUDA graph, its block size and resident blocks per SM
+    chosen by the autotuner, against the plain single-scene kernel run medium by medium on the
+    same paths (same estimator and paths: equal RMSE)."""
     import torch
+    from paper_1706_03024_gb300.autotune import tune_batch
     from paper_1706_03024_gb300.scene import Batch, Scene
 
     media = sg.cfg3_batched_media(n_media=args.batch_media, seed=0)
-    bt = Batch(media, device=local, seed=rank, medium_id=0)
+    tune = None
+    block, bps = 0, 0
+    if args.autotune:
+        res = tune_batch(lambda b, k: Batch(media, device=local, seed=rank, medium_id=0,
+                                            block_size=b, blocks_per_sm=k))
+        block, bps = res.best.block_size, res.best.regroup
+        tune = {"chosen": {"block_size": block, "blocks_per_sm": bps},
+                "trials": [{"block_size": c.block_size, "blocks_per_sm": c.regroup,
+                            "events_per_s": v} for c, v in res.trials]}
+    bt = Batch(media, device=local, seed=rank, medium_id=0, block_size=block, blocks_per_sm=bps)
     for _ in range(max(1, args.warmup - 2)):
         bt.launch()
     torch.cuda.synchronize()
-    ms, events = [], 0
+    ms = []
     counters = None
     barrier()
     for i in range(args.batch_steps):
@@ -212,20 +305,36 @@ def bench_batched(args, local, rank, flush, stream, barrier, reduce_max, reduce_
     plain_value = reduce_sum(float(plain_events)) / (plain_ms / 1000.0)
     for S in scenes:
         S.close()
-    ops = algorithmic_ops(counters)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    peak = sms * 128 * float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
-    achieved = ops / (sum(ms) / len(ms) / 1000.0)
+    alu, mufu, rng = rooflines(counters, sum(ms) / len(ms) / 1000.0, sms,
+                               float(measured_peaks().get("sm_max_mhz", 2070.0)))
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        sub = media[:16]
+
+        def run(scale, threads):
+            ev_, paths = 0, 0
+            for m, sc in enumerate(sub):
+                n = max(int(int(sc["params"]["n_paths"]) * scale), 64)
+                r = cpu_oracle_rate(sc, n, n_threads=threads, film=False, medium_id=m)
+                ev_ += r["events"]
+                paths += n
+            return ev_, paths
+        cpu = cpu_rates(run, "the first 16 of the 256 media with their full path counts "
+                             "(fp64); one core: 1/16 of each medium's paths")
+    n_total = int(bt.n_paths.sum())
     bt.close()
     return {"workload": "256 media, edges 16-128, 1-3 dyes, albedo 0.5-0.999, 1e4-1e6 paths each"
-                        f" ({int(bt.n_paths.sum())} paths)",
-            "events_per_s": value, "ms_per_step": step_ms, "steps": len(ms),
+                        f" ({n_total} paths)",
+            "autotune": tune, "launch": {"block_size": block, "blocks_per_sm": bps},
+            "events_per_s": value, "paths_per_s": reduce_sum(float(n_total)) / (step_ms / 1000.0),
+            "ms_per_step": step_ms, "steps": len(ms),
             "ms_steps": [round(v, 3) for v in ms],
             "plain_per_medium_events_per_s": plain_value, "plain_ms": plain_ms,
             "plain_launches": len(media), "speedup_vs_plain": value / plain_value,
-            "events_per_step": counters["events"],
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                         "unit": "Tops/s", "frac": achieved / peak}}
+            "events_per_step": counters["events"], "counters_per_step": counters,
+            "roofline": alu, "roofline_mufu": mufu, "roofline_rng_contract": rng,
+            "cpu_baseline": cpu}
 
 
 def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum):
@@ -276,6 +385,19 @@ def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_
                                               form="plain"), args.adjoint_steps)
     ev = reduce_sum(float(events))
     chunks = -(-n // (1 << 21))   # the replay runs its two passes per chunk of 2^21 paths
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        adj_h = adj.double().cpu().numpy()
+        n1 = 256 * 256   # one path per pixel
+
+        def run(scale, threads):
+            m = max(int(n1 * scale), 256)
+            r = oracle.render(sc, n_paths=m, n_threads=threads, majorant_scale=1.0 + mg)
+            oracle.adjoint(sc, adj_h, n_paths=m, n_threads=threads, majorant_scale=1.0 + mg)
+            return r["counters"]["events"], m
+        cpu = cpu_rates(run, "65,536 paths (1 per pixel) of the same scene, forward render and "
+                             "path-replay adjoint (fp64; events of the forward over the time of both)")
     return {"workload": f"2 x 64^3 blob dyes, 256x256x81 ortho film, {n} paths, loss sum((I-T)^2)",
             "macro_cell": mc,
             "adjoint_events_per_s": ev / (adj_ms / 1000.0), "adjoint_ms": adj_ms,
@@ -286,7 +408,8 @@ def bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_
             "plain_events_per_s": ev / (plain_ms / 1000.0), "plain_ms": plain_ms,
             "adjoint_over_forward": adj_ms / fwd_ms, "events_per_step": events,
             "launches_per_step": 3 + 2 * chunks,
-            "grad_sigma_s": float(gs.item()), "grad_conc_abs_max": float(gc.abs().max().item())}
+            "grad_sigma_s": float(gs.item()), "grad_conc_abs_max": float(gc.abs().max().item()),
+            "cpu_baseline": cpu}
 
 
 def bench_paper(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum):
@@ -396,13 +519,22 @@ def bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_su
     plain_value = reduce_sum(float(c_p["events"])) / (plain_ms / 1000.0)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peaks = measured_peaks()
-    peak_ops = sms * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     t = sum(ms) / len(ms) / 1000.0
-    ops = algorithmic_ops(c)
+    alu, mufu, rng = rooflines(c, t, sms, float(peaks.get("sm_max_mhz", 2070.0)))
     gathers = c["steps"] + c["connect_steps"]
     D = int(sc["dyes"]["abs_shape"].shape[0])
     alg_bytes = 4 * D * gathers
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        n_cpu = args.sheet_cpu_paths
+
+        def run(scale, threads):
+            m = max(int(n_cpu * scale), 256)
+            r = cpu_oracle_rate(sc, m, n_threads=threads, film=True)
+            return r["events"], m
+        cpu = cpu_rates(run, f"{n_cpu} paths (1/{n // n_cpu} of the workload's) of the same scene "
+                             "with the film (fp64)")
     return {"workload": "light sheet: 256^3 x 4 blob dyes, albedo 0.999, 0.05 cm sheet at 488 nm, "
                         f"1024x1024x81 ortho film, {n} paths",
             "launch": kw, "events_per_s": value, "paths_per_s": reduce_sum(float(n)) / (step_ms / 1000.0),
@@ -410,8 +542,8 @@ def bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_su
             "plain_events_per_s": plain_value, "plain_ms": plain_ms, "plain_paths": n_plain,
             "speedup_vs_plain": value / plain_value,
             "per_path": {k: c[k] / n for k in ("events", "steps", "connections", "connect_steps")},
-            "roofline_alu": {"bound": "alu", "achieved": ops / t / 1e12, "peak": peak_ops / 1e12,
-                             "unit": "Tops/s", "frac": ops / t / peak_ops},
+            "roofline_alu": alu, "roofline_mufu": mufu, "roofline_rng_contract": rng,
+            "cpu_baseline": cpu,
             "roofline_hbm_gathers": {"bound": "hbm", "achieved": alg_bytes / t / 1e9, "peak": hbm,
                                      "unit": "GB/s", "frac": alg_bytes / t / 1e9 / hbm,
                                      "sector_frac": 8 * alg_bytes / D / t / 1e9 / hbm,
@@ -502,10 +634,9 @@ def run_ours(args):
         one_step("plain")
     torch.cuda.synchronize()
 
+    clock_dir = tempfile.mkdtemp(prefix="fluoro_clocks_")
     ms_w, ev_w, cnt_w, clocks = timed("wavefront", args.steps,
-                                      os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                                      if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                                      else f"/tmp/clocks_rank{rank}.csv")
+                                      os.path.join(clock_dir, f"clocks_rank{rank}.csv"))
     ms_p, ev_p, cnt_p, _ = timed("plain", max(1, min(args.steps, args.plain_steps)))
     step_ms_w_local = sum(ms_w) / len(ms_w)
 
@@ -620,14 +751,32 @@ def run_ours(args):
     e2e_s = reduce_max((time.perf_counter() - t0) / args.e2e_steps)
     e2e_value = reduce_sum(float(e2e_events / args.e2e_steps)) / e2e_s
 
+    # the trace kernel alone: the same launches without the tally and film clears (accumulate),
+    # timed with CUDA events on the launching stream
+    kevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        kevs[i][0].record(stream)
+        S.render(path_offset=offset, accumulate=True, **tuned)
+        kevs[i][1].record(stream)
+    torch.cuda.synchronize()
+    kernel_ms = reduce_max(sum(a.elapsed_time(b) for a, b in kevs) / args.steps)
+
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = sms * 128 * sm_max * 1e6
-    ops = algorithmic_ops(cnt_w)
-    achieved = ops / (sum(ms_w) / len(ms_w) / 1000.0)
-    traffic = kernel_traffic("trace_wavefront_warp_cornell_traffic.json")
+    alu, mufu, rng = rooflines(cnt_w, kernel_ms / 1000.0, sms, sm_max)
+    alu["kernel_ms"] = kernel_ms
+    alu["traffic"] = kernel_traffic("trace_wavefront_warp_cornell_traffic.json")
+    prof = kernel_profile("trace_wavefront_warp_cornell_ncu.json")
+    film_atomics = None
+    if prof and prof.get("film_red_requests_per_path"):
+        reqs = prof["film_red_requests_per_path"] * n_paths
+        film_atomics = {"requests_per_step": reqs, "per_s": reqs / (kernel_ms / 1000.0),
+                        "source": "ncu L2 reduction requests per path on the reduced capture, "
+                                  "scaled to the step's paths"}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -668,13 +817,14 @@ def run_ours(args):
                 "hero_wavelength": hero,
             },
             "counters_per_step": cnt_w,
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic,
-                         "note": f"32-bit lane ops from counters x per-unit counts; peak = {sms} SMs"
-                                 f" x 128 lanes x {sm_max:.0f} MHz"},
+            "roofline": alu,
+            "roofline_mufu": mufu,
+            "roofline_rng_contract": rng,
+            "ncu": prof,
+            "film_atomics": film_atomics,
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps + len(ms_p)
+            "gpu_launches": 2 * args.steps + len(ms_p)
             + (0 if batched is None else batched["steps"] + batched["plain_launches"])
             + (0 if adjoint is None else adjoint["launches_per_step"] * args.adjoint_steps)
             + (0 if paper is None else 2 * args.paper_steps)
@@ -728,6 +878,8 @@ def main():
     ap.add_argument("--no-sheet", action="store_true",
                     help="skip the full-size light-sheet workload (256^3 x 4 grids, 67M paths)")
     ap.add_argument("--sheet-steps", type=int, default=2)
+    ap.add_argument("--sheet-cpu-paths", type=int, default=1 << 18,
+                    help="light-sheet paths the CPU oracle baseline traces")
     ap.add_argument("--sheet-paths", type=int, default=0,
                     help="override the light-sheet path count (small profiling cases only)")
     ap.add_argument("--adjoint-paths", type=int, default=0,

@@ -263,6 +263,24 @@ int flr_read_tallies(flr_ctx *ctx, double *face, double *absorbed, double *emitt
 int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float *grad_conc,
                 float *grad_sigma_s, void *stream);
 
+/* Diagnostic for derivative checks of flr_adjoint (the paper has no derivatives). For the same
+ * paths as flr_adjoint with the same p, writes to device out [p->n_paths] (fp64, path i of the
+ * launch at out[i]) S_i = sum_k adj_film[pixel_k][bin_k] value_k(theta) W_k(theta): the path's
+ * adjoint-weighted film contributions under the frozen-sampling estimator at a perturbed medium
+ * theta = (dye slot pert_dye's concentration in voxel pert_voxel plus pert_delta (pert_dye -1:
+ * none), sigma_s plus pert_sigma_s). Every decision is sampled in the current medium as flr_adjoint
+ * replays it; the decisions theta changes enter through their likelihood ratios W (null collision
+ * (sigma_bar - sigma_t(theta)) / (sigma_bar - sigma_t), real collision with particle e
+ * sigma_e(theta) / sigma_e, Sec. 4.1), and each transmittance (Eq. 6) is the ratio-tracking
+ * product at theta over the same points, with flr_adjoint's roulette rule decided at the current
+ * medium. The sums are deterministic per path, so central differences
+ * (S_i(+h) - S_i(-h)) / 2h with common random numbers are smooth and sum to flr_adjoint's
+ * gradient up to O(h^2). p->macro_cell, skip_cell, paper_mode and hero must be 0 (FLR_ERR_ARG);
+ * a concentration perturbation needs a medium with grids. Asynchronous on `stream`. */
+int flr_debug_frozen_sums(flr_ctx *ctx, const flr_params *p, const float *adj_film, int pert_dye,
+                          int64_t pert_voxel, float pert_delta, float pert_sigma_s, double *out,
+                          void *stream);
+
 /* Batched persistent form (independent media in one launch). flr_batch_prepare validates n_media
  * media (each as flr_set_medium would; source rows via source_first/source_count, at most 8 lines
  * per medium; the sensor is not used), copies their grids into one library-owned interleaved
@@ -296,13 +314,16 @@ int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const u
  * p->n_paths). All scratch -- spectral tables, fixed-point tallies, counters, the work counter and
  * the interleaved copy of the grids -- lives in one static device array of 4 MiB + 64 KiB that
  * every GPU loading this library holds until the process exits; media with more than
- * FLR_NOALLOC_MAX_VOXELS voxels are rejected with FLR_ERR_ARG; p->macro_cell and p->majorant_margin are
- * ignored (one majorant per bin, no margin), and so is p->paper_mode; p->hero must be 0. The first call
- * on a device looks up
- * that array's device address (with that device current), so make that first call before any
- * stream capture. Every call uses the same array and clears what must start at zero, so calls
- * that overlap on the GPU (other streams, other host threads) race with each other. The call
- * synchronises `stream` (it reads grid maxima and the tallies back). */
+ * FLR_NOALLOC_MAX_VOXELS voxels are rejected with FLR_ERR_ARG. It renders the full RTE with one
+ * majorant per bin: p->paper_mode, p->macro_cell, p->skip_cell, p->majorant_margin and p->hero
+ * must be 0 (FLR_ERR_ARG otherwise; the array has no room for cell grids). The first call on a
+ * device looks up that array's device address (with that device current) and keeps it for the
+ * life of the process, so make that first call before any stream capture, and do not call this
+ * entry point on a device after cudaDeviceReset. Every call uses the same array and clears what
+ * must start at zero, so calls that overlap on the GPU (other streams, other host threads) race
+ * with each other. The call synchronises `stream` (it reads grid maxima and the tallies back).
+ * It returns FLR_ERR_BUDGET (outputs written) when a path or a connection ran out of its step
+ * budget, and in the checked build FLR_ERR_CHECK when a device index was out of range. */
 #define FLR_NOALLOC_MAX_VOXELS (1 << 18)
 int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins, int n_dyes,
                        const float *abs_shape, const float *emit_spec, const float *eps,
@@ -311,9 +332,12 @@ int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins, int n_dye
                        double *face, double *absorbed, double *emitted, uint64_t *counters,
                        void *stream);
 
-/* Synchronise the device and report the device error word (FLR_OK if clean). In the checked
- * build it also reports, and clears, the first device index found out of range since the last
- * call (FLR_ERR_CHECK; any context of the process sees it). */
+/* Synchronise the device and report, then clear, the context's device error word: FLR_ERR_BUDGET
+ * if a launch of this context since the previous flr_status cut a path or a sensor connection
+ * short at its step budget (max_steps, or 65,536 ratio-tracking steps; the tallies stay valid
+ * for the paths that finished, and the counters step_budget / connect_budget say how many),
+ * FLR_OK if clean. In the checked build it also reports, and clears, the first device index
+ * found out of range since the last call (FLR_ERR_CHECK; any context of the process sees it). */
 int flr_status(flr_ctx *ctx);
 const char *flr_last_error(flr_ctx *ctx);
 

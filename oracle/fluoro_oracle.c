@@ -43,14 +43,14 @@
 #define OR_MAX_DYES 4
 #define OR_MAX_EMITTERS 32
 #define OR_MAX_BINS 128
-#define OR_NCOUNTERS 16
+#define OR_NCOUNTERS 17
 #define OR_PI 3.14159265358979323846
 
 /* counters (same meaning as the GPU library's, defined independently) */
 enum {
     OC_PATHS = 0, OC_EVENTS, OC_NULLS, OC_ESCAPES, OC_ABSORBED_DEAD, OC_RR_KILLS, OC_CAP_HITS,
     OC_STEP_BUDGET, OC_CONNECTIONS, OC_VF_REJECTED, OC_WALL_BOUNCES, OC_EMISSIONS, OC_SCATTERS,
-    OC_DYE_ABSORPTIONS, OC_STEPS, OC_MAJORANT_VIOLATIONS
+    OC_DYE_ABSORPTIONS, OC_STEPS, OC_MAJORANT_VIOLATIONS, OC_IFACE_REFLECTIONS
 };
 
 typedef struct {
@@ -96,6 +96,16 @@ typedef struct {
     const or_emitter *emitters;
     /* sensor */
     or_sensor sensor;
+    /* Interfaces and glossy walls (the glass vials and the glossy Cornell box of Sec. 5; the
+     * paper specifies neither, these are the physically standard choices):
+     *   ior > 1: every open face is a smooth dielectric interface between the solution (index
+     *   ior) and the outside (index 1): Fresnel reflection for unpolarised light, Snell
+     *   refraction, total internal reflection beyond the critical angle. 0 or 1: index-matched.
+     *   wall BRDF: wall_albedo [(1 - g)/pi + g (e + 2)/(2 pi) cos^e alpha], g = wall_gloss,
+     *   e = wall_exponent, alpha the angle between the outgoing direction and the mirror
+     *   direction of the incoming one (a diffuse lobe plus a normalised Phong lobe). */
+    double ior;
+    double wall_gloss, wall_exponent;
 } or_scene;
 
 typedef struct {
@@ -213,6 +223,10 @@ typedef struct {
     double *mc_cmax;                         /* [cells][n_dyes] */
     double *mc_smax;                         /* [cells]         */
     int sk, sdims[3];
+    /* interfaces: dielectric open faces, the entry face of each emitter (-1: none) */
+    int dielectric;
+    double ior;
+    int entry_face[OR_MAX_EMITTERS];
     unsigned char *sk_dist;                  /* Chebyshev distance to a cell with matter */
 } tables;
 
@@ -442,6 +456,22 @@ static void build_tables(const or_scene *s, tables *t)
         t->em_bin[k] = snap_bin(s->emitters[k].lambda_nm, s->lambda0, s->dlambda, s->n_bins);
     }
     if (s->n_emitters > 0) t->em_cdf32[s->n_emitters - 1] = 1.0f;
+    /* dielectric open faces; an emitter enters through face f when its parallelogram lies in
+     * that face's plane and its direction (or normal) points into the box */
+    t->dielectric = s->ior > 1.0;
+    t->ior = t->dielectric ? s->ior : 1.0;
+    for (int k = 0; k < s->n_emitters; ++k) {
+        const or_emitter *e = &s->emitters[k];
+        t->entry_face[k] = -1;
+        if (!t->dielectric) continue;
+        for (int a = 0; a < 3 && t->entry_face[k] < 0; ++a) {
+            if (e->eu[a] != 0.0 || e->ev[a] != 0.0) continue;
+            int f = -1;
+            if (e->origin[a] == s->lo[a] && e->dir[a] > 0.0) f = 2 * a;
+            if (e->origin[a] == s->hi[a] && e->dir[a] < 0.0) f = 2 * a + 1;
+            if (f >= 0 && !(s->wall_mask & (1 << f))) t->entry_face[k] = f;
+        }
+    }
     const or_sensor *c = &s->sensor;
     if (c->kind == 1) {
         double lu = sqrt(c->U[0] * c->U[0] + c->U[1] * c->U[1] + c->U[2] * c->U[2]);
@@ -625,6 +655,72 @@ static void normal_axis(const double n[3], int *k, double *sign)
     for (int i = 1; i < 3; ++i) if (fabs(n[i]) > fabs(n[best])) best = i;
     *k = best;
     *sign = n[best] > 0.0 ? 1.0 : -1.0;
+}
+
+/* Fresnel equations for unpolarised light at a smooth interface from index n1 into n2: the
+ * reflected fraction (r_s^2 + r_p^2) / 2 for a ray meeting it at cos_i, and the refracted ray's
+ * cosine in cos_t (Snell: n1 sin_i = n2 sin_t); beyond the critical angle everything is reflected
+ * (total internal reflection, cos_t = 0). */
+static double fresnel(double cos_i, double n1, double n2, double *cos_t)
+{
+    double sin_t2 = (n1 / n2) * (n1 / n2) * fmax(0.0, 1.0 - cos_i * cos_i);
+    if (sin_t2 >= 1.0) { *cos_t = 0.0; return 1.0; }
+    double ct = sqrt(1.0 - sin_t2);
+    *cos_t = ct;
+    double rs = (n1 * cos_i - n2 * ct) / (n1 * cos_i + n2 * ct);
+    double rp = (n2 * cos_i - n1 * ct) / (n2 * cos_i + n1 * ct);
+    return 0.5 * (rs * rs + rp * rp);
+}
+
+/* A photon meets the plane of box face `face` (axis k = face / 2) moving along w, from index n1
+ * into n2. Returns 1 if it is reflected (w mirrored in the plane), 0 if refracted (w bent by
+ * Snell's law: tangential components scaled by n1 / n2, normal component cos_t with its sign). */
+static int interface_event(int face, double w[3], double n1, double n2, double u)
+{
+    int k = face / 2;
+    double ct;
+    double F = fresnel(fabs(w[k]), n1, n2, &ct);
+    if (u < F) {
+        w[k] = -w[k];
+        return 1;
+    }
+    double sg = w[k] > 0.0 ? 1.0 : -1.0;
+    for (int a = 0; a < 3; ++a) if (a != k) w[a] *= n1 / n2;
+    w[k] = sg * ct;
+    return 0;
+}
+
+/* Orthonormal tangents t1, t2 of a unit vector n (Duff, Burgess, Christensen, Hery, Kensler,
+ * Liani, Villemin, "Building an orthonormal basis, revisited", JCGT 2017). */
+static void tangent_frame(const double n[3], double t1[3], double t2[3])
+{
+    double sg = n[2] >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sg + n[2]);
+    double b = n[0] * n[1] * a;
+    t1[0] = 1.0 + sg * n[0] * n[0] * a; t1[1] = sg * b; t1[2] = -sg * n[0];
+    t2[0] = b; t2[1] = sg + n[1] * n[1] * a; t2[2] = -n[1];
+}
+
+/* Direction of the normalised Phong lobe about the unit vector r: density (e + 1)/(2 pi) cos^e
+ * alpha over the sphere around r, cos alpha = u1^(1/(e+1)), azimuth 2 pi u2 in r's tangent frame. */
+static void phong_dir(double u1, double u2, const double r[3], double e, double w[3])
+{
+    double ca = pow(u1, 1.0 / (e + 1.0));
+    double sa = sqrt(fmax(0.0, 1.0 - ca * ca));
+    double phi = 2.0 * OR_PI * u2;
+    double t1[3], t2[3];
+    tangent_frame(r, t1, t2);
+    for (int k = 0; k < 3; ++k) w[k] = sa * cos(phi) * t1[k] + sa * sin(phi) * t2[k] + ca * r[k];
+}
+
+/* Wall BRDF divided by the albedo, times the outgoing cosine cos_o, toward direction o for a
+ * photon whose mirror direction is r: (1 - g) cos_o / pi + g (e + 2)/(2 pi) cos^e alpha cos_o. */
+static double wall_brdf_cos(const or_scene *s, const double r[3], const double o[3], double cos_o)
+{
+    double g = s->wall_gloss, e = s->wall_exponent;
+    double ca = r[0] * o[0] + r[1] * o[1] + r[2] * o[2];
+    double lobe = ca > 0.0 ? (e + 2.0) / (2.0 * OR_PI) * pow(ca, e) : 0.0;
+    return ((1.0 - g) / OR_PI + g * lobe) * cos_o;
 }
 
 /* ---------------------------------------------------------------------------------------- */
@@ -1335,7 +1431,7 @@ int or_render(const or_scene *s, const or_params *p, or_result *r)
     if (r->film && s->sensor.kind)
         memset(r->film, 0, sizeof(double) * (size_t)s->sensor.width * s->sensor.height * B);
 #ifdef _OPENMP
-    if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+    omp_set_num_threads(p->n_threads > 0 ? p->n_threads : omp_get_num_procs());
 #endif
     int64_t N = (int64_t)p->n_paths;
 #pragma omp parallel
@@ -1603,7 +1699,7 @@ int or_render_camera(const or_scene *s, const or_params *p, double *film, uint64
     memset(film, 0, sizeof(double) * (size_t)npix * s->n_bins);
     memset(counters, 0, sizeof(uint64_t) * OR_NCOUNTERS);
 #ifdef _OPENMP
-    if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+    omp_set_num_threads(p->n_threads > 0 ? p->n_threads : omp_get_num_procs());
 #endif
     const int64_t N = (int64_t)p->n_paths;
     const double film_scale = N > 0 ? (double)npix / (double)N : 0.0;
@@ -1701,7 +1797,7 @@ int or_adjoint(const or_scene *s, const or_params *p, const double *adj, double 
     if (have_grid) memset(grad_c, 0, sizeof(double) * (size_t)D * nv);
     *grad_sigma_s = 0.0;
 #ifdef _OPENMP
-    if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+    omp_set_num_threads(p->n_threads > 0 ? p->n_threads : omp_get_num_procs());
 #endif
     const int64_t N = (int64_t)p->n_paths;
     const double inv_n = N > 0 ? 1.0 / (double)N : 0.0;

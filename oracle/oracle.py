@@ -22,7 +22,7 @@ _lib = None
 COUNTER_NAMES = [
     "paths", "events", "nulls", "escapes", "absorbed_dead", "rr_kills", "cap_hits", "step_budget",
     "connections", "vf_rejected", "wall_bounces", "emissions", "scatters", "dye_absorptions",
-    "steps", "majorant_violations",
+    "steps", "majorant_violations", "iface_reflections",
 ]
 
 MAX_DYES = 4
@@ -53,6 +53,7 @@ class Scene(C.Structure):
         ("wall_mask", C.c_int), ("wall_albedo", C.c_double),
         ("n_emitters", C.c_int), ("emitters", C.POINTER(Emitter)),
         ("sensor", Sensor),
+        ("ior", C.c_double), ("wall_gloss", C.c_double), ("wall_exponent", C.c_double),
     ]
 
 
@@ -185,6 +186,9 @@ class _SceneHolder:
         s.sigma_a0 = float(md["sigma_a0"])
         s.wall_mask = int(md["wall_mask"])
         s.wall_albedo = float(md["wall_albedo"])
+        s.ior = float(md.get("ior", 1.0))
+        s.wall_gloss = float(md.get("wall_gloss", 0.0))
+        s.wall_exponent = float(md.get("wall_exponent", 0.0))
         s.n_emitters = len(ems)
         s.emitters = C.cast(self.emitters, C.POINTER(Emitter))
         sn = scene["sensor"]
@@ -237,7 +241,7 @@ def render_camera(scene, n_paths, path_offset=0, seed=None, medium_id=0, n_threa
                 max_events, max_steps, 1.0, False, None)
     sn = scene["sensor"]
     film = np.zeros((sn["height"], sn["width"], h.n_bins))
-    counters = np.zeros(16, dtype=np.uint64)
+    counters = np.zeros(len(COUNTER_NAMES), dtype=np.uint64)
     rc = L.or_render_camera(C.byref(h.scene), C.byref(p), film.ctypes.data, counters.ctypes.data)
     if rc != 0:
         raise ValueError(f"oracle camera render rejected the scene (rc={rc})")
@@ -277,7 +281,7 @@ def _render(L, h, scene, p, film, path_events):
     face = np.zeros((2, 6, B))
     absorbed = np.zeros((D + 1, B))
     emitted = np.zeros((max(D, 1), B))
-    counters = np.zeros(16, dtype=np.uint64)
+    counters = np.zeros(len(COUNTER_NAMES), dtype=np.uint64)
     sn = scene["sensor"]
     fl = None
     if film and sn["kind"] != "none":

@@ -873,7 +873,13 @@ int flr_status(flr_ctx *ctx)
     int w = 0;
     e = cudaMemcpy(&w, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "read error word");
-    if (w) return fail(ctx, FLR_ERR_BUDGET, "device error word set");
+    if (w) {
+        // reported once: the word covers the launches since the previous flr_status
+        e = cudaMemset(ctx->d_error, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "clear error word");
+        return fail(ctx, FLR_ERR_BUDGET, "a path or a sensor connection ran out of its step budget "
+                                         "(counters step_budget / connect_budget)");
+    }
     unsigned long long cw = 0ull;
     e = check_word_take(&cw);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "read check word");
@@ -932,6 +938,59 @@ int flr_debug_sample_emission(flr_ctx *ctx, int dye, const float *u, int64_t n, 
 // Adjoint by path replay.
 
 static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem, const char *what);
+
+int flr_debug_frozen_sums(flr_ctx *ctx, const flr_params *p, const float *adj_film, int pert_dye,
+                          int64_t pert_voxel, float pert_delta, float pert_sigma_s, double *out,
+                          void *stream)
+{
+    const NvtxRange nvtx_range("flr_debug_frozen_sums");
+    if (!ctx) return FLR_ERR_ARG;
+    if (!p || !adj_film || !out) return fail(ctx, FLR_ERR_ARG, "frozen sums: params, adj_film and out are required");
+    if (ctx->B <= 0 || !ctx->medium_set || ctx->sources.empty())
+        return fail(ctx, FLR_ERR_STATE, "frozen sums: spectrum, dyes, medium and sources must be set");
+    if (!ctx->sensor_set) return fail(ctx, FLR_ERR_STATE, "frozen sums: needs a sensor");
+    if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
+        return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
+    if (p->hero != 0 || p->paper_mode != 0 || p->macro_cell != 0 || p->skip_cell != 0)
+        return fail(ctx, FLR_ERR_ARG, "frozen sums: one majorant per bin, no hero paths, no paper mode");
+    if (!(p->majorant_margin >= 0.0f && p->majorant_margin <= 100.0f))
+        return fail(ctx, FLR_ERR_ARG, "params: majorant_margin in [0, 100]");
+    if (!is_device_pointer(adj_film) || !is_device_pointer(out))
+        return fail(ctx, FLR_ERR_ARG, "frozen sums: adj_film and out must be device memory");
+    const long long nv = nvox(ctx->medium);
+    if (pert_dye >= ctx->medium.n_dyes || pert_dye < -1)
+        return fail(ctx, FLR_ERR_ARG, "frozen sums: pert_dye must be -1 or a dye slot of the medium");
+    if (pert_dye >= 0 && (!medium_has_grid(ctx->medium) || pert_voxel < 0 || pert_voxel >= nv))
+        return fail(ctx, FLR_ERR_ARG, "frozen sums: a concentration perturbation needs grids and a voxel inside them");
+    if (!std::isfinite(pert_delta) || !std::isfinite(pert_sigma_s))
+        return fail(ctx, FLR_ERR_ARG, "frozen sums: finite perturbations");
+    DeviceGuard g(ctx->device);
+    int rc = prepare_tables(ctx, p->majorant_margin);
+    if (rc != FLR_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    SceneDev S;
+    rc = fill_scene(ctx, S, true, 0, 0);
+    if (rc != FLR_OK) return rc;
+    if (p->n_paths == 0) return FLR_OK;
+    RunDev R;
+    std::memset(&R, 0, sizeof(R));
+    R.n_paths = p->n_paths;
+    R.path_offset = p->path_offset;
+    R.seed = p->seed;
+    R.medium_id = p->medium_id;
+    set_round_keys(R);
+    R.n_rr = p->n_rr;
+    R.max_inelastic = p->max_inelastic;
+    R.analog = p->analog;
+    R.max_events = p->max_events;
+    R.max_steps = p->max_steps;
+    R.film_scale = (float)(1.0 / (double)p->n_paths);
+    R.error_word = ctx->d_error;
+    cudaError_t e = launch_frozen_sums(S, R, pert_dye, (long long)pert_voxel, pert_delta, pert_sigma_s,
+                                       adj_film, out, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch frozen-sum kernel");
+    return FLR_OK;
+}
 
 // Contributions kept per path between the two adjoint passes, and paths replayed per pass pair.
 constexpr int ADJ_K = 32;
@@ -1351,6 +1410,10 @@ extern "C" int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return FLR_ERR_ARG;
     if (p->hero != 0) return FLR_ERR_ARG;   /* hero paths: flr_render only */
+    // one majorant per bin and the full RTE only: the static scratch holds no local-majorant or
+    // empty-space cell grid, and the other settings would change the tallies flr_render gives
+    if (p->paper_mode != 0 || p->skip_cell != 0 || p->macro_cell != 0 || p->majorant_margin != 0.0f)
+        return FLR_ERR_ARG;
     if (p->film && !is_device_pointer(p->film)) return FLR_ERR_ARG;
     if (p->path_events && !is_device_pointer(p->path_events)) return FLR_ERR_ARG;
     if (c.sensor_set && c.sensor.kind == FLR_SENSOR_PINHOLE) {
@@ -1433,10 +1496,15 @@ extern "C" int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins
     }
     std::vector<unsigned long long> t(tal_size(FLR_MAX_BINS));
     unsigned long long hc[FLR_NCOUNTERS];
+    int herr = 0;
     e = cudaMemcpyAsync(t.data(), tallies, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err_word, sizeof(herr), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return FLR_ERR_CUDA;
+    // checked build: an index found out of range during this call (the access was skipped)
+    unsigned long long cw = 0ull;
+    if (check_word_take(&cw) != cudaSuccess) return FLR_ERR_CUDA;
     const int B = c.B, D = mm.n_dyes;
     const double inv = p->n_paths ? 1.0 / ((double)p->n_paths * TALLY_ONE) : 0.0;
     if (face)
@@ -1447,5 +1515,6 @@ extern "C" int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins
         for (int i = 0; i < D * B; ++i) emitted[i] = (double)t[tal_emitted(B) + i] * inv;
     if (counters)
         for (int k = 0; k < FLR_NCOUNTERS; ++k) counters[k] = hc[k];
-    return FLR_OK;
+    if (cw) return FLR_ERR_CHECK;
+    return herr ? FLR_ERR_BUDGET : FLR_OK;
 }

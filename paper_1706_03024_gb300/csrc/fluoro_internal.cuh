@@ -197,6 +197,10 @@ cudaError_t launch_pack_grid(const float *const *conc, const float *uniform, int
 cudaError_t launch_solvent_any(const uint8_t *s, long long n, unsigned int *out, cudaStream_t st);
 cudaError_t launch_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, long long n,
                           uint32_t *out, cudaStream_t st);
+// frozen-sampling per-path sums of adj x film contributions at a perturbed medium (diagnostic)
+cudaError_t launch_frozen_sums(const SceneDev &S, const RunDev &R, int pert_dye, long long pert_voxel,
+                               float pert_delta, float pert_dsig, const float *adj, double *out,
+                               cudaStream_t st);
 cudaError_t launch_sample_emission(const SceneDev &S, int dye, const float *u, long long n,
                                    int32_t *out, cudaStream_t st);
 int trace_block_default();

@@ -1075,6 +1075,14 @@ __device__ __forceinline__ Smem block_prologue(const SceneDev &S, unsigned char 
     return sm;
 }
 
+// Sets the launch's error word when a path or a connection of this block ran out of its step
+// budget (flr_status then reports FLR_ERR_BUDGET). Called by every thread after a block barrier.
+__device__ __forceinline__ void budget_flag(const RunDev &R, const Smem &sm)
+{
+    if (threadIdx.x == 0 && R.error_word && (sm.cnt[FLR_C_STEP_BUDGET] | sm.cnt[FLR_C_CONNECT_BUDGET]))
+        atomicOr(R.error_word, 1);
+}
+
 __device__ __forceinline__ void block_epilogue(const SceneDev &S, const RunDev &R, const Smem &sm,
                                                const RegCnt &rc)
 {
@@ -1091,6 +1099,7 @@ __device__ __forceinline__ void block_epilogue(const SceneDev &S, const RunDev &
         if ((threadIdx.x & 31) == 0 && v) atomicAdd(&sm.cnt[idx[i]], v);
     }
     __syncthreads();
+    budget_flag(R, sm);
     if (!sm.tal_global)
         for (int i = threadIdx.x; i < tal_size(S.B); i += blockDim.x)
             if (sm.tal[i]) atomicAdd(&R.tallies[i], sm.tal[i]);
@@ -1806,6 +1815,149 @@ __global__ void __launch_bounds__(256, 1) k_adjoint(SceneDev S, RunDev R, AdjDev
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gsig += __shfl_xor_sync(0xffffffffu, gsig, o);
     if ((threadIdx.x & 31) == 0 && gsig != 0.0f && A.grad_sigma_s) atomicAdd(A.grad_sigma_s, gsig);
+    __syncthreads();
+    budget_flag(R, sm);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Frozen-sampling evaluation (a diagnostic for derivative checks; the paper has no derivatives).
+// Every path is replayed with its decisions sampled in the current medium theta_0, as flr_adjoint
+// replays it, while its film contributions are those of a perturbed medium theta: dye P.dye's
+// concentration in voxel P.voxel plus P.delta, and sigma_s plus P.dsig. Each decision d that
+// theta changes enters through its likelihood ratio p_theta(d) / p_theta0(d):
+//   null collision at x    (sigma_bar - sigma_t(theta, x)) / (sigma_bar - sigma_t(theta_0, x))
+//   real collision with e  sigma_e(theta, x) / sigma_e(theta_0, x)   (Sec. 4.1 shares)
+// and each transmittance is the ratio-tracking product at theta over the same points (Eq. 6); the
+// roulette of a transmittance estimate takes its decision on the theta_0 estimate, as sampling
+// does. Per path the result is S_p(theta) = sum_k adj[pixel_k][bin_k] value_k(theta) W_k(theta)
+// (W_k the product of the ratios before contribution k), accumulated in fp64 in path order: the
+// same path gives the same bits, so central differences (S_p(theta+h) - S_p(theta-h)) / 2h with
+// common random numbers are smooth per path and vanish exactly for paths the perturbation does
+// not touch. Their sum over paths is the derivative flr_adjoint estimates, up to O(h^2).
+struct PertDev {
+    int dye;          // < 0: no concentration perturbation
+    long long voxel;
+    float delta, dsig;
+    const float *adj; // [H][W][B]
+    double *out;      // [n_paths]
+};
+
+// Change of each coefficient at x (voxel v, solvent indicator sv) under the perturbation.
+__device__ __forceinline__ float pert_dye_at(const SceneDev &S, const Smem &sm, const PertDev &P, int v, int b)
+{
+    return (P.dye >= 0 && (long long)v == P.voxel) ? sm.sig_a[tab_sig_a_at(S.B, P.dye, b)] * P.delta : 0.0f;
+}
+
+struct FrozenObs {
+    const SceneDev &S;
+    const Smem &sm;
+    const PertDev &P;
+    float *W;
+    __device__ __forceinline__ void null_event(float3 x, int b, const Coeffs &k, float sb) const
+    {
+        const MedS_<false> m{S, sm};
+        const int v = S.homogeneous ? -1 : voxel_of(m, x);
+        const float sv = (S.solvent && v >= 0) ? (__ldg(&S.solvent[v]) ? 1.0f : 0.0f) : 1.0f;
+        const float d = sv * P.dsig + (v >= 0 ? pert_dye_at(S, sm, P, v, b) : 0.0f);
+        const float den = sb - k.total;
+        if (d != 0.0f && den > 0.0f) *W *= 1.0f - d / den;
+    }
+    __device__ __forceinline__ void real_event(float3 x, int b, const Coeffs &k, int ev) const
+    {
+        if (ev < 0) {
+            if (P.dsig != 0.0f && S.sigma_s > 0.0f) *W *= 1.0f + P.dsig / S.sigma_s;
+        } else if (ev < S.D && ev == P.dye && !S.homogeneous && k.dye[ev] > 0.0f) {
+            const MedS_<false> m{S, sm};
+            const int v = voxel_of(m, x);
+            const float d = pert_dye_at(S, sm, P, v, b);
+            if (d != 0.0f) *W *= 1.0f + d / k.dye[ev];
+        }
+    }
+};
+
+// adj x value_k(theta) of one connection (0 if it does not reach the film); value_k as
+// adjoint_weight computes it, the transmittance at theta with the adjoint's roulette rule.
+__device__ __forceinline__ float frozen_contribution(const SceneDev &S, const RunDev &R, const Smem &sm,
+                                                     const PertDev &P, const Conn &c, RegCnt &rc)
+{
+    const ConnGeom g = connect_geom(S, sm, c.x, c.lamb);
+    if (!g.ok) return 0.0f;
+    const MedS_<false> m{S, sm};
+    const float sb = sm.maj[c.bin];
+    float T = 1.0f;
+    if (sb > 0.0f) {
+        if (S.homogeneous) {
+            T = __expf(-(sigma_t_at(m, c.x, c.bin) + P.dsig) * g.tl);
+        } else {
+            const float isb = sm.inv_maj[c.bin];
+            float T0 = 1.0f, t = 0.0f;
+            U4 blk = U4{0, 0, 0, 0};
+            uint32_t j = 0;
+            int it = 0;
+            for (; it < MAX_CONNECT_STEPS; ++it) {
+                if ((j & 3u) == 0u) blk = draw_rk(R, c.pid, c.step, 2u + (j >> 2));
+                const uint32_t q = j & 3u;
+                const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
+                ++j;
+                t -= __logf(1.0f - u) * isb;
+                if (t >= g.tl) break;
+                rc.connect_steps++;
+                const float3 p = make_float3(c.x.x + t * g.dir.x, c.x.y + t * g.dir.y, c.x.z + t * g.dir.z);
+                const float st = sigma_t_at(m, p, c.bin);
+                const int v = voxel_of(m, p);
+                const float sv = S.solvent ? (__ldg(&S.solvent[v]) ? 1.0f : 0.0f) : 1.0f;
+                const float d = sv * P.dsig + pert_dye_at(S, sm, P, v, c.bin);
+                const float f0 = 1.0f - st * isb;
+                T0 *= fmaxf(0.0f, f0);
+                T *= fmaxf(0.0f, f0 - d * isb);
+                if (T0 < RT_RR_ADJ_THRESHOLD) {
+                    if ((j & 3u) == 0u) blk = draw_rk(R, c.pid, c.step, 2u + (j >> 2));
+                    const uint32_t q2 = j & 3u;
+                    const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
+                    ++j;
+                    if (u2 < 0.5f) {
+                        T0 *= 2.0f;
+                        T *= 2.0f;
+                    } else {
+                        T = 0.0f;
+                        break;
+                    }
+                }
+            }
+            if (it == MAX_CONNECT_STEPS) {
+                T = 0.0f;
+                cnt_add(sm, FLR_C_CONNECT_BUDGET);
+            }
+        }
+    }
+    const float val = c.w * g.gf * T * R.film_scale;
+    if (!(val > 0.0f)) return 0.0f;
+    return __ldg(&P.adj[(size_t)g.pix * S.B + c.bin]) * val;
+}
+
+__global__ void __launch_bounds__(256) k_frozen_sums(SceneDev S, RunDev R, PertDev P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
+    const MedS_<false> m{S, sm};
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
+        float W = 1.0f;
+        double sum = 0.0;
+        const FrozenObs obs{S, sm, P, &W};
+        Path p;
+        Conn c = spawn(m, R, sm, R.path_offset + i, p);
+        if (c.valid) sum += (double)frozen_contribution(S, R, sm, P, c, rc) * (double)W;
+        while (p.alive) {
+            c = track_step(m, R, sm, p, rc, obs);
+            if (c.valid) sum += (double)frozen_contribution(S, R, sm, P, c, rc) * (double)W;
+        }
+        P.out[i] = sum;
+    }
+    __syncthreads();
+    budget_flag(R, sm);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -2115,10 +2267,14 @@ __global__ void __launch_bounds__(WARP_BLOCK, (MODE == WM_RENDER && !MC) ? 5 : 4
     }
     if (MODE == WM_RENDER) {
         block_epilogue(S, R, sm, rc);
-    } else if (MODE == WM_ADJ_GRAD) {
+    } else {
+        if (MODE == WM_ADJ_GRAD) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) gsig += __shfl_xor_sync(FULL, gsig, o);
-        if (lane == 0 && gsig != 0.0f && A.grad_sigma_s) atomicAdd(A.grad_sigma_s, gsig);
+            for (int o = 16; o > 0; o >>= 1) gsig += __shfl_xor_sync(FULL, gsig, o);
+            if (lane == 0 && gsig != 0.0f && A.grad_sigma_s) atomicAdd(A.grad_sigma_s, gsig);
+        }
+        __syncthreads();
+        budget_flag(R, sm);
     }
 }
 
@@ -2891,6 +3047,7 @@ __device__ __forceinline__ void counters_epilogue(const RunDev &R, const Smem &s
         if ((threadIdx.x & 31) == 0 && v) atomicAdd(&sm.cnt[idx[i]], v);
     }
     __syncthreads();
+    budget_flag(R, sm);
     for (int i = threadIdx.x; i < FLR_NCOUNTERS; i += blockDim.x)
         if (sm.cnt[i]) atomicAdd(&R.counters[i], sm.cnt[i]);
 }
@@ -3392,6 +3549,28 @@ cudaError_t launch_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, l
     if (blocks < 1) blocks = 1;
     k_philox<<<(unsigned)blocks, 256, 0, st>>>(seed, medium, reinterpret_cast<const uint4 *>(ctr), n,
                                                 reinterpret_cast<uint4 *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frozen_sums(const SceneDev &S, const RunDev &R, int pert_dye, long long pert_voxel,
+                               float pert_delta, float pert_dsig, const float *adj, double *out,
+                               cudaStream_t st)
+{
+    const int block = 256;
+    const int smem = trace_smem_bytes(S.B, FLR_FORM_PLAIN, block);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_frozen_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_frozen_sums, block, smem);
+    if (occ < 1) occ = 1;
+    long long grid = (long long)num_sms() * occ;
+    const long long need = ((long long)R.n_paths + block - 1) / block;
+    if (need < grid) grid = need;
+    if (grid < 1) grid = 1;
+    PertDev P{pert_dye, pert_voxel, pert_delta, pert_dsig, adj, out};
+    k_frozen_sums<<<(unsigned)grid, block, smem, st>>>(S, R, P);
     return cudaGetLastError();
 }
 

@@ -98,6 +98,8 @@ SIGNATURES = {
                                    C.c_void_p]),
     "flr_adjoint": (C.c_int, [C.c_void_p, C.POINTER(flr_params), C.c_void_p, C.c_void_p,
                               C.c_void_p, C.c_void_p]),
+    "flr_debug_frozen_sums": (C.c_int, [C.c_void_p, C.POINTER(flr_params), C.c_void_p, C.c_int,
+                                        C.c_int64, C.c_float, C.c_float, C.c_void_p, C.c_void_p]),
     "flr_batch_prepare": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(flr_medium), C.c_void_p,
                                     C.POINTER(flr_params)]),
     "flr_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -243,6 +245,13 @@ def flr_debug_sample_emission(ctx, dye, u_ptr, n, out_ptr, stream=0):
 def flr_adjoint(ctx, params, adj_ptr, grad_conc_ptr, grad_sigma_s_ptr, stream=0):
     return load().flr_adjoint(ctx, C.byref(params), adj_ptr, grad_conc_ptr, grad_sigma_s_ptr,
                               C.c_void_p(int(stream)))
+
+
+def flr_debug_frozen_sums(ctx, params, adj_ptr, pert_dye, pert_voxel, pert_delta, pert_sigma_s,
+                          out_ptr, stream=0):
+    return load().flr_debug_frozen_sums(ctx, C.byref(params), adj_ptr, int(pert_dye),
+                                        int(pert_voxel), float(pert_delta), float(pert_sigma_s),
+                                        out_ptr, C.c_void_p(int(stream)))
 
 
 def flr_batch_prepare(ctx, n_media, media, n_paths_ptr, params):

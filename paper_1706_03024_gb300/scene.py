@@ -220,6 +220,23 @@ class Scene:
                               grad_sigma_s.data_ptr() if grad_sigma_s is not None else None,
                               st.cuda_stream), self.ctx, "flr_adjoint")
 
+    def frozen_sums(self, adj, pert=(-1, 0, 0.0, 0.0), n_paths=None, path_offset=0, seed=None,
+                    medium_id=0, majorant_margin=0.0, stream=None):
+        """Per-path adjoint-weighted film contributions under the frozen-sampling estimator at the
+        perturbed medium pert = (dye slot or -1, voxel, delta, d_sigma_s) (flr_debug_frozen_sums):
+        an fp64 tensor [n_paths] for the paths adjoint() replays with the same arguments."""
+        p = self._params(n_paths, path_offset, seed, medium_id, "plain",
+                         majorant_margin=majorant_margin)
+        out = torch.empty(int(p.n_paths), dtype=torch.float64,
+                          device=torch.device("cuda", self.device))
+        adj = adj.contiguous()
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        d, v, delta, ds = pert
+        N.check(N.flr_debug_frozen_sums(self.ctx, p, adj.data_ptr(), -1 if d is None else d, v,
+                                        delta, ds, out.data_ptr(), st.cuda_stream), self.ctx,
+                "flr_debug_frozen_sums")
+        return out
+
     def read(self, stream=None):
         B, D = self.B, self.D
         face = np.zeros((2, 6, B))

@@ -77,3 +77,26 @@ def integrated_independent(g_outs, o_outs, key, rel=5e-3):
     over4 = (d > np.maximum(rel * np.abs(mo), 4.0 * se)) & big
     ok = int(over3.sum()) <= 1 and not over4.any()
     return ok, {"gpu": mg[big].tolist()[:12], "oracle": mo[big].tolist()[:12]}
+
+
+def paired_integrated(g_outs, o_outs, key, rel=5e-3, z=4.0, floor=1e-3):
+    """Same seed, same path ids, batch by batch: the GPU and the oracle trace nearly the same
+    paths, so their integrated tallies (per row: face x fluoresced, or dye) differ only through the
+    paths whose fp32 and fp64 trajectories part. With d_k = gpu_k - oracle_k over K batches of the
+    same path ids and SE_d its standard error, a row passes if |mean d| <= rel |oracle| (0.5 %);
+    a row whose paired standard error is too large for that test to mean anything (z SE_d above
+    rel |oracle|) must instead satisfy |mean d| <= z SE_d. Returns (ok, worst relative difference
+    over the precise rows, number of precise rows, details)."""
+    gs = np.stack([x[key].sum(axis=-1) for x in g_outs]).reshape(len(g_outs), -1)
+    os_ = np.stack([x[key].sum(axis=-1) for x in o_outs]).reshape(len(o_outs), -1)
+    d = gs - os_
+    md, sd = batch_mean_se(d)
+    mo = os_.mean(axis=0)
+    big = np.abs(mo) >= floor * max(np.abs(mo).max(), 1e-300)
+    precise = big & (z * sd <= rel * np.abs(mo))
+    loose = big & ~precise
+    ok = bool(np.all(np.abs(md[precise]) <= rel * np.abs(mo[precise])) and
+              np.all(np.abs(md[loose]) <= z * sd[loose]))
+    worst = float((np.abs(md[precise]) / np.abs(mo[precise])).max()) if precise.any() else 0.0
+    return ok, worst, int(precise.sum()), {"mean_diff": md[big].tolist(), "se": sd[big].tolist(),
+                                           "oracle": mo[big].tolist()}

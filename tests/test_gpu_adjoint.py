@@ -13,6 +13,7 @@ import torch
 
 import oracle
 import scenegen as sg
+from paper_1706_03024_gb300 import native as N
 from paper_1706_03024_gb300.scene import FluoroRender, Scene
 from tests.gpu_common import require_gpu
 from tests.stats import batch_mean_se, parity_verdict
@@ -220,3 +221,62 @@ def test_adjoint_full_size_linearity_and_finiteness():
     assert scale > 0
     assert torch.allclose(out[2][0], comb, rtol=1e-3, atol=1e-4 * scale)
     assert abs(out[2][1] - (out[0][1] + 2 * out[1][1])) <= 1e-3 * (abs(out[0][1]) + 2 * abs(out[1][1]))
+
+
+def test_cfg4_gradient_against_frozen_central_differences_on_64_voxels():
+    """Config 4 at full size (2 x 64^3 blob dyes, sigma_s 30, 256 x 256 x 81 ortho film, 32 paths
+    per pixel): the gradient of the L2 loss sum (I - T)^2 against a seeded target T, taken by
+    flr_adjoint at theta_0 as the gradient of the linear functional sum(adj I) with
+    adj = 2 (I(theta_0) - T), against central differences with a step of 1e-3 of the value, common
+    random numbers (same seed and path ids) and the frozen-sampling estimator
+    (flr_debug_frozen_sums), on 64 seeded random voxels (c >= 0.05) and sigma_s. Eight disjoint path
+    batches give an adjoint and a difference per batch; each parameter passes if the mean
+    difference is within max(3 SE, 1 % of the gradient) (plus 1e-6 of the largest, for gradients
+    near zero). The frozen estimator's derivative is the score-function estimator flr_adjoint
+    evaluates (Eq. 6 for the transmittance terms), so the two agree per path up to O(h^2)."""
+    sc = sg.cfg4_adjoint(field_seed=0, seed=0)
+    n = sc["params"]["n_paths"]
+    assert n == 256 * 256 * 32 and sc["medium"]["conc"].shape == (2, 64, 64, 64)
+    mg = 0.1
+    S = Scene(sc)
+    target = Scene(sg.cfg4_adjoint(field_seed=1, seed=1000)).render(form="wavefront_warp").clone()
+    film = S.render(form="wavefront_warp", majorant_margin=mg)
+    adj = (2.0 * (film - target)).float().contiguous()
+    conc = sc["medium"]["conc"]
+    rng = np.random.default_rng(64)
+    cand = np.argwhere(conc >= 0.05)
+    pick = cand[rng.choice(cand.shape[0], size=64, replace=False)]
+    nz, ny, nx = conc.shape[1:]
+    voxels = [(int(d), int((z * ny + y) * nx + x), float(conc[d, z, y, x])) for d, z, y, x in pick]
+    s0 = float(sc["medium"]["sigma_s"])
+    K = 8
+    m = n // K
+    fd = np.zeros((K, 65))
+    ad = np.zeros((K, 65))
+    for k in range(K):
+        gc = torch.zeros(S.conc_t.shape, dtype=torch.float32, device="cuda")
+        gs = torch.zeros(1, dtype=torch.float32, device="cuda")
+        S.adjoint(adj, gc, gs, n_paths=m, path_offset=k * m, majorant_margin=mg)
+        g = gc.double().cpu().numpy().reshape(2, -1)
+        for j, (d, v, c0) in enumerate(voxels):
+            h = 1e-3 * c0
+            sp = S.frozen_sums(adj, (d, v, h, 0.0), n_paths=m, path_offset=k * m, majorant_margin=mg)
+            sm = S.frozen_sums(adj, (d, v, -h, 0.0), n_paths=m, path_offset=k * m, majorant_margin=mg)
+            fd[k, j] = float((sp - sm).sum()) / (2 * h)
+            ad[k, j] = g[d, v]
+        h = 1e-3 * s0
+        sp = S.frozen_sums(adj, (-1, 0, 0.0, h), n_paths=m, path_offset=k * m, majorant_margin=mg)
+        sm = S.frozen_sums(adj, (-1, 0, 0.0, -h), n_paths=m, path_offset=k * m, majorant_margin=mg)
+        fd[k, 64] = float((sp - sm).sum()) / (2 * h)
+        ad[k, 64] = float(gs.item())
+    assert S.status() == N.FLR_OK
+    ma, sa = batch_mean_se(ad)
+    md, sd = batch_mean_se(fd - ad)
+    scale = np.abs(ma[:64]).max()
+    tol = np.maximum(3 * sd, 1e-2 * np.abs(ma))
+    tol[:64] += 1e-6 * scale
+    bad = np.where(np.abs(md) > tol)[0]
+    assert bad.size == 0, [(int(j), ma[j], md[j], sd[j]) for j in bad]
+    # the check has teeth: most of the 64 voxel gradients and the sigma_s gradient are resolved
+    assert int((np.abs(ma[:64]) > 3 * sa[:64]).sum()) >= 32
+    assert abs(ma[64]) > 3 * sa[64]

@@ -19,7 +19,8 @@ import scenegen as sg
 from paper_1706_03024_gb300 import native as N
 from paper_1706_03024_gb300.scene import Scene
 from tests.gpu_common import (bin_parity, compare_integrated, gpu_batches,
-                              integrated_independent, oracle_batches, require_gpu, totals)
+                              integrated_independent, oracle_batches, paired_integrated,
+                              require_gpu, totals)
 
 pytestmark = pytest.mark.gpu
 
@@ -80,7 +81,9 @@ def test_emission_bins_bitwise_against_oracle():
 
 
 def _check_workload(sc, K, n_per, forms=("plain",), film_min_nonzero=None, path_id_frac=0.99,
-                    **kw):
+                    launch=None, **kw):
+    """kw: estimator settings both sides take; launch: GPU launch shape (block size, regroup)."""
+    launch = launch or {}
     o = oracle_batches(sc, K, n_per, path_events=True, **kw)
     o_events = np.concatenate([x["path_events"] for x in o])
     S = Scene(sc)
@@ -90,7 +93,7 @@ def _check_workload(sc, K, n_per, forms=("plain",), film_min_nonzero=None, path_
         g = []
         for k in range(K):
             f = S.render(n_paths=n_per, path_offset=k * n_per, form=form,
-                         path_events=pe[k * n_per:(k + 1) * n_per], **kw)
+                         path_events=pe[k * n_per:(k + 1) * n_per], **launch, **kw)
             r = S.read()
             r["film"] = f.double().cpu().numpy() if f is not None else None
             g.append(r)
@@ -116,7 +119,8 @@ def _check_workload(sc, K, n_per, forms=("plain",), film_min_nonzero=None, path_
         seed2 = int(sc["params"]["seed"]) + 1000
         gi = []
         for k in range(K):
-            f = S.render(n_paths=n_per, path_offset=k * n_per, form=form, seed=seed2, **kw)
+            f = S.render(n_paths=n_per, path_offset=k * n_per, form=form, seed=seed2, **launch,
+                         **kw)
             r = S.read()
             r["film"] = f.double().cpu().numpy() if f is not None else None
             gi.append(r)
@@ -165,6 +169,16 @@ def test_cfg2_empty_space_leap_parity():
     same way in fp64."""
     sc = sg.cfg2_cornell_box(width=48, height=48, grid=48, n_paths=1)
     _check_workload(sc, 32, 6000, forms=("plain", "wavefront_warp"), path_id_frac=0.95, skip_cell=2)
+
+
+def test_cfg2_benchmarked_launch_shape_reduced_parity():
+    """The launch shape the bench times on the Cornell box (warp-regrouped form, blocks of 128, one
+    tracking step per round, empty-space leaps over cells of one voxel) with every criterion: per
+    bin of the face, absorbed and emitted tallies, per pixel of the film, same-seed integrated
+    tallies within 0.5 %, and an independent seed with the chi-square band on the film."""
+    sc = sg.cfg2_cornell_box(width=48, height=48, grid=48, n_paths=1)
+    _check_workload(sc, 32, 6000, forms=("wavefront_warp",), path_id_frac=0.95, skip_cell=1,
+                    launch={"block_size": 128, "regroup": 1})
 
 
 def test_cfg5_macro_cell_parity():
@@ -334,6 +348,22 @@ def test_invalid_arguments_are_rejected():
     assert S.status() == N.FLR_OK
 
 
+def test_step_budget_is_reported_once_by_status():
+    """A path cut short at its step budget sets the context's error word: flr_status reports
+    FLR_ERR_BUDGET once and then clears it; every launch form reports it."""
+    sc = sg.cfg2_cornell_box(width=8, height=8, grid=16, n_paths=2000)
+    S = Scene(sc)
+    assert S.status() == N.FLR_OK
+    for form in ("plain", "wavefront", "wavefront_warp"):
+        S.render(form=form, max_steps=1)
+        assert S.read()["counters"]["step_budget"] > 0
+        assert S.status() == N.FLR_ERR_BUDGET, form
+        assert "budget" in N.flr_last_error(S.ctx)
+        assert S.status() == N.FLR_OK, form
+        S.render(form=form)
+        assert S.status() == N.FLR_OK, form
+
+
 # ------------------------------------------------------------------------------------------
 # Full-size workload (the benchmarked configuration): sampled paths and invariants
 
@@ -355,9 +385,15 @@ BENCH_LAUNCH = {"form": "wavefront_warp", "block_size": 128, "regroup": 1}
 @pytest.mark.parametrize("launch", [{"form": "wavefront"}, dict(BENCH_LAUNCH, skip_cell=1)],
                          ids=["wavefront", "bench_launch"])
 def test_cfg2_full_size_sampled_paths_and_invariants(launch):
+    """The Cornell-box workload at full size (512 x 512 pinhole, 16 spp, 128^3 grids, 4,194,304
+    paths). Bookkeeping and film checks on every path; event counts of 200 sampled paths against
+    the oracle's same paths; and, for the benchmarked launch shape, the integrated tallies of all
+    4,194,304 paths against the oracle's same paths (16 batches, same seed) within 0.5 % (rows
+    too noisy for that within 4 paired standard errors, see paired_integrated)."""
     sc = sg.cfg2_cornell_box()  # 512 x 512 pinhole, 16 spp, 128^3 grids
     n = sc["params"]["n_paths"]
     assert n == 512 * 512 * 16
+    sk = launch.get("skip_cell", 0)
     S = Scene(sc)
     pe = torch.zeros(n, dtype=torch.int32, device="cuda")
     film = S.render(path_events=pe, **launch)
@@ -371,23 +407,28 @@ def test_cfg2_full_size_sampled_paths_and_invariants(launch):
     same = 0
     for pid in ids:
         o = oracle.render(sc, n_paths=1, path_offset=int(pid), film=False, path_events=True,
-                          n_threads=1, skip_cell=launch.get("skip_cell", 0))
+                          n_threads=1, skip_cell=sk)
         same += int(o["path_events"][0] == ev[pid])
     assert same >= 0.95 * len(ids), same
-    # integrated escape through the open front vs an oracle sample of the same paths
-    o = oracle.render(sc, n_paths=65536, film=False, skip_cell=launch.get("skip_cell", 0))
-    S2 = Scene(sc)
-    S2.render(n_paths=65536, film=False, **launch)
-    g = S2.read()
+    # integrated tallies against the oracle's same paths, batch by batch
+    K = 16
+    m = n // K if launch.get("form") == "wavefront_warp" else 4096
+    g = gpu_batches(sc, K, m, film=False, scene_obj=S, skip_cell=sk,
+                    **{k: v for k, v in launch.items() if k != "skip_cell"})
+    o = oracle_batches(sc, K, m, film=False, skip_cell=sk)
     for key in ("face", "absorbed", "emitted"):
-        assert compare_integrated(g[key].sum(-1), o[key].sum(-1), rel=1e-2) <= 1e-2, key
+        ok, worst, n_precise, info = paired_integrated(g, o, key)
+        assert ok, (key, worst, info)
+        if launch.get("form") == "wavefront_warp":
+            assert n_precise >= 1, (key, info)
 
 
 def test_cfg5_light_sheet_full_size_sampled_paths_and_invariants():
     """The light-sheet workload at full size in the benchmarked launch shape: 256^3 x 4 grids
     (larger than the L2), 1024 x 1024 x 81 film, 67,108,864 paths. Bookkeeping and film checks on
     every path; per-path event counts of sampled path ranges against the oracle; integrated
-    tallies of the first 32,768 paths against the oracle's same paths."""
+    tallies of the first 262,144 paths against the oracle's same paths (16 batches, same seed)
+    within 0.5 % (rows too noisy for that within 4 paired standard errors)."""
     sc = sg.cfg5_light_sheet()
     n = sc["params"]["n_paths"]
     assert n == 1024 * 1024 * 64
@@ -408,9 +449,10 @@ def test_cfg5_light_sheet_full_size_sampled_paths_and_invariants():
         same += int((o["path_events"] == ev[s0:s0 + 32]).sum())
         total += 32
     assert same >= 0.95 * total, (same, total)
-    m = 32768
-    o = oracle.render(sc, n_paths=m, film=False)
-    S.render(n_paths=m, film=False, **launch)
-    g = S.read()
+    del pe
+    K, m = 16, 16384
+    g = gpu_batches(sc, K, m, film=False, scene_obj=S, **launch)
+    o = oracle_batches(sc, K, m, film=False)
     for key in ("face", "absorbed", "emitted"):
-        assert compare_integrated(g[key].sum(-1), o[key].sum(-1), rel=1e-2) <= 1e-2, key
+        ok, worst, n_precise, info = paired_integrated(g, o, key)
+        assert ok, (key, worst, info)

@@ -5,7 +5,9 @@ framework's caching pool that has reserved the GPU), or they run under a fixed m
 forbids allocation at run time. This entry point keeps all of its scratch in one static device
 array instead. Here it must give what the allocating entry points give (flr_render followed by
 flr_read_tallies) on the same paths: the same fixed-point tallies, bit for bit, and the same film
-within fp32 atomic reordering -- on two calls in a row, since every call reuses the array.
+within fp32 atomic reordering -- on two calls in a row, since every call reuses the array -- in
+every launch form, with and without grids. Settings it cannot honour are rejected, and a path cut
+short at its step budget is reported.
 This file is collected last so that a stop-at-first-failure run has already run everything else.
 """
 import ctypes as C
@@ -21,12 +23,15 @@ from tests.gpu_common import require_gpu
 
 pytestmark = pytest.mark.gpu
 
+_FORMS = {"plain": N.FLR_FORM_PLAIN, "wavefront": N.FLR_FORM_WAVEFRONT,
+          "wavefront_warp": N.FLR_FORM_WAVEFRONT_WARP}
+
 
 def _ptr(a):
     return a.ctypes.data_as(C.c_void_p)
 
 
-def _noalloc(sc, conc_t, solv_t, n_paths, form, film):
+def _noalloc(sc, conc_t, solv_t, n_paths, form, film, **over):
     dy, md, sp = sc["dyes"], sc["medium"], sc["spectrum"]
     D = int(dy["eps"].shape[0])
     m = N.flr_medium()
@@ -35,9 +40,13 @@ def _noalloc(sc, conc_t, solv_t, n_paths, form, film):
     m.n_dyes = D
     for d in range(D):
         m.dye_ids[d] = d
-        m.conc[d] = conc_t[d].data_ptr()
-    _, nz, ny, nx = conc_t.shape
-    m.dims[:] = (nx, ny, nz)
+        if conc_t is not None:
+            m.conc[d] = conc_t[d].data_ptr()
+        else:
+            m.conc_uniform[d] = float(md["conc_uniform"][d])
+    if conc_t is not None:
+        _, nz, ny, nx = conc_t.shape
+        m.dims[:] = (nx, ny, nz)
     m.solvent = solv_t.data_ptr() if solv_t is not None else None
     m.sigma_s = md["sigma_s"]
     m.sigma_a0 = md["sigma_a0"]
@@ -49,10 +58,12 @@ def _noalloc(sc, conc_t, solv_t, n_paths, form, film):
     p.seed = sc["params"]["seed"]
     p.n_rr = sc["params"]["n_rr"]
     p.max_inelastic = -1
-    p.form = N.FLR_FORM_WAVEFRONT if form == "wavefront" else N.FLR_FORM_PLAIN
+    p.form = _FORMS[form]
     p.max_events = sc["params"]["max_events"]
     p.max_steps = sc["params"]["max_steps"]
     p.film = film.data_ptr()
+    for k, v in over.items():
+        setattr(p, k, v)
     B = sp["n_bins"]
     face, absorbed = np.zeros((2, 6, B)), np.zeros((D + 1, B))
     emitted, counters = np.zeros((D, B)), np.zeros(N.FLR_NCOUNTERS, np.uint64)
@@ -68,27 +79,44 @@ def _noalloc(sc, conc_t, solv_t, n_paths, form, film):
                 "counters": {n: int(v) for n, v in zip(N.COUNTER_NAMES, counters)}}
 
 
-def test_noalloc_render_matches_allocating_render_on_two_calls():
+def _same(got, want, film, want_film):
+    for key in ("face", "absorbed", "emitted"):
+        assert np.array_equal(got[key], want[key]), key
+    assert got["counters"] == want["counters"]
+    assert torch.allclose(film, want_film, rtol=1e-5, atol=1e-6 * float(want_film.max()))
+
+
+@pytest.mark.parametrize("form", ["wavefront", "wavefront_warp", "plain"])
+def test_noalloc_render_matches_allocating_render_on_two_calls(form):
     require_gpu()
     sc = sg.cfg2_cornell_box(width=32, height=32, grid=32, n_paths=20000)
     n = sc["params"]["n_paths"]
     S = Scene(sc)
-    want_film = S.render(form="wavefront").clone()
+    want_film = S.render(form=form).clone()
     want = S.read()
     conc_t = torch.from_numpy(sc["medium"]["conc"]).cuda()
     solv_t = torch.from_numpy(sc["medium"]["solvent"]).cuda()
     film = torch.full_like(want_film, 123.0)
     for call in range(2):
-        rc, got = _noalloc(sc, conc_t, solv_t, n, "wavefront", film)
+        rc, got = _noalloc(sc, conc_t, solv_t, n, form, film)
         assert rc == N.FLR_OK, call
-        for key in ("face", "absorbed", "emitted"):
-            assert np.array_equal(got[key], want[key]), (call, key)
-        assert got["counters"] == want["counters"], call
-        assert torch.allclose(film, want_film, rtol=1e-5, atol=1e-6 * float(want_film.max()))
-    # the plain launch form through the same static scratch
-    rc, got = _noalloc(sc, conc_t, solv_t, n, "plain", film)
-    assert rc == N.FLR_OK
-    assert np.array_equal(got["face"], want["face"])
+        _same(got, want, film, want_film)
+    S.close()
+
+
+def test_noalloc_homogeneous_medium_without_grids():
+    require_gpu()
+    sc = sg.cfg1_homogeneous_cube(n_paths=20000, film=32)
+    S = Scene(sc)
+    for form in ("wavefront_warp", "plain"):
+        want_film = S.render(form=form).clone()
+        want = S.read()
+        film = torch.full_like(want_film, -1.0)
+        for call in range(2):
+            rc, got = _noalloc(sc, None, None, sc["params"]["n_paths"], form, film)
+            assert rc == N.FLR_OK, (form, call)
+            _same(got, want, film, want_film)
+    S.close()
 
 
 def test_noalloc_rejects_grids_beyond_its_static_scratch():
@@ -99,3 +127,31 @@ def test_noalloc_rejects_grids_beyond_its_static_scratch():
     assert 65 ** 3 > N.FLR_NOALLOC_MAX_VOXELS
     rc, _ = _noalloc(sc, conc_t, None, 10, "plain", film)
     assert rc == N.FLR_ERR_ARG
+
+
+@pytest.mark.parametrize("over", [{"paper_mode": 1}, {"skip_cell": 1}, {"macro_cell": 4},
+                                  {"majorant_margin": 0.1}, {"hero": 2}])
+def test_noalloc_rejects_settings_it_cannot_honour(over):
+    require_gpu()
+    sc = sg.cfg2_cornell_box(width=8, height=8, grid=16, n_paths=100)
+    conc_t = torch.from_numpy(sc["medium"]["conc"]).cuda()
+    solv_t = torch.from_numpy(sc["medium"]["solvent"]).cuda()
+    film = torch.zeros((8, 8, sg.N_BINS), device="cuda")
+    rc, _ = _noalloc(sc, conc_t, solv_t, 100, "wavefront_warp", film, **over)
+    assert rc == N.FLR_ERR_ARG
+    rc, _ = _noalloc(sc, conc_t, solv_t, 100, "wavefront_warp", film)
+    assert rc == N.FLR_OK
+
+
+def test_noalloc_reports_paths_cut_at_their_step_budget():
+    require_gpu()
+    sc = sg.cfg2_cornell_box(width=8, height=8, grid=16, n_paths=2000)
+    conc_t = torch.from_numpy(sc["medium"]["conc"]).cuda()
+    solv_t = torch.from_numpy(sc["medium"]["solvent"]).cuda()
+    film = torch.zeros((8, 8, sg.N_BINS), device="cuda")
+    rc, got = _noalloc(sc, conc_t, solv_t, 2000, "wavefront_warp", film, max_steps=1)
+    assert rc == N.FLR_ERR_BUDGET
+    assert got["counters"]["step_budget"] > 0
+    # the next call starts from a clear error word
+    rc, got = _noalloc(sc, conc_t, solv_t, 2000, "wavefront_warp", film)
+    assert rc == N.FLR_OK and got["counters"]["step_budget"] == 0
