@@ -732,7 +732,14 @@ static double wall_brdf_cos(const or_scene *s, const double r[3], const double o
  *   pinhole importance x geometry: 1/(A_pix r^2 cos^3 theta), A_pix the pixel area on the
  *   image plane at unit distance (film = radiance averaged over image-plane area).
  * The connecting segment must leave the box through an open (non-wall) face. */
-typedef struct { int lambertian; int axis; double sign; } vtx_kind;
+typedef struct {
+    int lambertian;         /* 1: wall or light vertex with normal sign * e_axis              */
+    int axis;
+    double sign;
+    int glossy;             /* 1: wall vertex of a glossy wall; r is the incoming photon's mirror
+                               direction, and the intensity follows the whole wall BRDF          */
+    double r[3];
+} vtx_kind;
 
 /* Adjoint bookkeeping of one path: its tracking decisions and sensor connections in order. */
 typedef struct {
@@ -818,7 +825,7 @@ static void connect_sensor(const or_scene *s, const tables *t, const double x[3]
     if (vk.lambertian) {
         double co = vk.sign * dir[vk.axis];
         if (!(co > 0.0)) return;
-        f = co / OR_PI;
+        f = vk.glossy ? wall_brdf_cos(s, vk.r, dir, co) : co / OR_PI;
     } else {
         f = 1.0 / (4.0 * OR_PI);
     }
@@ -826,6 +833,15 @@ static void connect_sensor(const or_scene *s, const tables *t, const double x[3]
     double tl = exit_distance(s, x, dir, &face);
     if (face < 0) return;
     if (s->wall_mask & (1 << face)) return;
+    if (t->dielectric) {
+        /* the connection leaves through a dielectric face at normal incidence (the sensor is
+         * orthographic and looks along a face normal): the transmitted fraction 1 - F, and the
+         * radiance changes by 1 / ior^2 from the solution into the outside (L / n^2 is invariant
+         * along a refracted ray) */
+        double ct;
+        double F = fresnel(fabs(dir[face / 2]), t->ior, 1.0, &ct);
+        f *= (1.0 - F) / (t->ior * t->ior);
+    }
     if (c->kind == 2 && tl * tl > r2) return; /* eye inside the box: not supported, skip */
     double T = exp(-optical_depth(s, t, x, dir, tl, bin));
     double val = w * f * T * geom;
@@ -956,10 +972,22 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
         int ax; double sg;
         normal_axis(em->dir, &ax, &sg);
         cosine_dir(S0.u[3], S1.u[0], ax, sg, w);
-        vtx_kind vk = { 1, ax, sg };
+        vtx_kind vk = { 1, ax, sg, 0, { 0, 0, 0 } };
         if (!p->paper_mode) connect_sensor(s, t, x, bin, wt, vk, film, cnt, A);
     } else {
         for (int k = 0; k < 3; ++k) w[k] = em->dir[k];
+    }
+    if (t->entry_face[ek] >= 0) {
+        /* entering the solution through a dielectric face: Fresnel reflection sends the photon
+         * back out through that face, else Snell refraction bends it in (coin: slot 1, word 1) */
+        block4 S1 = rng_block(p->seed, p->medium_id, pid, STEP_SPAWN, 1);
+        int f = t->entry_face[ek];
+        if (interface_event(f, w, 1.0, t->ior, S1.u[1])) {
+            cnt[OC_IFACE_REFLECTIONS]++;
+            lt->face[0][f][bin] += wt * W;
+            cnt[OC_ESCAPES]++;
+            return 0;
+        }
     }
     int64_t n_events = 0;
     int n_inel = 0;
@@ -980,6 +1008,29 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
         }
         if (tf >= te) {
             for (int k = 0; k < 3; ++k) x[k] += te * w[k];
+            if (t->dielectric && !(s->wall_mask & (1 << face))) {
+                /* a dielectric face from inside: Fresnel reflection (an event; the coin is the
+                 * step's unused u_real) or refraction out of the solution (an escape) */
+                double wr[3] = { w[0], w[1], w[2] };
+                if (interface_event(face, wr, t->ior, 1.0, B0.u[1])) {
+                    if (n_events == p->max_events) { cnt[OC_CAP_HITS]++; break; }
+                    n_events++;
+                    cnt[OC_EVENTS]++;
+                    cnt[OC_IFACE_REFLECTIONS]++;
+                    for (int k = 0; k < 3; ++k) w[k] = wr[k];
+                    x[face / 2] = (face & 1) ? s->hi[face / 2] : s->lo[face / 2];
+                    if (n_events >= p->n_rr) {
+                        block4 B1 = rng_block(p->seed, p->medium_id, pid, (uint32_t)step, 1);
+                        double q = wt < 1.0 ? wt : 1.0;
+                        if (!(B1.u[2] < q)) { cnt[OC_RR_KILLS]++; break; }
+                        wt /= q;
+                    }
+                    continue;
+                }
+                lt->face[fl][face][bin] += wt * W;
+                cnt[OC_ESCAPES]++;
+                break;
+            }
             if (s->wall_mask & (1 << face)) {
                 /* Lambertian wall: a real event (in paper mode, excitation light reflected by a
                  * wall before any emission is dropped) */
@@ -999,9 +1050,26 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
                 double sg = (face & 1) ? -1.0 : 1.0;   /* inward normal */
                 /* snap onto the wall plane */
                 x[ax] = (face & 1) ? s->hi[ax] : s->lo[ax];
-                cosine_dir(B0.u[2], B0.u[3], ax, sg, w);
-                vtx_kind vk = { 1, ax, sg };
-                connect_sensor(s, t, x, bin, wt * W, vk, film, cnt, A);
+                if (s->wall_gloss > 0.0) {
+                    /* glossy wall: the sensor sees the whole BRDF; the path continues in the
+                     * Phong lobe about the mirror direction with probability g (lobe weight
+                     * (e + 2)/(e + 1) cos_o; below the wall it ends), else in the diffuse lobe */
+                    vtx_kind vk = { 1, ax, sg, 1, { w[0], w[1], w[2] } };
+                    vk.r[ax] = -w[ax];
+                    connect_sensor(s, t, x, bin, wt * W, vk, film, cnt, A);
+                    if (B1.u[0] < s->wall_gloss) {
+                        phong_dir(B0.u[2], B0.u[3], vk.r, s->wall_exponent, w);
+                        double co = sg * w[ax];
+                        if (!(co > 0.0)) { cnt[OC_ABSORBED_DEAD]++; break; }
+                        wt *= (s->wall_exponent + 2.0) / (s->wall_exponent + 1.0) * co;
+                    } else {
+                        cosine_dir(B0.u[2], B0.u[3], ax, sg, w);
+                    }
+                } else {
+                    cosine_dir(B0.u[2], B0.u[3], ax, sg, w);
+                    vtx_kind vk = { 1, ax, sg, 0, { 0, 0, 0 } };
+                    connect_sensor(s, t, x, bin, wt * W, vk, film, cnt, A);
+                }
                 if (n_events >= p->n_rr) {
                     double q = wt < 1.0 ? wt : 1.0;
                     if (!(B1.u[2] < q)) { cnt[OC_RR_KILLS]++; break; }
@@ -1070,7 +1138,7 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
             cnt[OC_SCATTERS]++;
             if (p->paper_mode && !fl) { cnt[OC_VF_REJECTED]++; break; }  /* excitation scattering */
             iso_dir(B0.u[3], B1.u[0], w);
-            vtx_kind vk = { 0, 0, 0.0 };
+            vtx_kind vk = { 0, 0, 0.0, 0, { 0, 0, 0 } };
             connect_sensor(s, t, x, bin, wt * W, vk, film, cnt, A);
         } else if (ev < s->n_dyes) {
             cnt[OC_DYE_ABSORPTIONS]++;
@@ -1091,7 +1159,7 @@ static uint32_t trace_path(const or_scene *s, const tables *t, const or_params *
             n_inel++;
             fl = 1;
             iso_dir(B0.u[3], B1.u[0], w);
-            vtx_kind vk = { 0, 0, 0.0 };
+            vtx_kind vk = { 0, 0, 0.0, 0, { 0, 0, 0 } };
             connect_sensor(s, t, x, bin, wt * W, vk, film, cnt, A);
         } else {
             lt->absorbed[s->n_dyes][bin] += wt * W;
@@ -1366,7 +1434,7 @@ static uint32_t trace_path_hero(const or_scene *s, const tables *t, const or_par
         if (ev < 0) {
             cnt[OC_SCATTERS]++;
             iso_dir(B0.u[3], B1.u[0], w);
-            vtx_kind vk = { 0, 0, 0.0 };
+            vtx_kind vk = { 0, 0, 0.0, 0, { 0, 0, 0 } };
             connect_sensor_hero(s, t, x, &h, wt, vk, film, cnt);
         } else if (ev < s->n_dyes) {
             cnt[OC_DYE_ABSORPTIONS]++;
@@ -1390,7 +1458,7 @@ static uint32_t trace_path_hero(const or_scene *s, const tables *t, const or_par
             n_inel++;
             fl = 1;
             iso_dir(B0.u[3], B1.u[0], w);
-            vtx_kind vk = { 0, 0, 0.0 };
+            vtx_kind vk = { 0, 0, 0.0, 0, { 0, 0, 0 } };
             connect_sensor_hero(s, t, x, &h, wt, vk, film, cnt);
         } else {
             /* grey background absorption: the weights stay */
@@ -1410,6 +1478,28 @@ static uint32_t trace_path_hero(const or_scene *s, const tables *t, const or_par
 /* ---------------------------------------------------------------------------------------- */
 /* Exported API (ctypes). Return 0 on success, negative on invalid input. */
 
+/* Interfaces and glossy walls: ior 0 or >= 1, gloss in [0, 1], exponent >= 0. With dielectric
+ * faces the sensor must be orthographic and look along a face normal (a connection through a
+ * flat interface to a pinhole needs the refraction point, which is not solved here); hero paths
+ * and the paper's model are index-matched and Lambertian only. */
+static int interfaces_supported(const or_scene *s, const or_params *p)
+{
+    if (!(s->ior == 0.0 || s->ior >= 1.0) || !(s->wall_gloss >= 0.0 && s->wall_gloss <= 1.0) ||
+        !(s->wall_exponent >= 0.0))
+        return 0;
+    int special = s->ior > 1.0 || s->wall_gloss > 0.0;
+    if (special && p && (p->hero > 0 || p->paper_mode)) return 0;
+    if (s->ior > 1.0) {
+        if (s->sensor.kind == 2) return 0;
+        if (s->sensor.kind == 1) {
+            int zeros = 0;
+            for (int k = 0; k < 3; ++k) zeros += s->sensor.view[k] == 0.0;
+            if (zeros != 2) return 0;
+        }
+    }
+    return 1;
+}
+
 int or_render(const or_scene *s, const or_params *p, or_result *r)
 {
     if (!s || !p || !r) return -1;
@@ -1419,6 +1509,7 @@ int or_render(const or_scene *s, const or_params *p, or_result *r)
     if (p->hero < 0 || p->hero > 4) return -1;
     if (p->hero > 0 && (p->macro_cell > 0 || p->paper_mode || p->frozen || p->pert_dye >= 0 ||
                         p->pert_sigma_s != 0.0)) return -1;
+    if (!interfaces_supported(s, p)) return -1;
     tables *t = (tables *)malloc(sizeof(tables));
     build_tables(s, t);
     apply_params(t, p);
@@ -1685,6 +1776,7 @@ int or_render_camera(const or_scene *s, const or_params *p, double *film, uint64
     if (s->n_bins <= 0 || s->n_bins > OR_MAX_BINS) return -1;
     if (s->n_dyes <= 0 || s->n_dyes > OR_MAX_DYES || s->sensor.kind == 0) return -2;
     if (s->n_emitters <= 0 || s->n_emitters > OR_MAX_EMITTERS) return -1;
+    if (s->ior > 1.0 || s->wall_gloss > 0.0) return -1;   /* index-matched, Lambertian only */
     for (int k = 0; k < s->n_emitters; ++k) {
         const or_emitter *e = &s->emitters[k];
         double n[3] = { e->eu[1] * e->ev[2] - e->eu[2] * e->ev[1], e->eu[2] * e->ev[0] - e->eu[0] * e->ev[2],
@@ -1783,6 +1875,7 @@ int or_adjoint(const or_scene *s, const or_params *p, const double *adj, double 
     if (!s || !p || !adj || !grad_sigma_s) return -1;
     if (s->sensor.kind == 0) return -1;
     if (s->n_bins <= 0 || s->n_bins > OR_MAX_BINS || s->n_dyes > OR_MAX_DYES) return -1;
+    if (!interfaces_supported(s, p)) return -1;
     if (s->n_emitters <= 0 || s->n_emitters > OR_MAX_EMITTERS) return -1;
     tables *t = (tables *)malloc(sizeof(tables));
     build_tables(s, t);

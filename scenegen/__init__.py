@@ -15,7 +15,10 @@ Scene dict layout (all arrays numpy, C-contiguous):
               concentration at the absorption peak), qy f32[D]
     medium:   lo, hi (cm), dims (nx,ny,nz) or None, conc f32[D,nz,ny,nx] or None,
               conc_uniform f32[D], solvent u8[nz,ny,nx] or None, sigma_s, sigma_a0 (cm^-1),
-              wall_mask (bit f = face f is a Lambertian wall; faces -x,+x,-y,+y,-z,+z), wall_albedo
+              wall_mask (bit f = face f is a Lambertian wall; faces -x,+x,-y,+y,-z,+z), wall_albedo;
+              optional: ior (refractive index of the solution, > 1 makes the open faces smooth
+              dielectric interfaces; default 1), wall_gloss (glossy share g of the walls' BRDF,
+              default 0), wall_exponent (Phong exponent of the glossy lobe)
     sources:  list of dict(kind 'collimated'|'lambertian', origin, eu, ev, dir, lines_nm, power)
     sensor:   dict(kind 'none'|'ortho'|'pinhole', width, height, origin, U, V, view, fov_y_deg)
     params:   n_paths, seed, n_rr, max_events, max_inelastic, analog
@@ -161,7 +164,8 @@ def voxel_centres(n, lo=0.0, hi=1.0):
     return lo + (np.arange(n, dtype=np.float64) + 0.5) * h
 
 
-def cfg2_cornell_box(width=512, height=512, spp=16, grid=128, seed=0, n_paths=None):
+def cfg2_cornell_box(width=512, height=512, spp=16, grid=128, seed=0, n_paths=None,
+                     wall_gloss=0.0, wall_exponent=0.0):
     """Cornell-box-style scene: a 1 cm box with Lambertian walls (rho 0.8) on all faces but the
     open front (-y); 4 non-overlapping dye spheres (radius 0.15-0.25 box), each filled with one
     Gaussian dye (emission peaks 450/520/600/680 nm, absorption peaks 30 nm lower, sigma 15/20 nm,
@@ -185,6 +189,9 @@ def cfg2_cornell_box(width=512, height=512, spp=16, grid=128, seed=0, n_paths=No
         solvent[inside] = 1
     walls = 0b111111 & ~(1 << FACE_NY)
     med = grid_medium(conc, solvent, sigma_s=50.0, wall_mask=walls, wall_albedo=0.8)
+    if wall_gloss > 0.0:   # the paper's glossy Cornell box (Sec. 5)
+        med["wall_gloss"] = float(wall_gloss)
+        med["wall_exponent"] = float(wall_exponent)
     light = rect_source("lambertian", (0.35, 0.35, 1.0), (0.3, 0.0, 0.0), (0.0, 0.3, 0.0),
                         (0.0, 0.0, -1.0), abs_peaks)
     cam = pinhole_sensor(width, height, eye=(0.5, -1.4, 0.5), right=(1, 0, 0), up=(0, 0, 1),
@@ -328,3 +335,32 @@ def paper_mode_scene(n=16, width=8, spp=1000, seed=7, sigma_s=3.0):
     return {"name": "paper_mode_scene", "spectrum": spectrum(), "dyes": dyes, "medium": med,
             "sources": [beam], "sensor": cam,
             "params": params(width * width * spp, seed=2)}
+
+
+def vial_scene(conc_gpl=1.0, ior=1.33, width=64, height=64, spp=16, seed=0, n_paths=None,
+               sigma_s=20.0, grid=None):
+    """The paper's dye vials (Sec. 5: AF488 solutions at 0.1, 1 and 10 g/L lit at 495 nm), as a
+    1 cm cuvette of solution with refractive index `ior` (water 1.33) whose six faces are smooth
+    dielectric interfaces to the air: one Gaussian dye (absorption 495/15 nm, emission 520/20 nm,
+    QY 0.9, peak absorption 1.5 cm^-1 per g/L) at `conc_gpl` in a scattering solvent (sigma_s),
+    a collimated 1 mm beam at 495 nm entering the -x face at the centre, and an orthographic
+    camera looking at the front (-y) face head-on (radiance travelling along -y). With `grid` the
+    dye fills a centred cylinder (the vial) of radius 0.35 cm along z on an n^3 grid instead of
+    the whole cuvette."""
+    dyes = make_dyes([495.0], [15.0], [520.0], [20.0], eps=[1.5], qy=[0.9])
+    if grid:
+        xc = voxel_centres(grid)
+        Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
+        inside = (X - 0.5) ** 2 + (Y - 0.5) ** 2 <= 0.35 ** 2
+        conc = (inside * conc_gpl).astype(np.float32)[None]
+        med = grid_medium(conc, inside.astype(np.uint8), sigma_s=sigma_s)
+    else:
+        med = homogeneous_medium(1, conc=conc_gpl, sigma_s=sigma_s)
+    med["ior"] = float(ior)
+    beam = rect_source("collimated", (0.0, 0.45, 0.45), (0.0, 0.1, 0.0), (0.0, 0.0, 0.1),
+                       (1.0, 0.0, 0.0), [495.0])
+    cam = ortho_sensor(width, height, (0.0, 0.0, 0.0), (1.0, 0.0, 0.0), (0.0, 0.0, 1.0),
+                       (0.0, -1.0, 0.0))
+    n = n_paths if n_paths is not None else width * height * spp
+    return {"name": "vial", "spectrum": spectrum(), "dyes": dyes, "medium": med,
+            "sources": [beam], "sensor": cam, "params": params(n, seed=seed, n_rr=5)}
