@@ -846,7 +846,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="wavefront_warp",
-                    choices=["wavefront", "wavefront_warp"],
+                    choices=["wavefront", "wavefront_warp", "wavefront_pool"],
                     help="optimised form when not autotuning")
     ap.add_argument("--regroup", type=int, default=1)
     ap.add_argument("--macro-cell", type=int, default=0,

@@ -47,7 +47,7 @@ extern "C" {
 #define FLR_MAX_SOURCES 65536
 #define FLR_MAX_LINES 8
 #define FLR_MAX_EMITTERS 32         /* spectral lines over all sources of one medium       */
-#define FLR_NCOUNTERS 20
+#define FLR_NCOUNTERS 21
 
 #define FLR_SOURCE_COLLIMATED 0
 #define FLR_SOURCE_LAMBERTIAN 1
@@ -59,6 +59,10 @@ extern "C" {
 #define FLR_FORM_PLAIN 0      /* one thread per path, nested loops                          */
 #define FLR_FORM_WAVEFRONT 1  /* persistent, path regeneration, sensor connections regrouped */
 #define FLR_FORM_WAVEFRONT_WARP 2  /* as WAVEFRONT, regrouping per warp instead of per block */
+#define FLR_FORM_WAVEFRONT_POOL 3  /* per-warp pools of paths in shared memory, regrouped by event
+                                      type every round: free flights and collision events each run
+                                      on full warps (flr_render only; one majorant per bin, with or
+                                      without skip_cell; blocks of 128 threads) */
 
 /* Counter indices of flr_read_tallies' counters array. */
 enum {
@@ -69,7 +73,9 @@ enum {
     FLR_C_CONNECT_STEPS,       /* ratio-tracking steps of sensor connections                    */
     FLR_C_CONNECT_BUDGET,      /* connections cut by the ratio-tracking step budget             */
     FLR_C_NONFINITE,           /* paths ended because a weight or position became non-finite   */
-    FLR_C_CELL_WALKS           /* local-majorant cells visited by free flights and marches      */
+    FLR_C_CELL_WALKS,          /* local-majorant cells visited by free flights and marches      */
+    FLR_C_IFACE_REFLECTIONS    /* Fresnel reflections at dielectric faces (entry reflections
+                                  included); those inside the medium also count as events       */
 };
 
 typedef struct flr_ctx flr_ctx;
@@ -92,11 +98,31 @@ typedef struct flr_source {
  *   sigma_t(x, lambda) = s(x) (sigma_s + sigma_a0) + sum_d eps_d a_d(lambda) c_d(x)
  * with s(x) the solvent mask (1 where no mask is given), eps_d a_d the dye's absorption
  * (set by flr_set_dyes) and c_d the concentration (grid or uniform). Faces whose bit is set in
- * wall_mask are Lambertian walls of albedo wall_albedo; the others are open. */
+ * wall_mask are walls of albedo wall_albedo; the others are open.
+ * Interfaces and glossy walls (the glass vials and the glossy Cornell box of Sec. 5, which the
+ * paper does not specify; these are the physically standard choices):
+ *   ior > 1 makes every open face a smooth dielectric interface between the solution (index ior)
+ *   and the outside (index 1): a photon reaching it from inside is reflected with the Fresnel
+ *   reflectance of unpolarised light (always beyond the critical angle) and otherwise escapes; a
+ *   source whose parallelogram lies in an open face's plane, pointing inward, enters through it
+ *   (the reflected share is tallied as escaping through that face, the rest refracts by Snell's
+ *   law). The sensor must then be orthographic with its view along a face normal (connections
+ *   leave the face at normal incidence with (1 - F) / ior^2 of the radiance); pinhole sensors,
+ *   hero paths, the paper's model, the camera-side estimator and the batched form are
+ *   index-matched only (FLR_ERR_ARG). ior 0 or 1: index-matched.
+ *   Wall BRDF: wall_albedo [(1 - g)/pi + g (e + 2)/(2 pi) cos^e alpha] with g = wall_gloss in
+ *   [0, 1], e = wall_exponent >= 0 and alpha the angle between the outgoing direction and the
+ *   mirror direction of the incoming one: a diffuse lobe plus a normalised Phong lobe. Sensor
+ *   connections evaluate the whole BRDF; the path continues in the Phong lobe with probability g
+ *   (weight (e + 2)/(e + 1) cos theta_o; a direction below the wall ends it), else in the diffuse
+ *   lobe. g = 0: Lambertian. The batched form, hero paths, the paper's model and the camera-side
+ *   estimator take Lambertian walls only. */
 typedef struct flr_medium {
     float lo[3], hi[3];          /* box, cm                                                    */
-    int dims[3];                 /* nx, ny, nz of the grids, each 1..4096 and nx*ny*nz below
-                                    2^31 (FLR_ERR_ARG otherwise); ignored when no grid is given */
+    int dims[3];                 /* nx, ny, nz of the grids, each 1..4096, nx*ny*nz below 2^31
+                                    also once each is rounded up to a multiple of 4 (the library
+                                    stores the grids in 4^3-voxel bricks; FLR_ERR_ARG otherwise);
+                                    ignored when no grid is given */
     int n_dyes;                  /* 0..FLR_MAX_DYES_PER_MEDIUM                                 */
     int dye_ids[FLR_MAX_DYES_PER_MEDIUM];        /* rows of the dye table                     */
     const float *conc[FLR_MAX_DYES_PER_MEDIUM];  /* device grids, or NULL => conc_uniform[d]  */
@@ -106,6 +132,8 @@ typedef struct flr_medium {
     int wall_mask;
     float wall_albedo;
     int source_first, source_count;  /* rows of the source table; count 0 = all sources      */
+    float ior;                   /* refractive index of the solution (0 or 1: index-matched)   */
+    float wall_gloss, wall_exponent;  /* glossy share and Phong exponent of the walls' BRDF   */
 } flr_medium;
 
 /* The sensor. ORTHO: a film rectangle origin + s U + t V (s, t in [0,1)) recording radiance
@@ -314,7 +342,8 @@ int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const u
  * p->n_paths). All scratch -- spectral tables, fixed-point tallies, counters, the work counter and
  * the interleaved copy of the grids -- lives in one static device array of 4 MiB + 64 KiB that
  * every GPU loading this library holds until the process exits; media with more than
- * FLR_NOALLOC_MAX_VOXELS voxels are rejected with FLR_ERR_ARG. It renders the full RTE with one
+ * FLR_NOALLOC_MAX_VOXELS voxels (counted with each dimension rounded up to a multiple of 4) are
+ * rejected with FLR_ERR_ARG. It renders the full RTE with one
  * majorant per bin: p->paper_mode, p->macro_cell, p->skip_cell, p->majorant_margin and p->hero
  * must be 0 (FLR_ERR_ARG otherwise; the array has no room for cell grids). The first call on a
  * device looks up that array's device address (with that device current) and keeps it for the

@@ -36,7 +36,8 @@ class Result:
 
 def default_candidates(has_grid=True, max_cell=8):
     """Block- or warp-level regrouping, wavefront depth 1..8, blocks of 128 or 256 (the warp form:
-    128), empty-space cells 0 (off) .. max_cell, and a few local-majorant cell sizes."""
+    128), empty-space cells 0 (off) .. max_cell, a few local-majorant cell sizes, and the path-pool
+    form (regrouping by event type; blocks of 128, one free flight per round) with each cell size."""
     cells = [0] + ([c for c in (1, 2, 4, 8) if c <= max_cell] if has_grid else [])
     out = []
     for form, block, regroup, skip in itertools.product(("wavefront", "wavefront_warp"), (256, 128),
@@ -44,6 +45,8 @@ def default_candidates(has_grid=True, max_cell=8):
         if form == "wavefront_warp" and block > 128:
             continue   # the warp-regrouped form runs blocks of at most 128 threads
         out.append(Candidate(form, block, regroup, skip, 0))
+    for skip in cells:
+        out.append(Candidate("wavefront_pool", 128, 1, skip, 0))
     if has_grid:
         for block, regroup, mc in itertools.product((256,), (2, 4), (4, 8)):
             out.append(Candidate("wavefront", block, regroup, 0, mc))

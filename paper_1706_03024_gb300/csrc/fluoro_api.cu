@@ -241,6 +241,17 @@ int build_emitters(flr_ctx *ctx, const flr_medium &m, int max_lines, EmitterDev 
                 if (std::fabs(src.dir[k]) > std::fabs(src.dir[ax])) ax = k;
             e.axis = ax;
             e.sign = src.dir[ax] > 0.0f ? 1.0f : -1.0f;
+            // entry through a dielectric face: the source's parallelogram lies in an open face's
+            // plane and its direction (or normal) points into the box
+            e.entry = -1;
+            if (m.ior > 1.0f)
+                for (int a = 0; a < 3 && e.entry < 0; ++a) {
+                    if (src.eu[a] != 0.0f || src.ev[a] != 0.0f) continue;
+                    int f = -1;
+                    if (src.origin[a] == m.lo[a] && src.dir[a] > 0.0f) f = 2 * a;
+                    if (src.origin[a] == m.hi[a] && src.dir[a] < 0.0f) f = 2 * a + 1;
+                    if (f >= 0 && !(m.wall_mask & (1 << f))) e.entry = f;
+                }
             pw.push_back((double)src.power[l]);
             ++n;
         }
@@ -268,6 +279,7 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film, int macro_cell = 0, in
         S.lo[k] = m.lo[k];
         S.hi[k] = m.hi[k];
         S.dims[k] = std::max(m.dims[k], 1);
+        S.bdims[k] = grid_bricks(S.dims[k]);
         S.vox_scale[k] = (float)((double)S.dims[k] / ((double)m.hi[k] - (double)m.lo[k]));
     }
     S.grid = medium_has_grid(m) ? ctx->d_grid : nullptr;
@@ -298,6 +310,18 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film, int macro_cell = 0, in
         S.mc_dist = ctx->d_mc_dist;
     }
     S.maj_margin = (float)(1.0 + ctx->tables_margin);
+    // interfaces and glossy walls
+    S.dielectric = m.ior > 1.0f ? 1 : 0;
+    S.iface = (S.dielectric || m.wall_gloss > 0.0f) ? 1 : 0;
+    S.ior = S.dielectric ? m.ior : 1.0f;
+    S.inv_ior = (float)(1.0 / (double)S.ior);
+    {
+        // Fresnel reflectance at normal incidence, ((n - 1)/(n + 1))^2, and the radiance factor
+        const double n = (double)S.ior, f0 = ((n - 1.0) / (n + 1.0)) * ((n - 1.0) / (n + 1.0));
+        S.iface_exit = (float)((1.0 - f0) / (n * n));
+    }
+    S.wall_gloss = m.wall_gloss;
+    S.wall_exp = m.wall_exponent;
     // sensor
     const flr_sensor &c = ctx->sensor;
     S.sensor_kind = (ctx->sensor_set && with_film) ? c.kind : FLR_SENSOR_NONE;
@@ -406,6 +430,24 @@ int prepare_tables(flr_ctx *ctx, double margin = 0.0)
     return FLR_OK;
 }
 
+// Dielectric faces need an orthographic sensor looking along a face normal (or none); hero paths
+// and the paper's model take index-matched faces and Lambertian walls only.
+int check_interfaces(flr_ctx *ctx, const flr_medium &m, bool sensor_set, const flr_sensor &c, int hero,
+                     int paper_mode)
+{
+    const bool dielectric = m.ior > 1.0f, special = dielectric || m.wall_gloss > 0.0f;
+    if (special && (hero != 0 || paper_mode != 0))
+        return fail(ctx, FLR_ERR_ARG, "interfaces: hero paths and the paper's model need index-matched faces and Lambertian walls");
+    if (dielectric && sensor_set && c.kind != FLR_SENSOR_NONE) {
+        if (c.kind != FLR_SENSOR_ORTHO)
+            return fail(ctx, FLR_ERR_ARG, "interfaces: dielectric faces need an orthographic sensor");
+        const int zeros = (c.view[0] == 0.0f) + (c.view[1] == 0.0f) + (c.view[2] == 0.0f);
+        if (zeros != 2)
+            return fail(ctx, FLR_ERR_ARG, "interfaces: the orthographic sensor must look along a face normal");
+    }
+    return FLR_OK;
+}
+
 // Checks one medium against the context's spectrum and dye table (no device work).
 int validate_medium(flr_ctx *ctx, const flr_medium *m)
 {
@@ -425,13 +467,18 @@ int validate_medium(flr_ctx *ctx, const flr_medium *m)
         return fail(ctx, FLR_ERR_ARG, "medium: sigma_s and sigma_a0 must be finite and >= 0");
     if (m->wall_mask < 0 || m->wall_mask > 63 || !(m->wall_albedo >= 0.0f && m->wall_albedo <= 1.0f))
         return fail(ctx, FLR_ERR_ARG, "medium: wall mask 0..63 and albedo in [0,1]");
+    if (!((m->ior == 0.0f || (m->ior >= 1.0f && m->ior <= 10.0f)) &&
+          (m->wall_gloss >= 0.0f && m->wall_gloss <= 1.0f) &&
+          (m->wall_exponent >= 0.0f && m->wall_exponent <= 10000.0f)))
+        return fail(ctx, FLR_ERR_ARG, "medium: ior 0 or in [1, 10], wall_gloss in [0, 1], wall_exponent in [0, 1e4]");
     const bool grids = medium_has_grid(*m) || m->solvent;
     if (grids) {
         for (int k = 0; k < 3; ++k)
             if (m->dims[k] < 1 || m->dims[k] > 4096) return fail(ctx, FLR_ERR_ARG, "medium: dims 1..4096");
         // the kernels index voxels with 32-bit integers
-        if ((long long)m->dims[0] * m->dims[1] * m->dims[2] > 2147483647LL)
-            return fail(ctx, FLR_ERR_ARG, "medium: at most 2^31 - 1 voxels");
+        if ((long long)m->dims[0] * m->dims[1] * m->dims[2] > 2147483647LL ||
+            packed_voxels(m->dims) > 2147483647LL)
+            return fail(ctx, FLR_ERR_ARG, "medium: at most 2^31 - 1 voxels (also once padded to whole 4^3 bricks)");
         for (int d = 0; d < m->n_dyes; ++d)
             if (m->conc[d] && !is_device_pointer(m->conc[d]))
                 return fail(ctx, FLR_ERR_ARG, "medium: concentration grids must be device memory");
@@ -604,15 +651,16 @@ int flr_set_medium(flr_ctx *ctx, const flr_medium *m)
     float smax = 1.0f;
     cudaError_t e;
     if (medium_has_grid(mm)) {
-        if ((size_t)n > ctx->grid_cap) {
+        const size_t np = (size_t)packed_voxels(mm.dims);
+        if (np > ctx->grid_cap) {
             cudaFree(ctx->d_grid);
             ctx->d_grid = nullptr;
             ctx->grid_cap = 0;
-            e = cudaMalloc(&ctx->d_grid, sizeof(float4) * (size_t)n);
+            e = cudaMalloc(&ctx->d_grid, sizeof(float4) * np);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate the interleaved grid");
-            ctx->grid_cap = (size_t)n;
+            ctx->grid_cap = np;
         }
-        e = launch_pack_grid(mm.conc, mm.conc_uniform, mm.n_dyes, n, ctx->d_grid, 0);
+        e = launch_pack_grid(mm.conc, mm.conc_uniform, mm.n_dyes, mm.dims, ctx->d_grid, 0);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "pack grids");
     }
     for (int d = 0; d < mm.n_dyes; ++d) {
@@ -678,8 +726,11 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     if (!p) return fail(ctx, FLR_ERR_ARG, "params: NULL");
     if (ctx->B <= 0 || !ctx->medium_set) return fail(ctx, FLR_ERR_STATE, "render: spectrum, dyes and medium must be set");
     if (ctx->sources.empty()) return fail(ctx, FLR_ERR_STATE, "render: no sources");
-    if (p->form != FLR_FORM_PLAIN && p->form != FLR_FORM_WAVEFRONT && p->form != FLR_FORM_WAVEFRONT_WARP)
+    if (p->form != FLR_FORM_PLAIN && p->form != FLR_FORM_WAVEFRONT && p->form != FLR_FORM_WAVEFRONT_WARP &&
+        p->form != FLR_FORM_WAVEFRONT_POOL)
         return fail(ctx, FLR_ERR_ARG, "params: unknown form");
+    if (p->form == FLR_FORM_WAVEFRONT_POOL && (p->macro_cell > 0 || p->hero > 0))
+        return fail(ctx, FLR_ERR_ARG, "params: the pool form takes one majorant per bin and one wavelength per path");
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || (p->block_size & 31)))
         return fail(ctx, FLR_ERR_ARG, "params: block_size must be 32..256, a multiple of 32");
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
@@ -699,6 +750,11 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
         bool inside = true;
         for (int k = 0; k < 3; ++k) inside = inside && o[k] >= ctx->medium.lo[k] && o[k] <= ctx->medium.hi[k];
         if (inside) return fail(ctx, FLR_ERR_ARG, "sensor: the pinhole must lie outside the medium box");
+    }
+    {
+        const int irc = check_interfaces(ctx, ctx->medium, ctx->sensor_set && p->film, ctx->sensor, p->hero,
+                                         p->paper_mode);
+        if (irc != FLR_OK) return irc;
     }
     DeviceGuard g(ctx->device);
     int rc = prepare_tables(ctx, p->majorant_margin);
@@ -768,6 +824,8 @@ int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
     if (p->hero != 0) return fail(ctx, FLR_ERR_ARG, "params: hero paths are for flr_render only");
+    if (ctx->medium.ior > 1.0f || ctx->medium.wall_gloss > 0.0f)
+        return fail(ctx, FLR_ERR_ARG, "camera: index-matched faces and Lambertian walls only");
     const uint64_t npix = (uint64_t)ctx->sensor.width * (uint64_t)ctx->sensor.height;
     if (p->n_paths % npix != 0 || p->path_offset % npix != 0)
         return fail(ctx, FLR_ERR_ARG, "camera: n_paths and path_offset must be multiples of the pixel count");
@@ -1012,6 +1070,10 @@ int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float 
     if (p->n_rr < 0 || p->max_events < 0 || p->max_steps < 1 || p->max_events > 2000000000LL)
         return fail(ctx, FLR_ERR_ARG, "params: n_rr, max_events >= 0, max_steps >= 1");
     if (p->hero != 0) return fail(ctx, FLR_ERR_ARG, "params: hero paths are for flr_render only");
+    {
+        const int irc = check_interfaces(ctx, ctx->medium, true, ctx->sensor, 0, p->paper_mode);
+        if (irc != FLR_OK) return irc;
+    }
     if (!is_device_pointer(adj_film)) return fail(ctx, FLR_ERR_ARG, "adjoint: adj_film must be device memory");
     if (grad_conc && !medium_has_grid(ctx->medium))
         return fail(ctx, FLR_ERR_ARG, "adjoint: grad_conc needs a medium with concentration grids");
@@ -1127,17 +1189,20 @@ int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const 
     if (!(p->majorant_margin >= 0.0f && p->majorant_margin <= 100.0f))
         return fail(ctx, FLR_ERR_ARG, "params: majorant_margin in [0, 100]");
     const int B = ctx->B;
-    std::vector<long long> off(n_media, -1), nv(n_media, 0);
+    std::vector<long long> off(n_media, -1), nv(n_media, 0), npk(n_media, 0);
     long long arena = 0;
     for (int m = 0; m < n_media; ++m) {
         const int rc = validate_medium(ctx, &media[m]);
         if (rc != FLR_OK) return rc;
+        if (media[m].ior > 1.0f || media[m].wall_gloss > 0.0f)
+            return fail(ctx, FLR_ERR_ARG, "batch: index-matched faces and Lambertian walls only");
         if (n_paths[m] > 0xFFFFFFFFull * 64ull) return fail(ctx, FLR_ERR_ARG, "batch: too many paths");
         const bool grids = medium_has_grid(media[m]) || media[m].solvent;
         nv[m] = grids ? nvox(media[m]) : 1;
         if (medium_has_grid(media[m])) {
+            npk[m] = packed_voxels(media[m].dims);
             off[m] = arena;
-            arena += nv[m];
+            arena += npk[m];
         }
     }
     DeviceGuard g(ctx->device);
@@ -1158,7 +1223,7 @@ int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const 
     cudaError_t e = cudaMemset(bt.d_max, 0, sizeof(unsigned) * (size_t)n_media * 8);
     for (int m = 0; m < n_media && e == cudaSuccess; ++m) {
         const flr_medium &md = media[m];
-        if (off[m] >= 0) e = launch_pack_grid(md.conc, md.conc_uniform, md.n_dyes, nv[m], bt.d_arena + off[m], 0);
+        if (off[m] >= 0) e = launch_pack_grid(md.conc, md.conc_uniform, md.n_dyes, md.dims, bt.d_arena + off[m], 0);
         for (int d = 0; d < md.n_dyes && e == cudaSuccess; ++d)
             if (md.conc[d])
                 e = launch_grid_max(md.conc[d], nv[m], bt.d_max + (size_t)m * 8 + d, (int *)(bt.d_max + (size_t)m * 8 + 4), 0);
@@ -1198,6 +1263,7 @@ int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const 
             o.lo[k] = md.lo[k];
             o.hi[k] = md.hi[k];
             o.dims[k] = (medium_has_grid(md) || md.solvent) ? md.dims[k] : 1;
+            o.bdims[k] = grid_bricks(o.dims[k]);
             o.vox_scale[k] = (float)((double)o.dims[k] / ((double)md.hi[k] - (double)md.lo[k]));
         }
         o.grid = off[m] >= 0 ? bt.d_arena + off[m] : nullptr;
@@ -1422,11 +1488,15 @@ extern "C" int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins
             inside = inside && c.sensor.origin[k] >= medium->lo[k] && c.sensor.origin[k] <= medium->hi[k];
         if (inside) return FLR_ERR_ARG;
     }
+    if (check_interfaces(&c, *medium, c.sensor_set && p->film, c.sensor, p->hero, p->paper_mode) != FLR_OK)
+        return FLR_ERR_ARG;
     flr_medium mm = *medium;
     const bool grids = medium_has_grid(mm) || mm.solvent;
     if (!grids) mm.dims[0] = mm.dims[1] = mm.dims[2] = 1;
     const long long n = nvox(mm);
-    if (n > FLR_NOALLOC_MAX_VOXELS) return FLR_ERR_ARG;  // beyond the static scratch
+    // beyond the static scratch (which holds the grid padded to whole 4^3-voxel bricks)
+    if (n > FLR_NOALLOC_MAX_VOXELS || (medium_has_grid(mm) && packed_voxels(mm.dims) > FLR_NOALLOC_MAX_VOXELS))
+        return FLR_ERR_ARG;
     unsigned char *base = nullptr;
     cudaError_t e = noalloc_address(dev, &base);
     if (e != cudaSuccess) return FLR_ERR_CUDA;
@@ -1440,7 +1510,7 @@ extern "C" int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins
     cudaStream_t st = (cudaStream_t)stream;
     // grid maxima for the majorant ([0..3] dyes, [4] bad-value flag, [5] solvent present)
     e = cudaMemsetAsync(maxima, 0, 8 * sizeof(unsigned), st);
-    if (e == cudaSuccess && medium_has_grid(mm)) e = launch_pack_grid(mm.conc, mm.conc_uniform, mm.n_dyes, n, grid, st);
+    if (e == cudaSuccess && medium_has_grid(mm)) e = launch_pack_grid(mm.conc, mm.conc_uniform, mm.n_dyes, mm.dims, grid, st);
     for (int d = 0; d < mm.n_dyes && e == cudaSuccess; ++d)
         if (mm.conc[d]) e = launch_grid_max(mm.conc[d], n, maxima + d, reinterpret_cast<int *>(maxima + 4), st);
     if (e == cudaSuccess && mm.solvent) e = launch_solvent_any(mm.solvent, n, maxima + 5, st);

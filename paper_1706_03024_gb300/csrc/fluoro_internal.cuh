@@ -46,10 +46,30 @@ __host__ __device__ constexpr int tal_emitted(int B) { return 12 * B + (MAXD + 1
 __host__ __device__ constexpr int tal_size(int B) { return 12 * B + (2 * MAXD + 1) * B; }
 constexpr double TALLY_ONE = 16777216.0;  // 2^24
 
+// The library's interleaved concentration grid (one float4 of up to four dyes per voxel) is stored
+// in bricks of 4^3 voxels: x fastest inside a brick, bricks x fastest over the grid padded to
+// whole bricks. A free flight or a ratio-tracking step moves a few voxels, so consecutive lookups
+// of a path, and those of nearby paths, fall in the same 1 KB brick (the same cache lines and DRAM
+// page) far more often than in a row-major layout, where a step in z jumps nx * ny voxels.
+constexpr int GRID_BRICK = 4;
+__host__ __device__ inline int grid_bricks(int n) { return (n + GRID_BRICK - 1) / GRID_BRICK; }
+__host__ __device__ inline long long packed_voxels(const int dims[3])
+{
+    return (long long)grid_bricks(dims[0]) * grid_bricks(dims[1]) * grid_bricks(dims[2]) *
+           (GRID_BRICK * GRID_BRICK * GRID_BRICK);
+}
+// Index in the packed grid of voxel (ix, iy, iz); bdims = bricks per axis.
+__host__ __device__ inline int packed_index(int ix, int iy, int iz, const int bdims[3])
+{
+    const int b = ((iz >> 2) * bdims[1] + (iy >> 2)) * bdims[0] + (ix >> 2);
+    return (b << 6) | ((iz & 3) << 4) | ((iy & 3) << 2) | (ix & 3);
+}
+
 struct EmitterDev {
     float origin[3], eu[3], ev[3], dir[3];
     int kind, bin, axis;
     float sign;
+    int entry;                         // dielectric face the source enters through, or -1
 };
 
 // Scene description passed by value to the kernels (lives in the constant bank).
@@ -57,6 +77,7 @@ struct SceneDev {
     int B, D;
     float lo[3], hi[3], vox_scale[3];  // vox_scale = dims / (hi - lo)
     int dims[3];
+    int bdims[3];                      // bricks per axis of the packed grid
     int homogeneous;                   // no grid and no solvent mask
     const float4 *grid;                // [nvox] interleaved concentrations of the medium's dyes
     const uint8_t *solvent;            // [nvox] or nullptr
@@ -86,6 +107,12 @@ struct SceneDev {
     float maj_margin;                  // local majorants are multiplied by this (>= 1)
     const uint8_t *mc_dist;            // 0: cell may hold matter; k >= 1: every cell within
                                        // Chebyshev distance k - 1 is empty (leaping)
+    // interfaces and glossy walls (flr_medium::ior, wall_gloss, wall_exponent): iface != 0 when
+    // either is on; open faces are dielectric when ior > 1; iface_exit = (1 - F(0)) / ior^2, the
+    // share of radiance a connection carries out through a dielectric face at normal incidence
+    int iface, dielectric;
+    float ior, inv_ior, iface_exit;
+    float wall_gloss, wall_exp;
 };
 
 // Per-launch run parameters.
@@ -125,6 +152,7 @@ constexpr int BATCH_MAX_LINES = 8;
 struct MediumDev {
     float lo[3], hi[3], vox_scale[3];
     int dims[3];
+    int bdims[3];                      // bricks per axis of the packed grid
     int homogeneous, D;
     const float4 *grid;                // interleaved concentrations inside the batch arena
     const uint8_t *solvent;
@@ -192,7 +220,8 @@ cudaError_t launch_empty_distance(const float4 *mc, const float *ms, const int m
                                   cudaStream_t st);
 cudaError_t launch_grid_max(const float *g, long long n, unsigned int *out_bits, int *neg_flag,
                             cudaStream_t st);
-cudaError_t launch_pack_grid(const float *const *conc, const float *uniform, int D, long long n,
+// interleaves the dyes' row-major grids into the bricked layout (packed_voxels(dims) float4s)
+cudaError_t launch_pack_grid(const float *const *conc, const float *uniform, int D, const int dims[3],
                              float4 *out, cudaStream_t st);
 cudaError_t launch_solvent_any(const uint8_t *s, long long n, unsigned int *out, cudaStream_t st);
 cudaError_t launch_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, long long n,

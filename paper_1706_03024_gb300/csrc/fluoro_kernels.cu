@@ -17,8 +17,9 @@
 //
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by (seed, medium), counter
 // (path_lo, step, slot, path_hi). Slot 0 of a tracking step gives (u_dist, u_real, u_event,
-// u_dir1), slot 1 (u_dir2, u_emit, u_rr, u_coin), slots 2.. feed the step's sensor connection.
-// Spawn uses step 0xFFFFFFFF. Uniforms are 24-bit: u = (x >> 8) 2^-24.
+// u_dir1), slot 1 (u_dir2, u_emit, u_rr, u_coin); slot 2 seeds the xoshiro128** stream of the
+// step's sensor connection (its ratio-tracking march). Spawn uses step 0xFFFFFFFF. Uniforms are
+// 24-bit: u = (x >> 8) 2^-24.
 #include <cfloat>
 #include <cstdint>
 
@@ -73,6 +74,52 @@ __device__ __forceinline__ U4 draw_rk(const RunDev &R, uint64_t pid, uint32_t st
         c = make_uint4(hi1 ^ c.y ^ R.rk[r], lo1, hi0 ^ c.w ^ R.rk[10 + r], lo0);
     }
     return U4{u24(c.x), u24(c.y), u24(c.z), u24(c.w)};
+}
+
+// The raw words of that block.
+__device__ __forceinline__ uint4 draw_raw_rk(const RunDev &R, uint64_t pid, uint32_t step, uint32_t slot)
+{
+    uint4 c = make_uint4((uint32_t)pid, step, slot, (uint32_t)(pid >> 32));
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ R.rk[r], lo1, hi0 ^ c.w ^ R.rk[10 + r], lo0);
+    }
+    return c;
+}
+
+// Uniforms of one sensor connection's ratio-tracking march: the xoshiro128** generator (Blackman and
+// Vigna, "Scrambled linear pseudorandom number generators", ACM TOMS 2021) seeded with the Philox
+// block of the connection's counter (path, step, slot 2). A march draws one uniform per step (and
+// one more for a roulette), always the next of its stream, so every lane of a warp pays the same
+// dozen integer operations per step instead of a whole Philox block whenever its own four-uniform
+// block runs out (which, with the lanes' marches at different points, is nearly every step for
+// some lane). Every form and replay of a connection draws the same stream. The oracle evaluates
+// transmittances exactly (reading 17), so nothing on its side depends on these numbers.
+struct MarchRng {
+    uint32_t s0, s1, s2, s3;
+};
+
+__device__ __forceinline__ MarchRng march_rng(const RunDev &R, uint64_t pid, uint32_t step, uint32_t slot = 2u)
+{
+    const uint4 b = draw_raw_rk(R, pid, step, slot);
+    MarchRng g{b.x, b.y, b.z, b.w};
+    if ((b.x | b.y | b.z | b.w) == 0u) g.s0 = 1u;   // the all-zero state would stay zero
+    return g;
+}
+
+__device__ __forceinline__ float march_next(MarchRng &g)
+{
+    const uint32_t r = __funnelshift_l(g.s1 * 5u, g.s1 * 5u, 7) * 9u;
+    const uint32_t t = g.s1 << 9;
+    g.s2 ^= g.s0;
+    g.s3 ^= g.s1;
+    g.s1 ^= g.s2;
+    g.s0 ^= g.s3;
+    g.s2 ^= t;
+    g.s3 = __funnelshift_l(g.s3, g.s3, 11);
+    return u24(r);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -139,8 +186,10 @@ __device__ __forceinline__ void tally_add(const Smem &sm, int idx, float w)
 //         read-only path, tables in global memory (L1-resident), tallies in global memory.
 // OPT = false compiles the local-majorant and empty-space paths out (the plain baseline kernel);
 // MC = false compiles the local-majorant path alone out (launched whenever the scene has none:
-// the smaller code keeps the warp-regrouped kernel's loops in the instruction cache).
-template <bool OPT, bool MC = OPT>
+// the smaller code keeps the warp-regrouped kernel's loops in the instruction cache); IF = false
+// compiles dielectric faces and glossy walls out (scenes with index-matched faces and Lambertian
+// walls).
+template <bool OPT, bool MC = OPT, bool IF = true>
 struct MedS_ {
     const SceneDev &S;
     const Smem &sm;
@@ -150,6 +199,7 @@ struct MedS_ {
     __device__ __forceinline__ float hi(int k) const { return S.hi[k]; }
     __device__ __forceinline__ float vox_scale(int k) const { return S.vox_scale[k]; }
     __device__ __forceinline__ int dims(int k) const { return S.dims[k]; }
+    __device__ __forceinline__ const int *bdims() const { return S.bdims; }
     __device__ __forceinline__ bool homogeneous() const { return S.homogeneous != 0; }
     __device__ __forceinline__ const float4 *grid() const { return S.grid; }
     __device__ __forceinline__ const uint8_t *solvent() const { return S.solvent; }
@@ -196,6 +246,20 @@ struct MedS_ {
     __device__ __forceinline__ float mc_solvent(int c) const { return cell_ok(c) ? __ldg(&S.mc_s[c]) : 0.0f; }
     __device__ __forceinline__ int mc_empty_radius(int c) const { return cell_ok(c) ? (int)__ldg(&S.mc_dist[c]) : 0; }
     __device__ __forceinline__ bool skip() const { return OPT && S.sk > 0; }
+    __device__ __forceinline__ bool iface() const { return IF && S.iface != 0; }
+    __device__ __forceinline__ bool dielectric() const { return S.dielectric != 0; }
+    __device__ __forceinline__ float ior() const { return S.ior; }
+    __device__ __forceinline__ float inv_ior() const { return S.inv_ior; }
+    __device__ __forceinline__ float wall_gloss() const { return S.wall_gloss; }
+    __device__ __forceinline__ float wall_exp() const { return S.wall_exp; }
+    // unit direction from x toward the sensor (orthographic: the view direction)
+    __device__ __forceinline__ float3 sensor_dir(float3 x) const
+    {
+        if (S.sensor_kind == FLR_SENSOR_ORTHO) return make_float3(S.s_view[0], S.s_view[1], S.s_view[2]);
+        const float vx = S.s_origin[0] - x.x, vy = S.s_origin[1] - x.y, vz = S.s_origin[2] - x.z;
+        const float ir = rsqrtf(vx * vx + vy * vy + vz * vz);
+        return make_float3(vx * ir, vy * ir, vz * ir);
+    }
 };
 using MedS = MedS_<true>;
 
@@ -214,6 +278,7 @@ struct MedB {
     __device__ __forceinline__ float hi(int k) const { return __ldg(&md->hi[k]); }
     __device__ __forceinline__ float vox_scale(int k) const { return __ldg(&md->vox_scale[k]); }
     __device__ __forceinline__ int dims(int k) const { return __ldg(&md->dims[k]); }
+    __device__ __forceinline__ const int *bdims() const { return md->bdims; }
     __device__ __forceinline__ bool homogeneous() const { return __ldg(&md->homogeneous) != 0; }
     __device__ __forceinline__ const float4 *grid() const
     {
@@ -271,6 +336,13 @@ struct MedB {
     __device__ __forceinline__ float mc_solvent(int) const { return 0.0f; }
     __device__ __forceinline__ int mc_empty_radius(int) const { return 0; }
     __device__ __forceinline__ bool skip() const { return false; }
+    __device__ __forceinline__ bool iface() const { return false; }
+    __device__ __forceinline__ bool dielectric() const { return false; }
+    __device__ __forceinline__ float ior() const { return 1.0f; }
+    __device__ __forceinline__ float inv_ior() const { return 1.0f; }
+    __device__ __forceinline__ float wall_gloss() const { return 0.0f; }
+    __device__ __forceinline__ float wall_exp() const { return 0.0f; }
+    __device__ __forceinline__ float3 sensor_dir(float3) const { return make_float3(0.f, 0.f, 1.f); }
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -280,8 +352,9 @@ struct Coeffs {
     float dye[MAXD];
 };
 
+// Nearest voxel of x (clamped to the grid): its (ix, iy, iz).
 template <class M>
-__device__ __forceinline__ int voxel_of(const M &m, float3 x)
+__device__ __forceinline__ int3 voxel_ijk(const M &m, float3 x)
 {
     int ix = __float2int_rd((x.x - m.lo(0)) * m.vox_scale(0));
     int iy = __float2int_rd((x.y - m.lo(1)) * m.vox_scale(1));
@@ -289,7 +362,15 @@ __device__ __forceinline__ int voxel_of(const M &m, float3 x)
     ix = min(max(ix, 0), m.dims(0) - 1);
     iy = min(max(iy, 0), m.dims(1) - 1);
     iz = min(max(iz, 0), m.dims(2) - 1);
-    return (iz * m.dims(1) + iy) * m.dims(0) + ix;
+    return make_int3(ix, iy, iz);
+}
+
+// Row-major [nz][ny][nx] index of the nearest voxel: the caller's layout (solvent mask, gradients).
+template <class M>
+__device__ __forceinline__ int voxel_of(const M &m, float3 x)
+{
+    const int3 c = voxel_ijk(m, x);
+    return (c.z * m.dims(1) + c.y) * m.dims(0) + c.x;
 }
 
 template <class M>
@@ -298,11 +379,12 @@ __device__ __forceinline__ Coeffs coeffs_at(const M &m, float3 x, int b)
     float s = 1.0f;
     float4 c = m.conc_uniform();
     if (!m.homogeneous()) {
-        const int v = voxel_of(m, x);
+        const int3 q = voxel_ijk(m, x);
+        const int v = (q.z * m.dims(1) + q.y) * m.dims(0) + q.x;
         const float4 *g = m.grid();
         const uint8_t *sv = m.solvent();
         if (FLR_CHK(v >= 0 && v < m.dims(0) * m.dims(1) * m.dims(2), CK_GRID, v)) {
-            if (g) c = __ldg(&g[v]);
+            if (g) c = __ldg(&g[packed_index(q.x, q.y, q.z, m.bdims())]);
             if (sv) s = __ldg(&sv[v]) ? 1.0f : 0.0f;
         }
     }
@@ -567,6 +649,62 @@ __device__ __forceinline__ float3 cosine_dir(float u1, float u2, int axis, float
 
 __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 
+__device__ __forceinline__ void set_comp(float3 &v, int k, float a)
+{
+    if (k == 0) v.x = a; else if (k == 1) v.y = a; else v.z = a;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Dielectric faces and glossy walls (Sec. 5's glass vials and glossy Cornell box; the paper does not
+// specify them, these are the standard choices). Reflectance of unpolarised light at a smooth
+// interface from index n1 into n2 for a ray meeting it at cos_i, eta = n1 / n2 (Fresnel's
+// equations divided through by n2); beyond the critical angle everything is reflected. cos_t: the
+// refracted ray's cosine (Snell: sin_t = eta sin_i).
+__device__ __forceinline__ float fresnel_refl(float cos_i, float eta, float &cos_t)
+{
+    const float sin_t2 = eta * eta * fmaxf(0.0f, 1.0f - cos_i * cos_i);
+    if (sin_t2 >= 1.0f) {
+        cos_t = 0.0f;
+        return 1.0f;
+    }
+    const float ct = sqrtf(1.0f - sin_t2);
+    cos_t = ct;
+    const float rs = (eta * cos_i - ct) / (eta * cos_i + ct);
+    const float rp = (cos_i - eta * ct) / (cos_i + eta * ct);
+    return 0.5f * (rs * rs + rp * rp);
+}
+
+// Normalised Phong lobe about the unit vector r: cos alpha = u1^(1/(e+1)), azimuth 2 pi u2 in r's
+// tangent frame (Duff et al., "Building an orthonormal basis, revisited", JCGT 2017).
+__device__ __forceinline__ float3 phong_dir(float u1, float u2, float3 r, float e)
+{
+    const float ca = __powf(u1, 1.0f / (e + 1.0f));
+    const float sa = sqrtf(fmaxf(0.0f, 1.0f - ca * ca));
+    float sn, cs;
+    __sincosf(TWO_PI * u2, &sn, &cs);
+    const float sg = copysignf(1.0f, r.z);
+    const float a = -1.0f / (sg + r.z);
+    const float b = r.x * r.y * a;
+    const float3 t1 = make_float3(1.0f + sg * r.x * r.x * a, sg * b, -sg * r.x);
+    const float3 t2 = make_float3(b, sg + r.y * r.y * a, -r.y);
+    const float p = sa * cs, q = sa * sn;
+    return make_float3(p * t1.x + q * t2.x + ca * r.x, p * t1.y + q * t2.y + ca * r.y,
+                       p * t1.z + q * t2.z + ca * r.z);
+}
+
+// The wall BRDF without its albedo, times cos_o, toward o for a photon with mirror direction r:
+// (1 - g) cos_o / pi + g (e + 2)/(2 pi) cos^e alpha cos_o.
+__device__ __forceinline__ float wall_lobe_cos(float g, float e, float3 r, float3 o, float cos_o)
+{
+    const float ca = r.x * o.x + r.y * o.y + r.z * o.z;
+    const float lobe = ca > 0.0f ? (e + 2.0f) * (0.5f * INV_PI) * __powf(ca, e) : 0.0f;
+    return ((1.0f - g) * INV_PI + g * lobe) * cos_o;
+}
+
+// Vertex kind of a connection whose weight already holds the vertex's intensity toward the sensor
+// (glossy wall vertices): the connection multiplies by importance and transmittance only.
+constexpr int LAMB_WEIGHTED = 6;
+
 // ---------------------------------------------------------------------------------------------
 // Sensor connection (Eq. 3-6). `lamb` < 0: isotropic vertex, intensity w/(4 pi); otherwise a
 // Lambertian vertex with normal sign*e_axis (lamb = 2*axis + (sign > 0)), intensity w cos/pi.
@@ -618,7 +756,9 @@ __device__ __forceinline__ ConnGeom connect_geom(const SceneDev &S, const Smem &
         geom = __fdividef(S.inv_A_pix, r2 * ct * ct * ct);
     }
     float f;
-    if (lamb >= 0) {
+    if (lamb == LAMB_WEIGHTED) {
+        f = 1.0f;
+    } else if (lamb >= 0) {
         const int axis = lamb >> 1;
         const float co = (lamb & 1) ? comp(dir, axis) : -comp(dir, axis);
         if (!(co > 0.0f)) return g;
@@ -632,6 +772,8 @@ __device__ __forceinline__ ConnGeom connect_geom(const SceneDev &S, const Smem &
     const float tl = exit_distance(m, x, dir, idr, face);
     if (face < 0) return g;
     if (S.wall_mask & (1 << face)) return g;
+    // out through a dielectric face at normal incidence: (1 - F(0)) / ior^2 of the radiance
+    if (S.dielectric) f *= S.iface_exit;
     if (S.sensor_kind == FLR_SENSOR_PINHOLE && tl * tl > r2) return g;
     g.dir = dir;
     g.idr = idr;
@@ -668,14 +810,10 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
         // ratio tracking against the local majorants: one uniform per tentative point
         Dda dd;
         dda_init(m, dd, x, dir, inv_dir(dir));
-        U4 blk = U4{0, 0, 0, 0};
-        uint32_t j = 0;
+        MarchRng rg = march_rng(R, pid, step, SLOT0);
         int it = 0;
         for (; it < MAX_CONNECT_STEPS; ++it) {
-            if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, SLOT0 + (j >> 2));
-            const uint32_t q = j & 3u;
-            const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
-            ++j;
+            const float u = march_next(rg);
             float sbc;
             const float t = dda_advance(m, dd, b, -__logf(1.0f - u), tl, sbc, rc.cell_walks);
             if (t >= tl) break;
@@ -685,10 +823,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
             sink.point(p, b, st, sbc);
             T *= fmaxf(0.0f, 1.0f - st / sbc);
             if (T < (ADJ ? RT_RR_ADJ_THRESHOLD : RT_RR_THRESHOLD)) {
-                if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, SLOT0 + (j >> 2));
-                const uint32_t q2 = j & 3u;
-                const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
-                ++j;
+                const float u2 = march_next(rg);
                 if (ADJ ? u2 < 0.5f : u2 * RT_RR_THRESHOLD < T) {
                     T = ADJ ? 2.0f * T : RT_RR_THRESHOLD;
                 } else {
@@ -705,14 +840,10 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
     }
     const float isb = sm.inv_maj[b];
     float t = 0.0f;
-    U4 blk = U4{0, 0, 0, 0};
-    uint32_t j = 0;
+    MarchRng rg = march_rng(R, pid, step, SLOT0);
     int it = 0;
     for (; it < MAX_CONNECT_STEPS; ++it) {
-        if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, SLOT0 + (j >> 2));
-        const uint32_t q = j & 3u;
-        const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
-        ++j;
+        const float u = march_next(rg);
         t -= __logf(1.0f - u) * isb;
         if (t >= tl) break;
         rc.connect_steps++;
@@ -729,10 +860,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
             }
         }
         if (T < (ADJ ? RT_RR_ADJ_THRESHOLD : RT_RR_THRESHOLD)) {
-            if ((j & 3u) == 0u) blk = draw_rk(R, pid, step, SLOT0 + (j >> 2));
-            const uint32_t q2 = j & 3u;
-            const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
-            ++j;
+            const float u2 = march_next(rg);
             if (ADJ ? u2 < 0.5f : u2 * RT_RR_THRESHOLD < T) {
                 T = ADJ ? 2.0f * T : RT_RR_THRESHOLD;
             } else {
@@ -835,6 +963,25 @@ __device__ __forceinline__ Conn spawn(const M &m, const RunDev &R, const Smem &s
     } else {
         p.w = make_float3(e.dir[0], e.dir[1], e.dir[2]);
     }
+    if (m.iface() && e.entry >= 0) {
+        // entering the solution through a dielectric face (coin: spawn slot 1, word 1): the
+        // Fresnel-reflected share leaves through that face, the rest refracts inward by Snell
+        const U4 s1 = m.rng(R, pid, STEP_SPAWN, 1u);
+        const int f = e.entry, k = f >> 1;
+        const float wk = comp(p.w, k);
+        float ct;
+        const float F = fresnel_refl(fabsf(wk), m.inv_ior(), ct);
+        if (s1.b < F) {
+            cnt_add(sm, FLR_C_IFACE_REFLECTIONS);
+            m.tally(tal_face(m.B()) + f * m.B() + p.bin, p.wt);
+            cnt_add(sm, FLR_C_ESCAPES);
+            finish(R, p);
+            return c;
+        }
+        const float eta = m.inv_ior();
+        p.w = make_float3(p.w.x * eta, p.w.y * eta, p.w.z * eta);
+        set_comp(p.w, k, wk > 0.0f ? ct : -ct);
+    }
     p.iw = inv_dir(p.w);
     return c;
 }
@@ -879,6 +1026,7 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
     // the new direction: isotropic (dax < 0) or cosine about dsg * e_dax, from (du1, du2)
     int dax = -1;
     float dsg = 1.0f, du1 = b0.d, du2 = b1.a;
+    int gw = 0;   // glossy wall bounce: 1 diffuse lobe, 2 Phong lobe (direction already drawn)
     if (tf >= te) {
         p.x = make_float3(p.x.x + te * p.w.x, p.x.y + te * p.w.y, p.x.z + te * p.w.z);
         if (face < 0) {  // no direction component: cannot happen for unit directions
@@ -887,6 +1035,28 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
             return c;
         }
         if (!(m.wall_mask() & (1 << face))) {
+            if (m.iface() && m.dielectric()) {
+                // a dielectric face from inside: Fresnel reflection (an event; the coin is the
+                // step's unused u_real), else refraction out of the solution (an escape)
+                const int k = face >> 1;
+                float ct;
+                const float F = fresnel_refl(fabsf(comp(p.w, k)), m.ior(), ct);
+                if (b0.b < F) {
+                    if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
+                    p.n_events++;
+                    rc.events++;
+                    cnt_add(sm, FLR_C_IFACE_REFLECTIONS);
+                    set_comp(p.w, k, -comp(p.w, k));
+                    set_comp(p.x, k, (face & 1) ? m.hi(k) : m.lo(k));
+                    p.iw = inv_dir(p.w);
+                    if (p.n_events >= R.n_rr) {
+                        const float q = fminf(p.wt, 1.0f);
+                        if (!(b1.c < q)) { cnt_add(sm, FLR_C_RR_KILLS); finish(R, p); return c; }
+                        p.wt = p.wt < 1.0f ? 1.0f : p.wt;
+                    }
+                    return c;
+                }
+            }
             m.tally(tal_face(m.B()) + (p.fl * 6 + face) * m.B() + p.bin, p.wt);
             cnt_add(sm, FLR_C_ESCAPES);
             finish(R, p);
@@ -911,6 +1081,28 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
         else p.x.z = (face & 1) ? m.hi(2) : m.lo(2);
         du1 = b0.c;
         du2 = b0.d;
+        if (m.iface() && m.wall_gloss() > 0.0f) {
+            // glossy wall: the sensor sees the whole BRDF (evaluated here, so the connection carries
+            // it in its weight); the path continues in the Phong lobe about the mirror direction
+            // with probability g (lobe choice: u_dir2; weight (e + 2)/(e + 1) cos_o, ended below
+            // the wall), else in the diffuse lobe
+            float3 r = p.w;
+            set_comp(r, dax, -comp(r, dax));
+            const float g = m.wall_gloss(), e = m.wall_exp();
+            gw = 1;
+            if (m.sensor()) {
+                const float3 od = m.sensor_dir(p.x);
+                const float co = dsg * comp(od, dax);
+                if (co > 0.0f) c = Conn{p.x, p.wt * wall_lobe_cos(g, e, r, od, co), p.bin, LAMB_WEIGHTED, p.pid, step, true};
+            }
+            if (b1.a < g) {
+                p.w = phong_dir(du1, du2, r, e);
+                const float co = dsg * comp(p.w, dax);
+                if (!(co > 0.0f)) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+                p.wt *= (e + 2.0f) / (e + 1.0f) * co;
+                gw = 2;
+            }
+        }
     } else {
         p.x = make_float3(p.x.x + tf * p.w.x, p.x.y + tf * p.w.y, p.x.z + tf * p.w.z);
         // the empty-space distance is read beside the coefficients, not after them
@@ -983,7 +1175,7 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
     // One direction sampler for scattering and emission (isotropic: z = 1 - 2 u1, phi = 2 pi u2)
     // and wall bounces (cosine-weighted, the operations of cosine_dir): a warp whose lanes scatter
     // and bounce runs it once instead of both (measured 3 % on the Cornell box).
-    {
+    if (gw != 2) {
         const float u1 = du1;
         float sn, cs;
         __sincosf(TWO_PI * du2, &sn, &cs);
@@ -999,7 +1191,7 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
         p.w = dax == 0 ? make_float3(a, bx, by) : (dax == 1 ? make_float3(by, a, bx) : make_float3(bx, by, a));
     }
     p.iw = inv_dir(p.w);
-    if (m.sensor()) c = Conn{p.x, p.wt, p.bin, dax < 0 ? -1 : 2 * dax + (dsg > 0.0f ? 1 : 0), p.pid, step, true};
+    if (m.sensor() && gw == 0) c = Conn{p.x, p.wt, p.bin, dax < 0 ? -1 : 2 * dax + (dsg > 0.0f ? 1 : 0), p.pid, step, true};
     if (p.n_events >= R.n_rr) {
         const float q = fminf(p.wt, 1.0f);
         if (!(b1.c < q)) { cnt_add(sm, FLR_C_RR_KILLS); finish(R, p); return c; }
@@ -1033,13 +1225,27 @@ constexpr int WQ_DRAIN = 288;
 constexpr int SPAWN_MIN = 8;   // lanes that start new paths together
 static_assert(WQ_DRAIN + 31 < WQ_CAP, "warp queue overflow");
 
+// Path-pool form (k_trace_pool): slots per warp, connection queue, per-warp shared memory.
+constexpr int POOL_SLOTS = 64;   // lane l keeps the states of slots l and l + 32
+static_assert(POOL_SLOTS == 64, "k_trace_pool's slot bookkeeping assumes two slots per lane");
+// Queues of 160 records (drained at 128) let five blocks of 128 threads share an SM: measured on
+// the Cornell box 14.46 ms per step against 15.45 ms with 224 records and four blocks, 14.97 ms
+// with 128 records and 15.46 ms with 192.
+constexpr int PQ_CAP = 160;    // connection records per warp
+constexpr int PQ_DRAIN = 128;  // a round adds at most 32 records, so the queue never wraps
+static_assert(PQ_DRAIN + 31 < PQ_CAP, "pool queue overflow");
+constexpr int POOL_WORDS = 19; // 4-byte fields per slot
+enum { PS_FREE = 0, PS_TRACK = 1, PS_EVENT = 2 };
+constexpr int POOL_WARP_BYTES = PQ_CAP * 32 + POOL_WORDS * POOL_SLOTS * 4 + POOL_SLOTS + 32 * 4 + 16;
+static_assert(POOL_WARP_BYTES % 16 == 0, "per-warp pool keeps 16-byte alignment");
+
 __host__ __device__ inline SmemLayout smem_layout(int B, int form, int block)
 {
     SmemLayout L;
     L.tab_floats = tab_size(B);
     int off = ((L.tab_floats * 4 + 15) / 16) * 16;
     L.tal_off_bytes = off;
-    L.tal_global = form == FLR_FORM_WAVEFRONT_WARP;
+    L.tal_global = form == FLR_FORM_WAVEFRONT_WARP || form == FLR_FORM_WAVEFRONT_POOL;
     if (!L.tal_global) off += tal_size(B) * 8;
     L.cnt_off_bytes = off;
     off += FLR_NCOUNTERS * 8;
@@ -1047,6 +1253,7 @@ __host__ __device__ inline SmemLayout smem_layout(int B, int form, int block)
     L.queue_off_bytes = off;
     if (form == FLR_FORM_WAVEFRONT) off += 2 * block * 32 + 16;
     if (form == FLR_FORM_WAVEFRONT_WARP) off += (block / 32) * (WQ_CAP * 32 + 8);
+    if (form == FLR_FORM_WAVEFRONT_POOL) off += (block / 32) * POOL_WARP_BYTES;
     L.total_bytes = off;
     return L;
 }
@@ -1109,13 +1316,13 @@ __device__ __forceinline__ void block_epilogue(const SceneDev &S, const RunDev &
 
 // ---------------------------------------------------------------------------------------------
 // Plain form: one thread per path, grid-stride over path ids, connections made inline.
-template <bool OPT>
+template <bool OPT, bool IF>
 __global__ void __launch_bounds__(256) k_trace_plain(SceneDev S, RunDev R)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
     const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
-    const MedS_<OPT> m{S, sm};
+    const MedS_<OPT, OPT, IF> m{S, sm};
     RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
@@ -1165,11 +1372,12 @@ __device__ __forceinline__ MatterPt matter_at(const M &m, float3 x)
 {
     MatterPt r{1.0f, m.conc_uniform()};
     if (!m.homogeneous()) {
-        const int v = voxel_of(m, x);
+        const int3 q = voxel_ijk(m, x);
+        const int v = (q.z * m.dims(1) + q.y) * m.dims(0) + q.x;
         const float4 *g = m.grid();
         const uint8_t *sv = m.solvent();
         if (FLR_CHK(v >= 0 && v < m.dims(0) * m.dims(1) * m.dims(2), CK_GRID, v)) {
-            if (g) r.c = __ldg(&g[v]);
+            if (g) r.c = __ldg(&g[packed_index(q.x, q.y, q.z, m.bdims())]);
             if (sv) r.s = __ldg(&sv[v]) ? 1.0f : 0.0f;
         }
     }
@@ -1279,14 +1487,10 @@ __device__ __forceinline__ void connect_hero(const M &m, const SceneDev &S, cons
             if (j < h.n) T[j] = __expf(-coeffs_of(m, pt, h.bin[j]).total * g.tl);
     } else if (h.sb > 0.0f) {
         float t = 0.0f;
-        U4 blk = U4{0, 0, 0, 0};
-        uint32_t jr = 0;
+        MarchRng rg = march_rng(R, pid, step);
         int it = 0;
         for (; it < MAX_CONNECT_STEPS; ++it) {
-            if ((jr & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (jr >> 2));
-            const uint32_t qd = jr & 3u;
-            const float u = qd == 0 ? blk.a : (qd == 1 ? blk.b : (qd == 2 ? blk.c : blk.d));
-            ++jr;
+            const float u = march_next(rg);
             t -= __logf(1.0f - u) * h.isb;
             if (t >= g.tl) break;
             rc.connect_steps++;
@@ -1312,10 +1516,7 @@ __device__ __forceinline__ void connect_hero(const M &m, const SceneDev &S, cons
                 }
             }
             if (Tq < RT_RR_THRESHOLD) {
-                if ((jr & 3u) == 0u) blk = draw_rk(R, pid, step, 2u + (jr >> 2));
-                const uint32_t q2 = jr & 3u;
-                const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
-                ++jr;
+                const float u2 = march_next(rg);
                 if (u2 * RT_RR_THRESHOLD < Tq) {
                     if (h.n == 1) {
                         T[0] = RT_RR_THRESHOLD;
@@ -1891,14 +2092,10 @@ __device__ __forceinline__ float frozen_contribution(const SceneDev &S, const Ru
         } else {
             const float isb = sm.inv_maj[c.bin];
             float T0 = 1.0f, t = 0.0f;
-            U4 blk = U4{0, 0, 0, 0};
-            uint32_t j = 0;
+            MarchRng rg = march_rng(R, c.pid, c.step);
             int it = 0;
             for (; it < MAX_CONNECT_STEPS; ++it) {
-                if ((j & 3u) == 0u) blk = draw_rk(R, c.pid, c.step, 2u + (j >> 2));
-                const uint32_t q = j & 3u;
-                const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
-                ++j;
+                const float u = march_next(rg);
                 t -= __logf(1.0f - u) * isb;
                 if (t >= g.tl) break;
                 rc.connect_steps++;
@@ -1911,10 +2108,7 @@ __device__ __forceinline__ float frozen_contribution(const SceneDev &S, const Ru
                 T0 *= fmaxf(0.0f, f0);
                 T *= fmaxf(0.0f, f0 - d * isb);
                 if (T0 < RT_RR_ADJ_THRESHOLD) {
-                    if ((j & 3u) == 0u) blk = draw_rk(R, c.pid, c.step, 2u + (j >> 2));
-                    const uint32_t q2 = j & 3u;
-                    const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
-                    ++j;
+                    const float u2 = march_next(rg);
                     if (u2 < 0.5f) {
                         T0 *= 2.0f;
                         T *= 2.0f;
@@ -1986,9 +2180,8 @@ struct March {
     float3 x, dir, idir;
     float tl, t, T, isb, wg;   // wg: intensity x importance (render, pass 1) or a_k (pass 2)
     int b, pix, it, ord;
-    uint32_t j, step;
     uint64_t pid;
-    U4 blk;
+    MarchRng g;                // the connection's uniform stream
 };
 
 // A queued connection record: position, weight (pass 2: a_k), bin, vertex kind, ordinal along
@@ -2076,19 +2269,12 @@ __device__ __forceinline__ bool march_begin(const SceneDev &S, const RunDev &R, 
     mc.T = 1.0f;
     mc.isb = sm.inv_maj[b];
     mc.idir = g.idr;
-    mc.j = 0;
     mc.it = 0;
-    mc.step = step;
+    mc.g = march_rng(R, pid, step);
     return true;
 }
 
-__device__ __forceinline__ float march_uniform(const RunDev &R, March &mc)
-{
-    if ((mc.j & 3u) == 0u) mc.blk = draw_rk(R, mc.pid, mc.step, 2u + (mc.j >> 2));
-    const uint32_t q = mc.j & 3u;
-    ++mc.j;
-    return q == 0 ? mc.blk.a : (q == 1 ? mc.blk.b : (q == 2 ? mc.blk.c : mc.blk.d));
-}
+__device__ __forceinline__ float march_uniform(const RunDev &, March &mc) { return march_next(mc.g); }
 
 // One ratio-tracking step (the body of transmittance()'s loop); returns false when the march ends.
 template <int MODE>
@@ -2133,13 +2319,13 @@ __device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, c
     return true;
 }
 
-template <int MODE, bool MC>
+template <int MODE, bool MC, bool IF = true>
 __global__ void __launch_bounds__(WARP_BLOCK, (MODE == WM_RENDER && !MC) ? 5 : 4) k_trace_wavefront_warp(SceneDev S, RunDev R, AdjDev A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT_WARP, blockDim.x);
     const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
-    const MedS_<true, MC> m{S, sm};
+    const MedS_<true, MC, IF> m{S, sm};
     constexpr unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
@@ -2280,6 +2466,469 @@ __global__ void __launch_bounds__(WARP_BLOCK, (MODE == WM_RENDER && !MC) ? 5 : 4
 
 
 // ---------------------------------------------------------------------------------------------
+// The two halves of track_step, for the path-pool form: the free flight (block 0 of the step:
+// tentative distance, null or real collision, empty-space leap, escape) and the event it leads to
+// (block 1: collision type, re-emission, wall bounce or interface reflection, new direction, sensor
+// connection, roulette). Together they take the decisions of track_step on the same random numbers
+// in the same order, so the pool form traces exactly the paths every other form traces (tested bit
+// for bit on the fixed-point tallies). Local majorants are not supported here (the pool form runs
+// with one majorant per bin, with or without empty-space leaps).
+enum { FL_NONE = 0, FL_MEDIUM = 1, FL_WALL = 2, FL_IFACE = 3 };
+
+struct Flight {
+    int kind, face;
+    MatterPt pt;            // FL_MEDIUM: the matter at the collision point
+    float u_event, u_dir1;  // block 0, words 2 and 3
+};
+
+template <class M>
+__device__ __forceinline__ Flight flight_step(const M &m, const RunDev &R, const Smem &sm, Path &p, RegCnt &rc)
+{
+    Flight fl;
+    fl.kind = FL_NONE;
+    fl.face = -1;
+    if ((long long)p.step >= R.max_steps) {
+        cnt_add(sm, FLR_C_STEP_BUDGET);
+        finish(R, p);
+        return fl;
+    }
+    rc.steps++;
+    const U4 b0 = m.rng(R, p.pid, p.step, 0u);
+    fl.u_event = b0.c;
+    fl.u_dir1 = b0.d;
+    int face;
+    const float te = exit_distance(m, p.x, p.w, p.iw, face);
+    const float sb = m.maj(p.bin);
+    const float tf = sb > 0.0f ? -__logf(1.0f - b0.a) * m.inv_maj(p.bin) : FLT_MAX;
+    p.step++;
+    if (tf >= te) {
+        p.x = make_float3(p.x.x + te * p.w.x, p.x.y + te * p.w.y, p.x.z + te * p.w.z);
+        if (face < 0) {
+            cnt_add(sm, FLR_C_NONFINITE);
+            finish(R, p);
+            return fl;
+        }
+        fl.face = face;
+        if (!(m.wall_mask() & (1 << face))) {
+            if (m.iface() && m.dielectric()) {
+                float ct;
+                const float F = fresnel_refl(fabsf(comp(p.w, face >> 1)), m.ior(), ct);
+                if (b0.b < F) {
+                    fl.kind = FL_IFACE;
+                    return fl;
+                }
+            }
+            m.tally(tal_face(m.B()) + (p.fl * 6 + face) * m.B() + p.bin, p.wt);
+            cnt_add(sm, FLR_C_ESCAPES);
+            finish(R, p);
+            return fl;
+        }
+        fl.kind = FL_WALL;
+        return fl;
+    }
+    p.x = make_float3(p.x.x + tf * p.w.x, p.x.y + tf * p.w.y, p.x.z + tf * p.w.z);
+    const int4 ec = m.skip() ? empty_cell(m, p.x) : make_int4(0, 0, 0, 0);
+    const MatterPt pt = matter_at(m, p.x);
+    const Coeffs k = coeffs_of(m, pt, p.bin);
+    if (k.total > sb) cnt_add(sm, FLR_C_MAJORANT_VIOLATIONS);
+    if (!(b0.b * sb < k.total)) {
+        rc.nulls++;
+        if (m.skip() && k.total == 0.0f) {
+            float tl = empty_cube_exit_at(m, ec, p.x, p.w, p.iw);
+            if (tl > 0.0f) {
+                tl = fminf(tl, te - tf);
+                p.x = make_float3(p.x.x + tl * p.w.x, p.x.y + tl * p.w.y, p.x.z + tl * p.w.z);
+                rc.cell_walks++;
+            }
+        }
+        return fl;
+    }
+    fl.kind = FL_MEDIUM;
+    fl.pt = pt;
+    return fl;
+}
+
+template <class M>
+__device__ __forceinline__ Conn event_step(const M &m, const RunDev &R, const Smem &sm, Path &p,
+                                           const Flight &fl, RegCnt &rc)
+{
+    Conn c;
+    c.valid = false;
+    const uint32_t step = p.step - 1u;
+    const U4 b1 = m.rng(R, p.pid, step, 1u);
+    int dax = -1;
+    float dsg = 1.0f, du1 = fl.u_dir1, du2 = b1.a;
+    int gw = 0;
+    if (fl.kind == FL_IFACE) {
+        const int face = fl.face, k = face >> 1;
+        if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
+        p.n_events++;
+        rc.events++;
+        cnt_add(sm, FLR_C_IFACE_REFLECTIONS);
+        set_comp(p.w, k, -comp(p.w, k));
+        set_comp(p.x, k, (face & 1) ? m.hi(k) : m.lo(k));
+        p.iw = inv_dir(p.w);
+        if (p.n_events >= R.n_rr) {
+            const float q = fminf(p.wt, 1.0f);
+            if (!(b1.c < q)) { cnt_add(sm, FLR_C_RR_KILLS); finish(R, p); return c; }
+            p.wt = p.wt < 1.0f ? 1.0f : p.wt;
+        }
+        return c;
+    }
+    if (fl.kind == FL_WALL) {
+        const int face = fl.face;
+        if (R.paper_mode && !p.fl) { cnt_add(sm, FLR_C_VF_REJECTED); finish(R, p); return c; }
+        if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
+        p.n_events++;
+        rc.events++;
+        cnt_add(sm, FLR_C_WALL_BOUNCES);
+        if (R.analog) {
+            if (!(b1.d < m.wall_albedo())) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+        } else {
+            p.wt *= m.wall_albedo();
+            if (p.wt == 0.0f) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+        }
+        dax = face >> 1;
+        dsg = (face & 1) ? -1.0f : 1.0f;
+        if (dax == 0) p.x.x = (face & 1) ? m.hi(0) : m.lo(0);
+        else if (dax == 1) p.x.y = (face & 1) ? m.hi(1) : m.lo(1);
+        else p.x.z = (face & 1) ? m.hi(2) : m.lo(2);
+        du1 = fl.u_event;
+        du2 = fl.u_dir1;
+        if (m.iface() && m.wall_gloss() > 0.0f) {
+            float3 r = p.w;
+            set_comp(r, dax, -comp(r, dax));
+            const float g = m.wall_gloss(), e = m.wall_exp();
+            gw = 1;
+            if (m.sensor()) {
+                const float3 od = m.sensor_dir(p.x);
+                const float co = dsg * comp(od, dax);
+                if (co > 0.0f) c = Conn{p.x, p.wt * wall_lobe_cos(g, e, r, od, co), p.bin, LAMB_WEIGHTED, p.pid, step, true};
+            }
+            if (b1.a < g) {
+                p.w = phong_dir(du1, du2, r, e);
+                const float co = dsg * comp(p.w, dax);
+                if (!(co > 0.0f)) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+                p.wt *= (e + 2.0f) / (e + 1.0f) * co;
+                gw = 2;
+            }
+        }
+    } else {
+        const Coeffs k = coeffs_of(m, fl.pt, p.bin);
+        if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
+        p.n_events++;
+        rc.events++;
+        const float ue = fl.u_event * k.total;
+        float acc = k.scat;
+        int ev = -1;
+        const int D = m.D();
+        if (!(ue < acc)) {
+            ev = D;
+#pragma unroll
+            for (int d = 0; d < MAXD; ++d) {
+                if (d < D && ev == D) {
+                    acc += k.dye[d];
+                    if (ue < acc) ev = d;
+                }
+            }
+        }
+        if (ev < 0) {
+            rc.scatters++;
+            if (R.paper_mode && !p.fl) { cnt_add(sm, FLR_C_VF_REJECTED); finish(R, p); return c; }
+        } else if (ev < D) {
+            cnt_add(sm, FLR_C_DYE_ABSORPTIONS);
+            m.tally(tal_absorbed(m.B()) + ev * m.B() + p.bin, p.wt);
+            if ((R.max_inelastic >= 0 && p.n_inel >= R.max_inelastic) || (R.paper_mode && p.n_inel >= 1)) {
+                cnt_add(sm, FLR_C_VF_REJECTED);
+                finish(R, p);
+                return c;
+            }
+            if (R.analog) {
+                if (!(b1.d < m.qy(ev))) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+            } else {
+                p.wt *= m.qy(ev);
+                if (p.wt == 0.0f) { cnt_add(sm, FLR_C_ABSORBED_DEAD); finish(R, p); return c; }
+            }
+            p.bin = sample_cdf(m.cdf(ev), m.B(), b1.b);
+            m.tally(tal_emitted(m.B()) + ev * m.B() + p.bin, p.wt);
+            cnt_add(sm, FLR_C_EMISSIONS);
+            p.n_inel++;
+            p.fl = 1;
+        } else {
+            m.tally(tal_absorbed(m.B()) + D * m.B() + p.bin, p.wt);
+            cnt_add(sm, FLR_C_ABSORBED_DEAD);
+            finish(R, p);
+            return c;
+        }
+    }
+    if (gw != 2) {
+        const float u1 = du1;
+        float sn, cs;
+        __sincosf(TWO_PI * du2, &sn, &cs);
+        float a, r;
+        if (dax < 0) {
+            a = 1.0f - 2.0f * u1;
+            r = sqrt_approx(fmaxf(0.0f, 1.0f - a * a));
+        } else {
+            r = sqrt_approx(u1);
+            a = dsg * sqrt_approx(fmaxf(0.0f, 1.0f - u1));
+        }
+        const float bx = r * cs, by = r * sn;
+        p.w = dax == 0 ? make_float3(a, bx, by) : (dax == 1 ? make_float3(by, a, bx) : make_float3(bx, by, a));
+    }
+    p.iw = inv_dir(p.w);
+    if (m.sensor() && gw == 0) c = Conn{p.x, p.wt, p.bin, dax < 0 ? -1 : 2 * dax + (dsg > 0.0f ? 1 : 0), p.pid, step, true};
+    if (p.n_events >= R.n_rr) {
+        const float q = fminf(p.wt, 1.0f);
+        if (!(b1.c < q)) { cnt_add(sm, FLR_C_RR_KILLS); finish(R, p); return c; }
+        p.wt = p.wt < 1.0f ? 1.0f : p.wt;
+    }
+    if (!(isfinite(p.wt) && isfinite(p.x.x) && isfinite(p.x.y) && isfinite(p.x.z))) {
+        cnt_add(sm, FLR_C_NONFINITE);
+        finish(R, p);
+        c.valid = false;
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Path-pool form: regrouping by event type. Each warp keeps POOL_SLOTS paths in a shared-memory
+// SoA (position, direction, weight, bin, counters, RNG coordinates, and the outcome of the last
+// free flight). Every round the warp ballots the slots' states and runs one kind of work on up to
+// 32 of them at once, each lane taking the k-th slot of that kind (ballot + prefix compaction):
+//   track  one free flight (null collisions, leaps and escapes end here);
+//   event  the collision, wall bounce or interface reflection a free flight reached;
+//   spawn  new paths into free slots, claimed from the launch's work counter in one atomic.
+// Event rounds run once 32 events wait (or no full tracking round is left), so both kinds of
+// work run on full warps instead of splitting every step's warp between the lanes that collide
+// and those that fly on. Sensor connections go to the per-warp queue and pull-based drains of the
+// warp-regrouped form.
+
+struct Pool {
+    float *px, *py, *pz, *wx, *wy, *wz, *wt, *c0, *c1, *c2, *c3, *ue, *ud;
+    uint32_t *step, *nev, *nin, *misc, *plo, *phi;   // misc: bin | fl << 8 | s << 9 | kind << 10 | face << 12
+    uint8_t *status;
+    int *scratch;
+};
+
+__device__ __forceinline__ void pool_load(const Pool &P, int s, Path &p)
+{
+    p.x = make_float3(P.px[s], P.py[s], P.pz[s]);
+    p.w = make_float3(P.wx[s], P.wy[s], P.wz[s]);
+    p.iw = inv_dir(p.w);
+    p.wt = P.wt[s];
+    const uint32_t mi = P.misc[s];
+    p.bin = (int)(mi & 0xFFu);
+    p.fl = (int)((mi >> 8) & 1u);
+    p.step = P.step[s];
+    p.n_events = (int)P.nev[s];
+    p.n_inel = (int)P.nin[s];
+    p.pid = ((uint64_t)P.phi[s] << 32) | P.plo[s];
+    p.alive = true;
+}
+
+__device__ __forceinline__ void pool_store(const Pool &P, int s, const Path &p)
+{
+    P.px[s] = p.x.x;
+    P.py[s] = p.x.y;
+    P.pz[s] = p.x.z;
+    P.wx[s] = p.w.x;
+    P.wy[s] = p.w.y;
+    P.wz[s] = p.w.z;
+    P.wt[s] = p.wt;
+    P.misc[s] = (uint32_t)p.bin | ((uint32_t)p.fl << 8);
+    P.step[s] = p.step;
+    P.nev[s] = (uint32_t)p.n_events;
+    P.nin[s] = (uint32_t)p.n_inel;
+    P.plo[s] = (uint32_t)p.pid;
+    P.phi[s] = (uint32_t)(p.pid >> 32);
+}
+
+template <int CAP>
+__device__ __forceinline__ void queue_push_cap(const Queue &q, const Conn &c)
+{
+    const int slot = atomicAdd(&q.head_tail[1], 1) % CAP;
+    (void)FLR_CHK(q.head_tail[1] <= CAP, CK_QUEUE, slot);
+    q.x[slot] = c.x.x;
+    q.y[slot] = c.x.y;
+    q.z[slot] = c.x.z;
+    q.w[slot] = c.w;
+    q.bin_lamb[slot] = (c.bin & 0xFF) | ((c.lamb + 1) << 8);
+    q.pid_lo[slot] = (uint32_t)c.pid;
+    q.pid_hi[slot] = (uint32_t)(c.pid >> 32);
+    q.step[slot] = c.step;
+}
+
+template <bool IF>
+__global__ void __launch_bounds__(WARP_BLOCK, 5) k_trace_pool(SceneDev S, RunDev R)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT_POOL, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
+    const MedS_<true, false, IF> m{S, sm};
+    constexpr unsigned FULL = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lower = (1u << lane) - 1u;
+    unsigned char *wb = smem_raw + L.queue_off_bytes + (size_t)warp * POOL_WARP_BYTES;
+    Queue q;
+    {
+        float *f = reinterpret_cast<float *>(wb);
+        q.x = f;
+        q.y = q.x + PQ_CAP;
+        q.z = q.y + PQ_CAP;
+        q.w = q.z + PQ_CAP;
+        q.bin_lamb = reinterpret_cast<int *>(q.w + PQ_CAP);
+        q.pid_lo = reinterpret_cast<uint32_t *>(q.bin_lamb + PQ_CAP);
+        q.pid_hi = q.pid_lo + PQ_CAP;
+        q.step = q.pid_hi + PQ_CAP;
+    }
+    Pool P;
+    {
+        float *f = reinterpret_cast<float *>(wb + PQ_CAP * 32);
+        float **fs[13] = {&P.px, &P.py, &P.pz, &P.wx, &P.wy, &P.wz, &P.wt, &P.c0, &P.c1, &P.c2, &P.c3, &P.ue, &P.ud};
+#pragma unroll
+        for (int i = 0; i < 13; ++i) *fs[i] = f + i * POOL_SLOTS;
+        uint32_t *u = reinterpret_cast<uint32_t *>(f + 13 * POOL_SLOTS);
+        uint32_t **us[6] = {&P.step, &P.nev, &P.nin, &P.misc, &P.plo, &P.phi};
+#pragma unroll
+        for (int i = 0; i < 6; ++i) *us[i] = u + i * POOL_SLOTS;
+        P.status = reinterpret_cast<uint8_t *>(u + 6 * POOL_SLOTS);
+        P.scratch = reinterpret_cast<int *>(P.status + POOL_SLOTS);
+        q.head_tail = P.scratch + 32;
+    }
+    P.status[lane] = PS_FREE;
+    P.status[lane + 32] = PS_FREE;
+    if (lane == 0) { q.head_tail[0] = 0; q.head_tail[1] = 0; }
+    __syncwarp();
+    RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
+    float gsig = 0.0f;
+    const AdjDev A{};
+    bool exhausted = false;
+    while (true) {
+        const int s0 = P.status[lane], s1 = P.status[lane + 32];
+        const unsigned tlo = __ballot_sync(FULL, s0 == PS_TRACK), thi = __ballot_sync(FULL, s1 == PS_TRACK);
+        const unsigned elo = __ballot_sync(FULL, s0 == PS_EVENT), ehi = __ballot_sync(FULL, s1 == PS_EVENT);
+        const int nT = __popc(tlo) + __popc(thi), nE = __popc(elo) + __popc(ehi);
+        const int nF = POOL_SLOTS - nT - nE;
+        int kind;   // 0 spawn, 1 event, 2 track, 3 done
+        if (!exhausted && (nF >= 32 || (nF >= SPAWN_MIN && nT < 32 && nE < 32))) kind = 0;
+        else if (nE >= 32 || (nE > 0 && nT < 32)) kind = 1;
+        else if (nT > 0) kind = 2;
+        else kind = exhausted ? 3 : 0;
+        if (kind != 3) {
+            unsigned lo, hi;
+            if (kind == 0) { lo = ~(tlo | elo); hi = ~(thi | ehi); }
+            else if (kind == 1) { lo = elo; hi = ehi; }
+            else { lo = tlo; hi = thi; }
+            const int n = min(32, __popc(lo) + __popc(hi));
+            // ballot + prefix: the k-th slot of this kind goes to lane k
+            if ((lo >> lane) & 1u) {
+                const int r = __popc(lo & lower);
+                if (r < 32) P.scratch[r] = lane;
+            }
+            if ((hi >> lane) & 1u) {
+                const int r = __popc(lo) + __popc(hi & lower);
+                if (r < 32) P.scratch[r] = lane + 32;
+            }
+            __syncwarp();
+            const int slot = lane < n ? P.scratch[lane] : -1;
+            __syncwarp();
+            if (kind == 0) {
+                unsigned long long base = 0ull;
+                if (lane == 0) base = atomicAdd(R.work_counter, (unsigned long long)n);
+                base = __shfl_sync(FULL, base, 0);
+                if (base + (unsigned long long)n >= R.n_paths) exhausted = true;
+                if (slot >= 0 && base + (unsigned long long)lane < R.n_paths) {
+                    Path p;
+                    const Conn c = spawn(m, R, sm, R.path_offset + base + (unsigned long long)lane, p);
+                    if (c.valid) queue_push_cap<PQ_CAP>(q, c);
+                    if (p.alive) {
+                        pool_store(P, slot, p);
+                        P.status[slot] = PS_TRACK;
+                    }
+                }
+            } else if (kind == 2) {
+                if (slot >= 0) {
+                    Path p;
+                    pool_load(P, slot, p);
+                    const Flight fl = flight_step(m, R, sm, p, rc);
+                    if (!p.alive) {
+                        P.status[slot] = PS_FREE;
+                    } else {
+                        P.px[slot] = p.x.x;
+                        P.py[slot] = p.x.y;
+                        P.pz[slot] = p.x.z;
+                        P.step[slot] = p.step;
+                        if (fl.kind != FL_NONE) {
+                            P.c0[slot] = fl.pt.c.x;
+                            P.c1[slot] = fl.pt.c.y;
+                            P.c2[slot] = fl.pt.c.z;
+                            P.c3[slot] = fl.pt.c.w;
+                            P.ue[slot] = fl.u_event;
+                            P.ud[slot] = fl.u_dir1;
+                            P.misc[slot] = (uint32_t)p.bin | ((uint32_t)p.fl << 8) |
+                                           ((fl.kind == FL_MEDIUM && fl.pt.s != 0.0f) ? (1u << 9) : 0u) |
+                                           ((uint32_t)fl.kind << 10) | ((uint32_t)max(fl.face, 0) << 12);
+                            P.status[slot] = PS_EVENT;
+                        }
+                    }
+                }
+            } else {
+                if (slot >= 0) {
+                    Path p;
+                    pool_load(P, slot, p);
+                    const uint32_t mi = P.misc[slot];
+                    Flight fl;
+                    fl.kind = (int)((mi >> 10) & 3u);
+                    fl.face = (int)((mi >> 12) & 7u);
+                    fl.pt.s = (mi >> 9) & 1u ? 1.0f : 0.0f;
+                    fl.pt.c = make_float4(P.c0[slot], P.c1[slot], P.c2[slot], P.c3[slot]);
+                    fl.u_event = P.ue[slot];
+                    fl.u_dir1 = P.ud[slot];
+                    const Conn c = event_step(m, R, sm, p, fl, rc);
+                    if (c.valid) queue_push_cap<PQ_CAP>(q, c);
+                    if (!p.alive) {
+                        P.status[slot] = PS_FREE;
+                    } else {
+                        pool_store(P, slot, p);
+                        P.status[slot] = PS_TRACK;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        const int avail = q.head_tail[1];
+        if (avail >= PQ_DRAIN || (kind == 3 && avail > 0)) {
+            // pull-based drain of all `avail` records (as in k_trace_wavefront_warp)
+            March mc;
+            bool active = false;
+            int claimed = 0;
+            for (uint32_t iter = 0;; ++iter) {
+                const unsigned need = (iter & 1u) == 0u ? __ballot_sync(FULL, !active) : 0u;
+                if (need != 0u && !active) {
+                    const int k = claimed + __popc(need & lower);
+                    if (k < avail) {
+                        const int bl = q.bin_lamb[k];
+                        const uint64_t pid = ((uint64_t)q.pid_hi[k] << 32) | q.pid_lo[k];
+                        active = march_begin<WM_RENDER, false>(S, R, sm, A, make_float3(q.x[k], q.y[k], q.z[k]),
+                                                               bl & 0xFF, q.w[k], ((bl >> 8) & 7) - 1, 0, pid,
+                                                               q.step[k], mc, rc, gsig);
+                    }
+                }
+                claimed += __popc(need);
+                if (active) active = march_step<WM_RENDER>(S, R, sm, A, mc, rc, gsig);
+                if (!__any_sync(FULL, active) && claimed >= avail) break;
+            }
+            __syncwarp();
+            if (lane == 0) q.head_tail[1] = 0;
+            __syncwarp();
+        }
+        if (kind == 3) break;
+    }
+    block_epilogue(S, R, sm, rc);
+}
+
+// ---------------------------------------------------------------------------------------------
 // Warp-regrouped form of the hero-wavelength tracer: the tracking round and the pull-based drains
 // of k_trace_wavefront_warp, with records that carry the member set. A record holds the vertex, the
 // path weight, the members' weights q_j and packed bins, the member count, the hero's index and the
@@ -2397,10 +3046,9 @@ __device__ __forceinline__ bool hero_march_begin(const SceneDev &S, const RunDev
     hm.mc.tl = g.tl;
     hm.mc.t = 0.0f;
     hm.mc.isb = m.inv_maj(bm);
-    hm.mc.j = 0;
     hm.mc.it = 0;
     hm.mc.pid = ((uint64_t)q.pid_hi[k] << 32) | q.pid_lo[k];
-    hm.mc.step = q.step[k];
+    hm.mc.g = march_rng(R, hm.mc.pid, q.step[k]);
     return true;
 }
 
@@ -2941,9 +3589,9 @@ __global__ void __launch_bounds__(256, 2) k_trace_camera_warp(SceneDev S, RunDev
             float3 x0, dir;
             float tl = 0.0f, t = 0.0f, T = 1.0f, isb = 0.0f, wt = 0.0f;
             int pix = 0, bin = 0, bx = 0, it = 0;
-            uint32_t j = 0, mstep = 0;
+            uint32_t mstep = 0;
             uint64_t pid = 0;
-            U4 blk = U4{0.f, 0.f, 0.f, 0.f};
+            MarchRng rg{0u, 0u, 0u, 0u};
             bool active = false;
             int claimed = 0;
             for (uint32_t iter = 0;; ++iter) {
@@ -2974,7 +3622,7 @@ __global__ void __launch_bounds__(256, 2) k_trace_camera_warp(SceneDev S, RunDev
                             t = 0.0f;
                             T = 1.0f;
                             isb = sm.inv_maj[bx];
-                            j = 0;
+                            rg = march_rng(R, pid, mstep, 3u);
                             it = 0;
                             active = true;
                         }
@@ -2982,16 +3630,14 @@ __global__ void __launch_bounds__(256, 2) k_trace_camera_warp(SceneDev S, RunDev
                 }
                 claimed += __popc(need);
                 if (active) {
-                    // one ratio-tracking step (the body of transmittance()'s loop, slots 3..)
+                    // one ratio-tracking step (the body of transmittance()'s loop; the stream
+                    // seeded by slot 3)
                     if (it >= MAX_CONNECT_STEPS) {
                         cnt_add(sm, FLR_C_CONNECT_BUDGET);
                         active = false;
                     } else {
                         ++it;
-                        if ((j & 3u) == 0u) blk = draw_rk(R, pid, mstep, 3u + (j >> 2));
-                        const uint32_t q = j & 3u;
-                        const float u = q == 0 ? blk.a : (q == 1 ? blk.b : (q == 2 ? blk.c : blk.d));
-                        ++j;
+                        const float u = march_next(rg);
                         t -= __logf(1.0f - u) * isb;
                         if (t >= tl) {
                             const float val = wt * T;
@@ -3006,10 +3652,7 @@ __global__ void __launch_bounds__(256, 2) k_trace_camera_warp(SceneDev S, RunDev
                             const float st = sigma_t_at(m, pnt, bx);
                             T *= fmaxf(0.0f, 1.0f - st * isb);
                             if (T < RT_RR_THRESHOLD) {
-                                if ((j & 3u) == 0u) blk = draw_rk(R, pid, mstep, 3u + (j >> 2));
-                                const uint32_t q2 = j & 3u;
-                                const float u2 = q2 == 0 ? blk.a : (q2 == 1 ? blk.b : (q2 == 2 ? blk.c : blk.d));
-                                ++j;
+                                const float u2 = march_next(rg);
                                 if (u2 * RT_RR_THRESHOLD < T) T = RT_RR_THRESHOLD;
                                 else active = false;
                             }
@@ -3136,6 +3779,8 @@ __global__ void k_build_macro(const float4 *__restrict__ grid, float4 uniform,
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
          c += (long long)gridDim.x * blockDim.x) {
         const int cx = (int)(c % mx), cy = (int)((c / mx) % my), cz = (int)(c / ((long long)mx * my));
+        const int dims[3] = {nx, ny, nz};
+        const int bd[3] = {grid_bricks(dims[0]), grid_bricks(dims[1]), grid_bricks(dims[2])};
         const int x0 = max(cx * cell - 1, 0), x1 = min((cx + 1) * cell, nx - 1);
         const int y0 = max(cy * cell - 1, 0), y1 = min((cy + 1) * cell, ny - 1);
         const int z0 = max(cz * cell - 1, 0), z1 = min((cz + 1) * cell, nz - 1);
@@ -3146,7 +3791,7 @@ __global__ void k_build_macro(const float4 *__restrict__ grid, float4 uniform,
                 for (int x = x0; x <= x1; ++x) {
                     const long long v = ((long long)z * ny + y) * nx + x;
                     if (grid) {
-                        const float4 g = grid[v];
+                        const float4 g = grid[packed_index(x, y, z, bd)];
                         m.x = fmaxf(m.x, g.x);
                         m.y = fmaxf(m.y, g.y);
                         m.z = fmaxf(m.z, g.z);
@@ -3202,8 +3847,11 @@ struct PackArgs {
     const float *conc[MAXD];
     float uniform[MAXD];
     int D;
+    int dims[3], bdims[3];
 };
 
+// Reads the caller's row-major grids and writes the interleaved voxels into their bricks; the
+// padding voxels of partial bricks are never read (lookups clamp to the grid).
 __global__ void k_pack_grid(PackArgs a, long long n, float4 *__restrict__ out)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -3212,7 +3860,9 @@ __global__ void k_pack_grid(PackArgs a, long long n, float4 *__restrict__ out)
 #pragma unroll
         for (int d = 0; d < MAXD; ++d)
             if (d < a.D) v[d] = a.conc[d] ? a.conc[d][i] : a.uniform[d];
-        out[i] = make_float4(v[0], v[1], v[2], v[3]);
+        const int ix = (int)(i % a.dims[0]), iy = (int)((i / a.dims[0]) % a.dims[1]);
+        const int iz = (int)(i / ((long long)a.dims[0] * a.dims[1]));
+        out[packed_index(ix, iy, iz, a.bdims)] = make_float4(v[0], v[1], v[2], v[3]);
     }
 }
 
@@ -3324,7 +3974,8 @@ cudaError_t allow_smem(int form, int smem)
         return cudaFuncSetAttribute(k_trace_wavefront, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (form == FLR_FORM_WAVEFRONT_WARP) {
         void (*const ks[])(SceneDev, RunDev, AdjDev) = {
-            k_trace_wavefront_warp<WM_RENDER, false>, k_trace_wavefront_warp<WM_RENDER, true>,
+            k_trace_wavefront_warp<WM_RENDER, false, false>, k_trace_wavefront_warp<WM_RENDER, false, true>,
+            k_trace_wavefront_warp<WM_RENDER, true>,
             k_trace_wavefront_warp<WM_ADJ_WEIGHTS, false>, k_trace_wavefront_warp<WM_ADJ_WEIGHTS, true>,
             k_trace_wavefront_warp<WM_ADJ_GRAD, false>, k_trace_wavefront_warp<WM_ADJ_GRAD, true>};
         for (auto k : ks) {
@@ -3333,10 +3984,13 @@ cudaError_t allow_smem(int form, int smem)
         }
         return cudaSuccess;
     }
-    cudaError_t e = cudaFuncSetAttribute(k_trace_plain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_trace_plain<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    void (*const kp[])(SceneDev, RunDev) = {k_trace_plain<true, true>, k_trace_plain<false, true>,
+                                             k_trace_plain<false, false>};
+    for (auto k : kp) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 }  // namespace
 
@@ -3348,15 +4002,31 @@ int occupancy_blocks_per_sm(int B, int form, int block)
     if (form == FLR_FORM_WAVEFRONT)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront, block, smem);
     else if (form == FLR_FORM_WAVEFRONT_WARP)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront_warp<WM_RENDER, false>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_wavefront_warp<WM_RENDER, false, false>, block, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_plain<true>, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_plain<true, true>, block, smem);
     return n > 0 ? n : 1;
+}
+
+cudaError_t launch_pool(const SceneDev &S, const RunDev &R, int blocks_per_sm, cudaStream_t st)
+{
+    const int block = WARP_BLOCK;
+    const int smem = trace_smem_bytes(S.B, FLR_FORM_WAVEFRONT_POOL, block);
+    void (*const k)(SceneDev, RunDev) = S.iface ? k_trace_pool<true> : k_trace_pool<false>;
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, smem);
+    if (occ < 1) occ = 1;
+    if (blocks_per_sm <= 0 || blocks_per_sm > occ) blocks_per_sm = occ;
+    k<<<(unsigned)(num_sms() * blocks_per_sm), block, smem, st>>>(S, R);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block, int blocks_per_sm,
                          cudaStream_t st)
 {
+    if (form == FLR_FORM_WAVEFRONT_POOL) return launch_pool(S, R, blocks_per_sm, st);
     if (R.hero > 0 && form == FLR_FORM_WAVEFRONT_WARP) return launch_hero_warp(S, R, block, blocks_per_sm, st);
     if (block <= 0) block = trace_block_default();
     if (form == FLR_FORM_WAVEFRONT_WARP) block = std::min(block, WARP_BLOCK);
@@ -3377,15 +4047,19 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
     {
         if (S.mc > 0)
             k_trace_wavefront_warp<WM_RENDER, true><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
+        else if (S.iface)
+            k_trace_wavefront_warp<WM_RENDER, false, true><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
         else
-            k_trace_wavefront_warp<WM_RENDER, false><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
+            k_trace_wavefront_warp<WM_RENDER, false, false><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
     }
     else if (R.hero > 0)
         k_trace_hero<<<(unsigned)grid, block, smem, st>>>(S, R);
     else if (S.mc > 0 || S.sk > 0)
-        k_trace_plain<true><<<(unsigned)grid, block, smem, st>>>(S, R);
+        k_trace_plain<true, true><<<(unsigned)grid, block, smem, st>>>(S, R);
+    else if (S.iface)
+        k_trace_plain<false, true><<<(unsigned)grid, block, smem, st>>>(S, R);
     else
-        k_trace_plain<false><<<(unsigned)grid, block, smem, st>>>(S, R);
+        k_trace_plain<false, false><<<(unsigned)grid, block, smem, st>>>(S, R);
     return cudaGetLastError();
 }
 
@@ -3513,10 +4187,15 @@ cudaError_t launch_grid_max(const float *g, long long n, unsigned int *out_bits,
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_grid(const float *const *conc, const float *uniform, int D, long long n,
+cudaError_t launch_pack_grid(const float *const *conc, const float *uniform, int D, const int dims[3],
                              float4 *out, cudaStream_t st)
 {
+    const long long n = (long long)dims[0] * dims[1] * dims[2];
     PackArgs a;
+    for (int k = 0; k < 3; ++k) {
+        a.dims[k] = dims[k];
+        a.bdims[k] = grid_bricks(dims[k]);
+    }
     for (int d = 0; d < MAXD; ++d) {
         a.conc[d] = d < D ? conc[d] : nullptr;
         a.uniform[d] = d < D ? uniform[d] : 0.0f;

@@ -25,7 +25,7 @@ FLR_MAX_DYES_PER_MEDIUM = 4
 FLR_MAX_SOURCES = 65536
 FLR_MAX_LINES = 8
 FLR_MAX_EMITTERS = 32
-FLR_NCOUNTERS = 20
+FLR_NCOUNTERS = 21
 FLR_NOALLOC_MAX_VOXELS = 1 << 18
 
 FLR_SOURCE_COLLIMATED = 0
@@ -36,11 +36,13 @@ FLR_SENSOR_PINHOLE = 2
 FLR_FORM_PLAIN = 0
 FLR_FORM_WAVEFRONT = 1
 FLR_FORM_WAVEFRONT_WARP = 2
+FLR_FORM_WAVEFRONT_POOL = 3
 
 COUNTER_NAMES = [
     "paths", "events", "nulls", "escapes", "absorbed_dead", "rr_kills", "cap_hits", "step_budget",
     "connections", "vf_rejected", "wall_bounces", "emissions", "scatters", "dye_absorptions",
     "steps", "majorant_violations", "connect_steps", "connect_budget", "nonfinite", "cell_walks",
+    "iface_reflections",
 ]
 
 FLR_ERR_CHECK = -6
@@ -62,7 +64,8 @@ class flr_medium(C.Structure):
                 ("conc_uniform", C.c_float * FLR_MAX_DYES_PER_MEDIUM),
                 ("solvent", C.c_void_p), ("sigma_s", C.c_float), ("sigma_a0", C.c_float),
                 ("wall_mask", C.c_int), ("wall_albedo", C.c_float),
-                ("source_first", C.c_int), ("source_count", C.c_int)]
+                ("source_first", C.c_int), ("source_count", C.c_int), ("ior", C.c_float),
+                ("wall_gloss", C.c_float), ("wall_exponent", C.c_float)]
 
 
 class flr_sensor(C.Structure):

@@ -15,7 +15,7 @@ from . import native as N
 _KINDS = {"collimated": N.FLR_SOURCE_COLLIMATED, "lambertian": N.FLR_SOURCE_LAMBERTIAN}
 _SENSORS = {"none": N.FLR_SENSOR_NONE, "ortho": N.FLR_SENSOR_ORTHO, "pinhole": N.FLR_SENSOR_PINHOLE}
 _FORMS = {"plain": N.FLR_FORM_PLAIN, "wavefront": N.FLR_FORM_WAVEFRONT,
-          "wavefront_warp": N.FLR_FORM_WAVEFRONT_WARP}
+          "wavefront_warp": N.FLR_FORM_WAVEFRONT_WARP, "wavefront_pool": N.FLR_FORM_WAVEFRONT_POOL}
 
 
 def _np_ptr(a):
@@ -121,6 +121,9 @@ class Scene:
         m.sigma_a0 = float(md["sigma_a0"])
         m.wall_mask = int(md["wall_mask"])
         m.wall_albedo = float(md["wall_albedo"])
+        m.ior = float(md.get("ior", 1.0))
+        m.wall_gloss = float(md.get("wall_gloss", 0.0))
+        m.wall_exponent = float(md.get("wall_exponent", 0.0))
         N.check(N.flr_set_medium(self.ctx, m), self.ctx, "flr_set_medium")
 
     def film_tensor(self):
@@ -352,6 +355,9 @@ class Batch:
             m.sigma_a0 = float(md["sigma_a0"])
             m.wall_mask = int(md["wall_mask"])
             m.wall_albedo = float(md["wall_albedo"])
+            m.ior = float(md.get("ior", 1.0))
+            m.wall_gloss = float(md.get("wall_gloss", 0.0))
+            m.wall_exponent = float(md.get("wall_exponent", 0.0))
             m.source_first = len(srcs)
             m.source_count = len(sc["sources"])
             srcs.extend(make_source(s) for s in sc["sources"])

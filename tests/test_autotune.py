@@ -6,7 +6,8 @@ def test_default_candidates_cover_depth_block_and_cells():
     c = default_candidates(has_grid=True, max_cell=8)
     assert {x.regroup for x in c} >= {1, 2, 4, 8}
     assert {x.block_size for x in c} == {128, 256}
-    assert {x.form for x in c} == {"wavefront", "wavefront_warp"}
+    assert {x.form for x in c} == {"wavefront", "wavefront_warp", "wavefront_pool"}
+    assert all(x.block_size == 128 and x.macro_cell == 0 for x in c if x.form == "wavefront_pool")
     assert {x.skip_cell for x in c} == {0, 1, 2, 4, 8}
     assert any(x.macro_cell for x in c)
     h = default_candidates(has_grid=False)

@@ -230,10 +230,18 @@ def test_cfg4_gradient_against_frozen_central_differences_on_64_voxels():
     adj = 2 (I(theta_0) - T), against central differences with a step of 1e-3 of the value, common
     random numbers (same seed and path ids) and the frozen-sampling estimator
     (flr_debug_frozen_sums), on 64 seeded random voxels (c >= 0.05) and sigma_s. Eight disjoint path
-    batches give an adjoint and a difference per batch; each parameter passes if the mean
-    difference is within max(3 SE, 1 % of the gradient) (plus 1e-6 of the largest, for gradients
-    near zero). The frozen estimator's derivative is the score-function estimator flr_adjoint
-    evaluates (Eq. 6 for the transmittance terms), so the two agree per path up to O(h^2)."""
+    batches give an adjoint and a difference per batch. The frozen estimator's derivative is the
+    score-function estimator flr_adjoint evaluates (Eq. 6 for the transmittance terms), so the two
+    agree path by path up to O(h^2) and fp32 rounding:
+      - each voxel passes if the mean difference is within max(3 SE, 1 % of the gradient) (plus
+        1e-6 of the largest, for gradients near zero);
+      - sigma_s enters every null and scattering decision and every transmittance of a path, and a
+        batch's sigma_s gradient is a few per cent of the sum of its paths' |derivatives| (a few
+        heavy paths of both signs carry it), so the per-path agreement is checked directly on the
+        heaviest paths (single-path replays, within 2e-3), and the batches against it: the mean
+        difference within max(3 SE, 1 % of the gradient, 1e-3 of the mean sum over paths of
+        |derivative|). The sigma_s difference is Richardson's combination (4 D(h/2) - D(h)) / 3 of
+        the steps 1e-3 and 5e-4 (the O(h^2) term of many decisions per path)."""
     sc = sg.cfg4_adjoint(field_seed=0, seed=0)
     n = sc["params"]["n_paths"]
     assert n == 256 * 256 * 32 and sc["medium"]["conc"].shape == (2, 64, 64, 64)
@@ -249,10 +257,13 @@ def test_cfg4_gradient_against_frozen_central_differences_on_64_voxels():
     nz, ny, nx = conc.shape[1:]
     voxels = [(int(d), int((z * ny + y) * nx + x), float(conc[d, z, y, x])) for d, z, y, x in pick]
     s0 = float(sc["medium"]["sigma_s"])
+    hs = 1e-3 * s0
     K = 8
     m = n // K
     fd = np.zeros((K, 65))
     ad = np.zeros((K, 65))
+    abs_sum = np.zeros(K)
+    heavy = None
     for k in range(K):
         gc = torch.zeros(S.conc_t.shape, dtype=torch.float32, device="cuda")
         gs = torch.zeros(1, dtype=torch.float32, device="cuda")
@@ -264,19 +275,41 @@ def test_cfg4_gradient_against_frozen_central_differences_on_64_voxels():
             sm = S.frozen_sums(adj, (d, v, -h, 0.0), n_paths=m, path_offset=k * m, majorant_margin=mg)
             fd[k, j] = float((sp - sm).sum()) / (2 * h)
             ad[k, j] = g[d, v]
-        h = 1e-3 * s0
-        sp = S.frozen_sums(adj, (-1, 0, 0.0, h), n_paths=m, path_offset=k * m, majorant_margin=mg)
-        sm = S.frozen_sums(adj, (-1, 0, 0.0, -h), n_paths=m, path_offset=k * m, majorant_margin=mg)
-        fd[k, 64] = float((sp - sm).sum()) / (2 * h)
+
+        def cdiff(h):
+            sp = S.frozen_sums(adj, (-1, 0, 0.0, h), n_paths=m, path_offset=k * m, majorant_margin=mg)
+            sm = S.frozen_sums(adj, (-1, 0, 0.0, -h), n_paths=m, path_offset=k * m, majorant_margin=mg)
+            return (sp - sm) / (2 * h)
+        d1, d2 = cdiff(hs), cdiff(hs / 2)
+        per_path = (4.0 * d2 - d1) / 3.0
+        fd[k, 64] = float(per_path.sum())
         ad[k, 64] = float(gs.item())
+        abs_sum[k] = float(per_path.abs().sum())
+        if k == 0:
+            heavy = torch.argsort(per_path.abs(), descending=True)[:16].cpu().numpy()
     assert S.status() == N.FLR_OK
     ma, sa = batch_mean_se(ad)
     md, sd = batch_mean_se(fd - ad)
     scale = np.abs(ma[:64]).max()
     tol = np.maximum(3 * sd, 1e-2 * np.abs(ma))
     tol[:64] += 1e-6 * scale
+    tol[64] = max(tol[64], 1e-3 * abs_sum.mean())
     bad = np.where(np.abs(md) > tol)[0]
-    assert bad.size == 0, [(int(j), ma[j], md[j], sd[j]) for j in bad]
+    assert bad.size == 0, [(int(j), ma[j], md[j], sd[j], tol[j]) for j in bad]
     # the check has teeth: most of the 64 voxel gradients and the sigma_s gradient are resolved
     assert int((np.abs(ma[:64]) > 3 * sa[:64]).sum()) >= 32
     assert abs(ma[64]) > 3 * sa[64]
+    # the heaviest paths one by one (a one-path launch: both sides scale by 1 instead of 1/m)
+    gc1 = torch.zeros(S.conc_t.shape, dtype=torch.float32, device="cuda")
+    gs1 = torch.zeros(1, dtype=torch.float32, device="cuda")
+    for i in heavy:
+        i = int(i)
+        S.adjoint(adj, gc1, gs1, n_paths=1, path_offset=i, majorant_margin=mg, form="plain")
+        a1 = float(gs1.item())
+        one = []
+        for h in (hs, hs / 2):
+            sp = float(S.frozen_sums(adj, (-1, 0, 0.0, h), n_paths=1, path_offset=i, majorant_margin=mg)[0])
+            sm = float(S.frozen_sums(adj, (-1, 0, 0.0, -h), n_paths=1, path_offset=i, majorant_margin=mg)[0])
+            one.append((sp - sm) / (2 * h))
+        f1 = (4.0 * one[1] - one[0]) / 3.0
+        assert abs(f1 - a1) <= 2e-3 * abs(a1) + 1e-12, (i, f1, a1)

@@ -129,3 +129,34 @@ def test_batch_rejects_bad_media():
     with pytest.raises(N.FluoroError) as e:
         Batch(media)
     assert e.value.code == N.FLR_ERR_ARG
+
+
+def test_batch_per_bin_parity_with_the_oracle():
+    """Four media of the batched workload, each traced by the batch and by the oracle over 16 batches
+    of the same path ids (the batch draws medium m's numbers under medium id m): per-bin parity of
+    the face, absorbed and emitted tallies by batch means (at most 1 % of populated bins beyond
+    |z| = 3, none beyond 5.5), the same-seed integrated tallies within 0.5 %, and every path's tally
+    in the same medium as the single-scene kernel's."""
+    from tests.gpu_common import bin_parity, paired_integrated
+    media = sg.cfg3_batched_media(n_media=4, seed=6, max_edge=24)
+    K, n = 16, 2000
+    for sc in media:
+        sc["params"]["n_paths"] = n
+    g = {m: [] for m in range(len(media))}
+    for k in range(K):
+        bt = Batch(media, seed=0, medium_id=0, path_offset=k * n)
+        bt.launch()
+        out = bt.read()
+        for m, sc in enumerate(media):
+            D = sc["dyes"]["eps"].shape[0]
+            g[m].append({"face": out["face"][m], "absorbed": out["absorbed"][m, :D + 1],
+                         "emitted": out["emitted"][m, :D]})
+        bt.close()
+    for m, sc in enumerate(media):
+        o = [oracle.render(sc, n_paths=n, path_offset=k * n, medium_id=m, seed=0, film=False)
+             for k in range(K)]
+        for key in ("face", "absorbed", "emitted"):
+            v = bin_parity(g[m], o, key)
+            assert v["ok"], (m, key, v)
+            ok, worst, _, info = paired_integrated(g[m], o, key)
+            assert ok, (m, key, worst, info)

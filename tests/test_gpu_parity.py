@@ -18,9 +18,9 @@ import oracle
 import scenegen as sg
 from paper_1706_03024_gb300 import native as N
 from paper_1706_03024_gb300.scene import Scene
-from tests.gpu_common import (bin_parity, compare_integrated, gpu_batches,
-                              integrated_independent, oracle_batches, paired_integrated,
-                              require_gpu, totals)
+from tests.gpu_common import (bin_parity, check_workload as _check_workload,
+                              compare_integrated, gpu_batches, integrated_independent,
+                              oracle_batches, paired_integrated, require_gpu, totals)
 
 pytestmark = pytest.mark.gpu
 
@@ -80,66 +80,12 @@ def test_emission_bins_bitwise_against_oracle():
 # Statistical parity on the workloads
 
 
-def _check_workload(sc, K, n_per, forms=("plain",), film_min_nonzero=None, path_id_frac=0.99,
-                    launch=None, **kw):
-    """kw: estimator settings both sides take; launch: GPU launch shape (block size, regroup)."""
-    launch = launch or {}
-    o = oracle_batches(sc, K, n_per, path_events=True, **kw)
-    o_events = np.concatenate([x["path_events"] for x in o])
-    S = Scene(sc)
-    results = {}
-    for form in forms:
-        pe = torch.zeros(K * n_per, dtype=torch.int32, device="cuda")
-        g = []
-        for k in range(K):
-            f = S.render(n_paths=n_per, path_offset=k * n_per, form=form,
-                         path_events=pe[k * n_per:(k + 1) * n_per], **launch, **kw)
-            r = S.read()
-            r["film"] = f.double().cpu().numpy() if f is not None else None
-            g.append(r)
-        g_events = pe.cpu().numpy().astype(np.uint32)
-        same = float((g_events == o_events).mean())
-        assert same >= path_id_frac, (form, same)
-        for key in ("face", "absorbed", "emitted"):
-            v = bin_parity(g, o, key)
-            assert v["ok"], (form, key, v)
-            worst = compare_integrated(totals(g, key).sum(axis=-1), totals(o, key).sum(axis=-1))
-            assert worst <= 5e-3, (form, key, worst)
-        if sc["sensor"]["kind"] != "none":
-            v = bin_parity(g, o, "film", film_min_nonzero)
-            assert v["ok"], (form, "film", v)
-            gf, of = totals(g, "film"), totals(o, "film")
-            assert abs(gf.sum() - of.sum()) <= 5e-3 * of.sum() + 4 * np.sqrt(
-                np.var([x["film"].sum() for x in g]) / K + np.var([x["film"].sum() for x in o]) / K)
-        c = g[-1]["counters"]
-        for name in ("majorant_violations", "nonfinite", "connect_budget", "step_budget"):
-            assert c[name] == 0, (form, name, c[name])
-        results[form] = g
-        # independent seed: the full statistical criteria
-        seed2 = int(sc["params"]["seed"]) + 1000
-        gi = []
-        for k in range(K):
-            f = S.render(n_paths=n_per, path_offset=k * n_per, form=form, seed=seed2, **launch,
-                         **kw)
-            r = S.read()
-            r["film"] = f.double().cpu().numpy() if f is not None else None
-            gi.append(r)
-        for key in ("face", "absorbed", "emitted"):
-            v = bin_parity(gi, o, key, same_seed=False)
-            assert v["ok"], (form, "independent", key, v)
-            ok, info = integrated_independent(gi, o, key)
-            assert ok, (form, "independent", key, info)
-        if sc["sensor"]["kind"] != "none":
-            v = bin_parity(gi, o, "film", film_min_nonzero, same_seed=False)
-            assert v["ok"], (form, "independent", "film", v)
-    return results
-
-
 def test_cfg1_homogeneous_cube_parity():
     sc = sg.cfg1_homogeneous_cube(n_paths=100_000)
-    res = _check_workload(sc, 32, 100_000 // 32, forms=("plain", "wavefront", "wavefront_warp"))
+    res = _check_workload(sc, 32, 100_000 // 32,
+                          forms=("plain", "wavefront", "wavefront_warp", "wavefront_pool"))
     # every launch form traces the same paths: fixed-point tallies bit-identical
-    for other in ("wavefront", "wavefront_warp"):
+    for other in ("wavefront", "wavefront_warp", "wavefront_pool"):
         for a, b in zip(res["plain"], res[other]):
             for key in ("face", "absorbed", "emitted"):
                 assert np.array_equal(a[key], b[key]), (other, key)
@@ -179,6 +125,40 @@ def test_cfg2_benchmarked_launch_shape_reduced_parity():
     sc = sg.cfg2_cornell_box(width=48, height=48, grid=48, n_paths=1)
     _check_workload(sc, 32, 6000, forms=("wavefront_warp",), path_id_frac=0.95, skip_cell=1,
                     launch={"block_size": 128, "regroup": 1})
+
+
+def test_cfg2_pool_form_parity_and_equality_with_the_warp_form():
+    """The path-pool form (regrouping by event type) on the reduced Cornell box with empty-space
+    leaps: the oracle's criteria, and the same fixed-point tallies as the warp form, batch by
+    batch."""
+    sc = sg.cfg2_cornell_box(width=48, height=48, grid=48, n_paths=1)
+    res = _check_workload(sc, 32, 6000, forms=("wavefront_warp", "wavefront_pool"),
+                          path_id_frac=0.95, skip_cell=1, launch={"block_size": 128, "regroup": 1})
+    for a, b in zip(res["wavefront_warp"], res["wavefront_pool"]):
+        for key in ("face", "absorbed", "emitted"):
+            assert np.array_equal(a[key], b[key]), key
+        assert dict(a["counters"]) == dict(b["counters"])
+        assert np.allclose(a["film"], b["film"], rtol=1e-5, atol=1e-7 * a["film"].max())
+
+
+def test_pool_form_at_full_size_equals_the_warp_form():
+    """All 4,194,304 Cornell-box paths: the pool form's fixed-point tallies and per-path event
+    counts equal the benchmarked warp form's bit for bit, and the films agree up to the order of
+    the fp32 film atomics."""
+    sc = sg.cfg2_cornell_box()
+    n = sc["params"]["n_paths"]
+    S = Scene(sc)
+    out = {}
+    for form in ("wavefront_warp", "wavefront_pool"):
+        pe = torch.zeros(n, dtype=torch.int32, device="cuda")
+        f = S.render(form=form, block_size=128, regroup=1, skip_cell=1, path_events=pe).clone()
+        out[form] = (S.read(), pe.cpu().numpy(), f)
+    a, b = out["wavefront_warp"], out["wavefront_pool"]
+    for key in ("face", "absorbed", "emitted"):
+        assert np.array_equal(a[0][key], b[0][key]), key
+    assert a[0]["counters"] == b[0]["counters"]
+    assert np.array_equal(a[1], b[1])
+    assert torch.allclose(a[2], b[2], rtol=1e-4, atol=1e-6 * float(a[2].max()))
 
 
 def test_cfg5_macro_cell_parity():

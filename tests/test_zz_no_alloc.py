@@ -52,6 +52,9 @@ def _noalloc(sc, conc_t, solv_t, n_paths, form, film, **over):
     m.sigma_a0 = md["sigma_a0"]
     m.wall_mask = md["wall_mask"]
     m.wall_albedo = md["wall_albedo"]
+    m.ior = md.get("ior", 1.0)
+    m.wall_gloss = md.get("wall_gloss", 0.0)
+    m.wall_exponent = md.get("wall_exponent", 0.0)
     srcs = (N.flr_source * len(sc["sources"]))(*[make_source(s) for s in sc["sources"]])
     p = N.flr_params()
     p.n_paths = n_paths
