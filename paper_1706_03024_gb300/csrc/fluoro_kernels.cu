@@ -2419,16 +2419,16 @@ __global__ void __launch_bounds__(WARP_BLOCK, (MODE == WM_RENDER && !MC) ? 5 : 4
         const bool any = __any_sync(FULL, p.alive || !exhausted);
         const int avail = q.head_tail[1];
         if (avail >= WQ_DRAIN || (!any && avail > 0)) {
-            // pull-based drain of all `avail` records
-            // Lanes claim new records only every second iteration: claims in step keep the lanes'
-            // Philox draws (one per four march steps) in two phases instead of four, and the
-            // set-up of new marches runs for several lanes at once (measured: every iteration
-            // 25.8, every second 25.2, every fourth 26.0 ms per step with 128-record queues).
+            // pull-based drain of all `avail` records; a lane whose march ended claims the next
+            // record in the next iteration (measured with the march streams: 13.14 ms per
+            // Cornell-box step and 33.3 ms per 8.4M light-sheet paths, against 13.28 / 35.5 ms
+            // claiming every second iteration, 13.70 / 36.3 every third and 14.20 / 37.1 every
+            // fourth; every second had been fastest while marches drew Philox blocks by phase)
             March mc;
             bool active = false;
             int claimed = 0;
-            for (uint32_t iter = 0;; ++iter) {
-                const unsigned need = (iter & 1u) == 0u ? __ballot_sync(FULL, !active) : 0u;
+            for (;;) {
+                const unsigned need = __ballot_sync(FULL, !active);
                 if (need != 0u && !active) {
                     const int k = claimed + __popc(need & lower);
                     if (k < avail) {
@@ -2903,8 +2903,8 @@ __global__ void __launch_bounds__(WARP_BLOCK, 5) k_trace_pool(SceneDev S, RunDev
             March mc;
             bool active = false;
             int claimed = 0;
-            for (uint32_t iter = 0;; ++iter) {
-                const unsigned need = (iter & 1u) == 0u ? __ballot_sync(FULL, !active) : 0u;
+            for (;;) {
+                const unsigned need = __ballot_sync(FULL, !active);
                 if (need != 0u && !active) {
                     const int k = claimed + __popc(need & lower);
                     if (k < avail) {
@@ -3171,8 +3171,8 @@ __global__ void __launch_bounds__(WARP_BLOCK, 4) k_trace_hero_warp(SceneDev S, R
             HMarch hm;
             bool active = false;
             int claimed = 0;
-            for (uint32_t iter = 0;; ++iter) {
-                const unsigned need = (iter & 1u) == 0u ? __ballot_sync(FULL, !active) : 0u;
+            for (;;) {
+                const unsigned need = __ballot_sync(FULL, !active);
                 if (need != 0u && !active) {
                     const int k = claimed + __popc(need & lower);
                     if (k < avail) active = hero_march_begin(S, R, sm, q, k, hm, rc);
@@ -3594,8 +3594,8 @@ __global__ void __launch_bounds__(256, 2) k_trace_camera_warp(SceneDev S, RunDev
             MarchRng rg{0u, 0u, 0u, 0u};
             bool active = false;
             int claimed = 0;
-            for (uint32_t iter = 0;; ++iter) {
-                const unsigned need = (iter & 1u) == 0u ? __ballot_sync(FULL, !active) : 0u;
+            for (;;) {
+                const unsigned need = __ballot_sync(FULL, !active);
                 if (need != 0u && !active) {
                     const int k = claimed + __popc(need & lower);
                     if (k < avail) {
