@@ -594,9 +594,14 @@ def run_ours(args):
                      "best_events_per_s_on_slice": max(v for _, v in res.trials)}
 
     def one_step(form):
-        # the plain kernel is the baseline: one thread per path, one majorant per bin
+        # the plain kernel is the baseline: one thread per path, one majorant per bin; with the
+        # tuned form's empty-space leaps or local majorants it separates their share of the
+        # speed-up from the regrouping's
         if form == "plain":
             S.render(form="plain", path_offset=offset)
+        elif form == "plain_leaps":
+            S.render(form="plain", path_offset=offset, skip_cell=tuned["skip_cell"],
+                     macro_cell=tuned["macro_cell"])
         else:
             S.render(path_offset=offset, **tuned)
 
@@ -638,6 +643,8 @@ def run_ours(args):
     ms_w, ev_w, cnt_w, clocks = timed("wavefront", args.steps,
                                       os.path.join(clock_dir, f"clocks_rank{rank}.csv"))
     ms_p, ev_p, cnt_p, _ = timed("plain", max(1, min(args.steps, args.plain_steps)))
+    one_step("plain_leaps")
+    ms_pl, ev_pl, _, _ = timed("plain_leaps", max(1, min(args.steps, args.plain_steps)))
     step_ms_w_local = sum(ms_w) / len(ms_w)
 
     # equal-RMSE check: each form's one-step film against a 16x-path reference (independent seed)
@@ -704,6 +711,8 @@ def run_ours(args):
     total_ev_p = reduce_sum(float(ev_p))
     value = total_ev_w / (step_ms_w / 1000.0)
     plain_value = total_ev_p / (step_ms_p / 1000.0)
+    step_ms_pl = reduce_max(sum(ms_pl) / len(ms_pl))
+    plain_leaps_value = reduce_sum(float(ev_pl)) / (step_ms_pl / 1000.0)
     paths_per_s = reduce_sum(float(n_paths)) / (step_ms_w / 1000.0)
 
     # --- batched persistent form: 256 media in one launch (CUDA graph) ----------------------
@@ -805,7 +814,13 @@ def run_ours(args):
                               "ms_steps": [round(v, 3) for v in ms_w]},
                 "plain": {"events_per_s": plain_value, "ms_per_step": step_ms_p,
                           "steps": len(ms_p), "ms_steps": [round(v, 3) for v in ms_p]},
+                "plain_leaps": {"events_per_s": plain_leaps_value, "ms_per_step": step_ms_pl,
+                                "steps": len(ms_pl), "ms_steps": [round(v, 3) for v in ms_pl],
+                                "launch": {"skip_cell": tuned["skip_cell"],
+                                           "macro_cell": tuned["macro_cell"]}},
                 "speedup_vs_plain": value / plain_value,
+                "speedup_from_leaps": plain_leaps_value / plain_value,
+                "speedup_from_regrouping": value / plain_leaps_value,
                 "equal_rmse": "same estimator and path ids; film RMSE against a 16x-path reference"
                               " in `rmse` (the local majorants of the wavefront form also lower the"
                               " transmittance estimate's variance)",
@@ -824,7 +839,7 @@ def run_ours(args):
             "film_atomics": film_atomics,
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": 2 * args.steps + len(ms_p)
+            "gpu_launches": 2 * args.steps + len(ms_p) + len(ms_pl)
             + (0 if batched is None else batched["steps"] + batched["plain_launches"])
             + (0 if adjoint is None else adjoint["launches_per_step"] * args.adjoint_steps)
             + (0 if paper is None else 2 * args.paper_steps)
