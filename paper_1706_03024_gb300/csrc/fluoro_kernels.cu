@@ -22,6 +22,7 @@
 // 24-bit: u = (x >> 8) 2^-24.
 #include <cfloat>
 #include <cstdint>
+#include <type_traits>
 
 #include "fluoro_internal.cuh"
 
@@ -188,9 +189,11 @@ __device__ __forceinline__ void tally_add(const Smem &sm, int idx, float w)
 // MC = false compiles the local-majorant path alone out (launched whenever the scene has none:
 // the smaller code keeps the warp-regrouped kernel's loops in the instruction cache); IF = false
 // compiles dielectric faces and glossy walls out (scenes with index-matched faces and Lambertian
-// walls).
-template <bool OPT, bool MC = OPT, bool IF = true>
+// walls). LZ = true compiles in the decisions taken without a grid read (minorant_known; launched
+// for media with grids and no solvent mask).
+template <bool OPT, bool MC = OPT, bool IF = true, bool LZ = false>
 struct MedS_ {
+    static constexpr bool kLazy = LZ;
     const SceneDev &S;
     const Smem &sm;
     __device__ __forceinline__ int B() const { return S.B; }
@@ -270,6 +273,7 @@ __device__ __forceinline__ void tally_add_global(unsigned long long *t, int idx,
 }
 
 struct MedB {
+    static constexpr bool kLazy = false;
     const MediumDev *__restrict__ md;
     int B_;
     __device__ __forceinline__ int B() const { return B_; }
@@ -793,7 +797,7 @@ struct NoSink {
     __device__ __forceinline__ void homogeneous(float) const {}
 };
 
-template <class G, bool OPT = true, bool MC = OPT, bool ADJ = false, uint32_t SLOT0 = 2u>
+template <class G, bool OPT = true, bool MC = OPT, bool ADJ = false, uint32_t SLOT0 = 2u, bool LZ = false>
 __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &R, const Smem &sm,
                                                float3 x, float3 dir, float tl, int b, uint64_t pid,
                                                uint32_t step, RegCnt &rc, const G &sink)
@@ -842,11 +846,25 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
     float t = 0.0f;
     MarchRng rg = march_rng(R, pid, step, SLOT0);
     int it = 0;
+    constexpr bool LAZY = LZ && !ADJ && std::is_same<G, NoSink>::value;
     for (; it < MAX_CONNECT_STEPS; ++it) {
         const float u = march_next(rg);
         t -= __logf(1.0f - u) * isb;
         if (t >= tl) break;
         rc.connect_steps++;
+        float u2 = -1.0f;   // the roulette coin, when the bound below draws it first
+        if (LAZY && !S.homogeneous && S.solvent == nullptr) {
+            // a coin that fails against the bound of the updated estimate ends the march
+            // whatever sigma_t is here (minorant_known)
+            const float tu = T * fmaxf(0.0f, 1.0f - (S.sigma_s + S.sigma_a0) * isb);
+            if (tu < RT_RR_THRESHOLD) {
+                u2 = march_next(rg);
+                if (!(u2 * RT_RR_THRESHOLD < tu)) {
+                    T = 0.0f;
+                    break;
+                }
+            }
+        }
         const float3 p = make_float3(x.x + t * dir.x, x.y + t * dir.y, x.z + t * dir.z);
         const float st = sigma_t_at(m, p, b);
         sink.point(p, b, st, sb);
@@ -860,7 +878,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
             }
         }
         if (T < (ADJ ? RT_RR_ADJ_THRESHOLD : RT_RR_THRESHOLD)) {
-            const float u2 = march_next(rg);
+            if (u2 < 0.0f) u2 = march_next(rg);
             if (ADJ ? u2 < 0.5f : u2 * RT_RR_THRESHOLD < T) {
                 T = ADJ ? 2.0f * T : RT_RR_THRESHOLD;
             } else {
@@ -878,7 +896,7 @@ __device__ __forceinline__ float transmittance(const SceneDev &S, const RunDev &
 
 // Sensor connection (Eq. 3-6). `lamb` < 0: isotropic vertex, intensity w/(4 pi); otherwise a
 // Lambertian vertex with normal sign*e_axis (lamb = 2*axis + (sign > 0)), intensity w cos/pi.
-template <bool OPT = true>
+template <bool OPT = true, bool LZ = false>
 __device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, const Smem &sm,
                                         float3 x, int b, float w, int lamb, uint64_t pid,
                                         uint32_t step, RegCnt &rc)
@@ -886,7 +904,8 @@ __device__ __forceinline__ void connect(const SceneDev &S, const RunDev &R, cons
     const ConnGeom g = connect_geom(S, sm, x, lamb);
     if (!g.ok) return;
     rc.connections++;
-    const float T = transmittance<NoSink, OPT>(S, R, sm, x, g.dir, g.tl, b, pid, step, rc, NoSink{});
+    const float T = transmittance<NoSink, OPT, OPT, false, 2u, LZ>(S, R, sm, x, g.dir, g.tl, b, pid, step, rc,
+                                                                 NoSink{});
     const float val = w * g.gf * T * R.film_scale;
     if (val > 0.0f) film_add(S, R, (size_t)g.pix * S.B + b, val);
 }
@@ -984,6 +1003,22 @@ __device__ __forceinline__ Conn spawn(const M &m, const RunDev &R, const Smem &s
     }
     p.iw = inv_dir(p.w);
     return c;
+}
+
+// Decisions that need no grid read. Where a medium has grids but no solvent mask (s(x) = 1), every
+// point has sigma_t >= sigma_s + sigma_a0 (the dye terms are >= 0) and sigma_t <= sigma_bar. So a
+// tentative collision with u_real sigma_bar < sigma_s + sigma_a0 is real, and then a scatter if
+// u_event sigma_bar < sigma_s, whatever the concentrations there; and a ratio-tracking step whose
+// roulette coin fails against T (1 - (sigma_s + sigma_a0) / sigma_bar), an upper bound of the
+// updated estimate, ends its march whatever they are. The bounds are formed with the operations
+// coeffs_at and the march use (fp32 rounding is monotone), so a decision taken from them is the
+// one the grid read would give: the same paths, tallies and film, fewer reads. In the dense
+// scattering media of high albedo most decisions are of this kind. Forward passes only: the
+// adjoint's observers need the coefficients at every point.
+template <class M>
+__device__ __forceinline__ bool minorant_known(const M &m)
+{
+    return M::kLazy && !m.homogeneous() && m.solvent() == nullptr;
 }
 
 // Observer of the tracking decisions (the adjoint replay scores them); NoObs is the forward's.
@@ -1105,43 +1140,51 @@ __device__ __forceinline__ Conn track_step(const M &m, const RunDev &R, const Sm
         }
     } else {
         p.x = make_float3(p.x.x + tf * p.w.x, p.x.y + tf * p.w.y, p.x.z + tf * p.w.z);
-        // the empty-space distance is read beside the coefficients, not after them
-        const int4 ec = m.skip() ? empty_cell(m, p.x) : make_int4(0, 0, 0, 0);
-        const Coeffs k = coeffs_at(m, p.x, p.bin);
-        if (k.total > sb) cnt_add(sm, FLR_C_MAJORANT_VIOLATIONS);
-        if (!(b0.b * sb < k.total)) {
-            rc.nulls++;
-            obs.null_event(p.x, p.bin, k, sb);
-            if (m.skip() && k.total == 0.0f) {
-                // every tentative collision in the empty cube around here would be a null: leave it
-                float tl = empty_cube_exit_at(m, ec, p.x, p.w, p.iw);
-                if (tl > 0.0f) {
-                    tl = fminf(tl, te - tf);
-                    p.x = make_float3(p.x.x + tl * p.w.x, p.x.y + tl * p.w.y, p.x.z + tl * p.w.z);
-                    rc.cell_walks++;
+        // a real scatter whatever the concentrations (minorant_known): no grid read
+        const bool sure = std::is_same<Obs, NoObs>::value && minorant_known(m) &&
+                          b0.b * sb < m.sigma_s() + m.sigma_a0() && b0.c * sb < m.sigma_s();
+        Coeffs k;
+        if (!sure) {
+            // the empty-space distance is read beside the coefficients, not after them
+            const int4 ec = m.skip() ? empty_cell(m, p.x) : make_int4(0, 0, 0, 0);
+            k = coeffs_at(m, p.x, p.bin);
+            if (k.total > sb) cnt_add(sm, FLR_C_MAJORANT_VIOLATIONS);
+            if (!(b0.b * sb < k.total)) {
+                rc.nulls++;
+                obs.null_event(p.x, p.bin, k, sb);
+                if (m.skip() && k.total == 0.0f) {
+                    // every tentative collision in the empty cube around here would be a null: leave it
+                    float tl = empty_cube_exit_at(m, ec, p.x, p.w, p.iw);
+                    if (tl > 0.0f) {
+                        tl = fminf(tl, te - tf);
+                        p.x = make_float3(p.x.x + tl * p.w.x, p.x.y + tl * p.w.y, p.x.z + tl * p.w.z);
+                        rc.cell_walks++;
+                    }
                 }
+                return c;
             }
-            return c;
         }
         if (p.n_events == R.max_events) { cnt_add(sm, FLR_C_CAP_HITS); finish(R, p); return c; }
         p.n_events++;
         rc.events++;
         // particle type in proportion to its coefficient (Sec. 4.1)
-        const float ue = b0.c * k.total;
-        float acc = k.scat;
         int ev = -1;
         const int D = m.D();
-        if (!(ue < acc)) {
-            ev = D;
+        if (!sure) {
+            const float ue = b0.c * k.total;
+            float acc = k.scat;
+            if (!(ue < acc)) {
+                ev = D;
 #pragma unroll
-            for (int d = 0; d < MAXD; ++d) {
-                if (d < D && ev == D) {
-                    acc += k.dye[d];
-                    if (ue < acc) ev = d;
+                for (int d = 0; d < MAXD; ++d) {
+                    if (d < D && ev == D) {
+                        acc += k.dye[d];
+                        if (ue < acc) ev = d;
+                    }
                 }
             }
+            obs.real_event(p.x, p.bin, k, ev);
         }
-        obs.real_event(p.x, p.bin, k, ev);
         if (ev < 0) {
             rc.scatters++;
             // the paper's model drops scattered excitation light (Sec. 4.1)
@@ -1316,22 +1359,22 @@ __device__ __forceinline__ void block_epilogue(const SceneDev &S, const RunDev &
 
 // ---------------------------------------------------------------------------------------------
 // Plain form: one thread per path, grid-stride over path ids, connections made inline.
-template <bool OPT, bool IF>
+template <bool OPT, bool IF, bool LZ = false>
 __global__ void __launch_bounds__(256) k_trace_plain(SceneDev S, RunDev R)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
     const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
-    const MedS_<OPT, OPT, IF> m{S, sm};
+    const MedS_<OPT, OPT, IF, LZ> m{S, sm};
     RegCnt rc = {0, 0, 0, 0, 0, 0, 0};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_paths; i += stride) {
         Path p;
         Conn c = spawn(m, R, sm, R.path_offset + i, p);
-        if (c.valid) connect<OPT>(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
+        if (c.valid) connect<OPT, LZ>(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
         while (p.alive) {
             c = track_step(m, R, sm, p, rc);
-            if (c.valid) connect<OPT>(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
+            if (c.valid) connect<OPT, LZ>(S, R, sm, c.x, c.bin, c.w, c.lamb, c.pid, c.step, rc);
         }
     }
     block_epilogue(S, R, sm, rc);
@@ -2277,7 +2320,7 @@ __device__ __forceinline__ bool march_begin(const SceneDev &S, const RunDev &R, 
 __device__ __forceinline__ float march_uniform(const RunDev &, March &mc) { return march_next(mc.g); }
 
 // One ratio-tracking step (the body of transmittance()'s loop); returns false when the march ends.
-template <int MODE>
+template <int MODE, bool LZ = false>
 __device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, const Smem &sm,
                                            const AdjDev &A, March &mc, RegCnt &rc, float &gsig)
 {
@@ -2294,6 +2337,16 @@ __device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, c
     }
     rc.connect_steps++;
     const MedS m{S, sm};
+    float u2 = -1.0f;   // the roulette coin, when the bound below draws it first
+    if (MODE == WM_RENDER && LZ && !S.homogeneous && S.solvent == nullptr) {
+        // upper bound of the updated estimate (minorant_known): a coin that fails against it ends
+        // the march whatever sigma_t is here
+        const float tu = mc.T * fmaxf(0.0f, 1.0f - (S.sigma_s + S.sigma_a0) * mc.isb);
+        if (tu < RT_RR_THRESHOLD) {
+            u2 = march_uniform(R, mc);
+            if (!(u2 * RT_RR_THRESHOLD < tu)) return false;
+        }
+    }
     const float3 p = make_float3(mc.x.x + mc.t * mc.dir.x, mc.x.y + mc.t * mc.dir.y,
                                  mc.x.z + mc.t * mc.dir.z);
     const int4 ec = S.sk > 0 ? empty_cell(m, p) : make_int4(0, 0, 0, 0);
@@ -2309,7 +2362,7 @@ __device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, c
     }
     constexpr bool ADJ = MODE != WM_RENDER;
     if (mc.T < (ADJ ? RT_RR_ADJ_THRESHOLD : RT_RR_THRESHOLD)) {
-        const float u2 = march_uniform(R, mc);
+        if (u2 < 0.0f) u2 = march_uniform(R, mc);
         if (ADJ ? u2 < 0.5f : u2 * RT_RR_THRESHOLD < mc.T) {
             mc.T = ADJ ? 2.0f * mc.T : RT_RR_THRESHOLD;
         } else {
@@ -2319,13 +2372,13 @@ __device__ __forceinline__ bool march_step(const SceneDev &S, const RunDev &R, c
     return true;
 }
 
-template <int MODE, bool MC, bool IF = true>
+template <int MODE, bool MC, bool IF = true, bool LZ = false>
 __global__ void __launch_bounds__(WARP_BLOCK, (MODE == WM_RENDER && !MC) ? 5 : 4) k_trace_wavefront_warp(SceneDev S, RunDev R, AdjDev A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(S.B, FLR_FORM_WAVEFRONT_WARP, blockDim.x);
     const Smem sm = block_prologue(S, smem_raw, L, R.tallies);
-    const MedS_<true, MC, IF> m{S, sm};
+    const MedS_<true, MC, IF, LZ> m{S, sm};
     constexpr unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
@@ -2442,7 +2495,7 @@ __global__ void __launch_bounds__(WARP_BLOCK, (MODE == WM_RENDER && !MC) ? 5 : 4
                     }
                 }
                 claimed += __popc(need);
-                if (active) active = march_step<MODE>(S, R, sm, A, mc, rc, gsig);
+                if (active) active = march_step<MODE, LZ>(S, R, sm, A, mc, rc, gsig);
                 if (!__any_sync(FULL, active) && claimed >= avail) break;
             }
             __syncwarp();
@@ -3975,7 +4028,7 @@ cudaError_t allow_smem(int form, int smem)
     if (form == FLR_FORM_WAVEFRONT_WARP) {
         void (*const ks[])(SceneDev, RunDev, AdjDev) = {
             k_trace_wavefront_warp<WM_RENDER, false, false>, k_trace_wavefront_warp<WM_RENDER, false, true>,
-            k_trace_wavefront_warp<WM_RENDER, true>,
+            k_trace_wavefront_warp<WM_RENDER, false, false, true>, k_trace_wavefront_warp<WM_RENDER, true>,
             k_trace_wavefront_warp<WM_ADJ_WEIGHTS, false>, k_trace_wavefront_warp<WM_ADJ_WEIGHTS, true>,
             k_trace_wavefront_warp<WM_ADJ_GRAD, false>, k_trace_wavefront_warp<WM_ADJ_GRAD, true>};
         for (auto k : ks) {
@@ -3985,7 +4038,7 @@ cudaError_t allow_smem(int form, int smem)
         return cudaSuccess;
     }
     void (*const kp[])(SceneDev, RunDev) = {k_trace_plain<true, true>, k_trace_plain<false, true>,
-                                             k_trace_plain<false, false>};
+                                             k_trace_plain<false, false>, k_trace_plain<false, false, true>};
     for (auto k : kp) {
         const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -4041,6 +4094,9 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
         if (need < grid) grid = need;
     }
     if (grid < 1) grid = 1;
+    // media with grids and no solvent mask: the instances with the decisions taken without a grid
+    // read (minorant_known)
+    const bool lazy = !S.homogeneous && S.solvent == nullptr;
     if (form == FLR_FORM_WAVEFRONT)
         k_trace_wavefront<<<(unsigned)grid, block, smem, st>>>(S, R);
     else if (form == FLR_FORM_WAVEFRONT_WARP)
@@ -4049,6 +4105,8 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
             k_trace_wavefront_warp<WM_RENDER, true><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
         else if (S.iface)
             k_trace_wavefront_warp<WM_RENDER, false, true><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
+        else if (lazy)
+            k_trace_wavefront_warp<WM_RENDER, false, false, true><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
         else
             k_trace_wavefront_warp<WM_RENDER, false, false><<<(unsigned)grid, block, smem, st>>>(S, R, AdjDev{});
     }
@@ -4058,6 +4116,8 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
         k_trace_plain<true, true><<<(unsigned)grid, block, smem, st>>>(S, R);
     else if (S.iface)
         k_trace_plain<false, true><<<(unsigned)grid, block, smem, st>>>(S, R);
+    else if (lazy)
+        k_trace_plain<false, false, true><<<(unsigned)grid, block, smem, st>>>(S, R);
     else
         k_trace_plain<false, false><<<(unsigned)grid, block, smem, st>>>(S, R);
     return cudaGetLastError();

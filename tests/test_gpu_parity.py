@@ -173,9 +173,43 @@ def test_cfg4_blobby_grid_ortho_parity():
 
 
 def test_cfg5_light_sheet_reduced_parity():
+    """The light sheet (grids, no solvent mask): the plain and warp forms run the instances that
+    take decisions without a grid read where the bounds settle them; the block form does not."""
     sc = sg.cfg5_light_sheet(grid=32, width=32, height=32, n_blobs=40, n_paths=1,
                              sigma_t_ref=20.0)
-    _check_workload(sc, 32, 1500, forms=("wavefront",), path_id_frac=0.95)
+    _check_workload(sc, 32, 1500, forms=("wavefront", "plain", "wavefront_warp"), path_id_frac=0.95,
+                    launch={"block_size": 128, "regroup": 1})
+
+
+@pytest.mark.parametrize("albedo", [0.999, 0.6])
+def test_decisions_without_grid_reads_change_nothing(albedo):
+    """A medium without a solvent mask runs the kernel instances that skip the grid read when a
+    bound settles the decision (a sure scatter; a march whose roulette coin fails against the bound
+    of its estimate). The same medium with an all-ones mask has the same coefficients at every
+    point and runs the instances that always read: the fixed-point tallies, counters and path
+    events must be identical bit for bit, the film equal up to fp32 atomic order."""
+    sc = sg.cfg5_light_sheet(grid=48, width=48, height=48, n_blobs=60, n_paths=1, albedo=albedo)
+    masked = dict(sc)
+    med = dict(sc["medium"])
+    nz, ny, nx = med["conc"].shape[1:]
+    med["solvent"] = np.ones((nz, ny, nx), dtype=np.uint8)
+    masked["medium"] = med
+    n = 40_000
+    for form in ("plain", "wavefront_warp"):
+        out = []
+        for scene in (sc, masked):
+            S = Scene(scene)
+            pe = torch.zeros(n, dtype=torch.int32, device="cuda")
+            f = S.render(n_paths=n, form=form, path_events=pe, block_size=128, regroup=1)
+            out.append((S.read(), f.clone(), pe.cpu().numpy()))
+            S.close()
+        (a, fa, pa), (b, fb, pb) = out
+        for key in ("face", "absorbed", "emitted"):
+            assert np.array_equal(a[key], b[key]), (form, key)
+        assert dict(a["counters"]) == dict(b["counters"]), form
+        assert np.array_equal(pa, pb), form
+        assert torch.allclose(fa, fb, rtol=1e-5, atol=1e-7 * float(fa.max())), form
+        assert a["counters"]["events"] > 0
 
 
 def test_cfg3_media_parity_sample():
