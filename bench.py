@@ -553,6 +553,69 @@ def bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_su
             "launches_per_step": 1}
 
 
+def bench_cube(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum):
+    """The homogeneous cube (1 cm, sigma_s 20, one dye, QY 0.9, pencil beam at 490 nm, 64x64x81
+    ortho film) at 1e8 paths: no grid, so tracking and connections are arithmetic alone (closed-form
+    transmittance) and the ALU roofline bounds it. The warp-regrouped form against the plain kernel
+    on the first eighth of the same path ids (same estimator: equal RMSE); the oracle on 1e7 paths
+    of the same cube (the 1e5-path parity case takes it 0.1 s, too short to time)."""
+    import torch
+    from paper_1706_03024_gb300 import shard
+    from paper_1706_03024_gb300.scene import Scene
+
+    n = int(args.cube_paths)
+    sc = sg.cfg1_homogeneous_cube(n_paths=n)
+    off, _ = shard.path_range(n, rank)
+    S = Scene(sc, device=local)
+    kw = {"form": "wavefront_warp", "block_size": 128, "regroup": 1}
+    n_plain = max(n // 8, 1)
+    S.render(n_paths=n, path_offset=off, **kw)                     # warm-up
+    S.render(n_paths=n_plain, path_offset=off, form="plain")
+    torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        ms, counters = [], None
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            counters = S.read()["counters"]
+            ms.append(a.elapsed_time(b))
+        return ms, counters
+
+    barrier()
+    ms, c = timed(lambda: S.render(n_paths=n, path_offset=off, **kw), args.cube_steps)
+    ms_p, c_p = timed(lambda: S.render(n_paths=n_plain, path_offset=off, form="plain"), 1)
+    S.close()
+    step_ms = reduce_max(sum(ms) / len(ms))
+    plain_ms = reduce_max(ms_p[0])
+    value = reduce_sum(float(c["events"])) / (step_ms / 1000.0)
+    plain_value = reduce_sum(float(c_p["events"])) / (plain_ms / 1000.0)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu, mufu, rng = rooflines(c, sum(ms) / len(ms) / 1000.0, sms,
+                               float(measured_peaks().get("sm_max_mhz", 2070.0)))
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        small = sg.cfg1_homogeneous_cube()
+        n_cpu = int(args.cube_cpu_paths)
+
+        def run(scale, threads):
+            m = max(int(n_cpu * scale), 256)
+            r = cpu_oracle_rate(small, m, n_threads=threads, film=True)
+            return r["events"], m
+        cpu = cpu_rates(run, f"{n_cpu} paths of the same cube with the film (fp64)")
+    return {"workload": f"homogeneous cube: sigma_s 20, one dye, pencil beam, 64x64x81 ortho film, {n} paths",
+            "launch": kw, "events_per_s": value, "paths_per_s": reduce_sum(float(n)) / (step_ms / 1000.0),
+            "ms_per_step": step_ms, "steps": len(ms), "ms_steps": [round(v, 3) for v in ms],
+            "plain_events_per_s": plain_value, "plain_ms": plain_ms, "plain_paths": n_plain,
+            "speedup_vs_plain": value / plain_value,
+            "per_path": {k: c[k] / n for k in ("events", "steps", "connections", "connect_steps")},
+            "roofline_alu": alu, "roofline_mufu": mufu, "roofline_rng_contract": rng,
+            "cpu_baseline": cpu, "launches_per_step": 1}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -727,6 +790,9 @@ def run_ours(args):
     sheet = None
     if not args.no_sheet:
         sheet = bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
+    cube = None
+    if not args.no_cube:
+        cube = bench_cube(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
     adjoint = None
     if not args.no_adjoint:
         adjoint = bench_adjoint(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum)
@@ -829,6 +895,7 @@ def run_ours(args):
                 "adjoint": adjoint,
                 "paper_model": paper,
                 "light_sheet": sheet,
+                "homogeneous_cube": cube,
                 "hero_wavelength": hero,
             },
             "counters_per_step": cnt_w,
@@ -844,6 +911,7 @@ def run_ours(args):
             + (0 if adjoint is None else adjoint["launches_per_step"] * args.adjoint_steps)
             + (0 if paper is None else 2 * args.paper_steps)
             + (0 if sheet is None else sheet["steps"] + 1)
+            + (0 if cube is None else cube["steps"] + 1)
             + (0 if hero is None else hero["launches"]),
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -893,7 +961,12 @@ def main():
     ap.add_argument("--no-sheet", action="store_true",
                     help="skip the full-size light-sheet workload (256^3 x 4 grids, 67M paths)")
     ap.add_argument("--sheet-steps", type=int, default=2)
-    ap.add_argument("--sheet-cpu-paths", type=int, default=1 << 18,
+    ap.add_argument("--no-cube", action="store_true",
+                    help="skip the homogeneous cube at 1e8 paths")
+    ap.add_argument("--cube-paths", type=int, default=100_000_000)
+    ap.add_argument("--cube-steps", type=int, default=2)
+    ap.add_argument("--cube-cpu-paths", type=int, default=10_000_000)
+    ap.add_argument("--sheet-cpu-paths", type=int, default=1 << 20,
                     help="light-sheet paths the CPU oracle baseline traces")
     ap.add_argument("--sheet-paths", type=int, default=0,
                     help="override the light-sheet path count (small profiling cases only)")

@@ -322,6 +322,19 @@ int fill_scene(flr_ctx *ctx, SceneDev &S, bool with_film, int macro_cell = 0, in
     }
     S.wall_gloss = m.wall_gloss;
     S.wall_exp = m.wall_exponent;
+    // the instances that settle decisions without a grid read pay where the bounds decide most
+    // steps: sigma_s + sigma_a0 (the minorant without a solvent mask) at least 0.9 of the
+    // majorant of every bin that has one (measured: the light sheet at 0.99 gains 8 %, the
+    // adjoint and paper-model media at lower albedo lose 13-16 % to the extra code)
+    S.lazy = 0;
+    if (S.grid && !S.solvent && ctx->h_tables.size() >= (size_t)tab_size(S.B)) {
+        const float *maj = ctx->h_tables.data() + tab_majorant(S.B);
+        const double smin = (double)m.sigma_s + (double)m.sigma_a0;
+        bool ok = true;
+        for (int b = 0; b < S.B && ok; ++b)
+            if (maj[b] > 0.0f && smin < 0.9 * (double)maj[b]) ok = false;
+        S.lazy = ok ? 1 : 0;
+    }
     // sensor
     const flr_sensor &c = ctx->sensor;
     S.sensor_kind = (ctx->sensor_set && with_film) ? c.kind : FLR_SENSOR_NONE;

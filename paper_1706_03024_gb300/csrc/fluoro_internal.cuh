@@ -113,6 +113,10 @@ struct SceneDev {
     int iface, dielectric;
     float ior, inv_ior, iface_exit;
     float wall_gloss, wall_exp;
+    // 1: launch the instances that settle decisions without a grid read where a bound fixes them
+    // (grids, no solvent mask, and sigma_s + sigma_a0 at least 0.9 of every bin's majorant, so
+    // that the bounds decide most steps)
+    int lazy;
 };
 
 // Per-launch run parameters.

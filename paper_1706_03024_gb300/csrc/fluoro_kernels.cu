@@ -4094,9 +4094,9 @@ cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block
         if (need < grid) grid = need;
     }
     if (grid < 1) grid = 1;
-    // media with grids and no solvent mask: the instances with the decisions taken without a grid
-    // read (minorant_known)
-    const bool lazy = !S.homogeneous && S.solvent == nullptr;
+    // the instances that take decisions without a grid read where a bound settles them
+    // (minorant_known), for the media where the bounds decide most steps (SceneDev::lazy)
+    const bool lazy = S.lazy != 0 && !S.homogeneous && S.solvent == nullptr;
     if (form == FLR_FORM_WAVEFRONT)
         k_trace_wavefront<<<(unsigned)grid, block, smem, st>>>(S, R);
     else if (form == FLR_FORM_WAVEFRONT_WARP)

@@ -181,14 +181,26 @@ def test_cfg5_light_sheet_reduced_parity():
                     launch={"block_size": 128, "regroup": 1})
 
 
-@pytest.mark.parametrize("albedo", [0.999, 0.6])
+def _minorant_ratio(sc):
+    """min over bins of (sigma_s + sigma_a0) / sigma_bar(bin): the library launches the instances
+    that skip reads for media with grids, no solvent mask and this ratio >= 0.9."""
+    md, dy = sc["medium"], sc["dyes"]
+    cmax = md["conc"].reshape(md["conc"].shape[0], -1).max(axis=1).astype(np.float64)
+    sig = np.asarray(dy["eps"], np.float64)[:, None] * np.asarray(dy["abs_shape"], np.float64)
+    smin = float(md["sigma_s"]) + float(md["sigma_a0"])
+    return float((smin / (smin + (sig * cmax[:, None]).sum(axis=0))).min())
+
+
+@pytest.mark.parametrize("albedo", [0.999, 0.99])
 def test_decisions_without_grid_reads_change_nothing(albedo):
-    """A medium without a solvent mask runs the kernel instances that skip the grid read when a
-    bound settles the decision (a sure scatter; a march whose roulette coin fails against the bound
-    of its estimate). The same medium with an all-ones mask has the same coefficients at every
-    point and runs the instances that always read: the fixed-point tallies, counters and path
-    events must be identical bit for bit, the film equal up to fp32 atomic order."""
+    """A medium without a solvent mask, whose sigma_s is most of every bin's majorant, runs the
+    kernel instances that skip the grid read when a bound settles the decision (a sure scatter; a
+    march whose roulette coin fails against the bound of its estimate). The same medium with an
+    all-ones mask has the same coefficients at every point and runs the instances that always
+    read: the fixed-point tallies, counters and path events must be identical bit for bit, the
+    film equal up to fp32 atomic order."""
     sc = sg.cfg5_light_sheet(grid=48, width=48, height=48, n_blobs=60, n_paths=1, albedo=albedo)
+    assert _minorant_ratio(sc) >= 0.9          # the skipping instances are the ones launched
     masked = dict(sc)
     med = dict(sc["medium"])
     nz, ny, nx = med["conc"].shape[1:]
