@@ -86,13 +86,15 @@ def rooflines(c, seconds, sms, sm_mhz):
     m = mufu_ops(c) / seconds
     r = rng_contract_ops(c) / seconds
     note = f"peak = {sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (maximum SM clock)"
+    src = peak_source("sm_max_mhz")
     return ({"bound": "alu", "achieved": a / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
-             "frac": a / alu_peak, "note": note},
+             "frac": a / alu_peak, "note": note, "peak_source": src},
             {"bound": "mufu", "achieved": m / 1e12, "peak": mufu_peak / 1e12, "unit": "Tops/s",
              "frac": m / mufu_peak, "ceiling_ms": 1000.0 * mufu_ops(c) / mufu_peak,
-             "note": f"peak = {sms} SMs x 16 x {sm_mhz:.0f} MHz"},
+             "note": f"peak = {sms} SMs x 16 x {sm_mhz:.0f} MHz", "peak_source": src},
             {"bound": "alu", "achieved": r / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
-             "frac": r / alu_peak, "note": "per-unit counts of the random-number contract"})
+             "frac": r / alu_peak, "note": "per-unit counts of the random-number contract",
+             "peak_source": src})
 
 
 def dist_env():
@@ -142,6 +144,14 @@ def stop_clock_sampler(proc, f, path):
         return None
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
             "samples": len(sm)}
+
+
+def peak_source(key):
+    """Where a roofline denominator comes from: the per-pod measurement, else the fallback."""
+    if key in measured_peaks():
+        return f"of measured ({key} in MEASURED_PEAKS.json)"
+    return {"hbm_gbs": "of fallback (6.8 TB/s, an earlier GB300 copy measurement)",
+            "sm_max_mhz": "of fallback (2070 MHz, the GB300's maximum SM clock)"}.get(key, "of fallback")
 
 
 def measured_peaks():
@@ -547,6 +557,7 @@ def bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_su
             "roofline_hbm_gathers": {"bound": "hbm", "achieved": alg_bytes / t / 1e9, "peak": hbm,
                                      "unit": "GB/s", "frac": alg_bytes / t / 1e9 / hbm,
                                      "sector_frac": 8 * alg_bytes / D / t / 1e9 / hbm,
+                                     "peak_source": peak_source("hbm_gbs"),
                                      "bytes_per_gather": 4 * D,
                                      "traffic": kernel_traffic(
                                          "trace_wavefront_warp_sheet_traffic.json")},
