@@ -207,12 +207,13 @@ def test_decisions_without_grid_reads_change_nothing(albedo):
     med["solvent"] = np.ones((nz, ny, nx), dtype=np.uint8)
     masked["medium"] = med
     n = 40_000
-    for form in ("plain", "wavefront_warp"):
+    for form, skip in (("plain", 0), ("wavefront_warp", 0), ("wavefront_warp", 1)):
         out = []
         for scene in (sc, masked):
             S = Scene(scene)
             pe = torch.zeros(n, dtype=torch.int32, device="cuda")
-            f = S.render(n_paths=n, form=form, path_events=pe, block_size=128, regroup=1)
+            f = S.render(n_paths=n, form=form, path_events=pe, block_size=128, regroup=1,
+                         skip_cell=skip)
             out.append((S.read(), f.clone(), pe.cpu().numpy()))
             S.close()
         (a, fa, pa), (b, fb, pb) = out
