@@ -160,7 +160,10 @@ typedef struct flr_params {
                                     ends the path (k = 1 is the paper's single inelastic event,
                                     Sec. 4.1 and V_f of Eq. 9)                                 */
     int analog;                  /* 0: weight *= QY (and wall albedo); 1: survival coins        */
-    int form;                    /* FLR_FORM_PLAIN, FLR_FORM_WAVEFRONT or FLR_FORM_WAVEFRONT_WARP */
+    int form;                    /* FLR_FORM_PLAIN, FLR_FORM_WAVEFRONT, FLR_FORM_WAVEFRONT_WARP or
+                                    FLR_FORM_WAVEFRONT_POOL (flr_render; the pool form without
+                                    macro_cell and hero); flr_render_camera and flr_adjoint take
+                                    the first three */
     int64_t max_events;          /* a real collision once n_events == max_events ends the path */
     int64_t max_steps;           /* tracking-step budget per path                               */
     float *film;                 /* device [H][W][n_bins] fp32, or NULL                         */
@@ -239,7 +242,12 @@ int flr_set_sensor(flr_ctx *ctx, const flr_sensor *sensor);
 
 /* Trace p->n_paths paths of the single scene on `stream`: face, absorption and emission tallies
  * accumulate inside the context (read them with flr_read_tallies); film contributions are added
- * to p->film already divided by p->n_paths. */
+ * to p->film already divided by p->n_paths. Every form traces the same paths (Sec. 3, Eq. 12;
+ * fixed-point tallies identical bit for bit, the film up to the order of fp32 additions). For a
+ * medium with grids, no solvent mask and sigma_s + sigma_a0 at least 0.9 of every bin's majorant,
+ * the plain and warp forms run kernels that take a decision without reading the grid where a bound
+ * settles it (sigma_t >= sigma_s + sigma_a0 everywhere: a sure scatter; a transmittance march
+ * whose roulette coin fails against the bound of its estimate); the results are the same. */
 int flr_render(flr_ctx *ctx, const flr_params *p, void *stream);
 
 /* The paper's own estimator of its single-inelastic model (Sec. 4.1-4.3, Eq. 12): paths start
