@@ -122,6 +122,25 @@ def test_noalloc_homogeneous_medium_without_grids():
     S.close()
 
 
+def test_noalloc_medium_without_mask_where_reads_are_skipped():
+    """A light-sheet medium (grids, no solvent mask, sigma_s most of every majorant): both entry
+    points launch the instances that take decisions without a grid read where a bound settles
+    them, and must agree bit for bit."""
+    require_gpu()
+    sc = sg.cfg5_light_sheet(grid=32, width=32, height=32, n_blobs=40, n_paths=20000,
+                             sigma_t_ref=20.0)
+    S = Scene(sc)
+    conc_t = torch.from_numpy(sc["medium"]["conc"]).cuda()
+    for form in ("wavefront_warp", "plain"):
+        want_film = S.render(form=form).clone()
+        want = S.read()
+        film = torch.full_like(want_film, 7.0)
+        rc, got = _noalloc(sc, conc_t, None, sc["params"]["n_paths"], form, film)
+        assert rc == N.FLR_OK, form
+        _same(got, want, film, want_film)
+    S.close()
+
+
 def test_noalloc_rejects_grids_beyond_its_static_scratch():
     require_gpu()
     sc = sg.cfg4_adjoint(grid=65, width=8, height=8, n_paths=10)
