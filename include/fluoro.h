@@ -236,6 +236,13 @@ int flr_set_sources(flr_ctx *ctx, int n, const flr_source *sources);
  * into a library-owned interleaved layout and reads their maxima back to build the per-bin
  * majorant, so this call synchronises the device. Grids must be finite and non-negative. */
 int flr_set_medium(flr_ctx *ctx, const flr_medium *medium);
+/* The same upload ordered on `stream` instead of the whole device: the grids are read on
+ * `stream` (the caller orders their writes before it), packed, and their maxima read back with
+ * one copy, which synchronises `stream` only; negative or non-finite values give FLR_ERR_ARG as
+ * above. Renders of this context still in flight on another stream must be ordered before
+ * `stream` by the caller (the upload overwrites the context's packed grid). Lets a caller
+ * overlap one context's upload and render with another context's work (a stream of scenes). */
+int flr_set_medium_async(flr_ctx *ctx, const flr_medium *medium, void *stream);
 
 /* The sensor (host struct, copied). kind NONE disables the film. */
 int flr_set_sensor(flr_ctx *ctx, const flr_sensor *sensor);

@@ -54,7 +54,7 @@ struct flr_ctx {
     unsigned long long *d_counters = nullptr;
     int *d_error = nullptr;
     unsigned long long *d_work = nullptr;
-    unsigned int *d_scratch = nullptr;  // [0] max bits, [1] flag, [2] any
+    unsigned int *d_scratch = nullptr;  // medium upload: [0..MAXD) dye maxima (bits), [MAXD] bad-value flag, [MAXD+1] solvent present
     // two-pass adjoint replay (warp-regrouped form): per-path contributions of one path chunk
     float *d_adj_ak = nullptr;
     size_t adj_ak_cap = 0;
@@ -428,7 +428,7 @@ int prepare_macro(flr_ctx *ctx, int cell, cudaStream_t st)
     return FLR_OK;
 }
 
-int prepare_tables(flr_ctx *ctx, double margin = 0.0)
+int prepare_tables(flr_ctx *ctx, double margin, cudaStream_t st)
 {
     if (margin != ctx->tables_margin) {
         ctx->tables_margin = margin;
@@ -436,8 +436,9 @@ int prepare_tables(flr_ctx *ctx, double margin = 0.0)
     }
     if (!ctx->tables_dirty) return FLR_OK;
     build_tables(ctx);
-    cudaError_t e = cudaMemcpy(ctx->d_tables, ctx->h_tables.data(), sizeof(float) * ctx->h_tables.size(),
-                               cudaMemcpyHostToDevice);
+    // ordered on the caller's stream (pageable source: staged before the call returns)
+    cudaError_t e = cudaMemcpyAsync(ctx->d_tables, ctx->h_tables.data(), sizeof(float) * ctx->h_tables.size(),
+                                    cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "upload spectral tables");
     ctx->tables_dirty = false;
     return FLR_OK;
@@ -523,7 +524,7 @@ int flr_create(flr_ctx **out, int cuda_device)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counters, sizeof(unsigned long long) * FLR_NCOUNTERS);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_error, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_work, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_scratch, sizeof(unsigned int) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_scratch, sizeof(unsigned int) * 8);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_tallies, 0, sizeof(unsigned long long) * tal_size(FLR_MAX_BINS));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * FLR_NCOUNTERS);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_error, 0, sizeof(int));
@@ -649,9 +650,11 @@ int flr_set_sources(flr_ctx *ctx, int n, const flr_source *s)
     return FLR_OK;
 }
 
-int flr_set_medium(flr_ctx *ctx, const flr_medium *m)
+// The medium upload on `st`: the grids are packed, and their maxima (and a bad-value flag and the
+// solvent mask's presence) are read back with one copy, synchronising `st`; `device_sync` keeps
+// flr_set_medium's contract of a synchronised device.
+static int set_medium_on(flr_ctx *ctx, const flr_medium *m, cudaStream_t st, bool device_sync)
 {
-    const NvtxRange nvtx_range("flr_set_medium");
     if (!ctx) return FLR_ERR_ARG;
     int vrc = validate_medium(ctx, m);
     if (vrc != FLR_OK) return vrc;
@@ -673,29 +676,32 @@ int flr_set_medium(flr_ctx *ctx, const flr_medium *m)
             if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate the interleaved grid");
             ctx->grid_cap = np;
         }
-        e = launch_pack_grid(mm.conc, mm.conc_uniform, mm.n_dyes, mm.dims, ctx->d_grid, 0);
+        e = launch_pack_grid(mm.conc, mm.conc_uniform, mm.n_dyes, mm.dims, ctx->d_grid, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "pack grids");
     }
-    for (int d = 0; d < mm.n_dyes; ++d) {
-        if (!mm.conc[d]) { cmax[d] = mm.conc_uniform[d]; continue; }
-        unsigned int h[2] = {0, 0};
-        e = cudaMemset(ctx->d_scratch, 0, sizeof(unsigned int) * 4);
-        if (e == cudaSuccess) e = launch_grid_max(mm.conc[d], n, ctx->d_scratch, (int *)(ctx->d_scratch + 1), 0);
-        if (e == cudaSuccess) e = cudaMemcpy(h, ctx->d_scratch, sizeof(h), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "grid maximum");
-        if (h[1]) return fail(ctx, FLR_ERR_ARG, "medium: concentration grid has negative or non-finite values");
-        std::memcpy(&cmax[d], &h[0], sizeof(float));
+    bool any_grid = false;
+    for (int d = 0; d < mm.n_dyes; ++d) any_grid = any_grid || mm.conc[d];
+    if (any_grid || mm.solvent) {
+        unsigned int h[MAXD + 2] = {0, 0, 0, 0, 0, 0};
+        e = cudaMemsetAsync(ctx->d_scratch, 0, sizeof(h), st);
+        for (int d = 0; d < mm.n_dyes && e == cudaSuccess; ++d)
+            if (mm.conc[d])
+                e = launch_grid_max(mm.conc[d], n, ctx->d_scratch + d, (int *)(ctx->d_scratch + MAXD), st);
+        if (e == cudaSuccess && mm.solvent) e = launch_solvent_any(mm.solvent, n, ctx->d_scratch + MAXD + 1, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, ctx->d_scratch, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "grid maxima");
+        if (h[MAXD]) return fail(ctx, FLR_ERR_ARG, "medium: concentration grid has negative or non-finite values");
+        for (int d = 0; d < mm.n_dyes; ++d)
+            if (mm.conc[d]) std::memcpy(&cmax[d], &h[d], sizeof(float));
+        if (mm.solvent) smax = h[MAXD + 1] ? 1.0f : 0.0f;
     }
-    if (mm.solvent) {
-        unsigned int h = 0;
-        e = cudaMemset(ctx->d_scratch, 0, sizeof(unsigned int) * 4);
-        if (e == cudaSuccess) e = launch_solvent_any(mm.solvent, n, ctx->d_scratch + 2, 0);
-        if (e == cudaSuccess) e = cudaMemcpy(&h, ctx->d_scratch + 2, sizeof(h), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "solvent mask");
-        smax = h ? 1.0f : 0.0f;
+    for (int d = 0; d < mm.n_dyes; ++d)
+        if (!mm.conc[d]) cmax[d] = mm.conc_uniform[d];
+    if (device_sync) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "set medium");
     }
-    e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "set medium");
     ctx->medium = mm;
     std::memcpy(ctx->cmax, cmax, sizeof(cmax));
     ctx->smax = smax;
@@ -703,6 +709,18 @@ int flr_set_medium(flr_ctx *ctx, const flr_medium *m)
     ctx->tables_dirty = true;
     ctx->mc_cell = 0;
     return FLR_OK;
+}
+
+int flr_set_medium(flr_ctx *ctx, const flr_medium *m)
+{
+    const NvtxRange nvtx_range("flr_set_medium");
+    return set_medium_on(ctx, m, 0, true);
+}
+
+int flr_set_medium_async(flr_ctx *ctx, const flr_medium *m, void *stream)
+{
+    const NvtxRange nvtx_range("flr_set_medium_async");
+    return set_medium_on(ctx, m, (cudaStream_t)stream, false);
 }
 
 int flr_set_sensor(flr_ctx *ctx, const flr_sensor *c)
@@ -770,7 +788,7 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
         if (irc != FLR_OK) return irc;
     }
     DeviceGuard g(ctx->device);
-    int rc = prepare_tables(ctx, p->majorant_margin);
+    int rc = prepare_tables(ctx, p->majorant_margin, (cudaStream_t)stream);
     if (rc != FLR_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     rc = prepare_macro(ctx, p->macro_cell > 0 ? p->macro_cell : p->skip_cell, st);
@@ -862,7 +880,7 @@ int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
         }
     }
     DeviceGuard g(ctx->device);
-    int rc = prepare_tables(ctx, 0.0);
+    int rc = prepare_tables(ctx, 0.0, (cudaStream_t)stream);
     if (rc != FLR_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     SceneDev S;
@@ -995,7 +1013,7 @@ int flr_debug_sample_emission(flr_ctx *ctx, int dye, const float *u, int64_t n, 
     if (n == 0) return FLR_OK;
     if (!is_device_pointer(u) || !is_device_pointer(out)) return fail(ctx, FLR_ERR_ARG, "sample: device buffers");
     DeviceGuard g(ctx->device);
-    int rc = prepare_tables(ctx);
+    int rc = prepare_tables(ctx, 0.0, (cudaStream_t)stream);
     if (rc != FLR_OK) return rc;
     SceneDev S;
     std::memset(&S, 0, sizeof(S));
@@ -1036,7 +1054,7 @@ int flr_debug_frozen_sums(flr_ctx *ctx, const flr_params *p, const float *adj_fi
     if (!std::isfinite(pert_delta) || !std::isfinite(pert_sigma_s))
         return fail(ctx, FLR_ERR_ARG, "frozen sums: finite perturbations");
     DeviceGuard g(ctx->device);
-    int rc = prepare_tables(ctx, p->majorant_margin);
+    int rc = prepare_tables(ctx, p->majorant_margin, (cudaStream_t)stream);
     if (rc != FLR_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     SceneDev S;
@@ -1098,7 +1116,7 @@ int flr_adjoint(flr_ctx *ctx, const flr_params *p, const float *adj_film, float 
     if (!(p->majorant_margin >= 0.0f && p->majorant_margin <= 100.0f))
         return fail(ctx, FLR_ERR_ARG, "params: majorant_margin in [0, 100]");
     DeviceGuard g(ctx->device);
-    int rc = prepare_tables(ctx, p->majorant_margin);
+    int rc = prepare_tables(ctx, p->majorant_margin, (cudaStream_t)stream);
     if (rc != FLR_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     rc = prepare_macro(ctx, p->macro_cell > 0 ? p->macro_cell : p->skip_cell, st);

@@ -94,6 +94,7 @@ SIGNATURES = {
                                C.c_void_p]),
     "flr_set_sources": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(flr_source)]),
     "flr_set_medium": (C.c_int, [C.c_void_p, C.POINTER(flr_medium)]),
+    "flr_set_medium_async": (C.c_int, [C.c_void_p, C.POINTER(flr_medium), C.c_void_p]),
     "flr_set_sensor": (C.c_int, [C.c_void_p, C.POINTER(flr_sensor)]),
     "flr_render": (C.c_int, [C.c_void_p, C.POINTER(flr_params), C.c_void_p]),
     "flr_render_camera": (C.c_int, [C.c_void_p, C.POINTER(flr_params), C.c_void_p]),
@@ -199,6 +200,10 @@ def flr_set_sources(ctx, n, sources):
 
 def flr_set_medium(ctx, medium):
     return load().flr_set_medium(ctx, C.byref(medium))
+
+
+def flr_set_medium_async(ctx, medium, stream):
+    return load().flr_set_medium_async(ctx, C.byref(medium), stream)
 
 
 def flr_set_sensor(ctx, sensor):

@@ -84,7 +84,9 @@ class Scene:
         N.check(N.flr_set_dyes(self.ctx, eps.shape[0], _np_ptr(a), _np_ptr(e), _np_ptr(eps),
                                _np_ptr(qy)), self.ctx, "flr_set_dyes")
 
-    def set_medium(self, md, grids=None):
+    def set_medium(self, md, grids=None, stream=None):
+        """Upload a medium description; grids (CUDA tensors) may replace md's host arrays. With a
+        stream, the upload is ordered on it (flr_set_medium_async) instead of the whole device."""
         m = N.flr_medium()
         m.lo[:] = md["lo"]
         m.hi[:] = md["hi"]
@@ -124,7 +126,11 @@ class Scene:
         m.ior = float(md.get("ior", 1.0))
         m.wall_gloss = float(md.get("wall_gloss", 0.0))
         m.wall_exponent = float(md.get("wall_exponent", 0.0))
-        N.check(N.flr_set_medium(self.ctx, m), self.ctx, "flr_set_medium")
+        if stream is not None:
+            N.check(N.flr_set_medium_async(self.ctx, m, stream.cuda_stream), self.ctx,
+                    "flr_set_medium_async")
+        else:
+            N.check(N.flr_set_medium(self.ctx, m), self.ctx, "flr_set_medium")
 
     def film_tensor(self):
         sn = self.sensor

@@ -45,6 +45,13 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(declared_functions()) == set(N.SIGNATURES), "binding and header disagree"
 
 
+def test_binding_forwards_every_declared_entry_point():
+    """native.py has a same-name Python function for each C entry point (argument marshalling
+    only), so no call of the boundary is reachable only through the raw library object."""
+    for name in declared_functions():
+        assert callable(getattr(N, name, None)), name
+
+
 def test_checked_build_exports_the_same_symbols(lib):
     """libfluoro_checked.so (FLR_CHECKED: device index tests) is the same boundary."""
     B.build(checked=True)
