@@ -265,13 +265,33 @@ def test_empty_ragged_and_single_path_launches():
     assert r["face"].sum() == 0 and r["counters"]["paths"] == 0
     for n in (1, 31, 257, 1001):
         pe = torch.zeros(n, dtype=torch.int32, device="cuda")
-        for form in ("plain", "wavefront"):
+        o = oracle.render(sc, n_paths=n, path_offset=12345, path_events=True)
+        for form in ("plain", "wavefront", "wavefront_warp", "wavefront_pool"):
+            pe.zero_()
             S.render(n_paths=n, path_offset=12345, form=form, path_events=pe)
             r = S.read()
-            o = oracle.render(sc, n_paths=n, path_offset=12345, path_events=True)
             assert r["counters"]["paths"] == n
             same = (pe.cpu().numpy().astype(np.uint32) == o["path_events"]).mean()
             assert same >= 0.97, (n, form, same)
+
+
+def test_ragged_launches_on_a_medium_that_skips_reads():
+    """Launches far smaller than the grid of resident warps, on a light-sheet medium whose
+    instances take decisions without grid reads: every path traced once, the same paths as the
+    oracle."""
+    sc = sg.cfg5_light_sheet(grid=32, width=16, height=16, n_blobs=40, n_paths=1, sigma_t_ref=20.0)
+    S = Scene(sc)
+    for n in (1, 33, 513):
+        pe = torch.zeros(n, dtype=torch.int32, device="cuda")
+        o = oracle.render(sc, n_paths=n, path_offset=777, path_events=True)
+        for form in ("plain", "wavefront_warp"):
+            pe.zero_()
+            S.render(n_paths=n, path_offset=777, form=form, path_events=pe, block_size=128, regroup=1)
+            r = S.read()
+            assert r["counters"]["paths"] == n
+            assert (pe.cpu().numpy() > 0).all(), (n, form)
+            same = (pe.cpu().numpy().astype(np.uint32) == o["path_events"]).mean()
+            assert same >= 0.9, (n, form, same)
 
 
 def test_scattering_only_conserves_exactly_and_empty_medium():
@@ -314,6 +334,13 @@ def test_maximum_bins_and_dyes():
     for key in ("face", "absorbed", "emitted"):
         assert bin_parity(g, o, key)["ok"], key
         assert compare_integrated(totals(g, key).sum(-1), totals(o, key).sum(-1)) <= 5e-3
+    # the warp and pool forms hold the largest tables beside their queues and pools: the same
+    # paths, so the same fixed-point tallies as the block form
+    for form in ("wavefront_warp", "wavefront_pool"):
+        gf = gpu_batches(sc, 16, 2000, form=form)
+        for a, b in zip(g, gf):
+            for key in ("face", "absorbed", "emitted"):
+                assert np.array_equal(a[key], b[key]), (form, key)
     gi = gpu_batches(sc, 16, 2000, form="wavefront", seed=99)
     for key in ("face", "absorbed", "emitted"):
         assert bin_parity(gi, o, key, same_seed=False)["ok"], key
