@@ -385,6 +385,19 @@ def test_invalid_arguments_are_rejected():
     par.block_size = 0
     par.form = 7
     assert N.flr_render(ctx, par, 0) == N.FLR_ERR_ARG
+    par.form = N.FLR_FORM_WAVEFRONT_POOL    # the pool form: one majorant per bin, one wavelength
+    par.macro_cell = 4
+    assert N.flr_render(ctx, par, 0) == N.FLR_ERR_ARG
+    par.macro_cell = 0
+    par.hero = 2
+    assert N.flr_render(ctx, par, 0) == N.FLR_ERR_ARG
+    par.form = N.FLR_FORM_WAVEFRONT_WARP
+    par.hero = 5
+    assert N.flr_render(ctx, par, 0) == N.FLR_ERR_ARG
+    par.hero = 0
+    m.conc[0] = host_grid.ctypes.data          # the stream-ordered upload validates the same way
+    assert N.flr_set_medium_async(ctx, m, 0) == N.FLR_ERR_ARG
+    assert "device memory" in N.flr_last_error(ctx)
     cam = N.flr_sensor()
     cam.kind = N.FLR_SENSOR_PINHOLE
     cam.width = cam.height = 8
