@@ -30,9 +30,17 @@ def _run_all():
           {"form": "wavefront_warp", "skip_cell": 2}, {"form": "wavefront_warp", "macro_cell": 4},
           {"form": "plain", "macro_cell": 4}, {"form": "plain", "hero": 4, "skip_cell": 1},
           {"form": "wavefront_warp", "hero": 4, "skip_cell": 1},
-          {"form": "wavefront_warp", "paper_mode": True}]),
+          {"form": "wavefront_warp", "paper_mode": True}, {"form": "wavefront_pool", "skip_cell": 1}]),
+        # grids without a solvent mask: the instances that skip reads a bound settles
         (sg.cfg5_light_sheet(grid=32, width=32, height=32, n_blobs=40, n_paths=20000,
-                             sigma_t_ref=20.0), [{"form": "wavefront_warp"}, {"form": "plain"}]),
+                             sigma_t_ref=20.0),
+         [{"form": "wavefront_warp"}, {"form": "plain"}, {"form": "wavefront_warp", "skip_cell": 1}]),
+        # dielectric faces and glossy walls
+        (sg.vial_scene(conc_gpl=1.0, ior=1.33, width=24, height=24, n_paths=20000, grid=32),
+         [{"form": f} for f in ("plain", "wavefront", "wavefront_warp", "wavefront_pool")]),
+        (sg.cfg2_cornell_box(width=32, height=32, grid=32, n_paths=20000, wall_gloss=0.5,
+                             wall_exponent=20.0),
+         [{"form": "wavefront_warp", "skip_cell": 1}, {"form": "plain"}]),
     ]
     for sc, launches in cases:
         S = Scene(sc)
