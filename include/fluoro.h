@@ -403,6 +403,16 @@ int flr_debug_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, int64_
 int flr_debug_sample_emission(flr_ctx *ctx, int dye, const float *u, int64_t n, int32_t *out,
                               void *stream);
 
+/* Debug: sigma_t(x, bin) of the current medium at n points (device [n][3] fp32, box
+ * coordinates) by the lookup every kernel uses (Sec. 4.1: s(x)(sigma_s + sigma_a0) +
+ * sum_d sig_a[d][bin] c_d(x), nearest voxel, fp32), into sigma_t (device [n] fp32), and the
+ * row-major index z*ny*nx + y*nx + x of the voxel read into voxel (device [n], may be NULL; -1
+ * for a medium without grids). Points outside the box take the nearest voxel (clamped).
+ * FLR_ERR_ARG for a bin outside [0, n_bins), n < 0 or host pointers; FLR_ERR_STATE without a
+ * medium. */
+int flr_debug_sigma_t(flr_ctx *ctx, const float *points, int64_t n, int bin, float *sigma_t,
+                      int32_t *voxel, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,5 +5,5 @@ reference legs are the only callers. The product path (paper_1706_03024_gb300) n
 """
 from .oracle import (  # noqa: F401
     COUNTER_NAMES, adjoint, build, lib, optical_depth, majorant, philox, render, render_camera,
-    sample_emission, iso_dir, cosine_dir,
+    sample_emission, sigma_t_at, iso_dir, cosine_dir,
 )

@@ -1849,6 +1849,21 @@ double or_optical_depth(const or_scene *s, const double *x0, const double *w, do
     return tau;
 }
 
+/* sigma_t(x, bin) at n points ([n][3]) by the nearest-voxel lookup the tracking uses (Sec. 4.1),
+ * and the row-major index of the voxel read (-1 for a medium without grids). */
+void or_sigma_t_at(const or_scene *s, const double *pts, int64_t n, int bin, double *out_sigma,
+                   int64_t *out_voxel)
+{
+    tables *t = (tables *)malloc(sizeof(tables));
+    build_tables(s, t);
+    for (int64_t i = 0; i < n; ++i) {
+        const double x[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+        out_sigma[i] = coeffs_at_p(s, t, x, bin, 0).total;
+        out_voxel[i] = t->homogeneous ? -1 : (int64_t)voxel_index(s, x);
+    }
+    free(t);
+}
+
 void or_majorant(const or_scene *s, double *out)
 {
     tables *t = (tables *)malloc(sizeof(tables));

@@ -110,6 +110,9 @@ def lib():
             L.or_optical_depth.restype = C.c_double
             L.or_majorant.argtypes = [C.POINTER(Scene), C.c_void_p]
             L.or_majorant.restype = None
+            L.or_sigma_t_at.argtypes = [C.POINTER(Scene), C.c_void_p, C.c_int64, C.c_int,
+                                        C.c_void_p, C.c_void_p]
+            L.or_sigma_t_at.restype = None
             L.or_adjoint.argtypes = [C.POINTER(Scene), C.POINTER(Params), C.c_void_p,
                                      C.c_void_p, C.c_void_p]
             L.or_adjoint.restype = C.c_int
@@ -344,6 +347,19 @@ def optical_depth(scene, x0, w, L, bin_index):
     w = np.ascontiguousarray(w, dtype=np.float64)
     return float(lib().or_optical_depth(C.byref(h.scene), x0.ctypes.data, w.ctypes.data,
                                         float(L), int(bin_index)))
+
+
+def sigma_t_at(scene, pts, bin_index):
+    """sigma_t at points [n, 3] in bin bin_index by the tracking's nearest-voxel lookup, and the
+    row-major voxel index read (-1 for a medium without grids)."""
+    h = _SceneHolder(scene)
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    n = pts.shape[0]
+    sig = np.zeros(n)
+    vox = np.zeros(n, dtype=np.int64)
+    lib().or_sigma_t_at(C.byref(h.scene), pts.ctypes.data, C.c_int64(n), int(bin_index),
+                        sig.ctypes.data, vox.ctypes.data)
+    return sig, vox
 
 
 def majorant(scene):

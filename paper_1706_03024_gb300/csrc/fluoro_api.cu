@@ -1023,6 +1023,26 @@ int flr_debug_sample_emission(flr_ctx *ctx, int dye, const float *u, int64_t n, 
     return e == cudaSuccess ? FLR_OK : cuda_fail(ctx, e, "sample emission");
 }
 
+int flr_debug_sigma_t(flr_ctx *ctx, const float *points, int64_t n, int bin, float *sigma_t,
+                      int32_t *voxel, void *stream)
+{
+    if (!ctx) return FLR_ERR_ARG;
+    if (ctx->B <= 0 || !ctx->medium_set) return fail(ctx, FLR_ERR_STATE, "sigma_t: spectrum, dyes and medium must be set");
+    if (bin < 0 || bin >= ctx->B || n < 0) return fail(ctx, FLR_ERR_ARG, "sigma_t: bin in [0, n_bins), n >= 0");
+    if (n == 0) return FLR_OK;
+    if (!points || !sigma_t || !is_device_pointer(points) || !is_device_pointer(sigma_t) ||
+        (voxel && !is_device_pointer(voxel)))
+        return fail(ctx, FLR_ERR_ARG, "sigma_t: points and outputs must be device memory");
+    DeviceGuard g(ctx->device);
+    int rc = prepare_tables(ctx, 0.0, (cudaStream_t)stream);
+    if (rc != FLR_OK) return rc;
+    SceneDev S;
+    rc = fill_scene(ctx, S, false);
+    if (rc != FLR_OK) return rc;
+    cudaError_t e = launch_debug_sigma_t(S, points, n, bin, sigma_t, voxel, (cudaStream_t)stream);
+    return e == cudaSuccess ? FLR_OK : cuda_fail(ctx, e, "sigma_t lookup");
+}
+
 // ---------------------------------------------------------------------------------------------
 // Adjoint by path replay.
 

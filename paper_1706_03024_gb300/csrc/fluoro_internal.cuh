@@ -234,6 +234,8 @@ cudaError_t launch_philox(uint32_t seed, uint32_t medium, const uint32_t *ctr, l
 cudaError_t launch_frozen_sums(const SceneDev &S, const RunDev &R, int pert_dye, long long pert_voxel,
                                float pert_delta, float pert_dsig, const float *adj, double *out,
                                cudaStream_t st);
+cudaError_t launch_debug_sigma_t(const SceneDev &S, const float *pts, long long n, int bin, float *out,
+                                 int32_t *vox, cudaStream_t st);
 cudaError_t launch_sample_emission(const SceneDev &S, int dye, const float *u, long long n,
                                    int32_t *out, cudaStream_t st);
 int trace_block_default();

@@ -3944,6 +3944,24 @@ __global__ void k_sample_emission(const float *__restrict__ cdf, int B, const fl
         out[i] = sample_cdf(cdf, B, u[i]);
 }
 
+// sigma_t(x, bin) of the current medium at points [n][3] by the lookup the tracking uses
+// (coeffs_at: nearest voxel, Sec. 4.1), and the row-major index of the voxel read (-1 without grids).
+__global__ void __launch_bounds__(256) k_debug_sigma_t(SceneDev S, const float *__restrict__ pts, long long n,
+                                                       int bin, float *__restrict__ out,
+                                                       int32_t *__restrict__ vox)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(S.B, FLR_FORM_PLAIN, blockDim.x);
+    const Smem sm = block_prologue(S, smem_raw, L, nullptr);
+    const MedS_<false> m{S, sm};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float3 x = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        out[i] = coeffs_at(m, x, bin).total;
+        if (vox) vox[i] = S.homogeneous ? -1 : voxel_of(m, x);
+    }
+}
+
 }  // namespace
 
 int device_sms()
@@ -4310,6 +4328,18 @@ cudaError_t launch_frozen_sums(const SceneDev &S, const RunDev &R, int pert_dye,
     if (grid < 1) grid = 1;
     PertDev P{pert_dye, pert_voxel, pert_delta, pert_dsig, adj, out};
     k_frozen_sums<<<(unsigned)grid, block, smem, st>>>(S, R, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_sigma_t(const SceneDev &S, const float *pts, long long n, int bin, float *out,
+                                 int32_t *vox, cudaStream_t st)
+{
+    long long blocks = (n + 255) / 256;
+    const long long cap = (long long)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    const int smem = trace_smem_bytes(S.B, FLR_FORM_PLAIN, 256);
+    k_debug_sigma_t<<<(unsigned)blocks, 256, smem, st>>>(S, pts, n, bin, out, vox);
     return cudaGetLastError();
 }
 
