@@ -413,6 +413,12 @@ int flr_debug_sample_emission(flr_ctx *ctx, int dye, const float *u, int64_t n, 
 int flr_debug_sigma_t(flr_ctx *ctx, const float *points, int64_t n, int bin, float *sigma_t,
                       int32_t *voxel, void *stream);
 
+/* Debug (failure injection on the host): the k-th device allocation the library makes from now on
+ * fails as out of memory (the calling entry point returns FLR_ERR_OOM, or FLR_ERR_CUDA where the
+ * failure surfaces as another CUDA error); the counter then stays at 0, and k = 0 disables it.
+ * Process-wide (all contexts, all threads). FLR_ERR_ARG for k < 0. No device fault is made. */
+int flr_debug_fail_alloc(int64_t k);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -119,6 +120,26 @@ int fail(flr_ctx *ctx, int code, const std::string &msg)
 {
     if (ctx) ctx->err = msg;
     return code;
+}
+
+// Every library-owned device buffer is allocated here. A test hook (flr_debug_fail_alloc) can make
+// the k-th following allocation fail as out of memory, so that each caller's error path runs on
+// the host without a real exhaustion; 0 (the default) leaves allocation alone.
+static std::atomic<long long> g_fail_alloc{0};
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+template <class T>
+cudaError_t dev_alloc(T **p, size_t bytes)
+{
+    return dev_alloc(reinterpret_cast<void **>(p), bytes);
 }
 
 int cuda_fail(flr_ctx *ctx, cudaError_t e, const char *what)
@@ -396,9 +417,9 @@ int prepare_macro(flr_ctx *ctx, int cell, cudaStream_t st)
         ctx->d_mc_s = nullptr;
         ctx->d_mc_dist = nullptr;
         ctx->mc_cap = 0;
-        cudaError_t e = cudaMalloc(&ctx->d_mc_c, sizeof(float4) * n);
-        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_mc_s, sizeof(float) * n);
-        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_mc_dist, n);
+        cudaError_t e = dev_alloc(&ctx->d_mc_c, sizeof(float4) * n);
+        if (e == cudaSuccess) e = dev_alloc(&ctx->d_mc_s, sizeof(float) * n);
+        if (e == cudaSuccess) e = dev_alloc(&ctx->d_mc_dist, n);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate the local-majorant grid");
         ctx->mc_cap = n;
     }
@@ -416,7 +437,7 @@ int prepare_macro(flr_ctx *ctx, int cell, cudaStream_t st)
         cudaFree(ctx->d_mc_tmp);
         ctx->d_mc_tmp = nullptr;
         ctx->mc_tmp_cap = 0;
-        e = cudaMalloc(&ctx->d_mc_tmp, n);
+        e = dev_alloc(&ctx->d_mc_tmp, n);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate the distance scratch");
         ctx->mc_tmp_cap = n;
     }
@@ -519,12 +540,12 @@ int flr_create(flr_ctx **out, int cuda_device)
     ctx->device = cuda_device;
     DeviceGuard g(cuda_device);
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tables, sizeof(float) * tab_size(FLR_MAX_BINS));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tallies, sizeof(unsigned long long) * tal_size(FLR_MAX_BINS));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counters, sizeof(unsigned long long) * FLR_NCOUNTERS);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_error, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_work, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_scratch, sizeof(unsigned int) * 8);
+    if (e == cudaSuccess) e = dev_alloc(&ctx->d_tables, sizeof(float) * tab_size(FLR_MAX_BINS));
+    if (e == cudaSuccess) e = dev_alloc(&ctx->d_tallies, sizeof(unsigned long long) * tal_size(FLR_MAX_BINS));
+    if (e == cudaSuccess) e = dev_alloc(&ctx->d_counters, sizeof(unsigned long long) * FLR_NCOUNTERS);
+    if (e == cudaSuccess) e = dev_alloc(&ctx->d_error, sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc(&ctx->d_work, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_alloc(&ctx->d_scratch, sizeof(unsigned int) * 8);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_tallies, 0, sizeof(unsigned long long) * tal_size(FLR_MAX_BINS));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * FLR_NCOUNTERS);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_error, 0, sizeof(int));
@@ -672,8 +693,11 @@ static int set_medium_on(flr_ctx *ctx, const flr_medium *m, cudaStream_t st, boo
             cudaFree(ctx->d_grid);
             ctx->d_grid = nullptr;
             ctx->grid_cap = 0;
-            e = cudaMalloc(&ctx->d_grid, sizeof(float4) * np);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate the interleaved grid");
+            e = dev_alloc(&ctx->d_grid, sizeof(float4) * np);
+            if (e != cudaSuccess) {
+                ctx->medium_set = false;   // the previous medium's grid is gone: renders need a new upload
+                return cuda_fail(ctx, e, "allocate the interleaved grid");
+            }
             ctx->grid_cap = np;
         }
         e = launch_pack_grid(mm.conc, mm.conc_uniform, mm.n_dyes, mm.dims, ctx->d_grid, st);
@@ -1023,6 +1047,13 @@ int flr_debug_sample_emission(flr_ctx *ctx, int dye, const float *u, int64_t n, 
     return e == cudaSuccess ? FLR_OK : cuda_fail(ctx, e, "sample emission");
 }
 
+int flr_debug_fail_alloc(int64_t k)
+{
+    if (k < 0) return FLR_ERR_ARG;
+    g_fail_alloc.store(k);
+    return FLR_OK;
+}
+
 int flr_debug_sigma_t(flr_ctx *ctx, const float *points, int64_t n, int bin, float *sigma_t,
                       int32_t *voxel, void *stream)
 {
@@ -1218,7 +1249,7 @@ static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem,
     cudaFree(*ptr);
     *ptr = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMalloc(ptr, std::max<size_t>(need, 1) * elem);
+    cudaError_t e = dev_alloc(ptr, std::max<size_t>(need, 1) * elem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, what);
     *cap = std::max<size_t>(need, 1);
     return FLR_OK;
@@ -1265,9 +1296,14 @@ int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const 
     if (rc == FLR_OK) rc = grow(ctx, (void **)&bt.d_tallies, &bt.tallies_cap, (size_t)n_media * tal_size(B), sizeof(unsigned long long), "batch tallies");
     if (rc == FLR_OK) rc = grow(ctx, (void **)&bt.d_media, &bt.media_cap, (size_t)n_media, sizeof(MediumDev), "batch media");
     if (rc != FLR_OK) return rc;
-    if (!bt.d_counters) {
-        cudaError_t e = cudaMalloc(&bt.d_counters, sizeof(unsigned long long) * FLR_NCOUNTERS);
-        if (e == cudaSuccess) e = cudaMalloc(&bt.d_head, sizeof(unsigned long long));
+    if (!bt.d_counters || !bt.d_head) {
+        // allocated as a pair: after a failure part-way, the next prepare starts the pair again
+        cudaFree(bt.d_counters);
+        cudaFree(bt.d_head);
+        bt.d_counters = nullptr;
+        bt.d_head = nullptr;
+        cudaError_t e = dev_alloc(&bt.d_counters, sizeof(unsigned long long) * FLR_NCOUNTERS);
+        if (e == cudaSuccess) e = dev_alloc(&bt.d_head, sizeof(unsigned long long));
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batch counters");
     }
     // pack grids, reduce maxima (slots [m][0..3] dyes, [m][4] bad-value flag, [m][5] solvent any)

@@ -124,6 +124,7 @@ SIGNATURES = {
                                             C.c_void_p, C.c_void_p]),
     "flr_debug_sigma_t": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
+    "flr_debug_fail_alloc": (C.c_int, [C.c_int64]),
     "flr_checked_build": (C.c_int, []),
     "flr_debug_check": (C.c_int, [C.c_int64, C.c_int64, C.c_void_p]),
 }
@@ -250,6 +251,10 @@ def flr_debug_check(index, bound, stream=0):
 def flr_debug_sample_emission(ctx, dye, u_ptr, n, out_ptr, stream=0):
     return load().flr_debug_sample_emission(ctx, int(dye), u_ptr, int(n), out_ptr,
                                             C.c_void_p(int(stream)))
+
+
+def flr_debug_fail_alloc(k):
+    return load().flr_debug_fail_alloc(int(k))
 
 
 def flr_debug_sigma_t(ctx, points_ptr, n, bin_index, sigma_ptr, voxel_ptr=None, stream=0):
