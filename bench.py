@@ -534,6 +534,14 @@ def bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_su
     alu, mufu, rng = rooflines(c, t, sms, float(peaks.get("sm_max_mhz", 2070.0)))
     gathers = c["steps"] + c["connect_steps"]
     D = int(sc["dyes"]["abs_shape"].shape[0])
+    # the film's L2 reduction requests: ncu's per-path count on the 2M-path capture, scaled
+    prof = kernel_profile("trace_wavefront_warp_sheet_ncu.json")
+    film_atomics = None
+    if prof and prof.get("film_red_requests_per_path"):
+        reqs = prof["film_red_requests_per_path"] * n
+        film_atomics = {"requests_per_step": reqs, "per_s": reqs / t,
+                        "source": "ncu L2 reduction requests per path on the 2M-path capture, "
+                                  "scaled to the step's paths"}
     alg_bytes = 4 * D * gathers
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -561,6 +569,8 @@ def bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_su
                                      "bytes_per_gather": 4 * D,
                                      "traffic": kernel_traffic(
                                          "trace_wavefront_warp_sheet_traffic.json")},
+            "ncu": prof,
+            "film_atomics": film_atomics,
             "launches_per_step": 1}
 
 
