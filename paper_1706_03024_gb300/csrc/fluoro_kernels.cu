@@ -1258,13 +1258,16 @@ struct SmemLayout {
 // Per-warp connection queue of the warp-regrouped form: capacity and drain threshold. A drain starts
 // once WQ_DRAIN records wait; one tracking round adds at most 32, so the queue never wraps. Longer
 // queues drain less often and amortise each drain's tail (measured on the Cornell box: 128 -> 256 ->
-// 320 records gave 26.0 -> 24.0 -> 23.6 ms per step); 320 records of 32 B per warp let five blocks
-// of 128 threads (WARP_BLOCK, at most 102 registers) share an SM's shared memory, which measured
-// 3 % faster than two blocks of 256 with 416-record queues. The adjoint's and the local-majorant
+// 320 records gave 26.0 -> 24.0 -> 23.6 ms per step, with the drains of that time); five blocks of
+// 128 threads (WARP_BLOCK, at most 102 registers) per SM measured 3 % faster than two blocks of 256
+// with 416-record queues. With drains that claim every iteration the optimum moved down: 256
+// records (drained at 224) gave 12.93 ms, against 13.14 (320 / 288), 12.97 (224 / 192), 13.2
+// (192 / 160) and 13.45 ms (160 / 128); the block count stays five (registers), and the shared
+// memory no longer held by queues is left to the L1. The adjoint's and the local-majorant
 // instances keep four blocks (128 registers): with five they spill.
 constexpr int WARP_BLOCK = 128;   // threads per block of the warp-regrouped form
-constexpr int WQ_CAP = 320;
-constexpr int WQ_DRAIN = 288;
+constexpr int WQ_CAP = 256;
+constexpr int WQ_DRAIN = 224;
 constexpr int SPAWN_MIN = 8;   // lanes that start new paths together
 static_assert(WQ_DRAIN + 31 < WQ_CAP, "warp queue overflow");
 
