@@ -248,9 +248,12 @@ int flr_set_medium_async(flr_ctx *ctx, const flr_medium *medium, void *stream);
 int flr_set_sensor(flr_ctx *ctx, const flr_sensor *sensor);
 
 /* Trace p->n_paths paths of the single scene on `stream`: face, absorption and emission tallies
- * accumulate inside the context (read them with flr_read_tallies); film contributions are added
- * to p->film already divided by p->n_paths. Every form traces the same paths (Sec. 3, Eq. 12;
- * fixed-point tallies identical bit for bit, the film up to the order of fp32 additions). For a
+ * accumulate inside the context (read them with flr_read_tallies); film contributions, already
+ * divided by p->n_paths, are summed exactly in 64-bit fixed point (units of 2^-32; at most 2^32
+ * per film value and launch) in a film-sized context buffer (8 bytes per film value, allocated on
+ * the first launch with a film), then written to p->film (accumulate = 0) or added to it when the
+ * launch ends: the film does not depend on the order of the contributions. Every form traces the
+ * same paths (Sec. 3, Eq. 12; fixed-point tallies identical bit for bit). For a
  * medium with grids, no solvent mask and sigma_s + sigma_a0 at least 0.9 of every bin's majorant,
  * the plain and warp forms run kernels that take a decision without reading the grid where a bound
  * settles it (sigma_t >= sigma_s + sigma_a0 everywhere: a sure scatter; a transmittance march
@@ -269,8 +272,8 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream);
  * p->paper_mode = 1. Path id i renders pixel i mod (W*H): p->n_paths and p->path_offset must be
  * multiples of W*H. Uses n_paths, path_offset, seed, medium_id, n_rr, analog, max_events,
  * max_steps, film, accumulate (0 clears the film and the counters), block_size and form
- * (FLR_FORM_PLAIN: one thread per path; the wavefront forms: warp-regrouped light samples, the
- * same film up to the order of fp32 additions); the rest is ignored. Requires a sensor and dyes, and sources of non-zero area (a pencil beam has no fluence
+ * (FLR_FORM_PLAIN: one thread per path; the wavefront forms: warp-regrouped light samples; the
+ * film summed in fixed point as flr_render sums it); the rest is ignored. Requires a sensor and dyes, and sources of non-zero area (a pencil beam has no fluence
  * density a camera path could meet: FLR_ERR_ARG). sigma_t must be positive wherever a dye is (the
  * dyes dissolved in a scattering solvent, the paper's setting): the collision estimator cannot
  * see emission where the medium never collides. Counters: paths, events (real collisions and wall
@@ -367,7 +370,9 @@ int flr_render_batch(flr_ctx *ctx, int n_media, const flr_medium *media, const u
  * must start at zero, so calls that overlap on the GPU (other streams, other host threads) race
  * with each other. The call synchronises `stream` (it reads grid maxima and the tallies back).
  * It returns FLR_ERR_BUDGET (outputs written) when a path or a connection ran out of its step
- * budget, and in the checked build FLR_ERR_CHECK when a device index was out of range. */
+ * budget, and in the checked build FLR_ERR_CHECK when a device index was out of range. With no
+ * room for a fixed-point accumulator, film contributions go to p->film by fp32 atomics: the film
+ * equals flr_render's up to the order (and rounding) of fp32 additions. */
 #define FLR_NOALLOC_MAX_VOXELS (1 << 18)
 int flr_render_noalloc(float lambda0_nm, float dlambda_nm, int n_bins, int n_dyes,
                        const float *abs_shape, const float *emit_spec, const float *eps,

@@ -63,6 +63,8 @@ struct flr_ctx {
     size_t adj_ovf_cap = 0;
     unsigned long long *d_adj_tal = nullptr;  // the replays' tallies (written, never read)
     size_t adj_tal_cap = 0;
+    unsigned long long *d_film_fx = nullptr;  // a launch's film sums in fixed point (film-sized)
+    size_t film_fx_cap = 0;
     uint64_t paths_since_clear = 0;
     std::vector<float> h_tables;
     // local majorants of the current medium (built on demand for one cell size)
@@ -135,6 +137,7 @@ cudaError_t dev_alloc(void **p, size_t bytes)
     }
     return cudaMalloc(p, bytes);
 }
+
 
 template <class T>
 cudaError_t dev_alloc(T **p, size_t bytes)
@@ -570,6 +573,7 @@ void flr_destroy(flr_ctx *ctx)
     cudaFree(ctx->d_adj_ak);
     cudaFree(ctx->d_adj_ovf);
     cudaFree(ctx->d_adj_tal);
+    cudaFree(ctx->d_film_fx);
     cudaFree(ctx->d_grid);
     cudaFree(ctx->d_mc_c);
     cudaFree(ctx->d_mc_s);
@@ -774,6 +778,11 @@ int flr_set_sensor(flr_ctx *ctx, const flr_sensor *c)
     return FLR_OK;
 }
 
+static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem, const char *what);
+
+// Zeroes the context's film accumulator for a launch over n film values (grown on demand).
+static int film_accumulator(flr_ctx *ctx, size_t n, cudaStream_t st);
+
 int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
 {
     const NvtxRange nvtx_range("flr_render");
@@ -821,15 +830,22 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     rc = fill_scene(ctx, S, p->film != nullptr, p->macro_cell, p->skip_cell);
     if (rc != FLR_OK) return rc;
     cudaError_t e = cudaSuccess;
+    const bool film_on = p->film && S.sensor_kind != FLR_SENSOR_NONE;
+    const size_t n_film = film_on ? (size_t)S.W * S.H * S.B : 0;
     if (!p->accumulate) {
         e = cudaMemsetAsync(ctx->d_tallies, 0, sizeof(unsigned long long) * tal_size(FLR_MAX_BINS), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * FLR_NCOUNTERS, st);
-        if (e == cudaSuccess && p->film && S.sensor_kind != FLR_SENSOR_NONE)
-            e = cudaMemsetAsync(p->film, 0, sizeof(float) * (size_t)S.W * S.H * S.B, st);
+        // a launch with paths writes every film value when it folds its sums
+        if (e == cudaSuccess && film_on && p->n_paths == 0)
+            e = cudaMemsetAsync(p->film, 0, sizeof(float) * n_film, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "clear tallies");
         ctx->paths_since_clear = 0;
     }
     if (p->n_paths == 0) return FLR_OK;
+    if (film_on) {
+        rc = film_accumulator(ctx, n_film, st);
+        if (rc != FLR_OK) return rc;
+    }
     e = cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reset work counter");
     RunDev R;
@@ -845,7 +861,8 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     R.max_events = p->max_events;
     R.max_steps = p->max_steps;
     R.film_scale = (float)(1.0 / (double)p->n_paths);
-    R.film = S.sensor_kind != FLR_SENSOR_NONE ? p->film : nullptr;
+    R.film = film_on ? p->film : nullptr;
+    R.film_fx = film_on ? ctx->d_film_fx : nullptr;
     R.path_events = p->path_events;
     R.tallies = ctx->d_tallies;
     R.counters = ctx->d_counters;
@@ -856,6 +873,10 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     R.hero = p->hero;
     e = launch_trace(S, R, p->form, p->block_size, p->blocks_per_sm, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch trace kernel");
+    if (film_on) {
+        e = launch_film_fold(p->film, ctx->d_film_fx, n_film, p->accumulate ? 1 : 0, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "fold film sums");
+    }
     ctx->paths_since_clear += p->n_paths;
     return FLR_OK;
 }
@@ -911,12 +932,16 @@ int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
     rc = fill_scene(ctx, S, true, 0, 0);
     if (rc != FLR_OK) return rc;
     cudaError_t e = cudaSuccess;
+    const size_t n_film = (size_t)S.W * S.H * S.B;
     if (!p->accumulate) {
         e = cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * FLR_NCOUNTERS, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(p->film, 0, sizeof(float) * (size_t)S.W * S.H * S.B, st);
+        // a launch with paths writes every film value when it folds its sums
+        if (e == cudaSuccess && p->n_paths == 0) e = cudaMemsetAsync(p->film, 0, sizeof(float) * n_film, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "clear film");
     }
     if (p->n_paths == 0) return FLR_OK;
+    rc = film_accumulator(ctx, n_film, st);
+    if (rc != FLR_OK) return rc;
     // the kernel's block tallies are flushed into a scratch copy: the camera estimator has none
     rc = grow(ctx, (void **)&ctx->d_adj_tal, &ctx->adj_tal_cap, (size_t)tal_size(FLR_MAX_BINS),
               sizeof(unsigned long long), "camera tallies");
@@ -934,6 +959,7 @@ int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
     R.max_steps = p->max_steps;
     R.film_scale = (float)((double)npix / (double)p->n_paths);
     R.film = p->film;
+    R.film_fx = ctx->d_film_fx;
     R.tallies = ctx->d_adj_tal;
     R.counters = ctx->d_counters;
     R.error_word = ctx->d_error;
@@ -941,6 +967,8 @@ int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
     e = cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = launch_camera(S, R, p->form, p->block_size, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch camera kernel");
+    e = launch_film_fold(p->film, ctx->d_film_fx, n_film, p->accumulate ? 1 : 0, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fold film sums");
     return FLR_OK;
 }
 
@@ -1053,6 +1081,7 @@ int flr_debug_fail_alloc(int64_t k)
     g_fail_alloc.store(k);
     return FLR_OK;
 }
+
 
 int flr_debug_sigma_t(flr_ctx *ctx, const float *points, int64_t n, int bin, float *sigma_t,
                       int32_t *voxel, void *stream)
@@ -1253,6 +1282,15 @@ static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem,
     if (e != cudaSuccess) return cuda_fail(ctx, e, what);
     *cap = std::max<size_t>(need, 1);
     return FLR_OK;
+}
+
+static int film_accumulator(flr_ctx *ctx, size_t n, cudaStream_t st)
+{
+    const int rc = grow(ctx, (void **)&ctx->d_film_fx, &ctx->film_fx_cap, n, sizeof(unsigned long long),
+                        "film accumulator");
+    if (rc != FLR_OK) return rc;
+    const cudaError_t e = cudaMemsetAsync(ctx->d_film_fx, 0, sizeof(unsigned long long) * n, st);
+    return e == cudaSuccess ? FLR_OK : cuda_fail(ctx, e, "clear film accumulator");
 }
 
 int flr_batch_prepare(flr_ctx *ctx, int n_media, const flr_medium *media, const uint64_t *n_paths,

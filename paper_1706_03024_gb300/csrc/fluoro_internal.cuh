@@ -127,6 +127,8 @@ struct RunDev {
     long long max_events, max_steps;
     float film_scale;                  // 1 / n_paths
     float *film;
+    unsigned long long *film_fx;       // the launch's film sums in fixed point (FILM_FX_ONE), or
+                                       // NULL: contributions go to `film` by fp32 atomics
     uint32_t *path_events;
     unsigned long long *tallies;       // tal_size(B)
     unsigned long long *counters;      // FLR_NCOUNTERS
@@ -214,6 +216,12 @@ cudaError_t launch_adjoint_warp(const SceneDev &S, const RunDev &R, const AdjDev
 cudaError_t launch_batch(const BatchDev &Bt, const RunDev &R, int block, int blocks_per_sm,
                          cudaStream_t st);
 int batch_occupancy_blocks_per_sm(int block);
+// Film contributions are summed per launch as integers in units of 2^-32 of the film's unit: exact,
+// so the sum does not depend on the order of the additions (up to 2^32 per film value).
+constexpr float FILM_FX_ONE = 4294967296.0f;
+constexpr double FILM_FX_INV = 1.0 / 4294967296.0;
+// film[j] = fx[j] * 2^-32 (add = 0) or film[j] + fx[j] * 2^-32 (add = 1), j < n, through fp64.
+cudaError_t launch_film_fold(float *film, const unsigned long long *fx, size_t n, int add, cudaStream_t st);
 cudaError_t launch_trace(const SceneDev &S, const RunDev &R, int form, int block, int blocks_per_sm,
                          cudaStream_t st);
 cudaError_t launch_build_macro(const float4 *grid, float4 uniform, const uint8_t *solvent,

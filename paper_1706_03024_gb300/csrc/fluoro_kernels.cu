@@ -145,10 +145,21 @@ __device__ __forceinline__ bool check_index(bool ok, int site, long long idx)
 #define FLR_CHK(ok, site, idx) true
 #endif
 
-// Film accumulation (fp32 atomics) at index idx of the [H][W][B] film.
+// Film accumulation at index idx of the [H][W][B] film. With an accumulator (R.film_fx) a
+// contribution adds round(val * 2^32) to a 64-bit integer, so the launch's sum is exact: a bin that
+// millions of paths reach keeps every contribution (an fp32 sum stops growing once the bin exceeds
+// 2^24 times a contribution), the result does not depend on the order of the additions, and the
+// L2 serialises integer additions to one address faster than fp32 ones. Without an accumulator
+// (the no-allocation entry point) the contribution goes to the fp32 film directly.
 __device__ __forceinline__ void film_add(const SceneDev &S, const RunDev &R, size_t idx, float val)
 {
-    if (FLR_CHK(idx < (size_t)S.W * S.H * S.B, CK_FILM, (long long)idx)) atomicAdd(&R.film[idx], val);
+    if (!FLR_CHK(idx < (size_t)S.W * S.H * S.B, CK_FILM, (long long)idx)) return;
+    if (R.film_fx == nullptr) {
+        atomicAdd(&R.film[idx], val);
+        return;
+    }
+    const unsigned long long fx = __float2ull_rn(val * FILM_FX_ONE);
+    if (fx) atomicAdd(&R.film_fx[idx], fx);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -3947,6 +3958,38 @@ __global__ void k_sample_emission(const float *__restrict__ cdf, int B, const fl
         out[i] = sample_cdf(cdf, B, u[i]);
 }
 
+// Folds a launch's fixed-point film sums into the fp32 film: film[j] = fx[j] 2^-32, or
+// film[j] + fx[j] 2^-32 when the launch adds to the film (one fp32 rounding per value and launch).
+// Two values per thread and iteration as 16-byte loads of the sums when both buffers allow it.
+__global__ void __launch_bounds__(256) k_film_fold(float *__restrict__ film,
+                                                   const unsigned long long *__restrict__ fx,
+                                                   long long n, int add)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(film) & 7) | (reinterpret_cast<uintptr_t>(fx) & 15)) == 0;
+    long long done = 0;
+    if (vec) {
+        const long long pairs = n / 2;
+        for (long long i = first; i < pairs; i += stride) {
+            const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(fx) + i);
+            float2 f = make_float2((float)((double)v.x * FILM_FX_INV), (float)((double)v.y * FILM_FX_INV));
+            float2 *o = reinterpret_cast<float2 *>(film) + i;
+            if (add) {
+                const float2 g = *o;
+                f.x = g.x + f.x;
+                f.y = g.y + f.y;
+            }
+            *o = f;
+        }
+        done = pairs * 2;
+    }
+    for (long long j = done + first; j < n; j += stride) {
+        const float f = (float)((double)fx[j] * FILM_FX_INV);
+        film[j] = add ? film[j] + f : f;
+    }
+}
+
 // sigma_t(x, bin) of the current medium at points [n][3] by the lookup the tracking uses
 // (coeffs_at: nearest voxel, Sec. 4.1), and the row-major index of the voxel read (-1 without grids).
 __global__ void __launch_bounds__(256) k_debug_sigma_t(SceneDev S, const float *__restrict__ pts, long long n,
@@ -4343,6 +4386,17 @@ cudaError_t launch_debug_sigma_t(const SceneDev &S, const float *pts, long long 
     if (blocks < 1) blocks = 1;
     const int smem = trace_smem_bytes(S.B, FLR_FORM_PLAIN, 256);
     k_debug_sigma_t<<<(unsigned)blocks, 256, smem, st>>>(S, pts, n, bin, out, vox);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_film_fold(float *film, const unsigned long long *fx, size_t n, int add, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    long long blocks = ((long long)n / 2 + 255) / 256;
+    const long long cap = (long long)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_film_fold<<<(unsigned)blocks, 256, 0, st>>>(film, fx, (long long)n, add);
     return cudaGetLastError();
 }
 
