@@ -53,7 +53,7 @@ def test_slab_closed_form_gpu_camera_and_light_paper_mode():
 
 def test_camera_forms_agree():
     """The plain and the warp-regrouped camera forms draw the same random numbers for the same
-    paths: the same film up to the order of fp32 additions."""
+    paths: the same film (fixed-point sums)."""
     sc = sg.paper_mode_scene(n=32, width=16)
     S = Scene(sc)
     n = 256 * 500
@@ -128,7 +128,7 @@ def test_camera_rejects_bad_arguments():
 
 def test_camera_full_size_invariants():
     """A 64^3 grid, 256x256 film, 8 paths per pixel: finite, non-negative, deterministic for a
-    fixed seed up to the fp32 film atomics, and its total within 5 % of the paper-mode light
+    fixed seed (the film's sums are fixed point), and its total within 5 % of the paper-mode light
     tracer's at the same size (the two estimators' batch errors are both below 1 % here)."""
     sc = sg.paper_mode_scene(n=64, width=256)
     S = Scene(sc)

@@ -108,7 +108,7 @@ BENCH_LAUNCH = {"form": "wavefront_warp", "block_size": 128, "regroup": 1}
 @pytest.mark.parametrize("case", range(7))
 def test_warp_form_equals_plain_form(case):
     """The warp-regrouped hero kernel traces the same paths and marches as the plain one: identical
-    fixed-point tallies, counters and per-path event counts, the same film up to atomic order; with
+    fixed-point tallies, counters and per-path event counts, the same film (fixed-point sums); with
     one member it is the single-wavelength warp kernel."""
     name, sc, kw = workloads()[case]
     S = Scene(sc)

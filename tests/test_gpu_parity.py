@@ -143,8 +143,8 @@ def test_cfg2_pool_form_parity_and_equality_with_the_warp_form():
 
 def test_pool_form_at_full_size_equals_the_warp_form():
     """All 4,194,304 Cornell-box paths: the pool form's fixed-point tallies and per-path event
-    counts equal the benchmarked warp form's bit for bit, and the films agree up to the order of
-    the fp32 film atomics."""
+    counts equal the benchmarked warp form's bit for bit, and the films agree (bit for bit, by the
+    fixed-point film sums; test_gpu_film.py asserts that on smaller launches)."""
     sc = sg.cfg2_cornell_box()
     n = sc["params"]["n_paths"]
     S = Scene(sc)
@@ -198,7 +198,7 @@ def test_decisions_without_grid_reads_change_nothing(albedo):
     march whose roulette coin fails against the bound of its estimate). The same medium with an
     all-ones mask has the same coefficients at every point and runs the instances that always
     read: the fixed-point tallies, counters and path events must be identical bit for bit, the
-    film equal up to fp32 atomic order."""
+    films agree (their sums are fixed point)."""
     sc = sg.cfg5_light_sheet(grid=48, width=48, height=48, n_blobs=60, n_paths=1, albedo=albedo)
     assert _minorant_ratio(sc) >= 0.9          # the skipping instances are the ones launched
     masked = dict(sc)

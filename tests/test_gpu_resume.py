@@ -1,7 +1,7 @@
 """Checkpoint and resume of a render. The tallies are additive and every random number is a
 function of (seed, medium, path id, step, slot), so a render split at any path id and resumed with
-accumulation gives the uninterrupted render's fixed-point tallies bit for bit, and its film up to the
-order of fp32 additions; a checkpoint is (tallies, film, next path id)."""
+accumulation gives the uninterrupted render's fixed-point tallies bit for bit, and its film up to one
+fp32 rounding per launch (each launch folds its exact sums into the fp32 film); a checkpoint is (tallies, film, next path id)."""
 import numpy as np
 import pytest
 

@@ -5,7 +5,8 @@ framework's caching pool that has reserved the GPU), or they run under a fixed m
 forbids allocation at run time. This entry point keeps all of its scratch in one static device
 array instead. Here it must give what the allocating entry points give (flr_render followed by
 flr_read_tallies) on the same paths: the same fixed-point tallies, bit for bit, and the same film
-within fp32 atomic reordering -- on two calls in a row, since every call reuses the array -- in
+up to fp32 rounding (this entry point adds contributions by fp32 atomics, flr_render sums them in
+fixed point) -- on two calls in a row, since every call reuses the array -- in
 every launch form, with and without grids. Settings it cannot honour are rejected, and a path cut
 short at its step budget is reported.
 This file is collected last so that a stop-at-first-failure run has already run everything else.
