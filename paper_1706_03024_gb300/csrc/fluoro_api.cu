@@ -881,8 +881,6 @@ int flr_render(flr_ctx *ctx, const flr_params *p, void *stream)
     return FLR_OK;
 }
 
-static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem, const char *what);
-
 int flr_render_camera(flr_ctx *ctx, const flr_params *p, void *stream)
 {
     const NvtxRange nvtx_range("flr_render_camera");
@@ -1105,8 +1103,6 @@ int flr_debug_sigma_t(flr_ctx *ctx, const float *points, int64_t n, int bin, flo
 
 // ---------------------------------------------------------------------------------------------
 // Adjoint by path replay.
-
-static int grow(flr_ctx *ctx, void **ptr, size_t *cap, size_t need, size_t elem, const char *what);
 
 int flr_debug_frozen_sums(flr_ctx *ctx, const flr_params *p, const float *adj_film, int pert_dye,
                           int64_t pert_voxel, float pert_delta, float pert_sigma_s, double *out,
