@@ -75,6 +75,32 @@ def rng_contract_ops(c):
     return sum(c[k] * v for k, v in RNG_OPS.items())
 
 
+# A render with a film launches the trace kernel and the fold of its fixed-point film sums.
+FILM_RENDER_LAUNCHES = 2
+
+
+def count_launches(steps, plain_renders, batched, adjoint, paper, paper_steps, sheet, cube, hero,
+                   adjoint_steps):
+    """The library's kernel launches inside the timed regions: the Cornell box's timed and
+    kernel-only steps and its plain renders (a film each), the batch (no film: one launch per
+    graph replay, one per medium for the plain baseline), the adjoint's passes (no film), the
+    paper model's camera and light renders, the light sheet's and the cube's timed renders and
+    their plain baselines, and the hero forms' renders."""
+    n = FILM_RENDER_LAUNCHES * (2 * steps + plain_renders)
+    if batched is not None:
+        n += batched["steps"] + batched["plain_launches"]
+    if adjoint is not None:
+        n += adjoint["launches_per_step"] * adjoint_steps
+    if paper is not None:
+        n += 2 * paper["launches_per_step"] * paper_steps
+    for w in (sheet, cube):
+        if w is not None:
+            n += w["launches_per_step"] * (w["steps"] + 1)
+    if hero is not None:
+        n += hero["launches"]
+    return n
+
+
 def rooflines(c, seconds, sms, sm_mhz):
     """ALU roofline of one launch from its counters (headline), its MUFU ceiling and the ALU
     figure under the random-number contract's counts. peak ALU = SMs x 128 lanes x clock; peak
@@ -483,7 +509,7 @@ def bench_paper(args, local, rank, flush, stream, barrier, reduce_max, reduce_su
                                  "rmse": light_rmse},
             "camera_over_light_at_equal_rmse": eff_cam / eff_light,
             "reference": "mean of 8 camera (16 spp) and 8 light-tracer (4.2M paths) films, other seeds",
-            "launches_per_step": 1}
+            "launches_per_step": FILM_RENDER_LAUNCHES}
 
 
 def bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum):
@@ -571,7 +597,7 @@ def bench_sheet(args, local, rank, flush, stream, barrier, reduce_max, reduce_su
                                          "trace_wavefront_warp_sheet_traffic.json")},
             "ncu": prof,
             "film_atomics": film_atomics,
-            "launches_per_step": 1}
+            "launches_per_step": FILM_RENDER_LAUNCHES}
 
 
 def bench_cube(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum):
@@ -634,7 +660,7 @@ def bench_cube(args, local, rank, flush, stream, barrier, reduce_max, reduce_sum
             "speedup_vs_plain": value / plain_value,
             "per_path": {k: c[k] / n for k in ("events", "steps", "connections", "connect_steps")},
             "roofline_alu": alu, "roofline_mufu": mufu, "roofline_rng_contract": rng,
-            "cpu_baseline": cpu, "launches_per_step": 1}
+            "cpu_baseline": cpu, "launches_per_step": FILM_RENDER_LAUNCHES}
 
 
 def run_ours(args):
@@ -781,7 +807,7 @@ def run_ours(args):
                 "efficiency_plain_hero4_over_plain_single": eff["plain_hero4"] / eff["plain_single"],
                 "equal_rmse_time_ms": {"warp_single": hero_ms["warp_single"],
                                        "warp_hero4": hero_ms["warp_hero4"] * (hero_rmse["warp_hero4"] / hero_rmse["warp_single"]) ** 2},
-                "launches": 3 * args.hero_steps}
+                "launches": 3 * args.hero_steps * FILM_RENDER_LAUNCHES}
 
     def reduce_max(x):
         return shard.reduce_scalar(x, "max", device=dev)
@@ -876,8 +902,9 @@ def run_ours(args):
     ctxs[1].close()
     S.set_medium(md)
 
-    # the trace kernel alone: the same launches without the tally and film clears (accumulate),
-    # timed with CUDA events on the launching stream
+    # the trace kernel: the same renders without the tally and film clears (accumulate), timed with
+    # CUDA events on the launching stream; the span also holds the film accumulator's clear and the
+    # fold of its sums into the film (about 0.07 ms of the Cornell box's 13 ms)
     kevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             for _ in range(args.steps)]
     for i in range(args.steps):
@@ -958,13 +985,9 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                     "how": "two contexts on two streams, step k+1 issued before step k is read",
                     "serial_value": serial_value},
-            "gpu_launches": 2 * args.steps + len(ms_p) + len(ms_pl)
-            + (0 if batched is None else batched["steps"] + batched["plain_launches"])
-            + (0 if adjoint is None else adjoint["launches_per_step"] * args.adjoint_steps)
-            + (0 if paper is None else 2 * args.paper_steps)
-            + (0 if sheet is None else sheet["steps"] + 1)
-            + (0 if cube is None else cube["steps"] + 1)
-            + (0 if hero is None else hero["launches"]),
+            "gpu_launches": count_launches(args.steps, len(ms_p) + len(ms_pl), batched, adjoint,
+                                           paper, args.paper_steps, sheet, cube, hero,
+                                           args.adjoint_steps),
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

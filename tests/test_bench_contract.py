@@ -70,3 +70,15 @@ def test_traffic_is_keyed_to_the_kernel_sources(tmp_path, monkeypatch):
     src.write_text("kernel v2")
     assert bench.kernel_traffic("t.json") is None
     assert bench.kernel_profile("p.json") is None
+
+
+def test_launch_count_includes_the_film_folds():
+    """Every render with a film launches the trace kernel and the fold of its fixed-point film sums;
+    the batch and the adjoint have no film."""
+    assert bench.FILM_RENDER_LAUNCHES == 2
+    none = bench.count_launches(20, 10, None, None, None, 3, None, None, None, 3)
+    assert none == 2 * (2 * 20 + 10)
+    n = bench.count_launches(20, 10, {"steps": 3, "plain_launches": 256}, {"launches_per_step": 5},
+                             {"launches_per_step": 2}, 3, {"launches_per_step": 2, "steps": 2},
+                             {"launches_per_step": 2, "steps": 2}, {"launches": 12}, 3)
+    assert n == none + (3 + 256) + 5 * 3 + 2 * 2 * 3 + 2 * (2 + 1) + 2 * (2 + 1) + 12
